@@ -1,0 +1,160 @@
+/*
+ * fmm.h -- C ABI of the GB300 (sm_103a) fused Strassen GEMM library.
+ *
+ * Operation (Section 1, Eq. 1 and its 2x2 partitioned form, Eq. 2):
+ *
+ *     C = alpha * A * B + beta * C
+ *
+ * with A (m x k), B (k x n), C (m x n), all ROW-MAJOR with leading dimensions
+ * lda >= k, ldb >= n, ldc >= n (elements, not bytes).  `levels` selects how
+ * many levels of Strassen's algorithm are applied:
+ *
+ *   levels = 0  classical product (the library's own comparator GEMM);
+ *   levels = 1  the seven products of Section 3, Eq. (3): each product
+ *               M_r = (sum_q U[q,r] A_q)(sum_q V[q,r] B_q) is accumulated
+ *               into every C quadrant it feeds, C_q += alpha*W[q,r]*M_r;
+ *   levels = 2  the 49 two-level products (Section 3.4), i.e. the Kronecker
+ *               square of the one-level table.
+ *
+ * Fringes (Section 3.5): each dimension d is padded with implicit zeros to
+ * 2^L * h, h = roundup(ceil(d / 2^L), 8); padded rows and columns are never
+ * read from or written to memory.
+ *
+ * Conventions shared by every entry point
+ *  - Pointers A, B, C, workspace are DEVICE pointers owned by the caller; the
+ *    library keeps no reference after the call returns.  `stream` is a
+ *    cudaStream_t passed as void*; NULL means the legacy default stream.
+ *  - Launches are asynchronous on `stream`.  A non-FMM_OK return means nothing
+ *    was launched.  Faults detected on the device (a bounded wait that timed
+ *    out) are reported by fmm_device_status().
+ *  - beta == 0 means C is not read (BLAS convention): NaN/Inf in C vanish.
+ *  - m, n or k == 0 is allowed; k == 0 only scales C by beta.
+ *  - C must not overlap A, B or the workspace (FMM_ERR_ARG).
+ *  - The fmm_gemm* entry points never allocate device memory; the workspace
+ *    they need is sized by fmm_workspace_size*() and passed in.
+ */
+#ifndef FMM_GB300_H
+#define FMM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum fmm_status {
+    FMM_OK = 0,
+    FMM_ERR_ARG = 1,          /* invalid argument (sizes, strides, aliasing) */
+    FMM_ERR_ALIGN = 2,        /* alignment the selected algorithm needs is missing */
+    FMM_ERR_UNSUPPORTED = 3,  /* combination not built (variant, levels, algo) */
+    FMM_ERR_WORKSPACE = 4,    /* workspace missing or smaller than required */
+    FMM_ERR_CUDA = 5,         /* a CUDA runtime/driver call failed */
+    FMM_ERR_TIMEOUT = 6       /* a device-side bounded wait gave up */
+} fmm_status;
+
+/* Arithmetic of the sub-products.  PAPER: FP32 SIMT only (Section 2.3); the
+ * tensor-core precisions below are this library's GB300 re-design. */
+typedef enum fmm_variant {
+    /* A, B, C float32.  Operand sums are formed in FP32, split into
+     * hi = bf16(P), lo = bf16(P - hi); each product is hi*hi + hi*lo + lo*hi
+     * on BF16 tensor cores with FP32 accumulation (FP32-accurate). */
+    FMM_F32_SPLIT3_BF16 = 0,
+    /* A, B bfloat16; C float32.  Sums formed in FP32, rounded once to BF16. */
+    FMM_BF16 = 1,
+    /* A, B float16; C float32.  Sums formed in FP32, scaled by a power of two
+     * per (product, 128-row / column panel) so that they fit FP16, rounded once;
+     * the scale is undone exactly in the epilogue. */
+    FMM_F16_SCALED = 2,
+    /* A, B, C float32.  Sums formed in FP32, rounded once to BF16. */
+    FMM_F32_PLAIN_BF16 = 3
+} fmm_variant;
+
+/* Where the operand linear combinations are formed. */
+typedef enum fmm_algo {
+    FMM_ALGO_AUTO = 0,
+    /* Operand sums of all 7^L products are formed by one streaming pass over
+     * A and B and stored (already rounded/split) in the workspace; the
+     * tensor-core kernel then loads them with TMA.  Handles any alignment. */
+    FMM_ALGO_PACKED = 1,
+    /* Operand sums are formed on chip while tiles are loaded (Section 3.1):
+     * TMA stages the W_A (W_B) source tiles, transform warps add them with
+     * their signs, round/split, and feed the tensor cores.  No workspace.
+     * Needs lda, ldb multiples of 4 (FP32) / 8 (16-bit) and 16-byte aligned
+     * A, B. */
+    FMM_ALGO_FUSED = 2,
+    /* levels == 2 only: top-level sums materialised in FP32 in the workspace
+     * (Section 3.4, hybrid), bottom level fused as in FMM_ALGO_FUSED. */
+    FMM_ALGO_HYBRID = 3
+} fmm_algo;
+
+typedef struct fmm_options {
+    int algo;       /* fmm_algo; 0 = automatic choice */
+    int tile_n;     /* 0 = automatic; otherwise 128 or 256 */
+    int num_ctas;   /* 0 = one persistent CTA per SM */
+    int reserved[5];
+} fmm_options;
+
+/* Bytes of workspace fmm_gemm needs for this problem (0 when none).  Returns
+ * (size_t)-1 for an unsupported combination. */
+size_t fmm_workspace_size(int64_t m, int64_t n, int64_t k, int levels, int variant);
+size_t fmm_workspace_size_ex(int64_t m, int64_t n, int64_t k, int levels, int variant,
+                             const fmm_options* opt);
+
+/* C = alpha*A*B + beta*C with `levels` Strassen levels (0, 1 or 2) in the
+ * arithmetic `variant` (fmm_variant).  A and B have the element type the
+ * variant names; C is float32.  `workspace` (device, >= 256-byte aligned) must
+ * hold fmm_workspace_size() bytes; it may be NULL when that size is 0. */
+fmm_status fmm_gemm(int64_t m, int64_t n, int64_t k, float alpha,
+                    const void* A, int64_t lda, const void* B, int64_t ldb,
+                    float beta, float* C, int64_t ldc, int levels, int variant,
+                    void* workspace, size_t ws_bytes, void* stream);
+
+/* As fmm_gemm, with explicit algorithm and tile options (NULL = defaults). */
+fmm_status fmm_gemm_ex(int64_t m, int64_t n, int64_t k, float alpha,
+                       const void* A, int64_t lda, const void* B, int64_t ldb,
+                       float beta, float* C, int64_t ldc, int levels, int variant,
+                       void* workspace, size_t ws_bytes, void* stream,
+                       const fmm_options* opt);
+
+/* Last error message of the calling host thread ("" when none). */
+const char* fmm_last_error(void);
+
+/* Synchronises `stream`, then reads and clears the device error word written
+ * by bounded waits inside the kernels.  Returns FMM_ERR_TIMEOUT if any wait
+ * gave up since the previous call, FMM_ERR_CUDA on a CUDA error. */
+fmm_status fmm_device_status(void* stream);
+
+/* Limit, in nanoseconds, of every device-side wait of kernels launched after
+ * this call (default 2e9).  Test hook for failure detection. */
+void fmm_set_wait_timeout_ns(uint64_t ns);
+
+/* Launches one CTA that waits on an mbarrier nothing ever arrives at, with
+ * the current wait limit, then records a timeout in the device error word.
+ * Exercises the bounded-wait failure path without faulting the GPU. */
+fmm_status fmm_debug_wait_timeout(void* stream);
+
+/* Writes the level-L product table (levels 0, 1 or 2) that the kernels use:
+ * U[(bi * 2^L + bj) * 7^L + r] is the coefficient of block (bi, bj) of A in the
+ * A-operand of product r; V likewise for B, W for the C update.  Each array
+ * must hold 4^L * 7^L entries.  Returns 7^L, or -1 on a bad argument.
+ * Source: Section 3, Eq. (3), and its Kronecker power for Section 3.4. */
+int fmm_product_table(int levels, int8_t* U, int8_t* V, int8_t* W);
+
+/* Phase timing.  While enabled, each launch of a phase -- 0: beta pass,
+ * 1: operand-sum passes, 2: tensor-core kernel -- is bracketed by two CUDA
+ * events recorded on the caller's stream.  fmm_profile_read waits for the
+ * recorded events, writes the summed milliseconds and launch counts of the
+ * three phases into ms[3] and launches[3] (either may be NULL) and forgets
+ * them.  Measurement hook; no effect on results. */
+fmm_status fmm_profile_enable(int on);
+fmm_status fmm_profile_read(double* ms, int64_t* launches);
+
+/* Library version string. */
+const char* fmm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FMM_GB300_H */

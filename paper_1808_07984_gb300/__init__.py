@@ -1,0 +1,209 @@
+"""GB300-native fused Strassen GEMM: thin Python binding of ``libfmm_gb300.so``.
+
+The binding only marshals arguments (device pointers, sizes, the current CUDA
+stream) to the C ABI declared in ``include/fmm.h``; every step of the product
+runs in the library's own sm_103a kernels.  PyTorch supplies device memory and
+streams.  There is no fallback: if the library is missing or the call fails, an
+exception is raised.
+
+Operation (Section 1, Eq. 1): ``C = alpha * A @ B + beta * C`` with ``levels``
+levels of Strassen's algorithm (Section 3, Eq. 3; Section 3.4 for two levels).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import _build
+
+__all__ = ["build", "load", "gemm", "workspace_size", "device_status", "product_table",
+           "VARIANTS", "ALGOS", "FmmError"]
+
+VARIANTS = {"split3": 0, "bf16": 1, "f16": 2, "plain_bf16": 3}
+ALGOS = {"auto": 0, "packed": 1, "fused": 2, "hybrid": 3}
+STATUS = {0: "FMM_OK", 1: "FMM_ERR_ARG", 2: "FMM_ERR_ALIGN", 3: "FMM_ERR_UNSUPPORTED",
+          4: "FMM_ERR_WORKSPACE", 5: "FMM_ERR_CUDA", 6: "FMM_ERR_TIMEOUT"}
+
+
+class FmmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("algo", ctypes.c_int), ("tile_n", ctypes.c_int), ("num_ctas", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
+
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the CUDA library in-tree (nvcc, sm_103a)."""
+    return _build.build(force=force)
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load() -> ctypes.CDLL:
+    """Load libfmm_gb300.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        raise FmmError(5, f"{_build.LIB} is missing: run paper_1808_07984_gb300.build()")
+    L = ctypes.CDLL(_build.LIB)
+    i64, i32, f32, vp, sz = ctypes.c_int64, ctypes.c_int, ctypes.c_float, ctypes.c_void_p, ctypes.c_size_t
+    L.fmm_workspace_size.restype = sz
+    L.fmm_workspace_size.argtypes = [i64, i64, i64, i32, i32]
+    L.fmm_workspace_size_ex.restype = sz
+    L.fmm_workspace_size_ex.argtypes = [i64, i64, i64, i32, i32, ctypes.POINTER(_Options)]
+    gemm_args = [i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, i32, i32, vp, sz, vp]
+    L.fmm_gemm.restype = i32
+    L.fmm_gemm.argtypes = gemm_args
+    L.fmm_gemm_ex.restype = i32
+    L.fmm_gemm_ex.argtypes = gemm_args + [ctypes.POINTER(_Options)]
+    L.fmm_last_error.restype = ctypes.c_char_p
+    L.fmm_last_error.argtypes = []
+    L.fmm_device_status.restype = i32
+    L.fmm_device_status.argtypes = [vp]
+    L.fmm_set_wait_timeout_ns.restype = None
+    L.fmm_set_wait_timeout_ns.argtypes = [ctypes.c_uint64]
+    L.fmm_debug_wait_timeout.restype = i32
+    L.fmm_debug_wait_timeout.argtypes = [vp]
+    L.fmm_product_table.restype = i32
+    L.fmm_product_table.argtypes = [i32, vp, vp, vp]
+    L.fmm_profile_enable.restype = i32
+    L.fmm_profile_enable.argtypes = [i32]
+    L.fmm_profile_read.restype = i32
+    L.fmm_profile_read.argtypes = [vp, vp]
+    L.fmm_version.restype = ctypes.c_char_p
+    L.fmm_version.argtypes = []
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != 0:
+        raise FmmError(status, load().fmm_last_error().decode())
+
+
+def _opts(algo="auto", tile_n=0, num_ctas=0):
+    o = _Options()
+    o.algo = ALGOS[algo] if isinstance(algo, str) else int(algo)
+    o.tile_n = int(tile_n)
+    o.num_ctas = int(num_ctas)
+    return o
+
+
+def _variant(v) -> int:
+    return VARIANTS[v] if isinstance(v, str) else int(v)
+
+
+def workspace_size(m, n, k, levels=1, variant="split3", algo="auto", tile_n=0) -> int:
+    o = _opts(algo, tile_n)
+    ws = load().fmm_workspace_size_ex(m, n, k, levels, _variant(variant), ctypes.byref(o))
+    if ws == ctypes.c_size_t(-1).value:
+        raise FmmError(3, "unsupported combination")
+    return int(ws)
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+_IN_DTYPE = {0: "float32", 1: "bfloat16", 2: "float16", 3: "float32"}
+
+
+def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
+         variant="split3", algo="auto", tile_n: int = 0, num_ctas: int = 0,
+         workspace=None, stream=None):
+    """C = alpha * A @ B + beta * C on the current CUDA device (torch tensors).
+
+    A (m x k) and B (k x n) are row-major CUDA tensors of the element type the
+    variant names (float32 for "split3"/"plain_bf16", bfloat16 for "bf16");
+    C is float32 and is allocated when None.  Rows may be padded (stride(0) >= cols)
+    but columns must be contiguous.  ``workspace`` is a uint8 CUDA tensor; one of
+    the right size is allocated when None.
+    """
+    import torch
+    v = _variant(variant)
+    m, k = A.shape
+    k2, n = B.shape
+    if k != k2:
+        raise FmmError(1, f"inner dimensions differ: {k} vs {k2}")
+    want = getattr(torch, _IN_DTYPE[v])
+    for name, X in (("A", A), ("B", B)):
+        if X.dtype != want:
+            raise FmmError(1, f"{name} must be {want} for variant {variant}")
+        if not X.is_cuda:
+            raise FmmError(1, f"{name} must be a CUDA tensor")
+        if X.numel() and X.stride(1) != 1:
+            raise FmmError(1, f"{name} must have contiguous rows")
+    if C is None:
+        C = torch.empty((m, n), dtype=torch.float32, device=A.device)
+        beta = 0.0
+    if C.dtype != torch.float32 or not C.is_cuda or (C.numel() and C.stride(1) != 1):
+        raise FmmError(1, "C must be a float32 CUDA tensor with contiguous rows")
+    ws_need = workspace_size(m, n, k, levels, v, algo, tile_n)
+    if workspace is None and ws_need > 0:
+        workspace = torch.empty(ws_need, dtype=torch.uint8, device=A.device)
+    ws_ptr = workspace.data_ptr() if workspace is not None else None
+    ws_bytes = workspace.numel() if workspace is not None else 0
+    o = _opts(algo, tile_n, num_ctas)
+    st = load().fmm_gemm_ex(m, n, k, float(alpha), A.data_ptr(), max(A.stride(0), 1),
+                            B.data_ptr(), max(B.stride(0), 1), float(beta), C.data_ptr(),
+                            max(C.stride(0), 1), int(levels), v, ws_ptr, ws_bytes,
+                            _stream_handle(stream), ctypes.byref(o))
+    _check(st)
+    return C
+
+
+def device_status(stream=None):
+    """Synchronise and raise FmmError if a device-side wait timed out."""
+    _check(load().fmm_device_status(_stream_handle(stream)))
+
+
+def set_wait_timeout_ns(ns: int):
+    load().fmm_set_wait_timeout_ns(int(ns))
+
+
+def debug_wait_timeout(stream=None):
+    _check(load().fmm_debug_wait_timeout(_stream_handle(stream)))
+
+
+PHASES = ("beta", "pack", "tensor")
+
+
+def profile_enable(on: bool = True):
+    """Bracket every launch of each phase with CUDA events (see fmm_profile_read)."""
+    _check(load().fmm_profile_enable(1 if on else 0))
+
+
+def profile_read():
+    """{phase: (milliseconds, launches)} summed since the previous read."""
+    import numpy as np
+    ms = np.zeros(3, dtype=np.float64)
+    n = np.zeros(3, dtype=np.int64)
+    _check(load().fmm_profile_read(ms.ctypes.data, n.ctypes.data))
+    return {p: (float(ms[i]), int(n[i])) for i, p in enumerate(PHASES)}
+
+
+def product_table(levels: int):
+    """(U, V, W) int8 arrays of shape (4**L, 7**L) as the kernels use them; row
+    index bi * 2**L + bj."""
+    import numpy as np
+    R, Q = 7 ** levels, 4 ** levels
+    U = np.zeros(Q * R, dtype=np.int8)
+    V = np.zeros(Q * R, dtype=np.int8)
+    W = np.zeros(Q * R, dtype=np.int8)
+    r = load().fmm_product_table(levels, U.ctypes.data, V.ctypes.data, W.ctypes.data)
+    if r != R:
+        raise FmmError(1, "bad levels")
+    return U.reshape(Q, R), V.reshape(Q, R), W.reshape(Q, R)

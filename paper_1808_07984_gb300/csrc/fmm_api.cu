@@ -1,0 +1,511 @@
+// fmm_api.cu -- the C ABI (include/fmm.h): argument checks, the Strassen planner (block
+// sizes, the 7^L product table, destination maps, tensor maps) and the launch sequence.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "fmm.h"
+#include "fmm_kernels.cuh"
+#include "launch.h"
+
+namespace fmm {
+
+// Device error word written by bounded waits inside the kernels (read and cleared by
+// fmm_device_status).
+__device__ unsigned int g_device_err;
+
+namespace {
+
+thread_local std::string g_last_error;
+std::atomic<uint64_t> g_timeout_ns{2000000000ull};
+
+// ------------------------------------------------------------- phase profiling
+// When enabled, every launch of a phase is bracketed by two CUDA events recorded on
+// the launching stream; fmm_profile_read sums their elapsed times.
+enum Phase { kPhaseBeta = 0, kPhasePack = 1, kPhaseTensor = 2, kNumPhases = 3 };
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  int phase = 0;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<EventPair> g_prof_pool;  // recorded, not yet read
+std::vector<EventPair> g_prof_free;
+
+struct PhaseScope {
+  EventPair ev;
+  cudaStream_t s;
+  bool on = false;
+  PhaseScope(int phase, cudaStream_t stream) : s(stream) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_on) return;
+    if (!g_prof_free.empty()) {
+      ev = g_prof_free.back();
+      g_prof_free.pop_back();
+    } else {
+      if (cudaEventCreate(&ev.a) != cudaSuccess || cudaEventCreate(&ev.b) != cudaSuccess) return;
+    }
+    ev.phase = phase;
+    on = cudaEventRecord(ev.a, s) == cudaSuccess;
+  }
+  ~PhaseScope() {
+    if (!on) return;
+    cudaEventRecord(ev.b, s);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_pool.push_back(ev);
+  }
+};
+
+fmm_status fail(fmm_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+fmm_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(FMM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+struct DeviceInfo {
+  bool init = false;
+  int sms = 0;
+  unsigned* err = nullptr;
+};
+
+std::mutex g_mu;
+DeviceInfo g_dev[64];
+EncodeTiledFn g_encode = nullptr;
+
+fmm_status device_info(DeviceInfo& out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 64) return fail(FMM_ERR_CUDA, "device ordinal out of range");
+  std::lock_guard<std::mutex> lk(g_mu);
+  DeviceInfo& d = g_dev[dev];
+  if (!d.init) {
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (major != 10) {
+      return fail(FMM_ERR_UNSUPPORTED, "this library is built for sm_103a (GB300); device is sm_" +
+                                           std::to_string(major) + std::to_string(minor));
+    }
+    e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    e = cudaGetSymbolAddress(reinterpret_cast<void**>(&d.err), g_device_err);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_device_err)");
+    d.init = true;
+  }
+  if (!g_encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+      return fail(FMM_ERR_CUDA, "cuTensorMapEncodeTiled entry point not available");
+    g_encode = reinterpret_cast<EncodeTiledFn>(fn);
+  }
+  out = d;
+  return FMM_OK;
+}
+
+// ---------------------------------------------------------------- planner
+// Eq. (3), Section 3: the seven products of one-level Strassen.  Quadrant q = 2*row + col
+// (Eq. 2).  kU[r][q]: coefficient of A_q in the A-operand of product r; kV[r][q]: of B_q in
+// its B-operand; kW[r][q]: coefficient with which M_r is added into C_q.
+constexpr int8_t kU[7][4] = {{1, 0, 0, 1}, {0, 0, 1, 1},  {1, 0, 0, 0}, {0, 0, 0, 1},
+                             {1, 1, 0, 0}, {-1, 0, 1, 0}, {0, 1, 0, -1}};
+constexpr int8_t kV[7][4] = {{1, 0, 0, 1}, {1, 0, 0, 0}, {0, 1, 0, -1}, {-1, 0, 1, 0},
+                             {0, 0, 0, 1}, {1, 1, 0, 0}, {0, 0, 1, 1}};
+constexpr int8_t kW[7][4] = {{1, 0, 0, 1},  {0, 0, 1, -1}, {0, 1, 0, 1}, {1, 0, 1, 0},
+                             {-1, 1, 0, 0}, {0, 0, 0, 1},  {1, 0, 0, 0}};
+
+struct Term {
+  int block;  // bi * 2^L + bj
+  int sign;
+};
+struct Product {
+  std::vector<Term> a, b, c;
+};
+
+int ipow(int b, int e) {
+  int r = 1;
+  while (e-- > 0) r *= b;
+  return r;
+}
+
+// Multi-level products (Section 3.4): product (r_1..r_L) takes block (q_1..q_L) -- block q_L
+// of ... of quadrant q_1 -- with coefficient prod_i X[r_i][q_i] (the Kronecker power).
+std::vector<Product> make_products(int L) {
+  const int R = ipow(7, L), Q = ipow(4, L), g = 1 << L;
+  std::vector<Product> out(R);
+  for (int r = 0; r < R; ++r) {
+    int rd[2] = {0, 0};
+    for (int i = L - 1, t = r; i >= 0; --i, t /= 7) rd[i] = t % 7;
+    for (int qi = 0; qi < Q; ++qi) {
+      int qd[2] = {0, 0};
+      for (int i = L - 1, t = qi; i >= 0; --i, t /= 4) qd[i] = t % 4;
+      int cu = 1, cv = 1, cw = 1, br = 0, bc = 0;
+      for (int i = 0; i < L; ++i) {
+        cu *= kU[rd[i]][qd[i]];
+        cv *= kV[rd[i]][qd[i]];
+        cw *= kW[rd[i]][qd[i]];
+        br = 2 * br + qd[i] / 2;
+        bc = 2 * bc + qd[i] % 2;
+      }
+      const int blk = br * g + bc;
+      if (cu) out[r].a.push_back({blk, cu});
+      if (cv) out[r].b.push_back({blk, cv});
+      if (cw) out[r].c.push_back({blk, cw});
+    }
+  }
+  return out;
+}
+
+int64_t block_size(int64_t d, int L) {
+  if (L == 0) return d;
+  const int64_t g = int64_t(1) << L;
+  const int64_t h = (d + g - 1) / g;
+  return (h + 7) / 8 * 8;
+}
+int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+struct Plan {
+  int L = 0, R = 1, terms = 3, in_type = kInF32;
+  bool bf16 = true;
+  int tile_n = 128;
+  int algo = FMM_ALGO_PACKED;
+  int64_t hm = 0, hn = 0, hk = 0, ldw = 0;
+  size_t a_bytes = 0, b_bytes = 0;  // per term array
+  size_t ws = 0;
+};
+
+fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, const fmm_options* opt,
+                     Plan& pl) {
+  if (m < 0 || n < 0 || k < 0) return fail(FMM_ERR_ARG, "negative dimension");
+  if (levels < 0 || levels > 2) return fail(FMM_ERR_UNSUPPORTED, "levels must be 0, 1 or 2");
+  pl.L = levels;
+  pl.R = ipow(7, levels);
+  switch (variant) {
+    case FMM_F32_SPLIT3_BF16: pl.terms = 3; pl.in_type = kInF32; pl.bf16 = true; break;
+    case FMM_F32_PLAIN_BF16: pl.terms = 1; pl.in_type = kInF32; pl.bf16 = true; break;
+    case FMM_BF16: pl.terms = 1; pl.in_type = kInBF16; pl.bf16 = true; break;
+    default: return fail(FMM_ERR_UNSUPPORTED, "variant not built");
+  }
+  const int algo = opt ? opt->algo : 0;
+  if (algo != FMM_ALGO_AUTO && algo != FMM_ALGO_PACKED)
+    return fail(FMM_ERR_UNSUPPORTED, "algorithm not built");
+  pl.algo = FMM_ALGO_PACKED;
+  pl.tile_n = (opt && opt->tile_n) ? opt->tile_n : 128;
+  if (!packed_config_supported(pl.tile_n, pl.terms, pl.bf16))
+    return fail(FMM_ERR_UNSUPPORTED, "tile_n must be 128 or 256");
+  pl.hm = block_size(m, levels);
+  pl.hn = block_size(n, levels);
+  pl.hk = block_size(k, levels);
+  pl.ldw = round_up(std::max<int64_t>(pl.hk, 1), 8);
+  if (pl.hm >= (int64_t(1) << 31) || pl.hn >= (int64_t(1) << 31) || pl.hk >= (int64_t(1) << 31))
+    return fail(FMM_ERR_ARG, "dimension too large");
+  pl.a_bytes = static_cast<size_t>(round_up(static_cast<int64_t>(pl.R) * pl.hm * pl.ldw * 2, 256));
+  pl.b_bytes = static_cast<size_t>(round_up(static_cast<int64_t>(pl.R) * pl.hn * pl.ldw * 2, 256));
+  const size_t arrays = pl.terms == 3 ? 2 : 1;
+  pl.ws = (m == 0 || n == 0 || k == 0) ? 0 : arrays * (pl.a_bytes + pl.b_bytes);
+  return FMM_OK;
+}
+
+bool overlaps(const void* a, size_t abytes, const void* b, size_t bbytes) {
+  if (!a || !b || abytes == 0 || bbytes == 0) return false;
+  const uintptr_t a0 = reinterpret_cast<uintptr_t>(a), b0 = reinterpret_cast<uintptr_t>(b);
+  return a0 < b0 + bbytes && b0 < a0 + abytes;
+}
+
+fmm_status encode_3d(CUtensorMap* map, void* base, int64_t inner, int64_t rows, int64_t depth,
+                     int64_t ld_elems, int box_rows) {
+  const cuuint64_t dims[3] = {static_cast<cuuint64_t>(inner), static_cast<cuuint64_t>(rows),
+                              static_cast<cuuint64_t>(depth)};
+  const cuuint64_t strides[2] = {static_cast<cuuint64_t>(ld_elems * 2),
+                                 static_cast<cuuint64_t>(ld_elems * 2 * rows)};
+  const cuuint32_t box[3] = {static_cast<cuuint32_t>(kBK), static_cast<cuuint32_t>(box_rows), 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(FMM_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string(r) + ")");
+  return FMM_OK;
+}
+
+size_t elem_bytes(int in_type) { return in_type == kInF32 ? 4 : 2; }
+
+fmm_status gemm_impl(int64_t m, int64_t n, int64_t k, float alpha, const void* A, int64_t lda,
+                     const void* B, int64_t ldb, float beta, float* C, int64_t ldc, int levels,
+                     int variant, void* ws, size_t ws_bytes, void* stream, const fmm_options* opt) {
+  g_last_error.clear();
+  Plan pl;
+  fmm_status st = make_plan(m, n, k, levels, variant, opt, pl);
+  if (st != FMM_OK) return st;
+  if (lda < std::max<int64_t>(1, k) || ldb < std::max<int64_t>(1, n) || ldc < std::max<int64_t>(1, n))
+    return fail(FMM_ERR_ARG, "leading dimension smaller than the row length");
+  if (m == 0 || n == 0) return FMM_OK;
+  if (!C) return fail(FMM_ERR_ARG, "C is NULL");
+  if (k > 0 && (!A || !B)) return fail(FMM_ERR_ARG, "A or B is NULL");
+  const size_t eb = elem_bytes(pl.in_type);
+  const size_t c_bytes = static_cast<size_t>(((m - 1) * ldc + n) * 4);
+  if (k > 0) {
+    const size_t a_span = static_cast<size_t>(((m - 1) * lda + k) * eb);
+    const size_t b_span = static_cast<size_t>(((k - 1) * ldb + n) * eb);
+    if (overlaps(C, c_bytes, A, a_span) || overlaps(C, c_bytes, B, b_span))
+      return fail(FMM_ERR_ARG, "C overlaps A or B");
+  }
+  if (pl.ws > 0) {
+    if (!ws || ws_bytes < pl.ws)
+      return fail(FMM_ERR_WORKSPACE, "workspace of " + std::to_string(pl.ws) + " bytes required");
+    if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(FMM_ERR_ALIGN, "workspace must be 256-byte aligned");
+    if (overlaps(C, c_bytes, ws, pl.ws)) return fail(FMM_ERR_ARG, "C overlaps the workspace");
+  }
+  DeviceInfo dev;
+  st = device_info(dev);
+  if (st != FMM_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+  // beta first: C <- beta * C (beta == 0: C is not read)
+  if (beta != 1.0f) {
+    PhaseScope ps(kPhaseBeta, s);
+    cudaError_t e = launch_beta(C, m, n, ldc, beta, dev.sms, s);
+    if (e != cudaSuccess) return cuda_fail(e, "beta pass");
+  }
+  if (k == 0 || alpha == 0.0f) return FMM_OK;
+
+  const std::vector<Product> prods = make_products(pl.L);
+  const int g = 1 << pl.L;
+  uint8_t* wsb = static_cast<uint8_t*>(ws);
+  uint16_t* a_hi = reinterpret_cast<uint16_t*>(wsb);
+  uint16_t* b_hi = reinterpret_cast<uint16_t*>(wsb + pl.a_bytes);
+  uint16_t* a_lo = pl.terms == 3 ? reinterpret_cast<uint16_t*>(wsb + pl.a_bytes + pl.b_bytes) : nullptr;
+  uint16_t* b_lo = pl.terms == 3 ? reinterpret_cast<uint16_t*>(wsb + 2 * pl.a_bytes + pl.b_bytes) : nullptr;
+
+  // ---- operand-sum passes (all 7^L A-operands, then all B-operands, K-major)
+  {
+    PhaseScope ps(kPhasePack, s);
+    PackParams pa;
+    std::memset(&pa, 0, sizeof pa);
+    pa.X = A;
+    pa.ldx = lda;
+    pa.rows = m;
+    pa.cols = k;
+    pa.hr = static_cast<int32_t>(pl.hm);
+    pa.hc = static_cast<int32_t>(pl.hk);
+    pa.gdim = g;
+    pa.nsrc = g * g;
+    pa.nprod = pl.R;
+    pa.terms = pl.terms;
+    pa.ld_out = pl.ldw;
+    pa.prod_stride = pl.hm * pl.ldw;
+    pa.out_hi = a_hi;
+    pa.out_lo = a_lo;
+    for (int r = 0; r < pl.R; ++r) {
+      pa.cnt[r] = static_cast<int8_t>(prods[r].a.size());
+      for (size_t t = 0; t < prods[r].a.size(); ++t)
+        pa.term[r][t] = {static_cast<int16_t>(prods[r].a[t].block), static_cast<int16_t>(prods[r].a[t].sign)};
+    }
+    cudaError_t e = launch_pack(pa, pl.in_type, pl.bf16 ? 0 : 1, false, dev.sms, s);
+    if (e != cudaSuccess) return cuda_fail(e, "operand-sum pass (A)");
+
+    PackParams pb = pa;
+    pb.X = B;
+    pb.ldx = ldb;
+    pb.rows = k;
+    pb.cols = n;
+    pb.hr = static_cast<int32_t>(pl.hk);
+    pb.hc = static_cast<int32_t>(pl.hn);
+    pb.prod_stride = pl.hn * pl.ldw;
+    pb.out_hi = b_hi;
+    pb.out_lo = b_lo;
+    for (int r = 0; r < pl.R; ++r) {
+      pb.cnt[r] = static_cast<int8_t>(prods[r].b.size());
+      for (size_t t = 0; t < prods[r].b.size(); ++t)
+        pb.term[r][t] = {static_cast<int16_t>(prods[r].b[t].block), static_cast<int16_t>(prods[r].b[t].sign)};
+    }
+    e = launch_pack(pb, pl.in_type, pl.bf16 ? 0 : 1, true, dev.sms, s);
+    if (e != cudaSuccess) return cuda_fail(e, "operand-sum pass (B)");
+  }
+
+  // ---- tensor-core pass
+  PackedParams* pp = new PackedParams;
+  std::memset(pp, 0, sizeof(PackedParams));
+  st = encode_3d(&pp->tmA[0], a_hi, pl.hk, pl.hm, pl.R, pl.ldw, kBM);
+  if (st == FMM_OK) st = encode_3d(&pp->tmB[0], b_hi, pl.hk, pl.hn, pl.R, pl.ldw, pl.tile_n);
+  if (st == FMM_OK && pl.terms == 3) {
+    st = encode_3d(&pp->tmA[1], a_lo, pl.hk, pl.hm, pl.R, pl.ldw, kBM);
+    if (st == FMM_OK) st = encode_3d(&pp->tmB[1], b_lo, pl.hk, pl.hn, pl.R, pl.ldw, pl.tile_n);
+  }
+  if (st != FMM_OK) {
+    delete pp;
+    return st;
+  }
+  pp->C = C;
+  pp->ldc = ldc;
+  pp->err = dev.err;
+  pp->timeout_ns = g_timeout_ns.load();
+  pp->tiles_m = static_cast<int32_t>((pl.hm + kBM - 1) / kBM);
+  pp->tiles_n = static_cast<int32_t>((pl.hn + pl.tile_n - 1) / pl.tile_n);
+  pp->nk = static_cast<int32_t>((pl.hk + kBK - 1) / kBK);
+  const int64_t items = static_cast<int64_t>(pl.R) * pp->tiles_m * pp->tiles_n;
+  if (items >= (int64_t(1) << 31)) {
+    delete pp;
+    return fail(FMM_ERR_ARG, "too many tiles");
+  }
+  pp->num_items = static_cast<int32_t>(items);
+  pp->num_products = pl.R;
+  pp->c_vec4 = (reinterpret_cast<uintptr_t>(C) % 16 == 0 && ldc % 4 == 0) ? 1 : 0;
+  for (int r = 0; r < pl.R; ++r) {
+    int cnt = 0;
+    for (const Term& t : prods[r].c) {
+      const int br = t.block / g, bc = t.block % g;
+      const int64_t rows = std::min<int64_t>(std::max<int64_t>(m - br * pl.hm, 0), pl.hm);
+      const int64_t cols = std::min<int64_t>(std::max<int64_t>(n - bc * pl.hn, 0), pl.hn);
+      if (rows == 0 || cols == 0) continue;
+      DestEntry& de = pp->prod[r].d[cnt++];
+      de.offset = br * pl.hm * ldc + bc * pl.hn;
+      de.rows = static_cast<int32_t>(rows);
+      de.cols = static_cast<int32_t>(cols);
+      de.coef = alpha * static_cast<float>(t.sign);
+    }
+    pp->prod[r].count = cnt;
+  }
+  int grid = opt && opt->num_ctas > 0 ? opt->num_ctas : dev.sms;
+  grid = static_cast<int>(std::min<int64_t>(grid, items));
+  cudaError_t e;
+  {
+    PhaseScope ps(kPhaseTensor, s);
+    e = launch_packed(*pp, pl.tile_n, pl.terms, pl.bf16, grid, s);
+  }
+  delete pp;
+  if (e != cudaSuccess) return cuda_fail(e, "tensor-core pass");
+  return FMM_OK;
+}
+
+}  // namespace
+}  // namespace fmm
+
+using namespace fmm;
+
+extern "C" {
+
+size_t fmm_workspace_size_ex(int64_t m, int64_t n, int64_t k, int levels, int variant,
+                             const fmm_options* opt) {
+  Plan pl;
+  if (make_plan(m, n, k, levels, variant, opt, pl) != FMM_OK) return static_cast<size_t>(-1);
+  return pl.ws;
+}
+
+size_t fmm_workspace_size(int64_t m, int64_t n, int64_t k, int levels, int variant) {
+  return fmm_workspace_size_ex(m, n, k, levels, variant, nullptr);
+}
+
+fmm_status fmm_gemm_ex(int64_t m, int64_t n, int64_t k, float alpha, const void* A, int64_t lda,
+                       const void* B, int64_t ldb, float beta, float* C, int64_t ldc, int levels,
+                       int variant, void* workspace, size_t ws_bytes, void* stream,
+                       const fmm_options* opt) {
+  return gemm_impl(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, levels, variant, workspace,
+                   ws_bytes, stream, opt);
+}
+
+fmm_status fmm_gemm(int64_t m, int64_t n, int64_t k, float alpha, const void* A, int64_t lda,
+                    const void* B, int64_t ldb, float beta, float* C, int64_t ldc, int levels,
+                    int variant, void* workspace, size_t ws_bytes, void* stream) {
+  return gemm_impl(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, levels, variant, workspace,
+                   ws_bytes, stream, nullptr);
+}
+
+const char* fmm_last_error(void) { return g_last_error.c_str(); }
+
+fmm_status fmm_device_status(void* stream) {
+  DeviceInfo dev;
+  fmm_status st = device_info(dev);
+  if (st != FMM_OK) return st;
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  unsigned word = 0;
+  e = cudaMemcpy(&word, dev.err, sizeof word, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
+  if (word != 0) {
+    const unsigned zero = 0;
+    e = cudaMemcpy(dev.err, &zero, sizeof zero, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "clearing the device error word");
+    char buf[96];
+    std::snprintf(buf, sizeof buf, "device-side wait timed out (error bits 0x%x)", word);
+    return fail(FMM_ERR_TIMEOUT, buf);
+  }
+  return FMM_OK;
+}
+
+void fmm_set_wait_timeout_ns(uint64_t ns) { g_timeout_ns.store(ns); }
+
+fmm_status fmm_debug_wait_timeout(void* stream) {
+  DeviceInfo dev;
+  fmm_status st = device_info(dev);
+  if (st != FMM_OK) return st;
+  cudaError_t e = launch_debug_wait(dev.err, g_timeout_ns.load(), static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "debug wait kernel");
+  return FMM_OK;
+}
+
+// Exports the level-L product table in the layout U[(bi*2^L + bj) * 7^L + r] (likewise V, W),
+// so that host-side tests can check it against the Brent equations without a GPU.
+int fmm_product_table(int levels, int8_t* U, int8_t* V, int8_t* W) {
+  if (levels < 0 || levels > 2 || !U || !V || !W) return -1;
+  const int R = ipow(7, levels), Q = ipow(4, levels);
+  std::memset(U, 0, static_cast<size_t>(R) * Q);
+  std::memset(V, 0, static_cast<size_t>(R) * Q);
+  std::memset(W, 0, static_cast<size_t>(R) * Q);
+  const std::vector<Product> prods = make_products(levels);
+  for (int r = 0; r < R; ++r) {
+    for (const Term& t : prods[r].a) U[t.block * R + r] = static_cast<int8_t>(t.sign);
+    for (const Term& t : prods[r].b) V[t.block * R + r] = static_cast<int8_t>(t.sign);
+    for (const Term& t : prods[r].c) W[t.block * R + r] = static_cast<int8_t>(t.sign);
+  }
+  return R;
+}
+
+fmm_status fmm_profile_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_on = on != 0;
+  return FMM_OK;
+}
+
+fmm_status fmm_profile_read(double* ms, int64_t* launches) {
+  std::vector<EventPair> recorded;
+  {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    recorded.swap(g_prof_pool);
+  }
+  for (int i = 0; i < kNumPhases; ++i) {
+    if (ms) ms[i] = 0.0;
+    if (launches) launches[i] = 0;
+  }
+  fmm_status st = FMM_OK;
+  for (EventPair& ev : recorded) {
+    cudaError_t e = cudaEventSynchronize(ev.b);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, ev.a, ev.b);
+    if (e != cudaSuccess) st = cuda_fail(e, "reading profile events");
+    if (ms) ms[ev.phase] += t;
+    if (launches) launches[ev.phase] += 1;
+  }
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_free.insert(g_prof_free.end(), recorded.begin(), recorded.end());
+  return st;
+}
+
+const char* fmm_version(void) { return "fmm-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,321 @@
+// fmm_kernels.cuh -- parameter blocks and device kernels of the fused Strassen GEMM.
+//
+// One persistent, warp-specialised tcgen05 kernel runs every Strassen product
+// ("instance" in Section 3.2) of one GEMM call:
+//
+//   work item  = (product r, 128 x BN output tile of the h_m x h_n block grid)
+//   warp 0     = TMA producer: per k-step, loads the A- and B-operand tiles of
+//                product r (hi and lo halves for the split-BF16 arithmetic) into a
+//                STAGES-deep shared-memory ring;
+//   warp 1     = TMEM allocator and single-thread UMMA issuer: 1 or 3 tcgen05.mma
+//                per 16-wide k-slice into a double-buffered FP32 TMEM accumulator;
+//   warps 4..7 = epilogue: tcgen05.ld of the finished accumulator, then, for every
+//                C block the product feeds, C_block += alpha * W[c, r] * M_r (the
+//                multi-destination write-back of Section 3.1), masked at fringes.
+//
+// The epilogue adds with element-wise atomic reductions (the atomic-update scheme
+// of Section 3.3), so items of different products that feed the same C block may
+// run concurrently on different SMs without a race; beta is applied to C by a
+// separate pass before the products start.
+#pragma once
+#include <cstdint>
+#include <cuda.h>
+#include "ptx.cuh"
+
+namespace fmm {
+
+constexpr int kBM = 128;          // rows of an output tile (UMMA M)
+constexpr int kBK = 64;           // k-elements per pipeline stage (128-byte 16-bit rows)
+constexpr int kMaxProducts = 49;  // 7^2
+constexpr int kMaxDest = 4;       // W_C <= 4 at two levels
+constexpr int kMaxSources = 16;   // 4^2 blocks per operand at two levels
+constexpr int kThreads = 256;
+
+enum ErrBits : unsigned {
+  kErrProducerWait = 1u,
+  kErrMmaWait = 2u,
+  kErrEpilogueWait = 4u,
+  kErrDebugWait = 8u,
+  kErrTransformWait = 16u,
+};
+
+struct DestEntry {
+  int64_t offset;  // element offset of the destination block's origin inside C
+  int32_t rows;    // rows of that block that exist in C (<= h_m)
+  int32_t cols;    // columns of that block that exist in C (<= h_n)
+  float coef;      // alpha * W[c, r]
+  int32_t pad;
+};
+
+struct ProductDests {
+  int32_t count;
+  int32_t pad;
+  DestEntry d[kMaxDest];
+};
+
+// Kernel parameters of the packed-operand path (operand sums already formed).
+struct alignas(64) PackedParams {
+  CUtensorMap tmA[2];  // A-operand sums, hi / lo: 3-D {k, row, product}, 16-bit
+  CUtensorMap tmB[2];  // B-operand sums transposed, hi / lo: 3-D {k, col, product}
+  float* C;
+  int64_t ldc;
+  unsigned int* err;
+  uint64_t timeout_ns;
+  int32_t tiles_m, tiles_n, nk, num_items;
+  int32_t num_products;
+  int32_t c_vec4;  // C rows are 16-byte aligned: vector reductions allowed
+  ProductDests prod[kMaxProducts];
+};
+
+// One signed source block of an operand sum.
+struct SrcTerm {
+  int16_t src;   // block index bi * 2^L + bj in the 2^L x 2^L grid
+  int16_t sign;  // +1 / -1
+};
+
+// Parameters of the operand-sum pass (forms all 7^L operand sums of A or B).
+struct PackParams {
+  const void* X;       // source matrix, row-major
+  int64_t ldx;
+  int64_t rows, cols;  // extent of X
+  int32_t hr, hc;      // block size along rows / cols of X
+  int32_t gdim;        // 2^L
+  int32_t nsrc;        // 4^L
+  int32_t nprod;       // 7^L
+  int32_t terms;       // 3: split hi/lo, 1: single rounding
+  int64_t ld_out;      // row stride of the output (elements)
+  int64_t prod_stride; // elements between consecutive products in the output
+  uint16_t* out_hi;
+  uint16_t* out_lo;
+  int8_t cnt[kMaxProducts];
+  SrcTerm term[kMaxProducts][kMaxDest];
+};
+
+__device__ __forceinline__ void decode_item(int item, int tiles_m, int tiles_n, int& r, int& tm,
+                                            int& tn) {
+  const int per_prod = tiles_m * tiles_n;
+  r = item / per_prod;
+  const int t = item - r * per_prod;
+  // grouped raster: 8 tile-rows at a time, column-major inside the group, so that
+  // concurrently running CTAs share operand panels in L2.
+  constexpr int G = 8;
+  const int group_size = G * tiles_n;
+  const int g = t / group_size;
+  const int first_m = g * G;
+  const int gm = min(tiles_m - first_m, G);
+  const int in_g = t - g * group_size;
+  tm = first_m + in_g % gm;
+  tn = in_g / gm;
+}
+
+template <int BN, int TERMS, int STAGES>
+struct PackedCfg {
+  static constexpr uint32_t kABytes = kBM * kBK * 2;
+  static constexpr uint32_t kBBytes = BN * kBK * 2;
+  static constexpr uint32_t kStageBytes = (TERMS == 3 ? 2u : 1u) * (kABytes + kBBytes);
+  static constexpr uint32_t kBarOffset = STAGES * kStageBytes;
+  static constexpr uint32_t kSmemBytes = kBarOffset + 256 + 1024;  // + barriers + alignment slack
+  static constexpr uint32_t kTmemCols = 2 * BN;
+};
+
+template <int BN, int TERMS, int STAGES, bool BF16>
+__global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_constant__ PackedParams p) {
+  using Cfg = PackedCfg<BN, TERMS, STAGES>;
+  static_assert(BN % 32 == 0 && BN >= 32 && BN <= 256, "UMMA N");
+  static_assert(Cfg::kTmemCols >= 32 && Cfg::kTmemCols <= 512, "TMEM columns");
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::kBarOffset);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + STAGES;
+  uint64_t* acc_full = bars + 2 * STAGES;
+  uint64_t* acc_empty = bars + 2 * STAGES + 2;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(smem_u32(&acc_full[a]), 1);
+      mbar_init(smem_u32(&acc_empty[a]), 4 * 32);
+    }
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0 && lane == 0) {
+    tma_prefetch_desc(&p.tmA[0]);
+    tma_prefetch_desc(&p.tmB[0]);
+    if (TERMS == 3) {
+      tma_prefetch_desc(&p.tmA[1]);
+      tma_prefetch_desc(&p.tmB[1]);
+    }
+  }
+  if (warp == 1) {
+    __syncwarp();
+    tmem_alloc(smem_u32(tmem_holder), Cfg::kTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_holder;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int item = blockIdx.x; ok && item < p.num_items; item += gridDim.x) {
+        int r, tm, tn;
+        decode_item(item, p.tiles_m, p.tiles_n, r, tm, tn);
+        for (int kb = 0; kb < p.nk; ++kb) {
+          if (!mbar_wait(smem_u32(&empty[stage]), phase ^ 1u, p.timeout_ns, abort_flag)) {
+            atomicOr(p.err, kErrProducerWait);
+            *abort_flag = 1;
+            ok = false;
+            break;
+          }
+          uint8_t* st = smem + stage * Cfg::kStageBytes;
+          const uint32_t fb = smem_u32(&full[stage]);
+          mbar_arrive_expect_tx(fb, Cfg::kStageBytes);
+          tma_load_3d(smem_u32(st), &p.tmA[0], fb, kb * kBK, tm * kBM, r);
+          tma_load_3d(smem_u32(st + Cfg::kABytes), &p.tmB[0], fb, kb * kBK, tn * BN, r);
+          if (TERMS == 3) {
+            tma_load_3d(smem_u32(st + Cfg::kABytes + Cfg::kBBytes), &p.tmA[1], fb, kb * kBK, tm * kBM, r);
+            tma_load_3d(smem_u32(st + 2 * Cfg::kABytes + Cfg::kBBytes), &p.tmB[1], fb, kb * kBK, tn * BN, r);
+          }
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      if (!ok) {
+        // let loads already in flight land before the CTA's shared memory goes away
+        const uint64_t t0 = globaltimer_ns();
+        while (globaltimer_ns() - t0 < 2000000ull) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = make_idesc_f16(kBM, BN, BF16);
+      int stage = 0;
+      uint32_t phase = 0;
+      int it = 0;
+      bool ok = true;
+      for (int item = blockIdx.x; ok && item < p.num_items; item += gridDim.x, ++it) {
+        const int acc = it & 1;
+        const uint32_t acc_par = (it >> 1) & 1;
+        if (!mbar_wait(smem_u32(&acc_empty[acc]), acc_par ^ 1u, p.timeout_ns, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * BN);
+        for (int kb = 0; kb < p.nk; ++kb) {
+          if (!mbar_wait(smem_u32(&full[stage]), phase, p.timeout_ns, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          uint8_t* st = smem + stage * Cfg::kStageBytes;
+          const uint64_t da_hi = make_sdesc_kmajor_sw128(smem_u32(st));
+          const uint64_t db_hi = make_sdesc_kmajor_sw128(smem_u32(st + Cfg::kABytes));
+          const uint64_t da_lo = make_sdesc_kmajor_sw128(smem_u32(st + Cfg::kABytes + Cfg::kBBytes));
+          const uint64_t db_lo = make_sdesc_kmajor_sw128(smem_u32(st + 2 * Cfg::kABytes + Cfg::kBBytes));
+#pragma unroll
+          for (int kk = 0; kk < kBK / 16; ++kk) {
+            const uint64_t ko = static_cast<uint64_t>(kk * 2);  // 32 bytes, encoded >> 4
+            umma_f16_ss(d_tmem, da_hi + ko, db_hi + ko, idesc, (kb | kk) != 0 ? 1u : 0u);
+            if (TERMS == 3) {
+              umma_f16_ss(d_tmem, da_hi + ko, db_lo + ko, idesc, 1u);
+              umma_f16_ss(d_tmem, da_lo + ko, db_hi + ko, idesc, 1u);
+            }
+          }
+          umma_commit(smem_u32(&empty[stage]));
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        umma_commit(smem_u32(&acc_full[acc]));
+      }
+      if (!ok) {
+        atomicOr(p.err, kErrMmaWait);
+        *abort_flag = 1;
+        // give UMMAs already issued time to finish before TMEM is released
+        const uint64_t t0 = globaltimer_ns();
+        while (globaltimer_ns() - t0 < 2000000ull) {
+        }
+      }
+    }
+  } else if (warp >= 4) {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int row_local = q * 32 + lane;
+    const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
+    int it = 0;
+    for (int item = blockIdx.x; item < p.num_items; item += gridDim.x, ++it) {
+      const int acc = it & 1;
+      const uint32_t acc_par = (it >> 1) & 1;
+      if (!mbar_wait(smem_u32(&acc_full[acc]), acc_par, p.timeout_ns, abort_flag)) {
+        if (lane == 0) atomicOr(p.err, kErrEpilogueWait);
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      int r, tm, tn;
+      decode_item(item, p.tiles_m, p.tiles_n, r, tm, tn);
+      const ProductDests& pd = p.prod[r];
+      const int row = tm * kBM + row_local;
+#pragma unroll 1
+      for (int c = 0; c < BN; c += 32) {
+        float v[32];
+        tmem_ld_32x32b_x32(tmem_base + lane_off + static_cast<uint32_t>(acc * BN + c), v);
+        const int col0 = tn * BN + c;
+#pragma unroll 1
+        for (int d = 0; d < pd.count; ++d) {
+          const DestEntry de = pd.d[d];
+          if (row >= de.rows || col0 >= de.cols) continue;
+          float* dst = p.C + de.offset + static_cast<int64_t>(row) * p.ldc + col0;
+          const float cf = de.coef;
+          if (p.c_vec4 && col0 + 32 <= de.cols) {
+            float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              atomicAdd(d4 + j, make_float4(cf * v[4 * j], cf * v[4 * j + 1], cf * v[4 * j + 2],
+                                            cf * v[4 * j + 3]));
+          } else {
+            const int lim = de.cols - col0;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (j < lim) atomicAdd(dst + j, cf * v[j]);
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(smem_u32(&acc_empty[acc]));
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem_base, Cfg::kTmemCols);
+  }
+}
+
+}  // namespace fmm

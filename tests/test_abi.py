@@ -1,0 +1,106 @@
+"""C-ABI library checks that need no GPU: it builds, loads, exports every declared
+symbol, rejects bad arguments before launching anything, and its product tables
+satisfy the Brent equations and agree with the oracle's restatement of Eq. (3)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1808_07984_gb300 as fmm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    fmm.build()
+    return fmm.load()
+
+
+def _declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(fmm_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared_functions()
+    assert "fmm_gemm" in names and "fmm_device_status" in names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_version(lib):
+    assert b"sm_103a" in lib.fmm_version()
+
+
+@pytest.mark.parametrize("levels", [0, 1, 2])
+def test_library_tables_match_oracle(lib, levels):
+    U, V, W = fmm.product_table(levels)
+    UL, VL, WL, rc = oracle.level_coefficients(levels)
+    g = 1 << levels
+    for row, (bi, bj) in enumerate(rc):
+        np.testing.assert_array_equal(U[bi * g + bj], UL[row])
+        np.testing.assert_array_equal(V[bi * g + bj], VL[row])
+        np.testing.assert_array_equal(W[bi * g + bj], WL[row])
+
+
+@pytest.mark.parametrize("levels", [1, 2])
+def test_library_tables_satisfy_brent(lib, levels):
+    """Independent of the oracle's arrays: rebuild the trilinear identity."""
+    U, V, W = fmm.product_table(levels)
+    g = 1 << levels
+    R = 7 ** levels
+    T = np.einsum("ar,br,cr->abc", U.astype(np.int64), V.astype(np.int64), W.astype(np.int64))
+    for a in range(g * g):
+        i, j = divmod(a, g)
+        for b in range(g * g):
+            j2, l = divmod(b, g)
+            for c in range(g * g):
+                i2, l2 = divmod(c, g)
+                assert T[a, b, c] == int(j == j2 and i == i2 and l == l2)
+    assert U.shape == (g * g, R)
+
+
+def test_workspace_sizes(lib):
+    # packed split3: two 16-bit arrays per operand, 7^L products of h x h blocks
+    assert fmm.workspace_size(512, 512, 512, 1, "split3") == 2 * 2 * (7 * 256 * 256 * 2)
+    assert fmm.workspace_size(512, 512, 512, 0, "split3") == 2 * 2 * (512 * 512 * 2)
+    assert fmm.workspace_size(512, 512, 512, 1, "plain_bf16") == 2 * (7 * 256 * 256 * 2)
+    assert fmm.workspace_size(0, 512, 512, 1, "split3") == 0
+    with pytest.raises(fmm.FmmError):
+        fmm.workspace_size(16, 16, 16, 3, "split3")
+
+
+def _call(lib, m=16, n=16, k=16, lda=16, ldb=16, ldc=16, levels=1, variant=0,
+          A=0x10000, B=0x20000, C=0x30000, ws=0x100000, ws_bytes=1 << 30):
+    return lib.fmm_gemm(m, n, k, 1.0, A, lda, B, ldb, 0.0, C, ldc, levels, variant,
+                        ws, ws_bytes, None)
+
+
+def test_argument_errors_need_no_gpu(lib):
+    # these are rejected by host-side checks before any CUDA call
+    assert _call(lib, m=-1) == 1
+    assert _call(lib, lda=8) == 1
+    assert _call(lib, ldb=8) == 1
+    assert _call(lib, ldc=8) == 1
+    assert _call(lib, levels=3) == 3
+    assert _call(lib, variant=9) == 3
+    assert _call(lib, C=0x10000 + 64) == 1               # C overlaps A
+    assert _call(lib, ws_bytes=16) == 4                  # workspace too small
+    assert _call(lib, ws=0x100010) == 2                  # workspace misaligned
+    assert b"workspace" in lib.fmm_last_error() or b"aligned" in lib.fmm_last_error()
+    assert _call(lib, m=0) == 0                          # empty problem: no-op
+
+
+def test_oracle_is_not_linked_by_the_library():
+    so = fmm.lib_path()
+    data = open(so, "rb").read()
+    assert b"oracle_gemm" not in data

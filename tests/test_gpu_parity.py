@@ -1,0 +1,189 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Integer inputs must agree bit for bit (every operand sum, product and partial sum
+is an integer below 2**24, exact in BF16 and FP32).  Floating-point inputs must
+agree within the normwise bound ||C - C64||_F / (||A||_F ||B||_F) <= tol, where
+tol is derived per arithmetic in ``tolerance()`` below.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1808_07984_gb300 as fmm
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    fmm.build()
+    fmm.load()
+    oracle.build()
+
+
+U_BF16 = 2.0 ** -8   # unit roundoff of bfloat16 (8-bit significand)
+
+
+def tolerance(variant, levels, k):
+    """Normwise error bound used by the parity tests.
+
+    split3: the dropped lo*lo term and the residual of the hi/lo split are each
+    below 2**-16 relative per operand pair, random in sign, so the normwise error
+    is about 2**-17 / sqrt(k); FP32 accumulation adds O(2**-24).  The north-star
+    bound 1e-6 holds for k >= 64; for tiny k the derived bound is used.  Each
+    Strassen level at most doubles the operand magnitudes and adds one more
+    signed combination, so 3**L margin is allowed.
+    plain BF16 rounding of the operand sums: about 2**-9 / sqrt(k) per product.
+    """
+    kk = max(k, 1)
+    if variant == "split3":
+        return max(1e-6, 8 * 2.0 ** -17 * 3 ** levels / math.sqrt(kk))
+    if variant == "bf16" and levels == 0:
+        return 1e-6  # inputs exactly representable, FP32 accumulation only
+    return 4 * U_BF16 * 3 ** levels / math.sqrt(kk)
+
+
+def _to_device(X, ld_pad, dtype):
+    rows, cols = X.shape
+    t = torch.zeros((rows, cols + ld_pad), dtype=dtype, device="cuda")
+    t[:, :cols] = torch.from_numpy(np.ascontiguousarray(X)).to(dtype=dtype, device="cuda")
+    return t[:, :cols]
+
+
+def run(m, n, k, levels, variant="split3", dist="uniform", seed=0, alpha=1.0, beta=0.0,
+        tile_n=0, pads=(0, 0, 0), c_fill=None, rows=None):
+    A, B = synth.problem(m, n, k, seed, dist)
+    in_dtype = torch.bfloat16 if variant == "bf16" else torch.float32
+    Ad = _to_device(A, pads[0], in_dtype)
+    Bd = _to_device(B, pads[1], in_dtype)
+    C0 = None
+    if beta != 0.0:
+        C0 = synth.uniform((m, n), seed + 5)
+        Cd = _to_device(C0, pads[2], torch.float32)
+    else:
+        Cd = _to_device(np.zeros((m, n), np.float32), pads[2], torch.float32)
+        if c_fill is not None:
+            Cd.fill_(c_fill)
+    fmm.gemm(Ad, Bd, Cd, alpha=alpha, beta=beta, levels=levels, variant=variant, tile_n=tile_n)
+    fmm.device_status()
+    C = Cd.cpu().numpy().astype(np.float64)
+    if variant == "bf16":
+        # the oracle sees exactly the bf16 values the GPU saw
+        Ab = Ad.cpu().contiguous().view(torch.int16).numpy().view(np.uint16)
+        Bb = Bd.cpu().contiguous().view(torch.int16).numpy().view(np.uint16)
+        C64 = oracle.classical(Ab, Bb, C0, alpha, beta, rows=rows, a_code=oracle.ORC_BF16,
+                               b_code=oracle.ORC_BF16)
+        An = float(np.linalg.norm(Ad.float().cpu().numpy()))
+        Bn = float(np.linalg.norm(Bd.float().cpu().numpy()))
+    else:
+        C64 = oracle.classical(A, B, C0, alpha, beta, rows=rows)
+        An = float(np.linalg.norm(A.astype(np.float64)))
+        Bn = float(np.linalg.norm(B.astype(np.float64)))
+    if rows is not None:
+        C = C[rows]
+        An = float(np.linalg.norm(A[rows].astype(np.float64)))
+    return C, C64, An, Bn
+
+
+# ------------------------------------------------------------ exact integers
+@pytest.mark.parametrize("variant", ["split3", "plain_bf16", "bf16"])
+@pytest.mark.parametrize("levels", [0, 1, 2])
+def test_int16_cube_bit_exact(variant, levels):
+    C, C64, _, _ = run(16, 16, 16, levels, variant, dist="int", seed=1)
+    np.testing.assert_array_equal(C, C64)
+
+
+@pytest.mark.parametrize("tile_n", [128, 256])
+@pytest.mark.parametrize("levels", [0, 1, 2])
+@pytest.mark.parametrize("m,n,k", [(300, 520, 200), (129, 257, 65), (1, 300, 1), (520, 8, 400)])
+def test_int_ragged_bit_exact(m, n, k, levels, tile_n):
+    C, C64, _, _ = run(m, n, k, levels, "split3", dist="int", seed=m + n + k, tile_n=tile_n)
+    np.testing.assert_array_equal(C, C64)
+
+
+def test_int_with_alpha_beta_bit_exact():
+    A, B = synth.problem(200, 136, 96, 3, "int")
+    C0 = synth.small_int((200, 136), 4)
+    Ad = torch.from_numpy(A).cuda()
+    Bd = torch.from_numpy(B).cuda()
+    Cd = torch.from_numpy(C0).cuda()
+    fmm.gemm(Ad, Bd, Cd, alpha=2.0, beta=-3.0, levels=2)
+    fmm.device_status()
+    np.testing.assert_array_equal(Cd.cpu().numpy(), oracle.classical(A, B, C0, 2.0, -3.0))
+
+
+# ------------------------------------------------------------------- floats
+def test_512_cube_one_level_split3_within_1e6():
+    C, C64, An, Bn = run(512, 512, 512, 1, "split3", seed=11)
+    err = oracle.normwise_error(C, C64, An, Bn)
+    assert err <= 1e-6, err
+
+
+@pytest.mark.parametrize("variant", ["split3", "plain_bf16", "bf16"])
+@pytest.mark.parametrize("levels", [0, 1, 2])
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (7, 13, 5), (130, 70, 300), (257, 129, 1000),
+                                   (640, 384, 96)])
+def test_float_shapes(m, n, k, levels, variant):
+    C, C64, An, Bn = run(m, n, k, levels, variant, dist="gaussian", seed=m * 7 + n + k)
+    err = oracle.normwise_error(C, C64, An, Bn)
+    assert err <= tolerance(variant, levels, k), err
+
+
+@pytest.mark.parametrize("levels", [0, 1, 2])
+def test_alpha_beta_and_padded_leading_dims(levels):
+    C, C64, An, Bn = run(300, 260, 150, levels, "split3", seed=5, alpha=-1.5, beta=0.75,
+                         pads=(5, 3, 9))
+    err = oracle.normwise_error(C, C64, An, Bn)
+    assert err <= tolerance("split3", levels, 150), err
+
+
+def test_beta_zero_does_not_read_c():
+    C, C64, An, Bn = run(130, 140, 150, 1, "split3", seed=6, c_fill=float("nan"))
+    assert np.all(np.isfinite(C))
+    assert oracle.normwise_error(C, C64, An, Bn) <= 1e-6
+
+
+def test_k_zero_scales_c():
+    Cd = torch.ones((33, 17), device="cuda")
+    A = torch.zeros((33, 0), device="cuda")
+    B = torch.zeros((0, 17), device="cuda")
+    fmm.gemm(A, B, Cd, alpha=1.0, beta=2.5, levels=1)
+    fmm.device_status()
+    assert torch.all(Cd == 2.5)
+
+
+def test_badly_scaled_two_level():
+    C, C64, An, Bn = run(512, 512, 512, 2, "split3", dist="badly_scaled", seed=8)
+    err = oracle.normwise_error(C, C64, An, Bn)
+    assert err <= 1e-6, err
+
+
+# -------------------------------------------------- full size, sampled rows
+@pytest.mark.parametrize("n,k,levels", [(16384, 16384, 2), (16384, 512, 2), (8192, 8192, 1)])
+def test_full_size_sampled_rows(n, k, levels):
+    m = n
+    rows = np.unique(synth.rng(123).integers(0, m, size=12))
+    C, C64, An, Bn = run(m, n, k, levels, "split3", seed=20, rows=rows, tile_n=0)
+    err = oracle.normwise_error(C, C64, An, Bn)
+    assert err <= 1e-6, err
+
+
+# ----------------------------------------------------------- failure path
+def test_bounded_wait_reports_timeout_and_context_survives():
+    fmm.set_wait_timeout_ns(20_000_000)  # 20 ms
+    try:
+        fmm.debug_wait_timeout()
+        with pytest.raises(fmm.FmmError) as ei:
+            fmm.device_status()
+        assert ei.value.status == 6
+    finally:
+        fmm.set_wait_timeout_ns(2_000_000_000)
+    fmm.device_status()  # word was cleared
+    C, C64, _, _ = run(64, 64, 64, 1, "split3", dist="int", seed=2)
+    np.testing.assert_array_equal(C, C64)
