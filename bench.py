@@ -1,0 +1,401 @@
+#!/usr/bin/env python
+"""Benchmark: effective TFLOPS (Eq. 4, 2mnk/t) of FP32-accurate two-level Strassen
+against the library's own classical tensor-core GEMM at the same accuracy, on GB300.
+
+Default workload: C = A @ B with m = n = k = 16384, A and B uniform[-1, 1] float32
+(seeded, synthetic), levels = 2, arithmetic "split3" (FP32 inputs, operand sums split
+into BF16 hi/lo, three BF16 tensor-core terms, FP32 accumulation).  A step is one
+full library call (beta pass, operand-sum passes, tensor-core kernel) on inputs that
+are already resident in HBM; inputs (1 GiB each) are larger than L2, so no flush is
+needed between steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle (FP64
+classical GEMM in C) on a bounded sample of rows of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "effective TFLOPS (2mnk/t) Strassen vs own classical GEMM on 1 GB300 at stated FP64 error"
+UNIT = "TFLOPS"
+FALLBACK_PEAK_TFLOPS = 1700.0  # sustained bf16, one earlier measurement on a GB300
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=16384, help="m = n")
+    ap.add_argument("--k", type=int, default=0, help="inner dimension (default: n)")
+    ap.add_argument("--levels", type=int, default=2)
+    ap.add_argument("--variant", default="split3")
+    ap.add_argument("--algo", default="auto")
+    ap.add_argument("--tile-n", type=int, default=0)
+    ap.add_argument("--err-rows", type=int, default=16)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-classical", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(a, k):
+    kind = "square" if k == a.n else "rank-k"
+    return f"strassen-L{a.levels}-{a.variant}-{kind}-m{a.n}-n{a.n}-k{k}"
+
+
+def config_dict(a, k, extra=None):
+    d = {
+        "workload": workload_name(a, k),
+        "m": a.n, "n": a.n, "k": k,
+        "levels": a.levels,
+        "variant": a.variant,
+        "algo": a.algo,
+        "inputs": "A, B float32 uniform[-1,1] seeded (synthetic); row-major; alpha=1, beta=0",
+        "l2": "inputs larger than L2 (no flush between steps)",
+        "comparator": "same library, levels=0, same arithmetic",
+    }
+    if extra:
+        d.update(extra)
+    return d
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f)
+    except OSError:
+        return None
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.uuid:
+                cmd += ["-i", self.uuid]
+            self.proc = subprocess.Popen(cmd, stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        rows = [r.strip().split(",") for r in self.tmp.read().splitlines() if r.strip()]
+        self.tmp.close()
+        os.unlink(self.tmp.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, r[5:9]):
+                if val.strip().lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------- oracle arm
+def cpu_oracle_rate(A, B, target_s, rows_hint=None):
+    """Time the FP64 classical oracle on a sample of output rows.  Returns
+    (TFLOPS, seconds, rows, cores)."""
+    import oracle
+    oracle.build()
+    cores = oracle.num_threads()
+    n, k = B.shape[1], A.shape[1]
+    if rows_hint is None:
+        probe = np.arange(cores) % A.shape[0]
+        t0 = time.perf_counter()
+        oracle.classical(A, B, rows=probe)
+        t1 = time.perf_counter() - t0
+        reps = max(1, int(target_s / max(t1, 1e-3)))
+        rows_hint = cores * reps
+    rows = np.arange(rows_hint) % A.shape[0]
+    t0 = time.perf_counter()
+    oracle.classical(A, B, rows=rows)
+    dt = time.perf_counter() - t0
+    return 2.0 * len(rows) * n * k / dt * 1e-12, dt, len(rows), cores
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    k = a.k or a.n
+    A = synth.uniform((a.n, k), 1234)
+    B = synth.uniform((k, a.n), 1235)
+    import oracle
+    oracle.build()
+    cores = oracle.num_threads()
+    # size one step so that warmup + steps end within about two minutes
+    budget = 100.0 / max(1, a.steps + a.warmup)
+    _, _, rows, _ = cpu_oracle_rate(A, B, budget)
+    for _ in range(a.warmup):
+        cpu_oracle_rate(A, B, budget, rows_hint=rows)
+    times = []
+    for _ in range(a.steps):
+        _, dt, _, _ = cpu_oracle_rate(A, B, budget, rows_hint=rows)
+        times.append(dt)
+    t = sum(times) / len(times)
+    val = 2.0 * rows * a.n * k / t * 1e-12
+    sample = f"{rows} of {a.n} output rows per step (FP64 classical oracle, all columns)"
+    line = {
+        "impl": "reference",
+        "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(a, k),
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def main():
+    a = parse_args()
+    if a.impl == "reference":
+        return run_reference(a)
+
+    import torch
+    import paper_1808_07984_gb300 as fmm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    fmm.build()
+    fmm.load()
+    k = a.k or a.n
+    m = n = a.n
+    # replicas: each rank multiplies its own seeded problem of the same shape
+    A = synth.uniform((m, k), 1234 + 2 * rank)
+    B = synth.uniform((k, n), 1235 + 2 * rank)
+    A_h = torch.from_numpy(A).pin_memory()
+    B_h = torch.from_numpy(B).pin_memory()
+    C_h = torch.empty((m, n), dtype=torch.float32).pin_memory()
+    A_d = A_h.to(dev)
+    B_d = B_h.to(dev)
+    C_d = torch.empty((m, n), dtype=torch.float32, device=dev)
+    ws_bytes = max(fmm.workspace_size(m, n, k, a.levels, a.variant, a.algo, a.tile_n),
+                   0 if a.no_classical else fmm.workspace_size(m, n, k, 0, a.variant, a.algo, a.tile_n))
+    ws = torch.empty(max(ws_bytes, 256), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(levels):
+        fmm.gemm(A_d, B_d, C_d, 1.0, 0.0, levels=levels, variant=a.variant, algo=a.algo,
+                 tile_n=a.tile_n, workspace=ws, stream=stream)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed(levels, steps, warmup, profile=False):
+        for _ in range(warmup):
+            step(levels)
+        fmm.device_status()
+        barrier()
+        torch.cuda.synchronize()
+        if profile:
+            fmm.profile_read()
+            fmm.profile_enable(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step(levels)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        prof = None
+        if profile:
+            fmm.profile_enable(False)
+            prof = fmm.profile_read()
+        fmm.device_status()
+        return e0.elapsed_time(e1) / steps, prof
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+
+    # ---- Strassen, device-resident (the headline value)
+    for _ in range(a.warmup):
+        step(a.levels)
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    ms, prof = timed(a.levels, a.steps, 0, profile=True)
+    clk = clocks.stop()
+    ms = max_over_ranks(ms)
+    flops = 2.0 * m * n * k
+    value = world * flops / (ms * 1e-3) * 1e-12
+
+    # ---- classical comparator at the same arithmetic
+    classical = None
+    if not a.no_classical:
+        ms0, prof0 = timed(0, a.steps, a.warmup, profile=True)
+        ms0 = max_over_ranks(ms0)
+        classical = {"value": world * flops / (ms0 * 1e-3) * 1e-12, "ms_per_step": ms0,
+                     "tensor_kernel_ms": prof0["tensor"][0] / max(prof0["tensor"][1], 1)}
+
+    # ---- end to end through host buffers (H2D of A, B and D2H of C inside the region)
+    def e2e_step():
+        A_d.copy_(A_h, non_blocking=True)
+        B_d.copy_(B_h, non_blocking=True)
+        step(a.levels)
+        C_h.copy_(C_d, non_blocking=True)
+
+    for _ in range(max(1, a.warmup)):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    fmm.device_status()
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / a.steps)
+    e2e = {"value": world * flops / (ms_e2e * 1e-3) * 1e-12, "unit": UNIT,
+           "h2d_bytes_per_step": int(A_h.numel() * 4 + B_h.numel() * 4),
+           "d2h_bytes_per_step": int(C_h.numel() * 4), "ms_per_step": ms_e2e}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    # ---- accuracy vs the FP64 oracle on sampled rows (rank 0's problem)
+    import oracle
+    step(a.levels)
+    torch.cuda.synchronize()
+    rows = np.unique(synth.rng(7).integers(0, m, size=a.err_rows))
+    C_s = C_d[torch.from_numpy(rows).to(dev)].cpu().numpy()
+    C64 = oracle.classical(A, B, rows=rows)
+    err = oracle.normwise_error(C_s, C64, np.linalg.norm(A[rows].astype(np.float64)),
+                                np.linalg.norm(B.astype(np.float64)))
+    err0 = None
+    if not a.no_classical:
+        step(0)
+        torch.cuda.synchronize()
+        C_s0 = C_d[torch.from_numpy(rows).to(dev)].cpu().numpy()
+        err0 = oracle.normwise_error(C_s0, C64, np.linalg.norm(A[rows].astype(np.float64)),
+                                     np.linalg.norm(B.astype(np.float64)))
+        classical["fp64_normwise_err_sampled"] = err0
+
+    # ---- roofline of the dominant kernel (the tensor-core kernel)
+    terms = 3 if a.variant == "split3" else 1
+    ker_ms = prof["tensor"][0] / max(prof["tensor"][1], 1)
+    mma_flops = (7.0 / 8.0) ** a.levels * flops * terms
+    achieved = mma_flops / (ker_ms * 1e-3) * 1e-12
+    peaks = load_peaks()
+    if peaks and "bf16_tflops_sustained" in peaks:
+        peak, peak_src = float(peaks["bf16_tflops_sustained"]), "measured (sustained bf16)"
+    else:
+        peak, peak_src = FALLBACK_PEAK_TFLOPS, "fallback"
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                "kernel": "fmm_packed_kernel", "kernel_ms": ker_ms,
+                "algorithmic_flops_per_launch": mma_flops}
+    phases = {p: {"ms_per_step": v[0] / a.steps, "launches": v[1]} for p, v in prof.items()}
+    gpu_launches = int(sum(v[1] for v in prof.values()))
+
+    cpu = None
+    if not a.no_cpu_baseline:
+        v, dt, nrows, cores = cpu_oracle_rate(A, B, a.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{nrows} of {m} output rows of the same product (FP64 classical oracle), "
+                         f"{dt:.1f} s"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
+        "config": config_dict(a, k, {"parallelism": f"replicas{world}" if world > 1 else "single"}),
+        "fp64_normwise_err_sampled": err,
+        "classical": classical,
+        "speedup_vs_classical": (value / classical["value"]) if classical else None,
+        "phases": phases,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clk,
+        "gpu_launches": gpu_launches,
+    }
+    print(json.dumps(line), flush=True)
+    print(f"[bench] {workload_name(a, k)}: {value:.1f} eff TFLOPS ({ms:.2f} ms/step), "
+          f"classical {classical['value'] if classical else float('nan'):.1f}, "
+          f"tensor kernel {ker_ms:.2f} ms = {achieved:.0f} TFLOP/s ({achieved / peak:.1%} of {peak_src}), "
+          f"err {err:.2e}", file=sys.stderr)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -92,7 +92,9 @@ typedef struct fmm_options {
     int algo;       /* fmm_algo; 0 = automatic choice */
     int tile_n;     /* 0 = automatic; otherwise 128 or 256 */
     int num_ctas;   /* 0 = one persistent CTA per SM */
-    int reserved[5];
+    int b_kmajor;   /* packed algorithm: 1 stores the B-operand sums transposed (K-major);
+                       0 (default) keeps them row-major and the tensor cores read B MN-major */
+    int reserved[4];
 } fmm_options;
 
 /* Bytes of workspace fmm_gemm needs for this problem (0 when none).  Returns

@@ -33,7 +33,7 @@ class FmmError(RuntimeError):
 
 class _Options(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int), ("tile_n", ctypes.c_int), ("num_ctas", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("b_kmajor", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 _lib = None
@@ -91,11 +91,12 @@ def _check(status: int):
         raise FmmError(status, load().fmm_last_error().decode())
 
 
-def _opts(algo="auto", tile_n=0, num_ctas=0):
+def _opts(algo="auto", tile_n=0, num_ctas=0, b_kmajor=0):
     o = _Options()
     o.algo = ALGOS[algo] if isinstance(algo, str) else int(algo)
     o.tile_n = int(tile_n)
     o.num_ctas = int(num_ctas)
+    o.b_kmajor = int(b_kmajor)
     return o
 
 
@@ -103,8 +104,8 @@ def _variant(v) -> int:
     return VARIANTS[v] if isinstance(v, str) else int(v)
 
 
-def workspace_size(m, n, k, levels=1, variant="split3", algo="auto", tile_n=0) -> int:
-    o = _opts(algo, tile_n)
+def workspace_size(m, n, k, levels=1, variant="split3", algo="auto", tile_n=0, b_kmajor=0) -> int:
+    o = _opts(algo, tile_n, 0, b_kmajor)
     ws = load().fmm_workspace_size_ex(m, n, k, levels, _variant(variant), ctypes.byref(o))
     if ws == ctypes.c_size_t(-1).value:
         raise FmmError(3, "unsupported combination")
@@ -123,7 +124,7 @@ _IN_DTYPE = {0: "float32", 1: "bfloat16", 2: "float16", 3: "float32"}
 
 def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
          variant="split3", algo="auto", tile_n: int = 0, num_ctas: int = 0,
-         workspace=None, stream=None):
+         workspace=None, stream=None, b_kmajor: int = 0):
     """C = alpha * A @ B + beta * C on the current CUDA device (torch tensors).
 
     A (m x k) and B (k x n) are row-major CUDA tensors of the element type the
@@ -151,12 +152,12 @@ def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
         beta = 0.0
     if C.dtype != torch.float32 or not C.is_cuda or (C.numel() and C.stride(1) != 1):
         raise FmmError(1, "C must be a float32 CUDA tensor with contiguous rows")
-    ws_need = workspace_size(m, n, k, levels, v, algo, tile_n)
+    ws_need = workspace_size(m, n, k, levels, v, algo, tile_n, b_kmajor)
     if workspace is None and ws_need > 0:
         workspace = torch.empty(ws_need, dtype=torch.uint8, device=A.device)
     ws_ptr = workspace.data_ptr() if workspace is not None else None
     ws_bytes = workspace.numel() if workspace is not None else 0
-    o = _opts(algo, tile_n, num_ctas)
+    o = _opts(algo, tile_n, num_ctas, b_kmajor)
     st = load().fmm_gemm_ex(m, n, k, float(alpha), A.data_ptr(), max(A.stride(0), 1),
                             B.data_ptr(), max(B.stride(0), 1), float(beta), C.data_ptr(),
                             max(C.stride(0), 1), int(levels), v, ws_ptr, ws_bytes,

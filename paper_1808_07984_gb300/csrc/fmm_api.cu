@@ -120,16 +120,6 @@ fmm_status device_info(DeviceInfo& out) {
 }
 
 // ---------------------------------------------------------------- planner
-// Eq. (3), Section 3: the seven products of one-level Strassen.  Quadrant q = 2*row + col
-// (Eq. 2).  kU[r][q]: coefficient of A_q in the A-operand of product r; kV[r][q]: of B_q in
-// its B-operand; kW[r][q]: coefficient with which M_r is added into C_q.
-constexpr int8_t kU[7][4] = {{1, 0, 0, 1}, {0, 0, 1, 1},  {1, 0, 0, 0}, {0, 0, 0, 1},
-                             {1, 1, 0, 0}, {-1, 0, 1, 0}, {0, 1, 0, -1}};
-constexpr int8_t kV[7][4] = {{1, 0, 0, 1}, {1, 0, 0, 0}, {0, 1, 0, -1}, {-1, 0, 1, 0},
-                             {0, 0, 0, 1}, {1, 1, 0, 0}, {0, 0, 1, 1}};
-constexpr int8_t kW[7][4] = {{1, 0, 0, 1},  {0, 0, 1, -1}, {0, 1, 0, 1}, {1, 0, 1, 0},
-                             {-1, 1, 0, 0}, {0, 0, 0, 1},  {1, 0, 0, 0}};
-
 struct Term {
   int block;  // bi * 2^L + bj
   int sign;
@@ -157,9 +147,9 @@ std::vector<Product> make_products(int L) {
       for (int i = L - 1, t = qi; i >= 0; --i, t /= 4) qd[i] = t % 4;
       int cu = 1, cv = 1, cw = 1, br = 0, bc = 0;
       for (int i = 0; i < L; ++i) {
-        cu *= kU[rd[i]][qd[i]];
-        cv *= kV[rd[i]][qd[i]];
-        cw *= kW[rd[i]][qd[i]];
+        cu *= strassen_u(rd[i], qd[i]);
+        cv *= strassen_v(rd[i], qd[i]);
+        cw *= strassen_w(rd[i], qd[i]);
         br = 2 * br + qd[i] / 2;
         bc = 2 * bc + qd[i] % 2;
       }
@@ -183,9 +173,12 @@ int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 struct Plan {
   int L = 0, R = 1, terms = 3, in_type = kInF32;
   bool bf16 = true;
+  bool b_mn = true;  // B-operand sums row-major (k x n), read MN-major by the tensor cores
   int tile_n = 128;
   int algo = FMM_ALGO_PACKED;
-  int64_t hm = 0, hn = 0, hk = 0, ldw = 0;
+  int64_t hm = 0, hn = 0, hk = 0;
+  int64_t lda_w = 0;  // row stride of the A-operand sums (h_k rounded up to 8)
+  int64_t ldb_w = 0;  // row stride of the B-operand sums (h_n or, K-major, h_k, rounded up to 8)
   size_t a_bytes = 0, b_bytes = 0;  // per term array
   size_t ws = 0;
 };
@@ -209,14 +202,17 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
   pl.tile_n = (opt && opt->tile_n) ? opt->tile_n : 128;
   if (!packed_config_supported(pl.tile_n, pl.terms, pl.bf16))
     return fail(FMM_ERR_UNSUPPORTED, "tile_n must be 128 or 256");
+  pl.b_mn = !(opt && opt->b_kmajor);
   pl.hm = block_size(m, levels);
   pl.hn = block_size(n, levels);
   pl.hk = block_size(k, levels);
-  pl.ldw = round_up(std::max<int64_t>(pl.hk, 1), 8);
+  pl.lda_w = round_up(std::max<int64_t>(pl.hk, 1), 8);
+  pl.ldb_w = pl.b_mn ? round_up(std::max<int64_t>(pl.hn, 1), 8) : pl.lda_w;
   if (pl.hm >= (int64_t(1) << 31) || pl.hn >= (int64_t(1) << 31) || pl.hk >= (int64_t(1) << 31))
     return fail(FMM_ERR_ARG, "dimension too large");
-  pl.a_bytes = static_cast<size_t>(round_up(static_cast<int64_t>(pl.R) * pl.hm * pl.ldw * 2, 256));
-  pl.b_bytes = static_cast<size_t>(round_up(static_cast<int64_t>(pl.R) * pl.hn * pl.ldw * 2, 256));
+  pl.a_bytes = static_cast<size_t>(round_up(static_cast<int64_t>(pl.R) * pl.hm * pl.lda_w * 2, 256));
+  pl.b_bytes = static_cast<size_t>(
+      round_up(static_cast<int64_t>(pl.R) * (pl.b_mn ? pl.hk : pl.hn) * pl.ldb_w * 2, 256));
   const size_t arrays = pl.terms == 3 ? 2 : 1;
   pl.ws = (m == 0 || n == 0 || k == 0) ? 0 : arrays * (pl.a_bytes + pl.b_bytes);
   return FMM_OK;
@@ -229,12 +225,12 @@ bool overlaps(const void* a, size_t abytes, const void* b, size_t bbytes) {
 }
 
 fmm_status encode_3d(CUtensorMap* map, void* base, int64_t inner, int64_t rows, int64_t depth,
-                     int64_t ld_elems, int box_rows) {
+                     int64_t ld_elems, int box_inner, int box_rows) {
   const cuuint64_t dims[3] = {static_cast<cuuint64_t>(inner), static_cast<cuuint64_t>(rows),
                               static_cast<cuuint64_t>(depth)};
   const cuuint64_t strides[2] = {static_cast<cuuint64_t>(ld_elems * 2),
                                  static_cast<cuuint64_t>(ld_elems * 2 * rows)};
-  const cuuint32_t box[3] = {static_cast<cuuint32_t>(kBK), static_cast<cuuint32_t>(box_rows), 1};
+  const cuuint32_t box[3] = {static_cast<cuuint32_t>(box_inner), static_cast<cuuint32_t>(box_rows), 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -292,60 +288,86 @@ fmm_status gemm_impl(int64_t m, int64_t n, int64_t k, float alpha, const void* A
   uint16_t* a_lo = pl.terms == 3 ? reinterpret_cast<uint16_t*>(wsb + pl.a_bytes + pl.b_bytes) : nullptr;
   uint16_t* b_lo = pl.terms == 3 ? reinterpret_cast<uint16_t*>(wsb + 2 * pl.a_bytes + pl.b_bytes) : nullptr;
 
-  // ---- operand-sum passes (all 7^L A-operands, then all B-operands, K-major)
+  // ---- operand-sum passes (all 7^L A-operands, then all B-operands)
   {
-    PhaseScope ps(kPhasePack, s);
-    PackParams pa;
-    std::memset(&pa, 0, sizeof pa);
-    pa.X = A;
-    pa.ldx = lda;
-    pa.rows = m;
-    pa.cols = k;
-    pa.hr = static_cast<int32_t>(pl.hm);
-    pa.hc = static_cast<int32_t>(pl.hk);
-    pa.gdim = g;
-    pa.nsrc = g * g;
-    pa.nprod = pl.R;
-    pa.terms = pl.terms;
-    pa.ld_out = pl.ldw;
-    pa.prod_stride = pl.hm * pl.ldw;
-    pa.out_hi = a_hi;
-    pa.out_lo = a_lo;
-    for (int r = 0; r < pl.R; ++r) {
-      pa.cnt[r] = static_cast<int8_t>(prods[r].a.size());
-      for (size_t t = 0; t < prods[r].a.size(); ++t)
-        pa.term[r][t] = {static_cast<int16_t>(prods[r].a[t].block), static_cast<int16_t>(prods[r].a[t].sign)};
+    SumParams sa;
+    std::memset(&sa, 0, sizeof sa);
+    sa.X = A;
+    sa.ldx = lda;
+    sa.rows = m;
+    sa.cols = k;
+    sa.hr = pl.hm;
+    sa.hc = pl.hk;
+    sa.ld_out = pl.lda_w;
+    sa.prod_stride = pl.hm * pl.lda_w;
+    sa.out_hi = a_hi;
+    sa.out_lo = a_lo;
+    sa.terms = pl.terms;
+    sa.vec_ok = (reinterpret_cast<uintptr_t>(A) % 16 == 0 && lda % 4 == 0) ? 1 : 0;
+    cudaError_t e;
+    {
+      PhaseScope ps(kPhasePack, s);
+      e = launch_operand_sums(sa, pl.L, false, pl.in_type, pl.bf16 ? 0 : 1, dev.sms, s);
     }
-    cudaError_t e = launch_pack(pa, pl.in_type, pl.bf16 ? 0 : 1, false, dev.sms, s);
     if (e != cudaSuccess) return cuda_fail(e, "operand-sum pass (A)");
-
-    PackParams pb = pa;
-    pb.X = B;
-    pb.ldx = ldb;
-    pb.rows = k;
-    pb.cols = n;
-    pb.hr = static_cast<int32_t>(pl.hk);
-    pb.hc = static_cast<int32_t>(pl.hn);
-    pb.prod_stride = pl.hn * pl.ldw;
-    pb.out_hi = b_hi;
-    pb.out_lo = b_lo;
-    for (int r = 0; r < pl.R; ++r) {
-      pb.cnt[r] = static_cast<int8_t>(prods[r].b.size());
-      for (size_t t = 0; t < prods[r].b.size(); ++t)
-        pb.term[r][t] = {static_cast<int16_t>(prods[r].b[t].block), static_cast<int16_t>(prods[r].b[t].sign)};
+    if (pl.b_mn) {
+      SumParams sb = sa;
+      sb.X = B;
+      sb.ldx = ldb;
+      sb.rows = k;
+      sb.cols = n;
+      sb.hr = pl.hk;
+      sb.hc = pl.hn;
+      sb.ld_out = pl.ldb_w;
+      sb.prod_stride = pl.hk * pl.ldb_w;
+      sb.out_hi = b_hi;
+      sb.out_lo = b_lo;
+      sb.vec_ok = (reinterpret_cast<uintptr_t>(B) % 16 == 0 && ldb % 4 == 0) ? 1 : 0;
+      {
+        PhaseScope ps(kPhasePack, s);
+        e = launch_operand_sums(sb, pl.L, true, pl.in_type, pl.bf16 ? 0 : 1, dev.sms, s);
+      }
+    } else {
+      PackParams pb;
+      std::memset(&pb, 0, sizeof pb);
+      pb.X = B;
+      pb.ldx = ldb;
+      pb.rows = k;
+      pb.cols = n;
+      pb.hr = static_cast<int32_t>(pl.hk);
+      pb.hc = static_cast<int32_t>(pl.hn);
+      pb.gdim = g;
+      pb.nsrc = g * g;
+      pb.nprod = pl.R;
+      pb.terms = pl.terms;
+      pb.ld_out = pl.ldb_w;
+      pb.prod_stride = pl.hn * pl.ldb_w;
+      pb.out_hi = b_hi;
+      pb.out_lo = b_lo;
+      for (int r = 0; r < pl.R; ++r) {
+        pb.cnt[r] = static_cast<int8_t>(prods[r].b.size());
+        for (size_t t = 0; t < prods[r].b.size(); ++t)
+          pb.term[r][t] = {static_cast<int16_t>(prods[r].b[t].block), static_cast<int16_t>(prods[r].b[t].sign)};
+      }
+      {
+        PhaseScope ps(kPhasePack, s);
+        e = launch_pack(pb, pl.in_type, pl.bf16 ? 0 : 1, true, dev.sms, s);
+      }
     }
-    e = launch_pack(pb, pl.in_type, pl.bf16 ? 0 : 1, true, dev.sms, s);
     if (e != cudaSuccess) return cuda_fail(e, "operand-sum pass (B)");
   }
 
   // ---- tensor-core pass
   PackedParams* pp = new PackedParams;
   std::memset(pp, 0, sizeof(PackedParams));
-  st = encode_3d(&pp->tmA[0], a_hi, pl.hk, pl.hm, pl.R, pl.ldw, kBM);
-  if (st == FMM_OK) st = encode_3d(&pp->tmB[0], b_hi, pl.hk, pl.hn, pl.R, pl.ldw, pl.tile_n);
-  if (st == FMM_OK && pl.terms == 3) {
-    st = encode_3d(&pp->tmA[1], a_lo, pl.hk, pl.hm, pl.R, pl.ldw, kBM);
-    if (st == FMM_OK) st = encode_3d(&pp->tmB[1], b_lo, pl.hk, pl.hn, pl.R, pl.ldw, pl.tile_n);
+  const int nb = pl.terms == 3 ? 2 : 1;
+  for (int t = 0; t < nb && st == FMM_OK; ++t) {
+    st = encode_3d(&pp->tmA[t], t ? a_lo : a_hi, pl.hk, pl.hm, pl.R, pl.lda_w, kBK, kBM);
+    if (st != FMM_OK) break;
+    if (pl.b_mn)
+      st = encode_3d(&pp->tmB[t], t ? b_lo : b_hi, pl.hn, pl.hk, pl.R, pl.ldb_w, 64, kBK);
+    else
+      st = encode_3d(&pp->tmB[t], t ? b_lo : b_hi, pl.hk, pl.hn, pl.R, pl.ldb_w, kBK, pl.tile_n);
   }
   if (st != FMM_OK) {
     delete pp;
@@ -386,7 +408,7 @@ fmm_status gemm_impl(int64_t m, int64_t n, int64_t k, float alpha, const void* A
   cudaError_t e;
   {
     PhaseScope ps(kPhaseTensor, s);
-    e = launch_packed(*pp, pl.tile_n, pl.terms, pl.bf16, grid, s);
+    e = launch_packed(*pp, pl.tile_n, pl.terms, pl.bf16, pl.b_mn, grid, s);
   }
   delete pp;
   if (e != cudaSuccess) return cuda_fail(e, "tensor-core pass");

@@ -31,6 +31,25 @@ constexpr int kMaxDest = 4;       // W_C <= 4 at two levels
 constexpr int kMaxSources = 16;   // 4^2 blocks per operand at two levels
 constexpr int kThreads = 256;
 
+// Eq. (3), Section 3: the seven products of one-level Strassen.  Quadrant q = 2*row + col
+// (Eq. 2).  strassen_u(r, q): coefficient of A_q in the A-operand of product r; strassen_v:
+// of B_q in its B-operand; strassen_w: coefficient with which M_r is added into C_q.
+__host__ __device__ constexpr int strassen_u(int r, int q) {
+  constexpr int8_t t[7][4] = {{1, 0, 0, 1}, {0, 0, 1, 1},  {1, 0, 0, 0}, {0, 0, 0, 1},
+                              {1, 1, 0, 0}, {-1, 0, 1, 0}, {0, 1, 0, -1}};
+  return t[r][q];
+}
+__host__ __device__ constexpr int strassen_v(int r, int q) {
+  constexpr int8_t t[7][4] = {{1, 0, 0, 1}, {1, 0, 0, 0}, {0, 1, 0, -1}, {-1, 0, 1, 0},
+                              {0, 0, 0, 1}, {1, 1, 0, 0}, {0, 0, 1, 1}};
+  return t[r][q];
+}
+__host__ __device__ constexpr int strassen_w(int r, int q) {
+  constexpr int8_t t[7][4] = {{1, 0, 0, 1},  {0, 0, 1, -1}, {0, 1, 0, 1}, {1, 0, 1, 0},
+                              {-1, 1, 0, 0}, {0, 0, 0, 1},  {1, 0, 0, 0}};
+  return t[r][q];
+}
+
 enum ErrBits : unsigned {
   kErrProducerWait = 1u,
   kErrMmaWait = 2u,
@@ -91,6 +110,20 @@ struct PackParams {
   SrcTerm term[kMaxProducts][kMaxDest];
 };
 
+// Parameters of the operand-sum pass over one operand (A or B), row-major in and out.
+struct SumParams {
+  const void* X;       // source matrix, row-major
+  int64_t ldx;
+  int64_t rows, cols;  // extent of X
+  int64_t hr, hc;      // block size along rows / cols of X
+  int64_t ld_out;      // row stride of the output (elements, multiple of 8)
+  int64_t prod_stride; // elements between consecutive products in the output
+  uint16_t* out_hi;
+  uint16_t* out_lo;
+  int32_t terms;       // 3: split hi/lo, 1: single rounding
+  int32_t vec_ok;      // X base and ldx allow vector loads
+};
+
 __device__ __forceinline__ void decode_item(int item, int tiles_m, int tiles_n, int& r, int& tm,
                                             int& tn) {
   const int per_prod = tiles_m * tiles_n;
@@ -118,7 +151,7 @@ struct PackedCfg {
   static constexpr uint32_t kTmemCols = 2 * BN;
 };
 
-template <int BN, int TERMS, int STAGES, bool BF16>
+template <int BN, int TERMS, int STAGES, bool BF16, bool B_MN>
 __global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_constant__ PackedParams p) {
   using Cfg = PackedCfg<BN, TERMS, STAGES>;
   static_assert(BN % 32 == 0 && BN >= 32 && BN <= 256, "UMMA N");
@@ -187,10 +220,21 @@ __global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_co
           const uint32_t fb = smem_u32(&full[stage]);
           mbar_arrive_expect_tx(fb, Cfg::kStageBytes);
           tma_load_3d(smem_u32(st), &p.tmA[0], fb, kb * kBK, tm * kBM, r);
-          tma_load_3d(smem_u32(st + Cfg::kABytes), &p.tmB[0], fb, kb * kBK, tn * BN, r);
-          if (TERMS == 3) {
+          if (TERMS == 3)
             tma_load_3d(smem_u32(st + Cfg::kABytes + Cfg::kBBytes), &p.tmA[1], fb, kb * kBK, tm * kBM, r);
-            tma_load_3d(smem_u32(st + 2 * Cfg::kABytes + Cfg::kBBytes), &p.tmB[1], fb, kb * kBK, tn * BN, r);
+          if (B_MN) {
+            // B operand sums stored k-rows x n-cols: BN/64 boxes of 64 (n) x 64 (k), 8 KB each
+#pragma unroll
+            for (int j = 0; j < BN / 64; ++j) {
+              tma_load_3d(smem_u32(st + Cfg::kABytes + j * 8192), &p.tmB[0], fb, tn * BN + 64 * j, kb * kBK, r);
+              if (TERMS == 3)
+                tma_load_3d(smem_u32(st + 2 * Cfg::kABytes + Cfg::kBBytes + j * 8192), &p.tmB[1], fb,
+                            tn * BN + 64 * j, kb * kBK, r);
+            }
+          } else {
+            tma_load_3d(smem_u32(st + Cfg::kABytes), &p.tmB[0], fb, kb * kBK, tn * BN, r);
+            if (TERMS == 3)
+              tma_load_3d(smem_u32(st + 2 * Cfg::kABytes + Cfg::kBBytes), &p.tmB[1], fb, kb * kBK, tn * BN, r);
           }
           if (++stage == STAGES) {
             stage = 0;
@@ -208,7 +252,7 @@ __global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_co
   } else if (warp == 1) {
     // ---------------------------------------------------------- MMA issuer
     if (lane == 0) {
-      constexpr uint32_t idesc = make_idesc_f16(kBM, BN, BF16);
+      constexpr uint32_t idesc = make_idesc_f16(kBM, BN, BF16, B_MN);
       int stage = 0;
       uint32_t phase = 0;
       int it = 0;
@@ -230,16 +274,22 @@ __global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_co
           tc_fence_after();
           uint8_t* st = smem + stage * Cfg::kStageBytes;
           const uint64_t da_hi = make_sdesc_kmajor_sw128(smem_u32(st));
-          const uint64_t db_hi = make_sdesc_kmajor_sw128(smem_u32(st + Cfg::kABytes));
           const uint64_t da_lo = make_sdesc_kmajor_sw128(smem_u32(st + Cfg::kABytes + Cfg::kBBytes));
-          const uint64_t db_lo = make_sdesc_kmajor_sw128(smem_u32(st + 2 * Cfg::kABytes + Cfg::kBBytes));
+          const uint64_t db_hi = B_MN ? make_sdesc_mnmajor_sw128(smem_u32(st + Cfg::kABytes), 8192, 1024)
+                                      : make_sdesc_kmajor_sw128(smem_u32(st + Cfg::kABytes));
+          const uint64_t db_lo =
+              B_MN ? make_sdesc_mnmajor_sw128(smem_u32(st + 2 * Cfg::kABytes + Cfg::kBBytes), 8192, 1024)
+                   : make_sdesc_kmajor_sw128(smem_u32(st + 2 * Cfg::kABytes + Cfg::kBBytes));
 #pragma unroll
           for (int kk = 0; kk < kBK / 16; ++kk) {
-            const uint64_t ko = static_cast<uint64_t>(kk * 2);  // 32 bytes, encoded >> 4
-            umma_f16_ss(d_tmem, da_hi + ko, db_hi + ko, idesc, (kb | kk) != 0 ? 1u : 0u);
+            // K-major: 16 elements = 32 bytes inside the swizzle row; MN-major: 16 k-rows =
+            // two 1024-byte atoms.  Descriptor start addresses are encoded >> 4.
+            const uint64_t ka = static_cast<uint64_t>(kk * 2);
+            const uint64_t kb16 = B_MN ? static_cast<uint64_t>(kk * 128) : ka;
+            umma_f16_ss(d_tmem, da_hi + ka, db_hi + kb16, idesc, (kb | kk) != 0 ? 1u : 0u);
             if (TERMS == 3) {
-              umma_f16_ss(d_tmem, da_hi + ko, db_lo + ko, idesc, 1u);
-              umma_f16_ss(d_tmem, da_lo + ko, db_hi + ko, idesc, 1u);
+              umma_f16_ss(d_tmem, da_hi + ka, db_lo + kb16, idesc, 1u);
+              umma_f16_ss(d_tmem, da_lo + ka, db_hi + kb16, idesc, 1u);
             }
           }
           umma_commit(smem_u32(&empty[stage]));

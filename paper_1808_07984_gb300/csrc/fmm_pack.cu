@@ -7,6 +7,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <cstring>
 #include "fmm_kernels.cuh"
 #include "launch.h"
 
@@ -30,61 +31,164 @@ __device__ __forceinline__ uint16_t round16(float x) {
   return __half_as_ushort(__float2half_rn(x));
 }
 
-// A-side: out[r][i][l] = sum_t sign_t * X[block(src_t) origin + (i, l)], i < hr, l < hc.
-// Each thread handles 4 consecutive l of one row.
-template <typename T, int OUT16, int NSRC>
-__global__ void __launch_bounds__(256) pack_rows_kernel(const __grid_constant__ PackParams p) {
-  const T* X = static_cast<const T*>(p.X);
-  const int64_t quads_per_row = (p.hc + 3) / 4;  // a partial last quad writes into the row padding
-  const int64_t total = static_cast<int64_t>(p.hr) * quads_per_row;
-  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
-       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t i = idx / quads_per_row;
-    const int64_t l0 = (idx - i * quads_per_row) * 4;
-    float v[NSRC][4];
+// Operand sums of all 7^L products of one operand, row-major in and row-major out.
+//   X is (rows x cols), viewed as a 2^L x 2^L grid of hr x hc blocks (zero outside X);
+//   out[r][i][l] = sum_q coef(r, q) * X_q[i, l] for i < hr, l < hc, in FP32, then either
+//   rounded once to 16 bits or split into hi = bf16(P), lo = bf16(P - hi).
+// coef is strassen_u for A and strassen_v for B (Eq. 3); for two levels the product
+// (r1, r2) takes block (q1, q2) with coefficient coef(r1, q1) * coef(r2, q2) and the sum is
+// formed as sum_q2 coef(r2, q2) * (sum_q1 coef(r1, q1) * X_(q1, q2)).
+// Each thread handles EPT consecutive columns of one row.
+template <bool IS_B>
+__device__ __forceinline__ constexpr int coef(int r, int q) {
+  return IS_B ? strassen_v(r, q) : strassen_u(r, q);
+}
+
+template <int TERMS, int OUT16, int EPT>
+__device__ __forceinline__ void store_sum(const SumParams& p, int64_t o, const float (&acc)[EPT]) {
+  if (TERMS == 3) {
+    uint16_t h[EPT], w[EPT];
 #pragma unroll
-    for (int s = 0; s < NSRC; ++s) {
-      const int bi = s / p.gdim, bj = s - (s / p.gdim) * p.gdim;
-      const int64_t gr = static_cast<int64_t>(bi) * p.hr + i;
-      const int64_t gc = static_cast<int64_t>(bj) * p.hc + l0;
+    for (int e = 0; e < EPT; ++e) {
+      const __nv_bfloat16 hb = __float2bfloat16_rn(acc[e]);
+      h[e] = __bfloat16_as_ushort(hb);
+      w[e] = __bfloat16_as_ushort(__float2bfloat16_rn(acc[e] - __bfloat162float(hb)));
+    }
+    if (EPT == 8) {
+      *reinterpret_cast<uint4*>(p.out_hi + o) =
+          make_uint4(h[0] | (uint32_t(h[1]) << 16), h[2] | (uint32_t(h[3]) << 16),
+                     h[4] | (uint32_t(h[5]) << 16), h[6] | (uint32_t(h[7]) << 16));
+      *reinterpret_cast<uint4*>(p.out_lo + o) =
+          make_uint4(w[0] | (uint32_t(w[1]) << 16), w[2] | (uint32_t(w[3]) << 16),
+                     w[4] | (uint32_t(w[5]) << 16), w[6] | (uint32_t(w[7]) << 16));
+    } else {
+      *reinterpret_cast<uint2*>(p.out_hi + o) =
+          make_uint2(h[0] | (uint32_t(h[1]) << 16), h[2] | (uint32_t(h[3]) << 16));
+      *reinterpret_cast<uint2*>(p.out_lo + o) =
+          make_uint2(w[0] | (uint32_t(w[1]) << 16), w[2] | (uint32_t(w[3]) << 16));
+    }
+  } else {
+    uint16_t h[EPT];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        v[s][e] = (gr < p.rows && gc + e < p.cols && l0 + e < p.hc)
-                      ? load_as_float<T>(X + gr * p.ldx + gc + e)
-                      : 0.f;
+    for (int e = 0; e < EPT; ++e) h[e] = round16<OUT16>(acc[e]);
+    if (EPT == 8) {
+      *reinterpret_cast<uint4*>(p.out_hi + o) =
+          make_uint4(h[0] | (uint32_t(h[1]) << 16), h[2] | (uint32_t(h[3]) << 16),
+                     h[4] | (uint32_t(h[5]) << 16), h[6] | (uint32_t(h[7]) << 16));
+    } else {
+      *reinterpret_cast<uint2*>(p.out_hi + o) =
+          make_uint2(h[0] | (uint32_t(h[1]) << 16), h[2] | (uint32_t(h[3]) << 16));
+    }
+  }
+}
+
+template <typename T, int EPT>
+__device__ __forceinline__ void load_group(const SumParams& p, const T* X, int64_t gr, int64_t gc,
+                                           int64_t l0, float (&v)[EPT]) {
+  const bool row_ok = gr < p.rows;
+  if (row_ok && p.vec_ok && gc + EPT <= p.cols && l0 + EPT <= p.hc) {
+    const T* src = X + gr * p.ldx + gc;
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+      for (int e = 0; e < EPT; e += 4) {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(src + e));
+        v[e] = q.x; v[e + 1] = q.y; v[e + 2] = q.z; v[e + 3] = q.w;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < EPT; e += 4) {
+        const uint2 q = __ldg(reinterpret_cast<const uint2*>(src + e));
+        T t[4];
+        memcpy(t, &q, sizeof q);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[e + u] = load_as_float<T>(&t[u]);
       }
     }
-    for (int r = 0; r < p.nprod; ++r) {
-      float acc[4] = {0.f, 0.f, 0.f, 0.f};
-      const int cnt = p.cnt[r];
-      for (int t = 0; t < cnt; ++t) {
-        const SrcTerm st = p.term[r][t];
+  } else {
 #pragma unroll
-        for (int s = 0; s < NSRC; ++s) {
-          if (s == st.src) {
+    for (int e = 0; e < EPT; ++e)
+      v[e] = (row_ok && gc + e < p.cols && l0 + e < p.hc) ? load_as_float<T>(X + gr * p.ldx + gc + e) : 0.f;
+  }
+}
+
+template <typename T, int OUT16, int L, bool IS_B, int TERMS, int EPT>
+__global__ void __launch_bounds__(256) operand_sums_kernel(const __grid_constant__ SumParams p) {
+  constexpr int G = 1 << L;
+  const T* X = static_cast<const T*>(p.X);
+  const int64_t groups = (p.hc + EPT - 1) / EPT;
+  const int64_t total = p.hr * groups;
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = idx / groups;
+    const int64_t l0 = (idx - i * groups) * EPT;
+    const int64_t orow = i * p.ld_out + l0;
+    if (L == 0) {
+      float v[EPT];
+      load_group<T, EPT>(p, X, i, l0, l0, v);
+      store_sum<TERMS, OUT16, EPT>(p, orow, v);
+    } else if (L == 1) {
+      float v[4][EPT];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) acc[e] = st.sign > 0 ? acc[e] + v[s][e] : acc[e] - v[s][e];
+      for (int q = 0; q < 4; ++q)
+        load_group<T, EPT>(p, X, (q / 2) * p.hr + i, (q % 2) * p.hc + l0, l0, v[q]);
+#pragma unroll
+      for (int r = 0; r < 7; ++r) {
+        float acc[EPT];
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) acc[e] = 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int c = coef<IS_B>(r, q);
+#pragma unroll
+          for (int e = 0; e < EPT; ++e) {
+            if (c > 0) acc[e] += v[q][e];
+            if (c < 0) acc[e] -= v[q][e];
           }
         }
+        store_sum<TERMS, OUT16, EPT>(p, r * p.prod_stride + orow, acc);
       }
-      const int64_t o = r * p.prod_stride + i * p.ld_out + l0;
-      ushort4 hi, lo;
-      if (p.terms == 3) {
-        uint16_t h[4], w[4];
+    } else {
+      // source (q1, q2) is block (2*(q1/2) + q2/2, 2*(q1%2) + q2%2) of the 4 x 4 grid
+      float v[16][EPT];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const __nv_bfloat16 hb = __float2bfloat16_rn(acc[e]);
-          h[e] = __bfloat16_as_ushort(hb);
-          w[e] = __bfloat16_as_ushort(__float2bfloat16_rn(acc[e] - __bfloat162float(hb)));
+      for (int q1 = 0; q1 < 4; ++q1)
+#pragma unroll
+        for (int q2 = 0; q2 < 4; ++q2) {
+          const int bi = 2 * (q1 / 2) + q2 / 2, bj = 2 * (q1 % 2) + q2 % 2;
+          load_group<T, EPT>(p, X, bi * p.hr + i, bj * p.hc + l0, l0, v[q1 * 4 + q2]);
         }
-        hi = make_ushort4(h[0], h[1], h[2], h[3]);
-        lo = make_ushort4(w[0], w[1], w[2], w[3]);
-        *reinterpret_cast<ushort4*>(p.out_lo + o) = lo;
-      } else {
-        hi = make_ushort4(round16<OUT16>(acc[0]), round16<OUT16>(acc[1]), round16<OUT16>(acc[2]),
-                          round16<OUT16>(acc[3]));
+#pragma unroll
+      for (int r1 = 0; r1 < 7; ++r1) {
+        float S[4][EPT];
+#pragma unroll
+        for (int q2 = 0; q2 < 4; ++q2) {
+#pragma unroll
+          for (int e = 0; e < EPT; ++e) S[q2][e] = 0.f;
+#pragma unroll
+          for (int q1 = 0; q1 < 4; ++q1) {
+            const int c = coef<IS_B>(r1, q1);
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) S[q2][e] = c > 0 ? S[q2][e] + v[q1 * 4 + q2][e]
+                                                   : (c < 0 ? S[q2][e] - v[q1 * 4 + q2][e] : S[q2][e]);
+          }
+        }
+#pragma unroll
+        for (int r2 = 0; r2 < 7; ++r2) {
+          float acc[EPT];
+#pragma unroll
+          for (int e = 0; e < EPT; ++e) acc[e] = 0.f;
+#pragma unroll
+          for (int q2 = 0; q2 < 4; ++q2) {
+            const int c = coef<IS_B>(r2, q2);
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) {
+              if (c > 0) acc[e] += S[q2][e];
+              if (c < 0) acc[e] -= S[q2][e];
+            }
+          }
+          store_sum<TERMS, OUT16, EPT>(p, (r1 * 7 + r2) * p.prod_stride + orow, acc);
+        }
       }
-      *reinterpret_cast<ushort4*>(p.out_hi + o) = hi;
     }
   }
 }
@@ -175,17 +279,8 @@ __global__ void debug_wait_kernel(unsigned* err, uint64_t timeout_ns) {
 template <typename T, int OUT16>
 static cudaError_t launch_pack_t(const PackParams& p, bool transpose, int num_sms, cudaStream_t s) {
   const int nsrc = p.nsrc;
-  if (!transpose) {
-    const int64_t total = static_cast<int64_t>(p.hr) * ((p.hc + 3) / 4);
-    if (total == 0) return cudaSuccess;
-    const int grid = static_cast<int>(std::min<int64_t>((total + 255) / 256, int64_t(num_sms) * 8));
-    switch (nsrc) {
-      case 1: pack_rows_kernel<T, OUT16, 1><<<grid, 256, 0, s>>>(p); break;
-      case 4: pack_rows_kernel<T, OUT16, 4><<<grid, 256, 0, s>>>(p); break;
-      case 16: pack_rows_kernel<T, OUT16, 16><<<grid, 256, 0, s>>>(p); break;
-      default: return cudaErrorInvalidValue;
-    }
-  } else {
+  if (!transpose) return cudaErrorInvalidValue;
+  {
     const int64_t ntiles = static_cast<int64_t>((p.hr + 31) / 32) * ((p.hc + 31) / 32);
     if (ntiles == 0) return cudaSuccess;
     const int grid = static_cast<int>(std::min<int64_t>(ntiles, int64_t(num_sms) * 4));
@@ -207,6 +302,45 @@ static cudaError_t launch_pack_t(const PackParams& p, bool transpose, int num_sm
   return cudaGetLastError();
 }
 
+template <typename T, int OUT16, int L, bool IS_B, int TERMS>
+static cudaError_t launch_sums_t(const SumParams& p, int num_sms, cudaStream_t s) {
+  constexpr int EPT = L == 2 ? 4 : 8;
+  const int64_t total = p.hr * ((p.hc + EPT - 1) / EPT);
+  if (total == 0) return cudaSuccess;
+  const int grid = static_cast<int>(std::min<int64_t>((total + 255) / 256, int64_t(num_sms) * 16));
+  operand_sums_kernel<T, OUT16, L, IS_B, TERMS, EPT><<<grid, 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename T, int OUT16, bool IS_B, int TERMS>
+static cudaError_t launch_sums_l(const SumParams& p, int levels, int num_sms, cudaStream_t s) {
+  switch (levels) {
+    case 0: return launch_sums_t<T, OUT16, 0, IS_B, TERMS>(p, num_sms, s);
+    case 1: return launch_sums_t<T, OUT16, 1, IS_B, TERMS>(p, num_sms, s);
+    case 2: return launch_sums_t<T, OUT16, 2, IS_B, TERMS>(p, num_sms, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <bool IS_B>
+static cudaError_t launch_sums_b(const SumParams& p, int levels, int in_type, int out16, int num_sms,
+                                 cudaStream_t s) {
+  if (in_type == kInF32) {
+    if (p.terms == 3) return launch_sums_l<float, 0, IS_B, 3>(p, levels, num_sms, s);
+    return out16 ? launch_sums_l<float, 1, IS_B, 1>(p, levels, num_sms, s)
+                 : launch_sums_l<float, 0, IS_B, 1>(p, levels, num_sms, s);
+  }
+  if (in_type == kInBF16) return launch_sums_l<__nv_bfloat16, 0, IS_B, 1>(p, levels, num_sms, s);
+  if (in_type == kInF16) return launch_sums_l<__half, 1, IS_B, 1>(p, levels, num_sms, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_operand_sums(const SumParams& p, int levels, bool is_b, int in_type, int out16,
+                                int num_sms, cudaStream_t s) {
+  return is_b ? launch_sums_b<true>(p, levels, in_type, out16, num_sms, s)
+              : launch_sums_b<false>(p, levels, in_type, out16, num_sms, s);
+}
+
 cudaError_t launch_pack(const PackParams& p, int in_type, int out16, bool transpose, int num_sms,
                         cudaStream_t s) {
   if (in_type == kInF32) {
@@ -222,6 +356,7 @@ cudaError_t launch_beta(float* C, int64_t m, int64_t n, int64_t ldc, float beta,
                         cudaStream_t s) {
   const int64_t total = m * n;
   if (total == 0) return cudaSuccess;
+  if (beta == 0.f && ldc == n) return cudaMemsetAsync(C, 0, static_cast<size_t>(total) * sizeof(float), s);
   const int grid = static_cast<int>(std::min<int64_t>((total + 255) / 256, int64_t(num_sms) * 16));
   beta_kernel<<<grid, 256, 0, s>>>(C, m, n, ldc, beta);
   return cudaGetLastError();

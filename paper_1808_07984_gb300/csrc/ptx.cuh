@@ -140,11 +140,13 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, float (&v)[32
 }
 
 // ------------------------------------------------------------- descriptors
-// Instruction descriptor, kind::f16: D = F32, A and B both BF16 (or both F16), both K-major.
-__host__ __device__ constexpr uint32_t make_idesc_f16(int M, int N, bool bf16) {
+// Instruction descriptor, kind::f16: D = F32, A and B both BF16 (or both F16), A K-major,
+// B K-major or (b_mn) MN-major.
+__host__ __device__ constexpr uint32_t make_idesc_f16(int M, int N, bool bf16, bool b_mn = false) {
   return (1u << 4)                               // D format: F32
          | ((bf16 ? 1u : 0u) << 7)               // A format: BF16 (1) / F16 (0)
          | ((bf16 ? 1u : 0u) << 10)              // B format
+         | ((b_mn ? 1u : 0u) << 16)              // B major-ness: MN
          | (static_cast<uint32_t>(N >> 3) << 17)  // N / 8
          | (static_cast<uint32_t>(M >> 4) << 24); // M / 16
 }
@@ -161,6 +163,20 @@ __device__ __forceinline__ uint64_t make_sdesc_kmajor_sw128(uint32_t addr) {
   d |= static_cast<uint64_t>(1024 >> 4) << 32;          // stride byte offset: 8 rows * 128 B
   d |= static_cast<uint64_t>(1) << 46;                  // descriptor version for tcgen05
   d |= static_cast<uint64_t>(2) << 61;                  // swizzle mode: 128B
+  return d;
+}
+
+// Shared-memory matrix descriptor for an MN-major operand tile in the 128-byte swizzled
+// canonical layout: 8 k-rows of 128 bytes (64 MN-elements) form a 1024-byte atom; atoms are
+// `sbo` bytes apart along K and `lbo` bytes apart along MN.  This is the layout a TMA load
+// with CU_TENSOR_MAP_SWIZZLE_128B writes for a box of 64 (MN, inner) x k rows.
+__device__ __forceinline__ uint64_t make_sdesc_mnmajor_sw128(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((addr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16;  // leading byte offset: MN atom stride
+  d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32;  // stride byte offset: K atom stride
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(2) << 61;
   return d;
 }
 
