@@ -119,6 +119,23 @@ fmm_status fmm_gemm_ex(int64_t m, int64_t n, int64_t k, float alpha,
                        void* workspace, size_t ws_bytes, void* stream,
                        const fmm_options* opt);
 
+/* fmm_gemm without a workspace argument, for callers that cannot allocate device
+ * memory (for example a plug-in whose host application owns every device allocation,
+ * or a latency-critical caller that must not call cudaMalloc / cudaFree because they
+ * can synchronise the device).  The operand sums go to a scratch array built into
+ * the library: 64 MiB per GPU, held from library load until process exit.  Problems
+ * whose fmm_workspace_size() exceeds 64 MiB are rejected with FMM_ERR_WORKSPACE;
+ * no device memory is allocated.  All calls on a device share that one scratch and
+ * it keeps the previous call's contents (nothing in it needs to start at zero):
+ * calls whose work overlaps on the GPU race on it and must be serialised by the
+ * caller.  The first call on each device looks up the scratch's device address;
+ * make that first call before any stream capture begins.  Other arguments and
+ * errors as fmm_gemm.  The paper has no counterpart to this entry point. */
+fmm_status fmm_gemm_noalloc(int64_t m, int64_t n, int64_t k, float alpha,
+                            const void* A, int64_t lda, const void* B, int64_t ldb,
+                            float beta, float* C, int64_t ldc, int levels, int variant,
+                            void* stream);
+
 /* Last error message of the calling host thread ("" when none). */
 const char* fmm_last_error(void);
 

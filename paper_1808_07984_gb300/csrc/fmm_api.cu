@@ -416,6 +416,9 @@ fmm_status gemm_impl(int64_t m, int64_t n, int64_t k, float alpha, const void* A
 }
 
 }  // namespace
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
 }  // namespace fmm
 
 using namespace fmm;

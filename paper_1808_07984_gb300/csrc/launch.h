@@ -1,11 +1,15 @@
 // launch.h -- host-side launchers shared by the C-ABI translation unit.
 #pragma once
 #include <cuda_runtime.h>
+#include <string>
 #include "fmm_kernels.cuh"
 
 namespace fmm {
 
 enum InType { kInF32 = 0, kInBF16 = 1, kInF16 = 2 };
+
+// Sets the calling thread's message returned by fmm_last_error().
+void set_last_error(const std::string& msg);
 
 cudaError_t launch_pack(const PackParams& p, int in_type, int out16, bool transpose, int num_sms,
                         cudaStream_t s);
