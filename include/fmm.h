@@ -94,7 +94,11 @@ typedef struct fmm_options {
     int num_ctas;   /* 0 = one persistent CTA per SM */
     int b_kmajor;   /* packed algorithm: 1 stores the B-operand sums transposed (K-major);
                        0 (default) keeps them row-major and the tensor cores read B MN-major */
-    int reserved[4];
+    int schedule;   /* order of the (product, tile) work items: 0 = automatic,
+                       1 = product-major (all tiles of one product, then the next),
+                       2 = tile rounds (each CTA runs all 7^L products of one output tile
+                           back to back, so its destination blocks stay in L2) */
+    int reserved[3];
 } fmm_options;
 
 /* Bytes of workspace fmm_gemm needs for this problem (0 when none).  Returns

@@ -174,6 +174,7 @@ struct Plan {
   int L = 0, R = 1, terms = 3, in_type = kInF32;
   bool bf16 = true;
   bool b_mn = true;  // B-operand sums row-major (k x n), read MN-major by the tensor cores
+  int schedule = kSchedProductMajor;
   int tile_n = 128;
   int algo = FMM_ALGO_PACKED;
   int64_t hm = 0, hn = 0, hk = 0;
@@ -199,13 +200,27 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
   if (algo != FMM_ALGO_AUTO && algo != FMM_ALGO_PACKED)
     return fail(FMM_ERR_UNSUPPORTED, "algorithm not built");
   pl.algo = FMM_ALGO_PACKED;
-  pl.tile_n = (opt && opt->tile_n) ? opt->tile_n : 128;
-  if (!packed_config_supported(pl.tile_n, pl.terms, pl.bf16))
-    return fail(FMM_ERR_UNSUPPORTED, "tile_n must be 128 or 256");
+  pl.tile_n = (opt && opt->tile_n) ? opt->tile_n : 0;
   pl.b_mn = !(opt && opt->b_kmajor);
+  const int sched = opt ? opt->schedule : 0;
+  if (sched < 0 || sched > 2) return fail(FMM_ERR_ARG, "schedule must be 0, 1 or 2");
+  // automatic choice (measured on GB300): tile rounds keep each tile's destination blocks in
+  // L2 and are never slower by more than 1 %, product-major order only for long products
   pl.hm = block_size(m, levels);
   pl.hn = block_size(n, levels);
   pl.hk = block_size(k, levels);
+  if (sched == 0)
+    pl.schedule = (levels == 2 && pl.hk >= 4096) ? kSchedProductMajor : kSchedTileRounds;
+  else
+    pl.schedule = sched == 2 ? kSchedTileRounds : kSchedProductMajor;
+  if (pl.tile_n == 0) {
+    // 256-wide tiles halve the A-operand traffic; keep 128 when that leaves fewer than four
+    // work items per SM on a 152-SM GB300
+    const int64_t items256 = static_cast<int64_t>(pl.R) * ((pl.hm + kBM - 1) / kBM) * ((pl.hn + 255) / 256);
+    pl.tile_n = items256 >= 4 * 152 ? 256 : 128;
+  }
+  if (!packed_config_supported(pl.tile_n, pl.terms, pl.bf16))
+    return fail(FMM_ERR_UNSUPPORTED, "tile_n must be 128 or 256");
   pl.lda_w = round_up(std::max<int64_t>(pl.hk, 1), 8);
   pl.ldb_w = pl.b_mn ? round_up(std::max<int64_t>(pl.hn, 1), 8) : pl.lda_w;
   if (pl.hm >= (int64_t(1) << 31) || pl.hn >= (int64_t(1) << 31) || pl.hk >= (int64_t(1) << 31))
@@ -375,6 +390,9 @@ fmm_status gemm_impl(int64_t m, int64_t n, int64_t k, float alpha, const void* A
   }
   pp->C = C;
   pp->ldc = ldc;
+  pp->alpha = alpha;
+  pp->schedule = pl.schedule;
+  pp->c_tma = (reinterpret_cast<uintptr_t>(C) % 16 == 0 && ldc % 4 == 0) ? 1 : 0;
   pp->err = dev.err;
   pp->timeout_ns = g_timeout_ns.load();
   pp->tiles_m = static_cast<int32_t>((pl.hm + kBM - 1) / kBM);
@@ -400,8 +418,31 @@ fmm_status gemm_impl(int64_t m, int64_t n, int64_t k, float alpha, const void* A
       de.rows = static_cast<int32_t>(rows);
       de.cols = static_cast<int32_t>(cols);
       de.coef = alpha * static_cast<float>(t.sign);
+      de.block = t.block;
     }
     pp->prod[r].count = cnt;
+  }
+  if (pp->c_tma) {
+    // one FP32 map per non-empty destination block, clipped to the block's extent in C
+    for (int b = 0; b < g * g && st == FMM_OK; ++b) {
+      const int br = b / g, bc = b % g;
+      const int64_t rows = std::min<int64_t>(std::max<int64_t>(m - br * pl.hm, 0), pl.hm);
+      const int64_t cols = std::min<int64_t>(std::max<int64_t>(n - bc * pl.hn, 0), pl.hn);
+      if (rows == 0 || cols == 0) continue;
+      const cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+      const cuuint64_t strides[1] = {static_cast<cuuint64_t>(ldc * 4)};
+      const cuuint32_t box[2] = {32, 32};
+      const cuuint32_t estr[2] = {1, 1};
+      CUresult cr = g_encode(&pp->tmC[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                             C + (br * pl.hm * ldc + bc * pl.hn), dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (cr != CUDA_SUCCESS) st = fail(FMM_ERR_CUDA, "cuTensorMapEncodeTiled (C) failed (" + std::to_string(cr) + ")");
+    }
+    if (st != FMM_OK) {
+      delete pp;
+      return st;
+    }
   }
   int grid = opt && opt->num_ctas > 0 ? opt->num_ctas : dev.sms;
   grid = static_cast<int>(std::min<int64_t>(grid, items));

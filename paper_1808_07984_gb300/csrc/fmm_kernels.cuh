@@ -63,7 +63,7 @@ struct DestEntry {
   int32_t rows;    // rows of that block that exist in C (<= h_m)
   int32_t cols;    // columns of that block that exist in C (<= h_n)
   float coef;      // alpha * W[c, r]
-  int32_t pad;
+  int32_t block;   // destination block index bi * 2^L + bj (selects its tensor map)
 };
 
 struct ProductDests {
@@ -73,16 +73,25 @@ struct ProductDests {
 };
 
 // Kernel parameters of the packed-operand path (operand sums already formed).
-struct alignas(64) PackedParams {
-  CUtensorMap tmA[2];  // A-operand sums, hi / lo: 3-D {k, row, product}, 16-bit
-  CUtensorMap tmB[2];  // B-operand sums transposed, hi / lo: 3-D {k, col, product}
+enum Schedule : int32_t {
+  kSchedProductMajor = 0,  // all tiles of product 0, then product 1, ... (operand reuse)
+  kSchedTileRounds = 1,    // each CTA runs every product of one tile in turn (C stays in L2)
+};
+
+struct PackedParams {
+  CUtensorMap tmA[2];   // A-operand sums, hi / lo: 3-D {k, row, product}, 16-bit
+  CUtensorMap tmB[2];   // B-operand sums, hi / lo: 3-D {n, k, product} (or {k, n, product})
+  CUtensorMap tmC[kMaxSources];  // one f32 map per destination block, clipped to its extent
   float* C;
   int64_t ldc;
   unsigned int* err;
   uint64_t timeout_ns;
+  float alpha;
   int32_t tiles_m, tiles_n, nk, num_items;
   int32_t num_products;
-  int32_t c_vec4;  // C rows are 16-byte aligned: vector reductions allowed
+  int32_t schedule;  // Schedule
+  int32_t c_tma;     // write-back by TMA reductions through tmC (C rows 16-byte aligned)
+  int32_t c_vec4;    // element-wise path: C rows are 16-byte aligned, vector reductions allowed
   ProductDests prod[kMaxProducts];
 };
 
@@ -124,13 +133,9 @@ struct SumParams {
   int32_t vec_ok;      // X base and ldx allow vector loads
 };
 
-__device__ __forceinline__ void decode_item(int item, int tiles_m, int tiles_n, int& r, int& tm,
-                                            int& tn) {
-  const int per_prod = tiles_m * tiles_n;
-  r = item / per_prod;
-  const int t = item - r * per_prod;
-  // grouped raster: 8 tile-rows at a time, column-major inside the group, so that
-  // concurrently running CTAs share operand panels in L2.
+// Grouped raster of the tile grid: 8 tile-rows at a time, column-major inside the group, so
+// that concurrently running CTAs share operand panels in L2.
+__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int& tm, int& tn) {
   constexpr int G = 8;
   const int group_size = G * tiles_n;
   const int g = t / group_size;
@@ -141,12 +146,44 @@ __device__ __forceinline__ void decode_item(int item, int tiles_m, int tiles_n, 
   tn = in_g / gm;
 }
 
+// Work item -> (product r, tile row tm, tile column tn).  CTA b runs items b, b + G, ...
+// (G = gridDim.x).  kSchedProductMajor: item = r * tiles + t.  kSchedTileRounds: tiles are
+// taken G at a time; within a round the item index is r * G + (t - round start), so CTA b
+// runs products 0..R-1 of one tile back to back; the last, partial round is spread over all
+// CTAs product by product.
+__device__ __forceinline__ void decode_item(int item, const PackedParams& p, int& r, int& tm, int& tn) {
+  const int tiles = p.tiles_m * p.tiles_n;
+  int t;
+  if (p.schedule == kSchedTileRounds) {
+    const int G = gridDim.x, R = p.num_products;
+    const int full = tiles / G;
+    const int items_full = full * G * R;
+    if (item < items_full) {
+      const int j = item / (G * R);
+      const int w = item - j * G * R;
+      r = w / G;
+      t = j * G + (w - r * G);
+    } else {
+      const int i2 = item - items_full;
+      const int rem = tiles - full * G;
+      r = i2 / rem;
+      t = full * G + (i2 - r * rem);
+    }
+  } else {
+    r = item / tiles;
+    t = item - r * tiles;
+  }
+  tile_coords(t, p.tiles_m, p.tiles_n, tm, tn);
+}
+
 template <int BN, int TERMS, int STAGES>
 struct PackedCfg {
   static constexpr uint32_t kABytes = kBM * kBK * 2;
   static constexpr uint32_t kBBytes = BN * kBK * 2;
   static constexpr uint32_t kStageBytes = (TERMS == 3 ? 2u : 1u) * (kABytes + kBBytes);
-  static constexpr uint32_t kBarOffset = STAGES * kStageBytes;
+  static constexpr uint32_t kEpiOffset = STAGES * kStageBytes;  // 4 warps x 2 x 4 KB staging
+  static constexpr uint32_t kEpiBytes = 4 * 2 * 4096;
+  static constexpr uint32_t kBarOffset = kEpiOffset + kEpiBytes;
   static constexpr uint32_t kSmemBytes = kBarOffset + 256 + 1024;  // + barriers + alignment slack
   static constexpr uint32_t kTmemCols = 2 * BN;
 };
@@ -208,7 +245,7 @@ __global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_co
       bool ok = true;
       for (int item = blockIdx.x; ok && item < p.num_items; item += gridDim.x) {
         int r, tm, tn;
-        decode_item(item, p.tiles_m, p.tiles_n, r, tm, tn);
+        decode_item(item, p, r, tm, tn);
         for (int kb = 0; kb < p.nk; ++kb) {
           if (!mbar_wait(smem_u32(&empty[stage]), phase ^ 1u, p.timeout_ns, abort_flag)) {
             atomicOr(p.err, kErrProducerWait);
@@ -312,9 +349,13 @@ __global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_co
     }
   } else if (warp >= 4) {
     // ------------------------------------------------------------ epilogue
+    // Each warp owns TMEM lanes 32q..32q+31 (rows of the tile) and, for the TMA write-back,
+    // two 4 KB staging buffers: a 32 x 32 FP32 block is written there in the 128-byte
+    // swizzled layout and added into every destination block by TMA reductions.
     const int q = warp & 3;  // TMEM lane quarter this warp may access
-    const int row_local = q * 32 + lane;
     const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
+    uint8_t* stage_base = smem + Cfg::kEpiOffset + q * 8192;
+    int buf = 0;
     int it = 0;
     for (int item = blockIdx.x; item < p.num_items; item += gridDim.x, ++it) {
       const int acc = it & 1;
@@ -326,37 +367,72 @@ __global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_co
       }
       tc_fence_after();
       int r, tm, tn;
-      decode_item(item, p.tiles_m, p.tiles_n, r, tm, tn);
+      decode_item(item, p, r, tm, tn);
       const ProductDests& pd = p.prod[r];
-      const int row = tm * kBM + row_local;
+      const int row0 = tm * kBM + q * 32;
+      const int row = row0 + lane;
+      bool has_sign[2] = {false, false};
+      for (int d = 0; d < pd.count; ++d) has_sign[pd.d[d].coef < 0.f ? 1 : 0] = true;
 #pragma unroll 1
       for (int c = 0; c < BN; c += 32) {
         float v[32];
         tmem_ld_32x32b_x32(tmem_base + lane_off + static_cast<uint32_t>(acc * BN + c), v);
+        if (c + 32 == BN) {
+          // every TMEM read of this accumulator is complete: hand it back to the MMA warp
+          tc_fence_before();
+          mbar_arrive(smem_u32(&acc_empty[acc]));
+        }
         const int col0 = tn * BN + c;
+        if (p.c_tma) {
 #pragma unroll 1
-        for (int d = 0; d < pd.count; ++d) {
-          const DestEntry de = pd.d[d];
-          if (row >= de.rows || col0 >= de.cols) continue;
-          float* dst = p.C + de.offset + static_cast<int64_t>(row) * p.ldc + col0;
-          const float cf = de.coef;
-          if (p.c_vec4 && col0 + 32 <= de.cols) {
-            float4* d4 = reinterpret_cast<float4*>(dst);
+          for (int sg = 0; sg < 2; ++sg) {
+            if (!has_sign[sg]) continue;
+            const float cf = sg ? -p.alpha : p.alpha;
+            uint8_t* sb = stage_base + buf * 4096;
+            if (lane == 0) bulk_wait_group_read<1>();  // this buffer's previous reductions read it
+            __syncwarp();
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-              atomicAdd(d4 + j, make_float4(cf * v[4 * j], cf * v[4 * j + 1], cf * v[4 * j + 2],
-                                            cf * v[4 * j + 3]));
-          } else {
-            const int lim = de.cols - col0;
+            for (int j = 0; j < 8; ++j) {
+              const float4 val = make_float4(cf * v[4 * j], cf * v[4 * j + 1], cf * v[4 * j + 2],
+                                             cf * v[4 * j + 3]);
+              *reinterpret_cast<float4*>(sb + lane * 128 + ((j ^ (lane & 7)) << 4)) = val;
+            }
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+              for (int d = 0; d < pd.count; ++d) {
+                const DestEntry& de = pd.d[d];
+                if ((de.coef < 0.f ? 1 : 0) != sg) continue;
+                tma_reduce_add_2d(&p.tmC[de.block], smem_u32(sb), col0, row0);
+              }
+              bulk_commit_group();
+            }
+            buf ^= 1;
+          }
+        } else {
+#pragma unroll 1
+          for (int d = 0; d < pd.count; ++d) {
+            const DestEntry de = pd.d[d];
+            if (row >= de.rows || col0 >= de.cols) continue;
+            float* dst = p.C + de.offset + static_cast<int64_t>(row) * p.ldc + col0;
+            const float cf = de.coef;
+            if (p.c_vec4 && col0 + 32 <= de.cols) {
+              float4* d4 = reinterpret_cast<float4*>(dst);
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (j < lim) atomicAdd(dst + j, cf * v[j]);
+              for (int j = 0; j < 8; ++j)
+                atomicAdd(d4 + j, make_float4(cf * v[4 * j], cf * v[4 * j + 1], cf * v[4 * j + 2],
+                                              cf * v[4 * j + 3]));
+            } else {
+              const int lim = de.cols - col0;
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                if (j < lim) atomicAdd(dst + j, cf * v[j]);
+            }
           }
         }
       }
-      tc_fence_before();
-      mbar_arrive(smem_u32(&acc_empty[acc]));
     }
+    if (lane == 0) bulk_wait_group<0>();  // reductions complete before the CTA retires
   }
 
   tc_fence_before();

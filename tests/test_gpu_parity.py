@@ -57,7 +57,7 @@ def _to_device(X, ld_pad, dtype):
 
 
 def run(m, n, k, levels, variant="split3", dist="uniform", seed=0, alpha=1.0, beta=0.0,
-        tile_n=0, pads=(0, 0, 0), c_fill=None, rows=None, b_kmajor=0):
+        tile_n=0, pads=(0, 0, 0), c_fill=None, rows=None, b_kmajor=0, schedule="auto"):
     A, B = synth.problem(m, n, k, seed, dist)
     in_dtype = torch.bfloat16 if variant == "bf16" else torch.float32
     Ad = _to_device(A, pads[0], in_dtype)
@@ -71,7 +71,7 @@ def run(m, n, k, levels, variant="split3", dist="uniform", seed=0, alpha=1.0, be
         if c_fill is not None:
             Cd.fill_(c_fill)
     fmm.gemm(Ad, Bd, Cd, alpha=alpha, beta=beta, levels=levels, variant=variant, tile_n=tile_n,
-             b_kmajor=b_kmajor)
+             b_kmajor=b_kmajor, schedule=schedule)
     fmm.device_status()
     C = Cd.cpu().numpy().astype(np.float64)
     if variant == "bf16":
@@ -107,6 +107,22 @@ def test_int16_cube_bit_exact(variant, levels):
 def test_int_ragged_bit_exact(m, n, k, levels, tile_n, b_kmajor):
     C, C64, _, _ = run(m, n, k, levels, "split3", dist="int", seed=m + n + k, tile_n=tile_n,
                        b_kmajor=b_kmajor)
+    np.testing.assert_array_equal(C, C64)
+
+
+@pytest.mark.parametrize("schedule", ["product", "rounds"])
+@pytest.mark.parametrize("levels", [0, 1, 2])
+@pytest.mark.parametrize("m,n,k", [(1000, 1200, 300), (136, 1800, 64)])
+def test_int_schedules_bit_exact(m, n, k, levels, schedule):
+    """Both work orders, with enough tiles for several rounds and a partial last round."""
+    C, C64, _, _ = run(m, n, k, levels, "split3", dist="int", seed=m + k, schedule=schedule)
+    np.testing.assert_array_equal(C, C64)
+
+
+@pytest.mark.parametrize("levels", [0, 1, 2])
+def test_unaligned_ldc_uses_elementwise_writeback(levels):
+    """ldc odd: rows of C are not 16-byte aligned, so the element-wise reduction path runs."""
+    C, C64, _, _ = run(257, 300, 130, levels, "split3", dist="int", seed=9, pads=(0, 0, 1))
     np.testing.assert_array_equal(C, C64)
 
 
