@@ -14,6 +14,7 @@
 #include "fmm.h"
 #include "fmm_kernels.cuh"
 #include "launch.h"
+#include "fmm_fused.cuh"
 
 namespace fmm {
 
@@ -197,10 +198,17 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
     default: return fail(FMM_ERR_UNSUPPORTED, "variant not built");
   }
   const int algo = opt ? opt->algo : 0;
-  if (algo != FMM_ALGO_AUTO && algo != FMM_ALGO_PACKED)
+  if (algo != FMM_ALGO_AUTO && algo != FMM_ALGO_PACKED && algo != FMM_ALGO_FUSED)
     return fail(FMM_ERR_UNSUPPORTED, "algorithm not built");
-  pl.algo = FMM_ALGO_PACKED;
+  pl.algo = algo == FMM_ALGO_FUSED ? FMM_ALGO_FUSED : FMM_ALGO_PACKED;
+  if (pl.algo == FMM_ALGO_FUSED && pl.in_type != kInF32)
+    return fail(FMM_ERR_UNSUPPORTED, "the fused algorithm takes FP32 A and B (split3 or plain_bf16)");
   pl.tile_n = (opt && opt->tile_n) ? opt->tile_n : 0;
+  if (pl.algo == FMM_ALGO_FUSED) {
+    if (pl.tile_n != 0 && pl.tile_n != kFusedTileN)
+      return fail(FMM_ERR_UNSUPPORTED, "the fused algorithm uses 128-wide tiles");
+    pl.tile_n = kFusedTileN;
+  }
   pl.b_mn = !(opt && opt->b_kmajor);
   const int sched = opt ? opt->schedule : 0;
   if (sched < 0 || sched > 2) return fail(FMM_ERR_ARG, "schedule must be 0, 1 or 2");
@@ -229,7 +237,7 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
   pl.b_bytes = static_cast<size_t>(
       round_up(static_cast<int64_t>(pl.R) * (pl.b_mn ? pl.hk : pl.hn) * pl.ldb_w * 2, 256));
   const size_t arrays = pl.terms == 3 ? 2 : 1;
-  pl.ws = (m == 0 || n == 0 || k == 0) ? 0 : arrays * (pl.a_bytes + pl.b_bytes);
+  pl.ws = (m == 0 || n == 0 || k == 0 || pl.algo == FMM_ALGO_FUSED) ? 0 : arrays * (pl.a_bytes + pl.b_bytes);
   return FMM_OK;
 }
 
@@ -255,6 +263,147 @@ fmm_status encode_3d(CUtensorMap* map, void* base, int64_t inner, int64_t rows, 
 }
 
 size_t elem_bytes(int in_type) { return in_type == kInF32 ? 4 : 2; }
+
+int64_t block_extent(int64_t d, int64_t h, int b) {
+  return std::min<int64_t>(std::max<int64_t>(d - b * h, 0), h);
+}
+
+// Work list, destination maps and C tensor maps shared by both tensor-core kernels.
+// `live` lists the products that run (their kernel-side index is their position in it).
+fmm_status fill_common(CommonParams& c, const Plan& pl, const std::vector<Product>& prods,
+                       const std::vector<int>& live, int64_t m, int64_t n, float alpha, float* C,
+                       int64_t ldc, const DeviceInfo& dev, const fmm_options* opt, int& grid) {
+  const int g = 1 << pl.L;
+  c.C = C;
+  c.ldc = ldc;
+  c.alpha = alpha;
+  c.schedule = pl.schedule;
+  c.c_tma = (reinterpret_cast<uintptr_t>(C) % 16 == 0 && ldc % 4 == 0) ? 1 : 0;
+  c.c_vec4 = c.c_tma;
+  c.err = dev.err;
+  c.timeout_ns = g_timeout_ns.load();
+  c.tiles_m = static_cast<int32_t>((pl.hm + kBM - 1) / kBM);
+  c.tiles_n = static_cast<int32_t>((pl.hn + pl.tile_n - 1) / pl.tile_n);
+  c.nk = static_cast<int32_t>((pl.hk + kBK - 1) / kBK);
+  const int64_t items = static_cast<int64_t>(live.size()) * c.tiles_m * c.tiles_n;
+  if (items >= (int64_t(1) << 31)) return fail(FMM_ERR_ARG, "too many tiles");
+  c.num_items = static_cast<int32_t>(items);
+  c.num_products = static_cast<int32_t>(live.size());
+  for (size_t i = 0; i < live.size(); ++i) {
+    int cnt = 0;
+    for (const Term& t : prods[live[i]].c) {
+      const int br = t.block / g, bc = t.block % g;
+      const int64_t rows = block_extent(m, pl.hm, br), cols = block_extent(n, pl.hn, bc);
+      if (rows == 0 || cols == 0) continue;
+      DestEntry& de = c.prod[i].d[cnt++];
+      de.offset = br * pl.hm * ldc + bc * pl.hn;
+      de.rows = static_cast<int32_t>(rows);
+      de.cols = static_cast<int32_t>(cols);
+      de.coef = alpha * static_cast<float>(t.sign);
+      de.block = t.block;
+    }
+    c.prod[i].count = cnt;
+  }
+  if (c.c_tma) {
+    // one FP32 map per non-empty destination block, clipped to the block's extent in C
+    for (int b = 0; b < g * g; ++b) {
+      const int64_t rows = block_extent(m, pl.hm, b / g), cols = block_extent(n, pl.hn, b % g);
+      if (rows == 0 || cols == 0) continue;
+      const cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+      const cuuint64_t strides[1] = {static_cast<cuuint64_t>(ldc * 4)};
+      const cuuint32_t box[2] = {32, 32};
+      const cuuint32_t estr[2] = {1, 1};
+      CUresult cr = g_encode(&c.tmC[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                             C + ((b / g) * pl.hm * ldc + (b % g) * pl.hn), dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (cr != CUDA_SUCCESS)
+        return fail(FMM_ERR_CUDA, "cuTensorMapEncodeTiled (C) failed (" + std::to_string(cr) + ")");
+    }
+  }
+  grid = opt && opt->num_ctas > 0 ? opt->num_ctas : dev.sms;
+  grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(grid, items)));
+  return FMM_OK;
+}
+
+// Fused path: FP32 source tiles are summed on chip; no workspace.
+fmm_status gemm_fused(const Plan& pl, int64_t m, int64_t n, int64_t k, float alpha, const void* A,
+                      int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc,
+                      const DeviceInfo& dev, const fmm_options* opt, cudaStream_t s) {
+  const std::vector<Product> prods = make_products(pl.L);
+  const int g = 1 << pl.L;
+  FusedParams* fp = new FusedParams;
+  std::memset(fp, 0, sizeof(FusedParams));
+  fmm_status st = FMM_OK;
+  std::vector<bool> a_live(g * g, false), b_live(g * g, false);
+  for (int b = 0; b < g * g && st == FMM_OK; ++b) {
+    const int bi = b / g, bj = b % g;
+    const float* Af = static_cast<const float*>(A);
+    const float* Bf = static_cast<const float*>(B);
+    // A block (bi, bj): rows of m, columns of k
+    const int64_t ar = block_extent(m, pl.hm, bi), ac = block_extent(k, pl.hk, bj);
+    if (ar > 0 && ac > 0) {
+      const cuuint64_t dims[2] = {static_cast<cuuint64_t>(ac), static_cast<cuuint64_t>(ar)};
+      const cuuint64_t strides[1] = {static_cast<cuuint64_t>(lda * 4)};
+      const cuuint32_t box[2] = {32, 128};
+      const cuuint32_t estr[2] = {1, 1};
+      CUresult cr = g_encode(&fp->tmSA[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                             const_cast<float*>(Af + (bi * pl.hm * lda + bj * pl.hk)), dims, strides,
+                             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (cr != CUDA_SUCCESS) st = fail(FMM_ERR_CUDA, "cuTensorMapEncodeTiled (A block) failed");
+      a_live[b] = true;
+    }
+    // B block (bi, bj): rows of k, columns of n
+    const int64_t br = block_extent(k, pl.hk, bi), bc = block_extent(n, pl.hn, bj);
+    if (st == FMM_OK && br > 0 && bc > 0) {
+      const cuuint64_t dims[2] = {static_cast<cuuint64_t>(bc), static_cast<cuuint64_t>(br)};
+      const cuuint64_t strides[1] = {static_cast<cuuint64_t>(ldb * 4)};
+      const cuuint32_t box[2] = {static_cast<cuuint32_t>(kFusedTileN), 32};
+      const cuuint32_t estr[2] = {1, 1};
+      CUresult cr = g_encode(&fp->tmSB[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                             const_cast<float*>(Bf + (bi * pl.hk * ldb + bj * pl.hn)), dims, strides,
+                             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (cr != CUDA_SUCCESS) st = fail(FMM_ERR_CUDA, "cuTensorMapEncodeTiled (B block) failed");
+      b_live[b] = true;
+    }
+  }
+  // products whose A- or B-operand has no block inside the matrices contribute nothing
+  std::vector<int> live;
+  for (int r = 0; r < pl.R && st == FMM_OK; ++r) {
+    ProductSrc ps;
+    std::memset(&ps, 0, sizeof ps);
+    for (const Term& t : prods[r].a)
+      if (a_live[t.block]) {
+        ps.a_block[ps.na] = static_cast<int8_t>(t.block);
+        ps.a_sign[ps.na++] = static_cast<int8_t>(t.sign);
+      }
+    for (const Term& t : prods[r].b)
+      if (b_live[t.block]) {
+        ps.b_block[ps.nb] = static_cast<int8_t>(t.block);
+        ps.b_sign[ps.nb++] = static_cast<int8_t>(t.sign);
+      }
+    if (ps.na == 0 || ps.nb == 0) continue;
+    fp->src[live.size()] = ps;
+    live.push_back(r);
+  }
+  int grid = 0;
+  if (st == FMM_OK && !live.empty()) st = fill_common(fp->c, pl, prods, live, m, n, alpha, C, ldc, dev, opt, grid);
+  if (st != FMM_OK || live.empty()) {
+    delete fp;
+    return st;
+  }
+  cudaError_t e;
+  {
+    PhaseScope ps(kPhaseTensor, s);
+    e = launch_fused(*fp, pl.terms, grid, s);
+  }
+  delete fp;
+  if (e != cudaSuccess) return cuda_fail(e, "fused tensor-core pass");
+  return FMM_OK;
+}
+
 
 fmm_status gemm_impl(int64_t m, int64_t n, int64_t k, float alpha, const void* A, int64_t lda,
                      const void* B, int64_t ldb, float beta, float* C, int64_t ldc, int levels,
@@ -282,6 +431,10 @@ fmm_status gemm_impl(int64_t m, int64_t n, int64_t k, float alpha, const void* A
     if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(FMM_ERR_ALIGN, "workspace must be 256-byte aligned");
     if (overlaps(C, c_bytes, ws, pl.ws)) return fail(FMM_ERR_ARG, "C overlaps the workspace");
   }
+  if (pl.algo == FMM_ALGO_FUSED && k > 0 &&
+      (reinterpret_cast<uintptr_t>(A) % 16 != 0 || reinterpret_cast<uintptr_t>(B) % 16 != 0 ||
+       lda % 4 != 0 || ldb % 4 != 0))
+    return fail(FMM_ERR_ALIGN, "the fused algorithm needs 16-byte aligned A and B and lda, ldb multiples of 4");
   DeviceInfo dev;
   st = device_info(dev);
   if (st != FMM_OK) return st;
@@ -294,6 +447,7 @@ fmm_status gemm_impl(int64_t m, int64_t n, int64_t k, float alpha, const void* A
     if (e != cudaSuccess) return cuda_fail(e, "beta pass");
   }
   if (k == 0 || alpha == 0.0f) return FMM_OK;
+  if (pl.algo == FMM_ALGO_FUSED) return gemm_fused(pl, m, n, k, alpha, A, lda, B, ldb, C, ldc, dev, opt, s);
 
   const std::vector<Product> prods = make_products(pl.L);
   const int g = 1 << pl.L;
@@ -384,68 +538,14 @@ fmm_status gemm_impl(int64_t m, int64_t n, int64_t k, float alpha, const void* A
     else
       st = encode_3d(&pp->tmB[t], t ? b_lo : b_hi, pl.hk, pl.hn, pl.R, pl.ldb_w, kBK, pl.tile_n);
   }
+  std::vector<int> live(pl.R);
+  for (int r = 0; r < pl.R; ++r) live[r] = r;
+  int grid = 0;
+  if (st == FMM_OK) st = fill_common(pp->c, pl, prods, live, m, n, alpha, C, ldc, dev, opt, grid);
   if (st != FMM_OK) {
     delete pp;
     return st;
   }
-  pp->C = C;
-  pp->ldc = ldc;
-  pp->alpha = alpha;
-  pp->schedule = pl.schedule;
-  pp->c_tma = (reinterpret_cast<uintptr_t>(C) % 16 == 0 && ldc % 4 == 0) ? 1 : 0;
-  pp->err = dev.err;
-  pp->timeout_ns = g_timeout_ns.load();
-  pp->tiles_m = static_cast<int32_t>((pl.hm + kBM - 1) / kBM);
-  pp->tiles_n = static_cast<int32_t>((pl.hn + pl.tile_n - 1) / pl.tile_n);
-  pp->nk = static_cast<int32_t>((pl.hk + kBK - 1) / kBK);
-  const int64_t items = static_cast<int64_t>(pl.R) * pp->tiles_m * pp->tiles_n;
-  if (items >= (int64_t(1) << 31)) {
-    delete pp;
-    return fail(FMM_ERR_ARG, "too many tiles");
-  }
-  pp->num_items = static_cast<int32_t>(items);
-  pp->num_products = pl.R;
-  pp->c_vec4 = (reinterpret_cast<uintptr_t>(C) % 16 == 0 && ldc % 4 == 0) ? 1 : 0;
-  for (int r = 0; r < pl.R; ++r) {
-    int cnt = 0;
-    for (const Term& t : prods[r].c) {
-      const int br = t.block / g, bc = t.block % g;
-      const int64_t rows = std::min<int64_t>(std::max<int64_t>(m - br * pl.hm, 0), pl.hm);
-      const int64_t cols = std::min<int64_t>(std::max<int64_t>(n - bc * pl.hn, 0), pl.hn);
-      if (rows == 0 || cols == 0) continue;
-      DestEntry& de = pp->prod[r].d[cnt++];
-      de.offset = br * pl.hm * ldc + bc * pl.hn;
-      de.rows = static_cast<int32_t>(rows);
-      de.cols = static_cast<int32_t>(cols);
-      de.coef = alpha * static_cast<float>(t.sign);
-      de.block = t.block;
-    }
-    pp->prod[r].count = cnt;
-  }
-  if (pp->c_tma) {
-    // one FP32 map per non-empty destination block, clipped to the block's extent in C
-    for (int b = 0; b < g * g && st == FMM_OK; ++b) {
-      const int br = b / g, bc = b % g;
-      const int64_t rows = std::min<int64_t>(std::max<int64_t>(m - br * pl.hm, 0), pl.hm);
-      const int64_t cols = std::min<int64_t>(std::max<int64_t>(n - bc * pl.hn, 0), pl.hn);
-      if (rows == 0 || cols == 0) continue;
-      const cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
-      const cuuint64_t strides[1] = {static_cast<cuuint64_t>(ldc * 4)};
-      const cuuint32_t box[2] = {32, 32};
-      const cuuint32_t estr[2] = {1, 1};
-      CUresult cr = g_encode(&pp->tmC[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
-                             C + (br * pl.hm * ldc + bc * pl.hn), dims, strides, box, estr,
-                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-      if (cr != CUDA_SUCCESS) st = fail(FMM_ERR_CUDA, "cuTensorMapEncodeTiled (C) failed (" + std::to_string(cr) + ")");
-    }
-    if (st != FMM_OK) {
-      delete pp;
-      return st;
-    }
-  }
-  int grid = opt && opt->num_ctas > 0 ? opt->num_ctas : dev.sms;
-  grid = static_cast<int>(std::min<int64_t>(grid, items));
   cudaError_t e;
   {
     PhaseScope ps(kPhaseTensor, s);

@@ -1,0 +1,309 @@
+// fmm_fused.cuh -- Strassen products with the operand sums formed on chip (Section 3.1).
+//
+// For product r the A-operand is P = sum_w sign_w * A_block(w) (W_A terms) and the
+// B-operand Q = sum_w sign_w * B_block(w) (W_B terms).  Per 64-deep k-step:
+//   warp 0      TMA-loads, for each k half (32 deep) and each source block, one FP32 tile
+//               into a 4-slot shared-memory ring (A: 128 rows x 32 k, 128-byte swizzle;
+//               B: 32 k-rows x 128 n, unswizzled) -- the W_A (W_B) submatrix tiles;
+//   warps 8-15  (transform) add every slot into FP32 register accumulators with its sign,
+//               then split the sums into BF16 hi / lo (or round once) and store them into
+//               the MMA operand stage (A K-major, B MN-major, 128-byte swizzle);
+//   warp 1      UMMA issue as in the packed kernel (mma_role);
+//   warps 4-7   multi-destination write-back (epilogue_role).
+// No workspace: the sums never leave the SM.  A and B are FP32, 16-byte aligned, with
+// leading dimensions that are multiples of 4.
+#pragma once
+#include <cuda_bf16.h>
+#include "fmm_kernels.cuh"
+
+namespace fmm {
+
+constexpr int kFusedThreads = 512;
+constexpr int kFusedBN = kFusedTileN;
+constexpr uint32_t kSlotBytes = 16384;
+
+template <int TERMS>
+struct FusedCfg {
+  using SL = StageLayout<kFusedBN, TERMS>;
+  static constexpr int kOpStages = TERMS == 3 ? 2 : 4;
+  static constexpr int kSlots = 4;
+  static constexpr uint32_t kSlotOffset = kOpStages * SL::kBytes;
+  static constexpr uint32_t kEpiOffset = kSlotOffset + kSlots * kSlotBytes;
+  static constexpr uint32_t kBarOffset = kEpiOffset + kEpiBytes;
+  static constexpr uint32_t kSmemBytes = kBarOffset + 512 + 1024;
+  static constexpr uint32_t kTmemCols = 2 * kFusedBN;
+};
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo_elem, float hi_elem) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo_elem, hi_elem);  // .x = lo_elem
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// Split 2 FP32 values into packed BF16x2 hi and lo words: hi = bf16(x), lo = bf16(x - hi).
+__device__ __forceinline__ void split2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+  hi = pack_bf16x2(x0, x1);
+  const float h0 = __uint_as_float(hi << 16);
+  const float h1 = __uint_as_float(hi & 0xFFFF0000u);
+  lo = pack_bf16x2(x0 - h0, x1 - h1);
+}
+
+template <int TERMS>
+__global__ void __launch_bounds__(kFusedThreads, 1) fmm_fused_kernel(const __grid_constant__ FusedParams fp) {
+  using Cfg = FusedCfg<TERMS>;
+  using SL = typename Cfg::SL;
+  constexpr int S = Cfg::kOpStages;
+  constexpr int NS = Cfg::kSlots;
+  const CommonParams& p = fp.c;
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::kBarOffset);
+  uint64_t* slot_full = bars;
+  uint64_t* slot_empty = bars + NS;
+  uint64_t* op_full = bars + 2 * NS;
+  uint64_t* op_empty = bars + 2 * NS + S;
+  uint64_t* acc_full = bars + 2 * NS + 2 * S;
+  uint64_t* acc_empty = bars + 2 * NS + 2 * S + 2;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * NS + 2 * S + 4);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+  uint8_t* slots = smem + Cfg::kSlotOffset;
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(smem_u32(&slot_full[s]), 1);
+      mbar_init(smem_u32(&slot_empty[s]), 8);  // one arrival per transform warp
+    }
+    for (int s = 0; s < S; ++s) {
+      mbar_init(smem_u32(&op_full[s]), 8);
+      mbar_init(smem_u32(&op_empty[s]), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(smem_u32(&acc_full[a]), 1);
+      mbar_init(smem_u32(&acc_empty[a]), 4 * 32);
+    }
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    __syncwarp();
+    tmem_alloc(smem_u32(tmem_holder), Cfg::kTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_holder;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int slot = 0;
+      uint32_t sph = 0;
+      bool ok = true;
+      auto issue = [&](const CUtensorMap* map, int x, int y) -> bool {
+        if (!mbar_wait(smem_u32(&slot_empty[slot]), sph ^ 1u, p.timeout_ns, abort_flag)) return false;
+        const uint32_t fb = smem_u32(&slot_full[slot]);
+        mbar_arrive_expect_tx(fb, kSlotBytes);
+        tma_load_2d(smem_u32(slots + slot * kSlotBytes), map, fb, x, y);
+        if (++slot == NS) {
+          slot = 0;
+          sph ^= 1u;
+        }
+        return true;
+      };
+      for (int item = blockIdx.x; ok && item < p.num_items; item += gridDim.x) {
+        int r, tm, tn;
+        decode_item(item, p, r, tm, tn);
+        const ProductSrc& ps = fp.src[r];
+        for (int kb = 0; ok && kb < p.nk; ++kb) {
+          for (int h = 0; ok && h < 2; ++h) {
+            for (int w = 0; ok && w < ps.na; ++w)
+              ok = issue(&fp.tmSA[ps.a_block[w]], kb * kBK + 32 * h, tm * kBM);
+            for (int w = 0; ok && w < ps.nb; ++w)
+              ok = issue(&fp.tmSB[ps.b_block[w]], tn * kFusedBN, kb * kBK + 32 * h);
+          }
+        }
+      }
+      if (!ok) {
+        atomicOr(p.err, kErrProducerWait);
+        *abort_flag = 1;
+        drain_pause(2000000ull);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      if (!mma_role<kFusedBN, TERMS, S, true, true>(p, smem, op_full, op_empty, acc_full, acc_empty,
+                                                    tmem_base, abort_flag)) {
+        atomicOr(p.err, kErrMmaWait);
+        *abort_flag = 1;
+        drain_pause(2000000ull);
+      }
+    }
+  } else if (warp >= 4 && warp < 8) {
+    if (!epilogue_role<kFusedBN>(p, smem + Cfg::kEpiOffset, acc_full, acc_empty, tmem_base, abort_flag,
+                                 warp, lane)) {
+      if (lane == 0) atomicOr(p.err, kErrEpilogueWait);
+      *abort_flag = 1;
+    }
+  } else if (warp >= 8) {
+    // ------------------------------------------------------------ transform
+    // Thread t (0..255).  A: per k half, rows t & 127, 8-wide k chunks 2*(t >> 7) + {0, 1}
+    // of the half's four.  B: per k half, units j = t + 256 v (v = 0..3): k-row j >> 5 of
+    // the half, n = 4 * (j & 31) .. + 3.  Every warp reads every slot.
+    const int t = threadIdx.x - 256;
+    const int arow = t & 127;
+    const int acc0 = 2 * (t >> 7);
+    int slot = 0;
+    uint32_t sph = 0;
+    int o = 0;
+    uint32_t oph = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; ok && item < p.num_items; item += gridDim.x) {
+      int r, tm, tn;
+      decode_item(item, p, r, tm, tn);
+      const ProductSrc& ps = fp.src[r];
+      for (int kb = 0; ok && kb < p.nk; ++kb) {
+        float aA[2][2][8];
+        float aB[2][4][4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+          for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int e = 0; e < 8; ++e) aA[h][u][e] = 0.f;
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) aB[h][v][e] = 0.f;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          for (int w = 0; w < ps.na; ++w) {
+            if (ok) ok = mbar_wait(smem_u32(&slot_full[slot]), sph, p.timeout_ns, abort_flag);
+            if (ok) {
+              const uint8_t* sl = slots + slot * kSlotBytes;
+              const float sg = ps.a_sign[w] < 0 ? -1.f : 1.f;
+#pragma unroll
+              for (int u = 0; u < 2; ++u) {
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                  const int ch = 2 * (acc0 + u) + e;  // 16-byte FP32 chunk of the 128-byte row
+                  const float4 x =
+                      *reinterpret_cast<const float4*>(sl + arow * 128 + ((ch ^ (arow & 7)) << 4));
+                  aA[h][u][4 * e] = fmaf(sg, x.x, aA[h][u][4 * e]);
+                  aA[h][u][4 * e + 1] = fmaf(sg, x.y, aA[h][u][4 * e + 1]);
+                  aA[h][u][4 * e + 2] = fmaf(sg, x.z, aA[h][u][4 * e + 2]);
+                  aA[h][u][4 * e + 3] = fmaf(sg, x.w, aA[h][u][4 * e + 3]);
+                }
+              }
+              __syncwarp();
+              if (lane == 0) mbar_arrive(smem_u32(&slot_empty[slot]));
+            }
+            if (++slot == NS) {
+              slot = 0;
+              sph ^= 1u;
+            }
+          }
+          for (int w = 0; w < ps.nb; ++w) {
+            if (ok) ok = mbar_wait(smem_u32(&slot_full[slot]), sph, p.timeout_ns, abort_flag);
+            if (ok) {
+              const uint8_t* sl = slots + slot * kSlotBytes;
+              const float sg = ps.b_sign[w] < 0 ? -1.f : 1.f;
+#pragma unroll
+              for (int v = 0; v < 4; ++v) {
+                const int j = t + 256 * v;
+                const float4 x = *reinterpret_cast<const float4*>(sl + (j >> 5) * 512 + (j & 31) * 16);
+                aB[h][v][0] = fmaf(sg, x.x, aB[h][v][0]);
+                aB[h][v][1] = fmaf(sg, x.y, aB[h][v][1]);
+                aB[h][v][2] = fmaf(sg, x.z, aB[h][v][2]);
+                aB[h][v][3] = fmaf(sg, x.w, aB[h][v][3]);
+              }
+              __syncwarp();
+              if (lane == 0) mbar_arrive(smem_u32(&slot_empty[slot]));
+            }
+            if (++slot == NS) {
+              slot = 0;
+              sph ^= 1u;
+            }
+          }
+        }
+        if (!ok) break;
+        // the operand stage must have been consumed by the UMMAs of its previous use
+        if (!mbar_wait(smem_u32(&op_empty[o]), oph ^ 1u, p.timeout_ns, abort_flag)) {
+          ok = false;
+          break;
+        }
+        uint8_t* st = smem + o * SL::kBytes;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int c = 4 * h + acc0 + u;  // 8-wide bf16 chunk of the 64-deep row
+            const uint32_t off = arow * 128 + ((c ^ (arow & 7)) << 4);
+            if (TERMS == 3) {
+              uint4 hv, lv;
+              split2(aA[h][u][0], aA[h][u][1], hv.x, lv.x);
+              split2(aA[h][u][2], aA[h][u][3], hv.y, lv.y);
+              split2(aA[h][u][4], aA[h][u][5], hv.z, lv.z);
+              split2(aA[h][u][6], aA[h][u][7], hv.w, lv.w);
+              *reinterpret_cast<uint4*>(st + SL::kAHi + off) = hv;
+              *reinterpret_cast<uint4*>(st + SL::kALo + off) = lv;
+            } else {
+              uint4 hv;
+              hv.x = pack_bf16x2(aA[h][u][0], aA[h][u][1]);
+              hv.y = pack_bf16x2(aA[h][u][2], aA[h][u][3]);
+              hv.z = pack_bf16x2(aA[h][u][4], aA[h][u][5]);
+              hv.w = pack_bf16x2(aA[h][u][6], aA[h][u][7]);
+              *reinterpret_cast<uint4*>(st + SL::kAHi + off) = hv;
+            }
+          }
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const int j = t + 256 * v;
+            const int kk = 32 * h + (j >> 5);  // k-row of the 64-deep stage
+            const int nq = j & 31;             // n = 4 nq .. 4 nq + 3
+            const int c = (nq & 15) >> 1;      // 8-wide chunk inside the 64-wide n atom
+            const uint32_t off = (nq >> 4) * 8192 + (kk >> 3) * 1024 + (kk & 7) * 128 +
+                                 ((c ^ (kk & 7)) << 4) + (nq & 1) * 8;
+            if (TERMS == 3) {
+              uint2 hv, lv;
+              split2(aB[h][v][0], aB[h][v][1], hv.x, lv.x);
+              split2(aB[h][v][2], aB[h][v][3], hv.y, lv.y);
+              *reinterpret_cast<uint2*>(st + SL::kBHi + off) = hv;
+              *reinterpret_cast<uint2*>(st + SL::kBLo + off) = lv;
+            } else {
+              uint2 hv;
+              hv.x = pack_bf16x2(aB[h][v][0], aB[h][v][1]);
+              hv.y = pack_bf16x2(aB[h][v][2], aB[h][v][3]);
+              *reinterpret_cast<uint2*>(st + SL::kBHi + off) = hv;
+            }
+          }
+        }
+        fence_proxy_async_smem();  // generic-proxy stores -> visible to the tensor core
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&op_full[o]));
+        if (++o == S) {
+          o = 0;
+          oph ^= 1u;
+        }
+      }
+    }
+    if (!ok) {
+      if (lane == 0) atomicOr(p.err, kErrTransformWait);
+      *abort_flag = 1;
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem_base, Cfg::kTmemCols);
+  }
+}
+
+}  // namespace fmm

@@ -1,22 +1,28 @@
-// fmm_kernels.cuh -- parameter blocks and device kernels of the fused Strassen GEMM.
+// fmm_kernels.cuh -- parameter blocks and device kernels of the Strassen GEMM library.
 //
-// One persistent, warp-specialised tcgen05 kernel runs every Strassen product
-// ("instance" in Section 3.2) of one GEMM call:
+// Two persistent, warp-specialised tcgen05 kernels run every Strassen product ("instance"
+// in Section 3.2) of one GEMM call.  A work item is (product r, 128 x BN output tile of the
+// h_m x h_n block grid).  Both kernels share the MMA and epilogue roles below:
 //
-//   work item  = (product r, 128 x BN output tile of the h_m x h_n block grid)
-//   warp 0     = TMA producer: per k-step, loads the A- and B-operand tiles of
-//                product r (hi and lo halves for the split-BF16 arithmetic) into a
-//                STAGES-deep shared-memory ring;
-//   warp 1     = TMEM allocator and single-thread UMMA issuer: 1 or 3 tcgen05.mma
-//                per 16-wide k-slice into a double-buffered FP32 TMEM accumulator;
-//   warps 4..7 = epilogue: tcgen05.ld of the finished accumulator, then, for every
-//                C block the product feeds, C_block += alpha * W[c, r] * M_r (the
-//                multi-destination write-back of Section 3.1), masked at fringes.
+//   MMA role (warp 1)        TMEM allocator and single-thread UMMA issuer: 1 or 3
+//                            tcgen05.mma per 16-wide k-slice into a double-buffered FP32
+//                            TMEM accumulator;
+//   epilogue role (warps 4-7) tcgen05.ld of the finished accumulator, then, for every C
+//                            block the product feeds, C_block += alpha * W[c, r] * M_r (the
+//                            multi-destination write-back of Section 3.1) by TMA reductions
+//                            (or element-wise reductions when C rows are not 16-byte
+//                            aligned), clipped at each block's real extent.
 //
-// The epilogue adds with element-wise atomic reductions (the atomic-update scheme
-// of Section 3.3), so items of different products that feed the same C block may
-// run concurrently on different SMs without a race; beta is applied to C by a
-// separate pass before the products start.
+// They differ in where the operand sums come from:
+//   fmm_packed_kernel  the sums were formed by a streaming pass and are TMA-loaded as BF16;
+//   fmm_fused_kernel   (fmm_fused.cuh) TMA stages the FP32 source tiles of every block a
+//                      product's operands combine, and transform warps add them with their
+//                      signs and split/round them into the MMA operand tiles on chip
+//                      (Section 3.1: the sums are formed while the tiles are packed).
+//
+// Every C update is a reduction, so items of different products that feed the same C block
+// may run on different SMs at the same time without a race (the atomic-update scheme of
+// Section 3.3); beta is applied to C by a separate pass before the products start.
 #pragma once
 #include <cstdint>
 #include <cuda.h>
@@ -30,6 +36,7 @@ constexpr int kMaxProducts = 49;  // 7^2
 constexpr int kMaxDest = 4;       // W_C <= 4 at two levels
 constexpr int kMaxSources = 16;   // 4^2 blocks per operand at two levels
 constexpr int kThreads = 256;
+constexpr int kFusedTileN = 128;  // output tile width of the fused kernel
 
 // Eq. (3), Section 3: the seven products of one-level Strassen.  Quadrant q = 2*row + col
 // (Eq. 2).  strassen_u(r, q): coefficient of A_q in the A-operand of product r; strassen_v:
@@ -78,9 +85,8 @@ enum Schedule : int32_t {
   kSchedTileRounds = 1,    // each CTA runs every product of one tile in turn (C stays in L2)
 };
 
-struct PackedParams {
-  CUtensorMap tmA[2];   // A-operand sums, hi / lo: 3-D {k, row, product}, 16-bit
-  CUtensorMap tmB[2];   // B-operand sums, hi / lo: 3-D {n, k, product} (or {k, n, product})
+// Part of the kernel parameters shared by both kernels: work list, destinations, C maps.
+struct CommonParams {
   CUtensorMap tmC[kMaxSources];  // one f32 map per destination block, clipped to its extent
   float* C;
   int64_t ldc;
@@ -93,6 +99,29 @@ struct PackedParams {
   int32_t c_tma;     // write-back by TMA reductions through tmC (C rows 16-byte aligned)
   int32_t c_vec4;    // element-wise path: C rows are 16-byte aligned, vector reductions allowed
   ProductDests prod[kMaxProducts];
+};
+
+// Kernel parameters of the packed-operand path (operand sums already formed).
+struct PackedParams {
+  CUtensorMap tmA[2];  // A-operand sums, hi / lo: 3-D {k, row, product}, 16-bit
+  CUtensorMap tmB[2];  // B-operand sums, hi / lo: 3-D {n, k, product} (or {k, n, product})
+  CommonParams c;
+};
+
+// Source blocks of one product's operands (fused path).
+struct ProductSrc {
+  int8_t na, nb;  // W_A, W_B (only blocks that exist in A / B are listed)
+  int8_t pad[2];
+  int8_t a_block[kMaxDest], a_sign[kMaxDest];
+  int8_t b_block[kMaxDest], b_sign[kMaxDest];
+};
+
+// Kernel parameters of the fused path (operand sums formed on chip).
+struct FusedParams {
+  CUtensorMap tmSA[kMaxSources];  // FP32 blocks of A: 2-D {k, m}, box 32 x 128, 128B swizzle
+  CUtensorMap tmSB[kMaxSources];  // FP32 blocks of B: 2-D {n, k}, box 128 x 32, no swizzle
+  ProductSrc src[kMaxProducts];
+  CommonParams c;
 };
 
 // One signed source block of an operand sum.
@@ -151,7 +180,7 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
 // taken G at a time; within a round the item index is r * G + (t - round start), so CTA b
 // runs products 0..R-1 of one tile back to back; the last, partial round is spread over all
 // CTAs product by product.
-__device__ __forceinline__ void decode_item(int item, const PackedParams& p, int& r, int& tm, int& tn) {
+__device__ __forceinline__ void decode_item(int item, const CommonParams& p, int& r, int& tm, int& tn) {
   const int tiles = p.tiles_m * p.tiles_n;
   int t;
   if (p.schedule == kSchedTileRounds) {
@@ -176,23 +205,191 @@ __device__ __forceinline__ void decode_item(int item, const PackedParams& p, int
   tile_coords(t, p.tiles_m, p.tiles_n, tm, tn);
 }
 
-template <int BN, int TERMS, int STAGES>
-struct PackedCfg {
+
+// Byte layout of one operand stage (both kernels): [A hi | B hi | A lo | B lo], A tile
+// 128 x 64 K-major, B tile 64 (k) x BN MN-major (or BN x 64 K-major), 128-byte swizzle.
+template <int BN, int TERMS>
+struct StageLayout {
   static constexpr uint32_t kABytes = kBM * kBK * 2;
   static constexpr uint32_t kBBytes = BN * kBK * 2;
-  static constexpr uint32_t kStageBytes = (TERMS == 3 ? 2u : 1u) * (kABytes + kBBytes);
-  static constexpr uint32_t kEpiOffset = STAGES * kStageBytes;  // 4 warps x 2 x 4 KB staging
-  static constexpr uint32_t kEpiBytes = 4 * 2 * 4096;
+  static constexpr uint32_t kBytes = (TERMS == 3 ? 2u : 1u) * (kABytes + kBBytes);
+  static constexpr uint32_t kAHi = 0, kBHi = kABytes, kALo = kABytes + kBBytes,
+                            kBLo = 2 * kABytes + kBBytes;
+};
+
+constexpr uint32_t kEpiBytes = 4 * 2 * 4096;  // epilogue staging: 4 warps x 2 x (32 x 32 FP32)
+
+// ------------------------------------------------------------------- MMA role
+// Single thread.  For each item: wait for a free accumulator, then for each k-step wait for
+// the operand stage, issue 4 k16 slices x (1 or 3) UMMAs, and release the stage; finally
+// signal the epilogue.  Returns false if a wait gave up.
+template <int BN, int TERMS, int STAGES, bool BF16, bool B_MN>
+__device__ __forceinline__ bool mma_role(const CommonParams& p, uint8_t* smem, uint64_t* full,
+                                         uint64_t* empty, uint64_t* acc_full, uint64_t* acc_empty,
+                                         uint32_t tmem_base, volatile int* abort_flag) {
+  using SL = StageLayout<BN, TERMS>;
+  constexpr uint32_t idesc = make_idesc_f16(kBM, BN, BF16, B_MN);
+  int stage = 0;
+  uint32_t phase = 0;
+  int it = 0;
+  for (int item = blockIdx.x; item < p.num_items; item += gridDim.x, ++it) {
+    const int acc = it & 1;
+    const uint32_t acc_par = (it >> 1) & 1;
+    if (!mbar_wait(smem_u32(&acc_empty[acc]), acc_par ^ 1u, p.timeout_ns, abort_flag)) return false;
+    tc_fence_after();
+    const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * BN);
+    for (int kb = 0; kb < p.nk; ++kb) {
+      if (!mbar_wait(smem_u32(&full[stage]), phase, p.timeout_ns, abort_flag)) return false;
+      tc_fence_after();
+      uint8_t* st = smem + stage * SL::kBytes;
+      const uint64_t da_hi = make_sdesc_kmajor_sw128(smem_u32(st + SL::kAHi));
+      const uint64_t da_lo = make_sdesc_kmajor_sw128(smem_u32(st + SL::kALo));
+      const uint64_t db_hi = B_MN ? make_sdesc_mnmajor_sw128(smem_u32(st + SL::kBHi), 8192, 1024)
+                                  : make_sdesc_kmajor_sw128(smem_u32(st + SL::kBHi));
+      const uint64_t db_lo = B_MN ? make_sdesc_mnmajor_sw128(smem_u32(st + SL::kBLo), 8192, 1024)
+                                  : make_sdesc_kmajor_sw128(smem_u32(st + SL::kBLo));
+#pragma unroll
+      for (int kk = 0; kk < kBK / 16; ++kk) {
+        // K-major: 16 elements = 32 bytes inside the swizzle row; MN-major: 16 k-rows = two
+        // 1024-byte atoms.  Descriptor start addresses are encoded >> 4.
+        const uint64_t ka = static_cast<uint64_t>(kk * 2);
+        const uint64_t kb16 = B_MN ? static_cast<uint64_t>(kk * 128) : ka;
+        umma_f16_ss(d_tmem, da_hi + ka, db_hi + kb16, idesc, (kb | kk) != 0 ? 1u : 0u);
+        if (TERMS == 3) {
+          umma_f16_ss(d_tmem, da_hi + ka, db_lo + kb16, idesc, 1u);
+          umma_f16_ss(d_tmem, da_lo + ka, db_hi + kb16, idesc, 1u);
+        }
+      }
+      umma_commit(smem_u32(&empty[stage]));
+      if (++stage == STAGES) {
+        stage = 0;
+        phase ^= 1u;
+      }
+    }
+    umma_commit(smem_u32(&acc_full[acc]));
+  }
+  return true;
+}
+
+// -------------------------------------------------------------- epilogue role
+// Warps 4..7.  Each warp owns TMEM lanes 32q..32q+31 (rows of the tile) and two 4 KB
+// staging buffers: a 32 x 32 FP32 block is written there in the 128-byte swizzled layout and
+// added into every destination block by TMA reductions.  Returns false if a wait gave up.
+template <int BN>
+__device__ __forceinline__ bool epilogue_role(const CommonParams& p, uint8_t* epi_smem,
+                                              uint64_t* acc_full, uint64_t* acc_empty,
+                                              uint32_t tmem_base, volatile int* abort_flag,
+                                              int warp, int lane) {
+  const int q = warp & 3;  // TMEM lane quarter this warp may access
+  const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
+  uint8_t* stage_base = epi_smem + q * 8192;
+  int buf = 0;
+  int it = 0;
+  bool ok = true;
+  for (int item = blockIdx.x; item < p.num_items; item += gridDim.x, ++it) {
+    const int acc = it & 1;
+    const uint32_t acc_par = (it >> 1) & 1;
+    if (!mbar_wait(smem_u32(&acc_full[acc]), acc_par, p.timeout_ns, abort_flag)) {
+      ok = false;
+      break;
+    }
+    tc_fence_after();
+    int r, tm, tn;
+    decode_item(item, p, r, tm, tn);
+    const ProductDests& pd = p.prod[r];
+    const int row0 = tm * kBM + q * 32;
+    const int row = row0 + lane;
+    bool has_sign[2] = {false, false};
+    for (int d = 0; d < pd.count; ++d) has_sign[pd.d[d].coef < 0.f ? 1 : 0] = true;
+#pragma unroll 1
+    for (int c = 0; c < BN; c += 32) {
+      float v[32];
+      tmem_ld_32x32b_x32(tmem_base + lane_off + static_cast<uint32_t>(acc * BN + c), v);
+      if (c + 32 == BN) {
+        // every TMEM read of this accumulator is complete: hand it back to the MMA warp
+        tc_fence_before();
+        mbar_arrive(smem_u32(&acc_empty[acc]));
+      }
+      const int col0 = tn * BN + c;
+      if (p.c_tma) {
+#pragma unroll 1
+        for (int sg = 0; sg < 2; ++sg) {
+          if (!has_sign[sg]) continue;
+          const float cf = sg ? -p.alpha : p.alpha;
+          uint8_t* sb = stage_base + buf * 4096;
+          if (lane == 0) bulk_wait_group_read<1>();  // this buffer's previous reductions read it
+          __syncwarp();
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const float4 val = make_float4(cf * v[4 * j], cf * v[4 * j + 1], cf * v[4 * j + 2],
+                                           cf * v[4 * j + 3]);
+            *reinterpret_cast<float4*>(sb + lane * 128 + ((j ^ (lane & 7)) << 4)) = val;
+          }
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) {
+            for (int d = 0; d < pd.count; ++d) {
+              const DestEntry& de = pd.d[d];
+              if ((de.coef < 0.f ? 1 : 0) != sg) continue;
+              tma_reduce_add_2d(&p.tmC[de.block], smem_u32(sb), col0, row0);
+            }
+            bulk_commit_group();
+          }
+          buf ^= 1;
+        }
+      } else {
+#pragma unroll 1
+        for (int d = 0; d < pd.count; ++d) {
+          const DestEntry de = pd.d[d];
+          if (row >= de.rows || col0 >= de.cols) continue;
+          float* dst = p.C + de.offset + static_cast<int64_t>(row) * p.ldc + col0;
+          const float cf = de.coef;
+          if (p.c_vec4 && col0 + 32 <= de.cols) {
+            float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              atomicAdd(d4 + j, make_float4(cf * v[4 * j], cf * v[4 * j + 1], cf * v[4 * j + 2],
+                                            cf * v[4 * j + 3]));
+          } else {
+            const int lim = de.cols - col0;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (j < lim) atomicAdd(dst + j, cf * v[j]);
+          }
+        }
+      }
+    }
+  }
+  if (lane == 0) bulk_wait_group<0>();  // reductions complete before the CTA retires
+  return ok;
+}
+
+// Spin for about `ns` nanoseconds (used after a wait gave up, so that copies and UMMAs
+// already in flight finish before shared memory and TMEM are released).
+__device__ __forceinline__ void drain_pause(uint64_t ns) {
+  const uint64_t t0 = globaltimer_ns();
+  while (globaltimer_ns() - t0 < ns) {
+  }
+}
+
+// ------------------------------------------------------------ packed kernel
+template <int BN, int TERMS, int STAGES>
+struct PackedCfg {
+  using SL = StageLayout<BN, TERMS>;
+  static constexpr uint32_t kStageBytes = SL::kBytes;
+  static constexpr uint32_t kEpiOffset = STAGES * kStageBytes;
   static constexpr uint32_t kBarOffset = kEpiOffset + kEpiBytes;
   static constexpr uint32_t kSmemBytes = kBarOffset + 256 + 1024;  // + barriers + alignment slack
   static constexpr uint32_t kTmemCols = 2 * BN;
 };
 
 template <int BN, int TERMS, int STAGES, bool BF16, bool B_MN>
-__global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_constant__ PackedParams p) {
+__global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_constant__ PackedParams pp) {
   using Cfg = PackedCfg<BN, TERMS, STAGES>;
-  static_assert(BN % 32 == 0 && BN >= 32 && BN <= 256, "UMMA N");
+  using SL = StageLayout<BN, TERMS>;
+  static_assert(BN % 64 == 0 && BN <= 256, "UMMA N");
   static_assert(Cfg::kTmemCols >= 32 && Cfg::kTmemCols <= 512, "TMEM columns");
+  const CommonParams& p = pp.c;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -220,11 +417,11 @@ __global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_co
     fence_mbar_init();
   }
   if (warp == 0 && lane == 0) {
-    tma_prefetch_desc(&p.tmA[0]);
-    tma_prefetch_desc(&p.tmB[0]);
+    tma_prefetch_desc(&pp.tmA[0]);
+    tma_prefetch_desc(&pp.tmB[0]);
     if (TERMS == 3) {
-      tma_prefetch_desc(&p.tmA[1]);
-      tma_prefetch_desc(&p.tmB[1]);
+      tma_prefetch_desc(&pp.tmA[1]);
+      tma_prefetch_desc(&pp.tmB[1]);
     }
   }
   if (warp == 1) {
@@ -248,30 +445,25 @@ __global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_co
         decode_item(item, p, r, tm, tn);
         for (int kb = 0; kb < p.nk; ++kb) {
           if (!mbar_wait(smem_u32(&empty[stage]), phase ^ 1u, p.timeout_ns, abort_flag)) {
-            atomicOr(p.err, kErrProducerWait);
-            *abort_flag = 1;
             ok = false;
             break;
           }
           uint8_t* st = smem + stage * Cfg::kStageBytes;
           const uint32_t fb = smem_u32(&full[stage]);
           mbar_arrive_expect_tx(fb, Cfg::kStageBytes);
-          tma_load_3d(smem_u32(st), &p.tmA[0], fb, kb * kBK, tm * kBM, r);
-          if (TERMS == 3)
-            tma_load_3d(smem_u32(st + Cfg::kABytes + Cfg::kBBytes), &p.tmA[1], fb, kb * kBK, tm * kBM, r);
+          tma_load_3d(smem_u32(st + SL::kAHi), &pp.tmA[0], fb, kb * kBK, tm * kBM, r);
+          if (TERMS == 3) tma_load_3d(smem_u32(st + SL::kALo), &pp.tmA[1], fb, kb * kBK, tm * kBM, r);
           if (B_MN) {
             // B operand sums stored k-rows x n-cols: BN/64 boxes of 64 (n) x 64 (k), 8 KB each
 #pragma unroll
             for (int j = 0; j < BN / 64; ++j) {
-              tma_load_3d(smem_u32(st + Cfg::kABytes + j * 8192), &p.tmB[0], fb, tn * BN + 64 * j, kb * kBK, r);
+              tma_load_3d(smem_u32(st + SL::kBHi + j * 8192), &pp.tmB[0], fb, tn * BN + 64 * j, kb * kBK, r);
               if (TERMS == 3)
-                tma_load_3d(smem_u32(st + 2 * Cfg::kABytes + Cfg::kBBytes + j * 8192), &p.tmB[1], fb,
-                            tn * BN + 64 * j, kb * kBK, r);
+                tma_load_3d(smem_u32(st + SL::kBLo + j * 8192), &pp.tmB[1], fb, tn * BN + 64 * j, kb * kBK, r);
             }
           } else {
-            tma_load_3d(smem_u32(st + Cfg::kABytes), &p.tmB[0], fb, kb * kBK, tn * BN, r);
-            if (TERMS == 3)
-              tma_load_3d(smem_u32(st + 2 * Cfg::kABytes + Cfg::kBBytes), &p.tmB[1], fb, kb * kBK, tn * BN, r);
+            tma_load_3d(smem_u32(st + SL::kBHi), &pp.tmB[0], fb, kb * kBK, tn * BN, r);
+            if (TERMS == 3) tma_load_3d(smem_u32(st + SL::kBLo), &pp.tmB[1], fb, kb * kBK, tn * BN, r);
           }
           if (++stage == STAGES) {
             stage = 0;
@@ -280,159 +472,26 @@ __global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_co
         }
       }
       if (!ok) {
-        // let loads already in flight land before the CTA's shared memory goes away
-        const uint64_t t0 = globaltimer_ns();
-        while (globaltimer_ns() - t0 < 2000000ull) {
-        }
+        atomicOr(p.err, kErrProducerWait);
+        *abort_flag = 1;
+        drain_pause(2000000ull);
       }
     }
   } else if (warp == 1) {
-    // ---------------------------------------------------------- MMA issuer
     if (lane == 0) {
-      constexpr uint32_t idesc = make_idesc_f16(kBM, BN, BF16, B_MN);
-      int stage = 0;
-      uint32_t phase = 0;
-      int it = 0;
-      bool ok = true;
-      for (int item = blockIdx.x; ok && item < p.num_items; item += gridDim.x, ++it) {
-        const int acc = it & 1;
-        const uint32_t acc_par = (it >> 1) & 1;
-        if (!mbar_wait(smem_u32(&acc_empty[acc]), acc_par ^ 1u, p.timeout_ns, abort_flag)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * BN);
-        for (int kb = 0; kb < p.nk; ++kb) {
-          if (!mbar_wait(smem_u32(&full[stage]), phase, p.timeout_ns, abort_flag)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          uint8_t* st = smem + stage * Cfg::kStageBytes;
-          const uint64_t da_hi = make_sdesc_kmajor_sw128(smem_u32(st));
-          const uint64_t da_lo = make_sdesc_kmajor_sw128(smem_u32(st + Cfg::kABytes + Cfg::kBBytes));
-          const uint64_t db_hi = B_MN ? make_sdesc_mnmajor_sw128(smem_u32(st + Cfg::kABytes), 8192, 1024)
-                                      : make_sdesc_kmajor_sw128(smem_u32(st + Cfg::kABytes));
-          const uint64_t db_lo =
-              B_MN ? make_sdesc_mnmajor_sw128(smem_u32(st + 2 * Cfg::kABytes + Cfg::kBBytes), 8192, 1024)
-                   : make_sdesc_kmajor_sw128(smem_u32(st + 2 * Cfg::kABytes + Cfg::kBBytes));
-#pragma unroll
-          for (int kk = 0; kk < kBK / 16; ++kk) {
-            // K-major: 16 elements = 32 bytes inside the swizzle row; MN-major: 16 k-rows =
-            // two 1024-byte atoms.  Descriptor start addresses are encoded >> 4.
-            const uint64_t ka = static_cast<uint64_t>(kk * 2);
-            const uint64_t kb16 = B_MN ? static_cast<uint64_t>(kk * 128) : ka;
-            umma_f16_ss(d_tmem, da_hi + ka, db_hi + kb16, idesc, (kb | kk) != 0 ? 1u : 0u);
-            if (TERMS == 3) {
-              umma_f16_ss(d_tmem, da_hi + ka, db_lo + kb16, idesc, 1u);
-              umma_f16_ss(d_tmem, da_lo + ka, db_hi + kb16, idesc, 1u);
-            }
-          }
-          umma_commit(smem_u32(&empty[stage]));
-          if (++stage == STAGES) {
-            stage = 0;
-            phase ^= 1u;
-          }
-        }
-        if (!ok) break;
-        umma_commit(smem_u32(&acc_full[acc]));
-      }
-      if (!ok) {
+      if (!mma_role<BN, TERMS, STAGES, BF16, B_MN>(p, smem, full, empty, acc_full, acc_empty, tmem_base,
+                                                 abort_flag)) {
         atomicOr(p.err, kErrMmaWait);
         *abort_flag = 1;
-        // give UMMAs already issued time to finish before TMEM is released
-        const uint64_t t0 = globaltimer_ns();
-        while (globaltimer_ns() - t0 < 2000000ull) {
-        }
+        drain_pause(2000000ull);
       }
     }
   } else if (warp >= 4) {
-    // ------------------------------------------------------------ epilogue
-    // Each warp owns TMEM lanes 32q..32q+31 (rows of the tile) and, for the TMA write-back,
-    // two 4 KB staging buffers: a 32 x 32 FP32 block is written there in the 128-byte
-    // swizzled layout and added into every destination block by TMA reductions.
-    const int q = warp & 3;  // TMEM lane quarter this warp may access
-    const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
-    uint8_t* stage_base = smem + Cfg::kEpiOffset + q * 8192;
-    int buf = 0;
-    int it = 0;
-    for (int item = blockIdx.x; item < p.num_items; item += gridDim.x, ++it) {
-      const int acc = it & 1;
-      const uint32_t acc_par = (it >> 1) & 1;
-      if (!mbar_wait(smem_u32(&acc_full[acc]), acc_par, p.timeout_ns, abort_flag)) {
-        if (lane == 0) atomicOr(p.err, kErrEpilogueWait);
-        *abort_flag = 1;
-        break;
-      }
-      tc_fence_after();
-      int r, tm, tn;
-      decode_item(item, p, r, tm, tn);
-      const ProductDests& pd = p.prod[r];
-      const int row0 = tm * kBM + q * 32;
-      const int row = row0 + lane;
-      bool has_sign[2] = {false, false};
-      for (int d = 0; d < pd.count; ++d) has_sign[pd.d[d].coef < 0.f ? 1 : 0] = true;
-#pragma unroll 1
-      for (int c = 0; c < BN; c += 32) {
-        float v[32];
-        tmem_ld_32x32b_x32(tmem_base + lane_off + static_cast<uint32_t>(acc * BN + c), v);
-        if (c + 32 == BN) {
-          // every TMEM read of this accumulator is complete: hand it back to the MMA warp
-          tc_fence_before();
-          mbar_arrive(smem_u32(&acc_empty[acc]));
-        }
-        const int col0 = tn * BN + c;
-        if (p.c_tma) {
-#pragma unroll 1
-          for (int sg = 0; sg < 2; ++sg) {
-            if (!has_sign[sg]) continue;
-            const float cf = sg ? -p.alpha : p.alpha;
-            uint8_t* sb = stage_base + buf * 4096;
-            if (lane == 0) bulk_wait_group_read<1>();  // this buffer's previous reductions read it
-            __syncwarp();
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const float4 val = make_float4(cf * v[4 * j], cf * v[4 * j + 1], cf * v[4 * j + 2],
-                                             cf * v[4 * j + 3]);
-              *reinterpret_cast<float4*>(sb + lane * 128 + ((j ^ (lane & 7)) << 4)) = val;
-            }
-            fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) {
-              for (int d = 0; d < pd.count; ++d) {
-                const DestEntry& de = pd.d[d];
-                if ((de.coef < 0.f ? 1 : 0) != sg) continue;
-                tma_reduce_add_2d(&p.tmC[de.block], smem_u32(sb), col0, row0);
-              }
-              bulk_commit_group();
-            }
-            buf ^= 1;
-          }
-        } else {
-#pragma unroll 1
-          for (int d = 0; d < pd.count; ++d) {
-            const DestEntry de = pd.d[d];
-            if (row >= de.rows || col0 >= de.cols) continue;
-            float* dst = p.C + de.offset + static_cast<int64_t>(row) * p.ldc + col0;
-            const float cf = de.coef;
-            if (p.c_vec4 && col0 + 32 <= de.cols) {
-              float4* d4 = reinterpret_cast<float4*>(dst);
-#pragma unroll
-              for (int j = 0; j < 8; ++j)
-                atomicAdd(d4 + j, make_float4(cf * v[4 * j], cf * v[4 * j + 1], cf * v[4 * j + 2],
-                                              cf * v[4 * j + 3]));
-            } else {
-              const int lim = de.cols - col0;
-#pragma unroll
-              for (int j = 0; j < 32; ++j)
-                if (j < lim) atomicAdd(dst + j, cf * v[j]);
-            }
-          }
-        }
-      }
+    if (!epilogue_role<BN>(p, smem + Cfg::kEpiOffset, acc_full, acc_empty, tmem_base, abort_flag, warp,
+                           lane)) {
+      if (lane == 0) atomicOr(p.err, kErrEpilogueWait);
+      *abort_flag = 1;
     }
-    if (lane == 0) bulk_wait_group<0>();  // reductions complete before the CTA retires
   }
 
   tc_fence_before();

@@ -26,4 +26,8 @@ cudaError_t launch_packed(const PackedParams& p, int tile_n, int terms, bool bf1
                           cudaStream_t s);
 bool packed_config_supported(int tile_n, int terms, bool bf16);
 
+// Tensor-core kernel that forms the operand sums on chip from FP32 source tiles
+// (tile 128 x 128; terms in {1, 3}).
+cudaError_t launch_fused(const FusedParams& p, int terms, int grid, cudaStream_t s);
+
 }  // namespace fmm

@@ -57,7 +57,8 @@ def _to_device(X, ld_pad, dtype):
 
 
 def run(m, n, k, levels, variant="split3", dist="uniform", seed=0, alpha=1.0, beta=0.0,
-        tile_n=0, pads=(0, 0, 0), c_fill=None, rows=None, b_kmajor=0, schedule="auto"):
+        tile_n=0, pads=(0, 0, 0), c_fill=None, rows=None, b_kmajor=0, schedule="auto",
+        algo="auto"):
     A, B = synth.problem(m, n, k, seed, dist)
     in_dtype = torch.bfloat16 if variant == "bf16" else torch.float32
     Ad = _to_device(A, pads[0], in_dtype)
@@ -71,7 +72,7 @@ def run(m, n, k, levels, variant="split3", dist="uniform", seed=0, alpha=1.0, be
         if c_fill is not None:
             Cd.fill_(c_fill)
     fmm.gemm(Ad, Bd, Cd, alpha=alpha, beta=beta, levels=levels, variant=variant, tile_n=tile_n,
-             b_kmajor=b_kmajor, schedule=schedule)
+             b_kmajor=b_kmajor, schedule=schedule, algo=algo)
     fmm.device_status()
     C = Cd.cpu().numpy().astype(np.float64)
     if variant == "bf16":
@@ -135,6 +136,57 @@ def test_int_with_alpha_beta_bit_exact():
     fmm.gemm(Ad, Bd, Cd, alpha=2.0, beta=-3.0, levels=2)
     fmm.device_status()
     np.testing.assert_array_equal(Cd.cpu().numpy(), oracle.classical(A, B, C0, 2.0, -3.0))
+
+
+# ------------------------------------------------- fused (on-chip operand sums)
+def _pad4(c):
+    return (-c) % 4
+
+
+@pytest.mark.parametrize("schedule", ["product", "rounds"])
+@pytest.mark.parametrize("levels", [0, 1, 2])
+@pytest.mark.parametrize("m,n,k", [(16, 16, 16), (300, 520, 200), (129, 257, 65), (1, 300, 1),
+                                   (520, 8, 400), (1000, 1200, 300)])
+def test_fused_int_bit_exact(m, n, k, levels, schedule):
+    C, C64, _, _ = run(m, n, k, levels, "split3", dist="int", seed=m + 2 * n + k, algo="fused",
+                       pads=(_pad4(k), _pad4(n), 0), schedule=schedule)
+    np.testing.assert_array_equal(C, C64)
+
+
+@pytest.mark.parametrize("variant", ["split3", "plain_bf16"])
+@pytest.mark.parametrize("levels", [0, 1, 2])
+@pytest.mark.parametrize("m,n,k", [(7, 13, 5), (257, 129, 1000), (640, 384, 96)])
+def test_fused_float_shapes(m, n, k, levels, variant):
+    C, C64, An, Bn = run(m, n, k, levels, variant, dist="gaussian", seed=m * 3 + n + k,
+                         algo="fused", pads=(_pad4(k), _pad4(n), 0))
+    err = oracle.normwise_error(C, C64, An, Bn)
+    assert err <= tolerance(variant, levels, k), err
+
+
+def test_fused_matches_packed_closely():
+    """Same arithmetic, different place of the sums: results agree to FP32 rounding."""
+    A, B = synth.problem(1024, 768, 896, 41, "uniform")
+    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    for levels in (1, 2):
+        Cp = fmm.gemm(Ad, Bd, levels=levels, algo="packed")
+        Cf = fmm.gemm(Ad, Bd, levels=levels, algo="fused")
+        fmm.device_status()
+        rel = ((Cp - Cf).norm() / Cp.norm()).item()
+        assert rel < 1e-6, rel
+
+
+def test_fused_full_size_sampled_rows():
+    rows = np.unique(synth.rng(5).integers(0, 8192, size=8))
+    C, C64, An, Bn = run(8192, 8192, 8192, 2, "split3", seed=21, rows=rows, algo="fused")
+    assert oracle.normwise_error(C, C64, An, Bn) <= 1e-6
+
+
+def test_fused_rejects_unaligned_leading_dimension():
+    A = torch.zeros((64, 65), device="cuda")
+    B = torch.zeros((65, 64), device="cuda")
+    with pytest.raises(fmm.FmmError) as ei:
+        fmm.gemm(A, B, levels=1, algo="fused")
+    assert ei.value.status == 2
 
 
 # ------------------------------------------------------------------- floats
