@@ -92,13 +92,11 @@ typedef struct fmm_options {
     int algo;       /* fmm_algo; 0 = automatic choice */
     int tile_n;     /* 0 = automatic; otherwise 128 or 256 */
     int num_ctas;   /* 0 = one persistent CTA per SM */
-    int b_kmajor;   /* packed algorithm: 1 stores the B-operand sums transposed (K-major);
-                       0 (default) keeps them row-major and the tensor cores read B MN-major */
     int schedule;   /* order of the (product, tile) work items: 0 = automatic,
                        1 = product-major (all tiles of one product, then the next),
                        2 = tile rounds (each CTA runs all 7^L products of one output tile
                            back to back, so its destination blocks stay in L2) */
-    int reserved[3];
+    int reserved[4];
 } fmm_options;
 
 /* Bytes of workspace fmm_gemm needs for this problem (0 when none).  Returns
@@ -139,6 +137,23 @@ fmm_status fmm_gemm_noalloc(int64_t m, int64_t n, int64_t k, float alpha,
                             const void* A, int64_t lda, const void* B, int64_t ldb,
                             float beta, float* C, int64_t ldc, int levels, int variant,
                             void* stream);
+
+/* Backward of C = A * B for a differentiable linear layer: given dC = dL/dC,
+ *     dA = dC * B^T   (m x k, leading dimension ldda)   and
+ *     dB = A^T * dC   (k x n, leading dimension lddb),
+ * each computed as a `levels`-level Strassen product (Section 3, Eq. 3) on the
+ * transposed views: no transposed copy of A, B or dC is made; the operand sums
+ * take the coefficients of the transposed quadrants and the tensor cores read
+ * the transposed operands in their other major-ness.  A and B have the type the
+ * variant names, dC is float32; dA and dB are float32 and are overwritten (either
+ * may be NULL to skip it).  The two products run one after the other on `stream`
+ * and share the workspace, which must hold fmm_workspace_size_backward() bytes. */
+fmm_status fmm_gemm_backward(int64_t m, int64_t n, int64_t k,
+                             const void* A, int64_t lda, const void* B, int64_t ldb,
+                             const float* dC, int64_t lddc, float* dA, int64_t ldda,
+                             float* dB, int64_t lddb, int levels, int variant,
+                             void* workspace, size_t ws_bytes, void* stream);
+size_t fmm_workspace_size_backward(int64_t m, int64_t n, int64_t k, int levels, int variant);
 
 /* Last error message of the calling host thread ("" when none). */
 const char* fmm_last_error(void);

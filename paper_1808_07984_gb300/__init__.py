@@ -33,7 +33,7 @@ class FmmError(RuntimeError):
 
 class _Options(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int), ("tile_n", ctypes.c_int), ("num_ctas", ctypes.c_int),
-                ("b_kmajor", ctypes.c_int), ("schedule", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("schedule", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 _lib = None
@@ -66,6 +66,11 @@ def load() -> ctypes.CDLL:
     L.fmm_gemm.argtypes = gemm_args
     L.fmm_gemm_ex.restype = i32
     L.fmm_gemm_ex.argtypes = gemm_args + [ctypes.POINTER(_Options)]
+    L.fmm_gemm_backward.restype = i32
+    L.fmm_gemm_backward.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64,
+                                    i32, i32, vp, sz, vp]
+    L.fmm_workspace_size_backward.restype = sz
+    L.fmm_workspace_size_backward.argtypes = [i64, i64, i64, i32, i32]
     L.fmm_last_error.restype = ctypes.c_char_p
     L.fmm_last_error.argtypes = []
     L.fmm_device_status.restype = i32
@@ -94,13 +99,12 @@ def _check(status: int):
 SCHEDULES = {"auto": 0, "product": 1, "rounds": 2}
 
 
-def _opts(algo="auto", tile_n=0, num_ctas=0, b_kmajor=0, schedule="auto"):
+def _opts(algo="auto", tile_n=0, num_ctas=0, schedule="auto"):
     o = _Options()
     o.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
     o.algo = ALGOS[algo] if isinstance(algo, str) else int(algo)
     o.tile_n = int(tile_n)
     o.num_ctas = int(num_ctas)
-    o.b_kmajor = int(b_kmajor)
     return o
 
 
@@ -108,8 +112,8 @@ def _variant(v) -> int:
     return VARIANTS[v] if isinstance(v, str) else int(v)
 
 
-def workspace_size(m, n, k, levels=1, variant="split3", algo="auto", tile_n=0, b_kmajor=0) -> int:
-    o = _opts(algo, tile_n, 0, b_kmajor)
+def workspace_size(m, n, k, levels=1, variant="split3", algo="auto", tile_n=0) -> int:
+    o = _opts(algo, tile_n)
     ws = load().fmm_workspace_size_ex(m, n, k, levels, _variant(variant), ctypes.byref(o))
     if ws == ctypes.c_size_t(-1).value:
         raise FmmError(3, "unsupported combination")
@@ -128,7 +132,7 @@ _IN_DTYPE = {0: "float32", 1: "bfloat16", 2: "float16", 3: "float32"}
 
 def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
          variant="split3", algo="auto", tile_n: int = 0, num_ctas: int = 0,
-         workspace=None, stream=None, b_kmajor: int = 0, schedule="auto"):
+         workspace=None, stream=None, schedule="auto"):
     """C = alpha * A @ B + beta * C on the current CUDA device (torch tensors).
 
     A (m x k) and B (k x n) are row-major CUDA tensors of the element type the
@@ -156,18 +160,96 @@ def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
         beta = 0.0
     if C.dtype != torch.float32 or not C.is_cuda or (C.numel() and C.stride(1) != 1):
         raise FmmError(1, "C must be a float32 CUDA tensor with contiguous rows")
-    ws_need = workspace_size(m, n, k, levels, v, algo, tile_n, b_kmajor)
+    ws_need = workspace_size(m, n, k, levels, v, algo, tile_n)
     if workspace is None and ws_need > 0:
         workspace = torch.empty(ws_need, dtype=torch.uint8, device=A.device)
     ws_ptr = workspace.data_ptr() if workspace is not None else None
     ws_bytes = workspace.numel() if workspace is not None else 0
-    o = _opts(algo, tile_n, num_ctas, b_kmajor, schedule)
+    o = _opts(algo, tile_n, num_ctas, schedule)
     st = load().fmm_gemm_ex(m, n, k, float(alpha), A.data_ptr(), max(A.stride(0), 1),
                             B.data_ptr(), max(B.stride(0), 1), float(beta), C.data_ptr(),
                             max(C.stride(0), 1), int(levels), v, ws_ptr, ws_bytes,
                             _stream_handle(stream), ctypes.byref(o))
     _check(st)
     return C
+
+
+def workspace_size_backward(m, n, k, levels=1, variant="split3") -> int:
+    ws = load().fmm_workspace_size_backward(m, n, k, levels, _variant(variant))
+    if ws == ctypes.c_size_t(-1).value:
+        raise FmmError(3, "unsupported combination")
+    return int(ws)
+
+
+def gemm_backward(A, B, dC, levels: int = 1, variant="split3", need_dA=True, need_dB=True,
+                  workspace=None, stream=None):
+    """(dA, dB) = (dC @ B.T, A.T @ dC) as Strassen products through fmm_gemm_backward.
+
+    A (m x k) and B (k x n) have the variant's element type, dC (m x n) is float32; the
+    gradients are float32 (None where not requested)."""
+    import torch
+    v = _variant(variant)
+    m, k = A.shape
+    k2, n = B.shape
+    if k != k2 or tuple(dC.shape) != (m, n):
+        raise FmmError(1, "shape mismatch")
+    want = getattr(torch, _IN_DTYPE[v])
+    for name, X in (("A", A), ("B", B)):
+        if X.dtype != want or not X.is_cuda or (X.numel() and X.stride(1) != 1):
+            raise FmmError(1, f"{name} must be a {want} CUDA tensor with contiguous rows")
+    if dC.dtype != torch.float32 or not dC.is_cuda or (dC.numel() and dC.stride(1) != 1):
+        raise FmmError(1, "dC must be a float32 CUDA tensor with contiguous rows")
+    dA = torch.empty((m, k), dtype=torch.float32, device=A.device) if need_dA else None
+    dB = torch.empty((k, n), dtype=torch.float32, device=A.device) if need_dB else None
+    ws_need = workspace_size_backward(m, n, k, levels, v)
+    if workspace is None and ws_need > 0:
+        workspace = torch.empty(ws_need, dtype=torch.uint8, device=A.device)
+    st = load().fmm_gemm_backward(
+        m, n, k, A.data_ptr(), max(A.stride(0), 1), B.data_ptr(), max(B.stride(0), 1),
+        dC.data_ptr(), max(dC.stride(0), 1),
+        dA.data_ptr() if dA is not None else None, max(k, 1),
+        dB.data_ptr() if dB is not None else None, max(n, 1),
+        int(levels), v, workspace.data_ptr() if workspace is not None else None,
+        workspace.numel() if workspace is not None else 0, _stream_handle(stream))
+    _check(st)
+    return dA, dB
+
+
+def _make_linear_fn():
+    import torch
+
+    class FmmLinearFn(torch.autograd.Function):
+        """C = A @ B with a hand-written backward dA = dC @ B^T, dB = A^T @ dC, all three
+        computed as Strassen products by the library (no autograd through torch ops)."""
+
+        @staticmethod
+        def forward(ctx, A, B, levels=1, variant="split3"):
+            ctx.save_for_backward(A, B)
+            ctx.levels = levels
+            ctx.variant = variant
+            return gemm(A, B, levels=levels, variant=variant)
+
+        @staticmethod
+        def backward(ctx, dC):
+            A, B = ctx.saved_tensors
+            dA, dB = gemm_backward(A, B, dC.contiguous().float(), levels=ctx.levels,
+                                   variant=ctx.variant, need_dA=ctx.needs_input_grad[0],
+                                   need_dB=ctx.needs_input_grad[1])
+            # FP32 gradients; autograd casts them to the inputs' dtype where that differs
+            return dA, dB, None, None
+
+    return FmmLinearFn
+
+
+_linear_fn = None
+
+
+def linear(A, B, levels: int = 1, variant="split3"):
+    """Differentiable C = A @ B (torch.autograd) backed by the Strassen library."""
+    global _linear_fn
+    if _linear_fn is None:
+        _linear_fn = _make_linear_fn()
+    return _linear_fn.apply(A, B, levels, variant)
 
 
 def device_status(stream=None):

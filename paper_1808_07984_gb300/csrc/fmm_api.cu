@@ -174,23 +174,28 @@ int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 struct Plan {
   int L = 0, R = 1, terms = 3, in_type = kInF32;
   bool bf16 = true;
-  bool b_mn = true;  // B-operand sums row-major (k x n), read MN-major by the tensor cores
-  int schedule = kSchedProductMajor;
+  // Operand layouts of the GEMM C (M x N) = A' (M x K) B' (K x N):
+  //   A' K-major: source stored M rows x K cols;  A' MN-major (a_mn): stored K rows x M cols;
+  //   B' MN-major (b_mn): stored K rows x N cols; B' K-major: stored N rows x K cols.
+  bool a_mn = false, b_mn = true;
   int tile_n = 128;
   int algo = FMM_ALGO_PACKED;
+  int schedule = kSchedProductMajor;
   int64_t hm = 0, hn = 0, hk = 0;
-  int64_t lda_w = 0;  // row stride of the A-operand sums (h_k rounded up to 8)
-  int64_t ldb_w = 0;  // row stride of the B-operand sums (h_n or, K-major, h_k, rounded up to 8)
+  int64_t lda_w = 0;  // row stride of the stored A-operand sums (rounded up to 8)
+  int64_t ldb_w = 0;  // row stride of the stored B-operand sums
   size_t a_bytes = 0, b_bytes = 0;  // per term array
   size_t ws = 0;
 };
 
 fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, const fmm_options* opt,
-                     Plan& pl) {
+                     bool a_mn, bool b_mn, Plan& pl) {
   if (m < 0 || n < 0 || k < 0) return fail(FMM_ERR_ARG, "negative dimension");
   if (levels < 0 || levels > 2) return fail(FMM_ERR_UNSUPPORTED, "levels must be 0, 1 or 2");
   pl.L = levels;
   pl.R = ipow(7, levels);
+  pl.a_mn = a_mn;
+  pl.b_mn = b_mn;
   switch (variant) {
     case FMM_F32_SPLIT3_BF16: pl.terms = 3; pl.in_type = kInF32; pl.bf16 = true; break;
     case FMM_F32_PLAIN_BF16: pl.terms = 1; pl.in_type = kInF32; pl.bf16 = true; break;
@@ -201,22 +206,21 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
   if (algo != FMM_ALGO_AUTO && algo != FMM_ALGO_PACKED && algo != FMM_ALGO_FUSED)
     return fail(FMM_ERR_UNSUPPORTED, "algorithm not built");
   pl.algo = algo == FMM_ALGO_FUSED ? FMM_ALGO_FUSED : FMM_ALGO_PACKED;
-  if (pl.algo == FMM_ALGO_FUSED && pl.in_type != kInF32)
-    return fail(FMM_ERR_UNSUPPORTED, "the fused algorithm takes FP32 A and B (split3 or plain_bf16)");
+  if (pl.algo == FMM_ALGO_FUSED && (pl.in_type != kInF32 || a_mn || !b_mn))
+    return fail(FMM_ERR_UNSUPPORTED, "the fused algorithm takes FP32 A and B (split3 or plain_bf16) in the forward product");
   pl.tile_n = (opt && opt->tile_n) ? opt->tile_n : 0;
   if (pl.algo == FMM_ALGO_FUSED) {
     if (pl.tile_n != 0 && pl.tile_n != kFusedTileN)
       return fail(FMM_ERR_UNSUPPORTED, "the fused algorithm uses 128-wide tiles");
     pl.tile_n = kFusedTileN;
   }
-  pl.b_mn = !(opt && opt->b_kmajor);
   const int sched = opt ? opt->schedule : 0;
   if (sched < 0 || sched > 2) return fail(FMM_ERR_ARG, "schedule must be 0, 1 or 2");
-  // automatic choice (measured on GB300): tile rounds keep each tile's destination blocks in
-  // L2 and are never slower by more than 1 %, product-major order only for long products
   pl.hm = block_size(m, levels);
   pl.hn = block_size(n, levels);
   pl.hk = block_size(k, levels);
+  // automatic choice (measured on GB300): tile rounds keep each tile's destination blocks in
+  // L2 and are never slower by more than 1 %; product-major order only for long products
   if (sched == 0)
     pl.schedule = (levels == 2 && pl.hk >= 4096) ? kSchedProductMajor : kSchedTileRounds;
   else
@@ -229,17 +233,25 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
   }
   if (!packed_config_supported(pl.tile_n, pl.terms, pl.bf16))
     return fail(FMM_ERR_UNSUPPORTED, "tile_n must be 128 or 256");
-  pl.lda_w = round_up(std::max<int64_t>(pl.hk, 1), 8);
-  pl.ldb_w = pl.b_mn ? round_up(std::max<int64_t>(pl.hn, 1), 8) : pl.lda_w;
   if (pl.hm >= (int64_t(1) << 31) || pl.hn >= (int64_t(1) << 31) || pl.hk >= (int64_t(1) << 31))
     return fail(FMM_ERR_ARG, "dimension too large");
-  pl.a_bytes = static_cast<size_t>(round_up(static_cast<int64_t>(pl.R) * pl.hm * pl.lda_w * 2, 256));
-  pl.b_bytes = static_cast<size_t>(
-      round_up(static_cast<int64_t>(pl.R) * (pl.b_mn ? pl.hk : pl.hn) * pl.ldb_w * 2, 256));
+  const int64_t a_rows = a_mn ? pl.hk : pl.hm;
+  pl.lda_w = round_up(std::max<int64_t>(a_mn ? pl.hm : pl.hk, 1), 8);
+  const int64_t b_rows = b_mn ? pl.hk : pl.hn;
+  pl.ldb_w = round_up(std::max<int64_t>(b_mn ? pl.hn : pl.hk, 1), 8);
+  pl.a_bytes = static_cast<size_t>(round_up(static_cast<int64_t>(pl.R) * a_rows * pl.lda_w * 2, 256));
+  pl.b_bytes = static_cast<size_t>(round_up(static_cast<int64_t>(pl.R) * b_rows * pl.ldb_w * 2, 256));
   const size_t arrays = pl.terms == 3 ? 2 : 1;
   pl.ws = (m == 0 || n == 0 || k == 0 || pl.algo == FMM_ALGO_FUSED) ? 0 : arrays * (pl.a_bytes + pl.b_bytes);
   return FMM_OK;
 }
+
+// One GEMM operand as the caller stores it (row-major, leading dimension ld, element type).
+struct Operand {
+  const void* X;
+  int64_t ld;
+  int type;
+};
 
 bool overlaps(const void* a, size_t abytes, const void* b, size_t bbytes) {
   if (!a || !b || abytes == 0 || bbytes == 0) return false;
@@ -405,25 +417,25 @@ fmm_status gemm_fused(const Plan& pl, int64_t m, int64_t n, int64_t k, float alp
 }
 
 
-fmm_status gemm_impl(int64_t m, int64_t n, int64_t k, float alpha, const void* A, int64_t lda,
-                     const void* B, int64_t ldb, float beta, float* C, int64_t ldc, int levels,
-                     int variant, void* ws, size_t ws_bytes, void* stream, const fmm_options* opt) {
-  g_last_error.clear();
-  Plan pl;
-  fmm_status st = make_plan(m, n, k, levels, variant, opt, pl);
-  if (st != FMM_OK) return st;
-  if (lda < std::max<int64_t>(1, k) || ldb < std::max<int64_t>(1, n) || ldc < std::max<int64_t>(1, n))
+// C (m x n) = alpha * A' B' + beta * C with the operand layouts of `pl`.  `a` stores A' as
+// m x k (K-major) or k x m (pl.a_mn); `b` stores B' as k x n (pl.b_mn) or n x k.
+fmm_status gemm_core(const Plan& pl, int64_t m, int64_t n, int64_t k, float alpha, Operand a,
+                     Operand b, float beta, float* C, int64_t ldc, void* ws, size_t ws_bytes,
+                     void* stream, const fmm_options* opt) {
+  const int64_t a_rows = pl.a_mn ? k : m, a_cols = pl.a_mn ? m : k;
+  const int64_t b_rows = pl.b_mn ? k : n, b_cols = pl.b_mn ? n : k;
+  if (a.ld < std::max<int64_t>(1, a_cols) || b.ld < std::max<int64_t>(1, b_cols) ||
+      ldc < std::max<int64_t>(1, n))
     return fail(FMM_ERR_ARG, "leading dimension smaller than the row length");
   if (m == 0 || n == 0) return FMM_OK;
   if (!C) return fail(FMM_ERR_ARG, "C is NULL");
-  if (k > 0 && (!A || !B)) return fail(FMM_ERR_ARG, "A or B is NULL");
-  const size_t eb = elem_bytes(pl.in_type);
+  if (k > 0 && (!a.X || !b.X)) return fail(FMM_ERR_ARG, "an input operand is NULL");
   const size_t c_bytes = static_cast<size_t>(((m - 1) * ldc + n) * 4);
   if (k > 0) {
-    const size_t a_span = static_cast<size_t>(((m - 1) * lda + k) * eb);
-    const size_t b_span = static_cast<size_t>(((k - 1) * ldb + n) * eb);
-    if (overlaps(C, c_bytes, A, a_span) || overlaps(C, c_bytes, B, b_span))
-      return fail(FMM_ERR_ARG, "C overlaps A or B");
+    const size_t a_span = static_cast<size_t>(((a_rows - 1) * a.ld + a_cols) * elem_bytes(a.type));
+    const size_t b_span = static_cast<size_t>(((b_rows - 1) * b.ld + b_cols) * elem_bytes(b.type));
+    if (overlaps(C, c_bytes, a.X, a_span) || overlaps(C, c_bytes, b.X, b_span))
+      return fail(FMM_ERR_ARG, "C overlaps an input operand");
   }
   if (pl.ws > 0) {
     if (!ws || ws_bytes < pl.ws)
@@ -432,11 +444,11 @@ fmm_status gemm_impl(int64_t m, int64_t n, int64_t k, float alpha, const void* A
     if (overlaps(C, c_bytes, ws, pl.ws)) return fail(FMM_ERR_ARG, "C overlaps the workspace");
   }
   if (pl.algo == FMM_ALGO_FUSED && k > 0 &&
-      (reinterpret_cast<uintptr_t>(A) % 16 != 0 || reinterpret_cast<uintptr_t>(B) % 16 != 0 ||
-       lda % 4 != 0 || ldb % 4 != 0))
+      (reinterpret_cast<uintptr_t>(a.X) % 16 != 0 || reinterpret_cast<uintptr_t>(b.X) % 16 != 0 ||
+       a.ld % 4 != 0 || b.ld % 4 != 0))
     return fail(FMM_ERR_ALIGN, "the fused algorithm needs 16-byte aligned A and B and lda, ldb multiples of 4");
   DeviceInfo dev;
-  st = device_info(dev);
+  fmm_status st = device_info(dev);
   if (st != FMM_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
@@ -447,81 +459,52 @@ fmm_status gemm_impl(int64_t m, int64_t n, int64_t k, float alpha, const void* A
     if (e != cudaSuccess) return cuda_fail(e, "beta pass");
   }
   if (k == 0 || alpha == 0.0f) return FMM_OK;
-  if (pl.algo == FMM_ALGO_FUSED) return gemm_fused(pl, m, n, k, alpha, A, lda, B, ldb, C, ldc, dev, opt, s);
+  if (pl.algo == FMM_ALGO_FUSED) return gemm_fused(pl, m, n, k, alpha, a.X, a.ld, b.X, b.ld, C, ldc, dev, opt, s);
 
   const std::vector<Product> prods = make_products(pl.L);
-  const int g = 1 << pl.L;
   uint8_t* wsb = static_cast<uint8_t*>(ws);
   uint16_t* a_hi = reinterpret_cast<uint16_t*>(wsb);
   uint16_t* b_hi = reinterpret_cast<uint16_t*>(wsb + pl.a_bytes);
   uint16_t* a_lo = pl.terms == 3 ? reinterpret_cast<uint16_t*>(wsb + pl.a_bytes + pl.b_bytes) : nullptr;
   uint16_t* b_lo = pl.terms == 3 ? reinterpret_cast<uint16_t*>(wsb + 2 * pl.a_bytes + pl.b_bytes) : nullptr;
 
-  // ---- operand-sum passes (all 7^L A-operands, then all B-operands)
+  // ---- operand-sum passes (all 7^L A-operands, then all B-operands), in the stored layout
   {
     SumParams sa;
     std::memset(&sa, 0, sizeof sa);
-    sa.X = A;
-    sa.ldx = lda;
-    sa.rows = m;
-    sa.cols = k;
-    sa.hr = pl.hm;
-    sa.hc = pl.hk;
+    sa.X = a.X;
+    sa.ldx = a.ld;
+    sa.rows = a_rows;
+    sa.cols = a_cols;
+    sa.hr = pl.a_mn ? pl.hk : pl.hm;
+    sa.hc = pl.a_mn ? pl.hm : pl.hk;
     sa.ld_out = pl.lda_w;
-    sa.prod_stride = pl.hm * pl.lda_w;
+    sa.prod_stride = sa.hr * pl.lda_w;
     sa.out_hi = a_hi;
     sa.out_lo = a_lo;
     sa.terms = pl.terms;
-    sa.vec_ok = (reinterpret_cast<uintptr_t>(A) % 16 == 0 && lda % 4 == 0) ? 1 : 0;
+    sa.vec_ok = (reinterpret_cast<uintptr_t>(a.X) % 16 == 0 && a.ld % 4 == 0) ? 1 : 0;
     cudaError_t e;
     {
       PhaseScope ps(kPhasePack, s);
-      e = launch_operand_sums(sa, pl.L, false, pl.in_type, pl.bf16 ? 0 : 1, dev.sms, s);
+      e = launch_operand_sums(sa, pl.L, false, pl.a_mn, a.type, pl.bf16 ? 0 : 1, dev.sms, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "operand-sum pass (A)");
-    if (pl.b_mn) {
-      SumParams sb = sa;
-      sb.X = B;
-      sb.ldx = ldb;
-      sb.rows = k;
-      sb.cols = n;
-      sb.hr = pl.hk;
-      sb.hc = pl.hn;
-      sb.ld_out = pl.ldb_w;
-      sb.prod_stride = pl.hk * pl.ldb_w;
-      sb.out_hi = b_hi;
-      sb.out_lo = b_lo;
-      sb.vec_ok = (reinterpret_cast<uintptr_t>(B) % 16 == 0 && ldb % 4 == 0) ? 1 : 0;
-      {
-        PhaseScope ps(kPhasePack, s);
-        e = launch_operand_sums(sb, pl.L, true, pl.in_type, pl.bf16 ? 0 : 1, dev.sms, s);
-      }
-    } else {
-      PackParams pb;
-      std::memset(&pb, 0, sizeof pb);
-      pb.X = B;
-      pb.ldx = ldb;
-      pb.rows = k;
-      pb.cols = n;
-      pb.hr = static_cast<int32_t>(pl.hk);
-      pb.hc = static_cast<int32_t>(pl.hn);
-      pb.gdim = g;
-      pb.nsrc = g * g;
-      pb.nprod = pl.R;
-      pb.terms = pl.terms;
-      pb.ld_out = pl.ldb_w;
-      pb.prod_stride = pl.hn * pl.ldb_w;
-      pb.out_hi = b_hi;
-      pb.out_lo = b_lo;
-      for (int r = 0; r < pl.R; ++r) {
-        pb.cnt[r] = static_cast<int8_t>(prods[r].b.size());
-        for (size_t t = 0; t < prods[r].b.size(); ++t)
-          pb.term[r][t] = {static_cast<int16_t>(prods[r].b[t].block), static_cast<int16_t>(prods[r].b[t].sign)};
-      }
-      {
-        PhaseScope ps(kPhasePack, s);
-        e = launch_pack(pb, pl.in_type, pl.bf16 ? 0 : 1, true, dev.sms, s);
-      }
+    SumParams sb = sa;
+    sb.X = b.X;
+    sb.ldx = b.ld;
+    sb.rows = b_rows;
+    sb.cols = b_cols;
+    sb.hr = pl.b_mn ? pl.hk : pl.hn;
+    sb.hc = pl.b_mn ? pl.hn : pl.hk;
+    sb.ld_out = pl.ldb_w;
+    sb.prod_stride = sb.hr * pl.ldb_w;
+    sb.out_hi = b_hi;
+    sb.out_lo = b_lo;
+    sb.vec_ok = (reinterpret_cast<uintptr_t>(b.X) % 16 == 0 && b.ld % 4 == 0) ? 1 : 0;
+    {
+      PhaseScope ps(kPhasePack, s);
+      e = launch_operand_sums(sb, pl.L, true, !pl.b_mn, b.type, pl.bf16 ? 0 : 1, dev.sms, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "operand-sum pass (B)");
   }
@@ -531,7 +514,10 @@ fmm_status gemm_impl(int64_t m, int64_t n, int64_t k, float alpha, const void* A
   std::memset(pp, 0, sizeof(PackedParams));
   const int nb = pl.terms == 3 ? 2 : 1;
   for (int t = 0; t < nb && st == FMM_OK; ++t) {
-    st = encode_3d(&pp->tmA[t], t ? a_lo : a_hi, pl.hk, pl.hm, pl.R, pl.lda_w, kBK, kBM);
+    if (pl.a_mn)
+      st = encode_3d(&pp->tmA[t], t ? a_lo : a_hi, pl.hm, pl.hk, pl.R, pl.lda_w, 64, kBK);
+    else
+      st = encode_3d(&pp->tmA[t], t ? a_lo : a_hi, pl.hk, pl.hm, pl.R, pl.lda_w, kBK, kBM);
     if (st != FMM_OK) break;
     if (pl.b_mn)
       st = encode_3d(&pp->tmB[t], t ? b_lo : b_hi, pl.hn, pl.hk, pl.R, pl.ldb_w, 64, kBK);
@@ -549,7 +535,7 @@ fmm_status gemm_impl(int64_t m, int64_t n, int64_t k, float alpha, const void* A
   cudaError_t e;
   {
     PhaseScope ps(kPhaseTensor, s);
-    e = launch_packed(*pp, pl.tile_n, pl.terms, pl.bf16, pl.b_mn, grid, s);
+    e = launch_packed(*pp, pl.tile_n, pl.terms, pl.bf16, pl.a_mn, pl.b_mn, grid, s);
   }
   delete pp;
   if (e != cudaSuccess) return cuda_fail(e, "tensor-core pass");
@@ -569,7 +555,7 @@ extern "C" {
 size_t fmm_workspace_size_ex(int64_t m, int64_t n, int64_t k, int levels, int variant,
                              const fmm_options* opt) {
   Plan pl;
-  if (make_plan(m, n, k, levels, variant, opt, pl) != FMM_OK) return static_cast<size_t>(-1);
+  if (make_plan(m, n, k, levels, variant, opt, false, true, pl) != FMM_OK) return static_cast<size_t>(-1);
   return pl.ws;
 }
 
@@ -581,15 +567,55 @@ fmm_status fmm_gemm_ex(int64_t m, int64_t n, int64_t k, float alpha, const void*
                        const void* B, int64_t ldb, float beta, float* C, int64_t ldc, int levels,
                        int variant, void* workspace, size_t ws_bytes, void* stream,
                        const fmm_options* opt) {
-  return gemm_impl(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, levels, variant, workspace,
-                   ws_bytes, stream, opt);
+  g_last_error.clear();
+  Plan pl;
+  fmm_status st = make_plan(m, n, k, levels, variant, opt, false, true, pl);
+  if (st != FMM_OK) return st;
+  return gemm_core(pl, m, n, k, alpha, Operand{A, lda, pl.in_type}, Operand{B, ldb, pl.in_type}, beta, C,
+                   ldc, workspace, ws_bytes, stream, opt);
 }
 
 fmm_status fmm_gemm(int64_t m, int64_t n, int64_t k, float alpha, const void* A, int64_t lda,
                     const void* B, int64_t ldb, float beta, float* C, int64_t ldc, int levels,
                     int variant, void* workspace, size_t ws_bytes, void* stream) {
-  return gemm_impl(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, levels, variant, workspace,
-                   ws_bytes, stream, nullptr);
+  return fmm_gemm_ex(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, levels, variant, workspace,
+                     ws_bytes, stream, nullptr);
+}
+
+size_t fmm_workspace_size_backward(int64_t m, int64_t n, int64_t k, int levels, int variant) {
+  Plan pa, pb;
+  if (make_plan(m, k, n, levels, variant, nullptr, false, false, pa) != FMM_OK ||
+      make_plan(k, n, m, levels, variant, nullptr, true, true, pb) != FMM_OK)
+    return static_cast<size_t>(-1);
+  return std::max(pa.ws, pb.ws);
+}
+
+fmm_status fmm_gemm_backward(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda,
+                             const void* B, int64_t ldb, const float* dC, int64_t lddc, float* dA,
+                             int64_t ldda, float* dB, int64_t lddb, int levels, int variant,
+                             void* workspace, size_t ws_bytes, void* stream) {
+  g_last_error.clear();
+  // dA (m x k) = dC (m x n) B^T: A' = dC stored m x n (K-major), B' = B^T stored as B, k x n
+  // (K-major, quadrants transposed).
+  if (dA) {
+    Plan pl;
+    fmm_status st = make_plan(m, k, n, levels, variant, nullptr, false, false, pl);
+    if (st != FMM_OK) return st;
+    st = gemm_core(pl, m, k, n, 1.0f, Operand{dC, lddc, kInF32}, Operand{B, ldb, pl.in_type}, 0.0f, dA,
+                   ldda, workspace, ws_bytes, stream, nullptr);
+    if (st != FMM_OK) return st;
+  }
+  // dB (k x n) = A^T dC: A' = A^T stored as A, m x k (MN-major, quadrants transposed),
+  // B' = dC stored m x n (MN-major).
+  if (dB) {
+    Plan pl;
+    fmm_status st = make_plan(k, n, m, levels, variant, nullptr, true, true, pl);
+    if (st != FMM_OK) return st;
+    st = gemm_core(pl, k, n, m, 1.0f, Operand{A, lda, pl.in_type}, Operand{dC, lddc, kInF32}, 0.0f, dB,
+                   lddb, workspace, ws_bytes, stream, nullptr);
+    if (st != FMM_OK) return st;
+  }
+  return FMM_OK;
 }
 
 const char* fmm_last_error(void) { return g_last_error.c_str(); }

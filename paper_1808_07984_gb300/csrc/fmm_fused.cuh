@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fmm_fused_kernel(const __gri
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      if (!mma_role<kFusedBN, TERMS, S, true, true>(p, smem, op_full, op_empty, acc_full, acc_empty,
+      if (!mma_role<kFusedBN, TERMS, S, true, false, true>(p, smem, op_full, op_empty, acc_full, acc_empty,
                                                     tmem_base, abort_flag)) {
         atomicOr(p.err, kErrMmaWait);
         *abort_flag = 1;

@@ -103,8 +103,8 @@ struct CommonParams {
 
 // Kernel parameters of the packed-operand path (operand sums already formed).
 struct PackedParams {
-  CUtensorMap tmA[2];  // A-operand sums, hi / lo: 3-D {k, row, product}, 16-bit
-  CUtensorMap tmB[2];  // B-operand sums, hi / lo: 3-D {n, k, product} (or {k, n, product})
+  CUtensorMap tmA[2];  // A-operand sums, hi / lo: 3-D {k, m, product} (MN-major: {m, k, product})
+  CUtensorMap tmB[2];  // B-operand sums, hi / lo: 3-D {n, k, product} (K-major: {k, n, product})
   CommonParams c;
 };
 
@@ -122,30 +122,6 @@ struct FusedParams {
   CUtensorMap tmSB[kMaxSources];  // FP32 blocks of B: 2-D {n, k}, box 128 x 32, no swizzle
   ProductSrc src[kMaxProducts];
   CommonParams c;
-};
-
-// One signed source block of an operand sum.
-struct SrcTerm {
-  int16_t src;   // block index bi * 2^L + bj in the 2^L x 2^L grid
-  int16_t sign;  // +1 / -1
-};
-
-// Parameters of the operand-sum pass (forms all 7^L operand sums of A or B).
-struct PackParams {
-  const void* X;       // source matrix, row-major
-  int64_t ldx;
-  int64_t rows, cols;  // extent of X
-  int32_t hr, hc;      // block size along rows / cols of X
-  int32_t gdim;        // 2^L
-  int32_t nsrc;        // 4^L
-  int32_t nprod;       // 7^L
-  int32_t terms;       // 3: split hi/lo, 1: single rounding
-  int64_t ld_out;      // row stride of the output (elements)
-  int64_t prod_stride; // elements between consecutive products in the output
-  uint16_t* out_hi;
-  uint16_t* out_lo;
-  int8_t cnt[kMaxProducts];
-  SrcTerm term[kMaxProducts][kMaxDest];
 };
 
 // Parameters of the operand-sum pass over one operand (A or B), row-major in and out.
@@ -206,8 +182,9 @@ __device__ __forceinline__ void decode_item(int item, const CommonParams& p, int
 }
 
 
-// Byte layout of one operand stage (both kernels): [A hi | B hi | A lo | B lo], A tile
-// 128 x 64 K-major, B tile 64 (k) x BN MN-major (or BN x 64 K-major), 128-byte swizzle.
+// Byte layout of one operand stage (both kernels): [A hi | B hi | A lo | B lo].  A tile:
+// 128 (m) x 64 (k) K-major, or (MN-major) two 64 (m) x 64 (k) boxes; B tile: 64 (k) x BN
+// MN-major as BN/64 boxes of 64 (n) x 64 (k), or BN x 64 K-major; 128-byte swizzle.
 template <int BN, int TERMS>
 struct StageLayout {
   static constexpr uint32_t kABytes = kBM * kBK * 2;
@@ -223,12 +200,12 @@ constexpr uint32_t kEpiBytes = 4 * 2 * 4096;  // epilogue staging: 4 warps x 2 x
 // Single thread.  For each item: wait for a free accumulator, then for each k-step wait for
 // the operand stage, issue 4 k16 slices x (1 or 3) UMMAs, and release the stage; finally
 // signal the epilogue.  Returns false if a wait gave up.
-template <int BN, int TERMS, int STAGES, bool BF16, bool B_MN>
+template <int BN, int TERMS, int STAGES, bool BF16, bool A_MN, bool B_MN>
 __device__ __forceinline__ bool mma_role(const CommonParams& p, uint8_t* smem, uint64_t* full,
                                          uint64_t* empty, uint64_t* acc_full, uint64_t* acc_empty,
                                          uint32_t tmem_base, volatile int* abort_flag) {
   using SL = StageLayout<BN, TERMS>;
-  constexpr uint32_t idesc = make_idesc_f16(kBM, BN, BF16, B_MN);
+  constexpr uint32_t idesc = make_idesc_f16(kBM, BN, BF16, A_MN, B_MN);
   int stage = 0;
   uint32_t phase = 0;
   int it = 0;
@@ -242,8 +219,10 @@ __device__ __forceinline__ bool mma_role(const CommonParams& p, uint8_t* smem, u
       if (!mbar_wait(smem_u32(&full[stage]), phase, p.timeout_ns, abort_flag)) return false;
       tc_fence_after();
       uint8_t* st = smem + stage * SL::kBytes;
-      const uint64_t da_hi = make_sdesc_kmajor_sw128(smem_u32(st + SL::kAHi));
-      const uint64_t da_lo = make_sdesc_kmajor_sw128(smem_u32(st + SL::kALo));
+      const uint64_t da_hi = A_MN ? make_sdesc_mnmajor_sw128(smem_u32(st + SL::kAHi), 8192, 1024)
+                                  : make_sdesc_kmajor_sw128(smem_u32(st + SL::kAHi));
+      const uint64_t da_lo = A_MN ? make_sdesc_mnmajor_sw128(smem_u32(st + SL::kALo), 8192, 1024)
+                                  : make_sdesc_kmajor_sw128(smem_u32(st + SL::kALo));
       const uint64_t db_hi = B_MN ? make_sdesc_mnmajor_sw128(smem_u32(st + SL::kBHi), 8192, 1024)
                                   : make_sdesc_kmajor_sw128(smem_u32(st + SL::kBHi));
       const uint64_t db_lo = B_MN ? make_sdesc_mnmajor_sw128(smem_u32(st + SL::kBLo), 8192, 1024)
@@ -252,8 +231,8 @@ __device__ __forceinline__ bool mma_role(const CommonParams& p, uint8_t* smem, u
       for (int kk = 0; kk < kBK / 16; ++kk) {
         // K-major: 16 elements = 32 bytes inside the swizzle row; MN-major: 16 k-rows = two
         // 1024-byte atoms.  Descriptor start addresses are encoded >> 4.
-        const uint64_t ka = static_cast<uint64_t>(kk * 2);
-        const uint64_t kb16 = B_MN ? static_cast<uint64_t>(kk * 128) : ka;
+        const uint64_t ka = A_MN ? static_cast<uint64_t>(kk * 128) : static_cast<uint64_t>(kk * 2);
+        const uint64_t kb16 = B_MN ? static_cast<uint64_t>(kk * 128) : static_cast<uint64_t>(kk * 2);
         umma_f16_ss(d_tmem, da_hi + ka, db_hi + kb16, idesc, (kb | kk) != 0 ? 1u : 0u);
         if (TERMS == 3) {
           umma_f16_ss(d_tmem, da_hi + ka, db_lo + kb16, idesc, 1u);
@@ -383,7 +362,7 @@ struct PackedCfg {
   static constexpr uint32_t kTmemCols = 2 * BN;
 };
 
-template <int BN, int TERMS, int STAGES, bool BF16, bool B_MN>
+template <int BN, int TERMS, int STAGES, bool BF16, bool A_MN, bool B_MN>
 __global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_constant__ PackedParams pp) {
   using Cfg = PackedCfg<BN, TERMS, STAGES>;
   using SL = StageLayout<BN, TERMS>;
@@ -451,8 +430,18 @@ __global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_co
           uint8_t* st = smem + stage * Cfg::kStageBytes;
           const uint32_t fb = smem_u32(&full[stage]);
           mbar_arrive_expect_tx(fb, Cfg::kStageBytes);
-          tma_load_3d(smem_u32(st + SL::kAHi), &pp.tmA[0], fb, kb * kBK, tm * kBM, r);
-          if (TERMS == 3) tma_load_3d(smem_u32(st + SL::kALo), &pp.tmA[1], fb, kb * kBK, tm * kBM, r);
+          if (A_MN) {
+            // A operand sums stored k-rows x m-cols: two boxes of 64 (m) x 64 (k), 8 KB each
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+              tma_load_3d(smem_u32(st + SL::kAHi + j * 8192), &pp.tmA[0], fb, tm * kBM + 64 * j, kb * kBK, r);
+              if (TERMS == 3)
+                tma_load_3d(smem_u32(st + SL::kALo + j * 8192), &pp.tmA[1], fb, tm * kBM + 64 * j, kb * kBK, r);
+            }
+          } else {
+            tma_load_3d(smem_u32(st + SL::kAHi), &pp.tmA[0], fb, kb * kBK, tm * kBM, r);
+            if (TERMS == 3) tma_load_3d(smem_u32(st + SL::kALo), &pp.tmA[1], fb, kb * kBK, tm * kBM, r);
+          }
           if (B_MN) {
             // B operand sums stored k-rows x n-cols: BN/64 boxes of 64 (n) x 64 (k), 8 KB each
 #pragma unroll
@@ -479,8 +468,8 @@ __global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_co
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      if (!mma_role<BN, TERMS, STAGES, BF16, B_MN>(p, smem, full, empty, acc_full, acc_empty, tmem_base,
-                                                 abort_flag)) {
+      if (!mma_role<BN, TERMS, STAGES, BF16, A_MN, B_MN>(p, smem, full, empty, acc_full, acc_empty,
+                                                       tmem_base, abort_flag)) {
         atomicOr(p.err, kErrMmaWait);
         *abort_flag = 1;
         drain_pause(2000000ull);

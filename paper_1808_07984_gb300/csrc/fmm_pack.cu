@@ -1,7 +1,7 @@
 // fmm_pack.cu -- streaming passes around the tensor-core kernel:
-//   * operand-sum pass: forms the 7^L signed sums of A-blocks (and of B-blocks,
-//     transposed to K-major) in FP32 and stores them rounded to 16 bits, or split
-//     into BF16 hi/lo halves (hi = bf16(P), lo = bf16(P - hi));
+//   * operand-sum pass: forms the 7^L signed sums of A-blocks (or B-blocks) in FP32 and
+//     stores them, in the source's own row-major layout, rounded to 16 bits or split into
+//     BF16 hi/lo halves (hi = bf16(P), lo = bf16(P - hi));
 //   * beta pass: C = beta * C (beta == 0 writes zeros without reading C);
 //   * a one-CTA kernel that exercises the bounded-wait failure path.
 #include <cuda_bf16.h>
@@ -39,9 +39,11 @@ __device__ __forceinline__ uint16_t round16(float x) {
 // (r1, r2) takes block (q1, q2) with coefficient coef(r1, q1) * coef(r2, q2) and the sum is
 // formed as sum_q2 coef(r2, q2) * (sum_q1 coef(r1, q1) * X_(q1, q2)).
 // Each thread handles EPT consecutive columns of one row.
-template <bool IS_B>
+template <bool IS_B, bool TRANSQ>
 __device__ __forceinline__ constexpr int coef(int r, int q) {
-  return IS_B ? strassen_v(r, q) : strassen_u(r, q);
+  // TRANSQ: the source is stored transposed, so its quadrant (i, j) is operand quadrant (j, i)
+  const int qq = TRANSQ ? 2 * (q % 2) + q / 2 : q;
+  return IS_B ? strassen_v(r, qq) : strassen_u(r, qq);
 }
 
 template <int TERMS, int OUT16, int EPT>
@@ -111,7 +113,7 @@ __device__ __forceinline__ void load_group(const SumParams& p, const T* X, int64
   }
 }
 
-template <typename T, int OUT16, int L, bool IS_B, int TERMS, int EPT>
+template <typename T, int OUT16, int L, bool IS_B, bool TRANSQ, int TERMS, int EPT>
 __global__ void __launch_bounds__(256) operand_sums_kernel(const __grid_constant__ SumParams p) {
   constexpr int G = 1 << L;
   const T* X = static_cast<const T*>(p.X);
@@ -138,7 +140,7 @@ __global__ void __launch_bounds__(256) operand_sums_kernel(const __grid_constant
         for (int e = 0; e < EPT; ++e) acc[e] = 0.f;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const int c = coef<IS_B>(r, q);
+          const int c = coef<IS_B, TRANSQ>(r, q);
 #pragma unroll
           for (int e = 0; e < EPT; ++e) {
             if (c > 0) acc[e] += v[q][e];
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(256) operand_sums_kernel(const __grid_constant
           for (int e = 0; e < EPT; ++e) S[q2][e] = 0.f;
 #pragma unroll
           for (int q1 = 0; q1 < 4; ++q1) {
-            const int c = coef<IS_B>(r1, q1);
+            const int c = coef<IS_B, TRANSQ>(r1, q1);
 #pragma unroll
             for (int e = 0; e < EPT; ++e) S[q2][e] = c > 0 ? S[q2][e] + v[q1 * 4 + q2][e]
                                                    : (c < 0 ? S[q2][e] - v[q1 * 4 + q2][e] : S[q2][e]);
@@ -179,7 +181,7 @@ __global__ void __launch_bounds__(256) operand_sums_kernel(const __grid_constant
           for (int e = 0; e < EPT; ++e) acc[e] = 0.f;
 #pragma unroll
           for (int q2 = 0; q2 < 4; ++q2) {
-            const int c = coef<IS_B>(r2, q2);
+            const int c = coef<IS_B, TRANSQ>(r2, q2);
 #pragma unroll
             for (int e = 0; e < EPT; ++e) {
               if (c > 0) acc[e] += S[q2][e];
@@ -187,63 +189,6 @@ __global__ void __launch_bounds__(256) operand_sums_kernel(const __grid_constant
             }
           }
           store_sum<TERMS, OUT16, EPT>(p, (r1 * 7 + r2) * p.prod_stride + orow, acc);
-        }
-      }
-    }
-  }
-}
-
-// B-side, transposed: X is the (k x n) matrix B; out[r][j][l] = sum_t sign_t * X[origin + (l, j)]
-// for j < hc (n direction) and l < hr (k direction), i.e. each operand sum is written K-major.
-// A 32 x 32 (l, j) tile of every source block is staged in shared memory.
-template <typename T, int OUT16, int NSRC>
-__global__ void __launch_bounds__(256) pack_cols_kernel(const __grid_constant__ PackParams p) {
-  extern __shared__ float tile[];  // [NSRC][32][33]
-  const T* X = static_cast<const T*>(p.X);
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
-  const int tiles_l = (p.hr + 31) / 32;
-  const int tiles_j = (p.hc + 31) / 32;
-  const int64_t ntiles = static_cast<int64_t>(tiles_l) * tiles_j;
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int l0 = static_cast<int>(t / tiles_j) * 32;
-    const int j0 = static_cast<int>(t % tiles_j) * 32;
-    __syncthreads();
-#pragma unroll
-    for (int s = 0; s < NSRC; ++s) {
-      const int bi = s / p.gdim, bj = s - (s / p.gdim) * p.gdim;
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int l = l0 + ty + 8 * u;
-        const int j = j0 + tx;
-        const int64_t gr = static_cast<int64_t>(bi) * p.hr + l;
-        const int64_t gc = static_cast<int64_t>(bj) * p.hc + j;
-        float x = 0.f;
-        if (l < p.hr && j < p.hc && gr < p.rows && gc < p.cols) x = load_as_float<T>(X + gr * p.ldx + gc);
-        tile[(s * 32 + ty + 8 * u) * 33 + tx] = x;
-      }
-    }
-    __syncthreads();
-    for (int r = 0; r < p.nprod; ++r) {
-      const int cnt = p.cnt[r];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int j = j0 + ty + 8 * u;
-        const int l = l0 + tx;
-        float acc = 0.f;
-        for (int t2 = 0; t2 < cnt; ++t2) {
-          const SrcTerm st = p.term[r][t2];
-          const float x = tile[(st.src * 32 + tx) * 33 + ty + 8 * u];
-          acc = st.sign > 0 ? acc + x : acc - x;
-        }
-        if (j < p.hc && l < p.hr) {
-          const int64_t o = r * p.prod_stride + static_cast<int64_t>(j) * p.ld_out + l;
-          if (p.terms == 3) {
-            const __nv_bfloat16 hb = __float2bfloat16_rn(acc);
-            p.out_hi[o] = __bfloat16_as_ushort(hb);
-            p.out_lo[o] = __bfloat16_as_ushort(__float2bfloat16_rn(acc - __bfloat162float(hb)));
-          } else {
-            p.out_hi[o] = round16<OUT16>(acc);
-          }
         }
       }
     }
@@ -276,80 +221,49 @@ __global__ void debug_wait_kernel(unsigned* err, uint64_t timeout_ns) {
 }
 
 // ------------------------------------------------------------------ launchers
-template <typename T, int OUT16>
-static cudaError_t launch_pack_t(const PackParams& p, bool transpose, int num_sms, cudaStream_t s) {
-  const int nsrc = p.nsrc;
-  if (!transpose) return cudaErrorInvalidValue;
-  {
-    const int64_t ntiles = static_cast<int64_t>((p.hr + 31) / 32) * ((p.hc + 31) / 32);
-    if (ntiles == 0) return cudaSuccess;
-    const int grid = static_cast<int>(std::min<int64_t>(ntiles, int64_t(num_sms) * 4));
-    const size_t smem = static_cast<size_t>(nsrc) * 32 * 33 * sizeof(float);
-    switch (nsrc) {
-      case 1: pack_cols_kernel<T, OUT16, 1><<<grid, 256, smem, s>>>(p); break;
-      case 4: pack_cols_kernel<T, OUT16, 4><<<grid, 256, smem, s>>>(p); break;
-      case 16: {
-        cudaError_t e = cudaFuncSetAttribute(pack_cols_kernel<T, OUT16, 16>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(smem));
-        if (e != cudaSuccess) return e;
-        pack_cols_kernel<T, OUT16, 16><<<grid, 256, smem, s>>>(p);
-        break;
-      }
-      default: return cudaErrorInvalidValue;
-    }
-  }
-  return cudaGetLastError();
-}
-
-template <typename T, int OUT16, int L, bool IS_B, int TERMS>
+template <typename T, int OUT16, int L, bool IS_B, bool TQ, int TERMS>
 static cudaError_t launch_sums_t(const SumParams& p, int num_sms, cudaStream_t s) {
   constexpr int EPT = L == 2 ? 4 : 8;
   const int64_t total = p.hr * ((p.hc + EPT - 1) / EPT);
   if (total == 0) return cudaSuccess;
   const int grid = static_cast<int>(std::min<int64_t>((total + 255) / 256, int64_t(num_sms) * 16));
-  operand_sums_kernel<T, OUT16, L, IS_B, TERMS, EPT><<<grid, 256, 0, s>>>(p);
+  operand_sums_kernel<T, OUT16, L, IS_B, TQ, TERMS, EPT><<<grid, 256, 0, s>>>(p);
   return cudaGetLastError();
 }
 
-template <typename T, int OUT16, bool IS_B, int TERMS>
+template <typename T, int OUT16, bool IS_B, bool TQ, int TERMS>
 static cudaError_t launch_sums_l(const SumParams& p, int levels, int num_sms, cudaStream_t s) {
   switch (levels) {
-    case 0: return launch_sums_t<T, OUT16, 0, IS_B, TERMS>(p, num_sms, s);
-    case 1: return launch_sums_t<T, OUT16, 1, IS_B, TERMS>(p, num_sms, s);
-    case 2: return launch_sums_t<T, OUT16, 2, IS_B, TERMS>(p, num_sms, s);
+    case 0: return launch_sums_t<T, OUT16, 0, IS_B, TQ, TERMS>(p, num_sms, s);
+    case 1: return launch_sums_t<T, OUT16, 1, IS_B, TQ, TERMS>(p, num_sms, s);
+    case 2: return launch_sums_t<T, OUT16, 2, IS_B, TQ, TERMS>(p, num_sms, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <bool IS_B>
+template <bool IS_B, bool TQ>
 static cudaError_t launch_sums_b(const SumParams& p, int levels, int in_type, int out16, int num_sms,
                                  cudaStream_t s) {
   if (in_type == kInF32) {
-    if (p.terms == 3) return launch_sums_l<float, 0, IS_B, 3>(p, levels, num_sms, s);
-    return out16 ? launch_sums_l<float, 1, IS_B, 1>(p, levels, num_sms, s)
-                 : launch_sums_l<float, 0, IS_B, 1>(p, levels, num_sms, s);
+    if (p.terms == 3) return launch_sums_l<float, 0, IS_B, TQ, 3>(p, levels, num_sms, s);
+    return out16 ? launch_sums_l<float, 1, IS_B, TQ, 1>(p, levels, num_sms, s)
+                 : launch_sums_l<float, 0, IS_B, TQ, 1>(p, levels, num_sms, s);
   }
-  if (in_type == kInBF16) return launch_sums_l<__nv_bfloat16, 0, IS_B, 1>(p, levels, num_sms, s);
-  if (in_type == kInF16) return launch_sums_l<__half, 1, IS_B, 1>(p, levels, num_sms, s);
+  if (in_type == kInBF16 && p.terms == 1 && !out16)
+    return launch_sums_l<__nv_bfloat16, 0, IS_B, TQ, 1>(p, levels, num_sms, s);
+  if (in_type == kInF16 && p.terms == 1 && out16)
+    return launch_sums_l<__half, 1, IS_B, TQ, 1>(p, levels, num_sms, s);
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_operand_sums(const SumParams& p, int levels, bool is_b, int in_type, int out16,
-                                int num_sms, cudaStream_t s) {
-  return is_b ? launch_sums_b<true>(p, levels, in_type, out16, num_sms, s)
-              : launch_sums_b<false>(p, levels, in_type, out16, num_sms, s);
-}
-
-cudaError_t launch_pack(const PackParams& p, int in_type, int out16, bool transpose, int num_sms,
-                        cudaStream_t s) {
-  if (in_type == kInF32) {
-    return out16 ? launch_pack_t<float, 1>(p, transpose, num_sms, s)
-                 : launch_pack_t<float, 0>(p, transpose, num_sms, s);
+cudaError_t launch_operand_sums(const SumParams& p, int levels, bool is_b, bool transq, int in_type,
+                                int out16, int num_sms, cudaStream_t s) {
+  if (is_b) {
+    return transq ? launch_sums_b<true, true>(p, levels, in_type, out16, num_sms, s)
+                  : launch_sums_b<true, false>(p, levels, in_type, out16, num_sms, s);
   }
-  if (in_type == kInBF16) return launch_pack_t<__nv_bfloat16, 0>(p, transpose, num_sms, s);
-  if (in_type == kInF16) return launch_pack_t<__half, 1>(p, transpose, num_sms, s);
-  return cudaErrorInvalidValue;
+  return transq ? launch_sums_b<false, true>(p, levels, in_type, out16, num_sms, s)
+                : launch_sums_b<false, false>(p, levels, in_type, out16, num_sms, s);
 }
 
 cudaError_t launch_beta(float* C, int64_t m, int64_t n, int64_t ldc, float beta, int num_sms,

@@ -5,10 +5,10 @@
 
 namespace fmm {
 
-template <int BN, int TERMS, int STAGES, bool BF16, bool B_MN>
+template <int BN, int TERMS, int STAGES, bool BF16, bool A_MN, bool B_MN>
 static cudaError_t launch_cfg(const PackedParams& p, int grid, cudaStream_t s) {
   using Cfg = PackedCfg<BN, TERMS, STAGES>;
-  auto kern = fmm_packed_kernel<BN, TERMS, STAGES, BF16, B_MN>;
+  auto kern = fmm_packed_kernel<BN, TERMS, STAGES, BF16, A_MN, B_MN>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(Cfg::kSmemBytes));
   if (e != cudaSuccess) return e;
@@ -23,24 +23,30 @@ bool packed_config_supported(int tile_n, int terms, bool bf16) {
   return true;
 }
 
-template <bool B_MN>
+template <bool A_MN, bool B_MN>
 static cudaError_t launch_mn(const PackedParams& p, int tile_n, int terms, bool bf16, int grid,
                              cudaStream_t s) {
   if (tile_n == 128) {
-    if (terms == 3) return launch_cfg<128, 3, 3, true, B_MN>(p, grid, s);
-    return bf16 ? launch_cfg<128, 1, 6, true, B_MN>(p, grid, s) : launch_cfg<128, 1, 6, false, B_MN>(p, grid, s);
+    if (terms == 3) return launch_cfg<128, 3, 3, true, A_MN, B_MN>(p, grid, s);
+    return bf16 ? launch_cfg<128, 1, 6, true, A_MN, B_MN>(p, grid, s)
+                : launch_cfg<128, 1, 6, false, A_MN, B_MN>(p, grid, s);
   }
   if (tile_n == 256) {
-    if (terms == 3) return launch_cfg<256, 3, 2, true, B_MN>(p, grid, s);
-    return bf16 ? launch_cfg<256, 1, 4, true, B_MN>(p, grid, s) : launch_cfg<256, 1, 4, false, B_MN>(p, grid, s);
+    if (terms == 3) return launch_cfg<256, 3, 2, true, A_MN, B_MN>(p, grid, s);
+    return bf16 ? launch_cfg<256, 1, 4, true, A_MN, B_MN>(p, grid, s)
+                : launch_cfg<256, 1, 4, false, A_MN, B_MN>(p, grid, s);
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_packed(const PackedParams& p, int tile_n, int terms, bool bf16, bool b_mn, int grid,
-                          cudaStream_t s) {
-  return b_mn ? launch_mn<true>(p, tile_n, terms, bf16, grid, s)
-              : launch_mn<false>(p, tile_n, terms, bf16, grid, s);
+// Operand layouts built: forward (A K-major, B MN-major), dA = dC B^T (A K-major, B K-major),
+// dB = A^T dC (A MN-major, B MN-major).
+cudaError_t launch_packed(const PackedParams& p, int tile_n, int terms, bool bf16, bool a_mn, bool b_mn,
+                          int grid, cudaStream_t s) {
+  if (!a_mn && b_mn) return launch_mn<false, true>(p, tile_n, terms, bf16, grid, s);
+  if (!a_mn && !b_mn) return launch_mn<false, false>(p, tile_n, terms, bf16, grid, s);
+  if (a_mn && b_mn) return launch_mn<true, true>(p, tile_n, terms, bf16, grid, s);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace fmm

@@ -11,19 +11,19 @@ enum InType { kInF32 = 0, kInBF16 = 1, kInF16 = 2 };
 // Sets the calling thread's message returned by fmm_last_error().
 void set_last_error(const std::string& msg);
 
-cudaError_t launch_pack(const PackParams& p, int in_type, int out16, bool transpose, int num_sms,
-                        cudaStream_t s);
-// Operand sums of all 7^levels products of A (is_b = false, coefficients U) or B (V).
-cudaError_t launch_operand_sums(const SumParams& p, int levels, bool is_b, int in_type, int out16,
-                                int num_sms, cudaStream_t s);
+// Operand sums of all 7^levels products of A (is_b = false, coefficients U) or B (V).  With
+// transq the stored source is the transpose of the operand, so block (i, j) of the source takes
+// the coefficient of operand block (j, i) at every level.
+cudaError_t launch_operand_sums(const SumParams& p, int levels, bool is_b, bool transq, int in_type,
+                                int out16, int num_sms, cudaStream_t s);
 cudaError_t launch_beta(float* C, int64_t m, int64_t n, int64_t ldc, float beta, int num_sms,
                         cudaStream_t s);
 cudaError_t launch_debug_wait(unsigned* err, uint64_t timeout_ns, cudaStream_t s);
 
 // Tensor-core kernel over packed operand sums.  tile_n in {128, 256}; terms in {1, 3};
 // bf16 selects BF16 (true) or FP16 (false) operands.
-cudaError_t launch_packed(const PackedParams& p, int tile_n, int terms, bool bf16, bool b_mn, int grid,
-                          cudaStream_t s);
+cudaError_t launch_packed(const PackedParams& p, int tile_n, int terms, bool bf16, bool a_mn, bool b_mn,
+                          int grid, cudaStream_t s);
 bool packed_config_supported(int tile_n, int terms, bool bf16);
 
 // Tensor-core kernel that forms the operand sums on chip from FP32 source tiles

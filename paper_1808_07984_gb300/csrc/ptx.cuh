@@ -161,12 +161,13 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, float (&v)[32
 }
 
 // ------------------------------------------------------------- descriptors
-// Instruction descriptor, kind::f16: D = F32, A and B both BF16 (or both F16), A K-major,
-// B K-major or (b_mn) MN-major.
-__host__ __device__ constexpr uint32_t make_idesc_f16(int M, int N, bool bf16, bool b_mn = false) {
+// Instruction descriptor, kind::f16: D = F32, A and B both BF16 (or both F16); each operand
+// K-major or (a_mn / b_mn) MN-major.
+__host__ __device__ constexpr uint32_t make_idesc_f16(int M, int N, bool bf16, bool a_mn, bool b_mn) {
   return (1u << 4)                               // D format: F32
          | ((bf16 ? 1u : 0u) << 7)               // A format: BF16 (1) / F16 (0)
          | ((bf16 ? 1u : 0u) << 10)              // B format
+         | ((a_mn ? 1u : 0u) << 15)              // A major-ness: MN
          | ((b_mn ? 1u : 0u) << 16)              // B major-ness: MN
          | (static_cast<uint32_t>(N >> 3) << 17)  // N / 8
          | (static_cast<uint32_t>(M >> 4) << 24); // M / 16

@@ -1,0 +1,139 @@
+"""Backward products dA = dC @ B^T and dB = A^T @ dC (fmm_gemm_backward) and the
+differentiable layer, against the FP64 oracle.  Integer inputs are bit-exact; floats
+within the normwise bounds of test_gpu_parity."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1808_07984_gb300 as fmm
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    fmm.build()
+    fmm.load()
+    oracle.build()
+
+
+def _tol(variant, levels, k):
+    kk = max(k, 1)
+    if variant == "split3":
+        return max(1e-6, 8 * 2.0 ** -17 * 3 ** levels / math.sqrt(kk))
+    return 4 * 2.0 ** -8 * 3 ** levels / math.sqrt(kk)
+
+
+def _err(X, X64, An, Bn):
+    return oracle.normwise_error(X, X64, An, Bn)
+
+
+@pytest.mark.parametrize("levels", [0, 1, 2])
+@pytest.mark.parametrize("m,n,k", [(16, 16, 16), (300, 200, 136), (129, 65, 257), (1, 40, 33)])
+def test_backward_int_bit_exact(m, n, k, levels):
+    A, B = synth.problem(m, n, k, 7 + m, "int")
+    dC = synth.small_int((m, n), 8 + n)
+    dA, dB = fmm.gemm_backward(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(),
+                               torch.from_numpy(dC).cuda(), levels=levels)
+    fmm.device_status()
+    np.testing.assert_array_equal(dA.cpu().numpy(), oracle.classical(dC, np.ascontiguousarray(B.T)))
+    np.testing.assert_array_equal(dB.cpu().numpy(), oracle.classical(np.ascontiguousarray(A.T), dC))
+
+
+@pytest.mark.parametrize("variant", ["split3", "plain_bf16"])
+@pytest.mark.parametrize("levels", [0, 1, 2])
+@pytest.mark.parametrize("m,n,k", [(257, 300, 140), (512, 384, 640)])
+def test_backward_float(m, n, k, levels, variant):
+    A, B = synth.problem(m, n, k, 3 * m + k, "gaussian")
+    dC = synth.gaussian((m, n), 11)
+    dA, dB = fmm.gemm_backward(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(),
+                               torch.from_numpy(dC).cuda(), levels=levels, variant=variant)
+    fmm.device_status()
+    Bt = np.ascontiguousarray(B.T)
+    At = np.ascontiguousarray(A.T)
+    nA, nB, nC = (np.linalg.norm(X.astype(np.float64)) for X in (A, B, dC))
+    assert _err(dA.cpu().numpy(), oracle.classical(dC, Bt), nC, nB) <= _tol(variant, levels, n)
+    assert _err(dB.cpu().numpy(), oracle.classical(At, dC), nA, nC) <= _tol(variant, levels, m)
+
+
+def test_backward_bf16_inputs_fp32_grads():
+    """BF16 A and B, FP32 dC: each operand sum is rounded once to BF16."""
+    m, n, k = 384, 256, 320
+    A, B = synth.problem(m, n, k, 4, "gaussian")
+    dC = synth.gaussian((m, n), 5)
+    Ab = torch.from_numpy(A).to(torch.bfloat16).cuda()
+    Bb = torch.from_numpy(B).to(torch.bfloat16).cuda()
+    dA, dB = fmm.gemm_backward(Ab, Bb, torch.from_numpy(dC).cuda(), levels=1, variant="bf16")
+    fmm.device_status()
+    assert dA.dtype == torch.float32 and dB.dtype == torch.float32
+    Abits = Ab.cpu().view(torch.int16).numpy().view(np.uint16)
+    Bbits = Bb.cpu().view(torch.int16).numpy().view(np.uint16)
+    dA64 = oracle.classical(dC, np.ascontiguousarray(Bbits.T), b_code=oracle.ORC_BF16)
+    dB64 = oracle.classical(np.ascontiguousarray(Abits.T), dC, a_code=oracle.ORC_BF16)
+    nA = float(Ab.float().norm())
+    nB = float(Bb.float().norm())
+    nC = float(np.linalg.norm(dC.astype(np.float64)))
+    assert _err(dA.cpu().numpy(), dA64, nC, nB) <= _tol("bf16", 1, n)
+    assert _err(dB.cpu().numpy(), dB64, nA, nC) <= _tol("bf16", 1, m)
+
+
+@pytest.mark.parametrize("levels", [1, 2])
+def test_linear_autograd_matches_oracle_and_finite_differences(levels):
+    m, n, k = 256, 192, 320
+    A, B = synth.problem(m, n, k, 12, "gaussian")
+    G = synth.gaussian((m, n), 13)
+    Ad = torch.from_numpy(A).cuda().requires_grad_(True)
+    Bd = torch.from_numpy(B).cuda().requires_grad_(True)
+    Gd = torch.from_numpy(G).cuda()
+    C = fmm.linear(Ad, Bd, levels=levels)
+    loss = (C * Gd).sum()
+    loss.backward()
+    fmm.device_status()
+    nA, nB, nG = (np.linalg.norm(X.astype(np.float64)) for X in (A, B, G))
+    dA64 = oracle.classical(G, np.ascontiguousarray(B.T))
+    dB64 = oracle.classical(np.ascontiguousarray(A.T), G)
+    assert _err(Ad.grad.cpu().numpy(), dA64, nG, nB) <= _tol("split3", levels, n)
+    assert _err(Bd.grad.cpu().numpy(), dB64, nA, nG) <= _tol("split3", levels, m)
+    # The loss is bilinear, so a central difference with any step is exact up to rounding:
+    # (L(A + E) - L(A - E)) / 2 = <G, E B> = <dA, E>.
+    E = torch.from_numpy(synth.gaussian((m, k), 14)).cuda()
+    with torch.no_grad():
+        lp = (fmm.linear(Ad + E, Bd, levels=levels) * Gd).double().sum()
+        lm = (fmm.linear(Ad - E, Bd, levels=levels) * Gd).double().sum()
+    fd = float((lp - lm) / 2)
+    an = float((Ad.grad.double() * E.double()).sum())
+    scale = float(np.linalg.norm(G) * np.linalg.norm(B.astype(np.float64)) * E.double().norm())
+    assert abs(fd - an) <= 1e-5 * scale
+
+
+def test_linear_layer_shapes_sampled_rows():
+    """Differentiable layer at 8192 x 4096 x 4096 with BF16 inputs; gradients checked on
+    sampled rows of dA and of dB against the FP64 oracle."""
+    m, k, n = 8192, 4096, 4096
+    rng = synth.rng(31)
+    A = torch.from_numpy(synth.gaussian((m, k), 32)).to(torch.bfloat16).cuda().requires_grad_(True)
+    B = torch.from_numpy(synth.gaussian((k, n), 33)).to(torch.bfloat16).cuda().requires_grad_(True)
+    dC = torch.from_numpy(synth.gaussian((m, n), 34)).cuda()
+    C = fmm.linear(A, B, levels=1, variant="bf16")
+    C.backward(dC)
+    fmm.device_status()
+    Af = A.detach().float().cpu().numpy().astype(np.float64)
+    Bf = B.detach().float().cpu().numpy().astype(np.float64)
+    dCn = dC.cpu().numpy()
+    ra = np.unique(rng.integers(0, m, size=6))
+    rb = np.unique(rng.integers(0, k, size=6))
+    # dA[ra] = dC[ra] B^T;  dB[rb] = A[:, rb]^T dC  (inputs are exact in FP64)
+    dA64 = oracle.classical(dCn, np.ascontiguousarray(Bf.T), rows=ra)
+    dB64 = oracle.classical(np.ascontiguousarray(Af.T), dCn, rows=rb)
+    gA = A.grad.float().cpu().numpy()[ra]
+    gB = B.grad.float().cpu().numpy()[rb]
+    # gradients come back in the inputs' dtype (BF16): allow that rounding on top
+    tol = _tol("bf16", 1, 4096) + 2.0 ** -8
+    assert _err(gA, dA64, np.linalg.norm(dCn[ra].astype(np.float64)), np.linalg.norm(Bf)) <= tol
+    assert _err(gB, dB64, np.linalg.norm(Af[:, rb]), np.linalg.norm(dCn.astype(np.float64))) <= tol

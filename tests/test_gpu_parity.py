@@ -57,8 +57,7 @@ def _to_device(X, ld_pad, dtype):
 
 
 def run(m, n, k, levels, variant="split3", dist="uniform", seed=0, alpha=1.0, beta=0.0,
-        tile_n=0, pads=(0, 0, 0), c_fill=None, rows=None, b_kmajor=0, schedule="auto",
-        algo="auto"):
+        tile_n=0, pads=(0, 0, 0), c_fill=None, rows=None, schedule="auto", algo="auto"):
     A, B = synth.problem(m, n, k, seed, dist)
     in_dtype = torch.bfloat16 if variant == "bf16" else torch.float32
     Ad = _to_device(A, pads[0], in_dtype)
@@ -72,7 +71,7 @@ def run(m, n, k, levels, variant="split3", dist="uniform", seed=0, alpha=1.0, be
         if c_fill is not None:
             Cd.fill_(c_fill)
     fmm.gemm(Ad, Bd, Cd, alpha=alpha, beta=beta, levels=levels, variant=variant, tile_n=tile_n,
-             b_kmajor=b_kmajor, schedule=schedule, algo=algo)
+             schedule=schedule, algo=algo)
     fmm.device_status()
     C = Cd.cpu().numpy().astype(np.float64)
     if variant == "bf16":
@@ -101,13 +100,11 @@ def test_int16_cube_bit_exact(variant, levels):
     np.testing.assert_array_equal(C, C64)
 
 
-@pytest.mark.parametrize("b_kmajor", [0, 1])
 @pytest.mark.parametrize("tile_n", [128, 256])
 @pytest.mark.parametrize("levels", [0, 1, 2])
 @pytest.mark.parametrize("m,n,k", [(300, 520, 200), (129, 257, 65), (1, 300, 1), (520, 8, 400)])
-def test_int_ragged_bit_exact(m, n, k, levels, tile_n, b_kmajor):
-    C, C64, _, _ = run(m, n, k, levels, "split3", dist="int", seed=m + n + k, tile_n=tile_n,
-                       b_kmajor=b_kmajor)
+def test_int_ragged_bit_exact(m, n, k, levels, tile_n):
+    C, C64, _, _ = run(m, n, k, levels, "split3", dist="int", seed=m + n + k, tile_n=tile_n)
     np.testing.assert_array_equal(C, C64)
 
 
@@ -206,11 +203,10 @@ def test_float_shapes(m, n, k, levels, variant):
     assert err <= tolerance(variant, levels, k), err
 
 
-@pytest.mark.parametrize("b_kmajor", [0, 1])
 @pytest.mark.parametrize("levels", [0, 1, 2])
-def test_alpha_beta_and_padded_leading_dims(levels, b_kmajor):
+def test_alpha_beta_and_padded_leading_dims(levels):
     C, C64, An, Bn = run(300, 260, 150, levels, "split3", seed=5, alpha=-1.5, beta=0.75,
-                         pads=(5, 3, 9), b_kmajor=b_kmajor)
+                         pads=(5, 3, 9))
     err = oracle.normwise_error(C, C64, An, Bn)
     assert err <= tolerance("split3", levels, 150), err
 
