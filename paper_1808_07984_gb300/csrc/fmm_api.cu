@@ -203,15 +203,18 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
     default: return fail(FMM_ERR_UNSUPPORTED, "variant not built");
   }
   const int algo = opt ? opt->algo : 0;
-  if (algo != FMM_ALGO_AUTO && algo != FMM_ALGO_PACKED && algo != FMM_ALGO_FUSED)
-    return fail(FMM_ERR_UNSUPPORTED, "algorithm not built");
-  pl.algo = algo == FMM_ALGO_FUSED ? FMM_ALGO_FUSED : FMM_ALGO_PACKED;
-  if (pl.algo == FMM_ALGO_FUSED && (pl.in_type != kInF32 || a_mn || !b_mn))
-    return fail(FMM_ERR_UNSUPPORTED, "the fused algorithm takes FP32 A and B (split3 or plain_bf16) in the forward product");
+  if (algo < FMM_ALGO_AUTO || algo > FMM_ALGO_HYBRID) return fail(FMM_ERR_UNSUPPORTED, "algorithm not built");
+  if (algo == FMM_ALGO_HYBRID && levels != 2)
+    return fail(FMM_ERR_UNSUPPORTED, "the hybrid algorithm is a two-level scheme (levels = 2)");
+  pl.algo = algo == FMM_ALGO_AUTO ? FMM_ALGO_PACKED : algo;
+  const bool on_chip = pl.algo == FMM_ALGO_FUSED || pl.algo == FMM_ALGO_HYBRID;
+  if (on_chip && (pl.in_type != kInF32 || a_mn || !b_mn))
+    return fail(FMM_ERR_UNSUPPORTED,
+                "the fused and hybrid algorithms take FP32 A and B (split3 or plain_bf16) in the forward product");
   pl.tile_n = (opt && opt->tile_n) ? opt->tile_n : 0;
-  if (pl.algo == FMM_ALGO_FUSED) {
+  if (on_chip) {
     if (pl.tile_n != 0 && pl.tile_n != kFusedTileN)
-      return fail(FMM_ERR_UNSUPPORTED, "the fused algorithm uses 128-wide tiles");
+      return fail(FMM_ERR_UNSUPPORTED, "the fused and hybrid algorithms use 128-wide tiles");
     pl.tile_n = kFusedTileN;
   }
   const int sched = opt ? opt->schedule : 0;
@@ -243,6 +246,12 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
   pl.b_bytes = static_cast<size_t>(round_up(static_cast<int64_t>(pl.R) * b_rows * pl.ldb_w * 2, 256));
   const size_t arrays = pl.terms == 3 ? 2 : 1;
   pl.ws = (m == 0 || n == 0 || k == 0 || pl.algo == FMM_ALGO_FUSED) ? 0 : arrays * (pl.a_bytes + pl.b_bytes);
+  if (pl.algo == FMM_ALGO_HYBRID && pl.ws > 0) {
+    // seven top-level sums of each operand in FP32, blocks of 2h x 2h
+    pl.a_bytes = static_cast<size_t>(round_up(7 * (2 * pl.hm) * (2 * pl.hk) * 4, 256));
+    pl.b_bytes = static_cast<size_t>(round_up(7 * (2 * pl.hk) * (2 * pl.hn) * 4, 256));
+    pl.ws = pl.a_bytes + pl.b_bytes;
+  }
   return FMM_OK;
 }
 
@@ -417,6 +426,111 @@ fmm_status gemm_fused(const Plan& pl, int64_t m, int64_t n, int64_t k, float alp
 }
 
 
+fmm_status encode_f32_2d(CUtensorMap* map, const float* base, int64_t cols, int64_t rows, int64_t ld,
+                         uint32_t box_cols, uint32_t box_rows, CUtensorMapSwizzle swz) {
+  const cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld * 4)};
+  const cuuint32_t box[2] = {box_cols, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult cr = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides,
+                         box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) return fail(FMM_ERR_CUDA, "cuTensorMapEncodeTiled (FP32 source) failed");
+  return FMM_OK;
+}
+
+// Hybrid two-level path (Section 3.4): the seven top-level operand sums of A and of B are
+// materialised in FP32 in the workspace (blocks of 2h_m x 2h_k and 2h_k x 2h_n, zero-padded);
+// the 49 bottom-level products are then formed on chip by the fused kernel from the quadrants
+// of those sums, and each is added into its composite destinations
+// W[q1, r1] * W[q2, r2] directly in C (no product ever reaches memory).
+fmm_status gemm_hybrid(const Plan& pl, int64_t m, int64_t n, int64_t k, float alpha, const void* A,
+                       int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, void* ws,
+                       const DeviceInfo& dev, const fmm_options* opt, cudaStream_t s) {
+  const int64_t h1m = 2 * pl.hm, h1k = 2 * pl.hk, h1n = 2 * pl.hn;
+  float* P = static_cast<float*>(ws);
+  float* Q = reinterpret_cast<float*>(static_cast<uint8_t*>(ws) + pl.a_bytes);
+  SumParams sa;
+  std::memset(&sa, 0, sizeof sa);
+  sa.X = A;
+  sa.ldx = lda;
+  sa.rows = m;
+  sa.cols = k;
+  sa.hr = h1m;
+  sa.hc = h1k;
+  sa.ld_out = h1k;
+  sa.prod_stride = h1m * h1k;
+  sa.out_f32 = P;
+  sa.terms = 0;
+  sa.vec_ok = (reinterpret_cast<uintptr_t>(A) % 16 == 0 && lda % 4 == 0) ? 1 : 0;
+  cudaError_t e;
+  {
+    PhaseScope ps(kPhasePack, s);
+    e = launch_operand_sums(sa, 1, false, false, kInF32, 0, dev.sms, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "top-level operand sums (A)");
+  SumParams sb = sa;
+  sb.X = B;
+  sb.ldx = ldb;
+  sb.rows = k;
+  sb.cols = n;
+  sb.hr = h1k;
+  sb.hc = h1n;
+  sb.ld_out = h1n;
+  sb.prod_stride = h1k * h1n;
+  sb.out_f32 = Q;
+  sb.vec_ok = (reinterpret_cast<uintptr_t>(B) % 16 == 0 && ldb % 4 == 0) ? 1 : 0;
+  {
+    PhaseScope ps(kPhasePack, s);
+    e = launch_operand_sums(sb, 1, true, false, kInF32, 0, dev.sms, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "top-level operand sums (B)");
+
+  FusedParams* fp = new FusedParams;
+  std::memset(fp, 0, sizeof(FusedParams));
+  fmm_status st = FMM_OK;
+  for (int r1 = 0; r1 < 7 && st == FMM_OK; ++r1) {
+    for (int q2 = 0; q2 < 4 && st == FMM_OK; ++q2) {
+      const int i2 = q2 / 2, j2 = q2 % 2;
+      st = encode_f32_2d(&fp->tmSA[r1 * 4 + q2], P + r1 * h1m * h1k + i2 * pl.hm * h1k + j2 * pl.hk,
+                         pl.hk, pl.hm, h1k, 32, kBM, CU_TENSOR_MAP_SWIZZLE_128B);
+      if (st == FMM_OK)
+        st = encode_f32_2d(&fp->tmSB[r1 * 4 + q2], Q + r1 * h1k * h1n + i2 * pl.hk * h1n + j2 * pl.hn,
+                           pl.hn, pl.hk, h1n, kFusedTileN, 32, CU_TENSOR_MAP_SWIZZLE_NONE);
+    }
+  }
+  const std::vector<Product> prods = make_products(2);
+  std::vector<int> live(49);
+  for (int r = 0; r < 49; ++r) {
+    live[r] = r;
+    const int r1 = r / 7, r2 = r % 7;
+    ProductSrc& ps = fp->src[r];
+    for (int q2 = 0; q2 < 4; ++q2) {
+      if (const int c = strassen_u(r2, q2)) {
+        ps.a_block[ps.na] = static_cast<int8_t>(r1 * 4 + q2);
+        ps.a_sign[ps.na++] = static_cast<int8_t>(c);
+      }
+      if (const int c = strassen_v(r2, q2)) {
+        ps.b_block[ps.nb] = static_cast<int8_t>(r1 * 4 + q2);
+        ps.b_sign[ps.nb++] = static_cast<int8_t>(c);
+      }
+    }
+  }
+  int grid = 0;
+  if (st == FMM_OK) st = fill_common(fp->c, pl, prods, live, m, n, alpha, C, ldc, dev, opt, grid);
+  if (st != FMM_OK) {
+    delete fp;
+    return st;
+  }
+  {
+    PhaseScope ps(kPhaseTensor, s);
+    e = launch_fused(*fp, pl.terms, grid, s);
+  }
+  delete fp;
+  if (e != cudaSuccess) return cuda_fail(e, "hybrid tensor-core pass");
+  return FMM_OK;
+}
+
 // C (m x n) = alpha * A' B' + beta * C with the operand layouts of `pl`.  `a` stores A' as
 // m x k (K-major) or k x m (pl.a_mn); `b` stores B' as k x n (pl.b_mn) or n x k.
 fmm_status gemm_core(const Plan& pl, int64_t m, int64_t n, int64_t k, float alpha, Operand a,
@@ -460,6 +574,8 @@ fmm_status gemm_core(const Plan& pl, int64_t m, int64_t n, int64_t k, float alph
   }
   if (k == 0 || alpha == 0.0f) return FMM_OK;
   if (pl.algo == FMM_ALGO_FUSED) return gemm_fused(pl, m, n, k, alpha, a.X, a.ld, b.X, b.ld, C, ldc, dev, opt, s);
+  if (pl.algo == FMM_ALGO_HYBRID)
+    return gemm_hybrid(pl, m, n, k, alpha, a.X, a.ld, b.X, b.ld, C, ldc, ws, dev, opt, s);
 
   const std::vector<Product> prods = make_products(pl.L);
   uint8_t* wsb = static_cast<uint8_t*>(ws);

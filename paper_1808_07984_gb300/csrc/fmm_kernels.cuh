@@ -117,9 +117,11 @@ struct ProductSrc {
 };
 
 // Kernel parameters of the fused path (operand sums formed on chip).
+constexpr int kMaxFusedSources = 28;  // hybrid two-level: 7 top-level sums x 4 quadrants
+
 struct FusedParams {
-  CUtensorMap tmSA[kMaxSources];  // FP32 blocks of A: 2-D {k, m}, box 32 x 128, 128B swizzle
-  CUtensorMap tmSB[kMaxSources];  // FP32 blocks of B: 2-D {n, k}, box 128 x 32, no swizzle
+  CUtensorMap tmSA[kMaxFusedSources];  // FP32 source blocks of A: 2-D {k, m}, box 32 x 128, 128B swizzle
+  CUtensorMap tmSB[kMaxFusedSources];  // FP32 source blocks of B: 2-D {n, k}, box 128 x 32, no swizzle
   ProductSrc src[kMaxProducts];
   CommonParams c;
 };
@@ -134,7 +136,8 @@ struct SumParams {
   int64_t prod_stride; // elements between consecutive products in the output
   uint16_t* out_hi;
   uint16_t* out_lo;
-  int32_t terms;       // 3: split hi/lo, 1: single rounding
+  float* out_f32;      // terms == 0: the sums are stored unrounded in FP32 here
+  int32_t terms;       // 3: split hi/lo, 1: single rounding, 0: FP32
   int32_t vec_ok;      // X base and ldx allow vector loads
 };
 

@@ -48,7 +48,11 @@ __device__ __forceinline__ constexpr int coef(int r, int q) {
 
 template <int TERMS, int OUT16, int EPT>
 __device__ __forceinline__ void store_sum(const SumParams& p, int64_t o, const float (&acc)[EPT]) {
-  if (TERMS == 3) {
+  if (TERMS == 0) {
+#pragma unroll
+    for (int e = 0; e < EPT; e += 4)
+      *reinterpret_cast<float4*>(p.out_f32 + o + e) = make_float4(acc[e], acc[e + 1], acc[e + 2], acc[e + 3]);
+  } else if (TERMS == 3) {
     uint16_t h[EPT], w[EPT];
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
@@ -246,6 +250,8 @@ static cudaError_t launch_sums_b(const SumParams& p, int levels, int in_type, in
                                  cudaStream_t s) {
   if (in_type == kInF32) {
     if (p.terms == 3) return launch_sums_l<float, 0, IS_B, TQ, 3>(p, levels, num_sms, s);
+    if (p.terms == 0) return levels == 1 ? launch_sums_t<float, 0, 1, IS_B, TQ, 0>(p, num_sms, s)
+                                         : cudaErrorInvalidValue;
     return out16 ? launch_sums_l<float, 1, IS_B, TQ, 1>(p, levels, num_sms, s)
                  : launch_sums_l<float, 0, IS_B, TQ, 1>(p, levels, num_sms, s);
   }

@@ -186,6 +186,36 @@ def test_fused_rejects_unaligned_leading_dimension():
     assert ei.value.status == 2
 
 
+# ------------------------------------------------------------- hybrid two-level
+@pytest.mark.parametrize("m,n,k", [(16, 16, 16), (300, 520, 200), (129, 257, 65), (1000, 1200, 300)])
+def test_hybrid_int_bit_exact(m, n, k):
+    C, C64, _, _ = run(m, n, k, 2, "split3", dist="int", seed=5 * m + n + k, algo="hybrid")
+    np.testing.assert_array_equal(C, C64)
+
+
+@pytest.mark.parametrize("variant", ["split3", "plain_bf16"])
+def test_hybrid_float(variant):
+    C, C64, An, Bn = run(640, 384, 768, 2, variant, dist="gaussian", seed=9, algo="hybrid")
+    assert oracle.normwise_error(C, C64, An, Bn) <= tolerance(variant, 2, 768)
+
+
+def test_hybrid_full_size_sampled_rows():
+    rows = np.unique(synth.rng(6).integers(0, 8192, size=8))
+    C, C64, An, Bn = run(8192, 8192, 8192, 2, "split3", seed=22, rows=rows, algo="hybrid")
+    assert oracle.normwise_error(C, C64, An, Bn) <= 1e-6
+
+
+# ------------------------------------------- large odd sizes with dynamic fringes
+@pytest.mark.parametrize("variant,levels", [("split3", 2), ("plain_bf16", 2), ("split3", 0)])
+def test_odd_30001_29999_4097_sampled_rows(variant, levels):
+    """m = 30001, n = 29999, k = 4097 with tight (odd) leading dimensions: unaligned rows,
+    element-wise write-back, zero-padded fringe blocks."""
+    rows = np.unique(np.concatenate([[0, 30000], synth.rng(7).integers(0, 30001, size=6)]))
+    C, C64, An, Bn = run(30001, 29999, 4097, levels, variant, dist="gaussian", seed=23, rows=rows)
+    err = oracle.normwise_error(C, C64, An, Bn)
+    assert err <= tolerance(variant, levels, 4097), err
+
+
 # ------------------------------------------------------------------- floats
 def test_512_cube_one_level_split3_within_1e6():
     C, C64, An, Bn = run(512, 512, 512, 1, "split3", seed=11)
