@@ -181,6 +181,9 @@ struct Plan {
   int tile_n = 128;
   int algo = FMM_ALGO_PACKED;
   int schedule = kSchedProductMajor;
+  bool scaled = false;      // FP16 operands with power-of-two scaling per panel
+  size_t scale_bytes = 0;   // panel maxima of A and B sums (scaled variant)
+  int64_t panels_a = 0, panels_b = 0;
   int64_t hm = 0, hn = 0, hk = 0;
   int64_t lda_w = 0;  // row stride of the stored A-operand sums (rounded up to 8)
   int64_t ldb_w = 0;  // row stride of the stored B-operand sums
@@ -200,8 +203,11 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
     case FMM_F32_SPLIT3_BF16: pl.terms = 3; pl.in_type = kInF32; pl.bf16 = true; break;
     case FMM_F32_PLAIN_BF16: pl.terms = 1; pl.in_type = kInF32; pl.bf16 = true; break;
     case FMM_BF16: pl.terms = 1; pl.in_type = kInBF16; pl.bf16 = true; break;
+    case FMM_F16_SCALED: pl.terms = 1; pl.in_type = kInF16; pl.bf16 = false; pl.scaled = true; break;
     default: return fail(FMM_ERR_UNSUPPORTED, "variant not built");
   }
+  if (pl.scaled && (a_mn || !b_mn))
+    return fail(FMM_ERR_UNSUPPORTED, "the scaled FP16 variant is built for the forward product");
   const int algo = opt ? opt->algo : 0;
   if (algo < FMM_ALGO_AUTO || algo > FMM_ALGO_HYBRID) return fail(FMM_ERR_UNSUPPORTED, "algorithm not built");
   if (algo == FMM_ALGO_HYBRID && levels != 2)
@@ -246,6 +252,12 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
   pl.b_bytes = static_cast<size_t>(round_up(static_cast<int64_t>(pl.R) * b_rows * pl.ldb_w * 2, 256));
   const size_t arrays = pl.terms == 3 ? 2 : 1;
   pl.ws = (m == 0 || n == 0 || k == 0 || pl.algo == FMM_ALGO_FUSED) ? 0 : arrays * (pl.a_bytes + pl.b_bytes);
+  if (pl.scaled && pl.ws > 0) {
+    pl.panels_a = (pl.hm + kBM - 1) / kBM;
+    pl.panels_b = (pl.hn + pl.tile_n - 1) / pl.tile_n;
+    pl.scale_bytes = static_cast<size_t>(round_up(pl.R * (pl.panels_a + pl.panels_b) * 4, 256));
+    pl.ws += pl.scale_bytes;
+  }
   if (pl.algo == FMM_ALGO_HYBRID && pl.ws > 0) {
     // seven top-level sums of each operand in FP32, blocks of 2h x 2h
     pl.a_bytes = static_cast<size_t>(round_up(7 * (2 * pl.hm) * (2 * pl.hk) * 4, 256));
@@ -583,6 +595,11 @@ fmm_status gemm_core(const Plan& pl, int64_t m, int64_t n, int64_t k, float alph
   uint16_t* b_hi = reinterpret_cast<uint16_t*>(wsb + pl.a_bytes);
   uint16_t* a_lo = pl.terms == 3 ? reinterpret_cast<uint16_t*>(wsb + pl.a_bytes + pl.b_bytes) : nullptr;
   uint16_t* b_lo = pl.terms == 3 ? reinterpret_cast<uint16_t*>(wsb + 2 * pl.a_bytes + pl.b_bytes) : nullptr;
+  unsigned* maxbits = pl.scaled ? reinterpret_cast<unsigned*>(wsb + pl.a_bytes + pl.b_bytes) : nullptr;
+  if (maxbits) {
+    cudaError_t e = cudaMemsetAsync(maxbits, 0, pl.scale_bytes, s);
+    if (e != cudaSuccess) return cuda_fail(e, "clearing the panel maxima");
+  }
 
   // ---- operand-sum passes (all 7^L A-operands, then all B-operands), in the stored layout
   {
@@ -600,6 +617,12 @@ fmm_status gemm_core(const Plan& pl, int64_t m, int64_t n, int64_t k, float alph
     sa.out_lo = a_lo;
     sa.terms = pl.terms;
     sa.vec_ok = (reinterpret_cast<uintptr_t>(a.X) % 16 == 0 && a.ld % 4 == 0) ? 1 : 0;
+    if (maxbits) {
+      sa.maxbits = maxbits;
+      sa.npanels = static_cast<int32_t>(pl.panels_a);
+      sa.panel_w = kBM;
+      sa.scale_rows = 1;
+    }
     cudaError_t e;
     {
       PhaseScope ps(kPhasePack, s);
@@ -618,6 +641,12 @@ fmm_status gemm_core(const Plan& pl, int64_t m, int64_t n, int64_t k, float alph
     sb.out_hi = b_hi;
     sb.out_lo = b_lo;
     sb.vec_ok = (reinterpret_cast<uintptr_t>(b.X) % 16 == 0 && b.ld % 4 == 0) ? 1 : 0;
+    if (maxbits) {
+      sb.maxbits = maxbits + pl.R * pl.panels_a;
+      sb.npanels = static_cast<int32_t>(pl.panels_b);
+      sb.panel_w = pl.tile_n;
+      sb.scale_rows = 0;
+    }
     {
       PhaseScope ps(kPhasePack, s);
       e = launch_operand_sums(sb, pl.L, true, !pl.b_mn, b.type, pl.bf16 ? 0 : 1, dev.sms, s);
@@ -647,6 +676,12 @@ fmm_status gemm_core(const Plan& pl, int64_t m, int64_t n, int64_t k, float alph
   if (st != FMM_OK) {
     delete pp;
     return st;
+  }
+  if (maxbits) {
+    pp->c.maxbits_a = maxbits;
+    pp->c.maxbits_b = maxbits + pl.R * pl.panels_a;
+    pp->c.panels_a = static_cast<int32_t>(pl.panels_a);
+    pp->c.panels_b = static_cast<int32_t>(pl.panels_b);
   }
   cudaError_t e;
   {

@@ -98,6 +98,11 @@ struct CommonParams {
   int32_t schedule;  // Schedule
   int32_t c_tma;     // write-back by TMA reductions through tmC (C rows 16-byte aligned)
   int32_t c_vec4;    // element-wise path: C rows are 16-byte aligned, vector reductions allowed
+  // power-of-two scaling of the operand sums (FP16 variant), else null: panel maxima of the
+  // A-operand sums per (product, tile row) and of the B-operand sums per (product, tile column)
+  const unsigned int* maxbits_a;
+  const unsigned int* maxbits_b;
+  int32_t panels_a, panels_b;
   ProductDests prod[kMaxProducts];
 };
 
@@ -139,7 +144,24 @@ struct SumParams {
   float* out_f32;      // terms == 0: the sums are stored unrounded in FP32 here
   int32_t terms;       // 3: split hi/lo, 1: single rounding, 0: FP32
   int32_t vec_ok;      // X base and ldx allow vector loads
+  // power-of-two scaling (FP16 operands): per (product, panel) maximum |sum| as float bits;
+  // panels are panel_w stored rows (scale_rows) or panel_w stored columns
+  unsigned int* maxbits;
+  int32_t npanels;
+  int32_t panel_w;
+  int32_t scale_rows;
 };
+
+// Shift s of a panel whose largest |sum| has float bits `maxbits`: the sums are stored as
+// sum * 2^-s, which puts the panel maximum in [2^14, 2^15) (FP16 normal range, no overflow);
+// s = 0 for an all-zero panel.  The epilogue multiplies by 2^(s_A + s_B) exactly.
+__host__ __device__ inline int panel_shift(unsigned int maxbits) {
+  if (maxbits == 0) return 0;
+  int e = static_cast<int>((maxbits >> 23) & 0xffu);
+  if (e == 0) e = 1;          // subnormal maximum: treat as 2^-126
+  if (e == 0xff) return 0;    // Inf / NaN: leave unscaled
+  return (e - 127) - 14;
+}
 
 // Grouped raster of the tile grid: 8 tile-rows at a time, column-major inside the group, so
 // that concurrently running CTAs share operand panels in L2.
@@ -280,9 +302,14 @@ __device__ __forceinline__ bool epilogue_role(const CommonParams& p, uint8_t* ep
     decode_item(item, p, r, tm, tn);
     const ProductDests& pd = p.prod[r];
     const int row0 = tm * kBM + q * 32;
-    const int row = row0 + lane;
+    // undo the operand scaling of this (product, tile) exactly: 2^(s_A + s_B)
+    const int shift = p.maxbits_a ? panel_shift(p.maxbits_a[r * p.panels_a + tm]) +
+                                        panel_shift(p.maxbits_b[r * p.panels_b + tn])
+                                  : 0;
+    // destinations are grouped by the sign of W[c, r] (coef = alpha * W[c, r])
+    auto wneg = [&](const DestEntry& de) { return ((de.coef < 0.f) != (p.alpha < 0.f)) ? 1 : 0; };
     bool has_sign[2] = {false, false};
-    for (int d = 0; d < pd.count; ++d) has_sign[pd.d[d].coef < 0.f ? 1 : 0] = true;
+    for (int d = 0; d < pd.count; ++d) has_sign[wneg(pd.d[d])] = true;
 #pragma unroll 1
     for (int c = 0; c < BN; c += 32) {
       float v[32];
@@ -293,52 +320,50 @@ __device__ __forceinline__ bool epilogue_role(const CommonParams& p, uint8_t* ep
         mbar_arrive(smem_u32(&acc_empty[acc]));
       }
       const int col0 = tn * BN + c;
-      if (p.c_tma) {
 #pragma unroll 1
-        for (int sg = 0; sg < 2; ++sg) {
-          if (!has_sign[sg]) continue;
-          const float cf = sg ? -p.alpha : p.alpha;
-          uint8_t* sb = stage_base + buf * 4096;
-          if (lane == 0) bulk_wait_group_read<1>();  // this buffer's previous reductions read it
-          __syncwarp();
+      for (int sg = 0; sg < 2; ++sg) {
+        if (!has_sign[sg]) continue;
+        const float cf = ldexpf(sg ? -p.alpha : p.alpha, shift);
+        uint8_t* sb = stage_base + buf * 4096;
+        if (lane == 0) bulk_wait_group_read<1>();  // this buffer's previous reductions read it
+        __syncwarp();
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const float4 val = make_float4(cf * v[4 * j], cf * v[4 * j + 1], cf * v[4 * j + 2],
-                                           cf * v[4 * j + 3]);
-            *reinterpret_cast<float4*>(sb + lane * 128 + ((j ^ (lane & 7)) << 4)) = val;
-          }
+        for (int j = 0; j < 8; ++j) {
+          const float4 val = make_float4(cf * v[4 * j], cf * v[4 * j + 1], cf * v[4 * j + 2],
+                                         cf * v[4 * j + 3]);
+          *reinterpret_cast<float4*>(sb + lane * 128 + ((j ^ (lane & 7)) << 4)) = val;
+        }
+        if (p.c_tma) {
           fence_proxy_async_smem();
           __syncwarp();
           if (lane == 0) {
             for (int d = 0; d < pd.count; ++d) {
               const DestEntry& de = pd.d[d];
-              if ((de.coef < 0.f ? 1 : 0) != sg) continue;
+              if (wneg(de) != sg) continue;
               tma_reduce_add_2d(&p.tmC[de.block], smem_u32(sb), col0, row0);
             }
             bulk_commit_group();
           }
-          buf ^= 1;
-        }
-      } else {
-#pragma unroll 1
-        for (int d = 0; d < pd.count; ++d) {
-          const DestEntry de = pd.d[d];
-          if (row >= de.rows || col0 >= de.cols) continue;
-          float* dst = p.C + de.offset + static_cast<int64_t>(row) * p.ldc + col0;
-          const float cf = de.coef;
-          if (p.c_vec4 && col0 + 32 <= de.cols) {
-            float4* d4 = reinterpret_cast<float4*>(dst);
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-              atomicAdd(d4 + j, make_float4(cf * v[4 * j], cf * v[4 * j + 1], cf * v[4 * j + 2],
-                                            cf * v[4 * j + 3]));
-          } else {
-            const int lim = de.cols - col0;
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (j < lim) atomicAdd(dst + j, cf * v[j]);
+        } else {
+          // C rows not 16-byte aligned: read the staged 32 x 32 block back transposed, so
+          // that lane j adds column col0 + j and every instruction covers 32 consecutive
+          // floats of one row.
+          __syncwarp();
+          for (int d = 0; d < pd.count; ++d) {
+            const DestEntry de = pd.d[d];
+            if (wneg(de) != sg) continue;
+            if (col0 + lane >= de.cols) continue;
+            float* dst = p.C + de.offset + static_cast<int64_t>(row0) * p.ldc + col0 + lane;
+            const int nrows = min(32, de.rows - row0);
+#pragma unroll 4
+            for (int i = 0; i < nrows; ++i) {
+              const float x = *reinterpret_cast<const float*>(sb + i * 128 + (((lane >> 2) ^ (i & 7)) << 4) +
+                                                              ((lane & 3) << 2));
+              atomicAdd(dst + static_cast<int64_t>(i) * p.ldc, x);
+            }
           }
         }
+        buf ^= 1;
       }
     }
   }

@@ -88,6 +88,33 @@ __device__ __forceinline__ void store_sum(const SumParams& p, int64_t o, const f
   }
 }
 
+// Hand one group of EPT sums of product r to its destination: store it (SCALE 0), fold its
+// largest magnitude into the panel maximum (SCALE 1), or store it scaled by 2^-s (SCALE 2).
+template <int SCALE, int TERMS, int OUT16, int EPT>
+__device__ __forceinline__ void emit(const SumParams& p, int r, int64_t i, int64_t l0, int64_t o,
+                                     float (&acc)[EPT]) {
+  if (SCALE == 0) {
+    store_sum<TERMS, OUT16, EPT>(p, o, acc);
+    return;
+  }
+  const int panel = static_cast<int>((p.scale_rows ? i : l0) / p.panel_w);
+  if (SCALE == 1) {
+    float mx = 0.f;
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) mx = fmaxf(mx, fabsf(acc[e]));
+    const unsigned bits = __float_as_uint(mx);
+    const unsigned active = __activemask();
+    const unsigned same = __match_any_sync(active, panel);
+    const unsigned red = __reduce_max_sync(same, bits);
+    if ((threadIdx.x & 31) == __ffs(same) - 1) atomicMax(&p.maxbits[r * p.npanels + panel], red);
+    return;
+  }
+  const int sft = panel_shift(p.maxbits[r * p.npanels + panel]);
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) acc[e] = ldexpf(acc[e], -sft);
+  store_sum<TERMS, OUT16, EPT>(p, o, acc);
+}
+
 template <typename T, int EPT>
 __device__ __forceinline__ void load_group(const SumParams& p, const T* X, int64_t gr, int64_t gc,
                                            int64_t l0, float (&v)[EPT]) {
@@ -117,7 +144,7 @@ __device__ __forceinline__ void load_group(const SumParams& p, const T* X, int64
   }
 }
 
-template <typename T, int OUT16, int L, bool IS_B, bool TRANSQ, int TERMS, int EPT>
+template <typename T, int OUT16, int L, bool IS_B, bool TRANSQ, int TERMS, int EPT, int SCALE>
 __global__ void __launch_bounds__(256) operand_sums_kernel(const __grid_constant__ SumParams p) {
   constexpr int G = 1 << L;
   const T* X = static_cast<const T*>(p.X);
@@ -131,7 +158,7 @@ __global__ void __launch_bounds__(256) operand_sums_kernel(const __grid_constant
     if (L == 0) {
       float v[EPT];
       load_group<T, EPT>(p, X, i, l0, l0, v);
-      store_sum<TERMS, OUT16, EPT>(p, orow, v);
+      emit<SCALE, TERMS, OUT16, EPT>(p, 0, i, l0, orow, v);
     } else if (L == 1) {
       float v[4][EPT];
 #pragma unroll
@@ -151,7 +178,7 @@ __global__ void __launch_bounds__(256) operand_sums_kernel(const __grid_constant
             if (c < 0) acc[e] -= v[q][e];
           }
         }
-        store_sum<TERMS, OUT16, EPT>(p, r * p.prod_stride + orow, acc);
+        emit<SCALE, TERMS, OUT16, EPT>(p, r, i, l0, r * p.prod_stride + orow, acc);
       }
     } else {
       // source (q1, q2) is block (2*(q1/2) + q2/2, 2*(q1%2) + q2%2) of the 4 x 4 grid
@@ -192,7 +219,7 @@ __global__ void __launch_bounds__(256) operand_sums_kernel(const __grid_constant
               if (c < 0) acc[e] -= S[q2][e];
             }
           }
-          store_sum<TERMS, OUT16, EPT>(p, (r1 * 7 + r2) * p.prod_stride + orow, acc);
+          emit<SCALE, TERMS, OUT16, EPT>(p, r1 * 7 + r2, i, l0, (r1 * 7 + r2) * p.prod_stride + orow, acc);
         }
       }
     }
@@ -225,22 +252,22 @@ __global__ void debug_wait_kernel(unsigned* err, uint64_t timeout_ns) {
 }
 
 // ------------------------------------------------------------------ launchers
-template <typename T, int OUT16, int L, bool IS_B, bool TQ, int TERMS>
+template <typename T, int OUT16, int L, bool IS_B, bool TQ, int TERMS, int SCALE = 0>
 static cudaError_t launch_sums_t(const SumParams& p, int num_sms, cudaStream_t s) {
   constexpr int EPT = L == 2 ? 4 : 8;
   const int64_t total = p.hr * ((p.hc + EPT - 1) / EPT);
   if (total == 0) return cudaSuccess;
   const int grid = static_cast<int>(std::min<int64_t>((total + 255) / 256, int64_t(num_sms) * 16));
-  operand_sums_kernel<T, OUT16, L, IS_B, TQ, TERMS, EPT><<<grid, 256, 0, s>>>(p);
+  operand_sums_kernel<T, OUT16, L, IS_B, TQ, TERMS, EPT, SCALE><<<grid, 256, 0, s>>>(p);
   return cudaGetLastError();
 }
 
-template <typename T, int OUT16, bool IS_B, bool TQ, int TERMS>
+template <typename T, int OUT16, bool IS_B, bool TQ, int TERMS, int SCALE = 0>
 static cudaError_t launch_sums_l(const SumParams& p, int levels, int num_sms, cudaStream_t s) {
   switch (levels) {
-    case 0: return launch_sums_t<T, OUT16, 0, IS_B, TQ, TERMS>(p, num_sms, s);
-    case 1: return launch_sums_t<T, OUT16, 1, IS_B, TQ, TERMS>(p, num_sms, s);
-    case 2: return launch_sums_t<T, OUT16, 2, IS_B, TQ, TERMS>(p, num_sms, s);
+    case 0: return launch_sums_t<T, OUT16, 0, IS_B, TQ, TERMS, SCALE>(p, num_sms, s);
+    case 1: return launch_sums_t<T, OUT16, 1, IS_B, TQ, TERMS, SCALE>(p, num_sms, s);
+    case 2: return launch_sums_t<T, OUT16, 2, IS_B, TQ, TERMS, SCALE>(p, num_sms, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -257,8 +284,13 @@ static cudaError_t launch_sums_b(const SumParams& p, int levels, int in_type, in
   }
   if (in_type == kInBF16 && p.terms == 1 && !out16)
     return launch_sums_l<__nv_bfloat16, 0, IS_B, TQ, 1>(p, levels, num_sms, s);
-  if (in_type == kInF16 && p.terms == 1 && out16)
-    return launch_sums_l<__half, 1, IS_B, TQ, 1>(p, levels, num_sms, s);
+  if (in_type == kInF16 && p.terms == 1 && out16) {
+    if (!p.maxbits) return launch_sums_l<__half, 1, IS_B, TQ, 1>(p, levels, num_sms, s);
+    // two passes: panel maxima, then the sums scaled by 2^-s (maxbits zeroed by the caller)
+    cudaError_t e = launch_sums_l<__half, 1, IS_B, TQ, 1, 1>(p, levels, num_sms, s);
+    if (e != cudaSuccess) return e;
+    return launch_sums_l<__half, 1, IS_B, TQ, 1, 2>(p, levels, num_sms, s);
+  }
   return cudaErrorInvalidValue;
 }
 

@@ -44,8 +44,10 @@ def tolerance(variant, levels, k):
     kk = max(k, 1)
     if variant == "split3":
         return max(1e-6, 8 * 2.0 ** -17 * 3 ** levels / math.sqrt(kk))
-    if variant == "bf16" and levels == 0:
+    if variant in ("bf16", "f16") and levels == 0:
         return 1e-6  # inputs exactly representable, FP32 accumulation only
+    if variant == "f16":
+        return 4 * 2.0 ** -11 * 3 ** levels / math.sqrt(kk)  # FP16: 11-bit significand
     return 4 * U_BF16 * 3 ** levels / math.sqrt(kk)
 
 
@@ -59,7 +61,7 @@ def _to_device(X, ld_pad, dtype):
 def run(m, n, k, levels, variant="split3", dist="uniform", seed=0, alpha=1.0, beta=0.0,
         tile_n=0, pads=(0, 0, 0), c_fill=None, rows=None, schedule="auto", algo="auto"):
     A, B = synth.problem(m, n, k, seed, dist)
-    in_dtype = torch.bfloat16 if variant == "bf16" else torch.float32
+    in_dtype = {"bf16": torch.bfloat16, "f16": torch.float16}.get(variant, torch.float32)
     Ad = _to_device(A, pads[0], in_dtype)
     Bd = _to_device(B, pads[1], in_dtype)
     C0 = None
@@ -74,12 +76,12 @@ def run(m, n, k, levels, variant="split3", dist="uniform", seed=0, alpha=1.0, be
              schedule=schedule, algo=algo)
     fmm.device_status()
     C = Cd.cpu().numpy().astype(np.float64)
-    if variant == "bf16":
-        # the oracle sees exactly the bf16 values the GPU saw
+    if variant in ("bf16", "f16"):
+        # the oracle sees exactly the 16-bit values the GPU saw
+        code = oracle.ORC_BF16 if variant == "bf16" else oracle.ORC_F16
         Ab = Ad.cpu().contiguous().view(torch.int16).numpy().view(np.uint16)
         Bb = Bd.cpu().contiguous().view(torch.int16).numpy().view(np.uint16)
-        C64 = oracle.classical(Ab, Bb, C0, alpha, beta, rows=rows, a_code=oracle.ORC_BF16,
-                               b_code=oracle.ORC_BF16)
+        C64 = oracle.classical(Ab, Bb, C0, alpha, beta, rows=rows, a_code=code, b_code=code)
         An = float(np.linalg.norm(Ad.float().cpu().numpy()))
         Bn = float(np.linalg.norm(Bd.float().cpu().numpy()))
     else:
@@ -93,7 +95,7 @@ def run(m, n, k, levels, variant="split3", dist="uniform", seed=0, alpha=1.0, be
 
 
 # ------------------------------------------------------------ exact integers
-@pytest.mark.parametrize("variant", ["split3", "plain_bf16", "bf16"])
+@pytest.mark.parametrize("variant", ["split3", "plain_bf16", "bf16", "f16"])
 @pytest.mark.parametrize("levels", [0, 1, 2])
 def test_int16_cube_bit_exact(variant, levels):
     C, C64, _, _ = run(16, 16, 16, levels, variant, dist="int", seed=1)
@@ -223,7 +225,7 @@ def test_512_cube_one_level_split3_within_1e6():
     assert err <= 1e-6, err
 
 
-@pytest.mark.parametrize("variant", ["split3", "plain_bf16", "bf16"])
+@pytest.mark.parametrize("variant", ["split3", "plain_bf16", "bf16", "f16"])
 @pytest.mark.parametrize("levels", [0, 1, 2])
 @pytest.mark.parametrize("m,n,k", [(1, 1, 1), (7, 13, 5), (130, 70, 300), (257, 129, 1000),
                                    (640, 384, 96)])
@@ -241,6 +243,20 @@ def test_alpha_beta_and_padded_leading_dims(levels):
     assert err <= tolerance("split3", levels, 150), err
 
 
+@pytest.mark.parametrize("levels", [0, 1, 2])
+@pytest.mark.parametrize("pad_c", [0, 1])
+def test_negative_alpha_bit_exact(levels, pad_c):
+    """alpha < 0 on both write-back paths (TMA reductions for aligned C, element-wise for
+    unaligned C)."""
+    A, B = synth.problem(136, 264, 72, 91, "int")
+    C0 = synth.small_int((136, 264), 92)
+    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    Cd = _to_device(C0, pad_c, torch.float32)
+    fmm.gemm(Ad, Bd, Cd, alpha=-2.0, beta=3.0, levels=levels)
+    fmm.device_status()
+    np.testing.assert_array_equal(Cd.cpu().numpy(), oracle.classical(A, B, C0, -2.0, 3.0))
+
+
 def test_beta_zero_does_not_read_c():
     C, C64, An, Bn = run(130, 140, 150, 1, "split3", seed=6, c_fill=float("nan"))
     assert np.all(np.isfinite(C))
@@ -254,6 +270,41 @@ def test_k_zero_scales_c():
     fmm.gemm(A, B, Cd, alpha=1.0, beta=2.5, levels=1)
     fmm.device_status()
     assert torch.all(Cd == 2.5)
+
+
+@pytest.mark.parametrize("levels", [0, 1, 2])
+@pytest.mark.parametrize("tile_n", [128, 256])
+def test_f16_scaled_int_ragged_bit_exact(levels, tile_n):
+    """Power-of-two scaling is exact: integer products stay bit-exact through FP16."""
+    C, C64, _, _ = run(300, 520, 200, levels, "f16", dist="int", seed=77, tile_n=tile_n)
+    np.testing.assert_array_equal(C, C64)
+
+
+@pytest.mark.parametrize("levels", [1, 2])
+def test_f16_scaled_badly_scaled_inputs(levels):
+    """Rows of A / columns of B spread over 10^-3..10^3: the per-panel shifts keep every
+    operand sum in FP16's normal range."""
+    C, C64, An, Bn = run(512, 512, 512, levels, "f16", dist="badly_scaled", seed=78)
+    assert np.all(np.isfinite(C))
+    err = oracle.normwise_error(C, C64, An, Bn)
+    assert err <= tolerance("f16", levels, 512), err
+
+
+def test_f16_large_values_do_not_overflow():
+    """Operand sums of FP16 inputs near 2^15 exceed FP16's range unscaled (65504)."""
+    A = (synth.uniform((256, 256), 80) * 30000.0).astype(np.float32)
+    B = (synth.uniform((256, 256), 81) * 30000.0).astype(np.float32)
+    Ad = torch.from_numpy(A).half().cuda()
+    Bd = torch.from_numpy(B).half().cuda()
+    C = fmm.gemm(Ad, Bd, levels=2, variant="f16")
+    fmm.device_status()
+    Ab = Ad.cpu().view(torch.int16).numpy().view(np.uint16)
+    Bb = Bd.cpu().view(torch.int16).numpy().view(np.uint16)
+    C64 = oracle.classical(Ab, Bb, a_code=oracle.ORC_F16, b_code=oracle.ORC_F16)
+    Cn = C.cpu().numpy()
+    assert np.all(np.isfinite(Cn))
+    err = oracle.normwise_error(Cn, C64, float(Ad.float().norm()), float(Bd.float().norm()))
+    assert err <= tolerance("f16", 2, 256), err
 
 
 def test_badly_scaled_two_level():
