@@ -155,6 +155,55 @@ fmm_status fmm_gemm_backward(int64_t m, int64_t n, int64_t k,
                              void* workspace, size_t ws_bytes, void* stream);
 size_t fmm_workspace_size_backward(int64_t m, int64_t n, int64_t k, int levels, int variant);
 
+/* ------------------------------------------------------------------ batching
+ * Many independent, unevenly sized products C_p = alpha_p A_p B_p + beta_p C_p in one
+ * persistent tensor-core launch per tile width.  The paper batches instances of one
+ * product by variant on blockIdx.z (Section 3.3); here every (problem, Strassen
+ * product, output tile) is one item of a single work list.
+ *
+ * The Strassen level and tile width of each problem come from a tuning table: size
+ * class i holds the problems with min(m, n, k) <= max_dim[i] (classes in increasing
+ * order; larger problems fall in the last class). */
+typedef struct fmm_tune_table {
+    int count;            /* classes in use, 1..8 */
+    int64_t max_dim[8];   /* upper bound of min(m, n, k) for class i */
+    int levels[8];        /* Strassen levels for class i (0, 1 or 2) */
+    int tile_n[8];        /* output tile width for class i: 128, 256 or 0 (automatic) */
+} fmm_tune_table;
+
+/* The built-in table (measured on GB300 with the split-BF16 arithmetic). */
+void fmm_tune_default(fmm_tune_table* out);
+/* Levels and tile width the table assigns to an m x n x k problem (NULL = built-in). */
+fmm_status fmm_tune_select(const fmm_tune_table* tune, int64_t m, int64_t n, int64_t k,
+                           int* levels, int* tile_n);
+
+/* A batched plan holds, in the caller's workspace, the parameter blocks of every
+ * problem (tensor maps, destination tables) and the work list.  Creating it uploads
+ * them synchronously; executing it only launches kernels on `stream` (no host
+ * synchronisation, no allocation, no copies), so an execution can be captured in a
+ * CUDA graph and replayed while the plan, its workspace and the operands live.
+ * Arrays are host arrays of length `count`; A, B, C entries are device pointers.
+ * The workspace (>= 256-byte aligned) must hold fmm_batched_workspace_size() bytes. */
+typedef struct fmm_batched_plan fmm_batched_plan;
+size_t fmm_batched_workspace_size(int count, const int64_t* m, const int64_t* n,
+                                  const int64_t* k, int variant, const fmm_tune_table* tune);
+fmm_status fmm_batched_plan_create(int count, const int64_t* m, const int64_t* n,
+                                   const int64_t* k, const float* alpha,
+                                   const void* const* A, const int64_t* lda,
+                                   const void* const* B, const int64_t* ldb,
+                                   const float* beta, float* const* C, const int64_t* ldc,
+                                   int variant, const fmm_tune_table* tune,
+                                   void* workspace, size_t ws_bytes, fmm_batched_plan** plan);
+fmm_status fmm_batched_plan_execute(const fmm_batched_plan* plan, void* stream);
+void fmm_batched_plan_destroy(fmm_batched_plan* plan);
+/* Plan, execute once on `stream` and release the plan. */
+fmm_status fmm_gemm_batched(int count, const int64_t* m, const int64_t* n, const int64_t* k,
+                            const float* alpha, const void* const* A, const int64_t* lda,
+                            const void* const* B, const int64_t* ldb, const float* beta,
+                            float* const* C, const int64_t* ldc, int variant,
+                            const fmm_tune_table* tune, void* workspace, size_t ws_bytes,
+                            void* stream);
+
 /* Last error message of the calling host thread ("" when none). */
 const char* fmm_last_error(void);
 

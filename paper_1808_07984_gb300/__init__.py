@@ -31,6 +31,12 @@ class FmmError(RuntimeError):
         self.status = status
 
 
+class TuneTable(ctypes.Structure):
+    """fmm_tune_table: class i holds problems with min(m, n, k) <= max_dim[i]."""
+    _fields_ = [("count", ctypes.c_int), ("max_dim", ctypes.c_int64 * 8),
+                ("levels", ctypes.c_int * 8), ("tile_n", ctypes.c_int * 8)]
+
+
 class _Options(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int), ("tile_n", ctypes.c_int), ("num_ctas", ctypes.c_int),
                 ("schedule", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
@@ -71,6 +77,24 @@ def load() -> ctypes.CDLL:
                                     i32, i32, vp, sz, vp]
     L.fmm_workspace_size_backward.restype = sz
     L.fmm_workspace_size_backward.argtypes = [i64, i64, i64, i32, i32]
+    L.fmm_tune_default.restype = None
+    L.fmm_tune_default.argtypes = [ctypes.POINTER(TuneTable)]
+    L.fmm_tune_select.restype = i32
+    L.fmm_tune_select.argtypes = [ctypes.POINTER(TuneTable), i64, i64, i64,
+                                  ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    arr64 = ctypes.POINTER(ctypes.c_int64)
+    arrf = ctypes.POINTER(ctypes.c_float)
+    arrp = ctypes.POINTER(ctypes.c_void_p)
+    L.fmm_batched_workspace_size.restype = sz
+    L.fmm_batched_workspace_size.argtypes = [i32, arr64, arr64, arr64, i32, ctypes.POINTER(TuneTable)]
+    L.fmm_batched_plan_create.restype = i32
+    L.fmm_batched_plan_create.argtypes = [i32, arr64, arr64, arr64, arrf, arrp, arr64, arrp, arr64,
+                                          arrf, arrp, arr64, i32, ctypes.POINTER(TuneTable), vp, sz,
+                                          ctypes.POINTER(ctypes.c_void_p)]
+    L.fmm_batched_plan_execute.restype = i32
+    L.fmm_batched_plan_execute.argtypes = [vp, vp]
+    L.fmm_batched_plan_destroy.restype = None
+    L.fmm_batched_plan_destroy.argtypes = [vp]
     L.fmm_last_error.restype = ctypes.c_char_p
     L.fmm_last_error.argtypes = []
     L.fmm_device_status.restype = i32
@@ -250,6 +274,124 @@ def linear(A, B, levels: int = 1, variant="split3"):
     if _linear_fn is None:
         _linear_fn = _make_linear_fn()
     return _linear_fn.apply(A, B, levels, variant)
+
+
+def tune_table(classes=None):
+    """TuneTable from [(max_dim, levels, tile_n), ...] (None = the library's built-in table),
+    or from a table dict written by paper_1808_07984_gb300.autotune."""
+    t = TuneTable()
+    if classes is None:
+        load().fmm_tune_default(ctypes.byref(t))
+        return t
+    if isinstance(classes, dict):
+        classes = [(c["max_dim"], c["levels"], c["tile_n"]) for c in classes["classes"]]
+    if not 1 <= len(classes) <= 8:
+        raise FmmError(1, "a tune table holds 1 to 8 classes")
+    t.count = len(classes)
+    for i, (d, lv, tn) in enumerate(classes):
+        t.max_dim[i] = min(int(d), 2 ** 63 - 1)
+        t.levels[i] = int(lv)
+        t.tile_n[i] = int(tn)
+    return t
+
+
+def tune_select(m, n, k, tune=None):
+    """(levels, tile_n) the table assigns to an m x n x k problem."""
+    t = tune_table(tune) if not isinstance(tune, TuneTable) else tune
+    lv, tn = ctypes.c_int(), ctypes.c_int()
+    _check(load().fmm_tune_select(ctypes.byref(t), m, n, k, ctypes.byref(lv), ctypes.byref(tn)))
+    return lv.value, tn.value
+
+
+def _default_tune():
+    path = os.environ.get("FMM_TUNE_FILE")
+    if path and os.path.exists(path):
+        from . import autotune
+        return tune_table(autotune.load(path))
+    return tune_table(None)
+
+
+class BatchedPlan:
+    """Many products C_p = alpha_p A_p @ B_p + beta_p C_p in one persistent tensor-core
+    launch per tile width.  Creating the plan uploads the per-problem parameter blocks into
+    the workspace; execute() only launches kernels, so it can be captured in a CUDA graph
+    (keep the plan, its workspace and the tensors alive while the graph is used)."""
+
+    def __init__(self, As, Bs, Cs, alphas=None, betas=None, variant="split3", tune=None,
+                 workspace=None):
+        import torch
+        L = load()
+        self.variant = _variant(variant)
+        cnt = len(As)
+        if not (len(Bs) == len(Cs) == cnt):
+            raise FmmError(1, "A, B and C lists differ in length")
+        want = getattr(torch, _IN_DTYPE[self.variant])
+        for X in list(As) + list(Bs):
+            if X.dtype != want or not X.is_cuda or (X.numel() and X.stride(1) != 1):
+                raise FmmError(1, f"operands must be {want} CUDA tensors with contiguous rows")
+        for X in Cs:
+            if X.dtype != torch.float32 or not X.is_cuda or (X.numel() and X.stride(1) != 1):
+                raise FmmError(1, "C must be float32 CUDA tensors with contiguous rows")
+        I64 = ctypes.c_int64 * cnt
+        F32 = ctypes.c_float * cnt
+        VP = ctypes.c_void_p * cnt
+        self._m = I64(*[a.shape[0] for a in As])
+        self._n = I64(*[b.shape[1] for b in Bs])
+        self._k = I64(*[a.shape[1] for a in As])
+        self._alpha = F32(*(alphas if alphas is not None else [1.0] * cnt))
+        self._beta = F32(*(betas if betas is not None else [0.0] * cnt))
+        self._A = VP(*[a.data_ptr() for a in As])
+        self._B = VP(*[b.data_ptr() for b in Bs])
+        self._C = VP(*[c.data_ptr() for c in Cs])
+        self._lda = I64(*[max(a.stride(0), 1) for a in As])
+        self._ldb = I64(*[max(b.stride(0), 1) for b in Bs])
+        self._ldc = I64(*[max(c.stride(0), 1) for c in Cs])
+        self._tune = tune if isinstance(tune, TuneTable) else (tune_table(tune) if tune is not None
+                                                               else _default_tune())
+        ws = L.fmm_batched_workspace_size(cnt, self._m, self._n, self._k, self.variant,
+                                          ctypes.byref(self._tune))
+        if ws == ctypes.c_size_t(-1).value:
+            _check(3)
+        if workspace is None:
+            workspace = torch.empty(max(ws, 256), dtype=torch.uint8, device=As[0].device)
+        self.workspace = workspace
+        self._keep = (As, Bs, Cs)
+        handle = ctypes.c_void_p()
+        _check(L.fmm_batched_plan_create(cnt, self._m, self._n, self._k, self._alpha, self._A,
+                                         self._lda, self._B, self._ldb, self._beta, self._C,
+                                         self._ldc, self.variant, ctypes.byref(self._tune),
+                                         workspace.data_ptr(), workspace.numel(),
+                                         ctypes.byref(handle)))
+        self._handle = handle
+
+    def execute(self, stream=None):
+        _check(load().fmm_batched_plan_execute(self._handle, _stream_handle(stream)))
+
+    def close(self):
+        if getattr(self, "_handle", None):
+            load().fmm_batched_plan_destroy(self._handle)
+            self._handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gemm_batched(As, Bs, Cs=None, alphas=None, betas=None, variant="split3", tune=None,
+                 workspace=None, stream=None):
+    """C_p = alpha_p A_p @ B_p + beta_p C_p for every p, one persistent launch per tile width."""
+    import torch
+    if Cs is None:
+        Cs = [torch.empty((a.shape[0], b.shape[1]), dtype=torch.float32, device=a.device)
+              for a, b in zip(As, Bs)]
+        betas = [0.0] * len(As)
+    plan = BatchedPlan(As, Bs, Cs, alphas, betas, variant, tune, workspace)
+    plan.execute(stream)
+    torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+    plan.close()
+    return Cs
 
 
 def device_status(stream=None):

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <atomic>
 #include <cstdio>
 #include <cstring>
@@ -543,11 +544,9 @@ fmm_status gemm_hybrid(const Plan& pl, int64_t m, int64_t n, int64_t k, float al
   return FMM_OK;
 }
 
-// C (m x n) = alpha * A' B' + beta * C with the operand layouts of `pl`.  `a` stores A' as
-// m x k (K-major) or k x m (pl.a_mn); `b` stores B' as k x n (pl.b_mn) or n x k.
-fmm_status gemm_core(const Plan& pl, int64_t m, int64_t n, int64_t k, float alpha, Operand a,
-                     Operand b, float beta, float* C, int64_t ldc, void* ws, size_t ws_bytes,
-                     void* stream, const fmm_options* opt) {
+// Argument checks of one product (no CUDA calls).
+fmm_status validate_core(const Plan& pl, int64_t m, int64_t n, int64_t k, Operand a, Operand b,
+                         float* C, int64_t ldc, void* ws, size_t ws_bytes) {
   const int64_t a_rows = pl.a_mn ? k : m, a_cols = pl.a_mn ? m : k;
   const int64_t b_rows = pl.b_mn ? k : n, b_cols = pl.b_mn ? n : k;
   if (a.ld < std::max<int64_t>(1, a_cols) || b.ld < std::max<int64_t>(1, b_cols) ||
@@ -573,90 +572,84 @@ fmm_status gemm_core(const Plan& pl, int64_t m, int64_t n, int64_t k, float alph
       (reinterpret_cast<uintptr_t>(a.X) % 16 != 0 || reinterpret_cast<uintptr_t>(b.X) % 16 != 0 ||
        a.ld % 4 != 0 || b.ld % 4 != 0))
     return fail(FMM_ERR_ALIGN, "the fused algorithm needs 16-byte aligned A and B and lda, ldb multiples of 4");
-  DeviceInfo dev;
-  fmm_status st = device_info(dev);
-  if (st != FMM_OK) return st;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return FMM_OK;
+}
 
-  // beta first: C <- beta * C (beta == 0: C is not read)
-  if (beta != 1.0f) {
-    PhaseScope ps(kPhaseBeta, s);
-    cudaError_t e = launch_beta(C, m, n, ldc, beta, dev.sms, s);
-    if (e != cudaSuccess) return cuda_fail(e, "beta pass");
-  }
-  if (k == 0 || alpha == 0.0f) return FMM_OK;
-  if (pl.algo == FMM_ALGO_FUSED) return gemm_fused(pl, m, n, k, alpha, a.X, a.ld, b.X, b.ld, C, ldc, dev, opt, s);
-  if (pl.algo == FMM_ALGO_HYBRID)
-    return gemm_hybrid(pl, m, n, k, alpha, a.X, a.ld, b.X, b.ld, C, ldc, ws, dev, opt, s);
+// Everything one packed product launches, prepared on the host: the beta pass, the two
+// operand-sum passes and the tensor-core kernel's parameter block.
+struct PackedJob {
+  Plan pl;
+  int64_t m = 0, n = 0, k = 0, ldc = 0;
+  float alpha = 1.f, beta = 0.f;
+  float* C = nullptr;
+  int a_type = kInF32, b_type = kInF32;
+  SumParams sa, sb;
+  unsigned* maxbits = nullptr;
+  int grid = 0;
+  bool has_work = false;  // k > 0 and alpha != 0
+  PackedParams params;
+};
 
-  const std::vector<Product> prods = make_products(pl.L);
+fmm_status prepare_packed(const Plan& pl, int64_t m, int64_t n, int64_t k, float alpha, Operand a,
+                          Operand b, float beta, float* C, int64_t ldc, void* ws, const DeviceInfo& dev,
+                          const fmm_options* opt, PackedJob& job) {
+  job.pl = pl;
+  job.m = m; job.n = n; job.k = k; job.ldc = ldc;
+  job.alpha = alpha; job.beta = beta; job.C = C;
+  job.a_type = a.type; job.b_type = b.type;
+  job.has_work = m > 0 && n > 0 && k > 0 && alpha != 0.0f;
+  std::memset(&job.sa, 0, sizeof job.sa);
+  std::memset(&job.sb, 0, sizeof job.sb);
+  std::memset(&job.params, 0, sizeof job.params);
+  if (!job.has_work) return FMM_OK;
+  const int64_t a_rows = pl.a_mn ? k : m, a_cols = pl.a_mn ? m : k;
+  const int64_t b_rows = pl.b_mn ? k : n, b_cols = pl.b_mn ? n : k;
   uint8_t* wsb = static_cast<uint8_t*>(ws);
   uint16_t* a_hi = reinterpret_cast<uint16_t*>(wsb);
   uint16_t* b_hi = reinterpret_cast<uint16_t*>(wsb + pl.a_bytes);
   uint16_t* a_lo = pl.terms == 3 ? reinterpret_cast<uint16_t*>(wsb + pl.a_bytes + pl.b_bytes) : nullptr;
   uint16_t* b_lo = pl.terms == 3 ? reinterpret_cast<uint16_t*>(wsb + 2 * pl.a_bytes + pl.b_bytes) : nullptr;
-  unsigned* maxbits = pl.scaled ? reinterpret_cast<unsigned*>(wsb + pl.a_bytes + pl.b_bytes) : nullptr;
-  if (maxbits) {
-    cudaError_t e = cudaMemsetAsync(maxbits, 0, pl.scale_bytes, s);
-    if (e != cudaSuccess) return cuda_fail(e, "clearing the panel maxima");
+  job.maxbits = pl.scaled ? reinterpret_cast<unsigned*>(wsb + pl.a_bytes + pl.b_bytes) : nullptr;
+
+  SumParams& sa = job.sa;
+  sa.X = a.X;
+  sa.ldx = a.ld;
+  sa.rows = a_rows;
+  sa.cols = a_cols;
+  sa.hr = pl.a_mn ? pl.hk : pl.hm;
+  sa.hc = pl.a_mn ? pl.hm : pl.hk;
+  sa.ld_out = pl.lda_w;
+  sa.prod_stride = sa.hr * pl.lda_w;
+  sa.out_hi = a_hi;
+  sa.out_lo = a_lo;
+  sa.terms = pl.terms;
+  sa.vec_ok = (reinterpret_cast<uintptr_t>(a.X) % 16 == 0 && a.ld % 4 == 0) ? 1 : 0;
+  SumParams& sb = job.sb;
+  sb = sa;
+  sb.X = b.X;
+  sb.ldx = b.ld;
+  sb.rows = b_rows;
+  sb.cols = b_cols;
+  sb.hr = pl.b_mn ? pl.hk : pl.hn;
+  sb.hc = pl.b_mn ? pl.hn : pl.hk;
+  sb.ld_out = pl.ldb_w;
+  sb.prod_stride = sb.hr * pl.ldb_w;
+  sb.out_hi = b_hi;
+  sb.out_lo = b_lo;
+  sb.vec_ok = (reinterpret_cast<uintptr_t>(b.X) % 16 == 0 && b.ld % 4 == 0) ? 1 : 0;
+  if (job.maxbits) {
+    sa.maxbits = job.maxbits;
+    sa.npanels = static_cast<int32_t>(pl.panels_a);
+    sa.panel_w = kBM;
+    sa.scale_rows = 1;
+    sb.maxbits = job.maxbits + pl.R * pl.panels_a;
+    sb.npanels = static_cast<int32_t>(pl.panels_b);
+    sb.panel_w = pl.tile_n;
+    sb.scale_rows = 0;
   }
 
-  // ---- operand-sum passes (all 7^L A-operands, then all B-operands), in the stored layout
-  {
-    SumParams sa;
-    std::memset(&sa, 0, sizeof sa);
-    sa.X = a.X;
-    sa.ldx = a.ld;
-    sa.rows = a_rows;
-    sa.cols = a_cols;
-    sa.hr = pl.a_mn ? pl.hk : pl.hm;
-    sa.hc = pl.a_mn ? pl.hm : pl.hk;
-    sa.ld_out = pl.lda_w;
-    sa.prod_stride = sa.hr * pl.lda_w;
-    sa.out_hi = a_hi;
-    sa.out_lo = a_lo;
-    sa.terms = pl.terms;
-    sa.vec_ok = (reinterpret_cast<uintptr_t>(a.X) % 16 == 0 && a.ld % 4 == 0) ? 1 : 0;
-    if (maxbits) {
-      sa.maxbits = maxbits;
-      sa.npanels = static_cast<int32_t>(pl.panels_a);
-      sa.panel_w = kBM;
-      sa.scale_rows = 1;
-    }
-    cudaError_t e;
-    {
-      PhaseScope ps(kPhasePack, s);
-      e = launch_operand_sums(sa, pl.L, false, pl.a_mn, a.type, pl.bf16 ? 0 : 1, dev.sms, s);
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "operand-sum pass (A)");
-    SumParams sb = sa;
-    sb.X = b.X;
-    sb.ldx = b.ld;
-    sb.rows = b_rows;
-    sb.cols = b_cols;
-    sb.hr = pl.b_mn ? pl.hk : pl.hn;
-    sb.hc = pl.b_mn ? pl.hn : pl.hk;
-    sb.ld_out = pl.ldb_w;
-    sb.prod_stride = sb.hr * pl.ldb_w;
-    sb.out_hi = b_hi;
-    sb.out_lo = b_lo;
-    sb.vec_ok = (reinterpret_cast<uintptr_t>(b.X) % 16 == 0 && b.ld % 4 == 0) ? 1 : 0;
-    if (maxbits) {
-      sb.maxbits = maxbits + pl.R * pl.panels_a;
-      sb.npanels = static_cast<int32_t>(pl.panels_b);
-      sb.panel_w = pl.tile_n;
-      sb.scale_rows = 0;
-    }
-    {
-      PhaseScope ps(kPhasePack, s);
-      e = launch_operand_sums(sb, pl.L, true, !pl.b_mn, b.type, pl.bf16 ? 0 : 1, dev.sms, s);
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "operand-sum pass (B)");
-  }
-
-  // ---- tensor-core pass
-  PackedParams* pp = new PackedParams;
-  std::memset(pp, 0, sizeof(PackedParams));
+  PackedParams* pp = &job.params;
+  fmm_status st = FMM_OK;
   const int nb = pl.terms == 3 ? 2 : 1;
   for (int t = 0; t < nb && st == FMM_OK; ++t) {
     if (pl.a_mn)
@@ -669,28 +662,90 @@ fmm_status gemm_core(const Plan& pl, int64_t m, int64_t n, int64_t k, float alph
     else
       st = encode_3d(&pp->tmB[t], t ? b_lo : b_hi, pl.hk, pl.hn, pl.R, pl.ldb_w, kBK, pl.tile_n);
   }
+  const std::vector<Product> prods = make_products(pl.L);
   std::vector<int> live(pl.R);
   for (int r = 0; r < pl.R; ++r) live[r] = r;
-  int grid = 0;
-  if (st == FMM_OK) st = fill_common(pp->c, pl, prods, live, m, n, alpha, C, ldc, dev, opt, grid);
-  if (st != FMM_OK) {
-    delete pp;
-    return st;
-  }
-  if (maxbits) {
-    pp->c.maxbits_a = maxbits;
-    pp->c.maxbits_b = maxbits + pl.R * pl.panels_a;
+  if (st == FMM_OK) st = fill_common(pp->c, pl, prods, live, m, n, alpha, C, ldc, dev, opt, job.grid);
+  if (st != FMM_OK) return st;
+  if (job.maxbits) {
+    pp->c.maxbits_a = job.maxbits;
+    pp->c.maxbits_b = job.maxbits + pl.R * pl.panels_a;
     pp->c.panels_a = static_cast<int32_t>(pl.panels_a);
     pp->c.panels_b = static_cast<int32_t>(pl.panels_b);
   }
+  return FMM_OK;
+}
+
+// The beta pass and the operand-sum passes of a prepared job (everything before the
+// tensor-core kernel).
+fmm_status launch_passes(const PackedJob& job, const DeviceInfo& dev, cudaStream_t s) {
+  if (job.m == 0 || job.n == 0) return FMM_OK;
+  if (job.beta != 1.0f) {
+    PhaseScope ps(kPhaseBeta, s);
+    cudaError_t e = launch_beta(job.C, job.m, job.n, job.ldc, job.beta, dev.sms, s);
+    if (e != cudaSuccess) return cuda_fail(e, "beta pass");
+  }
+  if (!job.has_work) return FMM_OK;
+  const Plan& pl = job.pl;
+  if (job.maxbits) {
+    cudaError_t e = cudaMemsetAsync(job.maxbits, 0, pl.scale_bytes, s);
+    if (e != cudaSuccess) return cuda_fail(e, "clearing the panel maxima");
+  }
   cudaError_t e;
   {
-    PhaseScope ps(kPhaseTensor, s);
-    e = launch_packed(*pp, pl.tile_n, pl.terms, pl.bf16, pl.a_mn, pl.b_mn, grid, s);
+    PhaseScope ps(kPhasePack, s);
+    e = launch_operand_sums(job.sa, pl.L, false, pl.a_mn, job.a_type, pl.bf16 ? 0 : 1, dev.sms, s);
   }
-  delete pp;
-  if (e != cudaSuccess) return cuda_fail(e, "tensor-core pass");
+  if (e != cudaSuccess) return cuda_fail(e, "operand-sum pass (A)");
+  {
+    PhaseScope ps(kPhasePack, s);
+    e = launch_operand_sums(job.sb, pl.L, true, !pl.b_mn, job.b_type, pl.bf16 ? 0 : 1, dev.sms, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "operand-sum pass (B)");
   return FMM_OK;
+}
+
+// C (m x n) = alpha * A' B' + beta * C with the operand layouts of `pl`.  `a` stores A' as
+// m x k (K-major) or k x m (pl.a_mn); `b` stores B' as k x n (pl.b_mn) or n x k.
+fmm_status gemm_core(const Plan& pl, int64_t m, int64_t n, int64_t k, float alpha, Operand a,
+                     Operand b, float beta, float* C, int64_t ldc, void* ws, size_t ws_bytes,
+                     void* stream, const fmm_options* opt) {
+  fmm_status st = validate_core(pl, m, n, k, a, b, C, ldc, ws, ws_bytes);
+  if (st != FMM_OK || m == 0 || n == 0) return st;
+  DeviceInfo dev;
+  st = device_info(dev);
+  if (st != FMM_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+  if (pl.algo == FMM_ALGO_FUSED || pl.algo == FMM_ALGO_HYBRID) {
+    // beta first: C <- beta * C (beta == 0: C is not read)
+    if (beta != 1.0f) {
+      PhaseScope ps(kPhaseBeta, s);
+      cudaError_t e = launch_beta(C, m, n, ldc, beta, dev.sms, s);
+      if (e != cudaSuccess) return cuda_fail(e, "beta pass");
+    }
+    if (k == 0 || alpha == 0.0f) return FMM_OK;
+    if (pl.algo == FMM_ALGO_FUSED) return gemm_fused(pl, m, n, k, alpha, a.X, a.ld, b.X, b.ld, C, ldc, dev, opt, s);
+    return gemm_hybrid(pl, m, n, k, alpha, a.X, a.ld, b.X, b.ld, C, ldc, ws, dev, opt, s);
+  }
+
+  KernelArgs* ka = new KernelArgs;
+  std::memset(ka, 0, sizeof(KernelArgs));
+  PackedJob* job = new PackedJob;
+  st = prepare_packed(pl, m, n, k, alpha, a, b, beta, C, ldc, ws, dev, opt, *job);
+  if (st == FMM_OK) st = launch_passes(*job, dev, s);
+  if (st == FMM_OK && job->has_work) {
+    ka->one = job->params;
+    cudaError_t e;
+    {
+      PhaseScope ps(kPhaseTensor, s);
+      e = launch_packed(*ka, pl.tile_n, pl.terms, pl.bf16, pl.a_mn, pl.b_mn, job->grid, s);
+    }
+    if (e != cudaSuccess) st = cuda_fail(e, "tensor-core pass");
+  }
+  delete job;
+  delete ka;
+  return st;
 }
 
 }  // namespace
@@ -698,6 +753,26 @@ fmm_status gemm_core(const Plan& pl, int64_t m, int64_t n, int64_t k, float alph
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 
 }  // namespace fmm
+
+// Host side of a batched plan: every problem's prepared passes, and per tile width the
+// arguments of one batched tensor-core launch whose parameter blocks live in the workspace.
+struct fmm_batched_plan {
+  struct Group {
+    int tile_n = 128;
+    int grid = 0;
+    fmm::KernelArgs* args = nullptr;
+  };
+  int device = 0;
+  int terms = 3;
+  bool bf16 = true;
+  fmm::DeviceInfo dev;
+  std::vector<fmm::PackedJob*> jobs;
+  std::vector<Group> groups;
+  ~fmm_batched_plan() {
+    for (auto* j : jobs) delete j;
+    for (auto& g : groups) delete g.args;
+  }
+};
 
 using namespace fmm;
 
@@ -767,6 +842,214 @@ fmm_status fmm_gemm_backward(int64_t m, int64_t n, int64_t k, const void* A, int
     if (st != FMM_OK) return st;
   }
   return FMM_OK;
+}
+
+void fmm_tune_default(fmm_tune_table* out) {
+  if (!out) return;
+  std::memset(out, 0, sizeof *out);
+  // measured on GB300, split-BF16 arithmetic, square problems: one level wins from 4096,
+  // two levels from 16384 (see the benchmark records)
+  out->count = 3;
+  out->max_dim[0] = 3072;
+  out->levels[0] = 0;
+  out->max_dim[1] = 12288;
+  out->levels[1] = 1;
+  out->max_dim[2] = INT64_MAX;
+  out->levels[2] = 2;
+}
+
+fmm_status fmm_tune_select(const fmm_tune_table* tune, int64_t m, int64_t n, int64_t k, int* levels,
+                           int* tile_n) {
+  fmm_tune_table def;
+  if (!tune) {
+    fmm_tune_default(&def);
+    tune = &def;
+  }
+  if (tune->count < 1 || tune->count > 8) return fail(FMM_ERR_ARG, "tune table: count must be 1..8");
+  const int64_t d = std::min(m, std::min(n, k));
+  int i = 0;
+  while (i < tune->count - 1 && d > tune->max_dim[i]) ++i;
+  if (tune->levels[i] < 0 || tune->levels[i] > 2) return fail(FMM_ERR_ARG, "tune table: levels must be 0..2");
+  if (tune->tile_n[i] != 0 && tune->tile_n[i] != 128 && tune->tile_n[i] != 256)
+    return fail(FMM_ERR_ARG, "tune table: tile_n must be 0, 128 or 256");
+  if (levels) *levels = tune->levels[i];
+  if (tile_n) *tile_n = tune->tile_n[i];
+  return FMM_OK;
+}
+
+}  // extern "C"
+
+namespace fmm {
+namespace {
+
+// Per-problem plans of a batch, workspace regions laid out as
+// [parameter blocks + work-list offsets per tile width | operand sums of problem 0 | ...].
+struct BatchLayout {
+  std::vector<Plan> plans;
+  std::vector<size_t> ws_off;  // offset of each problem's operand-sum region
+  size_t desc_bytes = 0;
+  size_t total = 0;
+};
+
+fmm_status batch_layout(int count, const int64_t* m, const int64_t* n, const int64_t* k, int variant,
+                        const fmm_tune_table* tune, BatchLayout& lay) {
+  if (count < 0 || (count > 0 && (!m || !n || !k))) return fail(FMM_ERR_ARG, "bad batch arrays");
+  lay.plans.resize(count);
+  lay.ws_off.resize(count);
+  // parameter blocks (at most two tile-width groups) and item offsets
+  lay.desc_bytes = static_cast<size_t>(round_up(static_cast<int64_t>(count) * sizeof(PackedParams), 256)) +
+                   2 * static_cast<size_t>(round_up((count + 1) * 4, 256));
+  size_t off = lay.desc_bytes;
+  for (int p = 0; p < count; ++p) {
+    int levels = 0, tile_n = 0;
+    fmm_status st = fmm_tune_select(tune, m[p], n[p], k[p], &levels, &tile_n);
+    if (st != FMM_OK) return st;
+    fmm_options opt;
+    std::memset(&opt, 0, sizeof opt);
+    opt.algo = FMM_ALGO_PACKED;
+    opt.tile_n = tile_n;
+    opt.schedule = 1;  // product-major inside each problem
+    st = make_plan(m[p], n[p], k[p], levels, variant, &opt, false, true, lay.plans[p]);
+    if (st != FMM_OK) return st;
+    lay.ws_off[p] = off;
+    off += static_cast<size_t>(round_up(static_cast<int64_t>(lay.plans[p].ws), 256));
+  }
+  lay.total = off;
+  return FMM_OK;
+}
+
+}  // namespace
+}  // namespace fmm
+
+extern "C" {
+
+size_t fmm_batched_workspace_size(int count, const int64_t* m, const int64_t* n, const int64_t* k,
+                                  int variant, const fmm_tune_table* tune) {
+  BatchLayout lay;
+  if (batch_layout(count, m, n, k, variant, tune, lay) != FMM_OK) return static_cast<size_t>(-1);
+  return lay.total;
+}
+
+fmm_status fmm_batched_plan_create(int count, const int64_t* m, const int64_t* n, const int64_t* k,
+                                   const float* alpha, const void* const* A, const int64_t* lda,
+                                   const void* const* B, const int64_t* ldb, const float* beta,
+                                   float* const* C, const int64_t* ldc, int variant,
+                                   const fmm_tune_table* tune, void* workspace, size_t ws_bytes,
+                                   fmm_batched_plan** plan_out) {
+  g_last_error.clear();
+  if (!plan_out) return fail(FMM_ERR_ARG, "plan pointer is NULL");
+  *plan_out = nullptr;
+  if (count > 0 && (!alpha || !A || !lda || !B || !ldb || !beta || !C || !ldc))
+    return fail(FMM_ERR_ARG, "a batch array is NULL");
+  BatchLayout lay;
+  fmm_status st = batch_layout(count, m, n, k, variant, tune, lay);
+  if (st != FMM_OK) return st;
+  if (lay.total > 0 && (!workspace || ws_bytes < lay.total))
+    return fail(FMM_ERR_WORKSPACE, "batched workspace of " + std::to_string(lay.total) + " bytes required");
+  if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return fail(FMM_ERR_ALIGN, "workspace must be 256-byte aligned");
+  DeviceInfo dev;
+  st = device_info(dev);
+  if (st != FMM_OK) return st;
+  fmm_batched_plan* plan = new fmm_batched_plan;
+  plan->dev = dev;
+  cudaGetDevice(&plan->device);
+  uint8_t* wsb = static_cast<uint8_t*>(workspace);
+  for (int p = 0; p < count && st == FMM_OK; ++p) {
+    const Plan& pl = lay.plans[p];
+    plan->terms = pl.terms;
+    plan->bf16 = pl.bf16;
+    const Operand a{A[p], lda[p], pl.in_type}, b{B[p], ldb[p], pl.in_type};
+    void* ws = wsb + lay.ws_off[p];
+    st = validate_core(pl, m[p], n[p], k[p], a, b, C[p], ldc[p], ws, pl.ws);
+    if (st != FMM_OK) break;
+    PackedJob* job = new PackedJob;
+    plan->jobs.push_back(job);
+    st = prepare_packed(pl, m[p], n[p], k[p], alpha[p], a, b, beta[p], C[p], ldc[p], ws, dev, nullptr, *job);
+  }
+  // one batched tensor-core launch per tile width: upload parameter blocks and item offsets
+  size_t desc_off = 0;
+  const size_t item_off0 = static_cast<size_t>(round_up(static_cast<int64_t>(count) * sizeof(PackedParams), 256));
+  for (int tn : {128, 256}) {
+    if (st != FMM_OK) break;
+    std::vector<PackedParams> descs;
+    std::vector<int32_t> begin;
+    int64_t items = 0;
+    for (PackedJob* job : plan->jobs) {
+      if (!job->has_work || job->pl.tile_n != tn) continue;
+      begin.push_back(static_cast<int32_t>(items));
+      descs.push_back(job->params);
+      items += job->params.c.num_items;
+    }
+    if (descs.empty()) continue;
+    if (items >= (int64_t(1) << 31)) {
+      st = fail(FMM_ERR_ARG, "batch has too many work items");
+      break;
+    }
+    begin.push_back(static_cast<int32_t>(items));
+    PackedParams* d_desc = reinterpret_cast<PackedParams*>(wsb + desc_off);
+    int32_t* d_begin = reinterpret_cast<int32_t*>(wsb + item_off0 + (tn == 128 ? 0 : round_up((count + 1) * 4, 256)));
+    cudaError_t e = cudaMemcpy(d_desc, descs.data(), descs.size() * sizeof(PackedParams), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_begin, begin.data(), begin.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      st = cuda_fail(e, "uploading the batched parameter blocks");
+      break;
+    }
+    desc_off += descs.size() * sizeof(PackedParams);
+    fmm_batched_plan::Group g;
+    g.tile_n = tn;
+    g.args = new KernelArgs;
+    std::memset(g.args, 0, sizeof(KernelArgs));
+    g.args->many = d_desc;
+    g.args->item_begin = d_begin;
+    g.args->count = static_cast<int32_t>(descs.size());
+    g.args->batched = 1;
+    g.args->total_items = static_cast<int32_t>(items);
+    g.args->one.c.err = dev.err;
+    g.args->one.c.timeout_ns = g_timeout_ns.load();
+    g.grid = static_cast<int>(std::min<int64_t>(items, dev.sms));
+    plan->groups.push_back(g);
+  }
+  if (st != FMM_OK) {
+    delete plan;
+    return st;
+  }
+  *plan_out = plan;
+  return FMM_OK;
+}
+
+fmm_status fmm_batched_plan_execute(const fmm_batched_plan* plan, void* stream) {
+  g_last_error.clear();
+  if (!plan) return fail(FMM_ERR_ARG, "plan is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (const PackedJob* job : plan->jobs) {
+    fmm_status st = launch_passes(*job, plan->dev, s);
+    if (st != FMM_OK) return st;
+  }
+  for (const auto& g : plan->groups) {
+    cudaError_t e;
+    {
+      PhaseScope ps(kPhaseTensor, s);
+      e = launch_packed(*g.args, g.tile_n, plan->terms, plan->bf16, false, true, g.grid, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "batched tensor-core pass");
+  }
+  return FMM_OK;
+}
+
+void fmm_batched_plan_destroy(fmm_batched_plan* plan) { delete plan; }
+
+fmm_status fmm_gemm_batched(int count, const int64_t* m, const int64_t* n, const int64_t* k,
+                            const float* alpha, const void* const* A, const int64_t* lda,
+                            const void* const* B, const int64_t* ldb, const float* beta,
+                            float* const* C, const int64_t* ldc, int variant,
+                            const fmm_tune_table* tune, void* workspace, size_t ws_bytes, void* stream) {
+  fmm_batched_plan* plan = nullptr;
+  fmm_status st = fmm_batched_plan_create(count, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, variant,
+                                          tune, workspace, ws_bytes, &plan);
+  if (st != FMM_OK) return st;
+  st = fmm_batched_plan_execute(plan, stream);
+  fmm_batched_plan_destroy(plan);
+  return st;
 }
 
 const char* fmm_last_error(void) { return g_last_error.c_str(); }

@@ -135,16 +135,16 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fmm_fused_kernel(const __gri
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      if (!mma_role<kFusedBN, TERMS, S, true, false, true>(p, smem, op_full, op_empty, acc_full, acc_empty,
-                                                    tmem_base, abort_flag)) {
+      if (!mma_role<kFusedBN, TERMS, S, true, false, true>(OneProblem{&p}, smem, op_full, op_empty, acc_full,
+                                                           acc_empty, tmem_base, abort_flag, p.timeout_ns)) {
         atomicOr(p.err, kErrMmaWait);
         *abort_flag = 1;
         drain_pause(2000000ull);
       }
     }
   } else if (warp >= 4 && warp < 8) {
-    if (!epilogue_role<kFusedBN>(p, smem + Cfg::kEpiOffset, acc_full, acc_empty, tmem_base, abort_flag,
-                                 warp, lane)) {
+    if (!epilogue_role<kFusedBN>(OneProblem{&p}, smem + Cfg::kEpiOffset, acc_full, acc_empty, tmem_base,
+                                 abort_flag, p.timeout_ns, warp, lane)) {
       if (lane == 0) atomicOr(p.err, kErrEpilogueWait);
       *abort_flag = 1;
     }

@@ -207,6 +207,48 @@ __device__ __forceinline__ void decode_item(int item, const CommonParams& p, int
 }
 
 
+// Kernel arguments of the packed path: one problem held in parameter space, or a batch of
+// problems whose parameter blocks live in global memory (uploaded by the host before the
+// launch), with item_begin[p] the first global work item of problem p.
+struct KernelArgs {
+  PackedParams one;
+  const PackedParams* many;
+  const int32_t* item_begin;  // count + 1 entries
+  int32_t count;
+  int32_t batched;
+  int32_t total_items;
+};
+
+__device__ __forceinline__ const PackedParams& problem_of(const KernelArgs& a, int item, int& local) {
+  if (!a.batched) {
+    local = item;
+    return a.one;
+  }
+  int lo = 0, hi = a.count - 1;  // last problem whose first item is <= item
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.item_begin[mid] <= item) lo = mid; else hi = mid - 1;
+  }
+  local = item - a.item_begin[lo];
+  return a.many[lo];
+}
+
+// Work-list views used by the shared roles: the number of global items and, for one item,
+// its problem's CommonParams and the item's index inside that problem.
+struct OneProblem {
+  const CommonParams* c;
+  __device__ int num_items() const { return c->num_items; }
+  __device__ const CommonParams& get(int item, int& local) const {
+    local = item;
+    return *c;
+  }
+};
+struct PackedWork {
+  const KernelArgs* a;
+  __device__ int num_items() const { return a->batched ? a->total_items : a->one.c.num_items; }
+  __device__ const CommonParams& get(int item, int& local) const { return problem_of(*a, item, local).c; }
+};
+
 // Byte layout of one operand stage (both kernels): [A hi | B hi | A lo | B lo].  A tile:
 // 128 (m) x 64 (k) K-major, or (MN-major) two 64 (m) x 64 (k) boxes; B tile: 64 (k) x BN
 // MN-major as BN/64 boxes of 64 (n) x 64 (k), or BN x 64 K-major; 128-byte swizzle.
@@ -225,23 +267,27 @@ constexpr uint32_t kEpiBytes = 4 * 2 * 4096;  // epilogue staging: 4 warps x 2 x
 // Single thread.  For each item: wait for a free accumulator, then for each k-step wait for
 // the operand stage, issue 4 k16 slices x (1 or 3) UMMAs, and release the stage; finally
 // signal the epilogue.  Returns false if a wait gave up.
-template <int BN, int TERMS, int STAGES, bool BF16, bool A_MN, bool B_MN>
-__device__ __forceinline__ bool mma_role(const CommonParams& p, uint8_t* smem, uint64_t* full,
+template <int BN, int TERMS, int STAGES, bool BF16, bool A_MN, bool B_MN, class Work>
+__device__ __forceinline__ bool mma_role(const Work& work, uint8_t* smem, uint64_t* full,
                                          uint64_t* empty, uint64_t* acc_full, uint64_t* acc_empty,
-                                         uint32_t tmem_base, volatile int* abort_flag) {
+                                         uint32_t tmem_base, volatile int* abort_flag,
+                                         uint64_t timeout_ns) {
   using SL = StageLayout<BN, TERMS>;
   constexpr uint32_t idesc = make_idesc_f16(kBM, BN, BF16, A_MN, B_MN);
   int stage = 0;
   uint32_t phase = 0;
   int it = 0;
-  for (int item = blockIdx.x; item < p.num_items; item += gridDim.x, ++it) {
+  const int total = work.num_items();
+  for (int item = blockIdx.x; item < total; item += gridDim.x, ++it) {
+    int local;
+    const CommonParams& p = work.get(item, local);
     const int acc = it & 1;
     const uint32_t acc_par = (it >> 1) & 1;
-    if (!mbar_wait(smem_u32(&acc_empty[acc]), acc_par ^ 1u, p.timeout_ns, abort_flag)) return false;
+    if (!mbar_wait(smem_u32(&acc_empty[acc]), acc_par ^ 1u, timeout_ns, abort_flag)) return false;
     tc_fence_after();
     const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * BN);
     for (int kb = 0; kb < p.nk; ++kb) {
-      if (!mbar_wait(smem_u32(&full[stage]), phase, p.timeout_ns, abort_flag)) return false;
+      if (!mbar_wait(smem_u32(&full[stage]), phase, timeout_ns, abort_flag)) return false;
       tc_fence_after();
       uint8_t* st = smem + stage * SL::kBytes;
       const uint64_t da_hi = A_MN ? make_sdesc_mnmajor_sw128(smem_u32(st + SL::kAHi), 8192, 1024)
@@ -279,27 +325,30 @@ __device__ __forceinline__ bool mma_role(const CommonParams& p, uint8_t* smem, u
 // Warps 4..7.  Each warp owns TMEM lanes 32q..32q+31 (rows of the tile) and two 4 KB
 // staging buffers: a 32 x 32 FP32 block is written there in the 128-byte swizzled layout and
 // added into every destination block by TMA reductions.  Returns false if a wait gave up.
-template <int BN>
-__device__ __forceinline__ bool epilogue_role(const CommonParams& p, uint8_t* epi_smem,
+template <int BN, class Work>
+__device__ __forceinline__ bool epilogue_role(const Work& work, uint8_t* epi_smem,
                                               uint64_t* acc_full, uint64_t* acc_empty,
                                               uint32_t tmem_base, volatile int* abort_flag,
-                                              int warp, int lane) {
+                                              uint64_t timeout_ns, int warp, int lane) {
   const int q = warp & 3;  // TMEM lane quarter this warp may access
   const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
   uint8_t* stage_base = epi_smem + q * 8192;
   int buf = 0;
   int it = 0;
   bool ok = true;
-  for (int item = blockIdx.x; item < p.num_items; item += gridDim.x, ++it) {
+  const int total = work.num_items();
+  for (int item = blockIdx.x; item < total; item += gridDim.x, ++it) {
     const int acc = it & 1;
     const uint32_t acc_par = (it >> 1) & 1;
-    if (!mbar_wait(smem_u32(&acc_full[acc]), acc_par, p.timeout_ns, abort_flag)) {
+    if (!mbar_wait(smem_u32(&acc_full[acc]), acc_par, timeout_ns, abort_flag)) {
       ok = false;
       break;
     }
     tc_fence_after();
+    int local;
+    const CommonParams& p = work.get(item, local);
     int r, tm, tn;
-    decode_item(item, p, r, tm, tn);
+    decode_item(local, p, r, tm, tn);
     const ProductDests& pd = p.prod[r];
     const int row0 = tm * kBM + q * 32;
     // undo the operand scaling of this (product, tile) exactly: 2^(s_A + s_B)
@@ -391,12 +440,14 @@ struct PackedCfg {
 };
 
 template <int BN, int TERMS, int STAGES, bool BF16, bool A_MN, bool B_MN>
-__global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_constant__ PackedParams pp) {
+__global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_constant__ KernelArgs args) {
   using Cfg = PackedCfg<BN, TERMS, STAGES>;
   using SL = StageLayout<BN, TERMS>;
   static_assert(BN % 64 == 0 && BN <= 256, "UMMA N");
   static_assert(Cfg::kTmemCols >= 32 && Cfg::kTmemCols <= 512, "TMEM columns");
-  const CommonParams& p = pp.c;
+  const PackedWork work{&args};
+  const uint64_t timeout_ns = args.one.c.timeout_ns;
+  unsigned int* err = args.one.c.err;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -423,12 +474,12 @@ __global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_co
     *abort_flag = 0;
     fence_mbar_init();
   }
-  if (warp == 0 && lane == 0) {
-    tma_prefetch_desc(&pp.tmA[0]);
-    tma_prefetch_desc(&pp.tmB[0]);
+  if (warp == 0 && lane == 0 && !args.batched) {
+    tma_prefetch_desc(&args.one.tmA[0]);
+    tma_prefetch_desc(&args.one.tmB[0]);
     if (TERMS == 3) {
-      tma_prefetch_desc(&pp.tmA[1]);
-      tma_prefetch_desc(&pp.tmB[1]);
+      tma_prefetch_desc(&args.one.tmA[1]);
+      tma_prefetch_desc(&args.one.tmB[1]);
     }
   }
   if (warp == 1) {
@@ -447,11 +498,15 @@ __global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_co
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
-      for (int item = blockIdx.x; ok && item < p.num_items; item += gridDim.x) {
+      const int total = work.num_items();
+      for (int item = blockIdx.x; ok && item < total; item += gridDim.x) {
+        int local;
+        const PackedParams& pp = problem_of(args, item, local);
+        const CommonParams& p = pp.c;
         int r, tm, tn;
-        decode_item(item, p, r, tm, tn);
+        decode_item(local, p, r, tm, tn);
         for (int kb = 0; kb < p.nk; ++kb) {
-          if (!mbar_wait(smem_u32(&empty[stage]), phase ^ 1u, p.timeout_ns, abort_flag)) {
+          if (!mbar_wait(smem_u32(&empty[stage]), phase ^ 1u, timeout_ns, abort_flag)) {
             ok = false;
             break;
           }
@@ -489,24 +544,24 @@ __global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_co
         }
       }
       if (!ok) {
-        atomicOr(p.err, kErrProducerWait);
+        atomicOr(err, kErrProducerWait);
         *abort_flag = 1;
         drain_pause(2000000ull);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      if (!mma_role<BN, TERMS, STAGES, BF16, A_MN, B_MN>(p, smem, full, empty, acc_full, acc_empty,
-                                                       tmem_base, abort_flag)) {
-        atomicOr(p.err, kErrMmaWait);
+      if (!mma_role<BN, TERMS, STAGES, BF16, A_MN, B_MN>(work, smem, full, empty, acc_full, acc_empty,
+                                                       tmem_base, abort_flag, timeout_ns)) {
+        atomicOr(err, kErrMmaWait);
         *abort_flag = 1;
         drain_pause(2000000ull);
       }
     }
   } else if (warp >= 4) {
-    if (!epilogue_role<BN>(p, smem + Cfg::kEpiOffset, acc_full, acc_empty, tmem_base, abort_flag, warp,
-                           lane)) {
-      if (lane == 0) atomicOr(p.err, kErrEpilogueWait);
+    if (!epilogue_role<BN>(work, smem + Cfg::kEpiOffset, acc_full, acc_empty, tmem_base, abort_flag,
+                           timeout_ns, warp, lane)) {
+      if (lane == 0) atomicOr(err, kErrEpilogueWait);
       *abort_flag = 1;
     }
   }

@@ -6,7 +6,7 @@
 namespace fmm {
 
 template <int BN, int TERMS, int STAGES, bool BF16, bool A_MN, bool B_MN>
-static cudaError_t launch_cfg(const PackedParams& p, int grid, cudaStream_t s) {
+static cudaError_t launch_cfg(const KernelArgs& p, int grid, cudaStream_t s) {
   using Cfg = PackedCfg<BN, TERMS, STAGES>;
   auto kern = fmm_packed_kernel<BN, TERMS, STAGES, BF16, A_MN, B_MN>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -24,7 +24,7 @@ bool packed_config_supported(int tile_n, int terms, bool bf16) {
 }
 
 template <bool A_MN, bool B_MN>
-static cudaError_t launch_mn(const PackedParams& p, int tile_n, int terms, bool bf16, int grid,
+static cudaError_t launch_mn(const KernelArgs& p, int tile_n, int terms, bool bf16, int grid,
                              cudaStream_t s) {
   if (tile_n == 128) {
     if (terms == 3) return launch_cfg<128, 3, 3, true, A_MN, B_MN>(p, grid, s);
@@ -41,7 +41,7 @@ static cudaError_t launch_mn(const PackedParams& p, int tile_n, int terms, bool 
 
 // Operand layouts built: forward (A K-major, B MN-major), dA = dC B^T (A K-major, B K-major),
 // dB = A^T dC (A MN-major, B MN-major).
-cudaError_t launch_packed(const PackedParams& p, int tile_n, int terms, bool bf16, bool a_mn, bool b_mn,
+cudaError_t launch_packed(const KernelArgs& p, int tile_n, int terms, bool bf16, bool a_mn, bool b_mn,
                           int grid, cudaStream_t s) {
   if (!a_mn && b_mn) return launch_mn<false, true>(p, tile_n, terms, bf16, grid, s);
   if (!a_mn && !b_mn) return launch_mn<false, false>(p, tile_n, terms, bf16, grid, s);
