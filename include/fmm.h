@@ -96,7 +96,9 @@ typedef struct fmm_options {
                        1 = product-major (all tiles of one product, then the next),
                        2 = tile rounds (each CTA runs all 7^L products of one output tile
                            back to back, so its destination blocks stay in L2) */
-    int reserved[4];
+    int bk;         /* packed algorithm, split3: k-depth of a pipeline stage, 0 = automatic,
+                       64 (128-byte swizzle) or 32 (64-byte swizzle, twice the stages) */
+    int reserved[3];
 } fmm_options;
 
 /* Bytes of workspace fmm_gemm needs for this problem (0 when none).  Returns

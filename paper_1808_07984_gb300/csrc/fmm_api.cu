@@ -180,6 +180,7 @@ struct Plan {
   //   B' MN-major (b_mn): stored K rows x N cols; B' K-major: stored N rows x K cols.
   bool a_mn = false, b_mn = true;
   int tile_n = 128;
+  int bk = 64;  // k-elements per pipeline stage of the packed kernel (64, or 32 for split3)
   int algo = FMM_ALGO_PACKED;
   int schedule = kSchedProductMajor;
   bool scaled = false;      // FP16 operands with power-of-two scaling per panel
@@ -243,6 +244,10 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
   }
   if (!packed_config_supported(pl.tile_n, pl.terms, pl.bf16))
     return fail(FMM_ERR_UNSUPPORTED, "tile_n must be 128 or 256");
+  const int bk = opt ? opt->bk : 0;
+  if (bk != 0 && bk != 32 && bk != 64) return fail(FMM_ERR_ARG, "bk must be 0, 32 or 64");
+  if (bk == 32 && pl.terms != 3) return fail(FMM_ERR_UNSUPPORTED, "32-deep stages are built for split3");
+  pl.bk = bk == 0 ? 64 : bk;
   if (pl.hm >= (int64_t(1) << 31) || pl.hn >= (int64_t(1) << 31) || pl.hk >= (int64_t(1) << 31))
     return fail(FMM_ERR_ARG, "dimension too large");
   const int64_t a_rows = a_mn ? pl.hk : pl.hm;
@@ -282,7 +287,8 @@ bool overlaps(const void* a, size_t abytes, const void* b, size_t bbytes) {
 }
 
 fmm_status encode_3d(CUtensorMap* map, void* base, int64_t inner, int64_t rows, int64_t depth,
-                     int64_t ld_elems, int box_inner, int box_rows) {
+                     int64_t ld_elems, int box_inner, int box_rows,
+                     CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B) {
   const cuuint64_t dims[3] = {static_cast<cuuint64_t>(inner), static_cast<cuuint64_t>(rows),
                               static_cast<cuuint64_t>(depth)};
   const cuuint64_t strides[2] = {static_cast<cuuint64_t>(ld_elems * 2),
@@ -290,7 +296,7 @@ fmm_status encode_3d(CUtensorMap* map, void* base, int64_t inner, int64_t rows, 
   const cuuint32_t box[3] = {static_cast<cuuint32_t>(box_inner), static_cast<cuuint32_t>(box_rows), 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(FMM_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string(r) + ")");
   return FMM_OK;
@@ -318,7 +324,7 @@ fmm_status fill_common(CommonParams& c, const Plan& pl, const std::vector<Produc
   c.timeout_ns = g_timeout_ns.load();
   c.tiles_m = static_cast<int32_t>((pl.hm + kBM - 1) / kBM);
   c.tiles_n = static_cast<int32_t>((pl.hn + pl.tile_n - 1) / pl.tile_n);
-  c.nk = static_cast<int32_t>((pl.hk + kBK - 1) / kBK);
+  c.nk = static_cast<int32_t>((pl.hk + pl.bk - 1) / pl.bk);  // fused and hybrid plans keep bk = 64
   const int64_t items = static_cast<int64_t>(live.size()) * c.tiles_m * c.tiles_n;
   if (items >= (int64_t(1) << 31)) return fail(FMM_ERR_ARG, "too many tiles");
   c.num_items = static_cast<int32_t>(items);
@@ -651,16 +657,19 @@ fmm_status prepare_packed(const Plan& pl, int64_t m, int64_t n, int64_t k, float
   PackedParams* pp = &job.params;
   fmm_status st = FMM_OK;
   const int nb = pl.terms == 3 ? 2 : 1;
+  // K-major tiles: BK-deep rows, 128-byte swizzle (BK 64) or 64-byte swizzle (BK 32);
+  // MN-major tiles: boxes of 64 (m or n) x BK (k), 128-byte swizzle
+  const CUtensorMapSwizzle kswz = pl.bk == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
   for (int t = 0; t < nb && st == FMM_OK; ++t) {
     if (pl.a_mn)
-      st = encode_3d(&pp->tmA[t], t ? a_lo : a_hi, pl.hm, pl.hk, pl.R, pl.lda_w, 64, kBK);
+      st = encode_3d(&pp->tmA[t], t ? a_lo : a_hi, pl.hm, pl.hk, pl.R, pl.lda_w, 64, pl.bk);
     else
-      st = encode_3d(&pp->tmA[t], t ? a_lo : a_hi, pl.hk, pl.hm, pl.R, pl.lda_w, kBK, kBM);
+      st = encode_3d(&pp->tmA[t], t ? a_lo : a_hi, pl.hk, pl.hm, pl.R, pl.lda_w, pl.bk, kBM, kswz);
     if (st != FMM_OK) break;
     if (pl.b_mn)
-      st = encode_3d(&pp->tmB[t], t ? b_lo : b_hi, pl.hn, pl.hk, pl.R, pl.ldb_w, 64, kBK);
+      st = encode_3d(&pp->tmB[t], t ? b_lo : b_hi, pl.hn, pl.hk, pl.R, pl.ldb_w, 64, pl.bk);
     else
-      st = encode_3d(&pp->tmB[t], t ? b_lo : b_hi, pl.hk, pl.hn, pl.R, pl.ldb_w, kBK, pl.tile_n);
+      st = encode_3d(&pp->tmB[t], t ? b_lo : b_hi, pl.hk, pl.hn, pl.R, pl.ldb_w, pl.bk, pl.tile_n, kswz);
   }
   const std::vector<Product> prods = make_products(pl.L);
   std::vector<int> live(pl.R);
@@ -739,7 +748,7 @@ fmm_status gemm_core(const Plan& pl, int64_t m, int64_t n, int64_t k, float alph
     cudaError_t e;
     {
       PhaseScope ps(kPhaseTensor, s);
-      e = launch_packed(*ka, pl.tile_n, pl.terms, pl.bf16, pl.a_mn, pl.b_mn, job->grid, s);
+      e = launch_packed(*ka, pl.tile_n, pl.terms, pl.bf16, pl.a_mn, pl.b_mn, pl.bk, job->grid, s);
     }
     if (e != cudaSuccess) st = cuda_fail(e, "tensor-core pass");
   }
@@ -759,6 +768,7 @@ void set_last_error(const std::string& msg) { g_last_error = msg; }
 struct fmm_batched_plan {
   struct Group {
     int tile_n = 128;
+    int bk = 64;
     int grid = 0;
     fmm::KernelArgs* args = nullptr;
   };
@@ -997,6 +1007,8 @@ fmm_status fmm_batched_plan_create(int count, const int64_t* m, const int64_t* n
     desc_off += descs.size() * sizeof(PackedParams);
     fmm_batched_plan::Group g;
     g.tile_n = tn;
+    for (PackedJob* job : plan->jobs)
+      if (job->has_work && job->pl.tile_n == tn) g.bk = job->pl.bk;
     g.args = new KernelArgs;
     std::memset(g.args, 0, sizeof(KernelArgs));
     g.args->many = d_desc;
@@ -1029,7 +1041,7 @@ fmm_status fmm_batched_plan_execute(const fmm_batched_plan* plan, void* stream) 
     cudaError_t e;
     {
       PhaseScope ps(kPhaseTensor, s);
-      e = launch_packed(*g.args, g.tile_n, plan->terms, plan->bf16, false, true, g.grid, s);
+      e = launch_packed(*g.args, g.tile_n, plan->terms, plan->bf16, false, true, g.bk, g.grid, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "batched tensor-core pass");
   }

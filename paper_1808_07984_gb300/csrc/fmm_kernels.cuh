@@ -31,7 +31,7 @@
 namespace fmm {
 
 constexpr int kBM = 128;          // rows of an output tile (UMMA M)
-constexpr int kBK = 64;           // k-elements per pipeline stage (128-byte 16-bit rows)
+constexpr int kBK = 64;           // k-elements per stage of the fused kernel and the default packed stage
 constexpr int kMaxProducts = 49;  // 7^2
 constexpr int kMaxDest = 4;       // W_C <= 4 at two levels
 constexpr int kMaxSources = 16;   // 4^2 blocks per operand at two levels
@@ -252,10 +252,11 @@ struct PackedWork {
 // Byte layout of one operand stage (both kernels): [A hi | B hi | A lo | B lo].  A tile:
 // 128 (m) x 64 (k) K-major, or (MN-major) two 64 (m) x 64 (k) boxes; B tile: 64 (k) x BN
 // MN-major as BN/64 boxes of 64 (n) x 64 (k), or BN x 64 K-major; 128-byte swizzle.
-template <int BN, int TERMS>
+template <int BN, int TERMS, int BK = kBK>
 struct StageLayout {
-  static constexpr uint32_t kABytes = kBM * kBK * 2;
-  static constexpr uint32_t kBBytes = BN * kBK * 2;
+  static_assert(BK == 64 || BK == 32, "k-step of 64 (128-byte swizzle) or 32 (64-byte swizzle)");
+  static constexpr uint32_t kABytes = kBM * BK * 2;
+  static constexpr uint32_t kBBytes = BN * BK * 2;
   static constexpr uint32_t kBytes = (TERMS == 3 ? 2u : 1u) * (kABytes + kBBytes);
   static constexpr uint32_t kAHi = 0, kBHi = kABytes, kALo = kABytes + kBBytes,
                             kBLo = 2 * kABytes + kBBytes;
@@ -267,12 +268,19 @@ constexpr uint32_t kEpiBytes = 4 * 2 * 4096;  // epilogue staging: 4 warps x 2 x
 // Single thread.  For each item: wait for a free accumulator, then for each k-step wait for
 // the operand stage, issue 4 k16 slices x (1 or 3) UMMAs, and release the stage; finally
 // signal the epilogue.  Returns false if a wait gave up.
-template <int BN, int TERMS, int STAGES, bool BF16, bool A_MN, bool B_MN, class Work>
+// K-major descriptor of a tile with BK-deep rows (128-byte swizzle for 64, 64-byte for 32).
+template <int BK>
+__device__ __forceinline__ uint64_t kmajor_desc(uint32_t addr) {
+  return BK == 64 ? make_sdesc_kmajor_sw128(addr) : make_sdesc_kmajor_sw64(addr);
+}
+
+template <int BN, int TERMS, int STAGES, bool BF16, bool A_MN, bool B_MN, class Work, int BK = kBK>
 __device__ __forceinline__ bool mma_role(const Work& work, uint8_t* smem, uint64_t* full,
                                          uint64_t* empty, uint64_t* acc_full, uint64_t* acc_empty,
                                          uint32_t tmem_base, volatile int* abort_flag,
                                          uint64_t timeout_ns) {
-  using SL = StageLayout<BN, TERMS>;
+  using SL = StageLayout<BN, TERMS, BK>;
+  constexpr uint32_t kMnAtom = BK * 128;  // MN-major: bytes between 64-wide atoms along M / N
   constexpr uint32_t idesc = make_idesc_f16(kBM, BN, BF16, A_MN, B_MN);
   int stage = 0;
   uint32_t phase = 0;
@@ -290,16 +298,16 @@ __device__ __forceinline__ bool mma_role(const Work& work, uint8_t* smem, uint64
       if (!mbar_wait(smem_u32(&full[stage]), phase, timeout_ns, abort_flag)) return false;
       tc_fence_after();
       uint8_t* st = smem + stage * SL::kBytes;
-      const uint64_t da_hi = A_MN ? make_sdesc_mnmajor_sw128(smem_u32(st + SL::kAHi), 8192, 1024)
-                                  : make_sdesc_kmajor_sw128(smem_u32(st + SL::kAHi));
-      const uint64_t da_lo = A_MN ? make_sdesc_mnmajor_sw128(smem_u32(st + SL::kALo), 8192, 1024)
-                                  : make_sdesc_kmajor_sw128(smem_u32(st + SL::kALo));
-      const uint64_t db_hi = B_MN ? make_sdesc_mnmajor_sw128(smem_u32(st + SL::kBHi), 8192, 1024)
-                                  : make_sdesc_kmajor_sw128(smem_u32(st + SL::kBHi));
-      const uint64_t db_lo = B_MN ? make_sdesc_mnmajor_sw128(smem_u32(st + SL::kBLo), 8192, 1024)
-                                  : make_sdesc_kmajor_sw128(smem_u32(st + SL::kBLo));
+      const uint64_t da_hi = A_MN ? make_sdesc_mnmajor_sw128(smem_u32(st + SL::kAHi), kMnAtom, 1024)
+                                  : kmajor_desc<BK>(smem_u32(st + SL::kAHi));
+      const uint64_t da_lo = A_MN ? make_sdesc_mnmajor_sw128(smem_u32(st + SL::kALo), kMnAtom, 1024)
+                                  : kmajor_desc<BK>(smem_u32(st + SL::kALo));
+      const uint64_t db_hi = B_MN ? make_sdesc_mnmajor_sw128(smem_u32(st + SL::kBHi), kMnAtom, 1024)
+                                  : kmajor_desc<BK>(smem_u32(st + SL::kBHi));
+      const uint64_t db_lo = B_MN ? make_sdesc_mnmajor_sw128(smem_u32(st + SL::kBLo), kMnAtom, 1024)
+                                  : kmajor_desc<BK>(smem_u32(st + SL::kBLo));
 #pragma unroll
-      for (int kk = 0; kk < kBK / 16; ++kk) {
+      for (int kk = 0; kk < BK / 16; ++kk) {
         // K-major: 16 elements = 32 bytes inside the swizzle row; MN-major: 16 k-rows = two
         // 1024-byte atoms.  Descriptor start addresses are encoded >> 4.
         const uint64_t ka = A_MN ? static_cast<uint64_t>(kk * 128) : static_cast<uint64_t>(kk * 2);
@@ -429,9 +437,9 @@ __device__ __forceinline__ void drain_pause(uint64_t ns) {
 }
 
 // ------------------------------------------------------------ packed kernel
-template <int BN, int TERMS, int STAGES>
+template <int BN, int TERMS, int STAGES, int BK = kBK>
 struct PackedCfg {
-  using SL = StageLayout<BN, TERMS>;
+  using SL = StageLayout<BN, TERMS, BK>;
   static constexpr uint32_t kStageBytes = SL::kBytes;
   static constexpr uint32_t kEpiOffset = STAGES * kStageBytes;
   static constexpr uint32_t kBarOffset = kEpiOffset + kEpiBytes;
@@ -439,10 +447,11 @@ struct PackedCfg {
   static constexpr uint32_t kTmemCols = 2 * BN;
 };
 
-template <int BN, int TERMS, int STAGES, bool BF16, bool A_MN, bool B_MN>
+template <int BN, int TERMS, int STAGES, bool BF16, bool A_MN, bool B_MN, int BK>
 __global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_constant__ KernelArgs args) {
-  using Cfg = PackedCfg<BN, TERMS, STAGES>;
-  using SL = StageLayout<BN, TERMS>;
+  using Cfg = PackedCfg<BN, TERMS, STAGES, BK>;
+  using SL = StageLayout<BN, TERMS, BK>;
+  constexpr uint32_t kMnAtom = BK * 128;
   static_assert(BN % 64 == 0 && BN <= 256, "UMMA N");
   static_assert(Cfg::kTmemCols >= 32 && Cfg::kTmemCols <= 512, "TMEM columns");
   const PackedWork work{&args};
@@ -514,28 +523,28 @@ __global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_co
           const uint32_t fb = smem_u32(&full[stage]);
           mbar_arrive_expect_tx(fb, Cfg::kStageBytes);
           if (A_MN) {
-            // A operand sums stored k-rows x m-cols: two boxes of 64 (m) x 64 (k), 8 KB each
+            // A operand sums stored k-rows x m-cols: two boxes of 64 (m) x BK (k)
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-              tma_load_3d(smem_u32(st + SL::kAHi + j * 8192), &pp.tmA[0], fb, tm * kBM + 64 * j, kb * kBK, r);
+              tma_load_3d(smem_u32(st + SL::kAHi + j * kMnAtom), &pp.tmA[0], fb, tm * kBM + 64 * j, kb * BK, r);
               if (TERMS == 3)
-                tma_load_3d(smem_u32(st + SL::kALo + j * 8192), &pp.tmA[1], fb, tm * kBM + 64 * j, kb * kBK, r);
+                tma_load_3d(smem_u32(st + SL::kALo + j * kMnAtom), &pp.tmA[1], fb, tm * kBM + 64 * j, kb * BK, r);
             }
           } else {
-            tma_load_3d(smem_u32(st + SL::kAHi), &pp.tmA[0], fb, kb * kBK, tm * kBM, r);
-            if (TERMS == 3) tma_load_3d(smem_u32(st + SL::kALo), &pp.tmA[1], fb, kb * kBK, tm * kBM, r);
+            tma_load_3d(smem_u32(st + SL::kAHi), &pp.tmA[0], fb, kb * BK, tm * kBM, r);
+            if (TERMS == 3) tma_load_3d(smem_u32(st + SL::kALo), &pp.tmA[1], fb, kb * BK, tm * kBM, r);
           }
           if (B_MN) {
-            // B operand sums stored k-rows x n-cols: BN/64 boxes of 64 (n) x 64 (k), 8 KB each
+            // B operand sums stored k-rows x n-cols: BN/64 boxes of 64 (n) x BK (k)
 #pragma unroll
             for (int j = 0; j < BN / 64; ++j) {
-              tma_load_3d(smem_u32(st + SL::kBHi + j * 8192), &pp.tmB[0], fb, tn * BN + 64 * j, kb * kBK, r);
+              tma_load_3d(smem_u32(st + SL::kBHi + j * kMnAtom), &pp.tmB[0], fb, tn * BN + 64 * j, kb * BK, r);
               if (TERMS == 3)
-                tma_load_3d(smem_u32(st + SL::kBLo + j * 8192), &pp.tmB[1], fb, tn * BN + 64 * j, kb * kBK, r);
+                tma_load_3d(smem_u32(st + SL::kBLo + j * kMnAtom), &pp.tmB[1], fb, tn * BN + 64 * j, kb * BK, r);
             }
           } else {
-            tma_load_3d(smem_u32(st + SL::kBHi), &pp.tmB[0], fb, kb * kBK, tn * BN, r);
-            if (TERMS == 3) tma_load_3d(smem_u32(st + SL::kBLo), &pp.tmB[1], fb, kb * kBK, tn * BN, r);
+            tma_load_3d(smem_u32(st + SL::kBHi), &pp.tmB[0], fb, kb * BK, tn * BN, r);
+            if (TERMS == 3) tma_load_3d(smem_u32(st + SL::kBLo), &pp.tmB[1], fb, kb * BK, tn * BN, r);
           }
           if (++stage == STAGES) {
             stage = 0;
@@ -551,8 +560,9 @@ __global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_co
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      if (!mma_role<BN, TERMS, STAGES, BF16, A_MN, B_MN>(work, smem, full, empty, acc_full, acc_empty,
-                                                       tmem_base, abort_flag, timeout_ns)) {
+      if (!mma_role<BN, TERMS, STAGES, BF16, A_MN, B_MN, PackedWork, BK>(work, smem, full, empty, acc_full,
+                                                                         acc_empty, tmem_base, abort_flag,
+                                                                         timeout_ns)) {
         atomicOr(err, kErrMmaWait);
         *abort_flag = 1;
         drain_pause(2000000ull);

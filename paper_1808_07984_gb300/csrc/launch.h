@@ -23,7 +23,7 @@ cudaError_t launch_debug_wait(unsigned* err, uint64_t timeout_ns, cudaStream_t s
 // Tensor-core kernel over packed operand sums.  tile_n in {128, 256}; terms in {1, 3};
 // bf16 selects BF16 (true) or FP16 (false) operands.
 cudaError_t launch_packed(const KernelArgs& p, int tile_n, int terms, bool bf16, bool a_mn, bool b_mn,
-                          int grid, cudaStream_t s);
+                          int bk, int grid, cudaStream_t s);
 bool packed_config_supported(int tile_n, int terms, bool bf16);
 
 // Tensor-core kernel that forms the operand sums on chip from FP32 source tiles

@@ -178,6 +178,18 @@ __host__ __device__ constexpr uint32_t make_idesc_f16(int M, int N, bool bf16, b
 // exactly the layout a TMA load with CU_TENSOR_MAP_SWIZZLE_128B and a 64-element
 // (16-bit) inner box writes.  `addr` must lie in a 1024-byte aligned atom; stepping K
 // by 16 elements inside the atom adds 32 bytes to the start address.
+// Same for a tile with 64-byte rows (32 16-bit elements of K) in the 64-byte swizzled layout:
+// 8-row atoms of 512 bytes, as a TMA load with CU_TENSOR_MAP_SWIZZLE_64B writes.
+__device__ __forceinline__ uint64_t make_sdesc_kmajor_sw64(uint32_t addr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((addr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>(1) << 16;
+  d |= static_cast<uint64_t>(512 >> 4) << 32;          // stride byte offset: 8 rows * 64 B
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(4) << 61;                  // swizzle mode: 64B
+  return d;
+}
+
 __device__ __forceinline__ uint64_t make_sdesc_kmajor_sw128(uint32_t addr) {
   uint64_t d = 0;
   d |= static_cast<uint64_t>((addr & 0x3FFFFu) >> 4);  // start address >> 4

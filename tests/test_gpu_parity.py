@@ -59,7 +59,7 @@ def _to_device(X, ld_pad, dtype):
 
 
 def run(m, n, k, levels, variant="split3", dist="uniform", seed=0, alpha=1.0, beta=0.0,
-        tile_n=0, pads=(0, 0, 0), c_fill=None, rows=None, schedule="auto", algo="auto"):
+        tile_n=0, pads=(0, 0, 0), c_fill=None, rows=None, schedule="auto", algo="auto", bk=0):
     A, B = synth.problem(m, n, k, seed, dist)
     in_dtype = {"bf16": torch.bfloat16, "f16": torch.float16}.get(variant, torch.float32)
     Ad = _to_device(A, pads[0], in_dtype)
@@ -73,7 +73,7 @@ def run(m, n, k, levels, variant="split3", dist="uniform", seed=0, alpha=1.0, be
         if c_fill is not None:
             Cd.fill_(c_fill)
     fmm.gemm(Ad, Bd, Cd, alpha=alpha, beta=beta, levels=levels, variant=variant, tile_n=tile_n,
-             schedule=schedule, algo=algo)
+             schedule=schedule, algo=algo, bk=bk)
     fmm.device_status()
     C = Cd.cpu().numpy().astype(np.float64)
     if variant in ("bf16", "f16"):
@@ -124,6 +124,22 @@ def test_unaligned_ldc_uses_elementwise_writeback(levels):
     """ldc odd: rows of C are not 16-byte aligned, so the element-wise reduction path runs."""
     C, C64, _, _ = run(257, 300, 130, levels, "split3", dist="int", seed=9, pads=(0, 0, 1))
     np.testing.assert_array_equal(C, C64)
+
+
+@pytest.mark.parametrize("tile_n", [128, 256])
+@pytest.mark.parametrize("levels", [0, 1, 2])
+@pytest.mark.parametrize("m,n,k", [(300, 520, 200), (129, 257, 65), (1000, 1200, 300)])
+def test_bk32_stages_bit_exact(m, n, k, levels, tile_n):
+    """32-deep pipeline stages (64-byte swizzled K-major tiles)."""
+    C, C64, _, _ = run(m, n, k, levels, "split3", dist="int", seed=3 * m + k, tile_n=tile_n, bk=32)
+    np.testing.assert_array_equal(C, C64)
+
+
+@pytest.mark.parametrize("levels", [0, 2])
+def test_bk32_float_and_unaligned(levels):
+    C, C64, An, Bn = run(640, 384, 768, levels, "split3", dist="gaussian", seed=4, bk=32,
+                         pads=(3, 1, 1), alpha=-1.0, beta=0.5)
+    assert oracle.normwise_error(C, C64, An, Bn) <= tolerance("split3", levels, 768)
 
 
 def test_int_with_alpha_beta_bit_exact():
