@@ -98,7 +98,11 @@ typedef struct fmm_options {
                            back to back, so its destination blocks stay in L2) */
     int bk;         /* packed algorithm, split3: k-depth of a pipeline stage, 0 = automatic,
                        64 (128-byte swizzle) or 32 (64-byte swizzle, twice the stages) */
-    int reserved[3];
+    int cta_pair;   /* packed algorithm: 0 = automatic, 1 = one CTA per 128-row tile,
+                       2 = CTA pairs (clusters of two CTAs share 256-row tiles through
+                           cta_group::2 UMMAs, each CTA loading half of the B tile;
+                           bk must be 64) */
+    int reserved[2];
 } fmm_options;
 
 /* Bytes of workspace fmm_gemm needs for this problem (0 when none).  Returns

@@ -181,6 +181,7 @@ struct Plan {
   bool a_mn = false, b_mn = true;
   int tile_n = 128;
   int bk = 64;  // k-elements per pipeline stage of the packed kernel (64, or 32 for split3)
+  bool pair = false;  // packed kernel in CTA pairs: 256-row tiles shared by two CTAs
   int algo = FMM_ALGO_PACKED;
   int schedule = kSchedProductMajor;
   bool scaled = false;      // FP16 operands with power-of-two scaling per panel
@@ -236,15 +237,22 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
     pl.schedule = (levels == 2 && pl.hk >= 4096) ? kSchedProductMajor : kSchedTileRounds;
   else
     pl.schedule = sched == 2 ? kSchedTileRounds : kSchedProductMajor;
+  const int bk = opt ? opt->bk : 0;
+  const int cta_pair = opt ? opt->cta_pair : 0;
+  if (cta_pair < 0 || cta_pair > 2) return fail(FMM_ERR_ARG, "cta_pair must be 0, 1 or 2");
+  if (cta_pair == 2 && (on_chip || bk == 32))
+    return fail(FMM_ERR_UNSUPPORTED, "CTA pairs are built for the packed algorithm with bk = 64");
+  // automatic choice: CTA pairs for the packed algorithm (each CTA loads half of the B tile)
+  pl.pair = !on_chip && bk != 32 && cta_pair != 1;
+  const int row_tile = pl.pair ? 2 * kBM : kBM;
   if (pl.tile_n == 0) {
     // 256-wide tiles halve the A-operand traffic; keep 128 when that leaves fewer than four
-    // work items per SM on a 152-SM GB300
-    const int64_t items256 = static_cast<int64_t>(pl.R) * ((pl.hm + kBM - 1) / kBM) * ((pl.hn + 255) / 256);
-    pl.tile_n = items256 >= 4 * 152 ? 256 : 128;
+    // work items per SM (per CTA pair) on a 152-SM GB300
+    const int64_t items256 = static_cast<int64_t>(pl.R) * ((pl.hm + row_tile - 1) / row_tile) * ((pl.hn + 255) / 256);
+    pl.tile_n = items256 >= 4 * (pl.pair ? 76 : 152) ? 256 : 128;
   }
   if (!packed_config_supported(pl.tile_n, pl.terms, pl.bf16))
     return fail(FMM_ERR_UNSUPPORTED, "tile_n must be 128 or 256");
-  const int bk = opt ? opt->bk : 0;
   if (bk != 0 && bk != 32 && bk != 64) return fail(FMM_ERR_ARG, "bk must be 0, 32 or 64");
   if (bk == 32 && pl.terms != 3) return fail(FMM_ERR_UNSUPPORTED, "32-deep stages are built for split3");
   pl.bk = bk == 0 ? 64 : bk;
@@ -322,7 +330,8 @@ fmm_status fill_common(CommonParams& c, const Plan& pl, const std::vector<Produc
   c.c_vec4 = c.c_tma;
   c.err = dev.err;
   c.timeout_ns = g_timeout_ns.load();
-  c.tiles_m = static_cast<int32_t>((pl.hm + kBM - 1) / kBM);
+  const int row_tile = pl.pair ? 2 * kBM : kBM;  // rows of one work item's output tile
+  c.tiles_m = static_cast<int32_t>((pl.hm + row_tile - 1) / row_tile);
   c.tiles_n = static_cast<int32_t>((pl.hn + pl.tile_n - 1) / pl.tile_n);
   c.nk = static_cast<int32_t>((pl.hk + pl.bk - 1) / pl.bk);  // fused and hybrid plans keep bk = 64
   const int64_t items = static_cast<int64_t>(live.size()) * c.tiles_m * c.tiles_n;
@@ -362,7 +371,10 @@ fmm_status fill_common(CommonParams& c, const Plan& pl, const std::vector<Produc
     }
   }
   grid = opt && opt->num_ctas > 0 ? opt->num_ctas : dev.sms;
-  grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(grid, items)));
+  if (pl.pair)  // whole pairs, at most one per item
+    grid = 2 * static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(grid / 2, items)));
+  else
+    grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(grid, items)));
   return FMM_OK;
 }
 
@@ -437,7 +449,7 @@ fmm_status gemm_fused(const Plan& pl, int64_t m, int64_t n, int64_t k, float alp
   cudaError_t e;
   {
     PhaseScope ps(kPhaseTensor, s);
-    e = launch_fused(*fp, pl.terms, grid, s);
+    e = launch_fused(*fp, pl.terms, kFusedTransformWarps, grid, s);
   }
   delete fp;
   if (e != cudaSuccess) return cuda_fail(e, "fused tensor-core pass");
@@ -543,7 +555,7 @@ fmm_status gemm_hybrid(const Plan& pl, int64_t m, int64_t n, int64_t k, float al
   }
   {
     PhaseScope ps(kPhaseTensor, s);
-    e = launch_fused(*fp, pl.terms, grid, s);
+    e = launch_fused(*fp, pl.terms, kFusedTransformWarps, grid, s);
   }
   delete fp;
   if (e != cudaSuccess) return cuda_fail(e, "hybrid tensor-core pass");
@@ -669,7 +681,8 @@ fmm_status prepare_packed(const Plan& pl, int64_t m, int64_t n, int64_t k, float
     if (pl.b_mn)
       st = encode_3d(&pp->tmB[t], t ? b_lo : b_hi, pl.hn, pl.hk, pl.R, pl.ldb_w, 64, pl.bk);
     else
-      st = encode_3d(&pp->tmB[t], t ? b_lo : b_hi, pl.hk, pl.hn, pl.R, pl.ldb_w, pl.bk, pl.tile_n, kswz);
+      st = encode_3d(&pp->tmB[t], t ? b_lo : b_hi, pl.hk, pl.hn, pl.R, pl.ldb_w, pl.bk,
+                     pl.pair ? pl.tile_n / 2 : pl.tile_n, kswz);
   }
   const std::vector<Product> prods = make_products(pl.L);
   std::vector<int> live(pl.R);
@@ -748,7 +761,7 @@ fmm_status gemm_core(const Plan& pl, int64_t m, int64_t n, int64_t k, float alph
     cudaError_t e;
     {
       PhaseScope ps(kPhaseTensor, s);
-      e = launch_packed(*ka, pl.tile_n, pl.terms, pl.bf16, pl.a_mn, pl.b_mn, pl.bk, job->grid, s);
+      e = launch_packed(*ka, pl.tile_n, pl.terms, pl.bf16, pl.a_mn, pl.b_mn, pl.bk, pl.pair, job->grid, s);
     }
     if (e != cudaSuccess) st = cuda_fail(e, "tensor-core pass");
   }
@@ -769,6 +782,7 @@ struct fmm_batched_plan {
   struct Group {
     int tile_n = 128;
     int bk = 64;
+    bool pair = false;
     int grid = 0;
     fmm::KernelArgs* args = nullptr;
   };
@@ -977,6 +991,7 @@ fmm_status fmm_batched_plan_create(int count, const int64_t* m, const int64_t* n
     st = prepare_packed(pl, m[p], n[p], k[p], alpha[p], a, b, beta[p], C[p], ldc[p], ws, dev, nullptr, *job);
   }
   // one batched tensor-core launch per tile width: upload parameter blocks and item offsets
+  // (every problem of a batch has the same CTA-pair setting: the automatic one)
   size_t desc_off = 0;
   const size_t item_off0 = static_cast<size_t>(round_up(static_cast<int64_t>(count) * sizeof(PackedParams), 256));
   for (int tn : {128, 256}) {
@@ -984,8 +999,10 @@ fmm_status fmm_batched_plan_create(int count, const int64_t* m, const int64_t* n
     std::vector<PackedParams> descs;
     std::vector<int32_t> begin;
     int64_t items = 0;
+    bool pair = false;
     for (PackedJob* job : plan->jobs) {
       if (!job->has_work || job->pl.tile_n != tn) continue;
+      pair = job->pl.pair;
       begin.push_back(static_cast<int32_t>(items));
       descs.push_back(job->params);
       items += job->params.c.num_items;
@@ -1018,7 +1035,9 @@ fmm_status fmm_batched_plan_create(int count, const int64_t* m, const int64_t* n
     g.args->total_items = static_cast<int32_t>(items);
     g.args->one.c.err = dev.err;
     g.args->one.c.timeout_ns = g_timeout_ns.load();
-    g.grid = static_cast<int>(std::min<int64_t>(items, dev.sms));
+    g.pair = pair;
+    g.grid = pair ? 2 * static_cast<int>(std::min<int64_t>(items, dev.sms / 2))
+                  : static_cast<int>(std::min<int64_t>(items, dev.sms));
     plan->groups.push_back(g);
   }
   if (st != FMM_OK) {
@@ -1041,7 +1060,7 @@ fmm_status fmm_batched_plan_execute(const fmm_batched_plan* plan, void* stream) 
     cudaError_t e;
     {
       PhaseScope ps(kPhaseTensor, s);
-      e = launch_packed(*g.args, g.tile_n, plan->terms, plan->bf16, false, true, g.bk, g.grid, s);
+      e = launch_packed(*g.args, g.tile_n, plan->terms, plan->bf16, false, true, g.bk, g.pair, g.grid, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "batched tensor-core pass");
   }

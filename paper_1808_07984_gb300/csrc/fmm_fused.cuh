@@ -18,7 +18,9 @@
 
 namespace fmm {
 
-constexpr int kFusedThreads = 512;
+// 256 threads for the producer / MMA / epilogue roles plus TW transform warps
+template <int TW>
+constexpr int fused_threads() { return 256 + 32 * TW; }
 constexpr int kFusedBN = kFusedTileN;
 constexpr uint32_t kSlotBytes = 16384;
 
@@ -47,8 +49,12 @@ __device__ __forceinline__ void split2(float x0, float x1, uint32_t& hi, uint32_
   lo = pack_bf16x2(x0 - h0, x1 - h1);
 }
 
-template <int TERMS>
-__global__ void __launch_bounds__(kFusedThreads, 1) fmm_fused_kernel(const __grid_constant__ FusedParams fp) {
+template <int TERMS, int TW>
+__global__ void __launch_bounds__(fused_threads<TW>(), 1) fmm_fused_kernel(const __grid_constant__ FusedParams fp) {
+  static_assert(TW == 8 || TW == 16, "transform warps");
+  constexpr int NT = 32 * TW;            // transform threads
+  constexpr int AU = 512 / NT;           // A units (row, 8-wide k chunk) per thread per k half
+  constexpr int BU = 1024 / NT;          // B units (k row, 4 n) per thread per k half
   using Cfg = FusedCfg<TERMS>;
   using SL = typename Cfg::SL;
   constexpr int S = Cfg::kOpStages;
@@ -74,10 +80,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fmm_fused_kernel(const __gri
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) {
       mbar_init(smem_u32(&slot_full[s]), 1);
-      mbar_init(smem_u32(&slot_empty[s]), 8);  // one arrival per transform warp
+      mbar_init(smem_u32(&slot_empty[s]), TW);  // one arrival per transform warp
     }
     for (int s = 0; s < S; ++s) {
-      mbar_init(smem_u32(&op_full[s]), 8);
+      mbar_init(smem_u32(&op_full[s]), TW);
       mbar_init(smem_u32(&op_empty[s]), 1);
     }
     for (int a = 0; a < 2; ++a) {
@@ -116,7 +122,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fmm_fused_kernel(const __gri
       };
       for (int item = blockIdx.x; ok && item < p.num_items; item += gridDim.x) {
         int r, tm, tn;
-        decode_item(item, p, r, tm, tn);
+        decode_item(item, p, r, tm, tn, gridDim.x);
         const ProductSrc& ps = fp.src[r];
         for (int kb = 0; ok && kb < p.nk; ++kb) {
           for (int h = 0; ok && h < 2; ++h) {
@@ -150,12 +156,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fmm_fused_kernel(const __gri
     }
   } else if (warp >= 8) {
     // ------------------------------------------------------------ transform
-    // Thread t (0..255).  A: per k half, rows t & 127, 8-wide k chunks 2*(t >> 7) + {0, 1}
-    // of the half's four.  B: per k half, units j = t + 256 v (v = 0..3): k-row j >> 5 of
-    // the half, n = 4 * (j & 31) .. + 3.  Every warp reads every slot.
+    // Thread t (0..NT-1).  A: per k half, row t & 127 and AU of the half's four 8-wide k
+    // chunks starting at AU * (t >> 7).  B: per k half, units j = t + NT v (v < BU): k-row
+    // j >> 5 of the half, n = 4 * (j & 31) .. + 3.  Every warp reads every slot.
     const int t = threadIdx.x - 256;
     const int arow = t & 127;
-    const int acc0 = 2 * (t >> 7);
+    const int acc0 = AU * (t >> 7);
     int slot = 0;
     uint32_t sph = 0;
     int o = 0;
@@ -163,19 +169,19 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fmm_fused_kernel(const __gri
     bool ok = true;
     for (int item = blockIdx.x; ok && item < p.num_items; item += gridDim.x) {
       int r, tm, tn;
-      decode_item(item, p, r, tm, tn);
+      decode_item(item, p, r, tm, tn, gridDim.x);
       const ProductSrc& ps = fp.src[r];
       for (int kb = 0; ok && kb < p.nk; ++kb) {
-        float aA[2][2][8];
-        float aB[2][4][4];
+        float aA[2][AU][8];
+        float aB[2][BU][4];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
 #pragma unroll
-          for (int u = 0; u < 2; ++u)
+          for (int u = 0; u < AU; ++u)
 #pragma unroll
             for (int e = 0; e < 8; ++e) aA[h][u][e] = 0.f;
 #pragma unroll
-          for (int v = 0; v < 4; ++v)
+          for (int v = 0; v < BU; ++v)
 #pragma unroll
             for (int e = 0; e < 4; ++e) aB[h][v][e] = 0.f;
         }
@@ -187,7 +193,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fmm_fused_kernel(const __gri
               const uint8_t* sl = slots + slot * kSlotBytes;
               const float sg = ps.a_sign[w] < 0 ? -1.f : 1.f;
 #pragma unroll
-              for (int u = 0; u < 2; ++u) {
+              for (int u = 0; u < AU; ++u) {
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
                   const int ch = 2 * (acc0 + u) + e;  // 16-byte FP32 chunk of the 128-byte row
@@ -213,8 +219,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fmm_fused_kernel(const __gri
               const uint8_t* sl = slots + slot * kSlotBytes;
               const float sg = ps.b_sign[w] < 0 ? -1.f : 1.f;
 #pragma unroll
-              for (int v = 0; v < 4; ++v) {
-                const int j = t + 256 * v;
+              for (int v = 0; v < BU; ++v) {
+                const int j = t + NT * v;
                 const float4 x = *reinterpret_cast<const float4*>(sl + (j >> 5) * 512 + (j & 31) * 16);
                 aB[h][v][0] = fmaf(sg, x.x, aB[h][v][0]);
                 aB[h][v][1] = fmaf(sg, x.y, aB[h][v][1]);
@@ -240,7 +246,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fmm_fused_kernel(const __gri
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
 #pragma unroll
-          for (int u = 0; u < 2; ++u) {
+          for (int u = 0; u < AU; ++u) {
             const int c = 4 * h + acc0 + u;  // 8-wide bf16 chunk of the 64-deep row
             const uint32_t off = arow * 128 + ((c ^ (arow & 7)) << 4);
             if (TERMS == 3) {
@@ -261,8 +267,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) fmm_fused_kernel(const __gri
             }
           }
 #pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            const int j = t + 256 * v;
+          for (int v = 0; v < BU; ++v) {
+            const int j = t + NT * v;
             const int kk = 32 * h + (j >> 5);  // k-row of the 64-deep stage
             const int nq = j & 31;             // n = 4 nq .. 4 nq + 3
             const int c = (nq & 15) >> 1;      // 8-wide chunk inside the 64-wide n atom

@@ -63,6 +63,7 @@ enum ErrBits : unsigned {
   kErrEpilogueWait = 4u,
   kErrDebugWait = 8u,
   kErrTransformWait = 16u,
+  kErrPairTmem = 32u,  // the two CTAs of a pair were given different TMEM columns
 };
 
 struct DestEntry {
@@ -176,16 +177,18 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
   tn = in_g / gm;
 }
 
-// Work item -> (product r, tile row tm, tile column tn).  CTA b runs items b, b + G, ...
-// (G = gridDim.x).  kSchedProductMajor: item = r * tiles + t.  kSchedTileRounds: tiles are
+// Work item -> (product r, tile row tm, tile column tn).  Worker b runs items b, b + G, ...
+// (G = number of workers).  kSchedProductMajor: item = r * tiles + t.  kSchedTileRounds: tiles are
 // taken G at a time; within a round the item index is r * G + (t - round start), so CTA b
 // runs products 0..R-1 of one tile back to back; the last, partial round is spread over all
 // CTAs product by product.
-__device__ __forceinline__ void decode_item(int item, const CommonParams& p, int& r, int& tm, int& tn) {
+// `workers` is the number of independent item streams: CTAs, or CTA pairs of the pair kernel.
+__device__ __forceinline__ void decode_item(int item, const CommonParams& p, int& r, int& tm, int& tn,
+                                            int workers) {
   const int tiles = p.tiles_m * p.tiles_n;
   int t;
   if (p.schedule == kSchedTileRounds) {
-    const int G = gridDim.x, R = p.num_products;
+    const int G = workers, R = p.num_products;
     const int full = tiles / G;
     const int items_full = full * G * R;
     if (item < items_full) {
@@ -250,13 +253,14 @@ struct PackedWork {
 };
 
 // Byte layout of one operand stage (both kernels): [A hi | B hi | A lo | B lo].  A tile:
-// 128 (m) x 64 (k) K-major, or (MN-major) two 64 (m) x 64 (k) boxes; B tile: 64 (k) x BN
-// MN-major as BN/64 boxes of 64 (n) x 64 (k), or BN x 64 K-major; 128-byte swizzle.
-template <int BN, int TERMS, int BK = kBK>
+// 128 (m) x 64 (k) K-major, or (MN-major) two 64 (m) x 64 (k) boxes; B tile: 64 (k) x BNL
+// MN-major as BNL/64 boxes of 64 (n) x 64 (k), or BNL x 64 K-major; 128-byte swizzle.  BNL
+// is the tile width BN, or BN / 2 for one CTA of a CTA pair (which holds half of B).
+template <int BN, int TERMS, int BK = kBK, int BNL = BN>
 struct StageLayout {
   static_assert(BK == 64 || BK == 32, "k-step of 64 (128-byte swizzle) or 32 (64-byte swizzle)");
   static constexpr uint32_t kABytes = kBM * BK * 2;
-  static constexpr uint32_t kBBytes = BN * BK * 2;
+  static constexpr uint32_t kBBytes = BNL * BK * 2;
   static constexpr uint32_t kBytes = (TERMS == 3 ? 2u : 1u) * (kABytes + kBBytes);
   static constexpr uint32_t kAHi = 0, kBHi = kABytes, kALo = kABytes + kBBytes,
                             kBLo = 2 * kABytes + kBBytes;
@@ -274,24 +278,36 @@ __device__ __forceinline__ uint64_t kmajor_desc(uint32_t addr) {
   return BK == 64 ? make_sdesc_kmajor_sw128(addr) : make_sdesc_kmajor_sw64(addr);
 }
 
-template <int BN, int TERMS, int STAGES, bool BF16, bool A_MN, bool B_MN, class Work, int BK = kBK>
+//
+// PAIR: the thread runs in the even CTA of a CTA pair and issues 256-row pair UMMAs (each
+// CTA contributes 128 rows of A and half of B, and receives its 128 rows of the accumulator);
+// its commits arrive on the barriers of both CTAs, and the accumulator is free again once the
+// epilogues of both CTAs have released it.
+template <int BN, int TERMS, int STAGES, bool BF16, bool A_MN, bool B_MN, class Work, int BK = kBK,
+          bool PAIR = false>
 __device__ __forceinline__ bool mma_role(const Work& work, uint8_t* smem, uint64_t* full,
                                          uint64_t* empty, uint64_t* acc_full, uint64_t* acc_empty,
                                          uint32_t tmem_base, volatile int* abort_flag,
                                          uint64_t timeout_ns) {
-  using SL = StageLayout<BN, TERMS, BK>;
+  using SL = StageLayout<BN, TERMS, BK, PAIR ? BN / 2 : BN>;
   constexpr uint32_t kMnAtom = BK * 128;  // MN-major: bytes between 64-wide atoms along M / N
-  constexpr uint32_t idesc = make_idesc_f16(kBM, BN, BF16, A_MN, B_MN);
+  constexpr uint32_t idesc = make_idesc_f16(PAIR ? 2 * kBM : kBM, BN, BF16, A_MN, B_MN);
   int stage = 0;
   uint32_t phase = 0;
   int it = 0;
   const int total = work.num_items();
-  for (int item = blockIdx.x; item < total; item += gridDim.x, ++it) {
+  const int first = PAIR ? static_cast<int>(blockIdx.x >> 1) : static_cast<int>(blockIdx.x);
+  const int stride = PAIR ? static_cast<int>(gridDim.x >> 1) : static_cast<int>(gridDim.x);
+  auto acc_free = [&](int j) {
+    const uint32_t bar = smem_u32(&acc_empty[j & 1]);
+    const uint32_t par = ((j >> 1) & 1) ^ 1u;
+    return PAIR ? mbar_wait_cluster(bar, par, timeout_ns, abort_flag) : mbar_wait(bar, par, timeout_ns, abort_flag);
+  };
+  for (int item = first; item < total; item += stride, ++it) {
     int local;
     const CommonParams& p = work.get(item, local);
     const int acc = it & 1;
-    const uint32_t acc_par = (it >> 1) & 1;
-    if (!mbar_wait(smem_u32(&acc_empty[acc]), acc_par ^ 1u, timeout_ns, abort_flag)) return false;
+    if (!acc_free(it)) return false;
     tc_fence_after();
     const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * BN);
     for (int kb = 0; kb < p.nk; ++kb) {
@@ -312,20 +328,36 @@ __device__ __forceinline__ bool mma_role(const Work& work, uint8_t* smem, uint64
         // 1024-byte atoms.  Descriptor start addresses are encoded >> 4.
         const uint64_t ka = A_MN ? static_cast<uint64_t>(kk * 128) : static_cast<uint64_t>(kk * 2);
         const uint64_t kb16 = B_MN ? static_cast<uint64_t>(kk * 128) : static_cast<uint64_t>(kk * 2);
-        umma_f16_ss(d_tmem, da_hi + ka, db_hi + kb16, idesc, (kb | kk) != 0 ? 1u : 0u);
-        if (TERMS == 3) {
-          umma_f16_ss(d_tmem, da_hi + ka, db_lo + kb16, idesc, 1u);
-          umma_f16_ss(d_tmem, da_lo + ka, db_hi + kb16, idesc, 1u);
+        if (PAIR) {
+          umma_f16_ss_pair(d_tmem, da_hi + ka, db_hi + kb16, idesc, (kb | kk) != 0 ? 1u : 0u);
+          if (TERMS == 3) {
+            umma_f16_ss_pair(d_tmem, da_hi + ka, db_lo + kb16, idesc, 1u);
+            umma_f16_ss_pair(d_tmem, da_lo + ka, db_hi + kb16, idesc, 1u);
+          }
+        } else {
+          umma_f16_ss(d_tmem, da_hi + ka, db_hi + kb16, idesc, (kb | kk) != 0 ? 1u : 0u);
+          if (TERMS == 3) {
+            umma_f16_ss(d_tmem, da_hi + ka, db_lo + kb16, idesc, 1u);
+            umma_f16_ss(d_tmem, da_lo + ka, db_hi + kb16, idesc, 1u);
+          }
         }
       }
-      umma_commit(smem_u32(&empty[stage]));
+      if (PAIR)
+        umma_commit_pair(smem_u32(&empty[stage]), 3);
+      else
+        umma_commit(smem_u32(&empty[stage]));
       if (++stage == STAGES) {
         stage = 0;
         phase ^= 1u;
       }
     }
-    umma_commit(smem_u32(&acc_full[acc]));
+    if (PAIR)
+      umma_commit_pair(smem_u32(&acc_full[acc]), 3);
+    else
+      umma_commit(smem_u32(&acc_full[acc]));
   }
+  // pair: both epilogues have released both accumulators before the CTAs may retire
+  if (PAIR && (!acc_free(it) || !acc_free(it + 1))) return false;
   return true;
 }
 
@@ -333,11 +365,14 @@ __device__ __forceinline__ bool mma_role(const Work& work, uint8_t* smem, uint64
 // Warps 4..7.  Each warp owns TMEM lanes 32q..32q+31 (rows of the tile) and two 4 KB
 // staging buffers: a 32 x 32 FP32 block is written there in the 128-byte swizzled layout and
 // added into every destination block by TMA reductions.  Returns false if a wait gave up.
-template <int BN, class Work>
+//
+// PAIR: the CTA with rank `rank` of a pair owns rows 128 * rank .. + 127 of each 256-row pair
+// tile; each warp releases the accumulator with one arrival on the even CTA's barrier.
+template <int BN, class Work, bool PAIR = false>
 __device__ __forceinline__ bool epilogue_role(const Work& work, uint8_t* epi_smem,
                                               uint64_t* acc_full, uint64_t* acc_empty,
                                               uint32_t tmem_base, volatile int* abort_flag,
-                                              uint64_t timeout_ns, int warp, int lane) {
+                                              uint64_t timeout_ns, int warp, int lane, int rank = 0) {
   const int q = warp & 3;  // TMEM lane quarter this warp may access
   const uint32_t lane_off = static_cast<uint32_t>(q * 32) << 16;
   uint8_t* stage_base = epi_smem + q * 8192;
@@ -345,7 +380,9 @@ __device__ __forceinline__ bool epilogue_role(const Work& work, uint8_t* epi_sme
   int it = 0;
   bool ok = true;
   const int total = work.num_items();
-  for (int item = blockIdx.x; item < total; item += gridDim.x, ++it) {
+  const int first = PAIR ? static_cast<int>(blockIdx.x >> 1) : static_cast<int>(blockIdx.x);
+  const int stride = PAIR ? static_cast<int>(gridDim.x >> 1) : static_cast<int>(gridDim.x);
+  for (int item = first; item < total; item += stride, ++it) {
     const int acc = it & 1;
     const uint32_t acc_par = (it >> 1) & 1;
     if (!mbar_wait(smem_u32(&acc_full[acc]), acc_par, timeout_ns, abort_flag)) {
@@ -356,13 +393,16 @@ __device__ __forceinline__ bool epilogue_role(const Work& work, uint8_t* epi_sme
     int local;
     const CommonParams& p = work.get(item, local);
     int r, tm, tn;
-    decode_item(local, p, r, tm, tn);
+    decode_item(local, p, r, tm, tn, stride);
     const ProductDests& pd = p.prod[r];
-    const int row0 = tm * kBM + q * 32;
-    // undo the operand scaling of this (product, tile) exactly: 2^(s_A + s_B)
-    const int shift = p.maxbits_a ? panel_shift(p.maxbits_a[r * p.panels_a + tm]) +
-                                        panel_shift(p.maxbits_b[r * p.panels_b + tn])
-                                  : 0;
+    const int tm_cta = PAIR ? 2 * tm + rank : tm;  // 128-row tile of this CTA
+    const int row0 = tm_cta * kBM + q * 32;
+    // undo the operand scaling of this (product, tile) exactly: 2^(s_A + s_B); rows past the
+    // last A panel (odd CTA of a last, half-empty pair tile) are zero and need none
+    const int shift = (p.maxbits_a && tm_cta < p.panels_a)
+                          ? panel_shift(p.maxbits_a[r * p.panels_a + tm_cta]) +
+                                panel_shift(p.maxbits_b[r * p.panels_b + tn])
+                          : 0;
     // destinations are grouped by the sign of W[c, r] (coef = alpha * W[c, r])
     auto wneg = [&](const DestEntry& de) { return ((de.coef < 0.f) != (p.alpha < 0.f)) ? 1 : 0; };
     bool has_sign[2] = {false, false};
@@ -374,7 +414,12 @@ __device__ __forceinline__ bool epilogue_role(const Work& work, uint8_t* epi_sme
       if (c + 32 == BN) {
         // every TMEM read of this accumulator is complete: hand it back to the MMA warp
         tc_fence_before();
-        mbar_arrive(smem_u32(&acc_empty[acc]));
+        if (PAIR) {
+          __syncwarp();
+          if (lane == 0) mbar_arrive_cluster(mapa_shared(smem_u32(&acc_empty[acc]), 0));
+        } else {
+          mbar_arrive(smem_u32(&acc_empty[acc]));
+        }
       }
       const int col0 = tn * BN + c;
 #pragma unroll 1
@@ -437,9 +482,9 @@ __device__ __forceinline__ void drain_pause(uint64_t ns) {
 }
 
 // ------------------------------------------------------------ packed kernel
-template <int BN, int TERMS, int STAGES, int BK = kBK>
+template <int BN, int TERMS, int STAGES, int BK = kBK, bool PAIR = false>
 struct PackedCfg {
-  using SL = StageLayout<BN, TERMS, BK>;
+  using SL = StageLayout<BN, TERMS, BK, PAIR ? BN / 2 : BN>;
   static constexpr uint32_t kStageBytes = SL::kBytes;
   static constexpr uint32_t kEpiOffset = STAGES * kStageBytes;
   static constexpr uint32_t kBarOffset = kEpiOffset + kEpiBytes;
@@ -447,12 +492,18 @@ struct PackedCfg {
   static constexpr uint32_t kTmemCols = 2 * BN;
 };
 
-template <int BN, int TERMS, int STAGES, bool BF16, bool A_MN, bool B_MN, int BK>
+// PAIR: launched in clusters of two CTAs (a CTA pair).  A work item is then a 256 x BN pair
+// tile: the even CTA loads A rows 0..127 and B columns 0..BN/2-1 of it, the odd CTA rows
+// 128..255 and columns BN/2..BN-1; both CTAs' loads complete on the even CTA's stage barrier,
+// the even CTA's MMA thread issues the pair UMMAs, and each CTA's epilogue writes back its own
+// 128 rows.
+template <int BN, int TERMS, int STAGES, bool BF16, bool A_MN, bool B_MN, int BK, bool PAIR>
 __global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_constant__ KernelArgs args) {
-  using Cfg = PackedCfg<BN, TERMS, STAGES, BK>;
-  using SL = StageLayout<BN, TERMS, BK>;
+  constexpr int BNL = PAIR ? BN / 2 : BN;  // columns of the B tile held by this CTA
+  using Cfg = PackedCfg<BN, TERMS, STAGES, BK, PAIR>;
+  using SL = StageLayout<BN, TERMS, BK, BNL>;
   constexpr uint32_t kMnAtom = BK * 128;
-  static_assert(BN % 64 == 0 && BN <= 256, "UMMA N");
+  static_assert(BN % 64 == 0 && BN <= 256 && BNL % 64 == 0, "UMMA N");
   static_assert(Cfg::kTmemCols >= 32 && Cfg::kTmemCols <= 512, "TMEM columns");
   const PackedWork work{&args};
   const uint64_t timeout_ns = args.one.c.timeout_ns;
@@ -470,6 +521,7 @@ __global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_co
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
+  const int rank = PAIR ? static_cast<int>(cluster_ctarank()) : 0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -478,7 +530,8 @@ __global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_co
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(smem_u32(&acc_full[a]), 1);
-      mbar_init(smem_u32(&acc_empty[a]), 4 * 32);
+      // one arrival per epilogue thread, or (pair) per epilogue warp of both CTAs
+      mbar_init(smem_u32(&acc_empty[a]), PAIR ? 2 * 4 : 4 * 32);
     }
     *abort_flag = 0;
     fence_mbar_init();
@@ -493,63 +546,99 @@ __global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_co
   }
   if (warp == 1) {
     __syncwarp();
-    tmem_alloc(smem_u32(tmem_holder), Cfg::kTmemCols);
-    tmem_relinquish();
+    if (PAIR) {
+      tmem_alloc_pair(smem_u32(tmem_holder), Cfg::kTmemCols);
+      tmem_relinquish_pair();
+    } else {
+      tmem_alloc(smem_u32(tmem_holder), Cfg::kTmemCols);
+      tmem_relinquish();
+    }
   }
   tc_fence_before();
   __syncthreads();
+  if (PAIR) cluster_sync();  // the peer's barriers are initialised before anyone signals them
   tc_fence_after();
   const uint32_t tmem_base = *tmem_holder;
+  const int first = PAIR ? static_cast<int>(blockIdx.x >> 1) : static_cast<int>(blockIdx.x);
+  const int stride = PAIR ? static_cast<int>(gridDim.x >> 1) : static_cast<int>(gridDim.x);
+  if (PAIR) {
+    // the pair UMMAs write the same TMEM columns in both CTAs: check that both hold them
+    if (threadIdx.x == 0 &&
+        ld_shared_cluster_u32(mapa_shared(smem_u32(tmem_holder), static_cast<uint32_t>(rank ^ 1))) != tmem_base) {
+      atomicOr(err, kErrPairTmem);
+      *abort_flag = 1;
+    }
+    __syncthreads();
+  }
+  const bool run = !PAIR || *abort_flag == 0;  // the same in both CTAs of a pair
 
-  if (warp == 0) {
+  if (!run) {
+    // nothing issued: fall through to the teardown
+  } else if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
       const int total = work.num_items();
-      for (int item = blockIdx.x; ok && item < total; item += gridDim.x) {
+      for (int item = first; ok && item < total; item += stride) {
         int local;
         const PackedParams& pp = problem_of(args, item, local);
         const CommonParams& p = pp.c;
         int r, tm, tn;
-        decode_item(local, p, r, tm, tn);
+        decode_item(local, p, r, tm, tn, stride);
+        const int a_row = (PAIR ? 2 * tm + rank : tm) * kBM;  // first A row of this CTA
+        const int b_col = tn * BN + rank * BNL;               // first B column of this CTA
         for (int kb = 0; kb < p.nk; ++kb) {
           if (!mbar_wait(smem_u32(&empty[stage]), phase ^ 1u, timeout_ns, abort_flag)) {
             ok = false;
             break;
           }
           uint8_t* st = smem + stage * Cfg::kStageBytes;
-          const uint32_t fb = smem_u32(&full[stage]);
-          mbar_arrive_expect_tx(fb, Cfg::kStageBytes);
+          const uint32_t fb_local = smem_u32(&full[stage]);
+          // pair: both CTAs' bytes complete on the even CTA's barrier, which expects them all
+          const uint32_t fb = PAIR ? mapa_shared(fb_local, 0) : fb_local;
+          if (rank == 0) mbar_arrive_expect_tx(fb_local, (PAIR ? 2 : 1) * Cfg::kStageBytes);
+          auto load = [&](uint32_t dst, const CUtensorMap* map, int c0, int c1) {
+            if (PAIR)
+              tma_load_3d_pair(dst, map, fb, c0, c1, r);
+            else
+              tma_load_3d(dst, map, fb, c0, c1, r);
+          };
           if (A_MN) {
             // A operand sums stored k-rows x m-cols: two boxes of 64 (m) x BK (k)
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-              tma_load_3d(smem_u32(st + SL::kAHi + j * kMnAtom), &pp.tmA[0], fb, tm * kBM + 64 * j, kb * BK, r);
-              if (TERMS == 3)
-                tma_load_3d(smem_u32(st + SL::kALo + j * kMnAtom), &pp.tmA[1], fb, tm * kBM + 64 * j, kb * BK, r);
+              load(smem_u32(st + SL::kAHi + j * kMnAtom), &pp.tmA[0], a_row + 64 * j, kb * BK);
+              if (TERMS == 3) load(smem_u32(st + SL::kALo + j * kMnAtom), &pp.tmA[1], a_row + 64 * j, kb * BK);
             }
           } else {
-            tma_load_3d(smem_u32(st + SL::kAHi), &pp.tmA[0], fb, kb * BK, tm * kBM, r);
-            if (TERMS == 3) tma_load_3d(smem_u32(st + SL::kALo), &pp.tmA[1], fb, kb * BK, tm * kBM, r);
+            load(smem_u32(st + SL::kAHi), &pp.tmA[0], kb * BK, a_row);
+            if (TERMS == 3) load(smem_u32(st + SL::kALo), &pp.tmA[1], kb * BK, a_row);
           }
           if (B_MN) {
-            // B operand sums stored k-rows x n-cols: BN/64 boxes of 64 (n) x BK (k)
+            // B operand sums stored k-rows x n-cols: BNL/64 boxes of 64 (n) x BK (k)
 #pragma unroll
-            for (int j = 0; j < BN / 64; ++j) {
-              tma_load_3d(smem_u32(st + SL::kBHi + j * kMnAtom), &pp.tmB[0], fb, tn * BN + 64 * j, kb * BK, r);
-              if (TERMS == 3)
-                tma_load_3d(smem_u32(st + SL::kBLo + j * kMnAtom), &pp.tmB[1], fb, tn * BN + 64 * j, kb * BK, r);
+            for (int j = 0; j < BNL / 64; ++j) {
+              load(smem_u32(st + SL::kBHi + j * kMnAtom), &pp.tmB[0], b_col + 64 * j, kb * BK);
+              if (TERMS == 3) load(smem_u32(st + SL::kBLo + j * kMnAtom), &pp.tmB[1], b_col + 64 * j, kb * BK);
             }
           } else {
-            tma_load_3d(smem_u32(st + SL::kBHi), &pp.tmB[0], fb, kb * BK, tn * BN, r);
-            if (TERMS == 3) tma_load_3d(smem_u32(st + SL::kBLo), &pp.tmB[1], fb, kb * BK, tn * BN, r);
+            load(smem_u32(st + SL::kBHi), &pp.tmB[0], kb * BK, b_col);
+            if (TERMS == 3) load(smem_u32(st + SL::kBLo), &pp.tmB[1], kb * BK, b_col);
           }
           if (++stage == STAGES) {
             stage = 0;
             phase ^= 1u;
           }
+        }
+      }
+      // pair: every stage release of the peer's MMA thread has arrived before the CTA retires
+      for (int i = 0; PAIR && ok && i < STAGES; ++i) {
+        ok = mbar_wait(smem_u32(&empty[stage]), phase ^ 1u, timeout_ns, abort_flag);
+        if (++stage == STAGES) {
+          stage = 0;
+          phase ^= 1u;
         }
       }
       if (!ok) {
@@ -559,18 +648,17 @@ __global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_co
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
-      if (!mma_role<BN, TERMS, STAGES, BF16, A_MN, B_MN, PackedWork, BK>(work, smem, full, empty, acc_full,
-                                                                         acc_empty, tmem_base, abort_flag,
-                                                                         timeout_ns)) {
+    if (lane == 0 && rank == 0) {
+      if (!mma_role<BN, TERMS, STAGES, BF16, A_MN, B_MN, PackedWork, BK, PAIR>(
+              work, smem, full, empty, acc_full, acc_empty, tmem_base, abort_flag, timeout_ns)) {
         atomicOr(err, kErrMmaWait);
         *abort_flag = 1;
         drain_pause(2000000ull);
       }
     }
   } else if (warp >= 4) {
-    if (!epilogue_role<BN>(work, smem + Cfg::kEpiOffset, acc_full, acc_empty, tmem_base, abort_flag,
-                           timeout_ns, warp, lane)) {
+    if (!epilogue_role<BN, PackedWork, PAIR>(work, smem + Cfg::kEpiOffset, acc_full, acc_empty, tmem_base,
+                                             abort_flag, timeout_ns, warp, lane, rank)) {
       if (lane == 0) atomicOr(err, kErrEpilogueWait);
       *abort_flag = 1;
     }
@@ -578,10 +666,14 @@ __global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_co
 
   tc_fence_before();
   __syncthreads();
+  if (PAIR) cluster_sync();  // neither CTA retires while the other may still signal it
   if (warp == 1) {
     __syncwarp();
     tc_fence_after();
-    tmem_dealloc(tmem_base, Cfg::kTmemCols);
+    if (PAIR)
+      tmem_dealloc_pair(tmem_base, Cfg::kTmemCols);
+    else
+      tmem_dealloc(tmem_base, Cfg::kTmemCols);
   }
 }
 

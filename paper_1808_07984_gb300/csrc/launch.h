@@ -21,13 +21,18 @@ cudaError_t launch_beta(float* C, int64_t m, int64_t n, int64_t ldc, float beta,
 cudaError_t launch_debug_wait(unsigned* err, uint64_t timeout_ns, cudaStream_t s);
 
 // Tensor-core kernel over packed operand sums.  tile_n in {128, 256}; terms in {1, 3};
-// bf16 selects BF16 (true) or FP16 (false) operands.
+// bf16 selects BF16 (true) or FP16 (false) operands; pair selects the CTA-pair kernel
+// (256-row tiles, clusters of two CTAs, grid even; bk = 64 only).
 cudaError_t launch_packed(const KernelArgs& p, int tile_n, int terms, bool bf16, bool a_mn, bool b_mn,
-                          int bk, int grid, cudaStream_t s);
+                          int bk, bool pair, int grid, cudaStream_t s);
+cudaError_t launch_packed_pair(const KernelArgs& p, int tile_n, int terms, bool bf16, bool a_mn, bool b_mn,
+                               int bk, int grid, cudaStream_t s);
 bool packed_config_supported(int tile_n, int terms, bool bf16);
 
 // Tensor-core kernel that forms the operand sums on chip from FP32 source tiles
 // (tile 128 x 128; terms in {1, 3}).
-cudaError_t launch_fused(const FusedParams& p, int terms, int grid, cudaStream_t s);
+// transform_warps in {8, 16}: warps that form the operand sums from the FP32 source tiles.
+constexpr int kFusedTransformWarps = 16;
+cudaError_t launch_fused(const FusedParams& p, int terms, int transform_warps, int grid, cudaStream_t s);
 
 }  // namespace fmm
