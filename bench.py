@@ -412,8 +412,10 @@ def main():
         peak, peak_src = float(peaks["bf16_tflops_sustained"]), "measured (sustained bf16)"
     else:
         peak, peak_src = FALLBACK_PEAK_TFLOPS, "fallback"
+    burst = float(peaks["bf16_tflops"]) if peaks and "bf16_tflops" in peaks else None
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": recorded_traffic(workload_name(a, k)),
+                "frac_of_burst_peak": (achieved / burst) if burst else None,
                 "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                 "peak_source": peak_src,
                 "kernel": "fmm_packed_kernel", "kernel_ms": ker_ms,

@@ -102,7 +102,10 @@ typedef struct fmm_options {
                        2 = CTA pairs (clusters of two CTAs share 256-row tiles through
                            cta_group::2 UMMAs, each CTA loading half of the B tile;
                            bk must be 64) */
-    int reserved[2];
+    int round_tiles; /* tile-rounds schedule: output tiles per round, 0 = automatic (as many
+                        as keep the C blocks that one round updates within about a third of
+                        the L2 cache, at most one per CTA or CTA pair) */
+    int reserved[1];
 } fmm_options;
 
 /* Bytes of workspace fmm_gemm needs for this problem (0 when none).  Returns

@@ -40,7 +40,7 @@ class TuneTable(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int), ("tile_n", ctypes.c_int), ("num_ctas", ctypes.c_int),
                 ("schedule", ctypes.c_int), ("bk", ctypes.c_int), ("cta_pair", ctypes.c_int),
-                ("reserved", ctypes.c_int * 2)]
+                ("round_tiles", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 _lib = None
@@ -124,8 +124,9 @@ def _check(status: int):
 SCHEDULES = {"auto": 0, "product": 1, "rounds": 2}
 
 
-def _opts(algo="auto", tile_n=0, num_ctas=0, schedule="auto", bk=0, cta_pair=None):
+def _opts(algo="auto", tile_n=0, num_ctas=0, schedule="auto", bk=0, cta_pair=None, round_tiles=0):
     o = _Options()
+    o.round_tiles = int(round_tiles)
     o.bk = int(bk)
     o.cta_pair = 0 if cta_pair is None else (2 if cta_pair else 1)
     o.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
@@ -159,7 +160,8 @@ _IN_DTYPE = {0: "float32", 1: "bfloat16", 2: "float16", 3: "float32"}
 
 def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
          variant="split3", algo="auto", tile_n: int = 0, num_ctas: int = 0,
-         workspace=None, stream=None, schedule="auto", bk: int = 0, cta_pair=None):
+         workspace=None, stream=None, schedule="auto", bk: int = 0, cta_pair=None,
+         round_tiles: int = 0):
     """C = alpha * A @ B + beta * C on the current CUDA device (torch tensors).
 
     A (m x k) and B (k x n) are row-major CUDA tensors of the element type the
@@ -193,7 +195,7 @@ def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
         workspace = torch.empty(ws_need, dtype=torch.uint8, device=A.device)
     ws_ptr = workspace.data_ptr() if workspace is not None else None
     ws_bytes = workspace.numel() if workspace is not None else 0
-    o = _opts(algo, tile_n, num_ctas, schedule, bk, cta_pair)
+    o = _opts(algo, tile_n, num_ctas, schedule, bk, cta_pair, round_tiles)
     st = load().fmm_gemm_ex(m, n, k, float(alpha), A.data_ptr(), max(A.stride(0), 1),
                             B.data_ptr(), max(B.stride(0), 1), float(beta), C.data_ptr(),
                             max(C.stride(0), 1), int(levels), v, ws_ptr, ws_bytes,

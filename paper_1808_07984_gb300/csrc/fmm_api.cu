@@ -231,12 +231,9 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
   pl.hm = block_size(m, levels);
   pl.hn = block_size(n, levels);
   pl.hk = block_size(k, levels);
-  // automatic choice (measured on GB300): tile rounds keep each tile's destination blocks in
-  // L2 and are never slower by more than 1 %; product-major order only for long products
-  if (sched == 0)
-    pl.schedule = (levels == 2 && pl.hk >= 4096) ? kSchedProductMajor : kSchedTileRounds;
-  else
-    pl.schedule = sched == 2 ? kSchedTileRounds : kSchedProductMajor;
+  // automatic choice (measured on GB300): tile rounds, which keep the destination blocks of
+  // a round in L2
+  pl.schedule = sched == 1 ? kSchedProductMajor : kSchedTileRounds;
   const int bk = opt ? opt->bk : 0;
   const int cta_pair = opt ? opt->cta_pair : 0;
   if (cta_pair < 0 || cta_pair > 2) return fail(FMM_ERR_ARG, "cta_pair must be 0, 1 or 2");
@@ -316,6 +313,10 @@ int64_t block_extent(int64_t d, int64_t h, int b) {
   return std::min<int64_t>(std::max<int64_t>(d - b * h, 0), h);
 }
 
+// C bytes that the items of one tile round may update (a quarter of the 129 MB L2 of a GB300,
+// so that the operand panels of the round stay resident beside them).
+constexpr int64_t kRoundL2Bytes = int64_t(32) << 20;
+
 // Work list, destination maps and C tensor maps shared by both tensor-core kernels.
 // `live` lists the products that run (their kernel-side index is their position in it).
 fmm_status fill_common(CommonParams& c, const Plan& pl, const std::vector<Product>& prods,
@@ -375,6 +376,22 @@ fmm_status fill_common(CommonParams& c, const Plan& pl, const std::vector<Produc
     grid = 2 * static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(grid / 2, items)));
   else
     grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(grid, items)));
+  // Tile rounds.  When an item moves at least half as many C bytes (read and write of each
+  // destination tile) as operand bytes, keep the C blocks of a round (every destination block
+  // of its tile positions: 4^L tiles each) within kRoundL2Bytes; otherwise one tile per worker,
+  // which shares operand panels between the most concurrent items.  Measured on GB300.
+  const int workers = pl.pair ? grid / 2 : grid;
+  int64_t dests = 0;
+  for (size_t i = 0; i < live.size(); ++i) dests += c.prod[i].count;
+  const double c_bytes = live.empty() ? 0.0 : 8.0 * row_tile * pl.tile_n * dests / live.size();
+  const double op_bytes = 2.0 * (row_tile + pl.tile_n) * pl.hk * (pl.terms == 3 ? 2 : 1);
+  const int64_t footprint = static_cast<int64_t>(g) * g * row_tile * pl.tile_n * 4;
+  int64_t rt = workers;
+  if (opt && opt->round_tiles > 0)
+    rt = opt->round_tiles;
+  else if (c_bytes >= 0.5 * op_bytes)
+    rt = std::max<int64_t>(1, kRoundL2Bytes / footprint);
+  c.round_tiles = rt >= workers ? 0 : static_cast<int32_t>(rt);
   return FMM_OK;
 }
 

@@ -96,7 +96,8 @@ struct CommonParams {
   float alpha;
   int32_t tiles_m, tiles_n, nk, num_items;
   int32_t num_products;
-  int32_t schedule;  // Schedule
+  int32_t schedule;     // Schedule
+  int32_t round_tiles;  // kSchedTileRounds: tiles per round (0 = one per worker)
   int32_t c_tma;     // write-back by TMA reductions through tmC (C rows 16-byte aligned)
   int32_t c_vec4;    // element-wise path: C rows are 16-byte aligned, vector reductions allowed
   // power-of-two scaling of the operand sums (FP16 variant), else null: panel maxima of the
@@ -177,18 +178,19 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
   tn = in_g / gm;
 }
 
-// Work item -> (product r, tile row tm, tile column tn).  Worker b runs items b, b + G, ...
-// (G = number of workers).  kSchedProductMajor: item = r * tiles + t.  kSchedTileRounds: tiles are
-// taken G at a time; within a round the item index is r * G + (t - round start), so CTA b
-// runs products 0..R-1 of one tile back to back; the last, partial round is spread over all
-// CTAs product by product.
+// Work item -> (product r, tile row tm, tile column tn).  Worker b runs items b, b + W, ...
+// (W = number of workers).  kSchedProductMajor: item = r * tiles + t.  kSchedTileRounds: tiles
+// are taken G at a time (G = round_tiles, or W); within a round the item index is
+// r * G + (t - round start), so the workers run all R products of G tiles before the next
+// round (with G = W, worker b runs products 0..R-1 of one tile back to back), and the C
+// blocks of a round can stay in L2; the last, partial round is spread product by product.
 // `workers` is the number of independent item streams: CTAs, or CTA pairs of the pair kernel.
 __device__ __forceinline__ void decode_item(int item, const CommonParams& p, int& r, int& tm, int& tn,
                                             int workers) {
   const int tiles = p.tiles_m * p.tiles_n;
   int t;
   if (p.schedule == kSchedTileRounds) {
-    const int G = workers, R = p.num_products;
+    const int G = p.round_tiles > 0 ? p.round_tiles : workers, R = p.num_products;
     const int full = tiles / G;
     const int items_full = full * G * R;
     if (item < items_full) {

@@ -32,7 +32,7 @@ bool packed_config_supported(int tile_n, int terms, bool bf16);
 // Tensor-core kernel that forms the operand sums on chip from FP32 source tiles
 // (tile 128 x 128; terms in {1, 3}).
 // transform_warps in {8, 16}: warps that form the operand sums from the FP32 source tiles.
-constexpr int kFusedTransformWarps = 16;
+constexpr int kFusedTransformWarps = 8;
 cudaError_t launch_fused(const FusedParams& p, int terms, int transform_warps, int grid, cudaStream_t s);
 
 }  // namespace fmm
