@@ -379,7 +379,9 @@ fmm_status fill_common(CommonParams& c, const Plan& pl, const std::vector<Produc
   // Tile rounds.  When an item moves at least half as many C bytes (read and write of each
   // destination tile) as operand bytes, keep the C blocks of a round (every destination block
   // of its tile positions: 4^L tiles each) within kRoundL2Bytes; otherwise one tile per worker,
-  // which shares operand panels between the most concurrent items.  Measured on GB300.
+  // which shares operand panels between the most concurrent items.  Element-wise reductions
+  // (C rows not 16-byte aligned) keep one tile per worker: small rounds make concurrent items
+  // add into the same C elements, and those atomics serialise.  Measured on GB300.
   const int workers = pl.pair ? grid / 2 : grid;
   int64_t dests = 0;
   for (size_t i = 0; i < live.size(); ++i) dests += c.prod[i].count;
@@ -389,7 +391,7 @@ fmm_status fill_common(CommonParams& c, const Plan& pl, const std::vector<Produc
   int64_t rt = workers;
   if (opt && opt->round_tiles > 0)
     rt = opt->round_tiles;
-  else if (c_bytes >= 0.5 * op_bytes)
+  else if (c.c_tma && c_bytes >= 0.5 * op_bytes)
     rt = std::max<int64_t>(1, kRoundL2Bytes / footprint);
   c.round_tiles = rt >= workers ? 0 : static_cast<int32_t>(rt);
   return FMM_OK;

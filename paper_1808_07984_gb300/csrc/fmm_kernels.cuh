@@ -396,7 +396,14 @@ __device__ __forceinline__ bool epilogue_role(const Work& work, uint8_t* epi_sme
     const CommonParams& p = work.get(item, local);
     int r, tm, tn;
     decode_item(local, p, r, tm, tn, stride);
-    const ProductDests& pd = p.prod[r];
+    // Registers for everything the write-back loops read: `p` may live in global memory
+    // (batched launch), so the compiler would reload it after every global reduction.
+    const ProductDests pd = p.prod[r];
+    const CUtensorMap* const tmC = p.tmC;
+    float* const Cm = p.C;
+    const int64_t ldc = p.ldc;
+    const bool c_tma = p.c_tma != 0;
+    const float alpha = p.alpha;
     const int tm_cta = PAIR ? 2 * tm + rank : tm;  // 128-row tile of this CTA
     const int row0 = tm_cta * kBM + q * 32;
     // undo the operand scaling of this (product, tile) exactly: 2^(s_A + s_B); rows past the
@@ -406,7 +413,7 @@ __device__ __forceinline__ bool epilogue_role(const Work& work, uint8_t* epi_sme
                                 panel_shift(p.maxbits_b[r * p.panels_b + tn])
                           : 0;
     // destinations are grouped by the sign of W[c, r] (coef = alpha * W[c, r])
-    auto wneg = [&](const DestEntry& de) { return ((de.coef < 0.f) != (p.alpha < 0.f)) ? 1 : 0; };
+    auto wneg = [&](const DestEntry& de) { return ((de.coef < 0.f) != (alpha < 0.f)) ? 1 : 0; };
     bool has_sign[2] = {false, false};
     for (int d = 0; d < pd.count; ++d) has_sign[wneg(pd.d[d])] = true;
 #pragma unroll 1
@@ -427,7 +434,7 @@ __device__ __forceinline__ bool epilogue_role(const Work& work, uint8_t* epi_sme
 #pragma unroll 1
       for (int sg = 0; sg < 2; ++sg) {
         if (!has_sign[sg]) continue;
-        const float cf = ldexpf(sg ? -p.alpha : p.alpha, shift);
+        const float cf = ldexpf(sg ? -alpha : alpha, shift);
         uint8_t* sb = stage_base + buf * 4096;
         if (lane == 0) bulk_wait_group_read<1>();  // this buffer's previous reductions read it
         __syncwarp();
@@ -437,14 +444,14 @@ __device__ __forceinline__ bool epilogue_role(const Work& work, uint8_t* epi_sme
                                          cf * v[4 * j + 3]);
           *reinterpret_cast<float4*>(sb + lane * 128 + ((j ^ (lane & 7)) << 4)) = val;
         }
-        if (p.c_tma) {
+        if (c_tma) {
           fence_proxy_async_smem();
           __syncwarp();
           if (lane == 0) {
             for (int d = 0; d < pd.count; ++d) {
               const DestEntry& de = pd.d[d];
               if (wneg(de) != sg) continue;
-              tma_reduce_add_2d(&p.tmC[de.block], smem_u32(sb), col0, row0);
+              tma_reduce_add_2d(&tmC[de.block], smem_u32(sb), col0, row0);
             }
             bulk_commit_group();
           }
@@ -457,13 +464,13 @@ __device__ __forceinline__ bool epilogue_role(const Work& work, uint8_t* epi_sme
             const DestEntry de = pd.d[d];
             if (wneg(de) != sg) continue;
             if (col0 + lane >= de.cols) continue;
-            float* dst = p.C + de.offset + static_cast<int64_t>(row0) * p.ldc + col0 + lane;
+            float* dst = Cm + de.offset + static_cast<int64_t>(row0) * ldc + col0 + lane;
             const int nrows = min(32, de.rows - row0);
 #pragma unroll 4
             for (int i = 0; i < nrows; ++i) {
               const float x = *reinterpret_cast<const float*>(sb + i * 128 + (((lane >> 2) ^ (i & 7)) << 4) +
                                                               ((lane & 3) << 2));
-              atomicAdd(dst + static_cast<int64_t>(i) * p.ldc, x);
+              red_add_global_f32(dst + static_cast<int64_t>(i) * ldc, x);
             }
           }
         }

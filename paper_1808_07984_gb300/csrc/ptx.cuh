@@ -144,6 +144,16 @@ __device__ __forceinline__ void tma_load_3d_pair(uint32_t dst, const void* map, 
       : "memory");
 }
 
+// *p += v in global memory, no return value.  `p` is a generic pointer known to address global
+// memory; stating the state space keeps the compiler from issuing a generic atomic.  The value
+// comes from a register, so no memory clobber: shared-memory loads around it may be reordered.
+__device__ __forceinline__ void red_add_global_f32(float* p, float v) {
+  asm volatile(
+      "{\n\t.reg .u64 ga;\n\t"
+      "cvta.to.global.u64 ga, %0;\n\t"
+      "red.global.add.f32 [ga], %1;\n\t}" ::"l"(p), "f"(v));
+}
+
 // TMA reduction: global[tile at {x, y}] += shared tile, element-wise (f32 add for an f32 map).
 __device__ __forceinline__ void tma_reduce_add_2d(const void* map, uint32_t src, int x, int y) {
   asm volatile(
