@@ -241,6 +241,8 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
     return fail(FMM_ERR_UNSUPPORTED, "CTA pairs are built for the packed algorithm with bk = 64");
   // automatic choice: CTA pairs for the packed algorithm (each CTA loads half of the B tile)
   pl.pair = !on_chip && bk != 32 && cta_pair != 1;
+  if (!on_chip && !pl.pair && (a_mn || !b_mn))
+    return fail(FMM_ERR_UNSUPPORTED, "single-CTA tiles are built for the forward product only");
   const int row_tile = pl.pair ? 2 * kBM : kBM;
   if (pl.tile_n == 0) {
     // 256-wide tiles halve the A-operand traffic; keep 128 when that leaves fewer than four

@@ -37,14 +37,13 @@ static cudaError_t launch_mn(const KernelArgs& p, int tile_n, int terms, bool bf
   return cudaErrorInvalidValue;
 }
 
-// Operand layouts built: forward (A K-major, B MN-major), dA = dC B^T (A K-major, B K-major),
-// dB = A^T dC (A MN-major, B MN-major).
+// Single-CTA kernels are built for the forward layout (A K-major, B MN-major) that
+// fmm_gemm_ex can select; the backward products (dA: A and B K-major, dB: both MN-major) and
+// batched launches always run as CTA pairs.
 cudaError_t launch_packed(const KernelArgs& p, int tile_n, int terms, bool bf16, bool a_mn, bool b_mn,
                           int bk, bool pair, int grid, cudaStream_t s) {
   if (pair) return launch_packed_pair(p, tile_n, terms, bf16, a_mn, b_mn, bk, grid, s);
   if (!a_mn && b_mn) return launch_mn<false, true>(p, tile_n, terms, bf16, bk, grid, s);
-  if (!a_mn && !b_mn) return launch_mn<false, false>(p, tile_n, terms, bf16, bk, grid, s);
-  if (a_mn && b_mn) return launch_mn<true, true>(p, tile_n, terms, bf16, bk, grid, s);
   return cudaErrorInvalidValue;
 }
 

@@ -59,7 +59,8 @@ def _to_device(X, ld_pad, dtype):
 
 
 def run(m, n, k, levels, variant="split3", dist="uniform", seed=0, alpha=1.0, beta=0.0,
-        tile_n=0, pads=(0, 0, 0), c_fill=None, rows=None, schedule="auto", algo="auto", bk=0):
+        tile_n=0, pads=(0, 0, 0), c_fill=None, rows=None, schedule="auto", algo="auto", bk=0,
+        cta_pair=None, round_tiles=0):
     A, B = synth.problem(m, n, k, seed, dist)
     in_dtype = {"bf16": torch.bfloat16, "f16": torch.float16}.get(variant, torch.float32)
     Ad = _to_device(A, pads[0], in_dtype)
@@ -73,7 +74,7 @@ def run(m, n, k, levels, variant="split3", dist="uniform", seed=0, alpha=1.0, be
         if c_fill is not None:
             Cd.fill_(c_fill)
     fmm.gemm(Ad, Bd, Cd, alpha=alpha, beta=beta, levels=levels, variant=variant, tile_n=tile_n,
-             schedule=schedule, algo=algo, bk=bk)
+             schedule=schedule, algo=algo, bk=bk, cta_pair=cta_pair, round_tiles=round_tiles)
     fmm.device_status()
     C = Cd.cpu().numpy().astype(np.float64)
     if variant in ("bf16", "f16"):
@@ -117,6 +118,55 @@ def test_int_schedules_bit_exact(m, n, k, levels, schedule):
     """Both work orders, with enough tiles for several rounds and a partial last round."""
     C, C64, _, _ = run(m, n, k, levels, "split3", dist="int", seed=m + k, schedule=schedule)
     np.testing.assert_array_equal(C, C64)
+
+
+@pytest.mark.parametrize("cta_pair", [False, True])
+@pytest.mark.parametrize("tile_n", [128, 256])
+@pytest.mark.parametrize("levels", [0, 1, 2])
+@pytest.mark.parametrize("m,n,k", [(300, 520, 200), (129, 257, 65), (1000, 1200, 300), (520, 8, 400),
+                                   (1, 300, 1)])
+def test_cta_pair_and_single_cta_bit_exact(m, n, k, levels, tile_n, cta_pair):
+    """Both tensor-core kernels: one CTA per 128-row tile, and CTA pairs sharing 256-row tiles
+    (odd numbers of 128-row tiles leave the odd CTA of the last pair with rows past the end)."""
+    C, C64, _, _ = run(m, n, k, levels, "split3", dist="int", seed=5 * m + k, tile_n=tile_n,
+                       cta_pair=cta_pair)
+    np.testing.assert_array_equal(C, C64)
+
+
+@pytest.mark.parametrize("cta_pair", [False, True])
+@pytest.mark.parametrize("round_tiles", [1, 3, 7, 1000])
+@pytest.mark.parametrize("levels", [1, 2])
+def test_round_sizes_bit_exact(levels, round_tiles, cta_pair):
+    """Tile rounds of any size (several full rounds and a partial last one)."""
+    C, C64, _, _ = run(1000, 1200, 300, levels, "split3", dist="int", seed=11 + round_tiles,
+                       schedule="rounds", round_tiles=round_tiles, cta_pair=cta_pair)
+    np.testing.assert_array_equal(C, C64)
+
+
+@pytest.mark.parametrize("cta_pair", [False, True])
+@pytest.mark.parametrize("levels", [0, 1, 2])
+def test_f16_scaled_odd_tile_rows(levels, cta_pair):
+    """Scaled FP16 with an odd number of 128-row panels (the odd CTA of the last pair has none)."""
+    m, n, k = 300, 200, 150
+    C, C64, An, Bn = run(m, n, k, levels, "f16", seed=21, cta_pair=cta_pair)
+    assert oracle.normwise_error(C, C64, An, Bn) <= tolerance("f16", levels, k)
+    C, C64, _, _ = run(m, n, k, levels, "f16", dist="int", seed=22, cta_pair=cta_pair)
+    np.testing.assert_array_equal(C, C64)
+
+
+@pytest.mark.parametrize("cta_pair", [False, True])
+@pytest.mark.parametrize("levels", [0, 1, 2])
+def test_unaligned_ldc_both_kernels(levels, cta_pair):
+    """Element-wise write-back (ldc odd) from both tensor-core kernels."""
+    C, C64, _, _ = run(513, 300, 130, levels, "split3", dist="int", seed=19, pads=(0, 0, 1),
+                       cta_pair=cta_pair)
+    np.testing.assert_array_equal(C, C64)
+
+
+def test_cta_pair_rejected_with_bk32():
+    A = torch.zeros((64, 64), device="cuda")
+    with pytest.raises(fmm.FmmError):
+        fmm.gemm(A, A, levels=1, bk=32, cta_pair=True)
 
 
 @pytest.mark.parametrize("levels", [0, 1, 2])
