@@ -221,11 +221,6 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
     return fail(FMM_ERR_UNSUPPORTED,
                 "the fused and hybrid algorithms take FP32 A and B (split3 or plain_bf16) in the forward product");
   pl.tile_n = (opt && opt->tile_n) ? opt->tile_n : 0;
-  if (on_chip) {
-    if (pl.tile_n != 0 && pl.tile_n != kFusedTileN)
-      return fail(FMM_ERR_UNSUPPORTED, "the fused and hybrid algorithms use 128-wide tiles");
-    pl.tile_n = kFusedTileN;
-  }
   const int sched = opt ? opt->schedule : 0;
   if (sched < 0 || sched > 2) return fail(FMM_ERR_ARG, "schedule must be 0, 1 or 2");
   pl.hm = block_size(m, levels);
@@ -237,10 +232,19 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
   const int bk = opt ? opt->bk : 0;
   const int cta_pair = opt ? opt->cta_pair : 0;
   if (cta_pair < 0 || cta_pair > 2) return fail(FMM_ERR_ARG, "cta_pair must be 0, 1 or 2");
-  if (cta_pair == 2 && (on_chip || bk == 32))
-    return fail(FMM_ERR_UNSUPPORTED, "CTA pairs are built for the packed algorithm with bk = 64");
-  // automatic choice: CTA pairs for the packed algorithm (each CTA loads half of the B tile)
-  pl.pair = !on_chip && bk != 32 && cta_pair != 1;
+  if (cta_pair == 2 && bk == 32)
+    return fail(FMM_ERR_UNSUPPORTED, "CTA pairs use 64-deep stages (bk = 64)");
+  if (on_chip && bk == 32) return fail(FMM_ERR_UNSUPPORTED, "the fused and hybrid algorithms use bk = 64");
+  // automatic choice: CTA pairs (each CTA loads, or forms, half of the B tile)
+  pl.pair = bk != 32 && cta_pair != 1;
+  if (on_chip) {
+    // fused tiles: 128 x 128 per CTA, 256 x 256 per CTA pair
+    const int fused_n = pl.pair ? 2 * kFusedTileN : kFusedTileN;
+    if (pl.tile_n != 0 && pl.tile_n != fused_n)
+      return fail(FMM_ERR_UNSUPPORTED, pl.pair ? "the fused and hybrid algorithms use 256-wide tiles in CTA pairs"
+                                               : "the fused and hybrid algorithms use 128-wide tiles");
+    pl.tile_n = fused_n;
+  }
   if (!on_chip && !pl.pair && (a_mn || !b_mn))
     return fail(FMM_ERR_UNSUPPORTED, "single-CTA tiles are built for the forward product only");
   const int row_tile = pl.pair ? 2 * kBM : kBM;
@@ -470,7 +474,7 @@ fmm_status gemm_fused(const Plan& pl, int64_t m, int64_t n, int64_t k, float alp
   cudaError_t e;
   {
     PhaseScope ps(kPhaseTensor, s);
-    e = launch_fused(*fp, pl.terms, kFusedTransformWarps, grid, s);
+    e = launch_fused(*fp, pl.terms, kFusedTransformWarps, pl.pair, grid, s);
   }
   delete fp;
   if (e != cudaSuccess) return cuda_fail(e, "fused tensor-core pass");
@@ -576,7 +580,7 @@ fmm_status gemm_hybrid(const Plan& pl, int64_t m, int64_t n, int64_t k, float al
   }
   {
     PhaseScope ps(kPhaseTensor, s);
-    e = launch_fused(*fp, pl.terms, kFusedTransformWarps, grid, s);
+    e = launch_fused(*fp, pl.terms, kFusedTransformWarps, pl.pair, grid, s);
   }
   delete fp;
   if (e != cudaSuccess) return cuda_fail(e, "hybrid tensor-core pass");

@@ -1,29 +1,55 @@
 // fmm_fused.cu -- instantiations and launcher of the fused (on-chip operand sums) kernel.
-#include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <algorithm>
 #include "fmm_fused.cuh"
 #include "launch.h"
 
 namespace fmm {
 
-template <int TERMS, int TW>
+template <int TERMS, int TW, bool PAIR>
 static cudaError_t launch_fused_t(const FusedParams& p, int grid, cudaStream_t s) {
-  using Cfg = FusedCfg<TERMS>;
-  auto kern = fmm_fused_kernel<TERMS, TW>;
+  using Cfg = FusedCfg<TERMS, PAIR>;
+  static_assert(Cfg::kSmemBytes <= 232448, "shared memory per CTA");
+  auto kern = fmm_fused_kernel<TERMS, TW, PAIR>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(Cfg::kSmemBytes));
   if (e != cudaSuccess) return e;
-  kern<<<grid, fused_threads<TW>(), Cfg::kSmemBytes, s>>>(p);
-  return cudaGetLastError();
+  if (!PAIR) {
+    kern<<<grid, fused_threads<TW>(), Cfg::kSmemBytes, s>>>(p);
+    return cudaGetLastError();
+  }
+  if (grid < 2 || grid % 2 != 0) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(fused_threads<TW>(), 1, 1);
+  cfg.dynamicSmemBytes = Cfg::kSmemBytes;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  // at most one wave of CTA pairs (how many fit depends on how the SMs are grouped)
+  cfg.gridDim = dim3(static_cast<unsigned>(grid), 1, 1);
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) == cudaSuccess && clusters >= 1)
+    grid = std::min(grid, 2 * clusters);
+  else
+    cudaGetLastError();
+  cfg.gridDim = dim3(static_cast<unsigned>(grid), 1, 1);
+  return cudaLaunchKernelEx(&cfg, kern, p);
 }
 
-cudaError_t launch_fused(const FusedParams& p, int terms, int transform_warps, int grid, cudaStream_t s) {
-  if (transform_warps == 16) {
-    if (terms == 3) return launch_fused_t<3, 16>(p, grid, s);
-    if (terms == 1) return launch_fused_t<1, 16>(p, grid, s);
-  } else if (transform_warps == 8) {
-    if (terms == 3) return launch_fused_t<3, 8>(p, grid, s);
-    if (terms == 1) return launch_fused_t<1, 8>(p, grid, s);
+cudaError_t launch_fused(const FusedParams& p, int terms, int transform_warps, bool pair, int grid,
+                         cudaStream_t s) {
+  if (transform_warps != 8) return cudaErrorInvalidValue;
+  if (pair) {
+    if (terms == 3) return launch_fused_t<3, 8, true>(p, grid, s);
+    if (terms == 1) return launch_fused_t<1, 8, true>(p, grid, s);
+  } else {
+    if (terms == 3) return launch_fused_t<3, 8, false>(p, grid, s);
+    if (terms == 1) return launch_fused_t<1, 8, false>(p, grid, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -12,6 +12,11 @@
 //   warps 4-7   multi-destination write-back (epilogue_role).
 // No workspace: the sums never leave the SM.  A and B are FP32, 16-byte aligned, with
 // leading dimensions that are multiples of 4.
+//
+// PAIR: clusters of two CTAs share a 256 x 256 output tile through cta_group::2 UMMAs.  Each
+// CTA stages and sums its own 128 rows of the A-operand and its own 128 columns of the
+// B-operand (the same per-CTA shared-memory traffic as a 128 x 128 tile, for twice the
+// UMMA work); the transform warps of both CTAs arrive on the even CTA's operand barrier.
 #pragma once
 #include <cuda_bf16.h>
 #include "fmm_kernels.cuh"
@@ -21,19 +26,20 @@ namespace fmm {
 // 256 threads for the producer / MMA / epilogue roles plus TW transform warps
 template <int TW>
 constexpr int fused_threads() { return 256 + 32 * TW; }
-constexpr int kFusedBN = kFusedTileN;
+constexpr int kFusedBN = kFusedTileN;  // columns of the B-operand each CTA forms
 constexpr uint32_t kSlotBytes = 16384;
 
-template <int TERMS>
+template <int TERMS, bool PAIR>
 struct FusedCfg {
-  using SL = StageLayout<kFusedBN, TERMS>;
+  static constexpr int kTileN = PAIR ? 2 * kFusedBN : kFusedBN;  // UMMA N
+  using SL = StageLayout<kTileN, TERMS, kBK, kFusedBN>;
   static constexpr int kOpStages = TERMS == 3 ? 2 : 4;
   static constexpr int kSlots = 4;
   static constexpr uint32_t kSlotOffset = kOpStages * SL::kBytes;
   static constexpr uint32_t kEpiOffset = kSlotOffset + kSlots * kSlotBytes;
   static constexpr uint32_t kBarOffset = kEpiOffset + kEpiBytes;
   static constexpr uint32_t kSmemBytes = kBarOffset + 512 + 1024;
-  static constexpr uint32_t kTmemCols = 2 * kFusedBN;
+  static constexpr uint32_t kTmemCols = 2 * kTileN;
 };
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo_elem, float hi_elem) {
@@ -49,16 +55,17 @@ __device__ __forceinline__ void split2(float x0, float x1, uint32_t& hi, uint32_
   lo = pack_bf16x2(x0 - h0, x1 - h1);
 }
 
-template <int TERMS, int TW>
+template <int TERMS, int TW, bool PAIR>
 __global__ void __launch_bounds__(fused_threads<TW>(), 1) fmm_fused_kernel(const __grid_constant__ FusedParams fp) {
   static_assert(TW == 8 || TW == 16, "transform warps");
   constexpr int NT = 32 * TW;            // transform threads
   constexpr int AU = 512 / NT;           // A units (row, 8-wide k chunk) per thread per k half
   constexpr int BU = 1024 / NT;          // B units (k row, 4 n) per thread per k half
-  using Cfg = FusedCfg<TERMS>;
+  using Cfg = FusedCfg<TERMS, PAIR>;
   using SL = typename Cfg::SL;
   constexpr int S = Cfg::kOpStages;
   constexpr int NS = Cfg::kSlots;
+  constexpr int TN = Cfg::kTileN;
   const CommonParams& p = fp.c;
 
   extern __shared__ uint8_t smem_raw[];
@@ -76,6 +83,7 @@ __global__ void __launch_bounds__(fused_threads<TW>(), 1) fmm_fused_kernel(const
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
+  const int rank = PAIR ? static_cast<int>(cluster_ctarank()) : 0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) {
@@ -83,27 +91,46 @@ __global__ void __launch_bounds__(fused_threads<TW>(), 1) fmm_fused_kernel(const
       mbar_init(smem_u32(&slot_empty[s]), TW);  // one arrival per transform warp
     }
     for (int s = 0; s < S; ++s) {
-      mbar_init(smem_u32(&op_full[s]), TW);
+      mbar_init(smem_u32(&op_full[s]), PAIR ? 2 * TW : TW);  // pair: transform warps of both CTAs
       mbar_init(smem_u32(&op_empty[s]), 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(smem_u32(&acc_full[a]), 1);
-      mbar_init(smem_u32(&acc_empty[a]), 4 * 32);
+      mbar_init(smem_u32(&acc_empty[a]), PAIR ? 2 * 4 : 4 * 32);
     }
     *abort_flag = 0;
     fence_mbar_init();
   }
   if (warp == 1) {
     __syncwarp();
-    tmem_alloc(smem_u32(tmem_holder), Cfg::kTmemCols);
-    tmem_relinquish();
+    if (PAIR) {
+      tmem_alloc_pair(smem_u32(tmem_holder), Cfg::kTmemCols);
+      tmem_relinquish_pair();
+    } else {
+      tmem_alloc(smem_u32(tmem_holder), Cfg::kTmemCols);
+      tmem_relinquish();
+    }
   }
   tc_fence_before();
   __syncthreads();
+  if (PAIR) cluster_sync();  // the peer's barriers are initialised before anyone signals them
   tc_fence_after();
   const uint32_t tmem_base = *tmem_holder;
+  const int first = PAIR ? static_cast<int>(blockIdx.x >> 1) : static_cast<int>(blockIdx.x);
+  const int stride = PAIR ? static_cast<int>(gridDim.x >> 1) : static_cast<int>(gridDim.x);
+  if (PAIR) {
+    if (threadIdx.x == 0 &&
+        ld_shared_cluster_u32(mapa_shared(smem_u32(tmem_holder), static_cast<uint32_t>(rank ^ 1))) != tmem_base) {
+      atomicOr(p.err, kErrPairTmem);
+      *abort_flag = 1;
+    }
+    __syncthreads();
+  }
+  const bool run = !PAIR || *abort_flag == 0;  // the same in both CTAs of a pair
 
-  if (warp == 0) {
+  if (!run) {
+    // nothing issued: fall through to the teardown
+  } else if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
       int slot = 0;
@@ -120,16 +147,18 @@ __global__ void __launch_bounds__(fused_threads<TW>(), 1) fmm_fused_kernel(const
         }
         return true;
       };
-      for (int item = blockIdx.x; ok && item < p.num_items; item += gridDim.x) {
+      for (int item = first; ok && item < p.num_items; item += stride) {
         int r, tm, tn;
-        decode_item(item, p, r, tm, tn, gridDim.x);
+        decode_item(item, p, r, tm, tn, stride);
         const ProductSrc& ps = fp.src[r];
+        const int a_row = (PAIR ? 2 * tm + rank : tm) * kBM;  // this CTA's rows and columns
+        const int b_col = tn * TN + rank * kFusedBN;
         for (int kb = 0; ok && kb < p.nk; ++kb) {
           for (int h = 0; ok && h < 2; ++h) {
             for (int w = 0; ok && w < ps.na; ++w)
-              ok = issue(&fp.tmSA[ps.a_block[w]], kb * kBK + 32 * h, tm * kBM);
+              ok = issue(&fp.tmSA[ps.a_block[w]], kb * kBK + 32 * h, a_row);
             for (int w = 0; ok && w < ps.nb; ++w)
-              ok = issue(&fp.tmSB[ps.b_block[w]], tn * kFusedBN, kb * kBK + 32 * h);
+              ok = issue(&fp.tmSB[ps.b_block[w]], b_col, kb * kBK + 32 * h);
           }
         }
       }
@@ -140,17 +169,17 @@ __global__ void __launch_bounds__(fused_threads<TW>(), 1) fmm_fused_kernel(const
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
-      if (!mma_role<kFusedBN, TERMS, S, true, false, true>(OneProblem{&p}, smem, op_full, op_empty, acc_full,
-                                                           acc_empty, tmem_base, abort_flag, p.timeout_ns)) {
+    if (lane == 0 && rank == 0) {
+      if (!mma_role<TN, TERMS, S, true, false, true, OneProblem, kBK, PAIR>(
+              OneProblem{&p}, smem, op_full, op_empty, acc_full, acc_empty, tmem_base, abort_flag, p.timeout_ns)) {
         atomicOr(p.err, kErrMmaWait);
         *abort_flag = 1;
         drain_pause(2000000ull);
       }
     }
   } else if (warp >= 4 && warp < 8) {
-    if (!epilogue_role<kFusedBN>(OneProblem{&p}, smem + Cfg::kEpiOffset, acc_full, acc_empty, tmem_base,
-                                 abort_flag, p.timeout_ns, warp, lane)) {
+    if (!epilogue_role<TN, OneProblem, PAIR>(OneProblem{&p}, smem + Cfg::kEpiOffset, acc_full, acc_empty,
+                                             tmem_base, abort_flag, p.timeout_ns, warp, lane, rank)) {
       if (lane == 0) atomicOr(p.err, kErrEpilogueWait);
       *abort_flag = 1;
     }
@@ -167,9 +196,9 @@ __global__ void __launch_bounds__(fused_threads<TW>(), 1) fmm_fused_kernel(const
     int o = 0;
     uint32_t oph = 0;
     bool ok = true;
-    for (int item = blockIdx.x; ok && item < p.num_items; item += gridDim.x) {
+    for (int item = first; ok && item < p.num_items; item += stride) {
       int r, tm, tn;
-      decode_item(item, p, r, tm, tn, gridDim.x);
+      decode_item(item, p, r, tm, tn, stride);
       const ProductSrc& ps = fp.src[r];
       for (int kb = 0; ok && kb < p.nk; ++kb) {
         float aA[2][AU][8];
@@ -290,11 +319,25 @@ __global__ void __launch_bounds__(fused_threads<TW>(), 1) fmm_fused_kernel(const
         }
         fence_proxy_async_smem();  // generic-proxy stores -> visible to the tensor core
         __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&op_full[o]));
+        if (lane == 0) {
+          if (PAIR)
+            mbar_arrive_cluster(mapa_shared(smem_u32(&op_full[o]), 0));
+          else
+            mbar_arrive(smem_u32(&op_full[o]));
+        }
         if (++o == S) {
           o = 0;
           oph ^= 1u;
         }
+      }
+    }
+    // pair: every operand-stage release of the even CTA's MMA thread has arrived before the
+    // CTA retires
+    for (int i = 0; PAIR && ok && i < S; ++i) {
+      ok = mbar_wait(smem_u32(&op_empty[o]), oph ^ 1u, p.timeout_ns, abort_flag);
+      if (++o == S) {
+        o = 0;
+        oph ^= 1u;
       }
     }
     if (!ok) {
@@ -305,10 +348,14 @@ __global__ void __launch_bounds__(fused_threads<TW>(), 1) fmm_fused_kernel(const
 
   tc_fence_before();
   __syncthreads();
+  if (PAIR) cluster_sync();  // neither CTA retires while the other may still signal it
   if (warp == 1) {
     __syncwarp();
     tc_fence_after();
-    tmem_dealloc(tmem_base, Cfg::kTmemCols);
+    if (PAIR)
+      tmem_dealloc_pair(tmem_base, Cfg::kTmemCols);
+    else
+      tmem_dealloc(tmem_base, Cfg::kTmemCols);
   }
 }
 

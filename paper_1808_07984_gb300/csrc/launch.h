@@ -29,10 +29,11 @@ cudaError_t launch_packed_pair(const KernelArgs& p, int tile_n, int terms, bool 
                                int bk, int grid, cudaStream_t s);
 bool packed_config_supported(int tile_n, int terms, bool bf16);
 
-// Tensor-core kernel that forms the operand sums on chip from FP32 source tiles
-// (tile 128 x 128; terms in {1, 3}).
-// transform_warps in {8, 16}: warps that form the operand sums from the FP32 source tiles.
+// Tensor-core kernel that forms the operand sums on chip from FP32 source tiles (tile
+// 128 x 128, or 256 x 256 for a CTA pair; terms in {1, 3}).  transform_warps: warps that
+// form the operand sums (8 built; 16 measured slower on GB300).
 constexpr int kFusedTransformWarps = 8;
-cudaError_t launch_fused(const FusedParams& p, int terms, int transform_warps, int grid, cudaStream_t s);
+cudaError_t launch_fused(const FusedParams& p, int terms, int transform_warps, bool pair, int grid,
+                         cudaStream_t s);
 
 }  // namespace fmm

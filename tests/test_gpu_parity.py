@@ -218,6 +218,24 @@ def test_fused_int_bit_exact(m, n, k, levels, schedule):
     np.testing.assert_array_equal(C, C64)
 
 
+@pytest.mark.parametrize("cta_pair", [False, True])
+@pytest.mark.parametrize("algo", ["fused", "hybrid"])
+@pytest.mark.parametrize("m,n,k", [(300, 520, 200), (129, 257, 65), (1000, 1200, 300), (520, 8, 400)])
+def test_fused_single_cta_and_pair_bit_exact(m, n, k, algo, cta_pair):
+    """On-chip sums with one CTA per 128 x 128 tile and with CTA pairs on 256 x 256 tiles."""
+    for levels in ((1, 2) if algo == "fused" else (2,)):
+        C, C64, _, _ = run(m, n, k, levels, "split3", dist="int", seed=7 * m + n + k, algo=algo,
+                           pads=(_pad4(k), _pad4(n), 0), cta_pair=cta_pair)
+        np.testing.assert_array_equal(C, C64)
+
+
+@pytest.mark.parametrize("cta_pair", [False, True])
+def test_fused_float_single_cta_and_pair(cta_pair):
+    C, C64, An, Bn = run(640, 384, 768, 1, "split3", dist="gaussian", seed=31, algo="fused",
+                         cta_pair=cta_pair)
+    assert oracle.normwise_error(C, C64, An, Bn) <= tolerance("split3", 1, 768)
+
+
 @pytest.mark.parametrize("variant", ["split3", "plain_bf16"])
 @pytest.mark.parametrize("levels", [0, 1, 2])
 @pytest.mark.parametrize("m,n,k", [(7, 13, 5), (257, 129, 1000), (640, 384, 96)])
