@@ -217,8 +217,10 @@ fmm_status fmm_gemm_batched(int count, const int64_t* m, const int64_t* n, const
 const char* fmm_last_error(void);
 
 /* Synchronises `stream`, then reads and clears the device error word written
- * by bounded waits inside the kernels.  Returns FMM_ERR_TIMEOUT if any wait
- * gave up since the previous call, FMM_ERR_CUDA on a CUDA error. */
+ * by bounded waits and self-checks inside the kernels.  Returns FMM_ERR_TIMEOUT
+ * if any wait gave up since the previous call; FMM_ERR_CUDA on a CUDA error or a
+ * failed device-side check (a CTA pair given different TMEM columns, a parameter
+ * block naming a tensor map outside its table; the kernel skipped its work). */
 fmm_status fmm_device_status(void* stream);
 
 /* Limit, in nanoseconds, of every device-side wait of kernels launched after

@@ -454,11 +454,13 @@ fmm_status gemm_fused(const Plan& pl, int64_t m, int64_t n, int64_t k, float alp
     for (const Term& t : prods[r].a)
       if (a_live[t.block]) {
         ps.a_block[ps.na] = static_cast<int8_t>(t.block);
+        if (t.sign < 0) ps.a_neg |= static_cast<uint8_t>(1u << ps.na);
         ps.a_sign[ps.na++] = static_cast<int8_t>(t.sign);
       }
     for (const Term& t : prods[r].b)
       if (b_live[t.block]) {
         ps.b_block[ps.nb] = static_cast<int8_t>(t.block);
+        if (t.sign < 0) ps.b_neg |= static_cast<uint8_t>(1u << ps.nb);
         ps.b_sign[ps.nb++] = static_cast<int8_t>(t.sign);
       }
     if (ps.na == 0 || ps.nb == 0) continue;
@@ -564,10 +566,12 @@ fmm_status gemm_hybrid(const Plan& pl, int64_t m, int64_t n, int64_t k, float al
     for (int q2 = 0; q2 < 4; ++q2) {
       if (const int c = strassen_u(r2, q2)) {
         ps.a_block[ps.na] = static_cast<int8_t>(r1 * 4 + q2);
+        if (c < 0) ps.a_neg |= static_cast<uint8_t>(1u << ps.na);
         ps.a_sign[ps.na++] = static_cast<int8_t>(c);
       }
       if (const int c = strassen_v(r2, q2)) {
         ps.b_block[ps.nb] = static_cast<int8_t>(r1 * 4 + q2);
+        if (c < 0) ps.b_neg |= static_cast<uint8_t>(1u << ps.nb);
         ps.b_sign[ps.nb++] = static_cast<int8_t>(c);
       }
     }
@@ -1123,7 +1127,14 @@ fmm_status fmm_device_status(void* stream) {
     const unsigned zero = 0;
     e = cudaMemcpy(dev.err, &zero, sizeof zero, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "clearing the device error word");
-    char buf[96];
+    char buf[160];
+    if (word & (kErrPairTmem | kErrBadParams)) {
+      std::snprintf(buf, sizeof buf, "device-side check failed: %s (error bits 0x%x)",
+                    (word & kErrPairTmem) ? "CTA pair holds different TMEM columns"
+                                          : "parameter block names a tensor map outside its table",
+                    word);
+      return fail(FMM_ERR_CUDA, buf);
+    }
     std::snprintf(buf, sizeof buf, "device-side wait timed out (error bits 0x%x)", word);
     return fail(FMM_ERR_TIMEOUT, buf);
   }

@@ -150,15 +150,28 @@ __global__ void __launch_bounds__(fused_threads<TW>(), 1) fmm_fused_kernel(const
       for (int item = first; ok && item < p.num_items; item += stride) {
         int r, tm, tn;
         decode_item(item, p, r, tm, tn, stride);
-        const ProductSrc& ps = fp.src[r];
+        // the product's source lists, read once into registers (indexed parameter loads in
+        // the loops below would each go to the constant cache)
+        const uint32_t* psw = reinterpret_cast<const uint32_t*>(&fp.src[r]);
+        const uint32_t hdr = psw[kSrcWordHeader], ablk = psw[kSrcWordABlock], bblk = psw[kSrcWordBBlock];
+        const int na = hdr & 0xff, nb = (hdr >> 8) & 0xff;
+        // every map index must name one of the kMaxFusedSources maps: refuse the item otherwise
+        bool maps_ok = na <= kMaxDest && nb <= kMaxDest;
+        for (int w = 0; w < na && maps_ok; ++w) maps_ok = ((ablk >> (8 * w)) & 0xff) < kMaxFusedSources;
+        for (int w = 0; w < nb && maps_ok; ++w) maps_ok = ((bblk >> (8 * w)) & 0xff) < kMaxFusedSources;
+        if (!maps_ok) {
+          atomicOr(p.err, kErrBadParams);
+          ok = false;
+          break;
+        }
         const int a_row = (PAIR ? 2 * tm + rank : tm) * kBM;  // this CTA's rows and columns
         const int b_col = tn * TN + rank * kFusedBN;
         for (int kb = 0; ok && kb < p.nk; ++kb) {
           for (int h = 0; ok && h < 2; ++h) {
-            for (int w = 0; ok && w < ps.na; ++w)
-              ok = issue(&fp.tmSA[ps.a_block[w]], kb * kBK + 32 * h, a_row);
-            for (int w = 0; ok && w < ps.nb; ++w)
-              ok = issue(&fp.tmSB[ps.b_block[w]], b_col, kb * kBK + 32 * h);
+            for (int w = 0; ok && w < na; ++w)
+              ok = issue(&fp.tmSA[(ablk >> (8 * w)) & 0xff], kb * kBK + 32 * h, a_row);
+            for (int w = 0; ok && w < nb; ++w)
+              ok = issue(&fp.tmSB[(bblk >> (8 * w)) & 0xff], b_col, kb * kBK + 32 * h);
           }
         }
       }
@@ -199,7 +212,10 @@ __global__ void __launch_bounds__(fused_threads<TW>(), 1) fmm_fused_kernel(const
     for (int item = first; ok && item < p.num_items; item += stride) {
       int r, tm, tn;
       decode_item(item, p, r, tm, tn, stride);
-      const ProductSrc& ps = fp.src[r];
+      // counts and sign masks of the product's source terms, read once into registers
+      const uint32_t hdr = reinterpret_cast<const uint32_t*>(&fp.src[r])[kSrcWordHeader];
+      const int na = hdr & 0xff, nb = (hdr >> 8) & 0xff;
+      const uint32_t a_neg = (hdr >> 16) & 0xff, b_neg = hdr >> 24;
       for (int kb = 0; ok && kb < p.nk; ++kb) {
         float aA[2][AU][8];
         float aB[2][BU][4];
@@ -216,11 +232,11 @@ __global__ void __launch_bounds__(fused_threads<TW>(), 1) fmm_fused_kernel(const
         }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          for (int w = 0; w < ps.na; ++w) {
+          for (int w = 0; w < na; ++w) {
             if (ok) ok = mbar_wait(smem_u32(&slot_full[slot]), sph, p.timeout_ns, abort_flag);
             if (ok) {
               const uint8_t* sl = slots + slot * kSlotBytes;
-              const float sg = ps.a_sign[w] < 0 ? -1.f : 1.f;
+              const float sg = ((a_neg >> w) & 1u) ? -1.f : 1.f;
 #pragma unroll
               for (int u = 0; u < AU; ++u) {
 #pragma unroll
@@ -242,11 +258,11 @@ __global__ void __launch_bounds__(fused_threads<TW>(), 1) fmm_fused_kernel(const
               sph ^= 1u;
             }
           }
-          for (int w = 0; w < ps.nb; ++w) {
+          for (int w = 0; w < nb; ++w) {
             if (ok) ok = mbar_wait(smem_u32(&slot_full[slot]), sph, p.timeout_ns, abort_flag);
             if (ok) {
               const uint8_t* sl = slots + slot * kSlotBytes;
-              const float sg = ps.b_sign[w] < 0 ? -1.f : 1.f;
+              const float sg = ((b_neg >> w) & 1u) ? -1.f : 1.f;
 #pragma unroll
               for (int v = 0; v < BU; ++v) {
                 const int j = t + NT * v;

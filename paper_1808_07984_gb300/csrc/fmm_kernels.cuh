@@ -24,6 +24,7 @@
 // may run on different SMs at the same time without a race (the atomic-update scheme of
 // Section 3.3); beta is applied to C by a separate pass before the products start.
 #pragma once
+#include <cstddef>
 #include <cstdint>
 #include <cuda.h>
 #include "ptx.cuh"
@@ -63,7 +64,8 @@ enum ErrBits : unsigned {
   kErrEpilogueWait = 4u,
   kErrDebugWait = 8u,
   kErrTransformWait = 16u,
-  kErrPairTmem = 32u,  // the two CTAs of a pair were given different TMEM columns
+  kErrPairTmem = 32u,   // the two CTAs of a pair were given different TMEM columns
+  kErrBadParams = 64u,  // a parameter block named a tensor map outside its table
 };
 
 struct DestEntry {
@@ -116,12 +118,18 @@ struct PackedParams {
 };
 
 // Source blocks of one product's operands (fused path).
-struct ProductSrc {
-  int8_t na, nb;  // W_A, W_B (only blocks that exist in A / B are listed)
-  int8_t pad[2];
+// Kernels read whole 32-bit words of it: kSrcWordHeader = {na, nb, a_neg, b_neg},
+// kSrcWordABlock = a_block[0..3], kSrcWordBBlock = b_block[0..3].
+struct alignas(4) ProductSrc {
+  int8_t na, nb;         // W_A, W_B (only blocks that exist in A / B are listed)
+  uint8_t a_neg, b_neg;  // bit w set: term w enters with coefficient -1
   int8_t a_block[kMaxDest], a_sign[kMaxDest];
   int8_t b_block[kMaxDest], b_sign[kMaxDest];
 };
+constexpr int kSrcWordHeader = 0, kSrcWordABlock = 1, kSrcWordBBlock = 3;
+static_assert(offsetof(ProductSrc, a_neg) == 2 && offsetof(ProductSrc, b_neg) == 3, "ProductSrc header word");
+static_assert(offsetof(ProductSrc, a_block) == 4 * kSrcWordABlock, "ProductSrc a_block word");
+static_assert(offsetof(ProductSrc, b_block) == 4 * kSrcWordBBlock, "ProductSrc b_block word");
 
 // Kernel parameters of the fused path (operand sums formed on chip).
 constexpr int kMaxFusedSources = 28;  // hybrid two-level: 7 top-level sums x 4 quadrants
@@ -415,7 +423,9 @@ __device__ __forceinline__ bool epilogue_role(const Work& work, uint8_t* epi_sme
     // destinations are grouped by the sign of W[c, r] (coef = alpha * W[c, r])
     auto wneg = [&](const DestEntry& de) { return ((de.coef < 0.f) != (alpha < 0.f)) ? 1 : 0; };
     bool has_sign[2] = {false, false};
-    for (int d = 0; d < pd.count; ++d) has_sign[wneg(pd.d[d])] = true;
+#pragma unroll
+    for (int d = 0; d < kMaxDest; ++d)
+      if (d < pd.count) has_sign[wneg(pd.d[d])] = true;
 #pragma unroll 1
     for (int c = 0; c < BN; c += 32) {
       float v[32];
@@ -448,9 +458,10 @@ __device__ __forceinline__ bool epilogue_role(const Work& work, uint8_t* epi_sme
           fence_proxy_async_smem();
           __syncwarp();
           if (lane == 0) {
-            for (int d = 0; d < pd.count; ++d) {
+#pragma unroll
+            for (int d = 0; d < kMaxDest; ++d) {
               const DestEntry& de = pd.d[d];
-              if (wneg(de) != sg) continue;
+              if (d >= pd.count || wneg(de) != sg) continue;
               tma_reduce_add_2d(&tmC[de.block], smem_u32(sb), col0, row0);
             }
             bulk_commit_group();
@@ -460,9 +471,10 @@ __device__ __forceinline__ bool epilogue_role(const Work& work, uint8_t* epi_sme
           // that lane j adds column col0 + j and every instruction covers 32 consecutive
           // floats of one row.
           __syncwarp();
-          for (int d = 0; d < pd.count; ++d) {
+#pragma unroll
+          for (int d = 0; d < kMaxDest; ++d) {
             const DestEntry de = pd.d[d];
-            if (wneg(de) != sg) continue;
+            if (d >= pd.count || wneg(de) != sg) continue;
             if (col0 + lane >= de.cols) continue;
             float* dst = Cm + de.offset + static_cast<int64_t>(row0) * ldc + col0 + lane;
             const int nrows = min(32, de.rows - row0);
