@@ -52,6 +52,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-classical", action="store_true")
+    ap.add_argument("--no-fused", action="store_true",
+                    help="skip the measurement of the on-chip-sums (fused) algorithm")
     return ap.parse_args()
 
 
@@ -262,9 +264,9 @@ def main():
     ws = torch.empty(max(ws_bytes, 256), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(levels):
-        fmm.gemm(A_d, B_d, C_d, 1.0, 0.0, levels=levels, variant=a.variant, algo=a.algo,
-                 tile_n=a.tile_n, workspace=ws, stream=stream)
+    def step(levels, algo=None):
+        fmm.gemm(A_d, B_d, C_d, 1.0, 0.0, levels=levels, variant=a.variant, algo=algo or a.algo,
+                 tile_n=0 if algo else a.tile_n, workspace=ws, stream=stream)
 
     def barrier():
         if dist is not None:
@@ -277,9 +279,9 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    def timed(levels, steps, warmup, profile=False):
+    def timed(levels, steps, warmup, profile=False, algo=None):
         for _ in range(warmup):
-            step(levels)
+            step(levels, algo)
         fmm.device_status()
         barrier()
         torch.cuda.synchronize()
@@ -290,7 +292,7 @@ def main():
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(steps):
-            step(levels)
+            step(levels, algo)
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -325,6 +327,19 @@ def main():
         ms0 = max_over_ranks(ms0)
         classical = {"value": world * flops / (ms0 * 1e-3) * 1e-12, "ms_per_step": ms0,
                      "tensor_kernel_ms": prof0["tensor"][0] / max(prof0["tensor"][1], 1)}
+
+    # ---- the same product with the operand sums formed on chip while the source tiles load
+    # (the fused algorithm: no workspace, sums never in HBM), measured beside the default
+    fused = None
+    do_fused = (not a.no_fused and a.algo == "auto" and a.variant in ("split3", "plain_bf16")
+                and a.levels in (1, 2))
+    if do_fused:
+        fsteps = max(1, min(a.steps, 5))
+        msf, proff = timed(a.levels, fsteps, 1, profile=True, algo="fused")
+        msf = max_over_ranks(msf)
+        fused = {"algo": "fused (operand sums formed in shared memory as the tiles load)",
+                 "value": world * flops / (msf * 1e-3) * 1e-12, "ms_per_step": msf, "steps": fsteps,
+                 "tensor_kernel_ms": proff["tensor"][0] / max(proff["tensor"][1], 1)}
 
     # ---- end to end through host buffers: every step copies its A, B from pinned host memory
     # and its C back to pinned host memory inside the timed region.  Two device buffer sets
@@ -401,6 +416,12 @@ def main():
         err0 = oracle.normwise_error(C_s0, C64, np.linalg.norm(A[rows].astype(np.float64)),
                                      np.linalg.norm(B.astype(np.float64)))
         classical["fp64_normwise_err_sampled"] = err0
+    if fused is not None:
+        step(a.levels, "fused")
+        torch.cuda.synchronize()
+        C_sf = C_d[torch.from_numpy(rows).to(dev)].cpu().numpy()
+        fused["fp64_normwise_err_sampled"] = oracle.normwise_error(
+            C_sf, C64, np.linalg.norm(A[rows].astype(np.float64)), np.linalg.norm(B.astype(np.float64)))
 
     # ---- roofline of the dominant kernel (the tensor-core kernel)
     terms = 3 if a.variant == "split3" else 1
@@ -437,6 +458,7 @@ def main():
         "config": config_dict(a, k, {"parallelism": f"replicas{world}" if world > 1 else "single"}),
         "fp64_normwise_err_sampled": err,
         "classical": classical,
+        "fused": fused,
         "speedup_vs_classical": (value / classical["value"]) if classical else None,
         "phases": phases,
         "roofline": roofline,
