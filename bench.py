@@ -425,8 +425,11 @@ def main():
 
     # ---- roofline of the dominant kernel (the tensor-core kernel)
     terms = 3 if a.variant == "split3" else 1
+    # per launch of the tensor-core kernel (a pipelined product launches it once per
+    # top-level product, each with 1/7 of the work)
+    launches_per_step = max(prof["tensor"][1], 1) / a.steps
     ker_ms = prof["tensor"][0] / max(prof["tensor"][1], 1)
-    mma_flops = (7.0 / 8.0) ** a.levels * flops * terms
+    mma_flops = (7.0 / 8.0) ** a.levels * flops * terms / launches_per_step
     achieved = mma_flops / (ker_ms * 1e-3) * 1e-12
     peaks = load_peaks()
     if peaks and "bf16_tflops_sustained" in peaks:
@@ -440,6 +443,7 @@ def main():
                 "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                 "peak_source": peak_src,
                 "kernel": "fmm_packed_kernel", "kernel_ms": ker_ms,
+                "launches_per_step": launches_per_step,
                 "algorithmic_flops_per_launch": mma_flops}
     phases = {p: {"ms_per_step": v[0] / a.steps, "launches": v[1]} for p, v in prof.items()}
     gpu_launches = int(sum(v[1] for v in prof.values()))

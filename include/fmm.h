@@ -103,9 +103,13 @@ typedef struct fmm_options {
                            cta_group::2 UMMAs, each CTA loading half of the B tile;
                            bk must be 64) */
     int round_tiles; /* tile-rounds schedule: output tiles per round, 0 = automatic (as many
-                        as keep the C blocks that one round updates within about a third of
-                        the L2 cache, at most one per CTA or CTA pair) */
-    int reserved[1];
+                        as keep the C blocks that one round updates within a quarter of the
+                        L2 cache when C traffic dominates, else one per CTA or CTA pair) */
+    int pipeline;    /* packed algorithm, levels >= 1: 0 = automatic, 1 = off, 2 = on.  On:
+                        the operand sums are formed in seven passes, one per top-level
+                        product, on an internal stream, and the tensor-core kernel runs each
+                        top-level product's 7^(L-1) products as soon as their sums exist, so
+                        the sum passes overlap the products (joined back into `stream`). */
 } fmm_options;
 
 /* Bytes of workspace fmm_gemm needs for this problem (0 when none).  Returns
@@ -162,6 +166,15 @@ fmm_status fmm_gemm_backward(int64_t m, int64_t n, int64_t k,
                              const float* dC, int64_t lddc, float* dA, int64_t ldda,
                              float* dB, int64_t lddb, int levels, int variant,
                              void* workspace, size_t ws_bytes, void* stream);
+/* As fmm_gemm_backward, with options (NULL = defaults).  The backward products run on
+ * the packed algorithm in CTA pairs: algo must be 0 or FMM_ALGO_PACKED, cta_pair 0 or 2;
+ * pipeline, round_tiles, schedule, tile_n and num_ctas apply as in fmm_gemm_ex. */
+fmm_status fmm_gemm_backward_ex(int64_t m, int64_t n, int64_t k,
+                                const void* A, int64_t lda, const void* B, int64_t ldb,
+                                const float* dC, int64_t lddc, float* dA, int64_t ldda,
+                                float* dB, int64_t lddb, int levels, int variant,
+                                void* workspace, size_t ws_bytes, void* stream,
+                                const fmm_options* opt);
 size_t fmm_workspace_size_backward(int64_t m, int64_t n, int64_t k, int levels, int variant);
 
 /* ------------------------------------------------------------------ batching

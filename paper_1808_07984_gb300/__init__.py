@@ -40,7 +40,7 @@ class TuneTable(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int), ("tile_n", ctypes.c_int), ("num_ctas", ctypes.c_int),
                 ("schedule", ctypes.c_int), ("bk", ctypes.c_int), ("cta_pair", ctypes.c_int),
-                ("round_tiles", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
+                ("round_tiles", ctypes.c_int), ("pipeline", ctypes.c_int)]
 
 
 _lib = None
@@ -76,6 +76,8 @@ def load() -> ctypes.CDLL:
     L.fmm_gemm_backward.restype = i32
     L.fmm_gemm_backward.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64,
                                     i32, i32, vp, sz, vp]
+    L.fmm_gemm_backward_ex.restype = i32
+    L.fmm_gemm_backward_ex.argtypes = L.fmm_gemm_backward.argtypes + [ctypes.POINTER(_Options)]
     L.fmm_workspace_size_backward.restype = sz
     L.fmm_workspace_size_backward.argtypes = [i64, i64, i64, i32, i32]
     L.fmm_tune_default.restype = None
@@ -124,9 +126,11 @@ def _check(status: int):
 SCHEDULES = {"auto": 0, "product": 1, "rounds": 2}
 
 
-def _opts(algo="auto", tile_n=0, num_ctas=0, schedule="auto", bk=0, cta_pair=None, round_tiles=0):
+def _opts(algo="auto", tile_n=0, num_ctas=0, schedule="auto", bk=0, cta_pair=None, round_tiles=0,
+          pipeline=None):
     o = _Options()
     o.round_tiles = int(round_tiles)
+    o.pipeline = 0 if pipeline is None else (2 if pipeline else 1)
     o.bk = int(bk)
     o.cta_pair = 0 if cta_pair is None else (2 if cta_pair else 1)
     o.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
@@ -161,7 +165,7 @@ _IN_DTYPE = {0: "float32", 1: "bfloat16", 2: "float16", 3: "float32"}
 def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
          variant="split3", algo="auto", tile_n: int = 0, num_ctas: int = 0,
          workspace=None, stream=None, schedule="auto", bk: int = 0, cta_pair=None,
-         round_tiles: int = 0):
+         round_tiles: int = 0, pipeline=None):
     """C = alpha * A @ B + beta * C on the current CUDA device (torch tensors).
 
     A (m x k) and B (k x n) are row-major CUDA tensors of the element type the
@@ -170,6 +174,8 @@ def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
     but columns must be contiguous.  ``workspace`` is a uint8 CUDA tensor; one of
     the right size is allocated when None.  ``cta_pair``: None = automatic, True = CTA
     pairs (256-row tiles shared by a cluster of two CTAs), False = one CTA per tile.
+    ``pipeline``: None = automatic, True / False = overlap the operand-sum passes with the
+    tensor-core kernel one top-level product at a time, or not.
     """
     import torch
     v = _variant(variant)
@@ -195,7 +201,7 @@ def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
         workspace = torch.empty(ws_need, dtype=torch.uint8, device=A.device)
     ws_ptr = workspace.data_ptr() if workspace is not None else None
     ws_bytes = workspace.numel() if workspace is not None else 0
-    o = _opts(algo, tile_n, num_ctas, schedule, bk, cta_pair, round_tiles)
+    o = _opts(algo, tile_n, num_ctas, schedule, bk, cta_pair, round_tiles, pipeline)
     st = load().fmm_gemm_ex(m, n, k, float(alpha), A.data_ptr(), max(A.stride(0), 1),
                             B.data_ptr(), max(B.stride(0), 1), float(beta), C.data_ptr(),
                             max(C.stride(0), 1), int(levels), v, ws_ptr, ws_bytes,
@@ -212,11 +218,11 @@ def workspace_size_backward(m, n, k, levels=1, variant="split3") -> int:
 
 
 def gemm_backward(A, B, dC, levels: int = 1, variant="split3", need_dA=True, need_dB=True,
-                  workspace=None, stream=None):
-    """(dA, dB) = (dC @ B.T, A.T @ dC) as Strassen products through fmm_gemm_backward.
+                  workspace=None, stream=None, pipeline=None):
+    """(dA, dB) = (dC @ B.T, A.T @ dC) as Strassen products through fmm_gemm_backward_ex.
 
     A (m x k) and B (k x n) have the variant's element type, dC (m x n) is float32; the
-    gradients are float32 (None where not requested)."""
+    gradients are float32 (None where not requested).  ``pipeline`` as in gemm()."""
     import torch
     v = _variant(variant)
     m, k = A.shape
@@ -234,13 +240,14 @@ def gemm_backward(A, B, dC, levels: int = 1, variant="split3", need_dA=True, nee
     ws_need = workspace_size_backward(m, n, k, levels, v)
     if workspace is None and ws_need > 0:
         workspace = torch.empty(ws_need, dtype=torch.uint8, device=A.device)
-    st = load().fmm_gemm_backward(
+    o = _opts(pipeline=pipeline)
+    st = load().fmm_gemm_backward_ex(
         m, n, k, A.data_ptr(), max(A.stride(0), 1), B.data_ptr(), max(B.stride(0), 1),
         dC.data_ptr(), max(dC.stride(0), 1),
         dA.data_ptr() if dA is not None else None, max(k, 1),
         dB.data_ptr() if dB is not None else None, max(n, 1),
         int(levels), v, workspace.data_ptr() if workspace is not None else None,
-        workspace.numel() if workspace is not None else 0, _stream_handle(stream))
+        workspace.numel() if workspace is not None else 0, _stream_handle(stream), ctypes.byref(o))
     _check(st)
     return dA, dB
 

@@ -35,6 +35,7 @@ enum Phase { kPhaseBeta = 0, kPhasePack = 1, kPhaseTensor = 2, kNumPhases = 3 };
 struct EventPair {
   cudaEvent_t a = nullptr, b = nullptr;
   int phase = 0;
+  int launches = 1;  // kernel launches the scope brackets
 };
 std::mutex g_prof_mu;
 bool g_prof_on = false;
@@ -45,7 +46,7 @@ struct PhaseScope {
   EventPair ev;
   cudaStream_t s;
   bool on = false;
-  PhaseScope(int phase, cudaStream_t stream) : s(stream) {
+  PhaseScope(int phase, cudaStream_t stream, int launches = 1) : s(stream) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (!g_prof_on) return;
     if (!g_prof_free.empty()) {
@@ -55,6 +56,7 @@ struct PhaseScope {
       if (cudaEventCreate(&ev.a) != cudaSuccess || cudaEventCreate(&ev.b) != cudaSuccess) return;
     }
     ev.phase = phase;
+    ev.launches = launches;
     on = cudaEventRecord(ev.a, s) == cudaSuccess;
   }
   ~PhaseScope() {
@@ -182,6 +184,7 @@ struct Plan {
   int tile_n = 128;
   int bk = 64;  // k-elements per pipeline stage of the packed kernel (64, or 32 for split3)
   bool pair = false;  // packed kernel in CTA pairs: 256-row tiles shared by two CTAs
+  bool pipeline = false;  // sum passes per top-level product, overlapped with the products
   int algo = FMM_ALGO_PACKED;
   int schedule = kSchedProductMajor;
   bool scaled = false;      // FP16 operands with power-of-two scaling per panel
@@ -247,6 +250,15 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
   }
   if (!on_chip && !pl.pair && (a_mn || !b_mn))
     return fail(FMM_ERR_UNSUPPORTED, "single-CTA tiles are built for the forward product only");
+  const int pipe = opt ? opt->pipeline : 0;
+  if (pipe < 0 || pipe > 2) return fail(FMM_ERR_ARG, "pipeline must be 0, 1 or 2");
+  // automatic choice (measured on GB300): per top-level product only for two-level products
+  // with short inner blocks (h_k <= 1024) on large C.  There each launch updates 1-2 of C's
+  // four quadrants, which keeps its C traffic in L2 (+16 % at 16384^2 x 4096, +17 % for
+  // 30001 x 29999 x 4097); for square products the seven launches cost more than the hidden
+  // sum passes save (-10 % at 16384^3).
+  pl.pipeline = !on_chip && levels >= 1 &&
+                (pipe == 2 || (pipe == 0 && levels == 2 && pl.hk <= 1024 && pl.hm >= 2048 && pl.hn >= 2048));
   const int row_tile = pl.pair ? 2 * kBM : kBM;
   if (pl.tile_n == 0) {
     // 256-wide tiles halve the A-operand traffic; keep 128 when that leaves fewer than four
@@ -520,6 +532,7 @@ fmm_status gemm_hybrid(const Plan& pl, int64_t m, int64_t n, int64_t k, float al
   sa.prod_stride = h1m * h1k;
   sa.out_f32 = P;
   sa.terms = 0;
+  sa.chunk = -1;
   sa.vec_ok = (reinterpret_cast<uintptr_t>(A) % 16 == 0 && lda % 4 == 0) ? 1 : 0;
   cudaError_t e;
   {
@@ -635,6 +648,8 @@ struct PackedJob {
   int grid = 0;
   bool has_work = false;  // k > 0 and alpha != 0
   PackedParams params;
+  // pipelined plans: one parameter block per top-level product (its 7^(L-1) products)
+  std::vector<PackedParams> chunks;
 };
 
 fmm_status prepare_packed(const Plan& pl, int64_t m, int64_t n, int64_t k, float alpha, Operand a,
@@ -670,6 +685,7 @@ fmm_status prepare_packed(const Plan& pl, int64_t m, int64_t n, int64_t k, float
   sa.out_hi = a_hi;
   sa.out_lo = a_lo;
   sa.terms = pl.terms;
+  sa.chunk = -1;  // every product (the pipelined path sets one top-level product per pass)
   sa.vec_ok = (reinterpret_cast<uintptr_t>(a.X) % 16 == 0 && a.ld % 4 == 0) ? 1 : 0;
   SumParams& sb = job.sb;
   sb = sa;
@@ -699,20 +715,28 @@ fmm_status prepare_packed(const Plan& pl, int64_t m, int64_t n, int64_t k, float
   fmm_status st = FMM_OK;
   const int nb = pl.terms == 3 ? 2 : 1;
   // K-major tiles: BK-deep rows, 128-byte swizzle (BK 64) or 64-byte swizzle (BK 32);
-  // MN-major tiles: boxes of 64 (m or n) x BK (k), 128-byte swizzle
+  // MN-major tiles: boxes of 64 (m or n) x BK (k), 128-byte swizzle.  Maps over products
+  // prod0 .. prod0 + nprod - 1 (the z coordinate counts from prod0).
   const CUtensorMapSwizzle kswz = pl.bk == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
-  for (int t = 0; t < nb && st == FMM_OK; ++t) {
-    if (pl.a_mn)
-      st = encode_3d(&pp->tmA[t], t ? a_lo : a_hi, pl.hm, pl.hk, pl.R, pl.lda_w, 64, pl.bk);
-    else
-      st = encode_3d(&pp->tmA[t], t ? a_lo : a_hi, pl.hk, pl.hm, pl.R, pl.lda_w, pl.bk, kBM, kswz);
-    if (st != FMM_OK) break;
-    if (pl.b_mn)
-      st = encode_3d(&pp->tmB[t], t ? b_lo : b_hi, pl.hn, pl.hk, pl.R, pl.ldb_w, 64, pl.bk);
-    else
-      st = encode_3d(&pp->tmB[t], t ? b_lo : b_hi, pl.hk, pl.hn, pl.R, pl.ldb_w, pl.bk,
-                     pl.pair ? pl.tile_n / 2 : pl.tile_n, kswz);
-  }
+  auto encode_maps = [&](PackedParams* q, int prod0, int nprod) -> fmm_status {
+    fmm_status es = FMM_OK;
+    for (int t = 0; t < nb && es == FMM_OK; ++t) {
+      uint16_t* ab = (t ? a_lo : a_hi) + prod0 * sa.prod_stride;
+      uint16_t* bb = (t ? b_lo : b_hi) + prod0 * sb.prod_stride;
+      if (pl.a_mn)
+        es = encode_3d(&q->tmA[t], ab, pl.hm, pl.hk, nprod, pl.lda_w, 64, pl.bk);
+      else
+        es = encode_3d(&q->tmA[t], ab, pl.hk, pl.hm, nprod, pl.lda_w, pl.bk, kBM, kswz);
+      if (es != FMM_OK) break;
+      if (pl.b_mn)
+        es = encode_3d(&q->tmB[t], bb, pl.hn, pl.hk, nprod, pl.ldb_w, 64, pl.bk);
+      else
+        es = encode_3d(&q->tmB[t], bb, pl.hk, pl.hn, nprod, pl.ldb_w, pl.bk,
+                       pl.pair ? pl.tile_n / 2 : pl.tile_n, kswz);
+    }
+    return es;
+  };
+  st = encode_maps(pp, 0, pl.R);
   const std::vector<Product> prods = make_products(pl.L);
   std::vector<int> live(pl.R);
   for (int r = 0; r < pl.R; ++r) live[r] = r;
@@ -724,7 +748,121 @@ fmm_status prepare_packed(const Plan& pl, int64_t m, int64_t n, int64_t k, float
     pp->c.panels_a = static_cast<int32_t>(pl.panels_a);
     pp->c.panels_b = static_cast<int32_t>(pl.panels_b);
   }
+  job.chunks.clear();
+  if (pl.pipeline) {
+    // top-level product c: products c * P .. c * P + P - 1 (P = 7^(L-1)), kernel-local 0 .. P-1
+    const int P = pl.R / 7;
+    job.chunks.resize(7, *pp);
+    for (int c = 0; c < 7 && st == FMM_OK; ++c) {
+      PackedParams& q = job.chunks[c];
+      st = encode_maps(&q, c * P, P);
+      for (int j = 0; j < kMaxProducts; ++j) q.c.prod[j] = j < P ? pp->c.prod[c * P + j] : ProductDests{};
+      q.c.num_products = P;
+      q.c.num_items = P * pp->c.tiles_m * pp->c.tiles_n;
+      if (job.maxbits) {
+        q.c.maxbits_a = pp->c.maxbits_a + static_cast<int64_t>(c) * P * pl.panels_a;
+        q.c.maxbits_b = pp->c.maxbits_b + static_cast<int64_t>(c) * P * pl.panels_b;
+      }
+    }
+  }
+  return st;
+}
+
+// Operand-sum passes (A, then B) of one top-level product of a pipelined job on stream s.
+fmm_status launch_chunk_sums(const PackedJob& job, int c, const DeviceInfo& dev, cudaStream_t s) {
+  const Plan& pl = job.pl;
+  SumParams sa = job.sa, sb = job.sb;
+  sa.chunk = sb.chunk = c;
+  for (int q = 0; q < 4; ++q) {
+    // the source of A' stored transposed (a_mn) swaps quadrants (i, j) and (j, i); likewise
+    // a K-major B' (stored n x k)
+    const int qa = pl.a_mn ? 2 * (q % 2) + q / 2 : q;
+    const int qb = !pl.b_mn ? 2 * (q % 2) + q / 2 : q;
+    sa.c1[q] = static_cast<int8_t>(strassen_u(c, qa));
+    sb.c1[q] = static_cast<int8_t>(strassen_v(c, qb));
+  }
+  PhaseScope ps(kPhasePack, s, 2);
+  cudaError_t e = launch_operand_sums(sa, pl.L, false, pl.a_mn, job.a_type, pl.bf16 ? 0 : 1, dev.sms, s);
+  if (e != cudaSuccess) return cuda_fail(e, "operand-sum pass (A)");
+  e = launch_operand_sums(sb, pl.L, true, !pl.b_mn, job.b_type, pl.bf16 ? 0 : 1, dev.sms, s);
+  if (e != cudaSuccess) return cuda_fail(e, "operand-sum pass (B)");
   return FMM_OK;
+}
+
+// Internal stream and events of the pipelined path, one set per device, created on first use.
+// Enqueueing holds g_pipe_mu so that concurrent callers do not interleave their records and
+// waits on the shared events.
+struct PipeResources {
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t ready[7] = {};
+};
+std::mutex g_pipe_mu;
+PipeResources g_pipe[64];
+
+fmm_status pipe_resources(int device, PipeResources*& out) {
+  if (device < 0 || device >= 64) return fail(FMM_ERR_CUDA, "device index out of range");
+  PipeResources& r = g_pipe[device];
+  if (!r.side) {
+    cudaError_t e = cudaStreamCreateWithFlags(&r.side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r.fork, cudaEventDisableTiming);
+    for (int c = 0; c < 7 && e == cudaSuccess; ++c) e = cudaEventCreateWithFlags(&r.ready[c], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      r.side = nullptr;
+      return cuda_fail(e, "creating the pipeline stream and events");
+    }
+  }
+  out = &r;
+  return FMM_OK;
+}
+
+// Pipelined job: beta and the sums of top-level product 0 on s; the sums of products 1..6 on
+// the side stream (after everything enqueued on s so far); the tensor-core kernel of each
+// top-level product on s once its sums exist.  The last wait joins the side stream into s.
+fmm_status launch_pipelined(const PackedJob& job, const DeviceInfo& dev, cudaStream_t s) {
+  const Plan& pl = job.pl;
+  int device = 0;
+  cudaError_t e = cudaGetDevice(&device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lk(g_pipe_mu);
+  PipeResources* res = nullptr;
+  fmm_status st = pipe_resources(device, res);
+  if (st != FMM_OK) return st;
+  if (job.beta != 1.0f) {
+    PhaseScope ps(kPhaseBeta, s);
+    e = launch_beta(job.C, job.m, job.n, job.ldc, job.beta, dev.sms, s);
+    if (e != cudaSuccess) return cuda_fail(e, "beta pass");
+  }
+  if (job.maxbits) {
+    e = cudaMemsetAsync(job.maxbits, 0, pl.scale_bytes, s);
+    if (e != cudaSuccess) return cuda_fail(e, "clearing the panel maxima");
+  }
+  e = cudaEventRecord(res->fork, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(res->side, res->fork, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "forking the pipeline stream");
+  st = launch_chunk_sums(job, 0, dev, s);
+  for (int c = 1; c < 7 && st == FMM_OK; ++c) {
+    st = launch_chunk_sums(job, c, dev, res->side);
+    if (st == FMM_OK && (e = cudaEventRecord(res->ready[c], res->side)) != cudaSuccess)
+      st = cuda_fail(e, "recording a pipeline event");
+  }
+  if (st != FMM_OK) return st;
+  KernelArgs* ka = new KernelArgs;
+  std::memset(ka, 0, sizeof(KernelArgs));
+  {
+    PhaseScope ps(kPhaseTensor, s, 7);
+    for (int c = 0; c < 7 && st == FMM_OK; ++c) {
+      if (c > 0 && (e = cudaStreamWaitEvent(s, res->ready[c], 0)) != cudaSuccess) {
+        st = cuda_fail(e, "waiting for a pipeline event");
+        break;
+      }
+      ka->one = job.chunks[c];
+      e = launch_packed(*ka, pl.tile_n, pl.terms, pl.bf16, pl.a_mn, pl.b_mn, pl.bk, pl.pair, job.grid, s);
+      if (e != cudaSuccess) st = cuda_fail(e, "tensor-core pass");
+    }
+  }
+  delete ka;
+  return st;
 }
 
 // The beta pass and the operand-sum passes of a prepared job (everything before the
@@ -784,6 +922,12 @@ fmm_status gemm_core(const Plan& pl, int64_t m, int64_t n, int64_t k, float alph
   std::memset(ka, 0, sizeof(KernelArgs));
   PackedJob* job = new PackedJob;
   st = prepare_packed(pl, m, n, k, alpha, a, b, beta, C, ldc, ws, dev, opt, *job);
+  if (st == FMM_OK && pl.pipeline && job->has_work && !job->chunks.empty()) {
+    st = launch_pipelined(*job, dev, s);
+    delete job;
+    delete ka;
+    return st;
+  }
   if (st == FMM_OK) st = launch_passes(*job, dev, s);
   if (st == FMM_OK && job->has_work) {
     ka->one = job->params;
@@ -869,32 +1013,40 @@ size_t fmm_workspace_size_backward(int64_t m, int64_t n, int64_t k, int levels, 
   return std::max(pa.ws, pb.ws);
 }
 
-fmm_status fmm_gemm_backward(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda,
-                             const void* B, int64_t ldb, const float* dC, int64_t lddc, float* dA,
-                             int64_t ldda, float* dB, int64_t lddb, int levels, int variant,
-                             void* workspace, size_t ws_bytes, void* stream) {
+fmm_status fmm_gemm_backward_ex(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda,
+                                const void* B, int64_t ldb, const float* dC, int64_t lddc, float* dA,
+                                int64_t ldda, float* dB, int64_t lddb, int levels, int variant,
+                                void* workspace, size_t ws_bytes, void* stream, const fmm_options* opt) {
   g_last_error.clear();
   // dA (m x k) = dC (m x n) B^T: A' = dC stored m x n (K-major), B' = B^T stored as B, k x n
   // (K-major, quadrants transposed).
   if (dA) {
     Plan pl;
-    fmm_status st = make_plan(m, k, n, levels, variant, nullptr, false, false, pl);
+    fmm_status st = make_plan(m, k, n, levels, variant, opt, false, false, pl);
     if (st != FMM_OK) return st;
     st = gemm_core(pl, m, k, n, 1.0f, Operand{dC, lddc, kInF32}, Operand{B, ldb, pl.in_type}, 0.0f, dA,
-                   ldda, workspace, ws_bytes, stream, nullptr);
+                   ldda, workspace, ws_bytes, stream, opt);
     if (st != FMM_OK) return st;
   }
   // dB (k x n) = A^T dC: A' = A^T stored as A, m x k (MN-major, quadrants transposed),
   // B' = dC stored m x n (MN-major).
   if (dB) {
     Plan pl;
-    fmm_status st = make_plan(k, n, m, levels, variant, nullptr, true, true, pl);
+    fmm_status st = make_plan(k, n, m, levels, variant, opt, true, true, pl);
     if (st != FMM_OK) return st;
     st = gemm_core(pl, k, n, m, 1.0f, Operand{A, lda, pl.in_type}, Operand{dC, lddc, kInF32}, 0.0f, dB,
-                   lddb, workspace, ws_bytes, stream, nullptr);
+                   lddb, workspace, ws_bytes, stream, opt);
     if (st != FMM_OK) return st;
   }
   return FMM_OK;
+}
+
+fmm_status fmm_gemm_backward(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda,
+                             const void* B, int64_t ldb, const float* dC, int64_t lddc, float* dA,
+                             int64_t ldda, float* dB, int64_t lddb, int levels, int variant,
+                             void* workspace, size_t ws_bytes, void* stream) {
+  return fmm_gemm_backward_ex(m, n, k, A, lda, B, ldb, dC, lddc, dA, ldda, dB, lddb, levels, variant,
+                              workspace, ws_bytes, stream, nullptr);
 }
 
 void fmm_tune_default(fmm_tune_table* out) {
@@ -1192,7 +1344,7 @@ fmm_status fmm_profile_read(double* ms, int64_t* launches) {
     if (e == cudaSuccess) e = cudaEventElapsedTime(&t, ev.a, ev.b);
     if (e != cudaSuccess) st = cuda_fail(e, "reading profile events");
     if (ms) ms[ev.phase] += t;
-    if (launches) launches[ev.phase] += 1;
+    if (launches) launches[ev.phase] += ev.launches;
   }
   std::lock_guard<std::mutex> lk(g_prof_mu);
   g_prof_free.insert(g_prof_free.end(), recorded.begin(), recorded.end());

@@ -160,6 +160,10 @@ struct SumParams {
   int32_t npanels;
   int32_t panel_w;
   int32_t scale_rows;
+  // chunk >= 0 (levels >= 1): form only the products whose top-level index is `chunk`, with
+  // top-level coefficients c1[q] (already mapped through the transposed-source rule)
+  int32_t chunk;
+  int8_t c1[4];
 };
 
 // Shift s of a panel whose largest |sum| has float bits `maxbits`: the sums are stored as

@@ -159,6 +159,51 @@ __global__ void __launch_bounds__(256) operand_sums_kernel(const __grid_constant
       float v[EPT];
       load_group<T, EPT>(p, X, i, l0, l0, v);
       emit<SCALE, TERMS, OUT16, EPT>(p, 0, i, l0, orow, v);
+    } else if (p.chunk >= 0) {
+      // one top-level product: read only the quadrants it combines
+      float S[L == 1 ? 1 : 4][EPT];
+#pragma unroll
+      for (int q2 = 0; q2 < (L == 1 ? 1 : 4); ++q2)
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) S[q2][e] = 0.f;
+#pragma unroll
+      for (int q1 = 0; q1 < 4; ++q1) {
+        const int c = p.c1[q1];
+        if (c == 0) continue;
+#pragma unroll
+        for (int q2 = 0; q2 < (L == 1 ? 1 : 4); ++q2) {
+          float v[EPT];
+          if (L == 1) {
+            load_group<T, EPT>(p, X, (q1 / 2) * p.hr + i, (q1 % 2) * p.hc + l0, l0, v);
+          } else {
+            const int bi = 2 * (q1 / 2) + q2 / 2, bj = 2 * (q1 % 2) + q2 % 2;
+            load_group<T, EPT>(p, X, bi * p.hr + i, bj * p.hc + l0, l0, v);
+          }
+#pragma unroll
+          for (int e = 0; e < EPT; ++e) S[q2][e] = c > 0 ? S[q2][e] + v[e] : S[q2][e] - v[e];
+        }
+      }
+      if (L == 1) {
+        emit<SCALE, TERMS, OUT16, EPT>(p, p.chunk, i, l0, p.chunk * p.prod_stride + orow, S[0]);
+      } else {
+#pragma unroll
+        for (int r2 = 0; r2 < 7; ++r2) {
+          float acc[EPT];
+#pragma unroll
+          for (int e = 0; e < EPT; ++e) acc[e] = 0.f;
+#pragma unroll
+          for (int q2 = 0; q2 < 4; ++q2) {
+            const int c = coef<IS_B, TRANSQ>(r2, q2);
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) {
+              if (c > 0) acc[e] += S[q2 < (L == 1 ? 1 : 4) ? q2 : 0][e];
+              if (c < 0) acc[e] -= S[q2 < (L == 1 ? 1 : 4) ? q2 : 0][e];
+            }
+          }
+          const int r = p.chunk * 7 + r2;
+          emit<SCALE, TERMS, OUT16, EPT>(p, r, i, l0, r * p.prod_stride + orow, acc);
+        }
+      }
     } else if (L == 1) {
       float v[4][EPT];
 #pragma unroll

@@ -46,6 +46,19 @@ def test_backward_int_bit_exact(m, n, k, levels):
     np.testing.assert_array_equal(dB.cpu().numpy(), oracle.classical(np.ascontiguousarray(A.T), dC))
 
 
+@pytest.mark.parametrize("levels", [1, 2])
+@pytest.mark.parametrize("m,n,k", [(300, 200, 136), (129, 65, 257)])
+def test_backward_pipelined_int_bit_exact(m, n, k, levels):
+    """Transposed-quadrant sums formed per top-level product (pipelined)."""
+    A, B = synth.problem(m, n, k, 9 + m, "int")
+    dC = synth.small_int((m, n), 10 + n)
+    dA, dB = fmm.gemm_backward(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(),
+                               torch.from_numpy(dC).cuda(), levels=levels, pipeline=True)
+    fmm.device_status()
+    np.testing.assert_array_equal(dA.cpu().numpy(), oracle.classical(dC, np.ascontiguousarray(B.T)))
+    np.testing.assert_array_equal(dB.cpu().numpy(), oracle.classical(np.ascontiguousarray(A.T), dC))
+
+
 @pytest.mark.parametrize("variant", ["split3", "plain_bf16"])
 @pytest.mark.parametrize("levels", [0, 1, 2])
 @pytest.mark.parametrize("m,n,k", [(257, 300, 140), (512, 384, 640)])

@@ -60,7 +60,7 @@ def _to_device(X, ld_pad, dtype):
 
 def run(m, n, k, levels, variant="split3", dist="uniform", seed=0, alpha=1.0, beta=0.0,
         tile_n=0, pads=(0, 0, 0), c_fill=None, rows=None, schedule="auto", algo="auto", bk=0,
-        cta_pair=None, round_tiles=0):
+        cta_pair=None, round_tiles=0, pipeline=None):
     A, B = synth.problem(m, n, k, seed, dist)
     in_dtype = {"bf16": torch.bfloat16, "f16": torch.float16}.get(variant, torch.float32)
     Ad = _to_device(A, pads[0], in_dtype)
@@ -74,7 +74,8 @@ def run(m, n, k, levels, variant="split3", dist="uniform", seed=0, alpha=1.0, be
         if c_fill is not None:
             Cd.fill_(c_fill)
     fmm.gemm(Ad, Bd, Cd, alpha=alpha, beta=beta, levels=levels, variant=variant, tile_n=tile_n,
-             schedule=schedule, algo=algo, bk=bk, cta_pair=cta_pair, round_tiles=round_tiles)
+             schedule=schedule, algo=algo, bk=bk, cta_pair=cta_pair, round_tiles=round_tiles,
+             pipeline=pipeline)
     fmm.device_status()
     C = Cd.cpu().numpy().astype(np.float64)
     if variant in ("bf16", "f16"):
@@ -161,6 +162,54 @@ def test_unaligned_ldc_both_kernels(levels, cta_pair):
     C, C64, _, _ = run(513, 300, 130, levels, "split3", dist="int", seed=19, pads=(0, 0, 1),
                        cta_pair=cta_pair)
     np.testing.assert_array_equal(C, C64)
+
+
+@pytest.mark.parametrize("pipeline", [False, True])
+@pytest.mark.parametrize("levels", [1, 2])
+@pytest.mark.parametrize("m,n,k", [(300, 520, 200), (129, 257, 65), (1000, 1200, 300), (520, 8, 400),
+                                   (1, 300, 1)])
+def test_pipelined_sums_bit_exact(m, n, k, levels, pipeline):
+    """Operand sums formed per top-level product on a side stream, overlapped with the
+    tensor-core kernel of the products whose sums exist (and the plain order)."""
+    C, C64, _, _ = run(m, n, k, levels, "split3", dist="int", seed=13 * m + k, pipeline=pipeline)
+    np.testing.assert_array_equal(C, C64)
+
+
+@pytest.mark.parametrize("variant", ["plain_bf16", "bf16", "f16"])
+@pytest.mark.parametrize("levels", [1, 2])
+def test_pipelined_other_variants(levels, variant):
+    C, C64, _, _ = run(300, 260, 200, levels, variant, dist="int", seed=17, pipeline=True)
+    np.testing.assert_array_equal(C, C64)
+    C, C64, An, Bn = run(300, 260, 200, levels, variant, seed=18, pipeline=True)
+    assert oracle.normwise_error(C, C64, An, Bn) <= tolerance(variant, levels, 200)
+
+
+@pytest.mark.parametrize("pad_c", [0, 1])
+@pytest.mark.parametrize("levels", [1, 2])
+def test_pipelined_alpha_beta(levels, pad_c):
+    """beta pass then pipelined sums and products; ldc aligned (TMA reductions) or odd."""
+    m, n, k = 257, 300, 130
+    A, B = synth.problem(m, n, k, 23, "int")
+    C0 = synth.small_int((m, n), 24)
+    Cd = _to_device(C0, pad_c, torch.float32)
+    fmm.gemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), Cd, alpha=-2.0, beta=3.0,
+             levels=levels, pipeline=True)
+    fmm.device_status()
+    np.testing.assert_array_equal(Cd.cpu().numpy(), oracle.classical(A, B, C0, -2.0, 3.0))
+
+
+def test_pipelined_back_to_back_calls_share_workspace():
+    """Consecutive pipelined calls on one stream with one workspace: the side stream of a call
+    starts only after the previous call's products have read the shared sums."""
+    A1, B1 = synth.problem(700, 600, 500, 31, "int")
+    A2, B2 = synth.problem(700, 600, 500, 32, "int")
+    d = [torch.from_numpy(X).cuda() for X in (A1, B1, A2, B2)]
+    ws = torch.empty(fmm.workspace_size(700, 600, 500, 2), dtype=torch.uint8, device="cuda")
+    C1 = fmm.gemm(d[0], d[1], levels=2, workspace=ws, pipeline=True)
+    C2 = fmm.gemm(d[2], d[3], levels=2, workspace=ws, pipeline=True)
+    fmm.device_status()
+    np.testing.assert_array_equal(C1.cpu().numpy(), oracle.classical(A1, B1))
+    np.testing.assert_array_equal(C2.cpu().numpy(), oracle.classical(A2, B2))
 
 
 def test_cta_pair_rejected_with_bk32():
