@@ -51,6 +51,8 @@ def parse_args():
     ap.add_argument("--err-rows", type=int, default=16)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=100.0,
+                    help="reference arm: CPU seconds for the whole warm-up + timed run")
     ap.add_argument("--no-classical", action="store_true")
     ap.add_argument("--no-fused", action="store_true",
                     help="skip the measurement of the on-chip-sums (fused) algorithm")
@@ -168,6 +170,28 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ------------------------------------------------------------- multi-rank helpers
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest of every rank's x (the slowest rank's time); x itself with one rank."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, flops_per_rank, ms):
+    """Whole-job effective TFLOPS: every rank's product counted, over the slowest rank's
+    time (weak scaling: each rank multiplies its own problem of the same shape)."""
+    return world * flops_per_rank / (ms * 1e-3) * 1e-12
+
+
+def rank_problem(n, k, rank):
+    """The seeded synthetic problem of one rank (replicas: a different problem per rank)."""
+    return synth.uniform((n, k), 1234 + 2 * rank), synth.uniform((k, n), 1235 + 2 * rank)
+
+
 # ------------------------------------------------------------- oracle arm
 def cpu_oracle_rate(A, B, target_s, rows_hint=None):
     """Time the FP64 classical oracle on a sample of output rows.  Returns
@@ -201,7 +225,7 @@ def run_reference(a):
     oracle.build()
     cores = oracle.num_threads()
     # size one step so that warmup + steps end within about two minutes
-    budget = 100.0 / max(1, a.steps + a.warmup)
+    budget = a.ref_seconds / max(1, a.steps + a.warmup)
     _, _, rows, _ = cpu_oracle_rate(A, B, budget)
     for _ in range(a.warmup):
         cpu_oracle_rate(A, B, budget, rows_hint=rows)
@@ -251,8 +275,7 @@ def main():
     k = a.k or a.n
     m = n = a.n
     # replicas: each rank multiplies its own seeded problem of the same shape
-    A = synth.uniform((m, k), 1234 + 2 * rank)
-    B = synth.uniform((k, n), 1235 + 2 * rank)
+    A, B = rank_problem(n, k, rank)
     A_h = torch.from_numpy(A).pin_memory()
     B_h = torch.from_numpy(B).pin_memory()
     C_h = torch.empty((m, n), dtype=torch.float32).pin_memory()
@@ -272,12 +295,8 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def slowest(x):
+        return max_over_ranks(x, dist, dev)
 
     def timed(levels, steps, warmup, profile=False, algo=None):
         for _ in range(warmup):
@@ -316,16 +335,16 @@ def main():
     clocks.start()
     ms, prof = timed(a.levels, a.steps, 0, profile=True)
     clk = clocks.stop()
-    ms = max_over_ranks(ms)
+    ms = slowest(ms)
     flops = 2.0 * m * n * k
-    value = world * flops / (ms * 1e-3) * 1e-12
+    value = job_value(world, flops, ms)
 
     # ---- classical comparator at the same arithmetic
     classical = None
     if not a.no_classical:
         ms0, prof0 = timed(0, a.steps, a.warmup, profile=True)
-        ms0 = max_over_ranks(ms0)
-        classical = {"value": world * flops / (ms0 * 1e-3) * 1e-12, "ms_per_step": ms0,
+        ms0 = slowest(ms0)
+        classical = {"value": job_value(world, flops, ms0), "ms_per_step": ms0,
                      "tensor_kernel_ms": prof0["tensor"][0] / max(prof0["tensor"][1], 1)}
 
     # ---- the same product with the operand sums formed on chip while the source tiles load
@@ -336,9 +355,9 @@ def main():
     if do_fused:
         fsteps = max(1, min(a.steps, 5))
         msf, proff = timed(a.levels, fsteps, 1, profile=True, algo="fused")
-        msf = max_over_ranks(msf)
+        msf = slowest(msf)
         fused = {"algo": "fused (operand sums formed in shared memory as the tiles load)",
-                 "value": world * flops / (msf * 1e-3) * 1e-12, "ms_per_step": msf, "steps": fsteps,
+                 "value": job_value(world, flops, msf), "ms_per_step": msf, "steps": fsteps,
                  "tensor_kernel_ms": proff["tensor"][0] / max(proff["tensor"][1], 1)}
 
     # ---- end to end through host buffers: every step copies its A, B from pinned host memory
@@ -387,8 +406,8 @@ def main():
     torch.cuda.synchronize()
     barrier()
     fmm.device_status()
-    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / a.steps)
-    e2e = {"value": world * flops / (ms_e2e * 1e-3) * 1e-12, "unit": UNIT,
+    ms_e2e = slowest(e0.elapsed_time(e1) / a.steps)
+    e2e = {"value": job_value(world, flops, ms_e2e), "unit": UNIT,
            "h2d_bytes_per_step": int(A_h.numel() * 4 + B_h.numel() * 4),
            "d2h_bytes_per_step": int(C_h.numel() * 4), "ms_per_step": ms_e2e,
            "overlap": "H2D, compute and D2H on three streams, two device buffer sets"}

@@ -253,12 +253,14 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
   const int pipe = opt ? opt->pipeline : 0;
   if (pipe < 0 || pipe > 2) return fail(FMM_ERR_ARG, "pipeline must be 0, 1 or 2");
   // automatic choice (measured on GB300): per top-level product only for two-level products
-  // with short inner blocks (h_k <= 1024) on large C.  There each launch updates 1-2 of C's
-  // four quadrants, which keeps its C traffic in L2 (+16 % at 16384^2 x 4096, +17 % for
-  // 30001 x 29999 x 4097); for square products the seven launches cost more than the hidden
-  // sum passes save (-10 % at 16384^3).
+  // with inner blocks of 512..1536 on large C.  There each launch updates 1-2 of C's four
+  // quadrants, which keeps its C traffic in L2 (+16 % at 16384^2 x 4096, +17 % for
+  // 30001 x 29999 x 4097); with shorter blocks the seven launches' ramps dominate (-25 % at
+  // 16384^2 x 1024), and for deep products they cost more than the hidden sum passes save
+  // (-10 % at 16384^3).
   pl.pipeline = !on_chip && levels >= 1 &&
-                (pipe == 2 || (pipe == 0 && levels == 2 && pl.hk <= 1024 && pl.hm >= 2048 && pl.hn >= 2048));
+                (pipe == 2 || (pipe == 0 && levels == 2 && pl.hk >= 512 && pl.hk <= 1536 &&
+                               pl.hm >= 2048 && pl.hn >= 2048));
   const int row_tile = pl.pair ? 2 * kBM : kBM;
   if (pl.tile_n == 0) {
     // 256-wide tiles halve the A-operand traffic; keep 128 when that leaves fewer than four
