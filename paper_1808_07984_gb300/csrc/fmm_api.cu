@@ -184,6 +184,7 @@ struct Plan {
   int tile_n = 128;
   int bk = 64;  // k-elements per pipeline stage of the packed kernel (64, or 32 for split3)
   bool pair = false;  // packed kernel in CTA pairs: 256-row tiles shared by two CTAs
+  int pipeline_mode = 0;  // fmm_options.pipeline: 0 automatic, 1 off, 2 on
   bool pipeline = false;  // sum passes per top-level product, overlapped with the products
   int algo = FMM_ALGO_PACKED;
   int schedule = kSchedProductMajor;
@@ -252,15 +253,8 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
     return fail(FMM_ERR_UNSUPPORTED, "single-CTA tiles are built for the forward product only");
   const int pipe = opt ? opt->pipeline : 0;
   if (pipe < 0 || pipe > 2) return fail(FMM_ERR_ARG, "pipeline must be 0, 1 or 2");
-  // automatic choice (measured on GB300): per top-level product only for two-level products
-  // with inner blocks of 512..1536 on large C.  There each launch updates 1-2 of C's four
-  // quadrants, which keeps its C traffic in L2 (+16 % at 16384^2 x 4096, +17 % for
-  // 30001 x 29999 x 4097); with shorter blocks the seven launches' ramps dominate (-25 % at
-  // 16384^2 x 1024), and for deep products they cost more than the hidden sum passes save
-  // (-10 % at 16384^3).
-  pl.pipeline = !on_chip && levels >= 1 &&
-                (pipe == 2 || (pipe == 0 && levels == 2 && pl.hk >= 512 && pl.hk <= 1536 &&
-                               pl.hm >= 2048 && pl.hn >= 2048));
+  pl.pipeline_mode = pipe;
+  pl.pipeline = !on_chip && levels >= 1 && pipe == 2;  // automatic: decided with C (prepare_packed)
   const int row_tile = pl.pair ? 2 * kBM : kBM;
   if (pl.tile_n == 0) {
     // 256-wide tiles halve the A-operand traffic; keep 128 when that leaves fewer than four
@@ -750,8 +744,17 @@ fmm_status prepare_packed(const Plan& pl, int64_t m, int64_t n, int64_t k, float
     pp->c.panels_a = static_cast<int32_t>(pl.panels_a);
     pp->c.panels_b = static_cast<int32_t>(pl.panels_b);
   }
+  // Automatic pipelining (measured on GB300): only for two-level products whose C rows are
+  // not 16-byte aligned, with inner blocks of 512..1536 and a large C.  Each launch then adds
+  // into 1-2 of C's four quadrants, which eases the contention of the element-wise
+  // reductions (+18 % for 30001 x 29999 x 4097); with aligned C it gains nothing (+2 % to
+  // -15 % on square and rank-k shapes: seven launches and their ramps cost what the hidden
+  // sum passes save).
+  if (pl.pipeline_mode == 0 && pl.algo == FMM_ALGO_PACKED && pl.L == 2 && !pp->c.c_tma && pl.hk >= 512 &&
+      pl.hk <= 1536 && pl.hm >= 2048 && pl.hn >= 2048)
+    job.pl.pipeline = true;
   job.chunks.clear();
-  if (pl.pipeline) {
+  if (job.pl.pipeline) {
     // top-level product c: products c * P .. c * P + P - 1 (P = 7^(L-1)), kernel-local 0 .. P-1
     const int P = pl.R / 7;
     job.chunks.resize(7, *pp);
@@ -924,7 +927,7 @@ fmm_status gemm_core(const Plan& pl, int64_t m, int64_t n, int64_t k, float alph
   std::memset(ka, 0, sizeof(KernelArgs));
   PackedJob* job = new PackedJob;
   st = prepare_packed(pl, m, n, k, alpha, a, b, beta, C, ldc, ws, dev, opt, *job);
-  if (st == FMM_OK && pl.pipeline && job->has_work && !job->chunks.empty()) {
+  if (st == FMM_OK && job->pl.pipeline && job->has_work && !job->chunks.empty()) {
     st = launch_pipelined(*job, dev, s);
     delete job;
     delete ka;
