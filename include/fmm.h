@@ -109,7 +109,9 @@ typedef struct fmm_options {
                         the operand sums are formed in seven passes, one per top-level
                         product, on an internal stream, and the tensor-core kernel runs each
                         top-level product's 7^(L-1) products as soon as their sums exist, so
-                        the sum passes overlap the products (joined back into `stream`). */
+                        the sum passes overlap the products (joined back into `stream`).
+                        The first pipelined call on a device creates that stream: make it
+                        before any stream capture begins. */
 } fmm_options;
 
 /* Bytes of workspace fmm_gemm needs for this problem (0 when none).  Returns

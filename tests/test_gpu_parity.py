@@ -212,6 +212,27 @@ def test_pipelined_back_to_back_calls_share_workspace():
     np.testing.assert_array_equal(C2.cpu().numpy(), oracle.classical(A2, B2))
 
 
+def test_pipelined_call_in_cuda_graph():
+    """A pipelined call captured in a CUDA graph (its side stream joins the capture through
+    the fork event) and replayed: the replay computes the same exact product."""
+    A, B = synth.problem(600, 520, 400, 41, "int")
+    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    C = torch.zeros((600, 520), device="cuda")
+    ws = torch.empty(fmm.workspace_size(600, 520, 400, 2), dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        fmm.gemm(Ad, Bd, C, levels=2, workspace=ws, pipeline=True, stream=s)  # creates the side stream
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        fmm.gemm(Ad, Bd, C, levels=2, workspace=ws, pipeline=True, stream=s)
+    C.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    fmm.device_status()
+    np.testing.assert_array_equal(C.cpu().numpy(), oracle.classical(A, B))
+
+
 def test_cta_pair_rejected_with_bk32():
     A = torch.zeros((64, 64), device="cuda")
     with pytest.raises(fmm.FmmError):
