@@ -648,9 +648,10 @@ struct PackedJob {
   std::vector<PackedParams> chunks;
 };
 
+// batched = true: the job joins a batched launch, which never pipelines.
 fmm_status prepare_packed(const Plan& pl, int64_t m, int64_t n, int64_t k, float alpha, Operand a,
                           Operand b, float beta, float* C, int64_t ldc, void* ws, const DeviceInfo& dev,
-                          const fmm_options* opt, PackedJob& job) {
+                          const fmm_options* opt, PackedJob& job, bool batched = false) {
   job.pl = pl;
   job.m = m; job.n = n; job.k = k; job.ldc = ldc;
   job.alpha = alpha; job.beta = beta; job.C = C;
@@ -753,6 +754,7 @@ fmm_status prepare_packed(const Plan& pl, int64_t m, int64_t n, int64_t k, float
   if (pl.pipeline_mode == 0 && pl.algo == FMM_ALGO_PACKED && pl.L == 2 && !pp->c.c_tma && pl.hk >= 512 &&
       pl.hk <= 1536 && pl.hm >= 2048 && pl.hn >= 2048)
     job.pl.pipeline = true;
+  if (batched) job.pl.pipeline = false;
   job.chunks.clear();
   if (job.pl.pipeline) {
     // top-level product c: products c * P .. c * P + P - 1 (P = 7^(L-1)), kernel-local 0 .. P-1
@@ -1174,7 +1176,8 @@ fmm_status fmm_batched_plan_create(int count, const int64_t* m, const int64_t* n
     if (st != FMM_OK) break;
     PackedJob* job = new PackedJob;
     plan->jobs.push_back(job);
-    st = prepare_packed(pl, m[p], n[p], k[p], alpha[p], a, b, beta[p], C[p], ldc[p], ws, dev, nullptr, *job);
+    st = prepare_packed(pl, m[p], n[p], k[p], alpha[p], a, b, beta[p], C[p], ldc[p], ws, dev, nullptr, *job,
+                        /*batched=*/true);
   }
   // one batched tensor-core launch per tile width: upload parameter blocks and item offsets
   // (every problem of a batch has the same CTA-pair setting: the automatic one)
