@@ -105,6 +105,10 @@ typedef struct fmm_options {
     int round_tiles; /* tile-rounds schedule: output tiles per round, 0 = automatic (as many
                         as keep the C blocks that one round updates within a quarter of the
                         L2 cache when C traffic dominates, else one per CTA or CTA pair) */
+    int fringe;      /* sizes that do not split evenly, levels >= 1: 0 = pad (implicit zero
+                        padding of every block to the padded size, Section 3.5), 1 = peel
+                        (Strassen on the largest core whose sizes are multiples of 8 * 2^L,
+                        then classical products for the k, row and column strips) */
     int pipeline;    /* packed algorithm, levels >= 1: 0 = automatic, 1 = off, 2 = on.  On:
                         the operand sums are formed in seven passes, one per top-level
                         product, on an internal stream, and the tensor-core kernel runs each
@@ -112,6 +116,7 @@ typedef struct fmm_options {
                         the sum passes overlap the products (joined back into `stream`).
                         The first pipelined call on a device creates that stream: make it
                         before any stream capture begins. */
+    int reserved[3]; /* zero */
 } fmm_options;
 
 /* Bytes of workspace fmm_gemm needs for this problem (0 when none).  Returns

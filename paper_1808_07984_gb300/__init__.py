@@ -40,7 +40,8 @@ class TuneTable(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int), ("tile_n", ctypes.c_int), ("num_ctas", ctypes.c_int),
                 ("schedule", ctypes.c_int), ("bk", ctypes.c_int), ("cta_pair", ctypes.c_int),
-                ("round_tiles", ctypes.c_int), ("pipeline", ctypes.c_int)]
+                ("round_tiles", ctypes.c_int), ("fringe", ctypes.c_int), ("pipeline", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
 
 
 _lib = None
@@ -126,10 +127,14 @@ def _check(status: int):
 SCHEDULES = {"auto": 0, "product": 1, "rounds": 2}
 
 
+FRINGES = {"pad": 0, "peel": 1}
+
+
 def _opts(algo="auto", tile_n=0, num_ctas=0, schedule="auto", bk=0, cta_pair=None, round_tiles=0,
-          pipeline=None):
+          pipeline=None, fringe="pad"):
     o = _Options()
     o.round_tiles = int(round_tiles)
+    o.fringe = FRINGES[fringe] if isinstance(fringe, str) else int(fringe)
     o.pipeline = 0 if pipeline is None else (2 if pipeline else 1)
     o.bk = int(bk)
     o.cta_pair = 0 if cta_pair is None else (2 if cta_pair else 1)
@@ -144,8 +149,9 @@ def _variant(v) -> int:
     return VARIANTS[v] if isinstance(v, str) else int(v)
 
 
-def workspace_size(m, n, k, levels=1, variant="split3", algo="auto", tile_n=0, cta_pair=None) -> int:
-    o = _opts(algo, tile_n, cta_pair=cta_pair)
+def workspace_size(m, n, k, levels=1, variant="split3", algo="auto", tile_n=0, cta_pair=None,
+                   fringe="pad") -> int:
+    o = _opts(algo, tile_n, cta_pair=cta_pair, fringe=fringe)
     ws = load().fmm_workspace_size_ex(m, n, k, levels, _variant(variant), ctypes.byref(o))
     if ws == ctypes.c_size_t(-1).value:
         raise FmmError(3, "unsupported combination")
@@ -165,7 +171,7 @@ _IN_DTYPE = {0: "float32", 1: "bfloat16", 2: "float16", 3: "float32"}
 def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
          variant="split3", algo="auto", tile_n: int = 0, num_ctas: int = 0,
          workspace=None, stream=None, schedule="auto", bk: int = 0, cta_pair=None,
-         round_tiles: int = 0, pipeline=None):
+         round_tiles: int = 0, pipeline=None, fringe="pad"):
     """C = alpha * A @ B + beta * C on the current CUDA device (torch tensors).
 
     A (m x k) and B (k x n) are row-major CUDA tensors of the element type the
@@ -175,7 +181,9 @@ def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
     the right size is allocated when None.  ``cta_pair``: None = automatic, True = CTA
     pairs (256-row tiles shared by a cluster of two CTAs), False = one CTA per tile.
     ``pipeline``: None = automatic, True / False = overlap the operand-sum passes with the
-    tensor-core kernel one top-level product at a time, or not.
+    tensor-core kernel one top-level product at a time, or not.  ``fringe``: "pad" (zero
+    padding of the blocks) or "peel" (Strassen on the evenly splitting core plus classical
+    strip products).
     """
     import torch
     v = _variant(variant)
@@ -196,12 +204,12 @@ def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
         beta = 0.0
     if C.dtype != torch.float32 or not C.is_cuda or (C.numel() and C.stride(1) != 1):
         raise FmmError(1, "C must be a float32 CUDA tensor with contiguous rows")
-    ws_need = workspace_size(m, n, k, levels, v, algo, tile_n, cta_pair)
+    ws_need = workspace_size(m, n, k, levels, v, algo, tile_n, cta_pair, fringe)
     if workspace is None and ws_need > 0:
         workspace = torch.empty(ws_need, dtype=torch.uint8, device=A.device)
     ws_ptr = workspace.data_ptr() if workspace is not None else None
     ws_bytes = workspace.numel() if workspace is not None else 0
-    o = _opts(algo, tile_n, num_ctas, schedule, bk, cta_pair, round_tiles, pipeline)
+    o = _opts(algo, tile_n, num_ctas, schedule, bk, cta_pair, round_tiles, pipeline, fringe)
     st = load().fmm_gemm_ex(m, n, k, float(alpha), A.data_ptr(), max(A.stride(0), 1),
                             B.data_ptr(), max(B.stride(0), 1), float(beta), C.data_ptr(),
                             max(C.stride(0), 1), int(levels), v, ws_ptr, ws_bytes,

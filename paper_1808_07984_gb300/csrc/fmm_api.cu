@@ -980,10 +980,60 @@ struct fmm_batched_plan {
 
 using namespace fmm;
 
+namespace fmm {
+namespace {
+
+// Dynamic peeling (Section 3.5 names it beside padding): the core m_e x n_e x k_e, each the
+// largest multiple of 8 * 2^L not above the size, splits evenly at every level, so its
+// Strassen product needs no padding; the strips around it are classical products.
+struct PeelPart {
+  int64_t r0, c0, k0;  // first row of C / A, first column of C / B, first k of A-columns / B-rows
+  int64_t m, n, k;
+  int levels;
+  bool accumulate;     // beta = 1 (adds to what an earlier part wrote)
+};
+
+std::vector<PeelPart> peel_parts(int64_t m, int64_t n, int64_t k, int levels) {
+  const int64_t q = int64_t(8) << levels;
+  const int64_t me = m / q * q, ne = n / q * q, ke = k / q * q;
+  std::vector<PeelPart> parts;
+  if (me == 0 || ne == 0 || ke == 0) {  // no core: one classical product
+    parts.push_back({0, 0, 0, m, n, k, 0, false});
+    return parts;
+  }
+  parts.push_back({0, 0, 0, me, ne, ke, levels, false});        // Strassen core
+  if (ke < k) parts.push_back({0, 0, ke, me, ne, k - ke, 0, true});  // k strip into the core
+  if (me < m) parts.push_back({me, 0, 0, m - me, n, k, 0, false});   // bottom rows, full width
+  if (ne < n) parts.push_back({0, ne, 0, me, n - ne, k, 0, false});  // right columns of the core rows
+  return parts;
+}
+
+fmm_options no_fringe(const fmm_options* opt) {
+  fmm_options o;
+  std::memset(&o, 0, sizeof o);
+  if (opt) o = *opt;
+  o.fringe = 0;
+  return o;
+}
+
+}  // namespace
+}  // namespace fmm
+
 extern "C" {
 
 size_t fmm_workspace_size_ex(int64_t m, int64_t n, int64_t k, int levels, int variant,
                              const fmm_options* opt) {
+  if (opt && opt->fringe == 1 && levels >= 1) {
+    const fmm_options o = no_fringe(opt);
+    size_t ws = 0;
+    for (const PeelPart& pp : peel_parts(m, n, k, levels)) {
+      Plan pl;
+      if (make_plan(pp.m, pp.n, pp.k, pp.levels, variant, &o, false, true, pl) != FMM_OK)
+        return static_cast<size_t>(-1);
+      ws = std::max(ws, pl.ws);
+    }
+    return ws;
+  }
   Plan pl;
   if (make_plan(m, n, k, levels, variant, opt, false, true, pl) != FMM_OK) return static_cast<size_t>(-1);
   return pl.ws;
@@ -998,6 +1048,29 @@ fmm_status fmm_gemm_ex(int64_t m, int64_t n, int64_t k, float alpha, const void*
                        int variant, void* workspace, size_t ws_bytes, void* stream,
                        const fmm_options* opt) {
   g_last_error.clear();
+  if (opt && (opt->fringe < 0 || opt->fringe > 1)) return fail(FMM_ERR_ARG, "fringe must be 0 or 1");
+  if (opt && opt->fringe == 1 && levels >= 1 && m > 0 && n > 0) {
+    // peeled: every part is an ordinary call on sub-views, in order on `stream` (they share
+    // the workspace); the parts cover C exactly once, and the k strip adds into the core
+    const fmm_options o = no_fringe(opt);
+    const std::vector<PeelPart> parts = peel_parts(m, n, k, levels);
+    Plan first;
+    fmm_status st = make_plan(m, n, k, levels, variant, &o, false, true, first);
+    if (st != FMM_OK) return st;
+    const size_t eb = elem_bytes(first.in_type);
+    for (const PeelPart& pp : parts) {
+      Plan pl;
+      st = make_plan(pp.m, pp.n, pp.k, pp.levels, variant, &o, false, true, pl);
+      if (st != FMM_OK) return st;
+      const void* Ap = static_cast<const uint8_t*>(A) + (pp.r0 * lda + pp.k0) * eb;
+      const void* Bp = static_cast<const uint8_t*>(B) + (pp.k0 * ldb + pp.c0) * eb;
+      float* Cp = C + pp.r0 * ldc + pp.c0;
+      st = gemm_core(pl, pp.m, pp.n, pp.k, alpha, Operand{Ap, lda, pl.in_type}, Operand{Bp, ldb, pl.in_type},
+                     pp.accumulate ? 1.0f : beta, Cp, ldc, workspace, ws_bytes, stream, &o);
+      if (st != FMM_OK) return st;
+    }
+    return FMM_OK;
+  }
   Plan pl;
   fmm_status st = make_plan(m, n, k, levels, variant, opt, false, true, pl);
   if (st != FMM_OK) return st;

@@ -60,7 +60,7 @@ def _to_device(X, ld_pad, dtype):
 
 def run(m, n, k, levels, variant="split3", dist="uniform", seed=0, alpha=1.0, beta=0.0,
         tile_n=0, pads=(0, 0, 0), c_fill=None, rows=None, schedule="auto", algo="auto", bk=0,
-        cta_pair=None, round_tiles=0, pipeline=None):
+        cta_pair=None, round_tiles=0, pipeline=None, fringe="pad"):
     A, B = synth.problem(m, n, k, seed, dist)
     in_dtype = {"bf16": torch.bfloat16, "f16": torch.float16}.get(variant, torch.float32)
     Ad = _to_device(A, pads[0], in_dtype)
@@ -75,7 +75,7 @@ def run(m, n, k, levels, variant="split3", dist="uniform", seed=0, alpha=1.0, be
             Cd.fill_(c_fill)
     fmm.gemm(Ad, Bd, Cd, alpha=alpha, beta=beta, levels=levels, variant=variant, tile_n=tile_n,
              schedule=schedule, algo=algo, bk=bk, cta_pair=cta_pair, round_tiles=round_tiles,
-             pipeline=pipeline)
+             pipeline=pipeline, fringe=fringe)
     fmm.device_status()
     C = Cd.cpu().numpy().astype(np.float64)
     if variant in ("bf16", "f16"):
@@ -231,6 +231,41 @@ def test_pipelined_call_in_cuda_graph():
     torch.cuda.synchronize()
     fmm.device_status()
     np.testing.assert_array_equal(C.cpu().numpy(), oracle.classical(A, B))
+
+
+@pytest.mark.parametrize("levels", [1, 2])
+@pytest.mark.parametrize("m,n,k", [(300, 520, 200), (129, 257, 65), (1000, 1200, 300), (33, 70, 17),
+                                   (5, 7, 3), (520, 8, 400), (64, 64, 64)])
+def test_peeled_fringes_bit_exact(m, n, k, levels):
+    """Dynamic peeling: Strassen on the evenly splitting core, classical k, row and column
+    strips (or one classical product when there is no core)."""
+    C, C64, _, _ = run(m, n, k, levels, "split3", dist="int", seed=29 * m + k, fringe="peel")
+    np.testing.assert_array_equal(C, C64)
+
+
+@pytest.mark.parametrize("levels", [1, 2])
+def test_peeled_alpha_beta_unaligned(levels):
+    m, n, k = 257, 301, 131
+    A, B = synth.problem(m, n, k, 37, "int")
+    C0 = synth.small_int((m, n), 38)
+    Cd = _to_device(C0, 1, torch.float32)
+    fmm.gemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), Cd, alpha=3.0, beta=-2.0,
+             levels=levels, fringe="peel")
+    fmm.device_status()
+    np.testing.assert_array_equal(Cd.cpu().numpy(), oracle.classical(A, B, C0, 3.0, -2.0))
+
+
+@pytest.mark.parametrize("variant", ["split3", "plain_bf16", "bf16", "f16"])
+def test_peeled_float(variant):
+    C, C64, An, Bn = run(500, 333, 271, 2, variant, seed=39, fringe="peel")
+    assert oracle.normwise_error(C, C64, An, Bn) <= tolerance(variant, 2, 271)
+
+
+def test_peeled_odd_30001_29999_4097_sampled_rows():
+    rows = np.array([0, 1, 29983, 29984, 30000])  # core rows and bottom-strip rows
+    C, C64, An, Bn = run(30001, 29999, 4097, 2, "split3", dist="gaussian", seed=5, rows=rows,
+                         fringe="peel")
+    assert oracle.normwise_error(C, C64, An, Bn) <= tolerance("split3", 2, 4097)
 
 
 def test_cta_pair_rejected_with_bk32():
