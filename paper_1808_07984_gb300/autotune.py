@@ -54,16 +54,25 @@ def build_table(probes: dict) -> dict:
 
 
 def autotune(sizes=(1024, 2048, 4096, 8192, 16384), variant: str = "split3",
-             levels=(0, 1, 2), tiles=(128, 256), steps: int = 3) -> dict:
+             levels=(0, 1, 2), tiles=(128, 256), steps: int = 3, prior: str | None = None,
+             keep: int = 2) -> dict:
+    """Measure the candidates of each probe size and build the table.  prior="model": rank
+    the candidates with the analytic model (model.py) and measure only the best ``keep``."""
     import torch
     probes = {}
     for d in sizes:
-        probes[d] = {(lv, tn): measure(d, lv, tn, variant, steps) for lv in levels for tn in tiles}
+        cands = [(lv, tn) for lv in levels for tn in tiles]
+        if prior == "model":
+            from . import model
+            cands = model.rank_candidates(d, variant, levels, tiles)[:keep]
+        probes[d] = {(lv, tn): measure(d, lv, tn, variant, steps) for lv, tn in cands}
     table = build_table(probes)
     table["variant"] = variant
     table["gpu"] = torch.cuda.get_device_name()
     table["probes_ms"] = {str(d): {f"L{lv}_N{tn}": round(ms, 4) for (lv, tn), ms in p.items()}
                           for d, p in probes.items()}
+    if prior:
+        table["prior"] = prior
     return table
 
 

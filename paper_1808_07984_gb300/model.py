@@ -1,0 +1,166 @@
+"""Analytic time model of one library call on a GB300 (the paper's Section 4 model, adapted).
+
+The paper models a fused Strassen product on V100 as arithmetic time plus the time of its
+extra memory operations (the W_A, W_B operand tiles each k-step and the W_C accumulator
+updates).  On GB300 the same three costs appear in different places:
+
+* the operand-sum pass reads A and B once and writes the 7^L sums (BF16, two arrays for the
+  split3 arithmetic): HBM-bound;
+* the tensor-core kernel does (7/8)^L of the classical UMMA work, 1 or 3 UMMAs per k16 slice,
+  in 256 x tile_n CTA-pair tiles distributed over 76 CTA pairs;
+* every work item adds its accumulator into W_C destination tiles of C (TMA reductions
+  through L2), which costs time the mainloop does not hide.
+
+    T = t_beta + t_pack + t_tensor + launches * t_launch
+    t_beta   = 4 m n / BW                                   (C zeroed or scaled)
+    t_pack   = pack_bytes / (BW * pack_eff)
+    t_tensor = W * (t_item_mma + t_item_fix + wb_bytes_item * wb_cost)
+    W        = ceil(items / workers)                        (items of the busiest CTA pair)
+    t_item_mma = terms * 2 * 256 * tile_n * h_k / (TC * tc_eff / workers)
+
+BW and TC are the measured HBM copy bandwidth and burst BF16 tensor rate of the pool's
+GB300s; pack_eff, tc_eff, wb_cost, t_item_fix and t_launch are fitted to measured library
+calls (``fit``).  ``DEFAULT`` holds the fit to square, panel and rank-k sweeps of split3
+products measured on GB300 (mean absolute error 6.4 % over 58 calls).  pack_eff and tc_eff
+come out slightly above 1: the sum pass streams closer to the HBM peak than the copy that
+measured BW, and the UMMA rate of a kernel timed inside a sequence of calls matches the
+burst figure.  The largest products run below the model (up to 15 % at 20480): there the
+power cap lowers the SM clock, which the model does not represent.
+
+Used by ``autotune.autotune(prior="model")`` to rank the (levels, tile_n) candidates of each
+size so that only the most promising ones are measured.
+"""
+from __future__ import annotations
+
+import math
+
+GB300 = {"sms": 152, "hbm_gbs": 6777.0, "tc_tflops": 1934.1}
+
+# fitted (``fit``) to the 58 measured split3 calls in tuned/gb300_model_samples.json
+DEFAULT = {"pack_eff": 1.158, "tc_eff": 1.051, "wb_cost_ns_per_kb": 10.44, "t_item_fix_us": 0.0,
+           "t_launch_us": 5.93}
+
+_TERMS = {"split3": 3, "plain_bf16": 1, "bf16": 1, "f16": 1}
+_IN_BYTES = {"split3": 4, "plain_bf16": 4, "bf16": 2, "f16": 2}
+_ARRAYS = {"split3": 2, "plain_bf16": 1, "bf16": 1, "f16": 1}
+
+
+def block(d: int, levels: int) -> int:
+    """Block size of the library's split rule: ceil(d / 2^L) rounded up to 8 (d > 0)."""
+    if d <= 0:
+        return 0
+    h = -(-d // (1 << levels))
+    return -(-h // 8) * 8
+
+
+def auto_tile_n(m: int, n: int, levels: int) -> int:
+    """The library's automatic tile width for CTA pairs (256 unless that leaves fewer than
+    four items per pair)."""
+    hm, hn = block(m, levels), block(n, levels)
+    items256 = 7 ** levels * -(-hm // 256) * -(-hn // 256)
+    return 256 if items256 >= 4 * (GB300["sms"] // 2) else 128
+
+
+def predict(m: int, n: int, k: int, levels: int, variant: str = "split3", tile_n: int = 0,
+            params: dict | None = None, hw: dict | None = None) -> dict:
+    """Predicted milliseconds of fmm_gemm(m, n, k, levels, variant) and its components."""
+    p = dict(DEFAULT, **(params or {}))
+    h = dict(GB300, **(hw or {}))
+    R = 7 ** levels
+    terms, e_in, arrays = _TERMS[variant], _IN_BYTES[variant], _ARRAYS[variant]
+    hm, hn, hk = block(m, levels), block(n, levels), block(k, levels)
+    tn = tile_n or auto_tile_n(m, n, levels)
+    bw = h["hbm_gbs"] * 1e9
+    t_beta = 4.0 * m * n / bw
+    pack_bytes = (m * k + k * n) * e_in + R * (hm * hk + hk * hn) * 2 * arrays
+    t_pack = pack_bytes / (bw * p["pack_eff"])
+    workers = h["sms"] // 2
+    items = R * -(-hm // 256) * -(-hn // tn)
+    per_worker = -(-items // workers)
+    tc = h["tc_tflops"] * 1e12 * p["tc_eff"] / workers
+    t_item_mma = terms * 2.0 * 256 * tn * hk / tc
+    wc = (12.0 / 7.0) ** levels  # average W_C of a product (12 nonzeros of W over 7 products)
+    wb_bytes_item = wc * 256 * tn * 4
+    t_item = t_item_mma + p["t_item_fix_us"] * 1e-6 + wb_bytes_item / 1024.0 * p["wb_cost_ns_per_kb"] * 1e-9
+    t_tensor = per_worker * t_item
+    launches = 4
+    t = t_beta + t_pack + t_tensor + launches * p["t_launch_us"] * 1e-6
+    return {"ms": t * 1e3, "beta_ms": t_beta * 1e3, "pack_ms": t_pack * 1e3,
+            "tensor_ms": t_tensor * 1e3, "items": items, "items_per_pair": per_worker,
+            "tile_n": tn, "eff_tflops": 2.0 * m * n * k / t * 1e-12}
+
+
+def best_levels(m: int, n: int, k: int, variant: str = "split3", params: dict | None = None) -> int:
+    """The level the model predicts fastest."""
+    return min(range(3), key=lambda L: predict(m, n, k, L, variant, params=params)["ms"])
+
+
+def rank_candidates(d: int, variant: str = "split3", levels=(0, 1, 2), tiles=(128, 256),
+                    params: dict | None = None) -> list:
+    """(levels, tile_n) candidates of a square d-problem, fastest predicted first."""
+    cands = [(L, t) for L in levels for t in tiles]
+    return sorted(cands, key=lambda c: predict(d, d, d, c[0], variant, tile_n=c[1], params=params)["ms"])
+
+
+def fit(samples, variant: str = "split3", start: dict | None = None, iters: int = 400) -> dict:
+    """Least-squares fit of the model's free parameters to measured calls.
+
+    samples: iterable of (m, n, k, levels, measured_ms).  Minimises the mean squared log
+    ratio of predicted to measured time by coordinate search (no dependency beyond math)."""
+    samples = list(samples)
+    p = dict(DEFAULT, **(start or {}))
+    keys = list(DEFAULT)
+
+    def loss(q):
+        s = 0.0
+        for m, n, k, L, ms in samples:
+            s += math.log(predict(m, n, k, L, variant, params=q)["ms"] / ms) ** 2
+        return s / max(len(samples), 1)
+
+    best = loss(p)
+    step = {key: 0.25 * p[key] for key in keys}
+    for _ in range(iters):
+        improved = False
+        for key in keys:
+            for sgn in (1, -1):
+                q = dict(p)
+                q[key] = max(1e-6, p[key] + sgn * step[key])
+                if key in ("pack_eff", "tc_eff"):
+                    q[key] = min(q[key], 1.2)
+                lq = loss(q)
+                if lq < best:
+                    p, best, improved = q, lq, True
+        if not improved:
+            for key in keys:
+                step[key] *= 0.5
+            if max(step[k_] / max(p[k_], 1e-9) for k_ in keys) < 1e-4:
+                break
+    return p
+
+
+def mean_abs_error(samples, variant: str = "split3", params: dict | None = None) -> float:
+    """Mean |predicted - measured| / measured over (m, n, k, levels, measured_ms) samples."""
+    samples = list(samples)
+    err = [abs(predict(m, n, k, L, variant, params=params)["ms"] - ms) / ms for m, n, k, L, ms in samples]
+    return sum(err) / max(len(err), 1)
+
+
+def load_samples(path: str):
+    """(m, n, k, levels, ms) samples of a calibration file."""
+    import json
+    with open(path) as f:
+        rec = json.load(f)
+    return [tuple(x) for x in rec["samples_m_n_k_levels_ms"]], rec.get("variant", "split3")
+
+
+if __name__ == "__main__":
+    import argparse
+    import os
+    ap = argparse.ArgumentParser(description="fit or check the GB300 time model")
+    ap.add_argument("--samples", default=os.path.join(os.path.dirname(__file__), "tuned",
+                                                      "gb300_model_samples.json"))
+    ap.add_argument("--fit", action="store_true")
+    a = ap.parse_args()
+    S, var = load_samples(a.samples)
+    prm = fit(S, var) if a.fit else DEFAULT
+    print({k_: round(v, 4) for k_, v in prm.items()}, "mean abs error", round(mean_abs_error(S, var, prm), 4))

@@ -60,3 +60,49 @@ def test_batched_workspace_is_sum_of_parts():
     parts = sum(fmm.workspace_size(m, n, k, fmm.tune_select(m, n, k)[0], "split3")
                 for m, n, k in zip(ms, ns, ks))
     assert ws >= parts
+
+
+# ------------------------------------------------------------ analytic model (CPU only)
+from paper_1808_07984_gb300 import model  # noqa: E402
+
+
+def test_model_block_rule_matches_library_rule():
+    for d in (1, 7, 8, 9, 100, 4097, 30001):
+        for L in (0, 1, 2):
+            assert model.block(d, L) % 8 == 0 and model.block(d, L) * 2 ** L >= d
+
+
+def test_model_components_and_classical_case():
+    r = model.predict(8192, 8192, 8192, 0)
+    assert r["ms"] > 0 and r["items"] == (8192 // 256) * (8192 // 256)
+    assert abs(r["ms"] - (r["beta_ms"] + r["pack_ms"] + r["tensor_ms"] + 4 * model.DEFAULT["t_launch_us"] * 1e-3)) < 1e-9
+
+
+def test_model_levels_trade_mma_for_sums_and_writeback():
+    """More levels: 7/8 of the UMMA work per level, more operand-sum bytes."""
+    a0, a2 = model.predict(16384, 16384, 16384, 0), model.predict(16384, 16384, 16384, 2)
+    assert a2["pack_ms"] > a0["pack_ms"]
+    assert model.best_levels(16384, 16384, 16384) == 2
+    assert model.best_levels(1024, 1024, 1024) in (0, 1)
+    assert model.best_levels(16384, 16384, 512) == 0  # rank-k: classical
+
+
+def test_model_fit_recovers_its_own_parameters():
+    truth = dict(model.DEFAULT, tc_eff=0.8, wb_cost_ns_per_kb=20.0)
+    S = [(d, d, d, L, model.predict(d, d, d, L, params=truth)["ms"]) for d in (2048, 4096, 8192, 16384)
+         for L in (0, 1, 2)]
+    p = model.fit(S, start=model.DEFAULT, iters=300)
+    assert model.mean_abs_error(S, params=p) < 0.01
+
+
+def test_model_calibration_samples_fit_within_ten_percent():
+    import os
+    path = os.path.join(os.path.dirname(model.__file__), "tuned", "gb300_model_samples.json")
+    S, var = model.load_samples(path)
+    assert len(S) >= 50
+    assert model.mean_abs_error(S, var) < 0.10
+
+
+def test_model_ranks_candidates():
+    c = model.rank_candidates(16384)
+    assert len(c) == 6 and c[0][0] == 2
