@@ -11,7 +11,9 @@ with A (m x k), B (k x n), C (m x n), row-major.  Two routes are provided:
 * ``strassen`` -- FP64 Strassen written from the seven products of Eq. (3)
   (the ``gpu_allops`` table of Section 3: M0..M6 and their C updates), applied
   recursively for ``levels`` levels, with zero padding of the fringes
-  (Section 3.5).  The leaf product is a library matmul in FP64.
+  (Section 3.5).  The leaf product is a library matmul in FP64.  ``basis=
+  "winograd"`` applies the Strassen-Winograd variant's seven products instead
+  (Section 6 names it among the algorithms the primitive can carry).
 
 Supporting definitions: the 2x2 coefficient matrices U, V, W of Eq. (3), their
 Kronecker powers for multi-level Strassen (Section 3.4), the Brent-equation
@@ -82,6 +84,58 @@ STRASSEN_W = np.array([
 ], dtype=np.int64)
 
 
+# ---------------------------------------------------------------------------
+# The Strassen-Winograd variant, which the paper names among the fast-matmul
+# algorithms its primitive could carry (Section 6).  In its usual form it shares
+# partial sums (S1..S4 of A, T1..T4 of B, U2..U4 of the products) to need 15
+# additions; written per product, as this primitive forms every operand and
+# every C update directly from the quadrants, its tables are (A0 = A11,
+# A1 = A12, A2 = A21, A3 = A22, likewise B and C):
+#   M0 = A0 B0;                                C0, C1, C2, C3 += M0
+#   M1 = A1 B2;                                C0 += M1
+#   M2 = (A0 + A1 - A2 - A3) B3;               C1 += M2
+#   M3 = A3 (B0 - B1 - B2 + B3);               C2 -= M3
+#   M4 = (A2 + A3)(B1 - B0);                   C1 += M4, C3 += M4
+#   M5 = (A2 + A3 - A0)(B0 - B1 + B3);         C1, C2, C3 += M5
+#   M6 = (A0 - A2)(B3 - B1);                   C2 += M6, C3 += M6
+# 14 nonzeros in each of U, V, W (12 for Strassen's).
+# ---------------------------------------------------------------------------
+WINOGRAD_U = np.array([
+    # r:  0   1   2   3   4   5   6
+    [1, 0, 1, 0, 0, -1, 1],    # A0
+    [0, 1, 1, 0, 0, 0, 0],     # A1
+    [0, 0, -1, 0, 1, 1, -1],   # A2
+    [0, 0, -1, 1, 1, 1, 0],    # A3
+], dtype=np.int64)
+
+WINOGRAD_V = np.array([
+    [1, 0, 0, 1, -1, 1, 0],    # B0
+    [0, 0, 0, -1, 1, -1, -1],  # B1
+    [0, 1, 0, -1, 0, 0, 0],    # B2
+    [0, 0, 1, 1, 0, 1, 1],     # B3
+], dtype=np.int64)
+
+WINOGRAD_W = np.array([
+    [1, 1, 0, 0, 0, 0, 0],     # C0
+    [1, 0, 1, 0, 1, 1, 0],     # C1
+    [1, 0, 0, -1, 0, 1, 1],    # C2
+    [1, 0, 0, 0, 1, 1, 1],     # C3
+], dtype=np.int64)
+
+def basis_tables(basis: str = "strassen"):
+    """(U, V, W) of a one-level basis, looked up when called."""
+    g = globals()
+    return tuple(g[f"{basis.upper()}_{x}"] for x in "UVW")
+
+
+class _Bases(dict):
+    def __missing__(self, key):
+        return basis_tables(key)
+
+
+BASES = _Bases()  # BASES["strassen"], BASES["winograd"]: the tables as they are now
+
+
 def quadrant_rc(q: int) -> tuple[int, int]:
     """Row and column of quadrant q under the numbering of Eq. (2)."""
     return q // 2, q % 2
@@ -148,10 +202,10 @@ def brent_residual(levels: int = 1, U=None, V=None, W=None) -> int:
     return total
 
 
-def operand_counts(levels: int):
+def operand_counts(levels: int, basis: str = "strassen"):
     """(W_A, W_B, W_C) of every instance: the number of nonzero coefficients
     in its A-operand, B-operand and C-update (Section 3.2)."""
-    UL, VL, WL, _ = level_coefficients(levels)
+    UL, VL, WL, _ = level_coefficients(levels, *basis_tables(basis))
     nnz = lambda M: [int(np.count_nonzero(M[:, r])) for r in range(M.shape[1])]
     return list(zip(nnz(UL), nnz(VL), nnz(WL)))
 
@@ -184,8 +238,9 @@ def _pad(X: np.ndarray, rows: int, cols: int) -> np.ndarray:
     return out
 
 
-def _strassen_rec(A: np.ndarray, B: np.ndarray, levels: int) -> np.ndarray:
-    """M = A @ B for exactly even-sized padded operands, by Eq. (3)."""
+def _strassen_rec(A: np.ndarray, B: np.ndarray, levels: int, U, V, W) -> np.ndarray:
+    """M = A @ B for exactly even-sized padded operands, by Eq. (3) (or another
+    one-level table U, V, W applied at every level)."""
     if levels == 0:
         return A @ B   # leaf: library FP64 matmul
     hm, hk = A.shape[0] // 2, A.shape[1] // 2
@@ -194,17 +249,17 @@ def _strassen_rec(A: np.ndarray, B: np.ndarray, levels: int) -> np.ndarray:
     Bq = [B[:hk, :hn], B[:hk, hn:], B[hk:, :hn], B[hk:, hn:]]
     Cq = [np.zeros((hm, hn)) for _ in range(4)]
     for r in range(7):
-        P = sum(STRASSEN_U[q, r] * Aq[q] for q in range(4) if STRASSEN_U[q, r])
-        Q = sum(STRASSEN_V[q, r] * Bq[q] for q in range(4) if STRASSEN_V[q, r])
-        M = _strassen_rec(P, Q, levels - 1)
+        P = sum(U[q, r] * Aq[q] for q in range(4) if U[q, r])
+        Q = sum(V[q, r] * Bq[q] for q in range(4) if V[q, r])
+        M = _strassen_rec(P, Q, levels - 1, U, V, W)
         for q in range(4):
-            if STRASSEN_W[q, r]:
-                Cq[q] += STRASSEN_W[q, r] * M
+            if W[q, r]:
+                Cq[q] += W[q, r] * M
     return np.block([[Cq[0], Cq[1]], [Cq[2], Cq[3]]])
 
 
 def strassen(A, B, C=None, alpha: float = 1.0, beta: float = 0.0,
-             levels: int = 1, align: int = 8) -> np.ndarray:
+             levels: int = 1, align: int = 8, basis: str = "strassen") -> np.ndarray:
     """FP64 Strassen: C_out = alpha * A B + beta * C, ``levels`` levels.
 
     beta is applied first (beta == 0 or C is None means C is not read), the
@@ -223,7 +278,7 @@ def strassen(A, B, C=None, alpha: float = 1.0, beta: float = 0.0,
         Mp = g * block_size(m, levels, align)
         Np = g * block_size(n, levels, align)
         Kp = g * block_size(k, levels, align)
-        prod = _strassen_rec(_pad(A, Mp, Kp), _pad(B, Kp, Np), levels)[:m, :n]
+        prod = _strassen_rec(_pad(A, Mp, Kp), _pad(B, Kp, Np), levels, *basis_tables(basis))[:m, :n]
     out = alpha * prod
     if C is not None and beta != 0.0:
         out = out + beta * np.asarray(C, dtype=np.float64)

@@ -248,3 +248,66 @@ def test_normwise_error_closed_forms():
 def test_effective_tflops_formula():
     assert oracle.effective_tflops(1000, 1000, 1000, 1e-3) == pytest.approx(2.0)
     assert oracle.effective_tflops(16384, 16384, 16384, 1.0) == pytest.approx(2 * 16384 ** 3 * 1e-12)
+
+
+# ------------------------------------------------ Strassen-Winograd basis (Section 6)
+def _winograd_textbook(A, B):
+    """One level of the Winograd variant in its shared-subexpression form (S1..S4, T1..T4,
+    U2..U4), written independently of the oracle's per-product tables."""
+    h, hk, hn = A.shape[0] // 2, A.shape[1] // 2, B.shape[1] // 2
+    A11, A12, A21, A22 = A[:h, :hk], A[:h, hk:], A[h:, :hk], A[h:, hk:]
+    B11, B12, B21, B22 = B[:hk, :hn], B[:hk, hn:], B[hk:, :hn], B[hk:, hn:]
+    S1 = A21 + A22
+    S2 = S1 - A11
+    S3 = A11 - A21
+    S4 = A12 - S2
+    T1 = B12 - B11
+    T2 = B22 - T1
+    T3 = B22 - B12
+    T4 = T2 - B21
+    M1, M2, M3, M4 = A11 @ B11, A12 @ B21, S4 @ B22, A22 @ T4
+    M5, M6, M7 = S1 @ T1, S2 @ T2, S3 @ T3
+    U2 = M1 + M6
+    U3 = U2 + M7
+    U4 = U2 + M5
+    return np.block([[M1 + M2, U4 + M3], [U3 - M4, U3 + M5]])
+
+
+@pytest.mark.parametrize("levels", [1, 2])
+def test_winograd_brent_equations_hold(levels):
+    assert oracle.brent_residual(levels, *oracle.BASES["winograd"]) == 0
+
+
+def test_winograd_brent_detects_every_single_coefficient_change():
+    U, V, W = (M.copy() for M in oracle.BASES["winograd"])
+    for M in (U, V, W):
+        for idx in itertools.product(range(4), range(7)):
+            old = M[idx]
+            for new in {-1, 0, 1} - {old}:
+                M[idx] = new
+                assert oracle.brent_residual(1, U, V, W) > 0
+            M[idx] = old
+
+
+def test_winograd_tables_equal_the_shared_subexpression_form():
+    A, B = synth.problem(16, 12, 10, seed=3, dist="int")
+    np.testing.assert_array_equal(oracle.strassen(A, B, levels=1, align=1, basis="winograd"),
+                                  _winograd_textbook(A.astype(np.float64), B.astype(np.float64)))
+
+
+def test_winograd_operand_counts():
+    c = oracle.operand_counts(1, "winograd")
+    assert [x[0] for x in c] == [1, 1, 4, 1, 2, 3, 2]   # W_A
+    assert [x[1] for x in c] == [1, 1, 1, 4, 2, 3, 2]   # W_B
+    assert [x[2] for x in c] == [4, 1, 1, 1, 2, 3, 2]   # W_C
+    assert sum(x[2] for x in c) == 14
+
+
+@pytest.mark.parametrize("levels", [1, 2])
+@pytest.mark.parametrize("m,n,k", [(16, 16, 16), (37, 21, 50), (64, 64, 64), (5, 130, 3)])
+def test_winograd_exact_on_small_integers(levels, m, n, k):
+    A, B = synth.problem(m, n, k, seed=7 * m + k, dist="int")
+    C = synth.small_int((m, n), 5)
+    want = oracle.classical(A, B, C, alpha=2.0, beta=-3.0)
+    got = oracle.strassen(A, B, C, alpha=2.0, beta=-3.0, levels=levels, basis="winograd")
+    np.testing.assert_array_equal(got, want)
