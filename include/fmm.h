@@ -116,7 +116,9 @@ typedef struct fmm_options {
                         the sum passes overlap the products (joined back into `stream`).
                         The first pipelined call on a device creates that stream: make it
                         before any stream capture begins. */
-    int reserved[3]; /* zero */
+    int basis;       /* 0 = Strassen (Eq. 3); 1 = the Strassen-Winograd variant written per
+                        product (14 nonzeros in each of U, V, W; levels <= 1, packed or fused) */
+    int reserved[2]; /* zero */
 } fmm_options;
 
 /* Bytes of workspace fmm_gemm needs for this problem (0 when none).  Returns
@@ -258,6 +260,8 @@ fmm_status fmm_debug_wait_timeout(void* stream);
  * must hold 4^L * 7^L entries.  Returns 7^L, or -1 on a bad argument.
  * Source: Section 3, Eq. (3), and its Kronecker power for Section 3.4. */
 int fmm_product_table(int levels, int8_t* U, int8_t* V, int8_t* W);
+/* As fmm_product_table for a basis (fmm_options.basis: 0 Strassen, 1 Strassen-Winograd). */
+int fmm_product_table_ex(int levels, int basis, int8_t* U, int8_t* V, int8_t* W);
 
 /* Phase timing.  While enabled, each launch of a phase -- 0: beta pass,
  * 1: operand-sum passes, 2: tensor-core kernel -- is bracketed by two CUDA

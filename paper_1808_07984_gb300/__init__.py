@@ -41,7 +41,7 @@ class _Options(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int), ("tile_n", ctypes.c_int), ("num_ctas", ctypes.c_int),
                 ("schedule", ctypes.c_int), ("bk", ctypes.c_int), ("cta_pair", ctypes.c_int),
                 ("round_tiles", ctypes.c_int), ("fringe", ctypes.c_int), ("pipeline", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3)]
+                ("basis", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 _lib = None
@@ -109,6 +109,8 @@ def load() -> ctypes.CDLL:
     L.fmm_debug_wait_timeout.argtypes = [vp]
     L.fmm_product_table.restype = i32
     L.fmm_product_table.argtypes = [i32, vp, vp, vp]
+    L.fmm_product_table_ex.restype = i32
+    L.fmm_product_table_ex.argtypes = [i32, i32, vp, vp, vp]
     L.fmm_profile_enable.restype = i32
     L.fmm_profile_enable.argtypes = [i32]
     L.fmm_profile_read.restype = i32
@@ -128,11 +130,13 @@ SCHEDULES = {"auto": 0, "product": 1, "rounds": 2}
 
 
 FRINGES = {"pad": 0, "peel": 1}
+BASES = {"strassen": 0, "winograd": 1}
 
 
 def _opts(algo="auto", tile_n=0, num_ctas=0, schedule="auto", bk=0, cta_pair=None, round_tiles=0,
-          pipeline=None, fringe="pad"):
+          pipeline=None, fringe="pad", basis="strassen"):
     o = _Options()
+    o.basis = BASES[basis] if isinstance(basis, str) else int(basis)
     o.round_tiles = int(round_tiles)
     o.fringe = FRINGES[fringe] if isinstance(fringe, str) else int(fringe)
     o.pipeline = 0 if pipeline is None else (2 if pipeline else 1)
@@ -150,8 +154,8 @@ def _variant(v) -> int:
 
 
 def workspace_size(m, n, k, levels=1, variant="split3", algo="auto", tile_n=0, cta_pair=None,
-                   fringe="pad") -> int:
-    o = _opts(algo, tile_n, cta_pair=cta_pair, fringe=fringe)
+                   fringe="pad", basis="strassen") -> int:
+    o = _opts(algo, tile_n, cta_pair=cta_pair, fringe=fringe, basis=basis)
     ws = load().fmm_workspace_size_ex(m, n, k, levels, _variant(variant), ctypes.byref(o))
     if ws == ctypes.c_size_t(-1).value:
         raise FmmError(3, "unsupported combination")
@@ -171,7 +175,7 @@ _IN_DTYPE = {0: "float32", 1: "bfloat16", 2: "float16", 3: "float32"}
 def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
          variant="split3", algo="auto", tile_n: int = 0, num_ctas: int = 0,
          workspace=None, stream=None, schedule="auto", bk: int = 0, cta_pair=None,
-         round_tiles: int = 0, pipeline=None, fringe="pad"):
+         round_tiles: int = 0, pipeline=None, fringe="pad", basis="strassen"):
     """C = alpha * A @ B + beta * C on the current CUDA device (torch tensors).
 
     A (m x k) and B (k x n) are row-major CUDA tensors of the element type the
@@ -183,7 +187,7 @@ def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
     ``pipeline``: None = automatic, True / False = overlap the operand-sum passes with the
     tensor-core kernel one top-level product at a time, or not.  ``fringe``: "pad" (zero
     padding of the blocks) or "peel" (Strassen on the evenly splitting core plus classical
-    strip products).
+    strip products).  ``basis``: "strassen" or "winograd" (one level).
     """
     import torch
     v = _variant(variant)
@@ -204,12 +208,12 @@ def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
         beta = 0.0
     if C.dtype != torch.float32 or not C.is_cuda or (C.numel() and C.stride(1) != 1):
         raise FmmError(1, "C must be a float32 CUDA tensor with contiguous rows")
-    ws_need = workspace_size(m, n, k, levels, v, algo, tile_n, cta_pair, fringe)
+    ws_need = workspace_size(m, n, k, levels, v, algo, tile_n, cta_pair, fringe, basis)
     if workspace is None and ws_need > 0:
         workspace = torch.empty(ws_need, dtype=torch.uint8, device=A.device)
     ws_ptr = workspace.data_ptr() if workspace is not None else None
     ws_bytes = workspace.numel() if workspace is not None else 0
-    o = _opts(algo, tile_n, num_ctas, schedule, bk, cta_pair, round_tiles, pipeline, fringe)
+    o = _opts(algo, tile_n, num_ctas, schedule, bk, cta_pair, round_tiles, pipeline, fringe, basis)
     st = load().fmm_gemm_ex(m, n, k, float(alpha), A.data_ptr(), max(A.stride(0), 1),
                             B.data_ptr(), max(B.stride(0), 1), float(beta), C.data_ptr(),
                             max(C.stride(0), 1), int(levels), v, ws_ptr, ws_bytes,
@@ -226,7 +230,7 @@ def workspace_size_backward(m, n, k, levels=1, variant="split3") -> int:
 
 
 def gemm_backward(A, B, dC, levels: int = 1, variant="split3", need_dA=True, need_dB=True,
-                  workspace=None, stream=None, pipeline=None):
+                  workspace=None, stream=None, pipeline=None, basis="strassen"):
     """(dA, dB) = (dC @ B.T, A.T @ dC) as Strassen products through fmm_gemm_backward_ex.
 
     A (m x k) and B (k x n) have the variant's element type, dC (m x n) is float32; the
@@ -248,7 +252,7 @@ def gemm_backward(A, B, dC, levels: int = 1, variant="split3", need_dA=True, nee
     ws_need = workspace_size_backward(m, n, k, levels, v)
     if workspace is None and ws_need > 0:
         workspace = torch.empty(ws_need, dtype=torch.uint8, device=A.device)
-    o = _opts(pipeline=pipeline)
+    o = _opts(pipeline=pipeline, basis=basis)
     st = load().fmm_gemm_backward_ex(
         m, n, k, A.data_ptr(), max(A.stride(0), 1), B.data_ptr(), max(B.stride(0), 1),
         dC.data_ptr(), max(dC.stride(0), 1),
@@ -445,7 +449,7 @@ def profile_read():
     return {p: (float(ms[i]), int(n[i])) for i, p in enumerate(PHASES)}
 
 
-def product_table(levels: int):
+def product_table(levels: int, basis="strassen"):
     """(U, V, W) int8 arrays of shape (4**L, 7**L) as the kernels use them; row
     index bi * 2**L + bj."""
     import numpy as np
@@ -453,7 +457,7 @@ def product_table(levels: int):
     U = np.zeros(Q * R, dtype=np.int8)
     V = np.zeros(Q * R, dtype=np.int8)
     W = np.zeros(Q * R, dtype=np.int8)
-    r = load().fmm_product_table(levels, U.ctypes.data, V.ctypes.data, W.ctypes.data)
+    r = load().fmm_product_table_ex(levels, BASES[basis], U.ctypes.data, V.ctypes.data, W.ctypes.data)
     if r != R:
         raise FmmError(1, "bad levels")
     return U.reshape(Q, R), V.reshape(Q, R), W.reshape(Q, R)

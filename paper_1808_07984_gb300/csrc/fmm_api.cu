@@ -140,7 +140,7 @@ int ipow(int b, int e) {
 
 // Multi-level products (Section 3.4): product (r_1..r_L) takes block (q_1..q_L) -- block q_L
 // of ... of quadrant q_1 -- with coefficient prod_i X[r_i][q_i] (the Kronecker power).
-std::vector<Product> make_products(int L) {
+std::vector<Product> make_products(int L, int basis = kBasisStrassen) {
   const int R = ipow(7, L), Q = ipow(4, L), g = 1 << L;
   std::vector<Product> out(R);
   for (int r = 0; r < R; ++r) {
@@ -151,9 +151,9 @@ std::vector<Product> make_products(int L) {
       for (int i = L - 1, t = qi; i >= 0; --i, t /= 4) qd[i] = t % 4;
       int cu = 1, cv = 1, cw = 1, br = 0, bc = 0;
       for (int i = 0; i < L; ++i) {
-        cu *= strassen_u(rd[i], qd[i]);
-        cv *= strassen_v(rd[i], qd[i]);
-        cw *= strassen_w(rd[i], qd[i]);
+        cu *= basis_u(basis, rd[i], qd[i]);
+        cv *= basis_v(basis, rd[i], qd[i]);
+        cw *= basis_w(basis, rd[i], qd[i]);
         br = 2 * br + qd[i] / 2;
         bc = 2 * bc + qd[i] % 2;
       }
@@ -185,6 +185,7 @@ struct Plan {
   int bk = 64;  // k-elements per pipeline stage of the packed kernel (64, or 32 for split3)
   bool pair = false;  // packed kernel in CTA pairs: 256-row tiles shared by two CTAs
   int pipeline_mode = 0;  // fmm_options.pipeline: 0 automatic, 1 off, 2 on
+  int basis = kBasisStrassen;  // one-level coefficient tables (Strassen, or Strassen-Winograd)
   bool pipeline = false;  // sum passes per top-level product, overlapped with the products
   int algo = FMM_ALGO_PACKED;
   int schedule = kSchedProductMajor;
@@ -253,6 +254,11 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
     return fail(FMM_ERR_UNSUPPORTED, "single-CTA tiles are built for the forward product only");
   const int pipe = opt ? opt->pipeline : 0;
   if (pipe < 0 || pipe > 2) return fail(FMM_ERR_ARG, "pipeline must be 0, 1 or 2");
+  const int basis = opt ? opt->basis : 0;
+  if (basis != kBasisStrassen && basis != kBasisWinograd) return fail(FMM_ERR_ARG, "basis must be 0 or 1");
+  if (basis == kBasisWinograd && (levels > 1 || pl.algo == FMM_ALGO_HYBRID))
+    return fail(FMM_ERR_UNSUPPORTED, "the Winograd basis is built for one level (packed or fused)");
+  pl.basis = levels == 0 ? kBasisStrassen : basis;
   pl.pipeline_mode = pipe;
   pl.pipeline = !on_chip && levels >= 1 && pipe == 2;  // automatic: decided with C (prepare_packed)
   const int row_tile = pl.pair ? 2 * kBM : kBM;
@@ -415,7 +421,7 @@ fmm_status fill_common(CommonParams& c, const Plan& pl, const std::vector<Produc
 fmm_status gemm_fused(const Plan& pl, int64_t m, int64_t n, int64_t k, float alpha, const void* A,
                       int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc,
                       const DeviceInfo& dev, const fmm_options* opt, cudaStream_t s) {
-  const std::vector<Product> prods = make_products(pl.L);
+  const std::vector<Product> prods = make_products(pl.L, pl.basis);
   const int g = 1 << pl.L;
   FusedParams* fp = new FusedParams;
   std::memset(fp, 0, sizeof(FusedParams));
@@ -734,7 +740,7 @@ fmm_status prepare_packed(const Plan& pl, int64_t m, int64_t n, int64_t k, float
     return es;
   };
   st = encode_maps(pp, 0, pl.R);
-  const std::vector<Product> prods = make_products(pl.L);
+  const std::vector<Product> prods = make_products(pl.L, pl.basis);
   std::vector<int> live(pl.R);
   for (int r = 0; r < pl.R; ++r) live[r] = r;
   if (st == FMM_OK) st = fill_common(pp->c, pl, prods, live, m, n, alpha, C, ldc, dev, opt, job.grid);
@@ -785,8 +791,8 @@ fmm_status launch_chunk_sums(const PackedJob& job, int c, const DeviceInfo& dev,
     // a K-major B' (stored n x k)
     const int qa = pl.a_mn ? 2 * (q % 2) + q / 2 : q;
     const int qb = !pl.b_mn ? 2 * (q % 2) + q / 2 : q;
-    sa.c1[q] = static_cast<int8_t>(strassen_u(c, qa));
-    sb.c1[q] = static_cast<int8_t>(strassen_v(c, qb));
+    sa.c1[q] = static_cast<int8_t>(basis_u(pl.basis, c, qa));
+    sb.c1[q] = static_cast<int8_t>(basis_v(pl.basis, c, qb));
   }
   PhaseScope ps(kPhasePack, s, 2);
   cudaError_t e = launch_operand_sums(sa, pl.L, false, pl.a_mn, job.a_type, pl.bf16 ? 0 : 1, dev.sms, s);
@@ -886,6 +892,15 @@ fmm_status launch_passes(const PackedJob& job, const DeviceInfo& dev, cudaStream
   if (job.maxbits) {
     cudaError_t e = cudaMemsetAsync(job.maxbits, 0, pl.scale_bytes, s);
     if (e != cudaSuccess) return cuda_fail(e, "clearing the panel maxima");
+  }
+  if (pl.basis != kBasisStrassen) {
+    // the sum kernel's full pass carries Strassen's tables; other bases form each one-level
+    // product in its own pass from run-time coefficients
+    for (int c = 0; c < 7; ++c) {
+      fmm_status st = launch_chunk_sums(job, c, dev, s);
+      if (st != FMM_OK) return st;
+    }
+    return FMM_OK;
   }
   cudaError_t e;
   {
@@ -1388,12 +1403,17 @@ fmm_status fmm_debug_wait_timeout(void* stream) {
 // Exports the level-L product table in the layout U[(bi*2^L + bj) * 7^L + r] (likewise V, W),
 // so that host-side tests can check it against the Brent equations without a GPU.
 int fmm_product_table(int levels, int8_t* U, int8_t* V, int8_t* W) {
+  return fmm_product_table_ex(levels, kBasisStrassen, U, V, W);
+}
+
+int fmm_product_table_ex(int levels, int basis, int8_t* U, int8_t* V, int8_t* W) {
   if (levels < 0 || levels > 2 || !U || !V || !W) return -1;
+  if (basis != kBasisStrassen && basis != kBasisWinograd) return -1;
   const int R = ipow(7, levels), Q = ipow(4, levels);
   std::memset(U, 0, static_cast<size_t>(R) * Q);
   std::memset(V, 0, static_cast<size_t>(R) * Q);
   std::memset(W, 0, static_cast<size_t>(R) * Q);
-  const std::vector<Product> prods = make_products(levels);
+  const std::vector<Product> prods = make_products(levels, basis);
   for (int r = 0; r < R; ++r) {
     for (const Term& t : prods[r].a) U[t.block * R + r] = static_cast<int8_t>(t.sign);
     for (const Term& t : prods[r].b) V[t.block * R + r] = static_cast<int8_t>(t.sign);

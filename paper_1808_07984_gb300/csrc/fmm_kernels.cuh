@@ -58,6 +58,35 @@ __host__ __device__ constexpr int strassen_w(int r, int q) {
   return t[r][q];
 }
 
+// The Strassen-Winograd variant (named among the fast-matmul algorithms the primitive can
+// carry, Section 6), written per product: each operand and each C update taken directly from
+// the quadrants (14 nonzeros in each table; its usual form shares partial sums instead).
+__host__ __device__ constexpr int winograd_u(int r, int q) {
+  constexpr int8_t t[7][4] = {{1, 0, 0, 0}, {0, 1, 0, 0},  {1, 1, -1, -1}, {0, 0, 0, 1},
+                              {0, 0, 1, 1}, {-1, 0, 1, 1}, {1, 0, -1, 0}};
+  return t[r][q];
+}
+__host__ __device__ constexpr int winograd_v(int r, int q) {
+  constexpr int8_t t[7][4] = {{1, 0, 0, 0},   {0, 0, 1, 0},   {0, 0, 0, 1}, {1, -1, -1, 1},
+                              {-1, 1, 0, 0}, {1, -1, 0, 1}, {0, -1, 0, 1}};
+  return t[r][q];
+}
+__host__ __device__ constexpr int winograd_w(int r, int q) {
+  constexpr int8_t t[7][4] = {{1, 1, 1, 1}, {1, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, -1, 0},
+                              {0, 1, 0, 1}, {0, 1, 1, 1}, {0, 0, 1, 1}};
+  return t[r][q];
+}
+enum Basis : int { kBasisStrassen = 0, kBasisWinograd = 1 };
+__host__ __device__ constexpr int basis_u(int basis, int r, int q) {
+  return basis == kBasisWinograd ? winograd_u(r, q) : strassen_u(r, q);
+}
+__host__ __device__ constexpr int basis_v(int basis, int r, int q) {
+  return basis == kBasisWinograd ? winograd_v(r, q) : strassen_v(r, q);
+}
+__host__ __device__ constexpr int basis_w(int basis, int r, int q) {
+  return basis == kBasisWinograd ? winograd_w(r, q) : strassen_w(r, q);
+}
+
 enum ErrBits : unsigned {
   kErrProducerWait = 1u,
   kErrMmaWait = 2u,

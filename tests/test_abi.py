@@ -52,6 +52,17 @@ def test_library_tables_match_oracle(lib, levels):
         np.testing.assert_array_equal(W[bi * g + bj], WL[row])
 
 
+@pytest.mark.parametrize("levels", [0, 1, 2])
+def test_library_winograd_tables_match_oracle(lib, levels):
+    U, V, W = fmm.product_table(levels, "winograd")
+    UL, VL, WL, rc = oracle.level_coefficients(levels, *oracle.BASES["winograd"])
+    g = 1 << levels
+    for row, (bi, bj) in enumerate(rc):
+        np.testing.assert_array_equal(U[bi * g + bj], UL[row])
+        np.testing.assert_array_equal(V[bi * g + bj], VL[row])
+        np.testing.assert_array_equal(W[bi * g + bj], WL[row])
+
+
 @pytest.mark.parametrize("levels", [1, 2])
 def test_library_tables_satisfy_brent(lib, levels):
     """Independent of the oracle's arrays: rebuild the trilinear identity."""

@@ -59,6 +59,17 @@ def test_backward_pipelined_int_bit_exact(m, n, k, levels):
     np.testing.assert_array_equal(dB.cpu().numpy(), oracle.classical(np.ascontiguousarray(A.T), dC))
 
 
+@pytest.mark.parametrize("m,n,k", [(300, 200, 136), (129, 65, 257)])
+def test_backward_winograd_int_bit_exact(m, n, k):
+    A, B = synth.problem(m, n, k, 19 + m, "int")
+    dC = synth.small_int((m, n), 20 + n)
+    dA, dB = fmm.gemm_backward(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(),
+                               torch.from_numpy(dC).cuda(), levels=1, basis="winograd")
+    fmm.device_status()
+    np.testing.assert_array_equal(dA.cpu().numpy(), oracle.classical(dC, np.ascontiguousarray(B.T)))
+    np.testing.assert_array_equal(dB.cpu().numpy(), oracle.classical(np.ascontiguousarray(A.T), dC))
+
+
 @pytest.mark.parametrize("variant", ["split3", "plain_bf16"])
 @pytest.mark.parametrize("levels", [0, 1, 2])
 @pytest.mark.parametrize("m,n,k", [(257, 300, 140), (512, 384, 640)])

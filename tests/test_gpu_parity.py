@@ -60,7 +60,7 @@ def _to_device(X, ld_pad, dtype):
 
 def run(m, n, k, levels, variant="split3", dist="uniform", seed=0, alpha=1.0, beta=0.0,
         tile_n=0, pads=(0, 0, 0), c_fill=None, rows=None, schedule="auto", algo="auto", bk=0,
-        cta_pair=None, round_tiles=0, pipeline=None, fringe="pad"):
+        cta_pair=None, round_tiles=0, pipeline=None, fringe="pad", basis="strassen"):
     A, B = synth.problem(m, n, k, seed, dist)
     in_dtype = {"bf16": torch.bfloat16, "f16": torch.float16}.get(variant, torch.float32)
     Ad = _to_device(A, pads[0], in_dtype)
@@ -75,7 +75,7 @@ def run(m, n, k, levels, variant="split3", dist="uniform", seed=0, alpha=1.0, be
             Cd.fill_(c_fill)
     fmm.gemm(Ad, Bd, Cd, alpha=alpha, beta=beta, levels=levels, variant=variant, tile_n=tile_n,
              schedule=schedule, algo=algo, bk=bk, cta_pair=cta_pair, round_tiles=round_tiles,
-             pipeline=pipeline, fringe=fringe)
+             pipeline=pipeline, fringe=fringe, basis=basis)
     fmm.device_status()
     C = Cd.cpu().numpy().astype(np.float64)
     if variant in ("bf16", "f16"):
@@ -266,6 +266,31 @@ def test_peeled_odd_30001_29999_4097_sampled_rows():
     C, C64, An, Bn = run(30001, 29999, 4097, 2, "split3", dist="gaussian", seed=5, rows=rows,
                          fringe="peel")
     assert oracle.normwise_error(C, C64, An, Bn) <= tolerance("split3", 2, 4097)
+
+
+@pytest.mark.parametrize("opts", [{}, {"algo": "fused"}, {"pipeline": True}, {"pads": (0, 0, 1)},
+                                  {"cta_pair": False}, {"fringe": "peel"}])
+@pytest.mark.parametrize("m,n,k", [(300, 520, 200), (129, 257, 65), (1000, 1200, 300), (1, 300, 1)])
+def test_winograd_basis_bit_exact(m, n, k, opts):
+    """The Strassen-Winograd variant's seven products (one level) through every path."""
+    o = dict(opts)
+    pads = o.pop("pads", (0, 0, 0))
+    if o.get("algo") == "fused":
+        pads = (_pad4(k), _pad4(n), 0)
+    C, C64, _, _ = run(m, n, k, 1, "split3", dist="int", seed=43 * m + k, basis="winograd", pads=pads, **o)
+    np.testing.assert_array_equal(C, C64)
+
+
+@pytest.mark.parametrize("variant", ["split3", "plain_bf16", "bf16", "f16"])
+def test_winograd_basis_float(variant):
+    C, C64, An, Bn = run(600, 520, 400, 1, variant, seed=45, basis="winograd")
+    assert oracle.normwise_error(C, C64, An, Bn) <= tolerance(variant, 1, 400)
+
+
+def test_winograd_basis_rejected_at_two_levels():
+    A = torch.zeros((64, 64), device="cuda")
+    with pytest.raises(fmm.FmmError):
+        fmm.gemm(A, A, levels=2, basis="winograd")
 
 
 def test_cta_pair_rejected_with_bk32():
