@@ -208,6 +208,16 @@ void fmm_tune_default(fmm_tune_table* out);
 fmm_status fmm_tune_select(const fmm_tune_table* tune, int64_t m, int64_t n, int64_t k,
                            int* levels, int* tile_n);
 
+/* Native autotuner: times square d x d x d products of `variant` at levels 0, 1, 2 and
+ * tile widths 128 and 256 for each probe size d = sizes[0..count-1] (1..8 sizes,
+ * increasing; `reps` timed calls after one warm-up, CUDA events on `stream`), and writes
+ * to *out one class per run of probes with the same fastest (levels, tile_n), class
+ * boundaries at the geometric means of neighbouring probe sizes.  times_ms, if not NULL,
+ * receives count * 6 times in milliseconds (probe-major, then levels, then tile 128, 256).
+ * Allocates and frees its own device buffers: a tuning call, not a product call. */
+fmm_status fmm_tune_measure(int variant, const int64_t* sizes, int count, int reps,
+                            fmm_tune_table* out, float* times_ms, void* stream);
+
 /* A batched plan holds, in the caller's workspace, the parameter blocks of every
  * problem (tensor maps, destination tables) and the work list.  Creating it uploads
  * them synchronously; executing it only launches kernels on `stream` (no host

@@ -83,6 +83,8 @@ def load() -> ctypes.CDLL:
     L.fmm_workspace_size_backward.argtypes = [i64, i64, i64, i32, i32]
     L.fmm_tune_default.restype = None
     L.fmm_tune_default.argtypes = [ctypes.POINTER(TuneTable)]
+    L.fmm_tune_measure.restype = i32
+    L.fmm_tune_measure.argtypes = [i32, vp, i32, i32, ctypes.POINTER(TuneTable), vp, vp]
     L.fmm_tune_select.restype = i32
     L.fmm_tune_select.argtypes = [ctypes.POINTER(TuneTable), i64, i64, i64,
                                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
@@ -318,6 +320,23 @@ def tune_table(classes=None):
         t.levels[i] = int(lv)
         t.tile_n[i] = int(tn)
     return t
+
+
+def tune_measure(sizes=(1024, 2048, 4096, 8192, 16384), variant="split3", reps: int = 3,
+                 stream=None) -> dict:
+    """Native autotuner (fmm_tune_measure): the table dict autotune.autotune returns, measured
+    by the library itself."""
+    import numpy as np
+    sz = np.asarray(sizes, dtype=np.int64)
+    times = np.zeros(6 * len(sz), dtype=np.float32)
+    t = TuneTable()
+    _check(load().fmm_tune_measure(_variant(variant), sz.ctypes.data, len(sz), int(reps), ctypes.byref(t),
+                                   times.ctypes.data, _stream_handle(stream)))
+    classes = [{"max_dim": int(t.max_dim[i]), "levels": int(t.levels[i]), "tile_n": int(t.tile_n[i])}
+               for i in range(t.count)]
+    probes = {str(int(d)): {f"L{L}_N{tn}": round(float(times[i * 6 + L * 2 + j]), 4)
+                            for L in range(3) for j, tn in enumerate((128, 256))} for i, d in enumerate(sz)}
+    return {"classes": classes, "variant": variant, "probes_ms": probes, "native": True}
 
 
 def tune_select(m, n, k, tune=None):

@@ -55,10 +55,16 @@ def build_table(probes: dict) -> dict:
 
 def autotune(sizes=(1024, 2048, 4096, 8192, 16384), variant: str = "split3",
              levels=(0, 1, 2), tiles=(128, 256), steps: int = 3, prior: str | None = None,
-             keep: int = 2) -> dict:
+             keep: int = 2, native: bool = False) -> dict:
     """Measure the candidates of each probe size and build the table.  prior="model": rank
-    the candidates with the analytic model (model.py) and measure only the best ``keep``."""
+    the candidates with the analytic model (model.py) and measure only the best ``keep``.
+    native=True: the library's own tuner (fmm_tune_measure) measures every candidate."""
     import torch
+    if native:
+        from . import tune_measure
+        table = tune_measure(sizes, variant, steps)
+        table["gpu"] = torch.cuda.get_device_name()
+        return table
     probes = {}
     for d in sizes:
         cands = [(lv, tn) for lv in levels for tn in tiles]

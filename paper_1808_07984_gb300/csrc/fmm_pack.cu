@@ -146,7 +146,6 @@ __device__ __forceinline__ void load_group(const SumParams& p, const T* X, int64
 
 template <typename T, int OUT16, int L, bool IS_B, bool TRANSQ, int TERMS, int EPT, int SCALE>
 __global__ void __launch_bounds__(256) operand_sums_kernel(const __grid_constant__ SumParams p) {
-  constexpr int G = 1 << L;
   const T* X = static_cast<const T*>(p.X);
   const int64_t groups = (p.hc + EPT - 1) / EPT;
   const int64_t total = p.hr * groups;

@@ -133,3 +133,15 @@ def test_batched_256_uneven_fp16_sampled():
         lv = fmm.tune_select(m, n, k)[0]
         assert err <= 4 * 2.0 ** -11 * 3 ** lv / math.sqrt(k), (shapes[i], err)
         worst = max(worst, err)
+
+
+def test_native_tuner_builds_a_valid_table():
+    t = fmm.tune_measure(sizes=(512, 1024, 2048), variant="split3", reps=2)
+    assert 1 <= len(t["classes"]) <= 3
+    prev = 0
+    for c in t["classes"]:
+        assert c["levels"] in (0, 1, 2) and c["tile_n"] in (128, 256) and c["max_dim"] > prev
+        prev = c["max_dim"]
+    assert set(t["probes_ms"]) == {"512", "1024", "2048"}
+    assert all(v > 0 for p in t["probes_ms"].values() for v in p.values())
+    fmm.tune_select(700, 700, 700, t)  # the table is usable by the batched entry points

@@ -106,3 +106,15 @@ def test_model_calibration_samples_fit_within_ten_percent():
 def test_model_ranks_candidates():
     c = model.rank_candidates(16384)
     assert len(c) == 6 and c[0][0] == 2
+
+
+def test_native_tuner_rejects_bad_arguments_without_gpu():
+    import ctypes
+    import numpy as np
+    import paper_1808_07984_gb300 as fmm
+    lib = fmm.load()
+    t = fmm.TuneTable()
+    sz = np.array([2048, 1024], dtype=np.int64)  # not increasing
+    assert lib.fmm_tune_measure(0, sz.ctypes.data, 2, 3, ctypes.byref(t), None, None) == 1
+    assert lib.fmm_tune_measure(0, sz.ctypes.data, 0, 3, ctypes.byref(t), None, None) == 1
+    assert lib.fmm_tune_measure(0, sz.ctypes.data, 1, 0, ctypes.byref(t), None, None) == 1
