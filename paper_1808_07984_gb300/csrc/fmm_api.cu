@@ -101,7 +101,7 @@ fmm_status device_info(DeviceInfo& out) {
     int major = 0, minor = 0;
     cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
     cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
-    if (major != 10) {
+    if (major != 10 || minor != 3) {
       return fail(FMM_ERR_UNSUPPORTED, "this library is built for sm_103a (GB300); device is sm_" +
                                            std::to_string(major) + std::to_string(minor));
     }
