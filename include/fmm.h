@@ -118,7 +118,13 @@ typedef struct fmm_options {
                         before any stream capture begins. */
     int basis;       /* 0 = Strassen (Eq. 3); 1 = the Strassen-Winograd variant written per
                         product (14 nonzeros in each of U, V, W; levels <= 1, packed or fused) */
-    int reserved[2]; /* zero */
+    int deterministic; /* 1 = ownership mode: each output tile position belongs to one CTA
+                          (pair), which applies the C updates of all 7^L products in a fixed
+                          order, each item's after the previous item's have completed; results
+                          are bitwise reproducible (tile-rounds schedule, one tile per CTA
+                          pair per round).  0 = updates from different CTAs may land in any
+                          order (default) */
+    int reserved[1]; /* zero */
 } fmm_options;
 
 /* Bytes of workspace fmm_gemm needs for this problem (0 when none).  Returns

@@ -41,7 +41,7 @@ class _Options(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int), ("tile_n", ctypes.c_int), ("num_ctas", ctypes.c_int),
                 ("schedule", ctypes.c_int), ("bk", ctypes.c_int), ("cta_pair", ctypes.c_int),
                 ("round_tiles", ctypes.c_int), ("fringe", ctypes.c_int), ("pipeline", ctypes.c_int),
-                ("basis", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+                ("basis", ctypes.c_int), ("deterministic", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 _lib = None
@@ -136,8 +136,9 @@ BASES = {"strassen": 0, "winograd": 1}
 
 
 def _opts(algo="auto", tile_n=0, num_ctas=0, schedule="auto", bk=0, cta_pair=None, round_tiles=0,
-          pipeline=None, fringe="pad", basis="strassen"):
+          pipeline=None, fringe="pad", basis="strassen", deterministic=False):
     o = _Options()
+    o.deterministic = 1 if deterministic else 0
     o.basis = BASES[basis] if isinstance(basis, str) else int(basis)
     o.round_tiles = int(round_tiles)
     o.fringe = FRINGES[fringe] if isinstance(fringe, str) else int(fringe)
@@ -177,7 +178,8 @@ _IN_DTYPE = {0: "float32", 1: "bfloat16", 2: "float16", 3: "float32"}
 def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
          variant="split3", algo="auto", tile_n: int = 0, num_ctas: int = 0,
          workspace=None, stream=None, schedule="auto", bk: int = 0, cta_pair=None,
-         round_tiles: int = 0, pipeline=None, fringe="pad", basis="strassen"):
+         round_tiles: int = 0, pipeline=None, fringe="pad", basis="strassen",
+         deterministic: bool = False):
     """C = alpha * A @ B + beta * C on the current CUDA device (torch tensors).
 
     A (m x k) and B (k x n) are row-major CUDA tensors of the element type the
@@ -189,7 +191,8 @@ def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
     ``pipeline``: None = automatic, True / False = overlap the operand-sum passes with the
     tensor-core kernel one top-level product at a time, or not.  ``fringe``: "pad" (zero
     padding of the blocks) or "peel" (Strassen on the evenly splitting core plus classical
-    strip products).  ``basis``: "strassen" or "winograd" (one level).
+    strip products).  ``basis``: "strassen" or "winograd" (one level).  ``deterministic``:
+    ownership mode, bitwise reproducible results.
     """
     import torch
     v = _variant(variant)
@@ -215,7 +218,8 @@ def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
         workspace = torch.empty(ws_need, dtype=torch.uint8, device=A.device)
     ws_ptr = workspace.data_ptr() if workspace is not None else None
     ws_bytes = workspace.numel() if workspace is not None else 0
-    o = _opts(algo, tile_n, num_ctas, schedule, bk, cta_pair, round_tiles, pipeline, fringe, basis)
+    o = _opts(algo, tile_n, num_ctas, schedule, bk, cta_pair, round_tiles, pipeline, fringe, basis,
+              deterministic)
     st = load().fmm_gemm_ex(m, n, k, float(alpha), A.data_ptr(), max(A.stride(0), 1),
                             B.data_ptr(), max(B.stride(0), 1), float(beta), C.data_ptr(),
                             max(C.stride(0), 1), int(levels), v, ws_ptr, ws_bytes,

@@ -186,6 +186,7 @@ struct Plan {
   bool pair = false;  // packed kernel in CTA pairs: 256-row tiles shared by two CTAs
   int pipeline_mode = 0;  // fmm_options.pipeline: 0 automatic, 1 off, 2 on
   int basis = kBasisStrassen;  // one-level coefficient tables (Strassen, or Strassen-Winograd)
+  bool deterministic = false;  // ownership mode (fixed order of the C updates)
   bool pipeline = false;  // sum passes per top-level product, overlapped with the products
   int algo = FMM_ALGO_PACKED;
   int schedule = kSchedProductMajor;
@@ -259,6 +260,10 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
   if (basis == kBasisWinograd && (levels > 1 || pl.algo == FMM_ALGO_HYBRID))
     return fail(FMM_ERR_UNSUPPORTED, "the Winograd basis is built for one level (packed or fused)");
   pl.basis = levels == 0 ? kBasisStrassen : basis;
+  const int det = opt ? opt->deterministic : 0;
+  if (det < 0 || det > 1) return fail(FMM_ERR_ARG, "deterministic must be 0 or 1");
+  pl.deterministic = det == 1;
+  if (pl.deterministic) pl.schedule = kSchedTileRounds;  // ownership needs whole-tile rounds
   pl.pipeline_mode = pipe;
   pl.pipeline = !on_chip && levels >= 1 && pipe == 2;  // automatic: decided with C (prepare_packed)
   const int row_tile = pl.pair ? 2 * kBM : kBM;
@@ -414,6 +419,17 @@ fmm_status fill_common(CommonParams& c, const Plan& pl, const std::vector<Produc
   else if (c.c_tma && c_bytes >= 0.5 * op_bytes)
     rt = std::max<int64_t>(1, kRoundL2Bytes / footprint);
   c.round_tiles = rt >= workers ? 0 : static_cast<int32_t>(rt);
+  if (pl.deterministic) {
+    // ownership: rounds of exactly one tile per worker, the last round padded with empty
+    // items, so that worker b runs every product of tile position b of each round
+    const int64_t tiles = static_cast<int64_t>(c.tiles_m) * c.tiles_n;
+    const int64_t rounds = (tiles + workers - 1) / workers;
+    const int64_t padded = rounds * workers * static_cast<int64_t>(live.size());
+    if (padded >= (int64_t(1) << 31)) return fail(FMM_ERR_ARG, "too many tiles");
+    c.deterministic = 1;
+    c.round_tiles = workers;
+    c.num_items = static_cast<int32_t>(padded);
+  }
   return FMM_OK;
 }
 
@@ -771,7 +787,10 @@ fmm_status prepare_packed(const Plan& pl, int64_t m, int64_t n, int64_t k, float
       st = encode_maps(&q, c * P, P);
       for (int j = 0; j < kMaxProducts; ++j) q.c.prod[j] = j < P ? pp->c.prod[c * P + j] : ProductDests{};
       q.c.num_products = P;
-      q.c.num_items = P * pp->c.tiles_m * pp->c.tiles_n;
+      const int64_t tiles = static_cast<int64_t>(pp->c.tiles_m) * pp->c.tiles_n;
+      q.c.num_items = static_cast<int32_t>(
+          pp->c.deterministic ? (tiles + pp->c.round_tiles - 1) / pp->c.round_tiles * pp->c.round_tiles * P
+                              : P * tiles);
       if (job.maxbits) {
         q.c.maxbits_a = pp->c.maxbits_a + static_cast<int64_t>(c) * P * pl.panels_a;
         q.c.maxbits_b = pp->c.maxbits_b + static_cast<int64_t>(c) * P * pl.panels_b;

@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(fused_threads<TW>(), 1) fmm_fused_kernel(const
       };
       for (int item = first; ok && item < p.num_items; item += stride) {
         int r, tm, tn;
-        decode_item(item, p, r, tm, tn, stride);
+        if (!decode_item(item, p, r, tm, tn, stride)) continue;  // empty item
         // the product's source lists, read once into registers (indexed parameter loads in
         // the loops below would each go to the constant cache)
         const uint32_t* psw = reinterpret_cast<const uint32_t*>(&fp.src[r]);
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(fused_threads<TW>(), 1) fmm_fused_kernel(const
     bool ok = true;
     for (int item = first; ok && item < p.num_items; item += stride) {
       int r, tm, tn;
-      decode_item(item, p, r, tm, tn, stride);
+      if (!decode_item(item, p, r, tm, tn, stride)) continue;  // empty item
       // counts and sign masks of the product's source terms, read once into registers
       const uint32_t hdr = reinterpret_cast<const uint32_t*>(&fp.src[r])[kSrcWordHeader];
       const int na = hdr & 0xff, nb = (hdr >> 8) & 0xff;

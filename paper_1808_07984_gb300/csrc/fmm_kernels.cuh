@@ -129,6 +129,10 @@ struct CommonParams {
   int32_t num_products;
   int32_t schedule;     // Schedule
   int32_t round_tiles;  // kSchedTileRounds: tiles per round (0 = one per worker)
+  // ownership: every round holds G tiles (the last one padded with empty items), so worker
+  // b applies all R products of its tile, and its epilogue lets an item's C updates complete
+  // before the next item's: the C sums come out in one fixed order (bitwise reproducible)
+  int32_t deterministic;
   int32_t c_tma;     // write-back by TMA reductions through tmC (C rows 16-byte aligned)
   int32_t c_vec4;    // element-wise path: C rows are 16-byte aligned, vector reductions allowed
   // power-of-two scaling of the operand sums (FP16 variant), else null: panel maxima of the
@@ -226,13 +230,14 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
 // round (with G = W, worker b runs products 0..R-1 of one tile back to back), and the C
 // blocks of a round can stay in L2; the last, partial round is spread product by product.
 // `workers` is the number of independent item streams: CTAs, or CTA pairs of the pair kernel.
-__device__ __forceinline__ void decode_item(int item, const CommonParams& p, int& r, int& tm, int& tn,
+__device__ __forceinline__ bool decode_item(int item, const CommonParams& p, int& r, int& tm, int& tn,
                                             int workers) {
   const int tiles = p.tiles_m * p.tiles_n;
   int t;
   if (p.schedule == kSchedTileRounds) {
     const int G = p.round_tiles > 0 ? p.round_tiles : workers, R = p.num_products;
-    const int full = tiles / G;
+    // ownership: every round is full (items past the last tile are empty)
+    const int full = p.deterministic ? (tiles + G - 1) / G : tiles / G;
     const int items_full = full * G * R;
     if (item < items_full) {
       const int j = item / (G * R);
@@ -249,7 +254,9 @@ __device__ __forceinline__ void decode_item(int item, const CommonParams& p, int
     r = item / tiles;
     t = item - r * tiles;
   }
+  if (t >= tiles) return false;  // padding of an ownership round
   tile_coords(t, p.tiles_m, p.tiles_n, tm, tn);
+  return true;
 }
 
 
@@ -346,9 +353,11 @@ __device__ __forceinline__ bool mma_role(const Work& work, uint8_t* smem, uint64
     const uint32_t par = ((j >> 1) & 1) ^ 1u;
     return PAIR ? mbar_wait_cluster(bar, par, timeout_ns, abort_flag) : mbar_wait(bar, par, timeout_ns, abort_flag);
   };
-  for (int item = first; item < total; item += stride, ++it) {
+  for (int item = first; item < total; item += stride) {
     int local;
     const CommonParams& p = work.get(item, local);
+    int r_, tm_, tn_;
+    if (!decode_item(local, p, r_, tm_, tn_, stride)) continue;  // empty item
     const int acc = it & 1;
     if (!acc_free(it)) return false;
     tc_fence_after();
@@ -398,6 +407,7 @@ __device__ __forceinline__ bool mma_role(const Work& work, uint8_t* smem, uint64
       umma_commit_pair(smem_u32(&acc_full[acc]), 3);
     else
       umma_commit(smem_u32(&acc_full[acc]));
+    ++it;
   }
   // pair: both epilogues have released both accumulators before the CTAs may retire
   if (PAIR && (!acc_free(it) || !acc_free(it + 1))) return false;
@@ -425,18 +435,19 @@ __device__ __forceinline__ bool epilogue_role(const Work& work, uint8_t* epi_sme
   const int total = work.num_items();
   const int first = PAIR ? static_cast<int>(blockIdx.x >> 1) : static_cast<int>(blockIdx.x);
   const int stride = PAIR ? static_cast<int>(gridDim.x >> 1) : static_cast<int>(gridDim.x);
-  for (int item = first; item < total; item += stride, ++it) {
+  for (int item = first; item < total; item += stride) {
+    int local;
+    const CommonParams& p = work.get(item, local);
+    int r, tm, tn;
+    if (!decode_item(local, p, r, tm, tn, stride)) continue;  // empty item
     const int acc = it & 1;
     const uint32_t acc_par = (it >> 1) & 1;
+    ++it;
     if (!mbar_wait(smem_u32(&acc_full[acc]), acc_par, timeout_ns, abort_flag)) {
       ok = false;
       break;
     }
     tc_fence_after();
-    int local;
-    const CommonParams& p = work.get(item, local);
-    int r, tm, tn;
-    decode_item(local, p, r, tm, tn, stride);
     // Registers for everything the write-back loops read: `p` may live in global memory
     // (batched launch), so the compiler would reload it after every global reduction.
     const ProductDests pd = p.prod[r];
@@ -522,6 +533,8 @@ __device__ __forceinline__ bool epilogue_role(const Work& work, uint8_t* epi_sme
         buf ^= 1;
       }
     }
+    // ownership: this item's reductions land before the next item's (same C tiles)
+    if (p.deterministic && lane == 0) bulk_wait_group<0>();
   }
   if (lane == 0) bulk_wait_group<0>();  // reductions complete before the CTA retires
   return ok;
@@ -640,7 +653,7 @@ __global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_co
         const PackedParams& pp = problem_of(args, item, local);
         const CommonParams& p = pp.c;
         int r, tm, tn;
-        decode_item(local, p, r, tm, tn, stride);
+        if (!decode_item(local, p, r, tm, tn, stride)) continue;  // empty item
         const int a_row = (PAIR ? 2 * tm + rank : tm) * kBM;  // first A row of this CTA
         const int b_col = tn * BN + rank * BNL;               // first B column of this CTA
         for (int kb = 0; kb < p.nk; ++kb) {

@@ -60,7 +60,8 @@ def _to_device(X, ld_pad, dtype):
 
 def run(m, n, k, levels, variant="split3", dist="uniform", seed=0, alpha=1.0, beta=0.0,
         tile_n=0, pads=(0, 0, 0), c_fill=None, rows=None, schedule="auto", algo="auto", bk=0,
-        cta_pair=None, round_tiles=0, pipeline=None, fringe="pad", basis="strassen"):
+        cta_pair=None, round_tiles=0, pipeline=None, fringe="pad", basis="strassen",
+        deterministic=False):
     A, B = synth.problem(m, n, k, seed, dist)
     in_dtype = {"bf16": torch.bfloat16, "f16": torch.float16}.get(variant, torch.float32)
     Ad = _to_device(A, pads[0], in_dtype)
@@ -75,7 +76,7 @@ def run(m, n, k, levels, variant="split3", dist="uniform", seed=0, alpha=1.0, be
             Cd.fill_(c_fill)
     fmm.gemm(Ad, Bd, Cd, alpha=alpha, beta=beta, levels=levels, variant=variant, tile_n=tile_n,
              schedule=schedule, algo=algo, bk=bk, cta_pair=cta_pair, round_tiles=round_tiles,
-             pipeline=pipeline, fringe=fringe, basis=basis)
+             pipeline=pipeline, fringe=fringe, basis=basis, deterministic=deterministic)
     fmm.device_status()
     C = Cd.cpu().numpy().astype(np.float64)
     if variant in ("bf16", "f16"):
@@ -291,6 +292,31 @@ def test_winograd_basis_rejected_at_two_levels():
     A = torch.zeros((64, 64), device="cuda")
     with pytest.raises(fmm.FmmError):
         fmm.gemm(A, A, levels=2, basis="winograd")
+
+
+@pytest.mark.parametrize("opts", [{}, {"cta_pair": False}, {"algo": "fused"}, {"pipeline": True},
+                                  {"pads": (0, 0, 1)}, {"levels": 1}, {"levels": 0}])
+@pytest.mark.parametrize("m,n,k", [(300, 520, 200), (1000, 1200, 300), (129, 257, 65)])
+def test_deterministic_ownership_bit_exact(m, n, k, opts):
+    """Ownership mode (padded last round, per-item completion) through every path."""
+    o = dict(opts)
+    levels = o.pop("levels", 2)
+    pads = o.pop("pads", (0, 0, 0))
+    if o.get("algo") == "fused":
+        pads = (_pad4(k), _pad4(n), 0)
+    C, C64, _, _ = run(m, n, k, levels, "split3", dist="int", seed=51 * m + k, deterministic=True,
+                       pads=pads, **o)
+    np.testing.assert_array_equal(C, C64)
+
+
+@pytest.mark.parametrize("opts", [{}, {"algo": "fused"}, {"pads": (0, 0, 1)}])
+def test_deterministic_results_are_bitwise_reproducible(opts):
+    """The same float product three times in ownership mode: identical bits each time."""
+    o = dict(opts)
+    pads = o.pop("pads", (0, 0, 0))
+    m, n, k = 2000, 1800, 1536
+    outs = [run(m, n, k, 2, "split3", seed=53, deterministic=True, pads=pads, **o)[0] for _ in range(3)]
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
 
 
 def test_cta_pair_rejected_with_bk32():
