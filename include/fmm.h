@@ -124,7 +124,12 @@ typedef struct fmm_options {
                           are bitwise reproducible (tile-rounds schedule, one tile per CTA
                           pair per round).  0 = updates from different CTAs may land in any
                           order (default) */
-    int reserved[1]; /* zero */
+    int outer_scaling; /* 1 = outside power-of-two scaling (packed, forward product): every row
+                          of A and column of B is scaled by 2^-e so that its largest magnitude
+                          lies in [1, 2) before the operand sums are formed, and C is scaled
+                          back exactly afterwards (keeps badly scaled rows and columns from
+                          losing accuracy in the Strassen sums; two more passes over C) */
+    int reserved[4]; /* zero */
 } fmm_options;
 
 /* Bytes of workspace fmm_gemm needs for this problem (0 when none).  Returns

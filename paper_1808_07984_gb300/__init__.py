@@ -41,7 +41,8 @@ class _Options(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int), ("tile_n", ctypes.c_int), ("num_ctas", ctypes.c_int),
                 ("schedule", ctypes.c_int), ("bk", ctypes.c_int), ("cta_pair", ctypes.c_int),
                 ("round_tiles", ctypes.c_int), ("fringe", ctypes.c_int), ("pipeline", ctypes.c_int),
-                ("basis", ctypes.c_int), ("deterministic", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
+                ("basis", ctypes.c_int), ("deterministic", ctypes.c_int), ("outer_scaling", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
 
 
 _lib = None
@@ -136,8 +137,9 @@ BASES = {"strassen": 0, "winograd": 1}
 
 
 def _opts(algo="auto", tile_n=0, num_ctas=0, schedule="auto", bk=0, cta_pair=None, round_tiles=0,
-          pipeline=None, fringe="pad", basis="strassen", deterministic=False):
+          pipeline=None, fringe="pad", basis="strassen", deterministic=False, outer_scaling=False):
     o = _Options()
+    o.outer_scaling = 1 if outer_scaling else 0
     o.deterministic = 1 if deterministic else 0
     o.basis = BASES[basis] if isinstance(basis, str) else int(basis)
     o.round_tiles = int(round_tiles)
@@ -157,8 +159,8 @@ def _variant(v) -> int:
 
 
 def workspace_size(m, n, k, levels=1, variant="split3", algo="auto", tile_n=0, cta_pair=None,
-                   fringe="pad", basis="strassen") -> int:
-    o = _opts(algo, tile_n, cta_pair=cta_pair, fringe=fringe, basis=basis)
+                   fringe="pad", basis="strassen", outer_scaling=False) -> int:
+    o = _opts(algo, tile_n, cta_pair=cta_pair, fringe=fringe, basis=basis, outer_scaling=outer_scaling)
     ws = load().fmm_workspace_size_ex(m, n, k, levels, _variant(variant), ctypes.byref(o))
     if ws == ctypes.c_size_t(-1).value:
         raise FmmError(3, "unsupported combination")
@@ -179,7 +181,7 @@ def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
          variant="split3", algo="auto", tile_n: int = 0, num_ctas: int = 0,
          workspace=None, stream=None, schedule="auto", bk: int = 0, cta_pair=None,
          round_tiles: int = 0, pipeline=None, fringe="pad", basis="strassen",
-         deterministic: bool = False):
+         deterministic: bool = False, outer_scaling: bool = False):
     """C = alpha * A @ B + beta * C on the current CUDA device (torch tensors).
 
     A (m x k) and B (k x n) are row-major CUDA tensors of the element type the
@@ -192,7 +194,8 @@ def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
     tensor-core kernel one top-level product at a time, or not.  ``fringe``: "pad" (zero
     padding of the blocks) or "peel" (Strassen on the evenly splitting core plus classical
     strip products).  ``basis``: "strassen" or "winograd" (one level).  ``deterministic``:
-    ownership mode, bitwise reproducible results.
+    ownership mode, bitwise reproducible results.  ``outer_scaling``: exact power-of-two
+    scaling of the rows of A and columns of B around the product (badly scaled inputs).
     """
     import torch
     v = _variant(variant)
@@ -213,13 +216,13 @@ def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
         beta = 0.0
     if C.dtype != torch.float32 or not C.is_cuda or (C.numel() and C.stride(1) != 1):
         raise FmmError(1, "C must be a float32 CUDA tensor with contiguous rows")
-    ws_need = workspace_size(m, n, k, levels, v, algo, tile_n, cta_pair, fringe, basis)
+    ws_need = workspace_size(m, n, k, levels, v, algo, tile_n, cta_pair, fringe, basis, outer_scaling)
     if workspace is None and ws_need > 0:
         workspace = torch.empty(ws_need, dtype=torch.uint8, device=A.device)
     ws_ptr = workspace.data_ptr() if workspace is not None else None
     ws_bytes = workspace.numel() if workspace is not None else 0
     o = _opts(algo, tile_n, num_ctas, schedule, bk, cta_pair, round_tiles, pipeline, fringe, basis,
-              deterministic)
+              deterministic, outer_scaling)
     st = load().fmm_gemm_ex(m, n, k, float(alpha), A.data_ptr(), max(A.stride(0), 1),
                             B.data_ptr(), max(B.stride(0), 1), float(beta), C.data_ptr(),
                             max(C.stride(0), 1), int(levels), v, ws_ptr, ws_bytes,

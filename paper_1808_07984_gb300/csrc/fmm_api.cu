@@ -187,6 +187,8 @@ struct Plan {
   int pipeline_mode = 0;  // fmm_options.pipeline: 0 automatic, 1 off, 2 on
   int basis = kBasisStrassen;  // one-level coefficient tables (Strassen, or Strassen-Winograd)
   bool deterministic = false;  // ownership mode (fixed order of the C updates)
+  bool outer_scaling = false;  // power-of-two row (A) / column (B) scaling around the product
+  size_t outer_off = 0;        // workspace offset of the row and column maxima
   bool pipeline = false;  // sum passes per top-level product, overlapped with the products
   int algo = FMM_ALGO_PACKED;
   int schedule = kSchedProductMajor;
@@ -264,6 +266,12 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
   if (det < 0 || det > 1) return fail(FMM_ERR_ARG, "deterministic must be 0 or 1");
   pl.deterministic = det == 1;
   if (pl.deterministic) pl.schedule = kSchedTileRounds;  // ownership needs whole-tile rounds
+  const int osc = opt ? opt->outer_scaling : 0;
+  if (osc < 0 || osc > 1) return fail(FMM_ERR_ARG, "outer_scaling must be 0 or 1");
+  if (osc == 1 && (on_chip || a_mn || !b_mn))
+    return fail(FMM_ERR_UNSUPPORTED, "outside scaling is built for the packed forward product");
+  pl.outer_scaling = osc == 1;
+  if (pl.outer_scaling) pl.pipeline = false;
   pl.pipeline_mode = pipe;
   pl.pipeline = !on_chip && levels >= 1 && pipe == 2;  // automatic: decided with C (prepare_packed)
   const int row_tile = pl.pair ? 2 * kBM : kBM;
@@ -299,6 +307,11 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
     pl.a_bytes = static_cast<size_t>(round_up(7 * (2 * pl.hm) * (2 * pl.hk) * 4, 256));
     pl.b_bytes = static_cast<size_t>(round_up(7 * (2 * pl.hk) * (2 * pl.hn) * 4, 256));
     pl.ws = pl.a_bytes + pl.b_bytes;
+  }
+  if (pl.outer_scaling && pl.ws > 0) {
+    // float bits of max |x| of the m rows of A and the n columns of B
+    pl.outer_off = pl.ws;
+    pl.ws += static_cast<size_t>(round_up((m + n) * 4, 256));
   }
   return FMM_OK;
 }
@@ -705,6 +718,8 @@ fmm_status prepare_packed(const Plan& pl, int64_t m, int64_t n, int64_t k, float
   sa.out_lo = a_lo;
   sa.terms = pl.terms;
   sa.chunk = -1;  // every product (the pipelined path sets one top-level product per pass)
+  unsigned* outer_rows = pl.outer_scaling ? reinterpret_cast<unsigned*>(wsb + pl.outer_off) : nullptr;
+  sa.row_maxbits = outer_rows;  // rows of A
   sa.vec_ok = (reinterpret_cast<uintptr_t>(a.X) % 16 == 0 && a.ld % 4 == 0) ? 1 : 0;
   SumParams& sb = job.sb;
   sb = sa;
@@ -718,6 +733,8 @@ fmm_status prepare_packed(const Plan& pl, int64_t m, int64_t n, int64_t k, float
   sb.prod_stride = sb.hr * pl.ldb_w;
   sb.out_hi = b_hi;
   sb.out_lo = b_lo;
+  sb.row_maxbits = nullptr;
+  sb.col_maxbits = outer_rows ? outer_rows + m : nullptr;  // columns of B (and of C)
   sb.vec_ok = (reinterpret_cast<uintptr_t>(b.X) % 16 == 0 && b.ld % 4 == 0) ? 1 : 0;
   if (job.maxbits) {
     sa.maxbits = job.maxbits;
@@ -773,7 +790,8 @@ fmm_status prepare_packed(const Plan& pl, int64_t m, int64_t n, int64_t k, float
   // reductions (+18 % for 30001 x 29999 x 4097); with aligned C it gains nothing (+2 % to
   // -15 % on square and rank-k shapes: seven launches and their ramps cost what the hidden
   // sum passes save).
-  if (pl.pipeline_mode == 0 && pl.algo == FMM_ALGO_PACKED && pl.L == 2 && !pp->c.c_tma && pl.hk >= 512 &&
+  if (pl.pipeline_mode == 0 && pl.algo == FMM_ALGO_PACKED && pl.L == 2 && !pp->c.c_tma && !pl.outer_scaling &&
+      pl.hk >= 512 &&
       pl.hk <= 1536 && pl.hm >= 2048 && pl.hn >= 2048)
     job.pl.pipeline = true;
   if (batched) job.pl.pipeline = false;
@@ -901,13 +919,25 @@ fmm_status launch_pipelined(const PackedJob& job, const DeviceInfo& dev, cudaStr
 // tensor-core kernel).
 fmm_status launch_passes(const PackedJob& job, const DeviceInfo& dev, cudaStream_t s) {
   if (job.m == 0 || job.n == 0) return FMM_OK;
-  if (job.beta != 1.0f) {
+  const Plan& pl = job.pl;
+  const bool outer = pl.outer_scaling && job.has_work;
+  if (outer) {
+    // maxima of the rows of A and columns of B, then beta * C into the scaled problem
+    PhaseScope ps(kPhaseBeta, s, 3);
+    cudaError_t e = launch_outer_maxbits(job.sa.X, job.m, job.k, job.sa.ldx, job.sb.X, job.n, job.sb.ldx,
+                                         job.a_type, const_cast<unsigned*>(job.sa.row_maxbits),
+                                         const_cast<unsigned*>(job.sb.col_maxbits), dev.sms, s);
+    if (e == cudaSuccess)
+      e = job.beta == 0.0f ? launch_beta(job.C, job.m, job.n, job.ldc, 0.0f, dev.sms, s)
+                           : launch_outer_rescale(job.C, job.m, job.n, job.ldc, job.sa.row_maxbits,
+                                                  job.sb.col_maxbits, -1, job.beta, dev.sms, s);
+    if (e != cudaSuccess) return cuda_fail(e, "outside-scaling passes");
+  } else if (job.beta != 1.0f) {
     PhaseScope ps(kPhaseBeta, s);
     cudaError_t e = launch_beta(job.C, job.m, job.n, job.ldc, job.beta, dev.sms, s);
     if (e != cudaSuccess) return cuda_fail(e, "beta pass");
   }
   if (!job.has_work) return FMM_OK;
-  const Plan& pl = job.pl;
   if (job.maxbits) {
     cudaError_t e = cudaMemsetAsync(job.maxbits, 0, pl.scale_bytes, s);
     if (e != cudaSuccess) return cuda_fail(e, "clearing the panel maxima");
@@ -978,6 +1008,12 @@ fmm_status gemm_core(const Plan& pl, int64_t m, int64_t n, int64_t k, float alph
       e = launch_packed(*ka, pl.tile_n, pl.terms, pl.bf16, pl.a_mn, pl.b_mn, pl.bk, pl.pair, job->grid, s);
     }
     if (e != cudaSuccess) st = cuda_fail(e, "tensor-core pass");
+    if (st == FMM_OK && pl.outer_scaling) {
+      // C out of the scaled problem: exact powers of two per row and column
+      PhaseScope ps(kPhaseBeta, s);
+      e = launch_outer_rescale(C, m, n, ldc, job->sa.row_maxbits, job->sb.col_maxbits, +1, 1.0f, dev.sms, s);
+      if (e != cudaSuccess) st = cuda_fail(e, "outside-scaling pass (C)");
+    }
   }
   delete job;
   delete ka;

@@ -197,7 +197,20 @@ struct SumParams {
   // top-level coefficients c1[q] (already mapped through the transposed-source rule)
   int32_t chunk;
   int8_t c1[4];
+  // outside power-of-two scaling (or null): float bits of max |x| per source row / column;
+  // each element is multiplied by 2^-e of its row (row_maxbits) or column (col_maxbits)
+  const unsigned int* row_maxbits;
+  const unsigned int* col_maxbits;
 };
+
+// Exponent e of a row's or column's largest magnitude (float bits): max in [2^e, 2^(e+1)),
+// e = 0 for an all-zero (or non-finite) vector; subnormal maxima count as 2^-126.
+__host__ __device__ inline int outer_exp(unsigned int maxbits) {
+  if (maxbits == 0) return 0;
+  const int f = static_cast<int>((maxbits >> 23) & 0xffu);
+  if (f == 0xff) return 0;
+  return (f == 0 ? 1 : f) - 127;
+}
 
 // Shift s of a panel whose largest |sum| has float bits `maxbits`: the sums are stored as
 // sum * 2^-s, which puts the panel maximum in [2^14, 2^15) (FP16 normal range, no overflow);

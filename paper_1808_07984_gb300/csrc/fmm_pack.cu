@@ -142,6 +142,16 @@ __device__ __forceinline__ void load_group(const SumParams& p, const T* X, int64
     for (int e = 0; e < EPT; ++e)
       v[e] = (row_ok && gc + e < p.cols && l0 + e < p.hc) ? load_as_float<T>(X + gr * p.ldx + gc + e) : 0.f;
   }
+  if (p.row_maxbits && row_ok) {  // outside scaling: exact powers of two
+    const int ex = outer_exp(p.row_maxbits[gr]);
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) v[e] = ldexpf(v[e], -ex);
+  }
+  if (p.col_maxbits) {
+#pragma unroll
+    for (int e = 0; e < EPT; ++e)
+      if (gc + e < p.cols) v[e] = ldexpf(v[e], -outer_exp(p.col_maxbits[gc + e]));
+  }
 }
 
 template <typename T, int OUT16, int L, bool IS_B, bool TRANSQ, int TERMS, int EPT, int SCALE>
@@ -270,6 +280,65 @@ __global__ void __launch_bounds__(256) operand_sums_kernel(const __grid_constant
   }
 }
 
+// Outside scaling: float bits of max |x| of every row of X (rows x cols, leading dimension
+// ld), one block per row.
+template <typename T>
+__global__ void row_maxbits_kernel(const T* X, int64_t rows, int64_t cols, int64_t ld, unsigned int* out) {
+  __shared__ float red[8];
+  for (int64_t i = blockIdx.x; i < rows; i += gridDim.x) {
+    float mx = 0.f;
+    for (int64_t j = threadIdx.x; j < cols; j += blockDim.x) mx = fmaxf(mx, fabsf(load_as_float<T>(X + i * ld + j)));
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < static_cast<int>(blockDim.x >> 5); ++w) mx = fmaxf(mx, red[w]);
+      out[i] = __float_as_uint(mx);
+    }
+    __syncthreads();
+  }
+}
+
+// Float bits of max |x| of every column of X: thread per column over a chunk of rows,
+// combined by atomicMax (non-negative floats order like their bit patterns).
+template <typename T>
+__global__ void col_maxbits_kernel(const T* X, int64_t rows, int64_t cols, int64_t ld, int64_t rows_per_chunk,
+                                   unsigned int* out) {
+  const int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (j >= cols) return;
+  const int64_t r0 = blockIdx.y * rows_per_chunk, r1 = min(rows, r0 + rows_per_chunk);
+  float mx = 0.f;
+  for (int64_t i = r0; i < r1; ++i) mx = fmaxf(mx, fabsf(load_as_float<T>(X + i * ld + j)));
+  if (mx > 0.f) atomicMax(out + j, __float_as_uint(mx));
+}
+
+// C[i][j] *= 2^(sign * (e_row(i) + e_col(j))) (sign -1 scales beta * C into the scaled
+// problem before the products, +1 takes the result back out of it).
+// One row per blockIdx.y step; 4 consecutive columns per thread (vector access when the rows
+// are 16-byte aligned).
+__global__ void outer_rescale_kernel(float* C, int64_t m, int64_t n, int64_t ldc, const unsigned int* row_maxbits,
+                                     const unsigned int* col_maxbits, int sign, float beta, int vec4) {
+  for (int64_t i = blockIdx.y; i < m; i += gridDim.y) {
+    const int er = outer_exp(row_maxbits[i]);
+    float* row = C + i * ldc;
+    for (int64_t j = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) * 4; j < n;
+         j += static_cast<int64_t>(gridDim.x) * blockDim.x * 4) {
+      if (vec4 && j + 4 <= n) {
+        float4 v = *reinterpret_cast<float4*>(row + j);
+        const uint4 cb = *reinterpret_cast<const uint4*>(col_maxbits + j);
+        v.x = ldexpf(beta * v.x, sign * (er + outer_exp(cb.x)));
+        v.y = ldexpf(beta * v.y, sign * (er + outer_exp(cb.y)));
+        v.z = ldexpf(beta * v.z, sign * (er + outer_exp(cb.z)));
+        v.w = ldexpf(beta * v.w, sign * (er + outer_exp(cb.w)));
+        *reinterpret_cast<float4*>(row + j) = v;
+      } else {
+        for (int64_t jj = j; jj < min(n, j + 4); ++jj)
+          row[jj] = ldexpf(beta * row[jj], sign * (er + outer_exp(col_maxbits[jj])));
+      }
+    }
+  }
+}
+
 __global__ void beta_kernel(float* C, int64_t m, int64_t n, int64_t ldc, float beta) {
   const int64_t total = m * n;
   for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
@@ -355,6 +424,41 @@ cudaError_t launch_beta(float* C, int64_t m, int64_t n, int64_t ldc, float beta,
   if (beta == 0.f && ldc == n) return cudaMemsetAsync(C, 0, static_cast<size_t>(total) * sizeof(float), s);
   const int grid = static_cast<int>(std::min<int64_t>((total + 255) / 256, int64_t(num_sms) * 16));
   beta_kernel<<<grid, 256, 0, s>>>(C, m, n, ldc, beta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_outer_maxbits(const void* A, int64_t m, int64_t k, int64_t lda, const void* B, int64_t n,
+                                int64_t ldb, int in_type, unsigned* row_bits, unsigned* col_bits, int num_sms,
+                                cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(col_bits, 0, static_cast<size_t>(n) * 4, s);
+  if (e != cudaSuccess) return e;
+  const int rgrid = static_cast<int>(std::min<int64_t>(m, int64_t(num_sms) * 32));
+  const int64_t chunk = 256;
+  const dim3 cgrid(static_cast<unsigned>((n + 255) / 256), static_cast<unsigned>((k + chunk - 1) / chunk));
+  if (in_type == kInF32) {
+    row_maxbits_kernel<float><<<rgrid, 256, 0, s>>>(static_cast<const float*>(A), m, k, lda, row_bits);
+    col_maxbits_kernel<float><<<cgrid, 256, 0, s>>>(static_cast<const float*>(B), k, n, ldb, chunk, col_bits);
+  } else if (in_type == kInBF16) {
+    row_maxbits_kernel<__nv_bfloat16><<<rgrid, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(A), m, k, lda, row_bits);
+    col_maxbits_kernel<__nv_bfloat16><<<cgrid, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(B), k, n, ldb, chunk,
+                                                             col_bits);
+  } else {
+    row_maxbits_kernel<__half><<<rgrid, 256, 0, s>>>(static_cast<const __half*>(A), m, k, lda, row_bits);
+    col_maxbits_kernel<__half><<<cgrid, 256, 0, s>>>(static_cast<const __half*>(B), k, n, ldb, chunk, col_bits);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_outer_rescale(float* C, int64_t m, int64_t n, int64_t ldc, const unsigned* row_bits,
+                                 const unsigned* col_bits, int sign, float beta, int num_sms, cudaStream_t s) {
+  if (m == 0 || n == 0) return cudaSuccess;
+  // column bits start 256-byte aligned in the workspace; C rows need 16-byte alignment
+  const int vec4 = (reinterpret_cast<uintptr_t>(C) % 16 == 0 && ldc % 4 == 0 &&
+                    reinterpret_cast<uintptr_t>(col_bits) % 16 == 0) ? 1 : 0;
+  const int64_t col_threads = (n + 3) / 4;
+  const dim3 grid(static_cast<unsigned>(std::min<int64_t>((col_threads + 255) / 256, 64)),
+                  static_cast<unsigned>(std::min<int64_t>(m, 65535)));
+  outer_rescale_kernel<<<grid, 256, 0, s>>>(C, m, n, ldc, row_bits, col_bits, sign, beta, vec4);
   return cudaGetLastError();
 }
 

@@ -19,6 +19,13 @@ cudaError_t launch_operand_sums(const SumParams& p, int levels, bool is_b, bool 
 cudaError_t launch_beta(float* C, int64_t m, int64_t n, int64_t ldc, float beta, int num_sms,
                         cudaStream_t s);
 cudaError_t launch_debug_wait(unsigned* err, uint64_t timeout_ns, cudaStream_t s);
+// Outside power-of-two scaling: float bits of max |x| of the rows of A (m x k) and of the
+// columns of B (k x n); and C <- 2^(sign (e_row + e_col)) * beta * C.
+cudaError_t launch_outer_maxbits(const void* A, int64_t m, int64_t k, int64_t lda, const void* B, int64_t n,
+                                int64_t ldb, int in_type, unsigned* row_bits, unsigned* col_bits, int num_sms,
+                                cudaStream_t s);
+cudaError_t launch_outer_rescale(float* C, int64_t m, int64_t n, int64_t ldc, const unsigned* row_bits,
+                                 const unsigned* col_bits, int sign, float beta, int num_sms, cudaStream_t s);
 
 // Tensor-core kernel over packed operand sums.  tile_n in {128, 256}; terms in {1, 3};
 // bf16 selects BF16 (true) or FP16 (false) operands; pair selects the CTA-pair kernel

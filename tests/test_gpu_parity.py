@@ -61,7 +61,7 @@ def _to_device(X, ld_pad, dtype):
 def run(m, n, k, levels, variant="split3", dist="uniform", seed=0, alpha=1.0, beta=0.0,
         tile_n=0, pads=(0, 0, 0), c_fill=None, rows=None, schedule="auto", algo="auto", bk=0,
         cta_pair=None, round_tiles=0, pipeline=None, fringe="pad", basis="strassen",
-        deterministic=False):
+        deterministic=False, outer_scaling=False):
     A, B = synth.problem(m, n, k, seed, dist)
     in_dtype = {"bf16": torch.bfloat16, "f16": torch.float16}.get(variant, torch.float32)
     Ad = _to_device(A, pads[0], in_dtype)
@@ -76,7 +76,8 @@ def run(m, n, k, levels, variant="split3", dist="uniform", seed=0, alpha=1.0, be
             Cd.fill_(c_fill)
     fmm.gemm(Ad, Bd, Cd, alpha=alpha, beta=beta, levels=levels, variant=variant, tile_n=tile_n,
              schedule=schedule, algo=algo, bk=bk, cta_pair=cta_pair, round_tiles=round_tiles,
-             pipeline=pipeline, fringe=fringe, basis=basis, deterministic=deterministic)
+             pipeline=pipeline, fringe=fringe, basis=basis, deterministic=deterministic,
+             outer_scaling=outer_scaling)
     fmm.device_status()
     C = Cd.cpu().numpy().astype(np.float64)
     if variant in ("bf16", "f16"):
@@ -317,6 +318,51 @@ def test_deterministic_results_are_bitwise_reproducible(opts):
     m, n, k = 2000, 1800, 1536
     outs = [run(m, n, k, 2, "split3", seed=53, deterministic=True, pads=pads, **o)[0] for _ in range(3)]
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+@pytest.mark.parametrize("levels", [0, 1, 2])
+@pytest.mark.parametrize("m,n,k,pads", [(300, 520, 200, (0, 0, 0)), (129, 257, 65, (0, 0, 1)),
+                                        (1000, 1200, 300, (0, 0, 0))])
+def test_outer_scaling_bit_exact(m, n, k, pads, levels):
+    """Power-of-two row and column scaling around the product is exact on integers."""
+    C, C64, _, _ = run(m, n, k, levels, "split3", dist="int", seed=61 * m + k, pads=pads, outer_scaling=True)
+    np.testing.assert_array_equal(C, C64)
+
+
+def test_outer_scaling_with_beta_and_fp16():
+    m, n, k = 257, 301, 131
+    A, B = synth.problem(m, n, k, 63, "int")
+    C0 = synth.small_int((m, n), 64)
+    Cd = torch.from_numpy(C0).cuda()
+    fmm.gemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), Cd, alpha=2.0, beta=-3.0, levels=2,
+             outer_scaling=True)
+    fmm.device_status()
+    np.testing.assert_array_equal(Cd.cpu().numpy(), oracle.classical(A, B, C0, 2.0, -3.0))
+    C, C64, _, _ = run(300, 200, 150, 1, "f16", dist="int", seed=65, outer_scaling=True)
+    np.testing.assert_array_equal(C, C64)
+
+
+def _componentwise(C, C64, A, B):
+    """max_ij |C - C64| / (||A_i|| ||B_:j||): the error of each element against its own scale."""
+    ra = np.linalg.norm(A.astype(np.float64), axis=1)[:, None]
+    cb = np.linalg.norm(B.astype(np.float64), axis=0)[None, :]
+    return float(np.max(np.abs(C - C64) / (ra * cb)))
+
+
+def test_outer_scaling_keeps_badly_scaled_rows_accurate():
+    """Rows of A and columns of B spread over 10^-3 .. 10^3: without outside scaling the
+    two-level sums swamp small rows and columns; with it every element keeps FP32-level
+    accuracy against its own scale."""
+    m = n = k = 512
+    A, B = synth.problem(m, n, k, 67, "badly_scaled")
+    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    C64 = oracle.classical(A, B)
+    plain = fmm.gemm(Ad, Bd, levels=2).cpu().numpy().astype(np.float64)
+    scaled = fmm.gemm(Ad, Bd, levels=2, outer_scaling=True).cpu().numpy().astype(np.float64)
+    fmm.device_status()
+    e_plain, e_scaled = _componentwise(plain, C64, A, B), _componentwise(scaled, C64, A, B)
+    assert e_scaled <= 1e-5, e_scaled
+    assert e_scaled * 10 < e_plain, (e_scaled, e_plain)
 
 
 def test_cta_pair_rejected_with_bk32():
