@@ -115,3 +115,30 @@ def test_oracle_is_not_linked_by_the_library():
     so = fmm.lib_path()
     data = open(so, "rb").read()
     assert b"oracle_gemm" not in data
+
+
+def _call_ex(lib, levels=1, algo=0, **opt):
+    o = fmm._Options()
+    for key, v in opt.items():
+        setattr(o, key, v)
+    o.algo = algo
+    return lib.fmm_gemm_ex(16, 16, 16, 1.0, 0x10000, 16, 0x20000, 16, 0.0, 0x30000, 16, levels, 0,
+                           0x100000, 1 << 30, None, ctypes.byref(o))
+
+
+def test_option_errors_need_no_gpu(lib):
+    """Every option value outside its range, and every unsupported combination, is refused by
+    the host before any CUDA call (FMM_ERR_ARG = 1, FMM_ERR_UNSUPPORTED = 3)."""
+    assert _call_ex(lib, cta_pair=3) == 1
+    assert _call_ex(lib, schedule=5) == 1
+    assert _call_ex(lib, bk=48) == 1
+    assert _call_ex(lib, pipeline=3) == 1
+    assert _call_ex(lib, basis=2) == 1
+    assert _call_ex(lib, deterministic=2) == 1
+    assert _call_ex(lib, outer_scaling=2) == 1
+    assert _call_ex(lib, fringe=2) == 1
+    assert _call_ex(lib, cta_pair=2, bk=32) == 3            # pairs need 64-deep stages
+    assert _call_ex(lib, levels=2, basis=1) == 3            # Winograd: one level
+    assert _call_ex(lib, algo=2, outer_scaling=1) == 3      # fused: no outside scaling
+    assert _call_ex(lib, algo=3, levels=1) == 3             # hybrid: two levels
+    assert _call_ex(lib, algo=9) == 3
