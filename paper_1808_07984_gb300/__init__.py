@@ -239,7 +239,7 @@ def workspace_size_backward(m, n, k, levels=1, variant="split3") -> int:
 
 
 def gemm_backward(A, B, dC, levels: int = 1, variant="split3", need_dA=True, need_dB=True,
-                  workspace=None, stream=None, pipeline=None, basis="strassen"):
+                  workspace=None, stream=None, pipeline=None, basis="strassen", deterministic=False):
     """(dA, dB) = (dC @ B.T, A.T @ dC) as Strassen products through fmm_gemm_backward_ex.
 
     A (m x k) and B (k x n) have the variant's element type, dC (m x n) is float32; the
@@ -261,7 +261,7 @@ def gemm_backward(A, B, dC, levels: int = 1, variant="split3", need_dA=True, nee
     ws_need = workspace_size_backward(m, n, k, levels, v)
     if workspace is None and ws_need > 0:
         workspace = torch.empty(ws_need, dtype=torch.uint8, device=A.device)
-    o = _opts(pipeline=pipeline, basis=basis)
+    o = _opts(pipeline=pipeline, basis=basis, deterministic=deterministic)
     st = load().fmm_gemm_backward_ex(
         m, n, k, A.data_ptr(), max(A.stride(0), 1), B.data_ptr(), max(B.stride(0), 1),
         dC.data_ptr(), max(dC.stride(0), 1),
@@ -281,20 +281,21 @@ def _make_linear_fn():
         computed as Strassen products by the library (no autograd through torch ops)."""
 
         @staticmethod
-        def forward(ctx, A, B, levels=1, variant="split3"):
+        def forward(ctx, A, B, levels=1, variant="split3", deterministic=False):
             ctx.save_for_backward(A, B)
             ctx.levels = levels
             ctx.variant = variant
-            return gemm(A, B, levels=levels, variant=variant)
+            ctx.deterministic = deterministic
+            return gemm(A, B, levels=levels, variant=variant, deterministic=deterministic)
 
         @staticmethod
         def backward(ctx, dC):
             A, B = ctx.saved_tensors
             dA, dB = gemm_backward(A, B, dC.contiguous().float(), levels=ctx.levels,
                                    variant=ctx.variant, need_dA=ctx.needs_input_grad[0],
-                                   need_dB=ctx.needs_input_grad[1])
+                                   need_dB=ctx.needs_input_grad[1], deterministic=ctx.deterministic)
             # FP32 gradients; autograd casts them to the inputs' dtype where that differs
-            return dA, dB, None, None
+            return dA, dB, None, None, None
 
     return FmmLinearFn
 
@@ -302,12 +303,13 @@ def _make_linear_fn():
 _linear_fn = None
 
 
-def linear(A, B, levels: int = 1, variant="split3"):
-    """Differentiable C = A @ B (torch.autograd) backed by the Strassen library."""
+def linear(A, B, levels: int = 1, variant="split3", deterministic: bool = False):
+    """Differentiable C = A @ B (torch.autograd) backed by the Strassen library.
+    deterministic=True: forward and backward in the ownership mode (bitwise reproducible)."""
     global _linear_fn
     if _linear_fn is None:
         _linear_fn = _make_linear_fn()
-    return _linear_fn.apply(A, B, levels, variant)
+    return _linear_fn.apply(A, B, levels, variant, deterministic)
 
 
 def tune_table(classes=None):

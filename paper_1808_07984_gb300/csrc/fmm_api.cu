@@ -95,6 +95,16 @@ fmm_status device_info(DeviceInfo& out) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   if (dev < 0 || dev >= 64) return fail(FMM_ERR_CUDA, "device ordinal out of range");
+  // The tensor maps are encoded through the driver API, which needs the device's primary
+  // context current in this thread.  A thread that has made no runtime call yet (for example
+  // autograd's device thread running this library's backward first) does not have it.
+  thread_local bool ctx_current[64] = {};
+  if (!ctx_current[dev]) {
+    e = cudaSetDevice(dev);
+    if (e == cudaSuccess) e = cudaFree(nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "making the device's context current");
+    ctx_current[dev] = true;
+  }
   std::lock_guard<std::mutex> lk(g_mu);
   DeviceInfo& d = g_dev[dev];
   if (!d.init) {

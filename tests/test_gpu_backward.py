@@ -161,3 +161,39 @@ def test_linear_layer_shapes_sampled_rows():
     tol = _tol("bf16", 1, 4096) + 2.0 ** -8
     assert _err(gA, dA64, np.linalg.norm(dCn[ra].astype(np.float64)), np.linalg.norm(Bf)) <= tol
     assert _err(gB, dB64, np.linalg.norm(Af[:, rb]), np.linalg.norm(dCn.astype(np.float64))) <= tol
+
+
+@pytest.mark.parametrize("levels", [1, 2])
+def test_linear_gradcheck_64(levels):
+    """torch.autograd.gradcheck of the library-backed layer at 64^3 (config C3's check).  The
+    layer is bilinear, so the central differences are exact up to the FP32 rounding of the
+    forward products; tolerances are set from that rounding, not from a truncation error."""
+    g = torch.Generator(device="cpu").manual_seed(77 + levels)
+    A = torch.randn((64, 64), generator=g).cuda().requires_grad_(True)
+    B = torch.randn((64, 64), generator=g).cuda().requires_grad_(True)
+    # the ownership mode makes repeated backward calls bitwise identical (gradcheck's
+    # reentrancy check uses a zero tolerance)
+    assert torch.autograd.gradcheck(lambda a, b: fmm.linear(a, b, levels=levels, deterministic=True), (A, B),
+                                    eps=1e-2, atol=2e-3, rtol=2e-3, fast_mode=True)
+    fmm.device_status()
+
+
+def test_library_call_from_a_fresh_thread():
+    """A thread that has made no CUDA call yet (as autograd's device thread may be) can call
+    the library: it makes the device's context current itself."""
+    import threading
+    A, B = synth.problem(96, 80, 64, 81, "int")
+    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    out = {}
+
+    def work():
+        try:
+            out["C"] = fmm.gemm(Ad, Bd, levels=1).cpu().numpy()
+        except Exception as exc:  # noqa: BLE001 - reported below
+            out["err"] = exc
+
+    t = threading.Thread(target=work)
+    t.start()
+    t.join()
+    assert "err" not in out, out.get("err")
+    np.testing.assert_array_equal(out["C"], oracle.classical(A, B))
