@@ -622,3 +622,25 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     fmm.device_status()  # word was cleared
     C, C64, _, _ = run(64, 64, 64, 1, "split3", dist="int", seed=2)
     np.testing.assert_array_equal(C, C64)
+
+
+@pytest.mark.parametrize("levels", [1, 2])
+@pytest.mark.parametrize("m,n,k", [(20000, 8, 40), (8, 20000, 40), (40, 48, 40000)])
+def test_extreme_aspect_ratios_bit_exact(m, n, k, levels):
+    """Tall, wide and deep problems: most tiles of a block are fringe, or the k loop is long."""
+    C, C64, _, _ = run(m, n, k, levels, "split3", dist="int", seed=m + 3 * n + k)
+    np.testing.assert_array_equal(C, C64)
+
+
+@pytest.mark.parametrize("opts", [{"outer_scaling": True}, {"deterministic": True}, {"pipeline": True},
+                                  {"fringe": "peel"}])
+def test_k_zero_and_alpha_zero_with_options(opts):
+    Cd = torch.ones((33, 17), device="cuda")
+    fmm.gemm(torch.zeros((33, 0), device="cuda"), torch.zeros((0, 17), device="cuda"), Cd, alpha=1.0,
+             beta=2.5, levels=1, **opts)
+    fmm.device_status()
+    assert torch.all(Cd == 2.5)
+    A, B = synth.problem(33, 17, 9, 5, "int")
+    fmm.gemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), Cd, alpha=0.0, beta=2.0, levels=1, **opts)
+    fmm.device_status()
+    assert torch.all(Cd == 5.0)
