@@ -14,6 +14,8 @@ with A (m x k), B (k x n), C (m x n), row-major.  Two routes are provided:
   (Section 3.5).  The leaf product is a library matmul in FP64.  ``basis=
   "winograd"`` applies the Strassen-Winograd variant's seven products instead
   (Section 6 names it among the algorithms the primitive can carry).
+* ``table_matmul`` -- FP64 one-level product by any basis table <g_m, g_k, g_n; R>
+  (the <3,2,3> scheme of rank 15 below, or the 2x2 tables), same fringe rule.
 
 Supporting definitions: the 2x2 coefficient matrices U, V, W of Eq. (3), their
 Kronecker powers for multi-level Strassen (Section 3.4), the Brent-equation
@@ -121,6 +123,55 @@ WINOGRAD_W = np.array([
     [1, 0, 0, -1, 0, 1, 1],    # C2
     [1, 0, 0, 0, 1, 1, 1],     # C3
 ], dtype=np.int64)
+
+# ---------------------------------------------------------------------------
+# A <3,2,3> basis of rank 15 (Section 6 names bases other than <2,2,2> as the
+# next step for the primitive).  A one-level basis <g_m, g_k, g_n; R> splits A
+# into a g_m x g_k grid of blocks, B into g_k x g_n and C into g_m x g_n, and
+# forms R products
+#     M_r = (sum_a U[a, r] A_a)(sum_b V[b, r] B_b),   C_c += W[c, r] M_r,
+# blocks numbered row-major in their grid: a = i*g_k + l, b = l*g_n + j,
+# c = i*g_n + j.  This scheme needs 15 products where the classical one needs
+# 18 (Hopcroft and Kerr showed 15 is the least for <3,2,3>).  It was found for
+# this package by a random walk over rank-reducing rewrites of the classical
+# scheme modulo 2, then a choice of signs; its correctness rests on the Brent
+# equations, which the tests check exactly, not on that search.  At most three
+# C blocks per product (30 nonzeros in W), 32 in each of U and V.
+# ---------------------------------------------------------------------------
+B323_U = np.array([
+    # r: 0   1   2   3   4   5   6   7   8   9  10  11  12  13  14
+    [-1,  1,  1, -1,  0,  0,  0,  0,  0,  1,  0,  0,  0,  0,  0],   # A(0,0)
+    [0,   1,  1,  0, -1,  0,  0,  0,  0,  1,  1,  0,  0,  0,  1],   # A(0,1)
+    [0,   0,  0,  1, -1,  1,  0,  0,  0,  0,  0, -1, -1,  1,  0],   # A(1,0)
+    [0,   0,  0,  0,  0,  1,  0,  0, -1,  0, -1, -1, -1,  0,  0],   # A(1,1)
+    [1,  -1, -1,  0,  0,  0,  0, -1,  0,  0,  0,  0,  1,  0,  0],   # A(2,0)
+    [0,   0, -1,  0,  0, -1,  1,  0,  1,  0,  0,  0,  1,  0,  0],   # A(2,1)
+], dtype=np.int64)
+
+B323_V = np.array([
+    [1,   0,  0,  0,  0, -1,  0, -1,  1,  0,  0,  0,  1,  0,  0],   # B(0,0)
+    [0,   0,  0,  1,  0, -1,  0,  0,  1,  0,  0,  0,  1,  1,  0],   # B(0,1)
+    [-1,  1,  0, -1, -1,  0,  0,  0,  0, -1,  0,  0,  0,  0, -1],   # B(0,2)
+    [-1,  1,  1,  0,  0,  0, -1,  0, -1,  0,  0,  0,  0,  0,  0],   # B(1,0)
+    [0,   0,  0,  0,  1,  1,  0,  0, -1,  0, -1,  1,  0, -1,  0],   # B(1,1)
+    [1,  -1, -1,  0,  0,  0,  0,  0,  0,  0,  1,  0,  0,  0,  1],   # B(1,2)
+], dtype=np.int64)
+
+B323_W = np.array([
+    [-1,  1,  0,  0,  0,  0,  0,  1,  0,  0,  0,  0,  0,  0,  1],   # C(0,0)
+    [0,   0,  0, -1, -1,  0,  0,  0,  0, -1,  0,  0,  0,  1,  0],   # C(0,1)
+    [0,   0,  0,  0,  0,  0,  0,  0,  0, -1,  0,  0,  0,  0,  1],   # C(0,2)
+    [0,   0,  0,  0,  0, -1, -1,  0,  1,  0,  0,  0,  0, -1,  0],   # C(1,0)
+    [0,   0,  0,  0,  0,  0,  0,  0,  0,  0,  0, -1,  0,  1,  0],   # C(1,1)
+    [0,   0,  0,  0,  1,  0,  0,  0,  0,  0, -1, -1,  0,  0,  1],   # C(1,2)
+    [0,   0,  0,  0,  0,  0, -1,  1,  0,  0,  0,  0,  0,  0,  0],   # C(2,0)
+    [0,   0,  0,  0,  0, -1,  0, -1,  0,  0,  0, -1,  1,  0,  0],   # C(2,1)
+    [0,  -1,  1,  0,  0,  0, -1,  0,  0, -1,  0,  0,  0,  0,  0],   # C(2,2)
+], dtype=np.int64)
+
+# block grid (g_m, g_k, g_n) of each one-level basis
+BASIS_DIMS = {"strassen": (2, 2, 2), "winograd": (2, 2, 2), "b323": (3, 2, 3)}
+
 
 def basis_tables(basis: str = "strassen"):
     """(U, V, W) of a one-level basis, looked up when called."""
@@ -279,6 +330,67 @@ def strassen(A, B, C=None, alpha: float = 1.0, beta: float = 0.0,
         Np = g * block_size(n, levels, align)
         Kp = g * block_size(k, levels, align)
         prod = _strassen_rec(_pad(A, Mp, Kp), _pad(B, Kp, Np), levels, *basis_tables(basis))[:m, :n]
+    out = alpha * prod
+    if C is not None and beta != 0.0:
+        out = out + beta * np.asarray(C, dtype=np.float64)
+    return out
+
+
+def grid_block(d: int, g: int, align: int = 8) -> int:
+    """Block size of a dimension d split g ways: the fringe rule above with g in
+    place of 2**L (g = 1 keeps d itself)."""
+    if g == 1:
+        return d
+    h = -(-d // g)
+    return -(-h // align) * align
+
+
+def brent_residual_grid(dims, U, V, W) -> int:
+    """Sum of |residuals| of the Brent equations of a one-level <g_m, g_k, g_n>
+    basis: the coefficient of A_(i,l) B_(l',j) in C_(i',j') must be 1 when
+    l == l', i == i', j == j' and 0 otherwise.  0 exactly when all hold."""
+    gm, gk, gn = dims
+    total = 0
+    for i, l, l2, j, i2, j2 in itertools.product(range(gm), range(gk), range(gk), range(gn),
+                                                 range(gm), range(gn)):
+        want = 1 if (l == l2 and i == i2 and j == j2) else 0
+        got = int(np.sum(U[i * gk + l] * V[l2 * gn + j] * W[i2 * gn + j2]))
+        total += abs(got - want)
+    return total
+
+
+def table_matmul(A, B, C=None, alpha: float = 1.0, beta: float = 0.0,
+                 basis: str = "b323", align: int = 8) -> np.ndarray:
+    """FP64 one-level product by a basis table: C_out = alpha * A B + beta * C.
+
+    Each dimension is padded with zeros to g * grid_block(d, g); the R products
+    M_r = (sum_a U[a, r] A_a)(sum_b V[b, r] B_b) are formed with a library FP64
+    matmul and added into C block c with coefficient W[c, r]; the padding is
+    dropped.  beta == 0 or C None: C is not read."""
+    U, V, W = basis_tables(basis)
+    gm, gk, gn = BASIS_DIMS[basis]
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    m, k = A.shape
+    k2, n = B.shape
+    assert k == k2
+    if min(m, n, k) == 0:
+        prod = np.zeros((m, n))
+    else:
+        hm, hk, hn = grid_block(m, gm, align), grid_block(k, gk, align), grid_block(n, gn, align)
+        Ap = _pad(A, gm * hm, gk * hk)
+        Bp = _pad(B, gk * hk, gn * hn)
+        Ab = [Ap[i * hm:(i + 1) * hm, l * hk:(l + 1) * hk] for i in range(gm) for l in range(gk)]
+        Bb = [Bp[l * hk:(l + 1) * hk, j * hn:(j + 1) * hn] for l in range(gk) for j in range(gn)]
+        Cb = [np.zeros((hm, hn)) for _ in range(gm * gn)]
+        for r in range(U.shape[1]):
+            P = sum(U[a, r] * Ab[a] for a in range(gm * gk) if U[a, r])
+            Q = sum(V[b, r] * Bb[b] for b in range(gk * gn) if V[b, r])
+            M = P @ Q
+            for c in range(gm * gn):
+                if W[c, r]:
+                    Cb[c] += W[c, r] * M
+        prod = np.block([[Cb[i * gn + j] for j in range(gn)] for i in range(gm)])[:m, :n]
     out = alpha * prod
     if C is not None and beta != 0.0:
         out = out + beta * np.asarray(C, dtype=np.float64)

@@ -311,3 +311,96 @@ def test_winograd_exact_on_small_integers(levels, m, n, k):
     want = oracle.classical(A, B, C, alpha=2.0, beta=-3.0)
     got = oracle.strassen(A, B, C, alpha=2.0, beta=-3.0, levels=levels, basis="winograd")
     np.testing.assert_array_equal(got, want)
+
+
+# ------------------------------------------------ a <3,2,3> basis of rank 15 (Section 6)
+def _classical_table(gm, gk, gn):
+    """The classical scheme of a <gm, gk, gn> grid as a basis table: one product per
+    (i, l, j), A(i,l) times B(l,j) into C(i,j)."""
+    R = gm * gk * gn
+    U = np.zeros((gm * gk, R), np.int64)
+    V = np.zeros((gk * gn, R), np.int64)
+    W = np.zeros((gm * gn, R), np.int64)
+    for r, (i, l, j) in enumerate(itertools.product(range(gm), range(gk), range(gn))):
+        U[i * gk + l, r] = V[l * gn + j, r] = W[i * gn + j, r] = 1
+    return U, V, W
+
+
+def test_brent_grid_accepts_classical_schemes_and_rejects_misplaced_blocks():
+    for dims in [(3, 2, 3), (2, 3, 2), (1, 2, 3), (2, 2, 2)]:
+        U, V, W = _classical_table(*dims)
+        assert oracle.brent_residual_grid(dims, U, V, W) == 0
+        if dims[0] > 1:
+            # the C blocks of one row taken for another's: a transposed or shifted index
+            Wbad = np.roll(W, dims[2], axis=0)
+            assert oracle.brent_residual_grid(dims, U, V, Wbad) > 0
+
+
+def test_brent_grid_agrees_with_the_square_form_on_the_2x2_tables():
+    for basis in ("strassen", "winograd"):
+        assert oracle.brent_residual_grid((2, 2, 2), *oracle.BASES[basis]) == 0
+    U, V, W = (M.copy() for M in oracle.BASES["strassen"])
+    U[0, 0] = -U[0, 0]
+    assert oracle.brent_residual_grid((2, 2, 2), U, V, W) == oracle.brent_residual(1, U, V, W) > 0
+
+
+def test_b323_brent_equations_hold():
+    U, V, W = oracle.BASES["b323"]
+    assert U.shape == (6, 15) and V.shape == (6, 15) and W.shape == (9, 15)
+    assert oracle.brent_residual_grid((3, 2, 3), U, V, W) == 0
+
+
+def test_b323_brent_detects_every_single_coefficient_change():
+    U, V, W = (M.copy() for M in oracle.BASES["b323"])
+    for M in (U, V, W):
+        for idx in itertools.product(range(M.shape[0]), range(15)):
+            old = M[idx]
+            for new in {-1, 0, 1} - {old}:
+                M[idx] = new
+                assert oracle.brent_residual_grid((3, 2, 3), U, V, W) > 0
+            M[idx] = old
+
+
+def test_b323_shape_of_the_scheme():
+    U, V, W = oracle.BASES["b323"]
+    assert set(np.unique(np.concatenate([U.ravel(), V.ravel(), W.ravel()]))) <= {-1, 0, 1}
+    assert [int(np.count_nonzero(M)) for M in (U, V, W)] == [32, 32, 30]
+    assert int(np.count_nonzero(W, axis=0).max()) == 3   # at most three C blocks per product
+
+
+def test_grid_block_rule():
+    assert oracle.grid_block(16384, 3) == 5464
+    assert oracle.grid_block(16384, 2) == oracle.block_size(16384, 1) == 8192
+    assert oracle.grid_block(1, 3) == 8
+    assert oracle.grid_block(30001, 3, align=1) == 10001
+    assert oracle.grid_block(77, 1) == 77
+
+
+@pytest.mark.parametrize("m,n,k", [(18, 18, 12), (7, 11, 5), (64, 40, 33), (3, 200, 2), (100, 1, 9)])
+@pytest.mark.parametrize("align", [1, 8])
+def test_b323_exact_on_small_integers(m, n, k, align):
+    A, B = synth.problem(m, n, k, seed=11 * m + n, dist="int")
+    C = synth.small_int((m, n), 5)
+    want = oracle.classical(A, B, C, alpha=2.0, beta=-3.0)
+    got = oracle.table_matmul(A, B, C, alpha=2.0, beta=-3.0, basis="b323", align=align)
+    np.testing.assert_array_equal(got, want)
+
+
+def test_table_matmul_with_the_strassen_table_is_one_level_strassen():
+    A, B = synth.problem(40, 24, 36, seed=5, dist="uniform")
+    np.testing.assert_array_equal(oracle.table_matmul(A, B, basis="strassen"),
+                                  oracle.strassen(A, B, levels=1))
+
+
+def test_table_matmul_empty_and_beta_only():
+    A, B = np.zeros((6, 0)), np.zeros((0, 9))
+    C = synth.small_int((6, 9), 5)
+    np.testing.assert_array_equal(oracle.table_matmul(A, B, C, beta=2.0), 2.0 * C)
+    assert oracle.table_matmul(np.zeros((0, 4)), np.zeros((4, 3))).shape == (0, 3)
+
+
+def test_b323_float_agrees_with_classical_within_fp64_rounding():
+    A, B = synth.problem(96, 90, 64, seed=9, dist="uniform")
+    got = oracle.table_matmul(A, B, basis="b323")
+    want = oracle.classical(A, B)
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(A).max() * np.abs(B).max() * 64
