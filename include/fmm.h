@@ -117,7 +117,12 @@ typedef struct fmm_options {
                         The first pipelined call on a device creates that stream: make it
                         before any stream capture begins. */
     int basis;       /* 0 = Strassen (Eq. 3); 1 = the Strassen-Winograd variant written per
-                        product (14 nonzeros in each of U, V, W; levels <= 1, packed or fused) */
+                        product (14 nonzeros in each of U, V, W; levels <= 1, packed or fused);
+                        2 = a <3,2,3> basis of rank 15 (levels <= 1, packed; A split into
+                        3 x 2 blocks, B into 2 x 3, C into 3 x 3; 15 products instead of the
+                        classical 18, so 5/6 of the classical MMA work against Strassen's 7/8;
+                        no pipelining).  Bases other than 0 form their operand sums in one
+                        table-driven pass per operand. */
     int deterministic; /* 1 = ownership mode: each output tile position belongs to one CTA
                           (pair), which applies the C updates of all 7^L products in a fixed
                           order, each item's after the previous item's have completed; results
@@ -196,6 +201,10 @@ fmm_status fmm_gemm_backward_ex(int64_t m, int64_t n, int64_t k,
                                 void* workspace, size_t ws_bytes, void* stream,
                                 const fmm_options* opt);
 size_t fmm_workspace_size_backward(int64_t m, int64_t n, int64_t k, int levels, int variant);
+/* Workspace of fmm_gemm_backward_ex with these options (the basis changes the block sizes);
+ * (size_t)-1 for an unsupported combination. */
+size_t fmm_workspace_size_backward_ex(int64_t m, int64_t n, int64_t k, int levels, int variant,
+                                      const fmm_options* opt);
 
 /* ------------------------------------------------------------------ batching
  * Many independent, unevenly sized products C_p = alpha_p A_p B_p + beta_p C_p in one
@@ -281,8 +290,17 @@ fmm_status fmm_debug_wait_timeout(void* stream);
  * must hold 4^L * 7^L entries.  Returns 7^L, or -1 on a bad argument.
  * Source: Section 3, Eq. (3), and its Kronecker power for Section 3.4. */
 int fmm_product_table(int levels, int8_t* U, int8_t* V, int8_t* W);
-/* As fmm_product_table for a basis (fmm_options.basis: 0 Strassen, 1 Strassen-Winograd). */
+/* As fmm_product_table for a basis (fmm_options.basis: 0 Strassen, 1 Strassen-Winograd,
+ * 2 the <3,2,3> basis of rank 15).  With the basis's block grid (g_m, g_k, g_n) and its R
+ * products (fmm_basis_shape): U[(i * g_k + l) * R + r] is the coefficient of A block (i, l)
+ * in product r, V[(l * g_n + j) * R + r] that of B block (l, j), W[(i * g_n + j) * R + r]
+ * that of product r in C block (i, j); U holds g_m g_k R entries, V g_k g_n R, W g_m g_n R.
+ * Returns R, or -1 for a bad argument or a basis and level count that are not built. */
 int fmm_product_table_ex(int levels, int basis, int8_t* U, int8_t* V, int8_t* W);
+/* Block grid and product count of `levels` levels of a basis: dims[0..3] = g_m, g_k, g_n,
+ * R (levels 0: 1, 1, 1, 1; Strassen and Strassen-Winograd: 2^L, 2^L, 2^L, 7^L; basis 2 at
+ * one level: 3, 2, 3, 15).  Returns 0, or -1 for a combination that is not built. */
+int fmm_basis_shape(int levels, int basis, int* dims);
 
 /* Phase timing.  While enabled, each launch of a phase -- 0: beta pass,
  * 1: operand-sum passes, 2: tensor-core kernel -- is bracketed by two CUDA

@@ -82,6 +82,8 @@ def load() -> ctypes.CDLL:
     L.fmm_gemm_backward_ex.argtypes = L.fmm_gemm_backward.argtypes + [ctypes.POINTER(_Options)]
     L.fmm_workspace_size_backward.restype = sz
     L.fmm_workspace_size_backward.argtypes = [i64, i64, i64, i32, i32]
+    L.fmm_workspace_size_backward_ex.restype = sz
+    L.fmm_workspace_size_backward_ex.argtypes = [i64, i64, i64, i32, i32, ctypes.POINTER(_Options)]
     L.fmm_tune_default.restype = None
     L.fmm_tune_default.argtypes = [ctypes.POINTER(TuneTable)]
     L.fmm_tune_measure.restype = i32
@@ -114,6 +116,8 @@ def load() -> ctypes.CDLL:
     L.fmm_product_table.argtypes = [i32, vp, vp, vp]
     L.fmm_product_table_ex.restype = i32
     L.fmm_product_table_ex.argtypes = [i32, i32, vp, vp, vp]
+    L.fmm_basis_shape.restype = i32
+    L.fmm_basis_shape.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_int)]
     L.fmm_profile_enable.restype = i32
     L.fmm_profile_enable.argtypes = [i32]
     L.fmm_profile_read.restype = i32
@@ -133,7 +137,7 @@ SCHEDULES = {"auto": 0, "product": 1, "rounds": 2}
 
 
 FRINGES = {"pad": 0, "peel": 1}
-BASES = {"strassen": 0, "winograd": 1}
+BASES = {"strassen": 0, "winograd": 1, "b323": 2}
 
 
 def _opts(algo="auto", tile_n=0, num_ctas=0, schedule="auto", bk=0, cta_pair=None, round_tiles=0,
@@ -193,7 +197,8 @@ def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
     ``pipeline``: None = automatic, True / False = overlap the operand-sum passes with the
     tensor-core kernel one top-level product at a time, or not.  ``fringe``: "pad" (zero
     padding of the blocks) or "peel" (Strassen on the evenly splitting core plus classical
-    strip products).  ``basis``: "strassen" or "winograd" (one level).  ``deterministic``:
+    strip products).  ``basis``: "strassen", "winograd" (one level) or "b323"
+    (the <3,2,3> basis of rank 15, one level, packed algorithm).  ``deterministic``:
     ownership mode, bitwise reproducible results.  ``outer_scaling``: exact power-of-two
     scaling of the rows of A and columns of B around the product (badly scaled inputs).
     """
@@ -258,10 +263,12 @@ def gemm_backward(A, B, dC, levels: int = 1, variant="split3", need_dA=True, nee
         raise FmmError(1, "dC must be a float32 CUDA tensor with contiguous rows")
     dA = torch.empty((m, k), dtype=torch.float32, device=A.device) if need_dA else None
     dB = torch.empty((k, n), dtype=torch.float32, device=A.device) if need_dB else None
-    ws_need = workspace_size_backward(m, n, k, levels, v)
+    o = _opts(pipeline=pipeline, basis=basis, deterministic=deterministic)
+    ws_need = load().fmm_workspace_size_backward_ex(m, n, k, levels, v, ctypes.byref(o))
+    if ws_need == ctypes.c_size_t(-1).value:
+        raise FmmError(3, "unsupported combination")
     if workspace is None and ws_need > 0:
         workspace = torch.empty(ws_need, dtype=torch.uint8, device=A.device)
-    o = _opts(pipeline=pipeline, basis=basis, deterministic=deterministic)
     st = load().fmm_gemm_backward_ex(
         m, n, k, A.data_ptr(), max(A.stride(0), 1), B.data_ptr(), max(B.stride(0), 1),
         dC.data_ptr(), max(dC.stride(0), 1),
@@ -477,15 +484,25 @@ def profile_read():
     return {p: (float(ms[i]), int(n[i])) for i, p in enumerate(PHASES)}
 
 
+def basis_shape(levels: int, basis="strassen"):
+    """(g_m, g_k, g_n, R): block grid and product count of ``levels`` levels of a basis."""
+    dims = (ctypes.c_int * 4)()
+    if load().fmm_basis_shape(levels, BASES[basis] if isinstance(basis, str) else int(basis), dims) != 0:
+        raise FmmError(3, "basis and levels not built")
+    return tuple(int(x) for x in dims)
+
+
 def product_table(levels: int, basis="strassen"):
-    """(U, V, W) int8 arrays of shape (4**L, 7**L) as the kernels use them; row
-    index bi * 2**L + bj."""
+    """(U, V, W) int8 arrays as the kernels use them: U of shape (g_m g_k, R) with row
+    i * g_k + l for A block (i, l), V (g_k g_n, R) with row l * g_n + j, W (g_m g_n, R) with
+    row i * g_n + j (for the 2x2 bases: (4**L, 7**L), row bi * 2**L + bj)."""
     import numpy as np
-    R, Q = 7 ** levels, 4 ** levels
-    U = np.zeros(Q * R, dtype=np.int8)
-    V = np.zeros(Q * R, dtype=np.int8)
-    W = np.zeros(Q * R, dtype=np.int8)
-    r = load().fmm_product_table_ex(levels, BASES[basis], U.ctypes.data, V.ctypes.data, W.ctypes.data)
+    gm, gk, gn, R = basis_shape(levels, basis)
+    U = np.zeros(gm * gk * R, dtype=np.int8)
+    V = np.zeros(gk * gn * R, dtype=np.int8)
+    W = np.zeros(gm * gn * R, dtype=np.int8)
+    b = BASES[basis] if isinstance(basis, str) else int(basis)
+    r = load().fmm_product_table_ex(levels, b, U.ctypes.data, V.ctypes.data, W.ctypes.data)
     if r != R:
         raise FmmError(1, "bad levels")
-    return U.reshape(Q, R), V.reshape(Q, R), W.reshape(Q, R)
+    return U.reshape(gm * gk, R), V.reshape(gk * gn, R), W.reshape(gm * gn, R)

@@ -14,6 +14,7 @@
 
 #include "fmm.h"
 #include "fmm_kernels.cuh"
+#include "fmm_bases.h"
 #include "launch.h"
 #include "fmm_fused.cuh"
 
@@ -151,6 +152,19 @@ int ipow(int b, int e) {
 // Multi-level products (Section 3.4): product (r_1..r_L) takes block (q_1..q_L) -- block q_L
 // of ... of quadrant q_1 -- with coefficient prod_i X[r_i][q_i] (the Kronecker power).
 std::vector<Product> make_products(int L, int basis = kBasisStrassen) {
+  if (basis == kBasis323 && L == 1) {
+    // a basis table: A blocks a = i*g_k + l, B blocks l*g_n + j, C blocks i*g_n + j
+    std::vector<Product> out(15);
+    for (int r = 0; r < 15; ++r) {
+      for (int a = 0; a < 6; ++a)
+        if (kB323U[a][r]) out[r].a.push_back({a, kB323U[a][r]});
+      for (int b = 0; b < 6; ++b)
+        if (kB323V[b][r]) out[r].b.push_back({b, kB323V[b][r]});
+      for (int c = 0; c < 9; ++c)
+        if (kB323W[c][r]) out[r].c.push_back({c, kB323W[c][r]});
+    }
+    return out;
+  }
   const int R = ipow(7, L), Q = ipow(4, L), g = 1 << L;
   std::vector<Product> out(R);
   for (int r = 0; r < R; ++r) {
@@ -176,6 +190,36 @@ std::vector<Product> make_products(int L, int basis = kBasisStrassen) {
   return out;
 }
 
+// Block grid (g_m, g_k, g_n) and product count R of `levels` levels of a basis; false for a
+// combination that is not built.
+struct BasisShape {
+  int gm, gk, gn, R;
+};
+bool basis_shape(int levels, int basis, BasisShape& out) {
+  if (levels < 0 || levels > 2) return false;
+  if (levels == 0) {
+    out = {1, 1, 1, 1};
+    return true;
+  }
+  if (basis == kBasisStrassen || basis == kBasisWinograd) {
+    const int g = 1 << levels;
+    out = {g, g, g, ipow(7, levels)};
+    return true;
+  }
+  if (basis == kBasis323 && levels == 1) {
+    out = {3, 2, 3, 15};
+    return true;
+  }
+  return false;
+}
+
+// Block size of a dimension d split g ways (Section 3.5 padding, blocks rounded up to 8).
+int64_t grid_block(int64_t d, int g) {
+  if (g == 1) return d;
+  const int64_t h = (d + g - 1) / g;
+  return (h + 7) / 8 * 8;
+}
+
 int64_t block_size(int64_t d, int L) {
   if (L == 0) return d;
   const int64_t g = int64_t(1) << L;
@@ -195,7 +239,8 @@ struct Plan {
   int bk = 64;  // k-elements per pipeline stage of the packed kernel (64, or 32 for split3)
   bool pair = false;  // packed kernel in CTA pairs: 256-row tiles shared by two CTAs
   int pipeline_mode = 0;  // fmm_options.pipeline: 0 automatic, 1 off, 2 on
-  int basis = kBasisStrassen;  // one-level coefficient tables (Strassen, or Strassen-Winograd)
+  int basis = kBasisStrassen;  // coefficient tables (Strassen, Strassen-Winograd or <3,2,3>)
+  int gm = 1, gk = 1, gn = 1;  // block grid of A (gm x gk), B (gk x gn) and C (gm x gn)
   bool deterministic = false;  // ownership mode (fixed order of the C updates)
   bool outer_scaling = false;  // power-of-two row (A) / column (B) scaling around the product
   size_t outer_off = 0;        // workspace offset of the row and column maxima
@@ -217,7 +262,6 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
   if (m < 0 || n < 0 || k < 0) return fail(FMM_ERR_ARG, "negative dimension");
   if (levels < 0 || levels > 2) return fail(FMM_ERR_UNSUPPORTED, "levels must be 0, 1 or 2");
   pl.L = levels;
-  pl.R = ipow(7, levels);
   pl.a_mn = a_mn;
   pl.b_mn = b_mn;
   switch (variant) {
@@ -241,9 +285,26 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
   pl.tile_n = (opt && opt->tile_n) ? opt->tile_n : 0;
   const int sched = opt ? opt->schedule : 0;
   if (sched < 0 || sched > 2) return fail(FMM_ERR_ARG, "schedule must be 0, 1 or 2");
-  pl.hm = block_size(m, levels);
-  pl.hn = block_size(n, levels);
-  pl.hk = block_size(k, levels);
+  const int basis = opt ? opt->basis : 0;
+  if (basis < kBasisStrassen || basis > kBasis323) return fail(FMM_ERR_ARG, "basis must be 0, 1 or 2");
+  if (basis == kBasisWinograd && (levels > 1 || pl.algo == FMM_ALGO_HYBRID))
+    return fail(FMM_ERR_UNSUPPORTED, "the Winograd basis is built for one level (packed or fused)");
+  if (basis == kBasis323 && levels > 1)
+    return fail(FMM_ERR_UNSUPPORTED, "the <3,2,3> basis is built for one level");
+  if (basis == kBasis323 && levels == 1 && on_chip)
+    return fail(FMM_ERR_UNSUPPORTED, "the <3,2,3> basis is built for the packed algorithm");
+  if (basis == kBasis323 && levels == 1 && opt && opt->pipeline == 2)
+    return fail(FMM_ERR_UNSUPPORTED, "the <3,2,3> basis forms its sums in one pass (no pipelining)");
+  pl.basis = levels == 0 ? kBasisStrassen : basis;
+  BasisShape shape;
+  if (!basis_shape(levels, pl.basis, shape)) return fail(FMM_ERR_UNSUPPORTED, "basis and levels not built");
+  pl.gm = shape.gm;
+  pl.gk = shape.gk;
+  pl.gn = shape.gn;
+  pl.R = shape.R;
+  pl.hm = grid_block(m, pl.gm);
+  pl.hn = grid_block(n, pl.gn);
+  pl.hk = grid_block(k, pl.gk);
   // automatic choice (measured on GB300): tile rounds, which keep the destination blocks of
   // a round in L2
   pl.schedule = sched == 1 ? kSchedProductMajor : kSchedTileRounds;
@@ -267,11 +328,6 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
     return fail(FMM_ERR_UNSUPPORTED, "single-CTA tiles are built for the forward product only");
   const int pipe = opt ? opt->pipeline : 0;
   if (pipe < 0 || pipe > 2) return fail(FMM_ERR_ARG, "pipeline must be 0, 1 or 2");
-  const int basis = opt ? opt->basis : 0;
-  if (basis != kBasisStrassen && basis != kBasisWinograd) return fail(FMM_ERR_ARG, "basis must be 0 or 1");
-  if (basis == kBasisWinograd && (levels > 1 || pl.algo == FMM_ALGO_HYBRID))
-    return fail(FMM_ERR_UNSUPPORTED, "the Winograd basis is built for one level (packed or fused)");
-  pl.basis = levels == 0 ? kBasisStrassen : basis;
   const int det = opt ? opt->deterministic : 0;
   if (det < 0 || det > 1) return fail(FMM_ERR_ARG, "deterministic must be 0 or 1");
   pl.deterministic = det == 1;
@@ -370,7 +426,7 @@ constexpr int64_t kRoundL2Bytes = int64_t(32) << 20;
 fmm_status fill_common(CommonParams& c, const Plan& pl, const std::vector<Product>& prods,
                        const std::vector<int>& live, int64_t m, int64_t n, float alpha, float* C,
                        int64_t ldc, const DeviceInfo& dev, const fmm_options* opt, int& grid) {
-  const int g = 1 << pl.L;
+  const int gn = pl.gn, nblocks = pl.gm * pl.gn;  // C blocks c = bi * gn + bj
   c.C = C;
   c.ldc = ldc;
   c.alpha = alpha;
@@ -390,7 +446,7 @@ fmm_status fill_common(CommonParams& c, const Plan& pl, const std::vector<Produc
   for (size_t i = 0; i < live.size(); ++i) {
     int cnt = 0;
     for (const Term& t : prods[live[i]].c) {
-      const int br = t.block / g, bc = t.block % g;
+      const int br = t.block / gn, bc = t.block % gn;
       const int64_t rows = block_extent(m, pl.hm, br), cols = block_extent(n, pl.hn, bc);
       if (rows == 0 || cols == 0) continue;
       DestEntry& de = c.prod[i].d[cnt++];
@@ -404,15 +460,15 @@ fmm_status fill_common(CommonParams& c, const Plan& pl, const std::vector<Produc
   }
   if (c.c_tma) {
     // one FP32 map per non-empty destination block, clipped to the block's extent in C
-    for (int b = 0; b < g * g; ++b) {
-      const int64_t rows = block_extent(m, pl.hm, b / g), cols = block_extent(n, pl.hn, b % g);
+    for (int b = 0; b < nblocks; ++b) {
+      const int64_t rows = block_extent(m, pl.hm, b / gn), cols = block_extent(n, pl.hn, b % gn);
       if (rows == 0 || cols == 0) continue;
       const cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
       const cuuint64_t strides[1] = {static_cast<cuuint64_t>(ldc * 4)};
       const cuuint32_t box[2] = {32, 32};
       const cuuint32_t estr[2] = {1, 1};
       CUresult cr = g_encode(&c.tmC[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
-                             C + ((b / g) * pl.hm * ldc + (b % g) * pl.hn), dims, strides, box, estr,
+                             C + ((b / gn) * pl.hm * ldc + (b % gn) * pl.hn), dims, strides, box, estr,
                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       if (cr != CUDA_SUCCESS)
@@ -426,7 +482,7 @@ fmm_status fill_common(CommonParams& c, const Plan& pl, const std::vector<Produc
     grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(grid, items)));
   // Tile rounds.  When an item moves at least half as many C bytes (read and write of each
   // destination tile) as operand bytes, keep the C blocks of a round (every destination block
-  // of its tile positions: 4^L tiles each) within kRoundL2Bytes; otherwise one tile per worker,
+  // of its tile positions: one tile in each of the g_m x g_n blocks) within kRoundL2Bytes; otherwise one tile per worker,
   // which shares operand panels between the most concurrent items.  Element-wise reductions
   // (C rows not 16-byte aligned) keep one tile per worker: small rounds make concurrent items
   // add into the same C elements, and those atomics serialise.  Measured on GB300.
@@ -435,7 +491,7 @@ fmm_status fill_common(CommonParams& c, const Plan& pl, const std::vector<Produc
   for (size_t i = 0; i < live.size(); ++i) dests += c.prod[i].count;
   const double c_bytes = live.empty() ? 0.0 : 8.0 * row_tile * pl.tile_n * dests / live.size();
   const double op_bytes = 2.0 * (row_tile + pl.tile_n) * pl.hk * (pl.terms == 3 ? 2 : 1);
-  const int64_t footprint = static_cast<int64_t>(g) * g * row_tile * pl.tile_n * 4;
+  const int64_t footprint = static_cast<int64_t>(nblocks) * row_tile * pl.tile_n * 4;
   int64_t rt = workers;
   if (opt && opt->round_tiles > 0)
     rt = opt->round_tiles;
@@ -685,6 +741,7 @@ struct PackedJob {
   float* C = nullptr;
   int a_type = kInF32, b_type = kInF32;
   SumParams sa, sb;
+  TableSumParams ta, tb;  // bases other than Strassen's: sums formed from the product table
   unsigned* maxbits = nullptr;
   int grid = 0;
   bool has_work = false;  // k > 0 and alpha != 0
@@ -704,6 +761,8 @@ fmm_status prepare_packed(const Plan& pl, int64_t m, int64_t n, int64_t k, float
   job.has_work = m > 0 && n > 0 && k > 0 && alpha != 0.0f;
   std::memset(&job.sa, 0, sizeof job.sa);
   std::memset(&job.sb, 0, sizeof job.sb);
+  std::memset(&job.ta, 0, sizeof job.ta);
+  std::memset(&job.tb, 0, sizeof job.tb);
   std::memset(&job.params, 0, sizeof job.params);
   if (!job.has_work) return FMM_OK;
   const int64_t a_rows = pl.a_mn ? k : m, a_cols = pl.a_mn ? m : k;
@@ -755,6 +814,29 @@ fmm_status prepare_packed(const Plan& pl, int64_t m, int64_t n, int64_t k, float
     sb.npanels = static_cast<int32_t>(pl.panels_b);
     sb.panel_w = pl.tile_n;
     sb.scale_rows = 0;
+  }
+  if (pl.basis != kBasisStrassen) {
+    // stored block s of the source (row-major in its grid) is operand block (bi, bj), or
+    // (bj, bi) when the source holds the operand transposed; its coefficient in product r
+    // is that block's entry of U (A) or V (B)
+    const std::vector<Product> tprods = make_products(pl.L, pl.basis);
+    auto fill_table = [&](TableSumParams& tp, const SumParams& sp, bool is_b, bool transq) -> bool {
+      tp.p = sp;
+      const int orows = is_b ? pl.gk : pl.gm, ocols = is_b ? pl.gn : pl.gk;
+      tp.grid_r = transq ? ocols : orows;
+      tp.grid_c = transq ? orows : ocols;
+      tp.nprod = pl.R;
+      if (tp.grid_r * tp.grid_c > kMaxTableBlocks || pl.R > kMaxTableRank) return false;
+      for (int r = 0; r < pl.R; ++r)
+        for (const Term& t : is_b ? tprods[r].b : tprods[r].a) {
+          const int oi = t.block / ocols, oj = t.block % ocols;
+          const int sblk = transq ? oj * tp.grid_c + oi : oi * tp.grid_c + oj;
+          tp.coef[sblk][r] = static_cast<int8_t>(t.sign);
+        }
+      return true;
+    };
+    if (!fill_table(job.ta, sa, false, pl.a_mn) || !fill_table(job.tb, sb, true, !pl.b_mn))
+      return fail(FMM_ERR_UNSUPPORTED, "basis table too large for the table pass");
   }
 
   PackedParams* pp = &job.params;
@@ -953,12 +1035,19 @@ fmm_status launch_passes(const PackedJob& job, const DeviceInfo& dev, cudaStream
     if (e != cudaSuccess) return cuda_fail(e, "clearing the panel maxima");
   }
   if (pl.basis != kBasisStrassen) {
-    // the sum kernel's full pass carries Strassen's tables; other bases form each one-level
-    // product in its own pass from run-time coefficients
-    for (int c = 0; c < 7; ++c) {
-      fmm_status st = launch_chunk_sums(job, c, dev, s);
-      if (st != FMM_OK) return st;
+    // the sum kernel's full pass carries Strassen's tables; other bases form every product's
+    // sums in one pass per operand from the product table
+    cudaError_t e;
+    {
+      PhaseScope ps(kPhasePack, s);
+      e = launch_table_sums(job.ta, job.a_type, pl.bf16 ? 0 : 1, dev.sms, s);
     }
+    if (e != cudaSuccess) return cuda_fail(e, "operand-sum pass (A, basis table)");
+    {
+      PhaseScope ps(kPhasePack, s);
+      e = launch_table_sums(job.tb, job.b_type, pl.bf16 ? 0 : 1, dev.sms, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "operand-sum pass (B, basis table)");
     return FMM_OK;
   }
   cudaError_t e;
@@ -1073,9 +1162,12 @@ struct PeelPart {
   bool accumulate;     // beta = 1 (adds to what an earlier part wrote)
 };
 
-std::vector<PeelPart> peel_parts(int64_t m, int64_t n, int64_t k, int levels) {
-  const int64_t q = int64_t(8) << levels;
-  const int64_t me = m / q * q, ne = n / q * q, ke = k / q * q;
+std::vector<PeelPart> peel_parts(int64_t m, int64_t n, int64_t k, int levels, const fmm_options* opt) {
+  // core sizes: multiples of 8 times the basis's block grid in each dimension
+  BasisShape sh;
+  if (!basis_shape(levels, opt ? opt->basis : 0, sh)) sh = {1 << levels, 1 << levels, 1 << levels, 0};
+  const int64_t qm = 8 * sh.gm, qn = 8 * sh.gn, qk = 8 * sh.gk;
+  const int64_t me = m / qm * qm, ne = n / qn * qn, ke = k / qk * qk;
   std::vector<PeelPart> parts;
   if (me == 0 || ne == 0 || ke == 0) {  // no core: one classical product
     parts.push_back({0, 0, 0, m, n, k, 0, false});
@@ -1106,7 +1198,7 @@ size_t fmm_workspace_size_ex(int64_t m, int64_t n, int64_t k, int levels, int va
   if (opt && opt->fringe == 1 && levels >= 1) {
     const fmm_options o = no_fringe(opt);
     size_t ws = 0;
-    for (const PeelPart& pp : peel_parts(m, n, k, levels)) {
+    for (const PeelPart& pp : peel_parts(m, n, k, levels, &o)) {
       Plan pl;
       if (make_plan(pp.m, pp.n, pp.k, pp.levels, variant, &o, false, true, pl) != FMM_OK)
         return static_cast<size_t>(-1);
@@ -1133,7 +1225,7 @@ fmm_status fmm_gemm_ex(int64_t m, int64_t n, int64_t k, float alpha, const void*
     // peeled: every part is an ordinary call on sub-views, in order on `stream` (they share
     // the workspace); the parts cover C exactly once, and the k strip adds into the core
     const fmm_options o = no_fringe(opt);
-    const std::vector<PeelPart> parts = peel_parts(m, n, k, levels);
+    const std::vector<PeelPart> parts = peel_parts(m, n, k, levels, &o);
     Plan first;
     fmm_status st = make_plan(m, n, k, levels, variant, &o, false, true, first);
     if (st != FMM_OK) return st;
@@ -1165,12 +1257,17 @@ fmm_status fmm_gemm(int64_t m, int64_t n, int64_t k, float alpha, const void* A,
                      ws_bytes, stream, nullptr);
 }
 
-size_t fmm_workspace_size_backward(int64_t m, int64_t n, int64_t k, int levels, int variant) {
+size_t fmm_workspace_size_backward_ex(int64_t m, int64_t n, int64_t k, int levels, int variant,
+                                      const fmm_options* opt) {
   Plan pa, pb;
-  if (make_plan(m, k, n, levels, variant, nullptr, false, false, pa) != FMM_OK ||
-      make_plan(k, n, m, levels, variant, nullptr, true, true, pb) != FMM_OK)
+  if (make_plan(m, k, n, levels, variant, opt, false, false, pa) != FMM_OK ||
+      make_plan(k, n, m, levels, variant, opt, true, true, pb) != FMM_OK)
     return static_cast<size_t>(-1);
   return std::max(pa.ws, pb.ws);
+}
+
+size_t fmm_workspace_size_backward(int64_t m, int64_t n, int64_t k, int levels, int variant) {
+  return fmm_workspace_size_backward_ex(m, n, k, levels, variant, nullptr);
 }
 
 fmm_status fmm_gemm_backward_ex(int64_t m, int64_t n, int64_t k, const void* A, int64_t lda,
@@ -1471,13 +1568,23 @@ int fmm_product_table(int levels, int8_t* U, int8_t* V, int8_t* W) {
   return fmm_product_table_ex(levels, kBasisStrassen, U, V, W);
 }
 
+int fmm_basis_shape(int levels, int basis, int* dims) {
+  BasisShape sh;
+  if (!dims || !basis_shape(levels, basis, sh)) return -1;
+  dims[0] = sh.gm;
+  dims[1] = sh.gk;
+  dims[2] = sh.gn;
+  dims[3] = sh.R;
+  return 0;
+}
+
 int fmm_product_table_ex(int levels, int basis, int8_t* U, int8_t* V, int8_t* W) {
-  if (levels < 0 || levels > 2 || !U || !V || !W) return -1;
-  if (basis != kBasisStrassen && basis != kBasisWinograd) return -1;
-  const int R = ipow(7, levels), Q = ipow(4, levels);
-  std::memset(U, 0, static_cast<size_t>(R) * Q);
-  std::memset(V, 0, static_cast<size_t>(R) * Q);
-  std::memset(W, 0, static_cast<size_t>(R) * Q);
+  BasisShape sh;
+  if (!U || !V || !W || !basis_shape(levels, basis, sh)) return -1;
+  const int R = sh.R;
+  std::memset(U, 0, static_cast<size_t>(R) * sh.gm * sh.gk);
+  std::memset(V, 0, static_cast<size_t>(R) * sh.gk * sh.gn);
+  std::memset(W, 0, static_cast<size_t>(R) * sh.gm * sh.gn);
   const std::vector<Product> prods = make_products(levels, basis);
   for (int r = 0; r < R; ++r) {
     for (const Term& t : prods[r].a) U[t.block * R + r] = static_cast<int8_t>(t.sign);

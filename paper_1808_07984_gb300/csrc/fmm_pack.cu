@@ -8,6 +8,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cstring>
+#include "fmm_bases.h"
 #include "fmm_kernels.cuh"
 #include "launch.h"
 
@@ -115,6 +116,13 @@ __device__ __forceinline__ void emit(const SumParams& p, int r, int64_t i, int64
   store_sum<TERMS, OUT16, EPT>(p, o, acc);
 }
 
+// 2^-e for an exponent of outer_exp (e in [-126, 127]), built from its bits: a normal float
+// for e <= 126 and the subnormal 2^-127 for e = 127.  Multiplying by it rounds once, exactly
+// as scaling by ldexp does.
+__device__ __forceinline__ float pow2_inverse(int e) {
+  return e <= 126 ? __int_as_float((127 - e) << 23) : __int_as_float(0x00400000);
+}
+
 template <typename T, int EPT>
 __device__ __forceinline__ void load_group(const SumParams& p, const T* X, int64_t gr, int64_t gc,
                                            int64_t l0, float (&v)[EPT]) {
@@ -143,14 +151,14 @@ __device__ __forceinline__ void load_group(const SumParams& p, const T* X, int64
       v[e] = (row_ok && gc + e < p.cols && l0 + e < p.hc) ? load_as_float<T>(X + gr * p.ldx + gc + e) : 0.f;
   }
   if (p.row_maxbits && row_ok) {  // outside scaling: exact powers of two
-    const int ex = outer_exp(p.row_maxbits[gr]);
+    const float f = pow2_inverse(outer_exp(p.row_maxbits[gr]));
 #pragma unroll
-    for (int e = 0; e < EPT; ++e) v[e] = ldexpf(v[e], -ex);
+    for (int e = 0; e < EPT; ++e) v[e] *= f;
   }
   if (p.col_maxbits) {
 #pragma unroll
     for (int e = 0; e < EPT; ++e)
-      if (gc + e < p.cols) v[e] = ldexpf(v[e], -outer_exp(p.col_maxbits[gc + e]));
+      if (gc + e < p.cols) v[e] *= pow2_inverse(outer_exp(p.col_maxbits[gc + e]));
   }
 }
 
@@ -280,6 +288,44 @@ __global__ void __launch_bounds__(256) operand_sums_kernel(const __grid_constant
   }
 }
 
+// Operand sums of a basis given as a table (TableSumParams): each thread loads EPT
+// consecutive columns of one row position from every stored block, then forms each
+// product's signed sum in FP32 (blocks in ascending order) and hands it to emit().
+template <typename T, int OUT16, int NB, int TERMS, int EPT, int SCALE>
+__global__ void __launch_bounds__(256) table_sums_kernel(const __grid_constant__ TableSumParams tp) {
+  const SumParams& p = tp.p;
+  const T* X = static_cast<const T*>(p.X);
+  const int64_t groups = (p.hc + EPT - 1) / EPT;
+  const int64_t total = p.hr * groups;
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = idx / groups;
+    const int64_t l0 = (idx - i * groups) * EPT;
+    const int64_t orow = i * p.ld_out + l0;
+    float v[NB][EPT];
+#pragma unroll
+    for (int sb = 0; sb < NB; ++sb)
+      load_group<T, EPT>(p, X, (sb / tp.grid_c) * p.hr + i, (sb % tp.grid_c) * p.hc + l0, l0, v[sb]);
+    for (int r = 0; r < tp.nprod; ++r) {
+      float acc[EPT];
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) acc[e] = 0.f;
+#pragma unroll
+      for (int sb = 0; sb < NB; ++sb) {
+        const int c = tp.coef[sb][r];
+        if (c > 0) {
+#pragma unroll
+          for (int e = 0; e < EPT; ++e) acc[e] += v[sb][e];
+        } else if (c < 0) {
+#pragma unroll
+          for (int e = 0; e < EPT; ++e) acc[e] -= v[sb][e];
+        }
+      }
+      emit<SCALE, TERMS, OUT16, EPT>(p, r, i, l0, r * p.prod_stride + orow, acc);
+    }
+  }
+}
+
 // Outside scaling: float bits of max |x| of every row of X (rows x cols, leading dimension
 // ld), one block per row.
 template <typename T>
@@ -403,6 +449,46 @@ static cudaError_t launch_sums_b(const SumParams& p, int levels, int in_type, in
     cudaError_t e = launch_sums_l<__half, 1, IS_B, TQ, 1, 1>(p, levels, num_sms, s);
     if (e != cudaSuccess) return e;
     return launch_sums_l<__half, 1, IS_B, TQ, 1, 2>(p, levels, num_sms, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T, int OUT16, int NB, int TERMS, int SCALE = 0>
+static cudaError_t launch_table_t(const TableSumParams& tp, int num_sms, cudaStream_t s) {
+  constexpr int EPT = NB <= 6 ? 8 : 4;
+  const int64_t total = tp.p.hr * ((tp.p.hc + EPT - 1) / EPT);
+  if (total == 0 || tp.nprod == 0) return cudaSuccess;
+  const int grid = static_cast<int>(std::min<int64_t>((total + 255) / 256, int64_t(num_sms) * 16));
+  table_sums_kernel<T, OUT16, NB, TERMS, EPT, SCALE><<<grid, 256, 0, s>>>(tp);
+  return cudaGetLastError();
+}
+
+template <typename T, int OUT16, int TERMS, int SCALE = 0>
+static cudaError_t launch_table_nb(const TableSumParams& tp, int num_sms, cudaStream_t s) {
+  switch (tp.grid_r * tp.grid_c) {
+    case 4: return launch_table_t<T, OUT16, 4, TERMS, SCALE>(tp, num_sms, s);
+    case 6: return launch_table_t<T, OUT16, 6, TERMS, SCALE>(tp, num_sms, s);
+    case 9: return launch_table_t<T, OUT16, 9, TERMS, SCALE>(tp, num_sms, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_table_sums(const TableSumParams& tp, int in_type, int out16, int num_sms, cudaStream_t s) {
+  if (tp.nprod < 0 || tp.nprod > kMaxTableRank) return cudaErrorInvalidValue;
+  const SumParams& p = tp.p;
+  if (in_type == kInF32) {
+    if (p.terms == 3) return launch_table_nb<float, 0, 3>(tp, num_sms, s);
+    if (p.terms == 1)
+      return out16 ? launch_table_nb<float, 1, 1>(tp, num_sms, s) : launch_table_nb<float, 0, 1>(tp, num_sms, s);
+    return cudaErrorInvalidValue;
+  }
+  if (in_type == kInBF16 && p.terms == 1 && !out16) return launch_table_nb<__nv_bfloat16, 0, 1>(tp, num_sms, s);
+  if (in_type == kInF16 && p.terms == 1 && out16) {
+    if (!p.maxbits) return launch_table_nb<__half, 1, 1>(tp, num_sms, s);
+    // two passes: panel maxima, then the sums scaled by 2^-s (maxbits zeroed by the caller)
+    cudaError_t e = launch_table_nb<__half, 1, 1, 1>(tp, num_sms, s);
+    if (e != cudaSuccess) return e;
+    return launch_table_nb<__half, 1, 1, 2>(tp, num_sms, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <string>
+#include "fmm_bases.h"
 #include "fmm_kernels.cuh"
 
 namespace fmm {
@@ -16,6 +17,8 @@ void set_last_error(const std::string& msg);
 // the coefficient of operand block (j, i) at every level.
 cudaError_t launch_operand_sums(const SumParams& p, int levels, bool is_b, bool transq, int in_type,
                                 int out16, int num_sms, cudaStream_t s);
+// Operand sums of every product of a basis table (see TableSumParams) for one operand.
+cudaError_t launch_table_sums(const TableSumParams& tp, int in_type, int out16, int num_sms, cudaStream_t s);
 cudaError_t launch_beta(float* C, int64_t m, int64_t n, int64_t ldc, float beta, int num_sms,
                         cudaStream_t s);
 cudaError_t launch_debug_wait(unsigned* err, uint64_t timeout_ns, cudaStream_t s);

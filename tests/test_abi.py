@@ -133,7 +133,8 @@ def test_option_errors_need_no_gpu(lib):
     assert _call_ex(lib, schedule=5) == 1
     assert _call_ex(lib, bk=48) == 1
     assert _call_ex(lib, pipeline=3) == 1
-    assert _call_ex(lib, basis=2) == 1
+    assert _call_ex(lib, basis=3) == 1
+    assert _call_ex(lib, basis=-1) == 1
     assert _call_ex(lib, deterministic=2) == 1
     assert _call_ex(lib, outer_scaling=2) == 1
     assert _call_ex(lib, fringe=2) == 1
@@ -142,3 +143,41 @@ def test_option_errors_need_no_gpu(lib):
     assert _call_ex(lib, algo=2, outer_scaling=1) == 3      # fused: no outside scaling
     assert _call_ex(lib, algo=3, levels=1) == 3             # hybrid: two levels
     assert _call_ex(lib, algo=9) == 3
+    assert _call_ex(lib, levels=2, basis=2) == 3            # <3,2,3>: one level
+    assert _call_ex(lib, algo=2, basis=2) == 3              # <3,2,3>: packed only
+    assert _call_ex(lib, basis=2, pipeline=2) == 3          # <3,2,3>: one table pass
+
+
+def test_basis_shapes(lib):
+    assert fmm.basis_shape(0, "b323") == (1, 1, 1, 1)
+    assert fmm.basis_shape(1, "b323") == (3, 2, 3, 15)
+    assert fmm.basis_shape(2, "strassen") == (4, 4, 4, 49)
+    assert fmm.basis_shape(1, "winograd") == (2, 2, 2, 7)
+    with pytest.raises(fmm.FmmError):
+        fmm.basis_shape(2, "b323")
+    with pytest.raises(fmm.FmmError):
+        fmm.basis_shape(1, 7)
+
+
+def test_library_b323_tables_match_oracle_and_brent(lib):
+    U, V, W = fmm.product_table(1, "b323")
+    OU, OV, OW = oracle.BASES["b323"]
+    np.testing.assert_array_equal(U, OU)
+    np.testing.assert_array_equal(V, OV)
+    np.testing.assert_array_equal(W, OW)
+    # and the exported arrays on their own satisfy the trilinear identity of <3,2,3>
+    for i, l, l2, j, i2, j2 in np.ndindex(3, 2, 2, 3, 3, 3):
+        got = int(np.sum(U[i * 2 + l].astype(np.int64) * V[l2 * 3 + j] * W[i2 * 3 + j2]))
+        assert got == (1 if (l == l2 and i == i2 and j == j2) else 0)
+    # at most three destinations per product: within the kernels' four-entry lists
+    assert int(np.count_nonzero(W, axis=0).max()) <= 4
+
+
+def test_b323_workspace_sizes(lib):
+    # 15 products of (h_m x h_k) A sums and (h_k x h_n) B sums, BF16 hi and lo
+    m = n = k = 3000
+    hm, hk, hn = oracle.grid_block(m, 3), oracle.grid_block(k, 2), oracle.grid_block(n, 3)
+    a = -(-15 * hm * hk * 2 // 256) * 256
+    b = -(-15 * hk * hn * 2 // 256) * 256
+    assert fmm.workspace_size(m, n, k, 1, basis="b323") == 2 * (a + b)
+    assert fmm.workspace_size(m, n, k, 1, "plain_bf16", basis="b323") == a + b

@@ -289,6 +289,59 @@ def test_winograd_basis_float(variant):
     assert oracle.normwise_error(C, C64, An, Bn) <= tolerance(variant, 1, 400)
 
 
+# ------------------------------------------------ the <3,2,3> basis of rank 15 (Section 6)
+@pytest.mark.parametrize("opts", [{}, {"pads": (0, 0, 1)}, {"cta_pair": False}, {"fringe": "peel"},
+                                  {"deterministic": True}, {"round_tiles": 1}, {"tile_n": 128},
+                                  {"tile_n": 256}, {"outer_scaling": True}, {"schedule": "product"}])
+@pytest.mark.parametrize("m,n,k", [(300, 520, 200), (129, 257, 65), (1000, 1200, 300), (1, 300, 1),
+                                   (7, 5, 3), (1800, 776, 130)])
+def test_b323_basis_bit_exact(m, n, k, opts):
+    """Fifteen products over 3 x 2 blocks of A and 2 x 3 of B, each added into its (at most
+    three) 3 x 3 blocks of C: exact on small integers through every packed option."""
+    o = dict(opts)
+    pads = o.pop("pads", (0, 0, 0))
+    C, C64, _, _ = run(m, n, k, 1, "split3", dist="int", seed=47 * m + k, basis="b323", pads=pads, **o)
+    np.testing.assert_array_equal(C, C64)
+
+
+@pytest.mark.parametrize("variant", ["split3", "plain_bf16", "bf16", "f16"])
+@pytest.mark.parametrize("m,n,k", [(600, 520, 400), (771, 1030, 515)])
+def test_b323_basis_float(variant, m, n, k):
+    C, C64, An, Bn = run(m, n, k, 1, variant, seed=49, basis="b323")
+    assert oracle.normwise_error(C, C64, An, Bn) <= tolerance(variant, 1, k)
+
+
+@pytest.mark.parametrize("variant", ["split3", "f16"])
+def test_b323_basis_alpha_beta(variant):
+    C, C64, An, Bn = run(700, 900, 350, 1, variant, seed=51, alpha=-1.5, beta=0.75, basis="b323")
+    assert oracle.normwise_error(C, C64, An, Bn) <= tolerance(variant, 1, 350)
+
+
+def test_b323_basis_matches_the_oracle_table_product():
+    """The library's fifteen products against the oracle's restatement of the same table
+    (FP64), on values whose sums and products are exact in every precision involved."""
+    m, n, k = 240, 330, 160
+    A, B = synth.problem(m, n, k, 53, "int")
+    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    C = fmm.gemm(Ad, Bd, levels=1, basis="b323")
+    fmm.device_status()
+    np.testing.assert_array_equal(C.cpu().numpy(), oracle.table_matmul(A, B, basis="b323"))
+
+
+def test_b323_basis_sampled_rows_4096():
+    rows = np.array([0, 1, 1365, 1366, 1367, 2730, 2731, 4095])  # first rows of each third
+    C, C64, An, Bn = run(4096, 4096, 4096, 1, "split3", seed=55, rows=rows, basis="b323")
+    assert oracle.normwise_error(C, C64, An, Bn) <= tolerance("split3", 1, 4096)
+
+
+def test_b323_basis_rejected_where_not_built():
+    A = torch.zeros((64, 64), device="cuda")
+    with pytest.raises(fmm.FmmError):
+        fmm.gemm(A, A, levels=2, basis="b323")
+    with pytest.raises(fmm.FmmError):
+        fmm.gemm(A, A, levels=1, basis="b323", algo="fused")
+
+
 def test_winograd_basis_rejected_at_two_levels():
     A = torch.zeros((64, 64), device="cuda")
     with pytest.raises(fmm.FmmError):
