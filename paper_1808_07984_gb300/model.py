@@ -16,6 +16,7 @@ updates).  On GB300 the same three costs appear in different places:
     t_pack   = pack_bytes / (BW * pack_eff)
     t_tensor = W * (t_item_mma + t_item_fix + wb_bytes_item * wb_cost)
     W        = ceil(items / workers)                        (items of the busiest CTA pair)
+    items    = R * ceil(h_m / 256) * ceil(h_n / tile_n)     (R products of a basis)
     t_item_mma = terms * 2 * 256 * tile_n * h_k / (TC * tc_eff / workers)
 
 BW and TC are the measured HBM copy bandwidth and burst BF16 tensor rate of the pool's
@@ -28,7 +29,10 @@ burst figure.  The largest products run below the model (up to 15 % at 20480): t
 power cap lowers the SM clock, which the model does not represent.
 
 Used by ``autotune.autotune(prior="model")`` to rank the (levels, tile_n) candidates of each
-size so that only the most promising ones are measured.
+size so that only the most promising ones are measured, and (``best_basis``) to choose
+between one-level bases: a basis with block grid (g_m, g_k, g_n), R products and nnz(W) C
+updates enters through the block sizes h = ceil(d / g) (rounded up to 8), the R operand sums
+per operand and the average W_C = nnz(W) / R.
 """
 from __future__ import annotations
 
@@ -41,35 +45,50 @@ DEFAULT = {"pack_eff": 1.158, "tc_eff": 1.051, "wb_cost_ns_per_kb": 10.44, "t_it
            "t_launch_us": 5.93}
 
 _TERMS = {"split3": 3, "plain_bf16": 1, "bf16": 1, "f16": 1}
+# one-level bases: block grid (g_m, g_k, g_n), products R and nonzeros of W (C updates)
+BASES = {"strassen": (2, 2, 2, 7, 12), "winograd": (2, 2, 2, 7, 14), "b323": (3, 2, 3, 15, 30)}
 _IN_BYTES = {"split3": 4, "plain_bf16": 4, "bf16": 2, "f16": 2}
 _ARRAYS = {"split3": 2, "plain_bf16": 1, "bf16": 1, "f16": 1}
 
 
-def block(d: int, levels: int) -> int:
-    """Block size of the library's split rule: ceil(d / 2^L) rounded up to 8 (d > 0)."""
+def block(d: int, levels: int, g: int = 0) -> int:
+    """Block size of the library's split rule: ceil(d / g) rounded up to 8 (d > 0), with
+    g = 2^L unless given."""
     if d <= 0:
         return 0
-    h = -(-d // (1 << levels))
+    h = -(-d // (g or (1 << levels)))
     return -(-h // 8) * 8
 
 
-def auto_tile_n(m: int, n: int, levels: int) -> int:
+def shape(levels: int, basis: str = "strassen"):
+    """(g_m, g_k, g_n, R, average C updates per product) of ``levels`` levels of a basis."""
+    if levels == 0:
+        return 1, 1, 1, 1, 1.0
+    gm, gk, gn, r, nw = BASES[basis]
+    if basis != "strassen" and levels != 1:
+        raise ValueError("bases other than Strassen's are built for one level")
+    return gm ** levels, gk ** levels, gn ** levels, r ** levels, (nw / r) ** levels
+
+
+def auto_tile_n(m: int, n: int, levels: int, basis: str = "strassen") -> int:
     """The library's automatic tile width for CTA pairs (256 unless that leaves fewer than
     four items per pair)."""
-    hm, hn = block(m, levels), block(n, levels)
-    items256 = 7 ** levels * -(-hm // 256) * -(-hn // 256)
+    gm, _, gn, R, _ = shape(levels, basis)
+    hm, hn = block(m, levels, gm), block(n, levels, gn)
+    items256 = R * -(-hm // 256) * -(-hn // 256)
     return 256 if items256 >= 4 * (GB300["sms"] // 2) else 128
 
 
 def predict(m: int, n: int, k: int, levels: int, variant: str = "split3", tile_n: int = 0,
-            params: dict | None = None, hw: dict | None = None) -> dict:
-    """Predicted milliseconds of fmm_gemm(m, n, k, levels, variant) and its components."""
+            params: dict | None = None, hw: dict | None = None, basis: str = "strassen") -> dict:
+    """Predicted milliseconds of fmm_gemm(m, n, k, levels, variant, basis) and its
+    components."""
     p = dict(DEFAULT, **(params or {}))
     h = dict(GB300, **(hw or {}))
-    R = 7 ** levels
+    gm, gk, gn, R, wc = shape(levels, basis)
     terms, e_in, arrays = _TERMS[variant], _IN_BYTES[variant], _ARRAYS[variant]
-    hm, hn, hk = block(m, levels), block(n, levels), block(k, levels)
-    tn = tile_n or auto_tile_n(m, n, levels)
+    hm, hn, hk = block(m, levels, gm), block(n, levels, gn), block(k, levels, gk)
+    tn = tile_n or auto_tile_n(m, n, levels, basis)
     bw = h["hbm_gbs"] * 1e9
     t_beta = 4.0 * m * n / bw
     pack_bytes = (m * k + k * n) * e_in + R * (hm * hk + hk * hn) * 2 * arrays
@@ -79,7 +98,7 @@ def predict(m: int, n: int, k: int, levels: int, variant: str = "split3", tile_n
     per_worker = -(-items // workers)
     tc = h["tc_tflops"] * 1e12 * p["tc_eff"] / workers
     t_item_mma = terms * 2.0 * 256 * tn * hk / tc
-    wc = (12.0 / 7.0) ** levels  # average W_C of a product (12 nonzeros of W over 7 products)
+    # wc: average W_C of a product (Strassen: 12 nonzeros of W over 7 products per level)
     wb_bytes_item = wc * 256 * tn * 4
     t_item = t_item_mma + p["t_item_fix_us"] * 1e-6 + wb_bytes_item / 1024.0 * p["wb_cost_ns_per_kb"] * 1e-9
     t_tensor = per_worker * t_item
@@ -93,6 +112,13 @@ def predict(m: int, n: int, k: int, levels: int, variant: str = "split3", tile_n
 def best_levels(m: int, n: int, k: int, variant: str = "split3", params: dict | None = None) -> int:
     """The level the model predicts fastest."""
     return min(range(3), key=lambda L: predict(m, n, k, L, variant, params=params)["ms"])
+
+
+def best_basis(m: int, n: int, k: int, variant: str = "split3", params: dict | None = None):
+    """(levels, basis) the model predicts fastest among classical, Strassen at one and two
+    levels and the other one-level bases."""
+    cands = [(0, "strassen"), (1, "strassen"), (2, "strassen"), (1, "winograd"), (1, "b323")]
+    return min(cands, key=lambda c: predict(m, n, k, c[0], variant, params=params, basis=c[1])["ms"])
 
 
 def rank_candidates(d: int, variant: str = "split3", levels=(0, 1, 2), tiles=(128, 256),

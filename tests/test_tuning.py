@@ -1,5 +1,7 @@
 """Tune-table selection and the autotuner's table construction (no GPU)."""
+import json
 import math
+import os
 
 import pytest
 
@@ -118,3 +120,36 @@ def test_native_tuner_rejects_bad_arguments_without_gpu():
     assert lib.fmm_tune_measure(0, sz.ctypes.data, 2, 3, ctypes.byref(t), None, None) == 1
     assert lib.fmm_tune_measure(0, sz.ctypes.data, 0, 3, ctypes.byref(t), None, None) == 1
     assert lib.fmm_tune_measure(0, sz.ctypes.data, 1, 0, ctypes.byref(t), None, None) == 1
+
+
+def test_model_basis_shapes_and_default_unchanged():
+    assert model.shape(1, "b323") == (3, 2, 3, 15, 2.0)
+    assert model.shape(2, "strassen")[:4] == (4, 4, 4, 49)
+    assert model.block(16384, 1, 3) == 5464
+    for d in (4096, 16384):
+        assert model.predict(d, d, d, 1)["ms"] == model.predict(d, d, d, 1, basis="strassen")["ms"]
+    with pytest.raises(ValueError):
+        model.shape(2, "b323")
+
+
+def test_model_b323_pays_for_padding_at_16384():
+    # 16384 / 3 rounds up to 22 row tiles of 256 per block: 3 % more tiles than needed
+    a = model.predict(16384, 16384, 16384, 1, basis="b323")
+    assert a["items"] == 15 * 22 * 22
+    b = model.predict(15360, 15360, 15360, 1, basis="b323")
+    assert b["items"] == 15 * 20 * 20
+
+
+def test_model_picks_the_measured_fastest_basis_on_square_sizes():
+    """Against the whole-call times measured on a GB300 (tuned/gb300_basis_samples.json):
+    the model's choice among classical, Strassen (one, two levels) and the <3,2,3> basis is
+    the measured fastest, or within 2 % of it, at every square size."""
+    path = os.path.join(os.path.dirname(model.__file__), "tuned", "gb300_basis_samples.json")
+    with open(path) as f:
+        rec = json.load(f)
+    cands = [(0, "strassen"), (1, "strassen"), (1, "b323"), (2, "strassen")]
+    for m, n, k, *ms in rec["rows"]:
+        if not (m == n == k):
+            continue
+        pick = min(cands, key=lambda c: model.predict(m, n, k, c[0], basis=c[1])["ms"])
+        assert ms[cands.index(pick)] <= 1.02 * min(ms), (m, pick, ms)
