@@ -464,8 +464,30 @@ def main():
                 "kernel": "fmm_packed_kernel", "kernel_ms": ker_ms,
                 "launches_per_step": launches_per_step,
                 "algorithmic_flops_per_launch": mma_flops}
+    # ---- roofline of the HBM-bound passes: the operand-sum passes (A and B) and the beta pass
+    hbm = float(peaks["hbm_gbs"]) if peaks and "hbm_gbs" in peaks else None
+    in_b = 2 if a.variant in ("bf16", "f16") else 4
+    out_b = 2 * (2 if a.variant == "split3" else 1)  # BF16/FP16 per stored term
+    g = 1 << a.levels
+    blk = (lambda d: d) if a.levels == 0 else (lambda d: -(-(-(-d // g)) // 8) * 8)
+    hm, hn, hk = blk(m), blk(n), blk(k)
+    sum_bytes = in_b * (m * k + k * n) + out_b * 7 ** a.levels * (hm * hk + hk * hn)
+    pack_ms = prof["pack"][0] / a.steps
+    beta_ms = prof["beta"][0] / a.steps
+    passes = {
+        "operand_sums": {"bound": "hbm", "algorithmic_bytes_per_step": sum_bytes, "ms_per_step": pack_ms,
+                         "achieved_gbs": sum_bytes / (pack_ms * 1e-3) * 1e-9 if pack_ms > 0 else None},
+        "beta": {"bound": "hbm", "kind": "C zeroed by cudaMemsetAsync (beta = 0)",
+                 "algorithmic_bytes_per_step": 4 * m * n, "ms_per_step": beta_ms,
+                 "achieved_gbs": 4 * m * n / (beta_ms * 1e-3) * 1e-9 if beta_ms > 0 else None},
+        "peak_gbs": hbm, "peak_source": "measured (HBM copy)" if hbm else None,
+    }
+    for v in (passes["operand_sums"], passes["beta"]):
+        v["frac"] = (v["achieved_gbs"] / hbm) if (hbm and v["achieved_gbs"]) else None
     phases = {p: {"ms_per_step": v[0] / a.steps, "launches": v[1]} for p, v in prof.items()}
-    gpu_launches = int(sum(v[1] for v in prof.values()))
+    # kernels of this library only: with beta = 0 and dense rows the beta phase is a
+    # cudaMemsetAsync, not a kernel of ours
+    gpu_launches = int(prof["pack"][1] + prof["tensor"][1])
 
     cpu = None
     if not a.no_cpu_baseline:
@@ -485,6 +507,7 @@ def main():
         "speedup_vs_classical": (value / classical["value"]) if classical else None,
         "phases": phases,
         "roofline": roofline,
+        "hbm_passes": passes,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clk,
