@@ -201,6 +201,9 @@ def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
     (the <3,2,3> basis of rank 15, one level, packed algorithm).  ``deterministic``:
     ownership mode, bitwise reproducible results.  ``outer_scaling``: exact power-of-two
     scaling of the rows of A and columns of B around the product (badly scaled inputs).
+    ``levels="auto"``: the level count and basis the analytic model (``model.py``) predicts
+    fastest for this shape and variant (classical, Strassen at one or two levels, or the
+    <3,2,3> basis); ``basis`` is then ignored.
     """
     import torch
     v = _variant(variant)
@@ -208,6 +211,8 @@ def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
     k2, n = B.shape
     if k != k2:
         raise FmmError(1, f"inner dimensions differ: {k} vs {k2}")
+    if levels == "auto":
+        levels, basis = choose(m, n, k, {x: name for name, x in VARIANTS.items()}[v])
     want = getattr(torch, _IN_DTYPE[v])
     for name, X in (("A", A), ("B", B)):
         if X.dtype != want:
@@ -234,6 +239,16 @@ def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
                             _stream_handle(stream), ctypes.byref(o))
     _check(st)
     return C
+
+
+def choose(m: int, n: int, k: int, variant="split3"):
+    """(levels, basis) that the analytic model predicts fastest for an m x n x k product:
+    classical, Strassen at one or two levels, or the <3,2,3> basis at one level."""
+    from . import model
+    if min(m, n, k) <= 0:
+        return 0, "strassen"
+    cands = [(0, "strassen"), (1, "strassen"), (2, "strassen"), (1, "b323")]
+    return min(cands, key=lambda c: model.predict(m, n, k, c[0], variant, basis=c[1])["ms"])
 
 
 def workspace_size_backward(m, n, k, levels=1, variant="split3") -> int:

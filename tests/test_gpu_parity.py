@@ -342,6 +342,15 @@ def test_b323_basis_rejected_where_not_built():
         fmm.gemm(A, A, levels=1, basis="b323", algo="fused")
 
 
+@pytest.mark.parametrize("m,n,k", [(3000, 3000, 3000), (1200, 900, 150), (2304, 2304, 2304)])
+def test_levels_auto_uses_the_models_choice(m, n, k):
+    A, B = synth.problem(m, n, k, 57 + m, "int")
+    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    C = fmm.gemm(Ad, Bd, levels="auto")
+    fmm.device_status()
+    np.testing.assert_array_equal(C.cpu().numpy(), oracle.classical(A, B))
+
+
 def test_winograd_basis_rejected_at_two_levels():
     A = torch.zeros((64, 64), device="cuda")
     with pytest.raises(fmm.FmmError):

@@ -153,3 +153,14 @@ def test_model_picks_the_measured_fastest_basis_on_square_sizes():
             continue
         pick = min(cands, key=lambda c: model.predict(m, n, k, c[0], basis=c[1])["ms"])
         assert ms[cands.index(pick)] <= 1.02 * min(ms), (m, pick, ms)
+
+
+def test_choose_follows_the_model():
+    assert fmm.choose(0, 10, 10) == (0, "strassen")
+    assert fmm.choose(13824, 13824, 13824) == (1, "b323")
+    assert fmm.choose(16384, 16384, 16384) == (2, "strassen")
+    assert fmm.choose(16384, 16384, 512)[0] == 0          # rank-k: classical
+    for shape in [(1000, 2000, 3000), (30001, 29999, 4097), (64, 64, 64)]:
+        lv, basis = fmm.choose(*shape, variant="f16")
+        assert lv in (0, 1, 2) and basis in ("strassen", "b323")
+        assert basis == "strassen" or lv == 1
