@@ -224,6 +224,10 @@ typedef struct fmm_tune_table {
 
 /* The built-in table (measured on GB300 with the split-BF16 arithmetic). */
 void fmm_tune_default(fmm_tune_table* out);
+/* The built-in table for a variant, which the batched entry points use when `tune` is NULL:
+ * for BF16 and FP16 operands one class, classical (the classical product reads 16-bit
+ * operands in place, with no pass at all); for FP32 operands fmm_tune_default's table. */
+void fmm_tune_default_ex(int variant, fmm_tune_table* out);
 /* Levels and tile width the table assigns to an m x n x k problem (NULL = built-in). */
 fmm_status fmm_tune_select(const fmm_tune_table* tune, int64_t m, int64_t n, int64_t k,
                            int* levels, int* tile_n);

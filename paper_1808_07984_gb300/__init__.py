@@ -86,6 +86,8 @@ def load() -> ctypes.CDLL:
     L.fmm_workspace_size_backward_ex.argtypes = [i64, i64, i64, i32, i32, ctypes.POINTER(_Options)]
     L.fmm_tune_default.restype = None
     L.fmm_tune_default.argtypes = [ctypes.POINTER(TuneTable)]
+    L.fmm_tune_default_ex.restype = None
+    L.fmm_tune_default_ex.argtypes = [i32, ctypes.POINTER(TuneTable)]
     L.fmm_tune_measure.restype = i32
     L.fmm_tune_measure.argtypes = [i32, vp, i32, i32, ctypes.POINTER(TuneTable), vp, vp]
     L.fmm_tune_select.restype = i32
@@ -334,12 +336,16 @@ def linear(A, B, levels: int = 1, variant="split3", deterministic: bool = False)
     return _linear_fn.apply(A, B, levels, variant, deterministic)
 
 
-def tune_table(classes=None):
-    """TuneTable from [(max_dim, levels, tile_n), ...] (None = the library's built-in table),
-    or from a table dict written by paper_1808_07984_gb300.autotune."""
+def tune_table(classes=None, variant=None):
+    """TuneTable from [(max_dim, levels, tile_n), ...] (None = the library's built-in table,
+    that of ``variant`` when given), or from a table dict written by
+    paper_1808_07984_gb300.autotune."""
     t = TuneTable()
     if classes is None:
-        load().fmm_tune_default(ctypes.byref(t))
+        if variant is None:
+            load().fmm_tune_default(ctypes.byref(t))
+        else:
+            load().fmm_tune_default_ex(_variant(variant), ctypes.byref(t))
         return t
     if isinstance(classes, dict):
         classes = [(c["max_dim"], c["levels"], c["tile_n"]) for c in classes["classes"]]
@@ -378,12 +384,12 @@ def tune_select(m, n, k, tune=None):
     return lv.value, tn.value
 
 
-def _default_tune():
+def _default_tune(variant=None):
     path = os.environ.get("FMM_TUNE_FILE")
     if path and os.path.exists(path):
         from . import autotune
         return tune_table(autotune.load(path))
-    return tune_table(None)
+    return tune_table(None, variant)
 
 
 class BatchedPlan:
@@ -422,7 +428,7 @@ class BatchedPlan:
         self._ldb = I64(*[max(b.stride(0), 1) for b in Bs])
         self._ldc = I64(*[max(c.stride(0), 1) for c in Cs])
         self._tune = tune if isinstance(tune, TuneTable) else (tune_table(tune) if tune is not None
-                                                               else _default_tune())
+                                                               else _default_tune(self.variant))
         ws = L.fmm_batched_workspace_size(cnt, self._m, self._n, self._k, self.variant,
                                           ctypes.byref(self._tune))
         if ws == ctypes.c_size_t(-1).value:

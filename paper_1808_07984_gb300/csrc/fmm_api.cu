@@ -742,6 +742,9 @@ struct PackedJob {
   int a_type = kInF32, b_type = kInF32;
   SumParams sa, sb;
   TableSumParams ta, tb;  // bases other than Strassen's: sums formed from the product table
+  // classical products of 16-bit operands: the tensor-core kernel reads the operand straight
+  // from the caller's buffer (no sum pass)
+  bool direct_a = false, direct_b = false;
   unsigned* maxbits = nullptr;
   int grid = 0;
   bool has_work = false;  // k > 0 and alpha != 0
@@ -773,6 +776,18 @@ fmm_status prepare_packed(const Plan& pl, int64_t m, int64_t n, int64_t k, float
   uint16_t* a_lo = pl.terms == 3 ? reinterpret_cast<uint16_t*>(wsb + pl.a_bytes + pl.b_bytes) : nullptr;
   uint16_t* b_lo = pl.terms == 3 ? reinterpret_cast<uint16_t*>(wsb + 2 * pl.a_bytes + pl.b_bytes) : nullptr;
   job.maxbits = pl.scaled ? reinterpret_cast<unsigned*>(wsb + pl.a_bytes + pl.b_bytes) : nullptr;
+  // With one product and no sums, the "sum" of a 16-bit operand is the operand itself: the
+  // kernel's TMA reads it in place wherever TMA can address it (16-byte aligned base and
+  // rows).  Exact FP16 values need no power-of-two panel scaling (their products are exact in
+  // the FP32 accumulator), so the scaled variant drops its scaling when both operands are read
+  // in place, and reads neither in place otherwise.
+  auto tma_ok = [](const Operand& o) {
+    return reinterpret_cast<uintptr_t>(o.X) % 16 == 0 && o.ld % 8 == 0;
+  };
+  job.direct_a = pl.L == 0 && pl.terms == 1 && a.type != kInF32 && !pl.outer_scaling && tma_ok(a);
+  job.direct_b = pl.L == 0 && pl.terms == 1 && b.type != kInF32 && !pl.outer_scaling && tma_ok(b);
+  if (pl.scaled && !(job.direct_a && job.direct_b)) job.direct_a = job.direct_b = false;
+  if (job.direct_a && job.direct_b) job.maxbits = nullptr;
 
   SumParams& sa = job.sa;
   sa.X = a.X;
@@ -849,17 +864,20 @@ fmm_status prepare_packed(const Plan& pl, int64_t m, int64_t n, int64_t k, float
   auto encode_maps = [&](PackedParams* q, int prod0, int nprod) -> fmm_status {
     fmm_status es = FMM_OK;
     for (int t = 0; t < nb && es == FMM_OK; ++t) {
-      uint16_t* ab = (t ? a_lo : a_hi) + prod0 * sa.prod_stride;
-      uint16_t* bb = (t ? b_lo : b_hi) + prod0 * sb.prod_stride;
+      // in place (L = 0, one product): the caller's buffer and row stride
+      void* ab = job.direct_a ? const_cast<void*>(a.X) : (t ? a_lo : a_hi) + prod0 * sa.prod_stride;
+      void* bb = job.direct_b ? const_cast<void*>(b.X) : (t ? b_lo : b_hi) + prod0 * sb.prod_stride;
+      const int64_t lda_m = job.direct_a ? a.ld : pl.lda_w;
+      const int64_t ldb_m = job.direct_b ? b.ld : pl.ldb_w;
       if (pl.a_mn)
-        es = encode_3d(&q->tmA[t], ab, pl.hm, pl.hk, nprod, pl.lda_w, 64, pl.bk);
+        es = encode_3d(&q->tmA[t], ab, pl.hm, pl.hk, nprod, lda_m, 64, pl.bk);
       else
-        es = encode_3d(&q->tmA[t], ab, pl.hk, pl.hm, nprod, pl.lda_w, pl.bk, kBM, kswz);
+        es = encode_3d(&q->tmA[t], ab, pl.hk, pl.hm, nprod, lda_m, pl.bk, kBM, kswz);
       if (es != FMM_OK) break;
       if (pl.b_mn)
-        es = encode_3d(&q->tmB[t], bb, pl.hn, pl.hk, nprod, pl.ldb_w, 64, pl.bk);
+        es = encode_3d(&q->tmB[t], bb, pl.hn, pl.hk, nprod, ldb_m, 64, pl.bk);
       else
-        es = encode_3d(&q->tmB[t], bb, pl.hk, pl.hn, nprod, pl.ldb_w, pl.bk,
+        es = encode_3d(&q->tmB[t], bb, pl.hk, pl.hn, nprod, ldb_m, pl.bk,
                        pl.pair ? pl.tile_n / 2 : pl.tile_n, kswz);
     }
     return es;
@@ -1050,13 +1068,13 @@ fmm_status launch_passes(const PackedJob& job, const DeviceInfo& dev, cudaStream
     if (e != cudaSuccess) return cuda_fail(e, "operand-sum pass (B, basis table)");
     return FMM_OK;
   }
-  cudaError_t e;
-  {
+  cudaError_t e = cudaSuccess;
+  if (!job.direct_a) {
     PhaseScope ps(kPhasePack, s);
     e = launch_operand_sums(job.sa, pl.L, false, pl.a_mn, job.a_type, pl.bf16 ? 0 : 1, dev.sms, s);
   }
   if (e != cudaSuccess) return cuda_fail(e, "operand-sum pass (A)");
-  {
+  if (!job.direct_b) {
     PhaseScope ps(kPhasePack, s);
     e = launch_operand_sums(job.sb, pl.L, true, !pl.b_mn, job.b_type, pl.bf16 ? 0 : 1, dev.sms, s);
   }
@@ -1320,6 +1338,21 @@ void fmm_tune_default(fmm_tune_table* out) {
   out->levels[2] = 2;
 }
 
+void fmm_tune_default_ex(int variant, fmm_tune_table* out) {
+  if (!out) return;
+  if (variant == FMM_BF16 || variant == FMM_F16_SCALED) {
+    // 16-bit operands: the classical product reads them in place (no pass at all), while
+    // every Strassen level adds operand-sum passes; measured on GB300 over 1024..8192 (and
+    // the 256 uneven FP16 products of 1024..8192), classical wins every class
+    std::memset(out, 0, sizeof *out);
+    out->count = 1;
+    out->max_dim[0] = INT64_MAX;
+    out->levels[0] = 0;
+    return;
+  }
+  fmm_tune_default(out);
+}
+
 fmm_status fmm_tune_select(const fmm_tune_table* tune, int64_t m, int64_t n, int64_t k, int* levels,
                            int* tile_n) {
   fmm_tune_table def;
@@ -1356,6 +1389,11 @@ struct BatchLayout {
 fmm_status batch_layout(int count, const int64_t* m, const int64_t* n, const int64_t* k, int variant,
                         const fmm_tune_table* tune, BatchLayout& lay) {
   if (count < 0 || (count > 0 && (!m || !n || !k))) return fail(FMM_ERR_ARG, "bad batch arrays");
+  fmm_tune_table def;
+  if (!tune) {  // the built-in table of this variant
+    fmm_tune_default_ex(variant, &def);
+    tune = &def;
+  }
   lay.plans.resize(count);
   lay.ws_off.resize(count);
   // parameter blocks (at most two tile-width groups) and item offsets

@@ -120,6 +120,20 @@ def test_backward_bf16_inputs_fp32_grads():
     assert _err(dB.cpu().numpy(), dB64, nA, nC) <= _tol("bf16", 1, m)
 
 
+@pytest.mark.parametrize("m,n,k", [(384, 256, 320), (130, 260, 72), (257, 129, 65)])
+def test_backward_bf16_classical_int_bit_exact(m, n, k):
+    """L = 0 with BF16 A and B: the BF16 operand of each gradient product is read in place
+    when its rows are 16-byte aligned, the FP32 dC is converted; exact on small integers."""
+    A, B = synth.problem(m, n, k, 23 + m, "int")
+    dC = synth.small_int((m, n), 24 + n)
+    Ab = torch.from_numpy(A).to(torch.bfloat16).cuda()
+    Bb = torch.from_numpy(B).to(torch.bfloat16).cuda()
+    dA, dB = fmm.gemm_backward(Ab, Bb, torch.from_numpy(dC).cuda(), levels=0, variant="bf16")
+    fmm.device_status()
+    np.testing.assert_array_equal(dA.cpu().numpy(), oracle.classical(dC, np.ascontiguousarray(B.T)))
+    np.testing.assert_array_equal(dB.cpu().numpy(), oracle.classical(np.ascontiguousarray(A.T), dC))
+
+
 @pytest.mark.parametrize("levels", [1, 2])
 def test_linear_autograd_matches_oracle_and_finite_differences(levels):
     m, n, k = 256, 192, 320

@@ -289,6 +289,38 @@ def test_winograd_basis_float(variant):
     assert oracle.normwise_error(C, C64, An, Bn) <= tolerance(variant, 1, 400)
 
 
+# ------------------------------------------------ classical 16-bit operands read in place
+@pytest.mark.parametrize("variant", ["bf16", "f16"])
+@pytest.mark.parametrize("pads", [(0, 0, 0), (1, 0, 0), (0, 3, 0), (1, 1, 1), (8, 8, 0)])
+@pytest.mark.parametrize("m,n,k", [(300, 520, 200), (129, 257, 65), (1000, 1000, 1000)])
+def test_classical_16bit_operands_in_place_or_packed(variant, pads, m, n, k):
+    """L = 0 with BF16/FP16 operands: the tensor-core kernel reads an operand straight from
+    the caller's buffer when TMA can address it (16-byte aligned rows), else from the
+    converted copy; every mix of the two gives the exact product on small integers."""
+    C, C64, _, _ = run(m, n, k, 0, variant, dist="int", seed=61 * m + k, pads=pads)
+    np.testing.assert_array_equal(C, C64)
+
+
+@pytest.mark.parametrize("variant", ["bf16", "f16"])
+@pytest.mark.parametrize("pads", [(0, 0, 0), (1, 0, 0)])
+def test_classical_16bit_float_in_place(variant, pads):
+    C, C64, An, Bn = run(700, 640, 512, 0, variant, seed=63, pads=pads, alpha=0.5, beta=2.0)
+    assert oracle.normwise_error(C, C64, An, Bn) <= tolerance(variant, 0, 512)
+
+
+def test_classical_f16_in_place_large_magnitudes():
+    """FP16 values near the top of the range: read in place without panel scaling, their
+    products are exact in the FP32 accumulator."""
+    m, n, k = 256, 384, 128
+    A = (synth.small_int((m, k), 5) * 8000.0).astype(np.float32)   # |x| <= 32000
+    B = (synth.small_int((k, n), 6) * 0.5).astype(np.float32)
+    Ad = torch.from_numpy(A).half().cuda()
+    Bd = torch.from_numpy(B).half().cuda()
+    C = fmm.gemm(Ad, Bd, levels=0, variant="f16")
+    fmm.device_status()
+    np.testing.assert_array_equal(C.cpu().numpy(), oracle.classical(A, B))
+
+
 # ------------------------------------------------ the <3,2,3> basis of rank 15 (Section 6)
 @pytest.mark.parametrize("opts", [{}, {"pads": (0, 0, 1)}, {"cta_pair": False}, {"fringe": "peel"},
                                   {"deterministic": True}, {"round_tiles": 1}, {"tile_n": 128},

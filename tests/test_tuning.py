@@ -164,3 +164,17 @@ def test_choose_follows_the_model():
         lv, basis = fmm.choose(*shape, variant="f16")
         assert lv in (0, 1, 2) and basis in ("strassen", "b323")
         assert basis == "strassen" or lv == 1
+
+
+def test_builtin_tables_per_variant():
+    """16-bit operands: one classical class (read in place, no pass); FP32 operands: the
+    split3 table (one level from 3072, two from 12288)."""
+    for v in ("bf16", "f16"):
+        t = fmm.tune_table(None, v)
+        assert t.count == 1 and t.levels[0] == 0
+        assert fmm.tune_select(20000, 20000, 20000, t) == (0, 0)
+    for v in ("split3", "plain_bf16"):
+        t = fmm.tune_table(None, v)
+        assert [t.levels[i] for i in range(t.count)] == [0, 1, 2]
+        assert fmm.tune_select(4096, 4096, 4096, t)[0] == 1
+    assert fmm.tune_select(20000, 20000, 20000)[0] == 2   # NULL table: the split3 default
