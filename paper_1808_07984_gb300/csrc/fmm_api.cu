@@ -888,6 +888,8 @@ fmm_status prepare_packed(const Plan& pl, int64_t m, int64_t n, int64_t k, float
   for (int r = 0; r < pl.R; ++r) live[r] = r;
   if (st == FMM_OK) st = fill_common(pp->c, pl, prods, live, m, n, alpha, C, ldc, dev, opt, job.grid);
   if (st != FMM_OK) return st;
+  // a classical product with beta = 0 writes every element of C exactly once: store it
+  pp->c.c_store = (pl.R == 1 && beta == 0.0f) ? 1 : 0;
   if (job.maxbits) {
     pp->c.maxbits_a = job.maxbits;
     pp->c.maxbits_b = job.maxbits + pl.R * pl.panels_a;
@@ -1037,12 +1039,12 @@ fmm_status launch_passes(const PackedJob& job, const DeviceInfo& dev, cudaStream
     cudaError_t e = launch_outer_maxbits(job.sa.X, job.m, job.k, job.sa.ldx, job.sb.X, job.n, job.sb.ldx,
                                          job.a_type, const_cast<unsigned*>(job.sa.row_maxbits),
                                          const_cast<unsigned*>(job.sb.col_maxbits), dev.sms, s);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && !(job.beta == 0.0f && job.params.c.c_store))
       e = job.beta == 0.0f ? launch_beta(job.C, job.m, job.n, job.ldc, 0.0f, dev.sms, s)
                            : launch_outer_rescale(job.C, job.m, job.n, job.ldc, job.sa.row_maxbits,
                                                   job.sb.col_maxbits, -1, job.beta, dev.sms, s);
     if (e != cudaSuccess) return cuda_fail(e, "outside-scaling passes");
-  } else if (job.beta != 1.0f) {
+  } else if (job.beta != 1.0f && !(job.has_work && job.params.c.c_store)) {
     PhaseScope ps(kPhaseBeta, s);
     cudaError_t e = launch_beta(job.C, job.m, job.n, job.ldc, job.beta, dev.sms, s);
     if (e != cudaSuccess) return cuda_fail(e, "beta pass");

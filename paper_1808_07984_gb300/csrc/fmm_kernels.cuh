@@ -135,6 +135,9 @@ struct CommonParams {
   int32_t deterministic;
   int32_t c_tma;     // write-back by TMA reductions through tmC (C rows 16-byte aligned)
   int32_t c_vec4;    // element-wise path: C rows are 16-byte aligned, vector reductions allowed
+  // one product and beta = 0: every output tile has exactly one item, whose write-back stores
+  // C instead of adding into it (no beta pass, no read of C)
+  int32_t c_store;
   // power-of-two scaling of the operand sums (FP16 variant), else null: panel maxima of the
   // A-operand sums per (product, tile row) and of the B-operand sums per (product, tile column)
   const unsigned int* maxbits_a;
@@ -468,6 +471,7 @@ __device__ __forceinline__ bool epilogue_role(const Work& work, uint8_t* epi_sme
     float* const Cm = p.C;
     const int64_t ldc = p.ldc;
     const bool c_tma = p.c_tma != 0;
+    const bool c_store = p.c_store != 0;
     const float alpha = p.alpha;
     const int tm_cta = PAIR ? 2 * tm + rank : tm;  // 128-row tile of this CTA
     const int row0 = tm_cta * kBM + q * 32;
@@ -519,7 +523,10 @@ __device__ __forceinline__ bool epilogue_role(const Work& work, uint8_t* epi_sme
             for (int d = 0; d < kMaxDest; ++d) {
               const DestEntry& de = pd.d[d];
               if (d >= pd.count || wneg(de) != sg) continue;
-              tma_reduce_add_2d(&tmC[de.block], smem_u32(sb), col0, row0);
+              if (c_store)
+                tma_store_2d(&tmC[de.block], smem_u32(sb), col0, row0);
+              else
+                tma_reduce_add_2d(&tmC[de.block], smem_u32(sb), col0, row0);
             }
             bulk_commit_group();
           }
@@ -539,7 +546,10 @@ __device__ __forceinline__ bool epilogue_role(const Work& work, uint8_t* epi_sme
             for (int i = 0; i < nrows; ++i) {
               const float x = *reinterpret_cast<const float*>(sb + i * 128 + (((lane >> 2) ^ (i & 7)) << 4) +
                                                               ((lane & 3) << 2));
-              red_add_global_f32(dst + static_cast<int64_t>(i) * ldc, x);
+              if (c_store)
+                dst[static_cast<int64_t>(i) * ldc] = x;
+              else
+                red_add_global_f32(dst + static_cast<int64_t>(i) * ldc, x);
             }
           }
         }

@@ -161,6 +161,12 @@ __device__ __forceinline__ void tma_reduce_add_2d(const void* map, uint32_t src,
       ::"l"(reinterpret_cast<uint64_t>(map)), "r"(src), "r"(x), "r"(y)
       : "memory");
 }
+// Plain TMA store of a staged tile (no read of the destination); clipped at the map's extent.
+__device__ __forceinline__ void tma_store_2d(const void* map, uint32_t src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%2, %3}], [%1];"
+               ::"l"(reinterpret_cast<uint64_t>(map)), "r"(src), "r"(x), "r"(y)
+               : "memory");
+}
 __device__ __forceinline__ void bulk_commit_group() {
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }

@@ -321,6 +321,29 @@ def test_classical_f16_in_place_large_magnitudes():
     np.testing.assert_array_equal(C.cpu().numpy(), oracle.classical(A, B))
 
 
+# ------------------------------------------------ classical products store C (beta = 0)
+@pytest.mark.parametrize("variant", ["split3", "bf16", "f16"])
+@pytest.mark.parametrize("pads", [(0, 0, 0), (0, 0, 1)])
+@pytest.mark.parametrize("m,n,k", [(300, 520, 200), (129, 257, 65), (1000, 1200, 300)])
+def test_classical_beta0_stores_c_without_reading_it(variant, pads, m, n, k):
+    """L = 0, beta = 0: each output tile has one item, whose write-back stores C (TMA store,
+    or plain stores when C rows are unaligned); NaN in C beforehand must not survive."""
+    C, C64, _, _ = run(m, n, k, 0, variant, dist="int", seed=67 * m + k, pads=pads, c_fill=float("nan"))
+    np.testing.assert_array_equal(C, C64)
+
+
+@pytest.mark.parametrize("opts", [{"deterministic": True}, {"cta_pair": False}, {"outer_scaling": True},
+                                  {"tile_n": 128}, {"fringe": "peel"}])
+def test_classical_beta0_store_under_options(opts):
+    C, C64, _, _ = run(700, 650, 300, 0, "split3", dist="int", seed=71, c_fill=float("nan"), **opts)
+    np.testing.assert_array_equal(C, C64)
+
+
+def test_classical_beta_nonzero_still_adds():
+    C, C64, An, Bn = run(640, 520, 256, 0, "split3", seed=73, alpha=0.5, beta=-1.25)
+    assert oracle.normwise_error(C, C64, An, Bn) <= tolerance("split3", 0, 256)
+
+
 # ------------------------------------------------ the <3,2,3> basis of rank 15 (Section 6)
 @pytest.mark.parametrize("opts", [{}, {"pads": (0, 0, 1)}, {"cta_pair": False}, {"fringe": "peel"},
                                   {"deterministic": True}, {"round_tiles": 1}, {"tile_n": 128},
