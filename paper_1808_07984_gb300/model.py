@@ -18,15 +18,17 @@ updates).  On GB300 the same three costs appear in different places:
     W        = ceil(items / workers)                        (items of the busiest CTA pair)
     items    = R * ceil(h_m / 256) * ceil(h_n / tile_n)     (R products of a basis)
     t_item_mma = terms * 2 * 256 * tile_n * h_k / (TC * tc_eff / workers)
+                 (times n128_slow for 128-wide tiles)
 
 BW and TC are the measured HBM copy bandwidth and burst BF16 tensor rate of the pool's
-GB300s; pack_eff, tc_eff, wb_cost, t_item_fix and t_launch are fitted to measured library
-calls (``fit``).  ``DEFAULT`` holds the fit to square, panel and rank-k sweeps of split3
-products measured on GB300 (mean absolute error 6.4 % over 58 calls).  pack_eff and tc_eff
-come out slightly above 1: the sum pass streams closer to the HBM peak than the copy that
-measured BW, and the UMMA rate of a kernel timed inside a sequence of calls matches the
-burst figure.  The largest products run below the model (up to 15 % at 20480): there the
-power cap lowers the SM clock, which the model does not represent.
+GB300s; pack_eff, tc_eff, wb_cost, t_item_fix, t_launch and n128_slow are fitted to measured
+library calls (``fit``).  ``DEFAULT`` holds the fit to square, panel and rank-k sweeps of
+split3 products measured on GB300 at the automatic tile width (mean absolute error 7.5 % over
+58 calls) together with calls at both tile widths (5.9 % over 30 calls).  pack_eff comes out
+at 1.0 (the sum pass streams at the measured copy bandwidth), tc_eff slightly above 1 (the
+UMMA rate of a kernel timed inside a sequence of calls matches the burst figure), and
+128-wide tiles run 25 % slower per flop.  The largest products run below the model (up to
+15 % at 20480): there the power cap lowers the SM clock, which the model does not represent.
 
 Used by ``autotune.autotune(prior="model")`` to rank the (levels, tile_n) candidates of each
 size so that only the most promising ones are measured, and (``best_basis``) to choose
@@ -40,9 +42,10 @@ import math
 
 GB300 = {"sms": 152, "hbm_gbs": 6777.0, "tc_tflops": 1934.1}
 
-# fitted (``fit``) to the 58 measured split3 calls in tuned/gb300_model_samples.json
-DEFAULT = {"pack_eff": 1.158, "tc_eff": 1.051, "wb_cost_ns_per_kb": 10.44, "t_item_fix_us": 0.0,
-           "t_launch_us": 5.93}
+# fitted (``fit``) to the 58 measured split3 calls in tuned/gb300_model_samples.json (automatic
+# tile width) and the 30 at explicit tile widths in tuned/gb300_tile_samples.json
+DEFAULT = {"pack_eff": 0.997, "tc_eff": 1.060, "wb_cost_ns_per_kb": 10.59, "t_item_fix_us": 0.0,
+           "t_launch_us": 5.57, "n128_slow": 1.249}
 
 _TERMS = {"split3": 3, "plain_bf16": 1, "bf16": 1, "f16": 1}
 # one-level bases: block grid (g_m, g_k, g_n), products R and nonzeros of W (C updates)
@@ -98,6 +101,10 @@ def predict(m: int, n: int, k: int, levels: int, variant: str = "split3", tile_n
     per_worker = -(-items // workers)
     tc = h["tc_tflops"] * 1e12 * p["tc_eff"] / workers
     t_item_mma = terms * 2.0 * 256 * tn * hk / tc
+    if tn == 128:
+        # 128-wide pair tiles: each CTA's UMMAs are N = 64 and every k-step loads the A panel
+        # for half the output of a 256-wide tile; measured slower per flop
+        t_item_mma *= p["n128_slow"]
     # wc: average W_C of a product (Strassen: 12 nonzeros of W over 7 products per level)
     wb_bytes_item = wc * 256 * tn * 4
     t_item = t_item_mma + p["t_item_fix_us"] * 1e-6 + wb_bytes_item / 1024.0 * p["wb_cost_ns_per_kb"] * 1e-9
@@ -128,19 +135,29 @@ def rank_candidates(d: int, variant: str = "split3", levels=(0, 1, 2), tiles=(12
     return sorted(cands, key=lambda c: predict(d, d, d, c[0], variant, tile_n=c[1], params=params)["ms"])
 
 
+def _pred_ms(sample, variant, params):
+    """Predicted ms of a sample (m, n, k, levels, ms) or (m, n, k, levels, tile_n, ms)."""
+    if len(sample) == 6:
+        m, n, k, L, tn, _ = sample
+    else:
+        (m, n, k, L, _), tn = sample, 0
+    return predict(m, n, k, L, variant, tile_n=tn, params=params)["ms"]
+
+
 def fit(samples, variant: str = "split3", start: dict | None = None, iters: int = 400) -> dict:
     """Least-squares fit of the model's free parameters to measured calls.
 
-    samples: iterable of (m, n, k, levels, measured_ms).  Minimises the mean squared log
-    ratio of predicted to measured time by coordinate search (no dependency beyond math)."""
+    samples: iterable of (m, n, k, levels, measured_ms), or (m, n, k, levels, tile_n,
+    measured_ms) for calls at an explicit tile width.  Minimises the mean squared log ratio of
+    predicted to measured time by coordinate search (no dependency beyond math)."""
     samples = list(samples)
     p = dict(DEFAULT, **(start or {}))
     keys = list(DEFAULT)
 
     def loss(q):
         s = 0.0
-        for m, n, k, L, ms in samples:
-            s += math.log(predict(m, n, k, L, variant, params=q)["ms"] / ms) ** 2
+        for smp in samples:
+            s += math.log(_pred_ms(smp, variant, q) / smp[-1]) ** 2
         return s / max(len(samples), 1)
 
     best = loss(p)
@@ -165,18 +182,20 @@ def fit(samples, variant: str = "split3", start: dict | None = None, iters: int 
 
 
 def mean_abs_error(samples, variant: str = "split3", params: dict | None = None) -> float:
-    """Mean |predicted - measured| / measured over (m, n, k, levels, measured_ms) samples."""
+    """Mean |predicted - measured| / measured over samples as ``fit`` takes them."""
     samples = list(samples)
-    err = [abs(predict(m, n, k, L, variant, params=params)["ms"] - ms) / ms for m, n, k, L, ms in samples]
+    err = [abs(_pred_ms(smp, variant, params) - smp[-1]) / smp[-1] for smp in samples]
     return sum(err) / max(len(err), 1)
 
 
 def load_samples(path: str):
-    """(m, n, k, levels, ms) samples of a calibration file."""
+    """Samples of a calibration file: (m, n, k, levels, ms), or (m, n, k, levels, tile_n, ms)
+    for a file of calls at explicit tile widths."""
     import json
     with open(path) as f:
         rec = json.load(f)
-    return [tuple(x) for x in rec["samples_m_n_k_levels_ms"]], rec.get("variant", "split3")
+    rows = rec["samples_m_n_k_levels_ms"] if "samples_m_n_k_levels_ms" in rec else rec["rows"]
+    return [tuple(x) for x in rows], rec.get("variant", "split3")
 
 
 if __name__ == "__main__":

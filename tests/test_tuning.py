@@ -178,3 +178,20 @@ def test_builtin_tables_per_variant():
         assert [t.levels[i] for i in range(t.count)] == [0, 1, 2]
         assert fmm.tune_select(4096, 4096, 4096, t)[0] == 1
     assert fmm.tune_select(20000, 20000, 20000)[0] == 2   # NULL table: the split3 default
+
+
+def test_model_tile_samples_and_ranking():
+    """Calls at explicit tile widths (tuned/gb300_tile_samples.json): the model fits them
+    within 10 %, and at every probe size its first-ranked candidate is the measured fastest
+    or within 5 % of it, so that autotune(prior="model") keeps the winner."""
+    path = os.path.join(os.path.dirname(model.__file__), "tuned", "gb300_tile_samples.json")
+    S, var = model.load_samples(path)
+    assert len(S) >= 30 and all(len(x) == 6 for x in S)
+    assert model.mean_abs_error(S, var) < 0.10
+    by_size = {}
+    for m, n, k, L, tn, ms in S:
+        if m in (2048, 4096, 8192, 16384) and m == n == k:
+            by_size.setdefault(m, {})[(L, tn)] = ms
+    for d, meas in by_size.items():
+        first = model.rank_candidates(d)[0]
+        assert meas[first] <= 1.05 * min(meas.values()), (d, first, meas)
