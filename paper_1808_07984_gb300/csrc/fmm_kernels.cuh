@@ -542,14 +542,22 @@ __device__ __forceinline__ bool epilogue_role(const Work& work, uint8_t* epi_sme
             if (col0 + lane >= de.cols) continue;
             float* dst = Cm + de.offset + static_cast<int64_t>(row0) * ldc + col0 + lane;
             const int nrows = min(32, de.rows - row0);
+            // two loops, not one with the branch inside: the reduction loop is the hot one
+            // (Strassen destinations), and a branch in it slows it measurably
+            if (c_store) {
 #pragma unroll 4
-            for (int i = 0; i < nrows; ++i) {
-              const float x = *reinterpret_cast<const float*>(sb + i * 128 + (((lane >> 2) ^ (i & 7)) << 4) +
-                                                              ((lane & 3) << 2));
-              if (c_store)
+              for (int i = 0; i < nrows; ++i) {
+                const float x = *reinterpret_cast<const float*>(sb + i * 128 + (((lane >> 2) ^ (i & 7)) << 4) +
+                                                                ((lane & 3) << 2));
                 dst[static_cast<int64_t>(i) * ldc] = x;
-              else
+              }
+            } else {
+#pragma unroll 4
+              for (int i = 0; i < nrows; ++i) {
+                const float x = *reinterpret_cast<const float*>(sb + i * 128 + (((lane >> 2) ^ (i & 7)) << 4) +
+                                                                ((lane & 3) << 2));
                 red_add_global_f32(dst + static_cast<int64_t>(i) * ldc, x);
+              }
             }
           }
         }
