@@ -12,7 +12,8 @@ updates).  On GB300 the same three costs appear in different places:
   through L2), which costs time the mainloop does not hide.
 
     T = t_beta + t_pack + t_tensor + launches * t_launch
-    t_beta   = 4 m n / BW                                   (C zeroed or scaled)
+    t_beta   = 4 m n / BW, levels > 0                       (C zeroed; a classical product
+                                                             stores C instead, so none)
     t_pack   = pack_bytes / (BW * pack_eff)
     t_tensor = W * (t_item_mma + t_item_fix + wb_bytes_item * wb_cost)
     W        = ceil(items / workers)                        (items of the busiest CTA pair)
@@ -23,8 +24,8 @@ updates).  On GB300 the same three costs appear in different places:
 BW and TC are the measured HBM copy bandwidth and burst BF16 tensor rate of the pool's
 GB300s; pack_eff, tc_eff, wb_cost, t_item_fix, t_launch and n128_slow are fitted to measured
 library calls (``fit``).  ``DEFAULT`` holds the fit to square, panel and rank-k sweeps of
-split3 products measured on GB300 at the automatic tile width (mean absolute error 7.5 % over
-58 calls) together with calls at both tile widths (5.9 % over 30 calls).  pack_eff comes out
+split3 products measured on GB300 at the automatic tile width (mean absolute error 6.9 % over
+58 calls) together with calls at both tile widths (6.6 % over 30 calls).  pack_eff comes out
 at 1.0 (the sum pass streams at the measured copy bandwidth), tc_eff slightly above 1 (the
 UMMA rate of a kernel timed inside a sequence of calls matches the burst figure), and
 128-wide tiles run 25 % slower per flop.  The largest products run below the model (up to
@@ -93,7 +94,7 @@ def predict(m: int, n: int, k: int, levels: int, variant: str = "split3", tile_n
     hm, hn, hk = block(m, levels, gm), block(n, levels, gn), block(k, levels, gk)
     tn = tile_n or auto_tile_n(m, n, levels, basis)
     bw = h["hbm_gbs"] * 1e9
-    t_beta = 4.0 * m * n / bw
+    t_beta = 4.0 * m * n / bw if levels > 0 else 0.0
     pack_bytes = (m * k + k * n) * e_in + R * (hm * hk + hk * hn) * 2 * arrays
     t_pack = pack_bytes / (bw * p["pack_eff"])
     workers = h["sms"] // 2
@@ -106,7 +107,9 @@ def predict(m: int, n: int, k: int, levels: int, variant: str = "split3", tile_n
         # for half the output of a 256-wide tile; measured slower per flop
         t_item_mma *= p["n128_slow"]
     # wc: average W_C of a product (Strassen: 12 nonzeros of W over 7 products per level)
-    wb_bytes_item = wc * 256 * tn * 4
+    # a classical product stores its tile (write only); Strassen products add into C (read and
+    # write of every destination tile)
+    wb_bytes_item = wc * 256 * tn * 4 * (0.5 if levels == 0 else 1.0)
     t_item = t_item_mma + p["t_item_fix_us"] * 1e-6 + wb_bytes_item / 1024.0 * p["wb_cost_ns_per_kb"] * 1e-9
     t_tensor = per_worker * t_item
     launches = 4
