@@ -146,7 +146,11 @@ size_t fmm_workspace_size_ex(int64_t m, int64_t n, int64_t k, int levels, int va
 /* C = alpha*A*B + beta*C with `levels` Strassen levels (0, 1 or 2) in the
  * arithmetic `variant` (fmm_variant).  A and B have the element type the
  * variant names; C is float32.  `workspace` (device, >= 256-byte aligned) must
- * hold fmm_workspace_size() bytes; it may be NULL when that size is 0. */
+ * hold fmm_workspace_size() bytes; it may be NULL when that size is 0.
+ * Classical products (levels 0): BF16 / FP16 operands whose base address and row
+ * stride are 16-byte aligned are read in place (the workspace then goes unused for
+ * them), and with beta = 0 the product is stored into C without a zeroing pass; C's
+ * old contents are never read when beta = 0, whatever the level count. */
 fmm_status fmm_gemm(int64_t m, int64_t n, int64_t k, float alpha,
                     const void* A, int64_t lda, const void* B, int64_t ldb,
                     float beta, float* C, int64_t ldc, int levels, int variant,
