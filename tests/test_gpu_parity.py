@@ -389,6 +389,37 @@ def test_b323_basis_sampled_rows_4096():
     assert oracle.normwise_error(C, C64, An, Bn) <= tolerance("split3", 1, 4096)
 
 
+def test_b323_deterministic_bitwise_reproducible():
+    m, n, k = 1900, 1700, 1100
+    outs = [run(m, n, k, 1, "split3", seed=75, deterministic=True, basis="b323")[0] for _ in range(3)]
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+def test_b323_outer_scaling_keeps_badly_scaled_rows_accurate():
+    """The <3,2,3> sums combine up to four blocks: without outside scaling badly scaled rows
+    and columns lose accuracy as with Strassen; with it every element keeps FP32-level accuracy
+    against its own scale."""
+    m = n = k = 600
+    A, B = synth.problem(m, n, k, 77, "badly_scaled")
+    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    C64 = oracle.classical(A, B)
+    scaled = fmm.gemm(Ad, Bd, levels=1, basis="b323", outer_scaling=True).cpu().numpy().astype(np.float64)
+    fmm.device_status()
+    assert _componentwise(scaled, C64, A, B) <= 1e-5
+
+
+def test_b323_f16_large_magnitudes_panel_scaled():
+    """FP16 operands near the top of the range: four-term sums would overflow FP16 unscaled;
+    the per-panel power-of-two scaling keeps them exact on these integers."""
+    m, n, k = 384, 390, 256
+    A = (synth.small_int((m, k), 7) * 8000.0).astype(np.float32)
+    B = (synth.small_int((k, n), 8) * 0.5).astype(np.float32)
+    C = fmm.gemm(torch.from_numpy(A).half().cuda(), torch.from_numpy(B).half().cuda(), levels=1,
+                 variant="f16", basis="b323")
+    fmm.device_status()
+    np.testing.assert_array_equal(C.cpu().numpy(), oracle.classical(A, B))
+
+
 def test_b323_basis_rejected_where_not_built():
     A = torch.zeros((64, 64), device="cuda")
     with pytest.raises(fmm.FmmError):
