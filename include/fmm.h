@@ -148,9 +148,9 @@ size_t fmm_workspace_size_ex(int64_t m, int64_t n, int64_t k, int levels, int va
  * variant names; C is float32.  `workspace` (device, >= 256-byte aligned) must
  * hold fmm_workspace_size() bytes; it may be NULL when that size is 0.
  * Classical products (levels 0): BF16 / FP16 operands whose base address and row
- * stride are 16-byte aligned are read in place (the workspace then goes unused for
- * them), and with beta = 0 the product is stored into C without a zeroing pass; C's
- * old contents are never read when beta = 0, whatever the level count. */
+ * stride are 16-byte aligned are read in place (when both are, no workspace is needed and
+ * `workspace` may be NULL), and with beta = 0 the product is stored into C without a
+ * zeroing pass; C's old contents are never read when beta = 0, whatever the level count. */
 fmm_status fmm_gemm(int64_t m, int64_t n, int64_t k, float alpha,
                     const void* A, int64_t lda, const void* B, int64_t ldb,
                     float beta, float* C, int64_t ldc, int levels, int variant,

@@ -702,6 +702,19 @@ fmm_status gemm_hybrid(const Plan& pl, int64_t m, int64_t n, int64_t k, float al
 }
 
 // Argument checks of one product (no CUDA calls).
+// TMA can read this operand in place: 16-byte aligned base and rows.
+bool tma_addressable(const Operand& o) {
+  return reinterpret_cast<uintptr_t>(o.X) % 16 == 0 && o.ld % 8 == 0;
+}
+
+// Operand "sums" of a classical product of 16-bit operands are the operands themselves; the
+// tensor-core kernel reads an operand in place when TMA can address it (prepare_packed), and
+// when both are read in place the product needs no workspace at all.
+bool in_place_operand(const Plan& pl, const Operand& o) {
+  return pl.algo == FMM_ALGO_PACKED && pl.L == 0 && pl.terms == 1 && o.type != kInF32 && !pl.outer_scaling &&
+         tma_addressable(o);
+}
+
 fmm_status validate_core(const Plan& pl, int64_t m, int64_t n, int64_t k, Operand a, Operand b,
                          float* C, int64_t ldc, void* ws, size_t ws_bytes) {
   const int64_t a_rows = pl.a_mn ? k : m, a_cols = pl.a_mn ? m : k;
@@ -719,11 +732,12 @@ fmm_status validate_core(const Plan& pl, int64_t m, int64_t n, int64_t k, Operan
     if (overlaps(C, c_bytes, a.X, a_span) || overlaps(C, c_bytes, b.X, b_span))
       return fail(FMM_ERR_ARG, "C overlaps an input operand");
   }
-  if (pl.ws > 0) {
-    if (!ws || ws_bytes < pl.ws)
-      return fail(FMM_ERR_WORKSPACE, "workspace of " + std::to_string(pl.ws) + " bytes required");
+  const size_t need = (in_place_operand(pl, a) && in_place_operand(pl, b)) ? 0 : pl.ws;
+  if (need > 0) {
+    if (!ws || ws_bytes < need)
+      return fail(FMM_ERR_WORKSPACE, "workspace of " + std::to_string(need) + " bytes required");
     if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(FMM_ERR_ALIGN, "workspace must be 256-byte aligned");
-    if (overlaps(C, c_bytes, ws, pl.ws)) return fail(FMM_ERR_ARG, "C overlaps the workspace");
+    if (overlaps(C, c_bytes, ws, need)) return fail(FMM_ERR_ARG, "C overlaps the workspace");
   }
   if (pl.algo == FMM_ALGO_FUSED && k > 0 &&
       (reinterpret_cast<uintptr_t>(a.X) % 16 != 0 || reinterpret_cast<uintptr_t>(b.X) % 16 != 0 ||
@@ -770,22 +784,20 @@ fmm_status prepare_packed(const Plan& pl, int64_t m, int64_t n, int64_t k, float
   if (!job.has_work) return FMM_OK;
   const int64_t a_rows = pl.a_mn ? k : m, a_cols = pl.a_mn ? m : k;
   const int64_t b_rows = pl.b_mn ? k : n, b_cols = pl.b_mn ? n : k;
+  // (no workspace at all when both operands are read in place: every region stays null)
   uint8_t* wsb = static_cast<uint8_t*>(ws);
-  uint16_t* a_hi = reinterpret_cast<uint16_t*>(wsb);
-  uint16_t* b_hi = reinterpret_cast<uint16_t*>(wsb + pl.a_bytes);
-  uint16_t* a_lo = pl.terms == 3 ? reinterpret_cast<uint16_t*>(wsb + pl.a_bytes + pl.b_bytes) : nullptr;
-  uint16_t* b_lo = pl.terms == 3 ? reinterpret_cast<uint16_t*>(wsb + 2 * pl.a_bytes + pl.b_bytes) : nullptr;
-  job.maxbits = pl.scaled ? reinterpret_cast<unsigned*>(wsb + pl.a_bytes + pl.b_bytes) : nullptr;
+  uint16_t* a_hi = wsb ? reinterpret_cast<uint16_t*>(wsb) : nullptr;
+  uint16_t* b_hi = wsb ? reinterpret_cast<uint16_t*>(wsb + pl.a_bytes) : nullptr;
+  uint16_t* a_lo = wsb && pl.terms == 3 ? reinterpret_cast<uint16_t*>(wsb + pl.a_bytes + pl.b_bytes) : nullptr;
+  uint16_t* b_lo = wsb && pl.terms == 3 ? reinterpret_cast<uint16_t*>(wsb + 2 * pl.a_bytes + pl.b_bytes) : nullptr;
+  job.maxbits = wsb && pl.scaled ? reinterpret_cast<unsigned*>(wsb + pl.a_bytes + pl.b_bytes) : nullptr;
   // With one product and no sums, the "sum" of a 16-bit operand is the operand itself: the
   // kernel's TMA reads it in place wherever TMA can address it (16-byte aligned base and
   // rows).  Exact FP16 values need no power-of-two panel scaling (their products are exact in
   // the FP32 accumulator), so the scaled variant drops its scaling when both operands are read
   // in place, and reads neither in place otherwise.
-  auto tma_ok = [](const Operand& o) {
-    return reinterpret_cast<uintptr_t>(o.X) % 16 == 0 && o.ld % 8 == 0;
-  };
-  job.direct_a = pl.L == 0 && pl.terms == 1 && a.type != kInF32 && !pl.outer_scaling && tma_ok(a);
-  job.direct_b = pl.L == 0 && pl.terms == 1 && b.type != kInF32 && !pl.outer_scaling && tma_ok(b);
+  job.direct_a = in_place_operand(pl, a);
+  job.direct_b = in_place_operand(pl, b);
   if (pl.scaled && !(job.direct_a && job.direct_b)) job.direct_a = job.direct_b = false;
   if (job.direct_a && job.direct_b) job.maxbits = nullptr;
 

@@ -308,6 +308,28 @@ def test_classical_16bit_float_in_place(variant, pads):
     assert oracle.normwise_error(C, C64, An, Bn) <= tolerance(variant, 0, 512)
 
 
+def test_classical_16bit_in_place_needs_no_workspace():
+    """Both operands read in place: the call runs with no workspace at all; an operand that
+    has to be converted (rows not 16-byte aligned) still asks for it (FMM_ERR_WORKSPACE)."""
+    m, n, k = 512, 384, 256
+    A, B = synth.problem(m, n, k, 79, "int")
+    L = fmm.load()
+    s = torch.cuda.current_stream().cuda_stream
+    for variant, dt in (("bf16", torch.bfloat16), ("f16", torch.float16)):
+        Ad = torch.from_numpy(A).to(dt).cuda()
+        Bd = torch.from_numpy(B).to(dt).cuda()
+        C = torch.full((m, n), float("nan"), device="cuda")
+        st = L.fmm_gemm(m, n, k, 1.0, Ad.data_ptr(), k, Bd.data_ptr(), n, 0.0, C.data_ptr(), n, 0,
+                        fmm.VARIANTS[variant], None, 0, s)
+        assert st == 0, fmm.load().fmm_last_error()
+        fmm.device_status()
+        np.testing.assert_array_equal(C.cpu().numpy(), oracle.classical(A, B))
+        Ap = torch.zeros((m, k + 1), dtype=dt, device="cuda")
+        st = L.fmm_gemm(m, n, k, 1.0, Ap.data_ptr(), k + 1, Bd.data_ptr(), n, 0.0, C.data_ptr(), n, 0,
+                        fmm.VARIANTS[variant], None, 0, s)
+        assert st == 4
+
+
 def test_classical_f16_in_place_large_magnitudes():
     """FP16 values near the top of the range: read in place without panel scaling, their
     products are exact in the FP32 accumulator."""
