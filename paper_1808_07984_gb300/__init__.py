@@ -229,7 +229,11 @@ def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
     if C.dtype != torch.float32 or not C.is_cuda or (C.numel() and C.stride(1) != 1):
         raise FmmError(1, "C must be a float32 CUDA tensor with contiguous rows")
     ws_need = workspace_size(m, n, k, levels, v, algo, tile_n, cta_pair, fringe, basis, outer_scaling)
-    if workspace is None and ws_need > 0:
+    # a classical product of 16-bit operands that TMA can read in place needs no workspace
+    in_place = (int(levels) == 0 and v in (VARIANTS["bf16"], VARIANTS["f16"]) and algo in ("auto", "packed")
+                and not outer_scaling
+                and all(X.data_ptr() % 16 == 0 and max(X.stride(0), 1) % 8 == 0 for X in (A, B)))
+    if workspace is None and ws_need > 0 and not in_place:
         workspace = torch.empty(ws_need, dtype=torch.uint8, device=A.device)
     ws_ptr = workspace.data_ptr() if workspace is not None else None
     ws_bytes = workspace.numel() if workspace is not None else 0
