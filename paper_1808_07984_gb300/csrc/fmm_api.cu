@@ -220,12 +220,6 @@ int64_t grid_block(int64_t d, int g) {
   return (h + 7) / 8 * 8;
 }
 
-int64_t block_size(int64_t d, int L) {
-  if (L == 0) return d;
-  const int64_t g = int64_t(1) << L;
-  const int64_t h = (d + g - 1) / g;
-  return (h + 7) / 8 * 8;
-}
 int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
 struct Plan {
