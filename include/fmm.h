@@ -118,7 +118,7 @@ typedef struct fmm_options {
                         before any stream capture begins. */
     int basis;       /* 0 = Strassen (Eq. 3); 1 = the Strassen-Winograd variant written per
                         product (14 nonzeros in each of U, V, W; levels <= 1, packed or fused);
-                        2 = a <3,2,3> basis of rank 15 (levels <= 1, packed; A split into
+                        2 = a <3,2,3> basis of rank 15 (levels <= 1, packed or fused; A split into
                         3 x 2 blocks, B into 2 x 3, C into 3 x 3; 15 products instead of the
                         classical 18, so 5/6 of the classical MMA work against Strassen's 7/8;
                         no pipelining).  Bases other than 0 form their operand sums in one

@@ -200,7 +200,7 @@ def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
     tensor-core kernel one top-level product at a time, or not.  ``fringe``: "pad" (zero
     padding of the blocks) or "peel" (Strassen on the evenly splitting core plus classical
     strip products).  ``basis``: "strassen", "winograd" (one level) or "b323"
-    (the <3,2,3> basis of rank 15, one level, packed algorithm).  ``deterministic``:
+    (the <3,2,3> basis of rank 15, one level, packed or fused algorithm).  ``deterministic``:
     ownership mode, bitwise reproducible results.  ``outer_scaling``: exact power-of-two
     scaling of the rows of A and columns of B around the product (badly scaled inputs).
     ``levels="auto"``: the level count and basis the analytic model (``model.py``) predicts

@@ -285,8 +285,8 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
     return fail(FMM_ERR_UNSUPPORTED, "the Winograd basis is built for one level (packed or fused)");
   if (basis == kBasis323 && levels > 1)
     return fail(FMM_ERR_UNSUPPORTED, "the <3,2,3> basis is built for one level");
-  if (basis == kBasis323 && levels == 1 && on_chip)
-    return fail(FMM_ERR_UNSUPPORTED, "the <3,2,3> basis is built for the packed algorithm");
+  if (basis == kBasis323 && levels == 1 && pl.algo == FMM_ALGO_HYBRID)
+    return fail(FMM_ERR_UNSUPPORTED, "the hybrid algorithm is a two-level Strassen scheme");
   if (basis == kBasis323 && levels == 1 && opt && opt->pipeline == 2)
     return fail(FMM_ERR_UNSUPPORTED, "the <3,2,3> basis forms its sums in one pass (no pipelining)");
   pl.basis = levels == 0 ? kBasisStrassen : basis;
@@ -511,17 +511,21 @@ fmm_status gemm_fused(const Plan& pl, int64_t m, int64_t n, int64_t k, float alp
                       int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc,
                       const DeviceInfo& dev, const fmm_options* opt, cudaStream_t s) {
   const std::vector<Product> prods = make_products(pl.L, pl.basis);
-  const int g = 1 << pl.L;
+  // A blocks a = i * g_k + l (g_m x g_k grid), B blocks b = l * g_n + j (g_k x g_n grid)
+  const int na_blk = pl.gm * pl.gk, nb_blk = pl.gk * pl.gn;
+  if (na_blk > kMaxFusedSources || nb_blk > kMaxFusedSources)
+    return fail(FMM_ERR_UNSUPPORTED, "too many source blocks for the fused kernel");
   FusedParams* fp = new FusedParams;
   std::memset(fp, 0, sizeof(FusedParams));
   fmm_status st = FMM_OK;
-  std::vector<bool> a_live(g * g, false), b_live(g * g, false);
-  for (int b = 0; b < g * g && st == FMM_OK; ++b) {
-    const int bi = b / g, bj = b % g;
+  std::vector<bool> a_live(na_blk, false), b_live(nb_blk, false);
+  for (int b = 0; b < std::max(na_blk, nb_blk) && st == FMM_OK; ++b) {
     const float* Af = static_cast<const float*>(A);
     const float* Bf = static_cast<const float*>(B);
-    // A block (bi, bj): rows of m, columns of k
-    const int64_t ar = block_extent(m, pl.hm, bi), ac = block_extent(k, pl.hk, bj);
+    // A block b = (bi, bj): rows of m, columns of k
+    const int bi = b / pl.gk, bj = b % pl.gk;
+    const int64_t ar = b < na_blk ? block_extent(m, pl.hm, bi) : 0;
+    const int64_t ac = b < na_blk ? block_extent(k, pl.hk, bj) : 0;
     if (ar > 0 && ac > 0) {
       const cuuint64_t dims[2] = {static_cast<cuuint64_t>(ac), static_cast<cuuint64_t>(ar)};
       const cuuint64_t strides[1] = {static_cast<cuuint64_t>(lda * 4)};
@@ -534,15 +538,17 @@ fmm_status gemm_fused(const Plan& pl, int64_t m, int64_t n, int64_t k, float alp
       if (cr != CUDA_SUCCESS) st = fail(FMM_ERR_CUDA, "cuTensorMapEncodeTiled (A block) failed");
       a_live[b] = true;
     }
-    // B block (bi, bj): rows of k, columns of n
-    const int64_t br = block_extent(k, pl.hk, bi), bc = block_extent(n, pl.hn, bj);
+    // B block b = (bl, bn): rows of k, columns of n
+    const int bl = b / pl.gn, bn = b % pl.gn;
+    const int64_t br = b < nb_blk ? block_extent(k, pl.hk, bl) : 0;
+    const int64_t bc = b < nb_blk ? block_extent(n, pl.hn, bn) : 0;
     if (st == FMM_OK && br > 0 && bc > 0) {
       const cuuint64_t dims[2] = {static_cast<cuuint64_t>(bc), static_cast<cuuint64_t>(br)};
       const cuuint64_t strides[1] = {static_cast<cuuint64_t>(ldb * 4)};
       const cuuint32_t box[2] = {static_cast<cuuint32_t>(kFusedTileN), 32};
       const cuuint32_t estr[2] = {1, 1};
       CUresult cr = g_encode(&fp->tmSB[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
-                             const_cast<float*>(Bf + (bi * pl.hk * ldb + bj * pl.hn)), dims, strides,
+                             const_cast<float*>(Bf + (bl * pl.hk * ldb + bn * pl.hn)), dims, strides,
                              box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       if (cr != CUDA_SUCCESS) st = fail(FMM_ERR_CUDA, "cuTensorMapEncodeTiled (B block) failed");
@@ -554,6 +560,10 @@ fmm_status gemm_fused(const Plan& pl, int64_t m, int64_t n, int64_t k, float alp
   for (int r = 0; r < pl.R && st == FMM_OK; ++r) {
     ProductSrc ps;
     std::memset(&ps, 0, sizeof ps);
+    if (prods[r].a.size() > static_cast<size_t>(kMaxDest) || prods[r].b.size() > static_cast<size_t>(kMaxDest)) {
+      st = fail(FMM_ERR_UNSUPPORTED, "a product combines more source blocks than the fused kernel takes");
+      break;
+    }
     for (const Term& t : prods[r].a)
       if (a_live[t.block]) {
         ps.a_block[ps.na] = static_cast<int8_t>(t.block);

@@ -144,7 +144,7 @@ def test_option_errors_need_no_gpu(lib):
     assert _call_ex(lib, algo=3, levels=1) == 3             # hybrid: two levels
     assert _call_ex(lib, algo=9) == 3
     assert _call_ex(lib, levels=2, basis=2) == 3            # <3,2,3>: one level
-    assert _call_ex(lib, algo=2, basis=2) == 3              # <3,2,3>: packed only
+    assert _call_ex(lib, algo=3, levels=2, basis=2) == 3    # <3,2,3>: no hybrid (two-level) form
     assert _call_ex(lib, basis=2, pipeline=2) == 3          # <3,2,3>: one table pass
 
 

@@ -447,7 +447,27 @@ def test_b323_basis_rejected_where_not_built():
     with pytest.raises(fmm.FmmError):
         fmm.gemm(A, A, levels=2, basis="b323")
     with pytest.raises(fmm.FmmError):
-        fmm.gemm(A, A, levels=1, basis="b323", algo="fused")
+        fmm.gemm(A, A, levels=2, basis="b323", algo="hybrid")
+
+
+@pytest.mark.parametrize("opts", [{}, {"cta_pair": False}, {"deterministic": True}, {"pads": (0, 0, 1)}])
+@pytest.mark.parametrize("m,n,k", [(300, 520, 200), (129, 257, 65), (1000, 1200, 300), (7, 5, 3)])
+def test_b323_fused_bit_exact(m, n, k, opts):
+    """The <3,2,3> basis with its operand sums formed on chip (fused kernel): up to four FP32
+    source tiles per operand, fifteen products, destinations in the 3 x 3 C grid."""
+    o = dict(opts)
+    pads = o.pop("pads", (0, 0, 0))
+    pads = (_pad4(k), _pad4(n), pads[2])
+    C, C64, _, _ = run(m, n, k, 1, "split3", dist="int", seed=81 * m + k, basis="b323", algo="fused",
+                       pads=pads, **o)
+    np.testing.assert_array_equal(C, C64)
+
+
+@pytest.mark.parametrize("variant", ["split3", "plain_bf16"])
+def test_b323_fused_float(variant):
+    C, C64, An, Bn = run(600, 520, 400, 1, variant, seed=83, basis="b323", algo="fused",
+                         pads=(_pad4(400), _pad4(520), 0))
+    assert oracle.normwise_error(C, C64, An, Bn) <= tolerance(variant, 1, 400)
 
 
 @pytest.mark.parametrize("m,n,k", [(3000, 3000, 3000), (1200, 900, 150), (2304, 2304, 2304)])
