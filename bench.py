@@ -33,7 +33,7 @@ import synth  # noqa: E402
 
 METRIC = "effective TFLOPS (2mnk/t) Strassen vs own classical GEMM on 1 GB300 at stated FP64 error"
 UNIT = "TFLOPS"
-FALLBACK_PEAK_TFLOPS = 1700.0  # sustained bf16, one earlier measurement on a GB300
+FALLBACK_PEAK_TFLOPS = 1900.0  # burst bf16, one earlier measurement on a GB300
 
 
 def parse_args():
@@ -56,7 +56,60 @@ def parse_args():
     ap.add_argument("--no-classical", action="store_true")
     ap.add_argument("--no-fused", action="store_true",
                     help="skip the measurement of the on-chip-sums (fused) algorithm")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the short measurements of the other configurations")
+    ap.add_argument("--extra-steps", type=int, default=3)
     return ap.parse_args()
+
+
+DTYPES = {"split3": "bf16x3", "plain_bf16": "bf16", "bf16": "bf16", "f16": "f16"}
+TERMS = {"split3": 3, "plain_bf16": 1, "bf16": 1, "f16": 1}
+
+
+def mma_flops(m, n, k, levels, variant, basis="strassen"):
+    """Algorithmic tensor-core work of one product: each level of a basis with R products on
+    a g_m x g_k x g_n block grid does R / (g_m g_k g_n) of the classical 2mnk (Strassen 7/8,
+    <3,2,3> 15/18), times the tensor-core terms of the arithmetic (split3: 3)."""
+    f = 1.0
+    if levels >= 1:
+        f = 15.0 / 18.0 if basis == "b323" else (7.0 / 8.0) ** levels
+    return f * 2.0 * m * n * k * TERMS[variant]
+
+
+def kernel_name(algo):
+    return "fmm_fused_kernel" if algo in ("fused", "hybrid") else "fmm_packed_kernel"
+
+
+def tensor_peak(peaks):
+    """(burst peak, sustained peak, source) in TFLOP/s.  Every timed region of this benchmark
+    lasts well under a second, so the burst figure is the denominator; the sustained one
+    (seconds of back-to-back GEMMs under the power cap, at a lower clock) is reported beside it."""
+    if peaks and "bf16_tflops" in peaks:
+        return (float(peaks["bf16_tflops"]), float(peaks.get("bf16_tflops_sustained", 0.0)) or None,
+                "measured (burst bf16)")
+    return FALLBACK_PEAK_TFLOPS, None, "fallback"
+
+
+def timed_call(fmm, torch, stream, fn, steps, warmup):
+    """Device time per call of fn() (CUDA events on `stream`) and the library's phase
+    profile {phase: (ms, launches)} over the timed calls."""
+    for _ in range(warmup):
+        fn()
+    fmm.device_status()
+    torch.cuda.synchronize()
+    fmm.profile_read()
+    fmm.profile_enable(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fmm.profile_enable(False)
+    prof = fmm.profile_read()
+    fmm.device_status()
+    return e0.elapsed_time(e1) / steps, prof
 
 
 def workload_name(a, k):
@@ -190,6 +243,180 @@ def job_value(world, flops_per_rank, ms):
 def rank_problem(n, k, rank):
     """The seeded synthetic problem of one rank (replicas: a different problem per rank)."""
     return synth.uniform((n, k), 1234 + 2 * rank), synth.uniform((k, n), 1235 + 2 * rank)
+
+
+# ------------------------------------------------------------- other configurations
+def sampled_error(oracle, C_d, A, B, rows, a_code=None, b_code=None):
+    """Normwise FP64 error of the sampled rows of C_d (A, B: host arrays, FP32 or 16-bit codes)."""
+    import torch
+    C_s = C_d[torch.from_numpy(rows).to(C_d.device)].cpu().numpy()
+    kw = {}
+    if a_code is not None:
+        kw = {"a_code": a_code, "b_code": b_code}
+    C64 = oracle.classical(A, B, rows=rows, **kw)
+    Af = A.astype(np.float64) if a_code is None else None
+    if a_code is not None:
+        import torch as _t
+        conv = (lambda X: _t.from_numpy(X.view(np.int16)).view(_t.bfloat16 if a_code == oracle.ORC_BF16
+                                                                 else _t.float16).float().numpy())
+        Af, Bf = conv(A).astype(np.float64), conv(B).astype(np.float64)
+    else:
+        Bf = B.astype(np.float64)
+    return oracle.normwise_error(C_s, C64, np.linalg.norm(Af[rows]), np.linalg.norm(Bf))
+
+
+def run_extras(a, fmm, torch, dev, stream, peak, peak_src):
+    """Short device-timed runs of the other configurations, each against the classical
+    product of the same arithmetic, with its sampled FP64 error and its tensor-core kernel's
+    roofline.  Inputs are synthetic and seeded (shapes and distributions of each config)."""
+    import oracle
+    steps, warm = max(1, a.extra_steps), 1
+    out = []
+
+    def entry(workload, cfg, m, n, k, runs, flops, err_of, comparator_levels=0):
+        """runs: {label: (levels, variant, basis, fn)}; the first label is the Strassen choice."""
+        e = {"config": dict(workload=workload, m=m, n=n, k=k, **cfg)}
+        for label, (lv, variant, basis, fn) in runs.items():
+            ms, prof = timed_call(fmm, torch, stream, fn, steps, warm)
+            ker_ms = prof["tensor"][0] / steps
+            mma = mma_flops(m, n, k, lv, variant, basis) * (flops / (2.0 * m * n * k))
+            r = {"levels": lv, "variant": variant, "basis": basis,
+                 "value": flops / (ms * 1e-3) * 1e-12, "ms_per_step": ms,
+                 "roofline": {"bound": "tensor", "kernel": "fmm_packed_kernel",
+                              "kernel_ms_per_step": ker_ms,
+                              "launches_per_step": prof["tensor"][1] / steps,
+                              "achieved": mma / (ker_ms * 1e-3) * 1e-12 if ker_ms > 0 else None,
+                              "peak": peak, "unit": "TFLOP/s", "peak_source": peak_src}}
+            if ker_ms > 0:
+                r["roofline"]["frac"] = r["roofline"]["achieved"] / peak
+            fn()
+            torch.cuda.synchronize()
+            r["fp64_normwise_err_sampled"] = err_of()
+            e[label] = r
+        labels = list(runs)
+        if "classical" in e and labels[0] != "classical":
+            e["speedup_vs_classical"] = e[labels[0]]["value"] / e["classical"]["value"]
+        out.append(e)
+
+    def split3_runs(Ad, Bd, Cd, ws, choices, variant="split3"):
+        runs = {}
+        for label, lv, basis in choices:
+            runs[label] = (lv, variant, basis,
+                           (lambda lv=lv, basis=basis: fmm.gemm(Ad, Bd, Cd, 1.0, 0.0, levels=lv, variant=variant,
+                                                               basis=basis, workspace=ws, stream=stream)))
+        return runs
+
+    def ws_for(m, n, k, choices, variant="split3"):
+        need = max(fmm.workspace_size(m, n, k, lv, variant, basis=basis) for _, lv, basis in choices)
+        return torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+
+    # rank-k: m = n = 16384, k in {512, 1024, 2048}, uniform[-1, 1], split3
+    for k in (512, 1024, 2048):
+        m = n = 16384
+        A, B = synth.uniform((m, k), 1300 + k), synth.uniform((k, n), 1301 + k)
+        Ad, Bd = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+        Cd = torch.empty((m, n), dtype=torch.float32, device=dev)
+        ch = [("strassen_L1", 1, "strassen"), ("classical", 0, "strassen")]
+        ws = ws_for(m, n, k, ch)
+        rows = np.unique(synth.rng(k).integers(0, m, size=8))
+        entry(f"strassen-L1-split3-rank-k-m{m}-n{n}-k{k}", {"variant": "split3",
+              "inputs": "uniform[-1,1] float32, seeded"}, m, n, k, split3_runs(Ad, Bd, Cd, ws, ch),
+              2.0 * m * n * k, lambda: sampled_error(oracle, Cd, A, B, rows))
+        del Ad, Bd, Cd, ws
+
+    # <3,2,3> basis at 12288^3 (blocks divide into whole 256-row tiles)
+    m = n = k = 12288
+    A, B = synth.uniform((m, k), 1400), synth.uniform((k, n), 1401)
+    Ad, Bd = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+    Cd = torch.empty((m, n), dtype=torch.float32, device=dev)
+    ch = [("b323_L1", 1, "b323"), ("strassen_L1", 1, "strassen"), ("classical", 0, "strassen")]
+    ws = ws_for(m, n, k, ch)
+    rows = np.unique(synth.rng(12288).integers(0, m, size=8))
+    entry("b323-L1-split3-square-m12288-n12288-k12288", {"variant": "split3",
+          "inputs": "uniform[-1,1] float32, seeded"}, m, n, k, split3_runs(Ad, Bd, Cd, ws, ch),
+          2.0 * m * n * k, lambda: sampled_error(oracle, Cd, A, B, rows))
+    del Ad, Bd, Cd, ws, A, B
+
+    # C5: 30001 x 29999 x 4097, N(0, 1), tight (odd) leading dimensions
+    m, n, k = 30001, 29999, 4097
+    A, B = synth.gaussian((m, k), 1500), synth.gaussian((k, n), 1501)
+    Ad, Bd = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+    Cd = torch.empty((m, n), dtype=torch.float32, device=dev)
+    rows = np.unique(np.concatenate([[0, m - 1], synth.rng(30001).integers(0, m, size=6)]))
+    for variant in ("split3", "plain_bf16"):
+        ch = [("strassen_L2", 2, "strassen"), ("strassen_L1", 1, "strassen"), ("classical", 0, "strassen")]
+        ws = ws_for(m, n, k, ch, variant)
+        entry(f"strassen-{variant}-odd-m{m}-n{n}-k{k}", {"variant": variant, "lda": k, "ldb": n, "ldc": n,
+              "inputs": "N(0,1) float32, seeded; tight (odd) leading dimensions"}, m, n, k,
+              split3_runs(Ad, Bd, Cd, ws, ch, variant), 2.0 * m * n * k,
+              lambda: sampled_error(oracle, Cd, A, B, rows))
+        del ws
+    del Ad, Bd, Cd, A, B
+
+    # C3: BF16 linear layer, forward C = A B and backward dA = dC B^T, dB = A^T dC
+    m, k, n = 8192, 4096, 4096
+    A = synth.gaussian((m, k), 1600)
+    B = synth.gaussian((k, n), 1601)
+    G = synth.gaussian((m, n), 1602)
+    Ad = torch.from_numpy(A).to(dev).to(torch.bfloat16)
+    Bd = torch.from_numpy(B).to(dev).to(torch.bfloat16)
+    Gd = torch.from_numpy(G).to(dev)
+    Cd = torch.empty((m, n), dtype=torch.float32, device=dev)
+    runs = {}
+    for label, lv in (("strassen_L1", 1), ("strassen_L2", 2), ("classical", 0)):
+        wsf = torch.empty(max(fmm.workspace_size(m, n, k, lv, "bf16"), 256), dtype=torch.uint8, device=dev)
+        wsb = torch.empty(max(fmm.workspace_size_backward(m, n, k, lv, "bf16"), 256), dtype=torch.uint8,
+                          device=dev)
+
+        def layer(lv=lv, wsf=wsf, wsb=wsb):
+            fmm.gemm(Ad, Bd, Cd, 1.0, 0.0, levels=lv, variant="bf16", workspace=wsf, stream=stream)
+            fmm.gemm_backward(Ad, Bd, Gd, levels=lv, variant="bf16", workspace=wsb, stream=stream)
+        runs[label] = (lv, "bf16", "strassen", layer)
+    Ab = Ad.cpu().view(torch.int16).numpy().view(np.uint16)
+    Bb = Bd.cpu().view(torch.int16).numpy().view(np.uint16)
+    rows = np.unique(synth.rng(8192).integers(0, m, size=6))
+    entry(f"strassen-bf16-linear-fwd-bwd-m{m}-k{k}-n{n}", {"variant": "bf16",
+          "step": "forward C = A B, backward dA = dC B^T and dB = A^T dC (three products)",
+          "inputs": "N(0,1) cast to BF16, dC N(0,1) float32, seeded"}, m, n, k, runs,
+          3 * 2.0 * m * n * k,
+          lambda: sampled_error(oracle, Cd, Ab, Bb, rows, oracle.ORC_BF16, oracle.ORC_BF16))
+    del Ad, Bd, Gd, Cd, runs
+
+    # C4: 256 uneven FP16 products (multiples of 256 in [1024, 8192]) in one persistent
+    # launch per tile width, replayed from a CUDA graph; the built-in FP16 table
+    shapes = synth.uneven_batch(256, seed=2024)
+    g = torch.Generator(device=dev).manual_seed(2025)
+    As = [(torch.rand((mm, kk), device=dev, generator=g) * 2 - 1).half() for mm, nn, kk in shapes]
+    Bs = [(torch.rand((kk, nn), device=dev, generator=g) * 2 - 1).half() for mm, nn, kk in shapes]
+    Cs = [torch.empty((mm, nn), dtype=torch.float32, device=dev) for mm, nn, kk in shapes]
+    plan = fmm.BatchedPlan(As, Bs, Cs, variant="f16")
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        plan.execute(side)
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(graph):
+        plan.execute()
+    flops = sum(2.0 * mm * nn * kk for mm, nn, kk in shapes)
+    ms, prof = timed_call(fmm, torch, stream, graph.replay, steps, warm)
+    levels_used = sorted({fmm.tune_select(mm, nn, kk, fmm.tune_table(None, "f16"))[0] for mm, nn, kk in shapes})
+    i0 = 0
+    mm, nn, kk = shapes[i0]
+    rsel = np.unique(synth.rng(2026).integers(0, mm, size=4))
+    Ab = As[i0].cpu().view(torch.int16).numpy().view(np.uint16)
+    Bb = Bs[i0].cpu().view(torch.int16).numpy().view(np.uint16)
+    out.append({"config": {"workload": "batched-f16-256-uneven-1024to8192-graph", "problems": 256,
+                           "variant": "f16", "levels_used": levels_used,
+                           "inputs": "uniform[-1,1] FP16, m, n, k uniform over multiples of 256 in [1024, 8192]"},
+                "batched": {"value": flops / (ms * 1e-3) * 1e-12, "ms_per_step": ms,
+                            "fp64_normwise_err_sampled_problem0": sampled_error(
+                                oracle, Cs[i0], Ab, Bb, rsel, oracle.ORC_F16, oracle.ORC_F16)}})
+    plan.close()
+    del As, Bs, Cs, graph
+    torch.cuda.empty_cache()
+    return out
 
 
 # ------------------------------------------------------------- oracle arm
@@ -451,27 +678,23 @@ def main():
             C_sf, C64, np.linalg.norm(A[rows].astype(np.float64)), np.linalg.norm(B.astype(np.float64)))
 
     # ---- roofline of the dominant kernel (the tensor-core kernel)
-    terms = 3 if a.variant == "split3" else 1
     # per launch of the tensor-core kernel (a pipelined product launches it once per
     # top-level product, each with 1/7 of the work)
     launches_per_step = max(prof["tensor"][1], 1) / a.steps
     ker_ms = prof["tensor"][0] / max(prof["tensor"][1], 1)
-    mma_flops = (7.0 / 8.0) ** a.levels * flops * terms / launches_per_step
-    achieved = mma_flops / (ker_ms * 1e-3) * 1e-12
+    per_launch = mma_flops(m, n, k, a.levels, a.variant) / launches_per_step
+    achieved = per_launch / (ker_ms * 1e-3) * 1e-12
     peaks = load_peaks()
-    if peaks and "bf16_tflops_sustained" in peaks:
-        peak, peak_src = float(peaks["bf16_tflops_sustained"]), "measured (sustained bf16)"
-    else:
-        peak, peak_src = FALLBACK_PEAK_TFLOPS, "fallback"
-    burst = float(peaks["bf16_tflops"]) if peaks and "bf16_tflops" in peaks else None
+    peak, sustained, peak_src = tensor_peak(peaks)
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": recorded_traffic(workload_name(a, k)),
-                "frac_of_burst_peak": (achieved / burst) if burst else None,
+                "frac_of_sustained_peak": (achieved / sustained) if sustained else None,
                 "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
-                "peak_source": peak_src,
-                "kernel": "fmm_packed_kernel", "kernel_ms": ker_ms,
+                "peak_source": peak_src + " of measured; timed region " +
+                               f"{a.steps * ms / 1e3:.2f} s",
+                "kernel": kernel_name(a.algo), "kernel_ms": ker_ms,
                 "launches_per_step": launches_per_step,
-                "algorithmic_flops_per_launch": mma_flops}
+                "algorithmic_flops_per_launch": per_launch}
     # ---- roofline of the HBM-bound passes: the operand-sum passes (A and B) and the beta pass
     hbm = float(peaks["hbm_gbs"]) if peaks and "hbm_gbs" in peaks else None
     in_b = 2 if a.variant in ("bf16", "f16") else 4
@@ -485,7 +708,9 @@ def main():
     passes = {
         "operand_sums": {"bound": "hbm", "algorithmic_bytes_per_step": sum_bytes, "ms_per_step": pack_ms,
                          "achieved_gbs": sum_bytes / (pack_ms * 1e-3) * 1e-9 if pack_ms > 0 else None},
-        "beta": {"bound": "hbm", "kind": "C zeroed by cudaMemsetAsync (beta = 0)",
+        "beta": {"bound": "hbm",
+                 "kind": ("none: the classical product stores C (beta = 0)" if a.levels == 0 and
+                          a.algo in ("auto", "packed") else "C zeroed by cudaMemsetAsync (beta = 0)"),
                  "algorithmic_bytes_per_step": 4 * m * n, "ms_per_step": beta_ms,
                  "achieved_gbs": 4 * m * n / (beta_ms * 1e-3) * 1e-9 if beta_ms > 0 else None},
         "peak_gbs": hbm, "peak_source": "measured (HBM copy)" if hbm else None,
@@ -497,6 +722,16 @@ def main():
     # cudaMemsetAsync, not a kernel of ours
     gpu_launches = int(prof["pack"][1] + prof["tensor"][1])
 
+    # ---- the other configurations, short runs (one GPU only)
+    extra = None
+    if not a.no_extra and world == 1:
+        del A_d, B_d, C_d, ws
+        torch.cuda.empty_cache()
+        try:
+            extra = run_extras(a, fmm, torch, dev, stream, peak, peak_src + " of measured")
+        except Exception as exc:  # noqa: BLE001 - reported in the line, the headline stands
+            extra = {"error": f"{type(exc).__name__}: {exc}"}
+
     cpu = None
     if not a.no_cpu_baseline:
         v, dt, nrows, cores = cpu_oracle_rate(A, B, a.cpu_seconds)
@@ -507,7 +742,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
+        "vs_baseline": None, "dtype": DTYPES[a.variant], "data": "synthetic",
         "config": config_dict(a, k, {"parallelism": f"replicas{world}" if world > 1 else "single"}),
         "fp64_normwise_err_sampled": err,
         "classical": classical,
@@ -520,6 +755,7 @@ def main():
         "e2e": e2e,
         "clocks": clk,
         "gpu_launches": gpu_launches,
+        "extra": extra,
     }
     print(json.dumps(line), flush=True)
     print(f"[bench] {workload_name(a, k)}: {value:.1f} eff TFLOPS ({ms:.2f} ms/step), "

@@ -167,9 +167,11 @@ fmm_status fmm_gemm_ex(int64_t m, int64_t n, int64_t k, float alpha,
  * memory (for example a plug-in whose host application owns every device allocation,
  * or a latency-critical caller that must not call cudaMalloc / cudaFree because they
  * can synchronise the device).  The operand sums go to a scratch array built into
- * the library: 64 MiB per GPU, held from library load until process exit.  Problems
- * whose fmm_workspace_size() exceeds 64 MiB are rejected with FMM_ERR_WORKSPACE;
- * no device memory is allocated.  All calls on a device share that one scratch and
+ * the library: 64 MiB per GPU, held from library load until process exit.  A problem
+ * that needs more scratch than that is rejected with FMM_ERR_WORKSPACE; a product that
+ * needs none at all (a classical product whose 16-bit operands the tensor cores read
+ * in place) runs whatever fmm_workspace_size() estimates for it.  No device memory is
+ * allocated.  All calls on a device share that one scratch and
  * it keeps the previous call's contents (nothing in it needs to start at zero):
  * calls whose work overlaps on the GPU race on it and must be serialised by the
  * caller.  The first call on each device looks up the scratch's device address;

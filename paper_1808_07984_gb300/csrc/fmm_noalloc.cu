@@ -8,8 +8,11 @@
 // this library's device image, so no device memory is allocated by the call.
 //
 // Limits and sharing rules (also stated in include/fmm.h):
-//  * the scratch holds kNoallocScratchBytes (64 MiB); problems whose workspace
-//    (fmm_workspace_size) is larger are rejected with FMM_ERR_WORKSPACE;
+//  * the scratch holds kNoallocScratchBytes (64 MiB); problems that need a larger
+//    workspace are rejected with FMM_ERR_WORKSPACE.  fmm_workspace_size does not know
+//    the operands' addresses, so for a classical product of 16-bit operands it counts a
+//    conversion workspace that aligned operands (read in place) do not need: such a call
+//    is tried without any workspace first;
 //  * every GPU on which the library is loaded keeps this array until the process exits;
 //  * all calls share the one array per device, and it keeps whatever the previous call
 //    left in it; calls whose work overlaps on the GPU (for example on two streams at once)
@@ -53,6 +56,12 @@ extern "C" fmm_status fmm_gemm_noalloc(int64_t m, int64_t n, int64_t k, float al
                     stream);
   }
   if (need > kNoallocScratchBytes) {
+    // The estimate may count a workspace this call does not need (16-bit operands read in
+    // place).  fmm_gemm checks every argument, the workspace included, before it launches
+    // anything, so a call without workspace either runs or fails with nothing enqueued.
+    const fmm_status st = fmm_gemm(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, levels, variant,
+                                   nullptr, 0, stream);
+    if (st != FMM_ERR_WORKSPACE) return st;
     char msg[160];
     std::snprintf(msg, sizeof msg,
                   "fmm_gemm_noalloc: this problem needs %zu bytes of scratch; the built-in "

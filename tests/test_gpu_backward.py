@@ -1,7 +1,6 @@
 """Backward products dA = dC @ B^T and dB = A^T @ dC (fmm_gemm_backward) and the
 differentiable layer, against the FP64 oracle.  Integer inputs are bit-exact; floats
 within the normwise bounds of test_gpu_parity."""
-import math
 
 import numpy as np
 import pytest
@@ -10,6 +9,7 @@ import torch
 import oracle
 import paper_1808_07984_gb300 as fmm
 import synth
+from bounds import tolerance
 
 pytestmark = pytest.mark.gpu
 
@@ -24,10 +24,7 @@ def _lib():
 
 
 def _tol(variant, levels, k):
-    kk = max(k, 1)
-    if variant == "split3":
-        return max(1e-6, 8 * 2.0 ** -17 * 3 ** levels / math.sqrt(kk))
-    return 4 * 2.0 ** -8 * 3 ** levels / math.sqrt(kk)
+    return tolerance(variant, levels, k)
 
 
 def _err(X, X64, An, Bn):
@@ -163,15 +160,16 @@ def test_linear_autograd_matches_oracle_and_finite_differences(levels):
     assert abs(fd - an) <= 1e-5 * scale
 
 
-def test_linear_layer_shapes_sampled_rows():
-    """Differentiable layer at 8192 x 4096 x 4096 with BF16 inputs; gradients checked on
-    sampled rows of dA and of dB against the FP64 oracle."""
+@pytest.mark.parametrize("levels", [1, 2])
+def test_linear_layer_shapes_sampled_rows(levels):
+    """Differentiable layer at 8192 x 4096 x 4096 with BF16 inputs (one and two levels);
+    gradients checked on sampled rows of dA and of dB against the FP64 oracle."""
     m, k, n = 8192, 4096, 4096
     rng = synth.rng(31)
     A = torch.from_numpy(synth.gaussian((m, k), 32)).to(torch.bfloat16).cuda().requires_grad_(True)
     B = torch.from_numpy(synth.gaussian((k, n), 33)).to(torch.bfloat16).cuda().requires_grad_(True)
     dC = torch.from_numpy(synth.gaussian((m, n), 34)).cuda()
-    C = fmm.linear(A, B, levels=1, variant="bf16")
+    C = fmm.linear(A, B, levels=levels, variant="bf16")
     C.backward(dC)
     fmm.device_status()
     Af = A.detach().float().cpu().numpy().astype(np.float64)
@@ -185,7 +183,7 @@ def test_linear_layer_shapes_sampled_rows():
     gA = A.grad.float().cpu().numpy()[ra]
     gB = B.grad.float().cpu().numpy()[rb]
     # gradients come back in the inputs' dtype (BF16): allow that rounding on top
-    tol = _tol("bf16", 1, 4096) + 2.0 ** -8
+    tol = _tol("bf16", levels, 4096) + 2.0 ** -8
     assert _err(gA, dA64, np.linalg.norm(dCn[ra].astype(np.float64)), np.linalg.norm(Bf)) <= tol
     assert _err(gB, dB64, np.linalg.norm(Af[:, rb]), np.linalg.norm(dCn.astype(np.float64))) <= tol
 
@@ -193,16 +191,63 @@ def test_linear_layer_shapes_sampled_rows():
 @pytest.mark.parametrize("levels", [1, 2])
 def test_linear_gradcheck_64(levels):
     """torch.autograd.gradcheck of the library-backed layer at 64^3 (config C3's check).  The
-    layer is bilinear, so the central differences are exact up to the FP32 rounding of the
-    forward products; tolerances are set from that rounding, not from a truncation error."""
+    library takes no FP64 operands, so the layer runs in FP32 (split3).  It is bilinear, so a
+    central difference with step 1 is exact up to the rounding of the forward products; the
+    tolerance is that rounding: the split3 normwise bound at k = 64 turned into a per-element
+    bound (times ||A||_F ||B||_F / sqrt(m n), six standard deviations)."""
     g = torch.Generator(device="cpu").manual_seed(77 + levels)
     A = torch.randn((64, 64), generator=g).cuda().requires_grad_(True)
     B = torch.randn((64, 64), generator=g).cuda().requires_grad_(True)
+    per_elem = 6 * _tol("split3", levels, 64) * float(A.norm() * B.norm()) / 64
     # the ownership mode makes repeated backward calls bitwise identical (gradcheck's
     # reentrancy check uses a zero tolerance)
     assert torch.autograd.gradcheck(lambda a, b: fmm.linear(a, b, levels=levels, deterministic=True), (A, B),
-                                    eps=1e-2, atol=2e-3, rtol=2e-3, fast_mode=True)
+                                    eps=1.0, atol=per_elem, rtol=0.0, fast_mode=True)
     fmm.device_status()
+
+
+def _fd64_gradients(A, B, G):
+    """dL/dA and dL/dB of L(A, B) = <G, A B> by FP64 central differences of the oracle's
+    product (step 1, exact for a bilinear map up to FP64 rounding).  Perturbing A[i, l]
+    changes only row i of the product, and B[l, j] only column j, so one oracle call per row
+    of A (its 64 perturbed copies stacked) and per column of B suffices."""
+    m, k = A.shape
+    n = B.shape[1]
+    dA = np.zeros((m, k))
+    for i in range(m):
+        rows = np.repeat(A[i:i + 1].astype(np.float64), k, axis=0)
+        plus = oracle.classical(rows + np.eye(k), B)
+        minus = oracle.classical(rows - np.eye(k), B)
+        dA[i] = (plus - minus) @ G[i].astype(np.float64) / 2.0
+    dB = np.zeros((k, n))
+    for j in range(n):
+        cols = np.repeat(B[:, j:j + 1].astype(np.float64), k, axis=1)
+        plus = oracle.classical(A, cols + np.eye(k))
+        minus = oracle.classical(A, cols - np.eye(k))
+        dB[:, j] = G[:, j].astype(np.float64) @ (plus - minus) / 2.0
+    return dA, dB
+
+
+@pytest.mark.parametrize("levels", [0, 1, 2])
+def test_linear_gradients_64_against_fp64_finite_differences(levels):
+    """Config C3's FP64 check: the layer's dA and dB at 64^3 against FP64 central differences
+    of the CPU oracle and against the classical FP64 gradient, normwise within the split3
+    bound at k = 64."""
+    A, B = synth.problem(64, 64, 64, 90 + levels, "gaussian")
+    G = synth.gaussian((64, 64), 93 + levels)
+    Ad = torch.from_numpy(A).cuda().requires_grad_(True)
+    Bd = torch.from_numpy(B).cuda().requires_grad_(True)
+    (fmm.linear(Ad, Bd, levels=levels) * torch.from_numpy(G).cuda()).sum().backward()
+    fmm.device_status()
+    fdA, fdB = _fd64_gradients(A, B, G)
+    gA64 = oracle.classical(G, np.ascontiguousarray(B.T))
+    gB64 = oracle.classical(np.ascontiguousarray(A.T), G)
+    # the two FP64 references agree to FP64 rounding
+    assert np.abs(fdA - gA64).max() <= 1e-9 and np.abs(fdB - gB64).max() <= 1e-9
+    nA, nB, nG = (np.linalg.norm(X.astype(np.float64)) for X in (A, B, G))
+    tol = _tol("split3", levels, 64)
+    assert _err(Ad.grad.cpu().numpy(), fdA, nG, nB) <= tol
+    assert _err(Bd.grad.cpu().numpy(), fdB, nA, nG) <= tol
 
 
 def test_library_call_from_a_fresh_thread():

@@ -1,6 +1,5 @@
 """Batched uneven products in one persistent launch (fmm_batched_plan_*), CUDA-graph
 capture and replay, the scaled FP16 arithmetic, against the FP64 oracle."""
-import math
 
 import numpy as np
 import pytest
@@ -9,6 +8,7 @@ import torch
 import oracle
 import paper_1808_07984_gb300 as fmm
 import synth
+from bounds import tolerance
 
 pytestmark = pytest.mark.gpu
 
@@ -69,8 +69,7 @@ def test_batched_float(variant):
         err = oracle.normwise_error(Cs[i].cpu().numpy(), C64, np.linalg.norm(hostA[i]),
                                     np.linalg.norm(hostB[i]))
         lv = fmm.tune_select(m, n, k, _table(MIXED))[0]
-        u = 2.0 ** -17 * 8 if variant == "split3" else 4 * 2.0 ** -11
-        assert err <= max(1e-6, u * 3 ** lv / math.sqrt(k)), (shapes[i], err)
+        assert err <= tolerance(variant, lv, k), (shapes[i], err)
 
 
 def test_batched_graph_capture_and_replay():
@@ -131,8 +130,35 @@ def test_batched_256_uneven_fp16_sampled():
         Bn = float(Bs[i].float().norm())
         err = oracle.normwise_error(Cs[i][torch.from_numpy(rows).cuda()].cpu().numpy(), C64, An, Bn)
         lv = fmm.tune_select(m, n, k)[0]
-        assert err <= 4 * 2.0 ** -11 * 3 ** lv / math.sqrt(k), (shapes[i], err)
+        assert err <= tolerance("f16", lv, k), (shapes[i], err)
         worst = max(worst, err)
+
+
+@pytest.mark.parametrize("levels", [1, 2])
+def test_batched_uneven_fp16_scaled_strassen_classes(levels):
+    """Config C4's defining feature at its sizes: problems drawn like the 256-problem batch
+    (multiples of 256 in [1024, 8192]) forced through one- and two-level Strassen classes of
+    the FP16 arithmetic, whose operand sums are scaled by a power of two per panel before
+    the FP16 rounding; sampled rows of every other problem against the oracle on the FP16
+    bit patterns."""
+    shapes = synth.uneven_batch(24, seed=2030 + levels)
+    g = torch.Generator(device="cuda").manual_seed(2040 + levels)
+    As = [(torch.rand((m, k), device="cuda", generator=g) * 2 - 1).half() for m, n, k in shapes]
+    Bs = [(torch.rand((k, n), device="cuda", generator=g) * 2 - 1).half() for m, n, k in shapes]
+    table = [(2 ** 62, levels, 0)]
+    Cs = fmm.gemm_batched(As, Bs, variant="f16", tune=table)
+    fmm.device_status()
+    rng = synth.rng(2050 + levels)
+    for i in range(0, len(shapes), 2):
+        m, n, k = shapes[i]
+        assert fmm.tune_select(m, n, k, table)[0] == levels
+        rsel = torch.from_numpy(np.unique(rng.integers(0, m, size=2))).cuda()
+        Ab = As[i][rsel].cpu().view(torch.int16).numpy().view(np.uint16)
+        Bb = Bs[i].cpu().view(torch.int16).numpy().view(np.uint16)
+        C64 = oracle.classical(Ab, Bb, a_code=oracle.ORC_F16, b_code=oracle.ORC_F16)
+        err = oracle.normwise_error(Cs[i][rsel].cpu().numpy(), C64, float(As[i][rsel].float().norm()),
+                                    float(Bs[i].float().norm()))
+        assert err <= tolerance("f16", levels, k), (shapes[i], err)
 
 
 def test_native_tuner_builds_a_valid_table():

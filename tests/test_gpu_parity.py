@@ -2,10 +2,10 @@
 
 Integer inputs must agree bit for bit (every operand sum, product and partial sum
 is an integer below 2**24, exact in BF16 and FP32).  Floating-point inputs must
-agree within the normwise bound ||C - C64||_F / (||A||_F ||B||_F) <= tol, where
-tol is derived per arithmetic in ``tolerance()`` below.
+agree within the normwise bound ||C - C64||_F / (||A||_F ||B||_F) <= tol, with tol
+from ``tests/bounds.py``: 1e-6 for the FP32-accurate split arithmetic wherever that
+arithmetic itself allows it, its own derived bound at smaller depths.
 """
-import math
 
 import numpy as np
 import pytest
@@ -14,6 +14,7 @@ import torch
 import oracle
 import paper_1808_07984_gb300 as fmm
 import synth
+from bounds import tolerance
 
 pytestmark = pytest.mark.gpu
 
@@ -25,30 +26,6 @@ def _lib():
     fmm.build()
     fmm.load()
     oracle.build()
-
-
-U_BF16 = 2.0 ** -8   # unit roundoff of bfloat16 (8-bit significand)
-
-
-def tolerance(variant, levels, k):
-    """Normwise error bound used by the parity tests.
-
-    split3: the dropped lo*lo term and the residual of the hi/lo split are each
-    below 2**-16 relative per operand pair, random in sign, so the normwise error
-    is about 2**-17 / sqrt(k); FP32 accumulation adds O(2**-24).  The north-star
-    bound 1e-6 holds for k >= 64; for tiny k the derived bound is used.  Each
-    Strassen level at most doubles the operand magnitudes and adds one more
-    signed combination, so 3**L margin is allowed.
-    plain BF16 rounding of the operand sums: about 2**-9 / sqrt(k) per product.
-    """
-    kk = max(k, 1)
-    if variant == "split3":
-        return max(1e-6, 8 * 2.0 ** -17 * 3 ** levels / math.sqrt(kk))
-    if variant in ("bf16", "f16") and levels == 0:
-        return 1e-6  # inputs exactly representable, FP32 accumulation only
-    if variant == "f16":
-        return 4 * 2.0 ** -11 * 3 ** levels / math.sqrt(kk)  # FP16: 11-bit significand
-    return 4 * U_BF16 * 3 ** levels / math.sqrt(kk)
 
 
 def _to_device(X, ld_pad, dtype):
@@ -79,7 +56,9 @@ def run(m, n, k, levels, variant="split3", dist="uniform", seed=0, alpha=1.0, be
              pipeline=pipeline, fringe=fringe, basis=basis, deterministic=deterministic,
              outer_scaling=outer_scaling)
     fmm.device_status()
-    C = Cd.cpu().numpy().astype(np.float64)
+    # sampled rows are gathered on the device (a full-size C is several GB)
+    Csel = Cd if rows is None else Cd[torch.from_numpy(np.asarray(rows)).to(Cd.device)]
+    C = Csel.cpu().numpy().astype(np.float64)
     if variant in ("bf16", "f16"):
         # the oracle sees exactly the 16-bit values the GPU saw
         code = oracle.ORC_BF16 if variant == "bf16" else oracle.ORC_F16
@@ -93,7 +72,6 @@ def run(m, n, k, levels, variant="split3", dist="uniform", seed=0, alpha=1.0, be
         An = float(np.linalg.norm(A.astype(np.float64)))
         Bn = float(np.linalg.norm(B.astype(np.float64)))
     if rows is not None:
-        C = C[rows]
         An = float(np.linalg.norm(A[rows].astype(np.float64)))
     return C, C64, An, Bn
 
@@ -797,6 +775,20 @@ def test_full_size_sampled_rows(n, k, levels):
     C, C64, An, Bn = run(m, n, k, levels, "split3", seed=20, rows=rows, tile_n=0)
     err = oracle.normwise_error(C, C64, An, Bn)
     assert err <= 1e-6, err
+
+
+@pytest.mark.parametrize("m,n,k,levels", [(16384, 16384, 16384, 2), (30001, 29999, 4097, 2),
+                                          (30001, 29999, 4097, 1)])
+def test_full_size_int_sampled_rows_bit_exact(m, n, k, levels):
+    """Small integers at the benchmark's sizes: every operand sum, product and partial sum is an
+    integer far below 2**24, so each sampled element must equal the FP64 oracle exactly.  This
+    reaches the full-size paths: 76 CTA pairs, three stages, 64-deep k-steps by the hundred,
+    tile rounds; at 30001 x 29999 x 4097 the tight leading dimensions (odd lda, ldb, ldc) take
+    the unaligned-operand sum pass and the element-wise write-back, and the last block row and
+    column are zero-padded fringes."""
+    rows = np.unique(np.concatenate([[0, m - 1], synth.rng(m + k).integers(0, m, size=6)]))
+    C, C64, _, _ = run(m, n, k, levels, "split3", dist="int", seed=k + levels, rows=rows)
+    np.testing.assert_array_equal(C, C64)
 
 
 # ----------------------------------------------------------- failure path
