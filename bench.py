@@ -77,7 +77,7 @@ def mma_flops(m, n, k, levels, variant, basis="strassen"):
 
 
 def kernel_name(algo):
-    return "fmm_fused_kernel" if algo in ("fused", "hybrid") else "fmm_packed_kernel"
+    return "fmm_fused_ts_kernel" if algo in ("fused", "hybrid") else "fmm_packed_kernel"
 
 
 def tensor_peak(peaks):
@@ -514,9 +514,9 @@ def main():
     ws = torch.empty(max(ws_bytes, 256), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(levels, algo=None):
+    def step(levels, algo=None, fused_kernel="auto"):
         fmm.gemm(A_d, B_d, C_d, 1.0, 0.0, levels=levels, variant=a.variant, algo=algo or a.algo,
-                 tile_n=0 if algo else a.tile_n, workspace=ws, stream=stream)
+                 tile_n=0 if algo else a.tile_n, workspace=ws, stream=stream, fused_kernel=fused_kernel)
 
     def barrier():
         if dist is not None:
@@ -525,9 +525,9 @@ def main():
     def slowest(x):
         return max_over_ranks(x, dist, dev)
 
-    def timed(levels, steps, warmup, profile=False, algo=None):
+    def timed(levels, steps, warmup, profile=False, algo=None, fused_kernel="auto"):
         for _ in range(warmup):
-            step(levels, algo)
+            step(levels, algo, fused_kernel)
         fmm.device_status()
         barrier()
         torch.cuda.synchronize()
@@ -538,7 +538,7 @@ def main():
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(steps):
-            step(levels, algo)
+            step(levels, algo, fused_kernel)
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -579,13 +579,26 @@ def main():
     fused = None
     do_fused = (not a.no_fused and a.algo == "auto" and a.variant in ("split3", "plain_bf16")
                 and a.levels in (1, 2))
+    on_chip = [("fused", "tmem", "fused: operand sums formed on chip as the tiles load; A-operand sums in "
+                                 "tensor memory, B-operand sums in shared memory; no workspace"),
+               ("fused_smem", "smem", "fused: operand sums formed on chip, both operands' sums written to "
+                                      "shared memory; no workspace")]
+    if a.levels == 2:
+        on_chip.append(("hybrid", "tmem", "hybrid: the seven top-level sums materialised in FP32, the 49 "
+                                          "bottom-level products' sums formed on chip (A in tensor memory)"))
     if do_fused:
+        fused = {}
         fsteps = max(1, min(a.steps, 5))
-        msf, proff = timed(a.levels, fsteps, 1, profile=True, algo="fused")
-        msf = slowest(msf)
-        fused = {"algo": "fused (operand sums formed in shared memory as the tiles load)",
-                 "value": job_value(world, flops, msf), "ms_per_step": msf, "steps": fsteps,
-                 "tensor_kernel_ms": proff["tensor"][0] / max(proff["tensor"][1], 1)}
+        for key, fk, desc in on_chip:
+            algo = "hybrid" if key == "hybrid" else "fused"
+            msf, proff = timed(a.levels, fsteps, 1, profile=True, algo=algo, fused_kernel=fk)
+            msf = slowest(msf)
+            ker = proff["tensor"][0] / max(proff["tensor"][1], 1)
+            mma = mma_flops(m, n, k, a.levels, a.variant)
+            fused[key] = {"algo": desc, "value": job_value(world, flops, msf), "ms_per_step": msf,
+                          "steps": fsteps, "tensor_kernel_ms": ker,
+                          "tensor_kernel_tflops": mma / (ker * 1e-3) * 1e-12,
+                          "kernel": "fmm_fused_ts_kernel" if fk == "tmem" else "fmm_fused_kernel"}
 
     # ---- end to end through host buffers: every step copies its A, B from pinned host memory
     # and its C back to pinned host memory inside the timed region.  Two device buffer sets
@@ -671,11 +684,12 @@ def main():
                                      np.linalg.norm(B.astype(np.float64)))
         classical["fp64_normwise_err_sampled"] = err0
     if fused is not None:
-        step(a.levels, "fused")
-        torch.cuda.synchronize()
-        C_sf = C_d[torch.from_numpy(rows).to(dev)].cpu().numpy()
-        fused["fp64_normwise_err_sampled"] = oracle.normwise_error(
-            C_sf, C64, np.linalg.norm(A[rows].astype(np.float64)), np.linalg.norm(B.astype(np.float64)))
+        for key, fk, _ in on_chip:
+            step(a.levels, "hybrid" if key == "hybrid" else "fused", fk)
+            torch.cuda.synchronize()
+            C_sf = C_d[torch.from_numpy(rows).to(dev)].cpu().numpy()
+            fused[key]["fp64_normwise_err_sampled"] = oracle.normwise_error(
+                C_sf, C64, np.linalg.norm(A[rows].astype(np.float64)), np.linalg.norm(B.astype(np.float64)))
 
     # ---- roofline of the dominant kernel (the tensor-core kernel)
     # per launch of the tensor-core kernel (a pipelined product launches it once per

@@ -134,7 +134,12 @@ typedef struct fmm_options {
                           lies in [1, 2) before the operand sums are formed, and C is scaled
                           back exactly afterwards (keeps badly scaled rows and columns from
                           losing accuracy in the Strassen sums; two more passes over C) */
-    int reserved[4]; /* zero */
+    int fused_kernel; /* fused and hybrid algorithms: 0 = automatic (2 in CTA pairs, else 1);
+                         1 = both operands' sums written to shared memory for the UMMAs;
+                         2 = CTA pairs only: the A-operand sums stored in tensor memory
+                         (tcgen05.st) and read from there by the UMMAs, the B-operand sums in
+                         shared memory (half the shared-memory traffic of the operand tiles) */
+    int reserved[3]; /* zero */
 } fmm_options;
 
 /* Bytes of workspace fmm_gemm needs for this problem (0 when none).  Returns

@@ -42,7 +42,7 @@ class _Options(ctypes.Structure):
                 ("schedule", ctypes.c_int), ("bk", ctypes.c_int), ("cta_pair", ctypes.c_int),
                 ("round_tiles", ctypes.c_int), ("fringe", ctypes.c_int), ("pipeline", ctypes.c_int),
                 ("basis", ctypes.c_int), ("deterministic", ctypes.c_int), ("outer_scaling", ctypes.c_int),
-                ("reserved", ctypes.c_int * 4)]
+                ("fused_kernel", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 _lib = None
@@ -142,9 +142,14 @@ FRINGES = {"pad": 0, "peel": 1}
 BASES = {"strassen": 0, "winograd": 1, "b323": 2}
 
 
+FUSED_KERNELS = {"auto": 0, "smem": 1, "tmem": 2}
+
+
 def _opts(algo="auto", tile_n=0, num_ctas=0, schedule="auto", bk=0, cta_pair=None, round_tiles=0,
-          pipeline=None, fringe="pad", basis="strassen", deterministic=False, outer_scaling=False):
+          pipeline=None, fringe="pad", basis="strassen", deterministic=False, outer_scaling=False,
+          fused_kernel="auto"):
     o = _Options()
+    o.fused_kernel = FUSED_KERNELS[fused_kernel] if isinstance(fused_kernel, str) else int(fused_kernel)
     o.outer_scaling = 1 if outer_scaling else 0
     o.deterministic = 1 if deterministic else 0
     o.basis = BASES[basis] if isinstance(basis, str) else int(basis)
@@ -187,7 +192,7 @@ def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
          variant="split3", algo="auto", tile_n: int = 0, num_ctas: int = 0,
          workspace=None, stream=None, schedule="auto", bk: int = 0, cta_pair=None,
          round_tiles: int = 0, pipeline=None, fringe="pad", basis="strassen",
-         deterministic: bool = False, outer_scaling: bool = False):
+         deterministic: bool = False, outer_scaling: bool = False, fused_kernel="auto"):
     """C = alpha * A @ B + beta * C on the current CUDA device (torch tensors).
 
     A (m x k) and B (k x n) are row-major CUDA tensors of the element type the
@@ -203,6 +208,8 @@ def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
     (the <3,2,3> basis of rank 15, one level, packed or fused algorithm).  ``deterministic``:
     ownership mode, bitwise reproducible results.  ``outer_scaling``: exact power-of-two
     scaling of the rows of A and columns of B around the product (badly scaled inputs).
+    ``fused_kernel`` (fused and hybrid algorithms): "auto", "smem" (both operands' sums in shared
+    memory) or "tmem" (CTA pairs: the A-operand sums in tensor memory).
     ``levels="auto"``: the level count and basis the analytic model (``model.py``) predicts
     fastest for this shape and variant (classical, Strassen at one or two levels, or the
     <3,2,3> basis); ``basis`` is then ignored.
@@ -238,7 +245,7 @@ def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
     ws_ptr = workspace.data_ptr() if workspace is not None else None
     ws_bytes = workspace.numel() if workspace is not None else 0
     o = _opts(algo, tile_n, num_ctas, schedule, bk, cta_pair, round_tiles, pipeline, fringe, basis,
-              deterministic, outer_scaling)
+              deterministic, outer_scaling, fused_kernel)
     st = load().fmm_gemm_ex(m, n, k, float(alpha), A.data_ptr(), max(A.stride(0), 1),
                             B.data_ptr(), max(B.stride(0), 1), float(beta), C.data_ptr(),
                             max(C.stride(0), 1), int(levels), v, ws_ptr, ws_bytes,

@@ -12,7 +12,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libfmm_gb300.so")
 
-SOURCES = ["fmm_api.cu", "fmm_pack.cu", "fmm_packed.cu", "fmm_packed_pair.cu", "fmm_fused.cu", "fmm_noalloc.cu", "fmm_tune.cu"]
+SOURCES = ["fmm_api.cu", "fmm_pack.cu", "fmm_packed.cu", "fmm_packed_pair.cu", "fmm_fused.cu", "fmm_fused_ts.cu", "fmm_noalloc.cu", "fmm_tune.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
          "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]

@@ -232,6 +232,7 @@ struct Plan {
   int tile_n = 128;
   int bk = 64;  // k-elements per pipeline stage of the packed kernel (64, or 32 for split3)
   bool pair = false;  // packed kernel in CTA pairs: 256-row tiles shared by two CTAs
+  bool fused_ts = false;  // fused kernel with the A-operand sums in tensor memory
   int pipeline_mode = 0;  // fmm_options.pipeline: 0 automatic, 1 off, 2 on
   int basis = kBasisStrassen;  // coefficient tables (Strassen, Strassen-Winograd or <3,2,3>)
   int gm = 1, gk = 1, gn = 1;  // block grid of A (gm x gk), B (gk x gn) and C (gm x gn)
@@ -318,6 +319,11 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
                                                : "the fused and hybrid algorithms use 128-wide tiles");
     pl.tile_n = fused_n;
   }
+  const int fk = opt ? opt->fused_kernel : 0;
+  if (fk < 0 || fk > 2) return fail(FMM_ERR_ARG, "fused_kernel must be 0, 1 or 2");
+  if (fk == 2 && on_chip && !pl.pair)
+    return fail(FMM_ERR_UNSUPPORTED, "the tensor-memory fused kernel runs in CTA pairs");
+  pl.fused_ts = on_chip && pl.pair && fk != 1;
   if (!on_chip && !pl.pair && (a_mn || !b_mn))
     return fail(FMM_ERR_UNSUPPORTED, "single-CTA tiles are built for the forward product only");
   const int pipe = opt ? opt->pipeline : 0;
@@ -589,7 +595,8 @@ fmm_status gemm_fused(const Plan& pl, int64_t m, int64_t n, int64_t k, float alp
   cudaError_t e;
   {
     PhaseScope ps(kPhaseTensor, s);
-    e = launch_fused(*fp, pl.terms, kFusedTransformWarps, pl.pair, grid, s);
+    e = pl.fused_ts ? launch_fused_ts(*fp, pl.terms, grid, s)
+                    : launch_fused(*fp, pl.terms, kFusedTransformWarps, pl.pair, grid, s);
   }
   delete fp;
   if (e != cudaSuccess) return cuda_fail(e, "fused tensor-core pass");
@@ -698,7 +705,8 @@ fmm_status gemm_hybrid(const Plan& pl, int64_t m, int64_t n, int64_t k, float al
   }
   {
     PhaseScope ps(kPhaseTensor, s);
-    e = launch_fused(*fp, pl.terms, kFusedTransformWarps, pl.pair, grid, s);
+    e = pl.fused_ts ? launch_fused_ts(*fp, pl.terms, grid, s)
+                    : launch_fused(*fp, pl.terms, kFusedTransformWarps, pl.pair, grid, s);
   }
   delete fp;
   if (e != cudaSuccess) return cuda_fail(e, "hybrid tensor-core pass");

@@ -55,6 +55,61 @@ __device__ __forceinline__ void split2(float x0, float x1, uint32_t& hi, uint32_
   lo = pack_bf16x2(x0 - h0, x1 - h1);
 }
 
+// Producer of the fused kernels (one thread): for every item, k-step and 32-deep k half, one
+// FP32 tile per source block of the product's A-operand (128 rows x 32 k, 128-byte swizzle),
+// then per source block of its B-operand (32 k x 128 n, this CTA's columns), each into the next
+// slot of an NS-slot ring.  Returns false if a wait gave up or a parameter block named a tensor
+// map outside its table (error bit set).
+template <int NS, bool PAIR>
+__device__ __forceinline__ bool fused_producer(const FusedParams& fp, uint8_t* slots, uint64_t* slot_full,
+                                               uint64_t* slot_empty, int rank, int first, int stride,
+                                               volatile int* abort_flag) {
+  const CommonParams& p = fp.c;
+  constexpr int TN = PAIR ? 2 * kFusedBN : kFusedBN;
+  int slot = 0;
+  uint32_t sph = 0;
+  bool ok = true;
+  auto issue = [&](const CUtensorMap* map, int x, int y) -> bool {
+    if (!mbar_wait(smem_u32(&slot_empty[slot]), sph ^ 1u, p.timeout_ns, abort_flag)) return false;
+    const uint32_t fb = smem_u32(&slot_full[slot]);
+    mbar_arrive_expect_tx(fb, kSlotBytes);
+    tma_load_2d(smem_u32(slots + slot * kSlotBytes), map, fb, x, y);
+    if (++slot == NS) {
+      slot = 0;
+      sph ^= 1u;
+    }
+    return true;
+  };
+  for (int item = first; ok && item < p.num_items; item += stride) {
+    int r, tm, tn;
+    if (!decode_item(item, p, r, tm, tn, stride)) continue;  // empty item
+    // the product's source lists, read once into registers (indexed parameter loads in
+    // the loops below would each go to the constant cache)
+    const uint32_t* psw = reinterpret_cast<const uint32_t*>(&fp.src[r]);
+    const uint32_t hdr = psw[kSrcWordHeader], ablk = psw[kSrcWordABlock], bblk = psw[kSrcWordBBlock];
+    const int na = hdr & 0xff, nb = (hdr >> 8) & 0xff;
+    // every map index must name one of the kMaxFusedSources maps: refuse the item otherwise
+    bool maps_ok = na <= kMaxDest && nb <= kMaxDest;
+    for (int w = 0; w < na && maps_ok; ++w) maps_ok = ((ablk >> (8 * w)) & 0xff) < kMaxFusedSources;
+    for (int w = 0; w < nb && maps_ok; ++w) maps_ok = ((bblk >> (8 * w)) & 0xff) < kMaxFusedSources;
+    if (!maps_ok) {
+      atomicOr(p.err, kErrBadParams);
+      return false;
+    }
+    const int a_row = (PAIR ? 2 * tm + rank : tm) * kBM;  // this CTA's rows and columns
+    const int b_col = tn * TN + rank * kFusedBN;
+    for (int kb = 0; ok && kb < p.nk; ++kb) {
+      for (int h = 0; ok && h < 2; ++h) {
+        for (int w = 0; ok && w < na; ++w)
+          ok = issue(&fp.tmSA[(ablk >> (8 * w)) & 0xff], kb * kBK + 32 * h, a_row);
+        for (int w = 0; ok && w < nb; ++w)
+          ok = issue(&fp.tmSB[(bblk >> (8 * w)) & 0xff], b_col, kb * kBK + 32 * h);
+      }
+    }
+  }
+  return ok;
+}
+
 template <int TERMS, int TW, bool PAIR>
 __global__ void __launch_bounds__(fused_threads<TW>(), 1) fmm_fused_kernel(const __grid_constant__ FusedParams fp) {
   static_assert(TW == 8 || TW == 16, "transform warps");
@@ -132,54 +187,11 @@ __global__ void __launch_bounds__(fused_threads<TW>(), 1) fmm_fused_kernel(const
     // nothing issued: fall through to the teardown
   } else if (warp == 0) {
     // ------------------------------------------------------------ producer
-    if (lane == 0) {
-      int slot = 0;
-      uint32_t sph = 0;
-      bool ok = true;
-      auto issue = [&](const CUtensorMap* map, int x, int y) -> bool {
-        if (!mbar_wait(smem_u32(&slot_empty[slot]), sph ^ 1u, p.timeout_ns, abort_flag)) return false;
-        const uint32_t fb = smem_u32(&slot_full[slot]);
-        mbar_arrive_expect_tx(fb, kSlotBytes);
-        tma_load_2d(smem_u32(slots + slot * kSlotBytes), map, fb, x, y);
-        if (++slot == NS) {
-          slot = 0;
-          sph ^= 1u;
-        }
-        return true;
-      };
-      for (int item = first; ok && item < p.num_items; item += stride) {
-        int r, tm, tn;
-        if (!decode_item(item, p, r, tm, tn, stride)) continue;  // empty item
-        // the product's source lists, read once into registers (indexed parameter loads in
-        // the loops below would each go to the constant cache)
-        const uint32_t* psw = reinterpret_cast<const uint32_t*>(&fp.src[r]);
-        const uint32_t hdr = psw[kSrcWordHeader], ablk = psw[kSrcWordABlock], bblk = psw[kSrcWordBBlock];
-        const int na = hdr & 0xff, nb = (hdr >> 8) & 0xff;
-        // every map index must name one of the kMaxFusedSources maps: refuse the item otherwise
-        bool maps_ok = na <= kMaxDest && nb <= kMaxDest;
-        for (int w = 0; w < na && maps_ok; ++w) maps_ok = ((ablk >> (8 * w)) & 0xff) < kMaxFusedSources;
-        for (int w = 0; w < nb && maps_ok; ++w) maps_ok = ((bblk >> (8 * w)) & 0xff) < kMaxFusedSources;
-        if (!maps_ok) {
-          atomicOr(p.err, kErrBadParams);
-          ok = false;
-          break;
-        }
-        const int a_row = (PAIR ? 2 * tm + rank : tm) * kBM;  // this CTA's rows and columns
-        const int b_col = tn * TN + rank * kFusedBN;
-        for (int kb = 0; ok && kb < p.nk; ++kb) {
-          for (int h = 0; ok && h < 2; ++h) {
-            for (int w = 0; ok && w < na; ++w)
-              ok = issue(&fp.tmSA[(ablk >> (8 * w)) & 0xff], kb * kBK + 32 * h, a_row);
-            for (int w = 0; ok && w < nb; ++w)
-              ok = issue(&fp.tmSB[(bblk >> (8 * w)) & 0xff], b_col, kb * kBK + 32 * h);
-          }
-        }
-      }
-      if (!ok) {
-        atomicOr(p.err, kErrProducerWait);
-        *abort_flag = 1;
-        drain_pause(2000000ull);
-      }
+    if (lane == 0 &&
+        !fused_producer<NS, PAIR>(fp, slots, slot_full, slot_empty, rank, first, stride, abort_flag)) {
+      atomicOr(p.err, kErrProducerWait);
+      *abort_flag = 1;
+      drain_pause(2000000ull);
     }
   } else if (warp == 1) {
     if (lane == 0 && rank == 0) {

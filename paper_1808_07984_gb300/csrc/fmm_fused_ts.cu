@@ -1,0 +1,47 @@
+// fmm_fused_ts.cu -- instantiations and launcher of the fused kernel whose A-operand sums are
+// held in tensor memory (fmm_fused_ts.cuh).
+#include <cuda_runtime.h>
+#include <algorithm>
+#include "fmm_fused_ts.cuh"
+#include "launch.h"
+
+namespace fmm {
+
+template <int TERMS>
+static cudaError_t launch_fused_ts_t(const FusedParams& p, int grid, cudaStream_t s) {
+  using Cfg = FusedTsCfg<TERMS>;
+  static_assert(Cfg::kSmemBytes <= 232448, "shared memory per CTA");
+  auto kern = fmm_fused_ts_kernel<TERMS>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(Cfg::kSmemBytes));
+  if (e != cudaSuccess) return e;
+  if (grid < 2 || grid % 2 != 0) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(fused_threads<8>(), 1, 1);
+  cfg.dynamicSmemBytes = Cfg::kSmemBytes;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  // at most one wave of CTA pairs (how many fit depends on how the SMs are grouped)
+  cfg.gridDim = dim3(static_cast<unsigned>(grid), 1, 1);
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) == cudaSuccess && clusters >= 1)
+    grid = std::min(grid, 2 * clusters);
+  else
+    cudaGetLastError();
+  cfg.gridDim = dim3(static_cast<unsigned>(grid), 1, 1);
+  return cudaLaunchKernelEx(&cfg, kern, p);
+}
+
+cudaError_t launch_fused_ts(const FusedParams& p, int terms, int grid, cudaStream_t s) {
+  if (terms == 3) return launch_fused_ts_t<3>(p, grid, s);
+  if (terms == 1) return launch_fused_ts_t<1>(p, grid, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace fmm

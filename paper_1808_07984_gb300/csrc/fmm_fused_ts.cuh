@@ -1,0 +1,329 @@
+// fmm_fused_ts.cuh -- Strassen products with the operand sums formed on chip (Section 3.1),
+// the A-operand sums held in tensor memory.
+//
+// Forming the sums on chip moves every source tile through shared memory (TMA write, then the
+// transform's read) and, in fmm_fused_kernel, writes both operands' BF16 sums back into shared
+// memory for the UMMAs to read again.  Here the A-operand sums never enter shared memory: the
+// transform threads store them into tensor memory with tcgen05.st, and the UMMAs take A from
+// TMEM (the ".kind::f16 [d], [a_tmem], b_desc" form).  Per CTA and 64-deep k-step that removes
+// the A-sum writes (32 KB for split3) and the UMMAs' A reads (48 KB) from shared memory.
+//
+// CTA pairs (clusters of two CTAs) on 256 x 256 output tiles:
+//   warp 0      producer (fused_producer): one FP32 tile per source block and 32-deep k half
+//               into a ring of kSlots 16 KB slots;
+//   warps 8-15  transform.  Warps 8-11 form k half 0 of every k-step, warps 12-15 half 1, each
+//               group reading only its own half's slots.  Thread (lane quarter q = warp % 4,
+//               lane l) owns A row 32q + l: it adds that row of each A source slot with its
+//               sign, splits the 32 sums into BF16 hi / lo and stores them into its CTA's TMEM
+//               at the stage's A columns (32 k per half = 16 columns per term).  It also adds
+//               8 k-rows x 4 columns of each B source slot and writes the split B sums into the
+//               stage's MN-major, 128-byte swizzled B tile in shared memory;
+//   warp 1      (even CTA) issues the cta_group::2 UMMAs: A from TMEM (each CTA's 128 rows),
+//               B from shared memory (each CTA's 128 columns);
+//   warps 4-7   multi-destination write-back (epilogue_role) of the accumulator.
+// TMEM (512 columns): the 256-column accumulator, then kStages A stages of 32 columns per term.
+// The accumulator is single-buffered (the A stages take the other half of TMEM): the UMMAs of
+// an item start once both epilogues have read the previous item's accumulator out.
+#pragma once
+#include "fmm_fused.cuh"
+
+namespace fmm {
+
+template <int TERMS>
+struct FusedTsCfg {
+  static constexpr int kTileN = 2 * kFusedBN;  // UMMA N of the pair tile
+  static constexpr int kStages = 3;            // operand stages (A in TMEM, B in shared memory)
+  static constexpr int kSlots = 6;             // FP32 source slots
+  static constexpr uint32_t kBTermBytes = kBK * kFusedBN * 2;  // 64 k x 128 n BF16 per term
+  static constexpr uint32_t kStageBytes = (TERMS == 3 ? 2u : 1u) * kBTermBytes;
+  static constexpr uint32_t kSlotOffset = kStages * kStageBytes;
+  static constexpr uint32_t kEpiOffset = kSlotOffset + kSlots * kSlotBytes;
+  static constexpr uint32_t kBarOffset = kEpiOffset + kEpiBytes;
+  static constexpr uint32_t kSmemBytes = kBarOffset + 512 + 1024;
+  static constexpr uint32_t kTmemCols = 512;
+  static constexpr uint32_t kTermCols = kBK / 2;                 // 64 BF16 per row = 32 columns
+  static constexpr uint32_t kAStageCols = (TERMS == 3 ? 2u : 1u) * kTermCols;
+  static constexpr uint32_t kACol0 = kTileN;                     // A stages after the accumulator
+  static_assert(kACol0 + kStages * kAStageCols <= kTmemCols, "TMEM columns");
+};
+
+// UMMA issue of the TS kernel (one thread of the even CTA).  Returns false if a wait gave up.
+template <int TERMS>
+__device__ __forceinline__ bool mma_role_ts(const CommonParams& p, uint8_t* smem, uint64_t* op_full,
+                                            uint64_t* op_empty, uint64_t* acc_full, uint64_t* acc_empty,
+                                            uint32_t tmem_base, volatile int* abort_flag) {
+  using Cfg = FusedTsCfg<TERMS>;
+  constexpr int S = Cfg::kStages;
+  constexpr uint32_t idesc = make_idesc_f16(2 * kBM, Cfg::kTileN, true, false, true);
+  constexpr uint32_t kMnAtom = kBK * 128;  // bytes between 64-wide n atoms of a B tile
+  const int first = static_cast<int>(blockIdx.x >> 1), stride = static_cast<int>(gridDim.x >> 1);
+  int o = 0;
+  uint32_t oph = 0;
+  int it = 0;
+  for (int item = first; item < p.num_items; item += stride) {
+    int r, tm, tn;
+    if (!decode_item(item, p, r, tm, tn, stride)) continue;  // empty item
+    // one accumulator: both epilogues have read the previous item's out of TMEM
+    if (!mbar_wait_cluster(smem_u32(&acc_empty[0]), (it & 1) ^ 1u, p.timeout_ns, abort_flag)) return false;
+    tc_fence_after();
+    for (int kb = 0; kb < p.nk; ++kb) {
+      if (!mbar_wait_cluster(smem_u32(&op_full[o]), oph, p.timeout_ns, abort_flag)) return false;
+      tc_fence_after();
+      uint8_t* st = smem + o * Cfg::kStageBytes;
+      const uint64_t db_hi = make_sdesc_mnmajor_sw128(smem_u32(st), kMnAtom, 1024);
+      const uint64_t db_lo = make_sdesc_mnmajor_sw128(smem_u32(st + Cfg::kBTermBytes), kMnAtom, 1024);
+      const uint32_t a_hi = tmem_base + Cfg::kACol0 + static_cast<uint32_t>(o) * Cfg::kAStageCols;
+      const uint32_t a_lo = a_hi + Cfg::kTermCols;
+#pragma unroll
+      for (int kk = 0; kk < kBK / 16; ++kk) {
+        // k16 slice: 8 TMEM columns of A; 16 k-rows (two 1024-byte atoms) of B, >> 4 encoded
+        const uint32_t ka = static_cast<uint32_t>(8 * kk);
+        const uint64_t kb16 = static_cast<uint64_t>(kk * 128);
+        umma_f16_ts_pair(tmem_base, a_hi + ka, db_hi + kb16, idesc, (kb | kk) != 0 ? 1u : 0u);
+        if (TERMS == 3) {
+          umma_f16_ts_pair(tmem_base, a_hi + ka, db_lo + kb16, idesc, 1u);
+          umma_f16_ts_pair(tmem_base, a_lo + ka, db_hi + kb16, idesc, 1u);
+        }
+      }
+      umma_commit_pair(smem_u32(&op_empty[o]), 3);
+      if (++o == S) {
+        o = 0;
+        oph ^= 1u;
+      }
+    }
+    umma_commit_pair(smem_u32(&acc_full[0]), 3);
+    ++it;
+  }
+  // both epilogues have read the last accumulator before the CTAs may retire
+  return it == 0 || mbar_wait_cluster(smem_u32(&acc_empty[0]), (it & 1) ^ 1u, p.timeout_ns, abort_flag);
+}
+
+template <int TERMS>
+__global__ void __launch_bounds__(fused_threads<8>(), 1) fmm_fused_ts_kernel(const __grid_constant__ FusedParams fp) {
+  using Cfg = FusedTsCfg<TERMS>;
+  constexpr int S = Cfg::kStages;
+  constexpr int NS = Cfg::kSlots;
+  const CommonParams& p = fp.c;
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Cfg::kBarOffset);
+  uint64_t* slot_full = bars;
+  uint64_t* slot_empty = bars + NS;
+  uint64_t* op_full = bars + 2 * NS;
+  uint64_t* op_empty = bars + 2 * NS + S;
+  uint64_t* acc_full = bars + 2 * NS + 2 * S;
+  uint64_t* acc_empty = bars + 2 * NS + 2 * S + 1;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * NS + 2 * S + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+  uint8_t* slots = smem + Cfg::kSlotOffset;
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int rank = static_cast<int>(cluster_ctarank());
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(smem_u32(&slot_full[s]), 1);
+      mbar_init(smem_u32(&slot_empty[s]), 4);  // the four transform warps of the slot's k half
+    }
+    for (int s = 0; s < S; ++s) {
+      mbar_init(smem_u32(&op_full[s]), 2 * 8);  // the transform warps of both CTAs
+      mbar_init(smem_u32(&op_empty[s]), 1);
+    }
+    mbar_init(smem_u32(&acc_full[0]), 1);
+    mbar_init(smem_u32(&acc_empty[0]), 2 * 4);  // the epilogue warps of both CTAs
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    __syncwarp();
+    tmem_alloc_pair(smem_u32(tmem_holder), Cfg::kTmemCols);
+    tmem_relinquish_pair();
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();  // the peer's barriers are initialised before anyone signals them
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_holder;
+  const int first = static_cast<int>(blockIdx.x >> 1);
+  const int stride = static_cast<int>(gridDim.x >> 1);
+  // the pair UMMAs use the same TMEM columns in both CTAs: check that both hold them
+  if (threadIdx.x == 0 &&
+      ld_shared_cluster_u32(mapa_shared(smem_u32(tmem_holder), static_cast<uint32_t>(rank ^ 1))) != tmem_base) {
+    atomicOr(p.err, kErrPairTmem);
+    *abort_flag = 1;
+  }
+  __syncthreads();
+  const bool run = *abort_flag == 0;  // the same in both CTAs of a pair
+
+  if (!run) {
+    // nothing issued: fall through to the teardown
+  } else if (warp == 0) {
+    if (lane == 0 && !fused_producer<NS, true>(fp, slots, slot_full, slot_empty, rank, first, stride, abort_flag)) {
+      atomicOr(p.err, kErrProducerWait);
+      *abort_flag = 1;
+      drain_pause(2000000ull);
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && rank == 0) {
+      if (!mma_role_ts<TERMS>(p, smem, op_full, op_empty, acc_full, acc_empty, tmem_base, abort_flag)) {
+        atomicOr(p.err, kErrMmaWait);
+        *abort_flag = 1;
+        drain_pause(2000000ull);
+      }
+    }
+  } else if (warp >= 4 && warp < 8) {
+    if (!epilogue_role<Cfg::kTileN, OneProblem, true, 1>(OneProblem{&p}, smem + Cfg::kEpiOffset, acc_full,
+                                                        acc_empty, tmem_base, abort_flag, p.timeout_ns, warp,
+                                                        lane, rank)) {
+      if (lane == 0) atomicOr(p.err, kErrEpilogueWait);
+      *abort_flag = 1;
+    }
+  } else if (warp >= 8) {
+    // ------------------------------------------------------------ transform
+    const int tw = warp - 8;
+    const int g = tw >> 2;             // k half this warp forms
+    const int q = tw & 3;              // TMEM lane quarter (= warp % 4)
+    const int arow = 32 * q + lane;    // A row of the tile (TMEM lane)
+    const int tb = (threadIdx.x - 256) & 127;  // thread within the half's group
+    const int bk0 = tb >> 5;           // first B k-row (of 32) of the half: bk0 + 4v, v < 8
+    const int nq = tb & 31;            // B columns 4 nq .. 4 nq + 3
+    const uint32_t lane_bits = static_cast<uint32_t>(32 * q) << 16;
+    int slot = 0;
+    uint32_t sph = 0;
+    int o = 0;
+    uint32_t oph = 0;
+    bool ok = true;
+    for (int item = first; ok && item < p.num_items; item += stride) {
+      int r, tm, tn;
+      if (!decode_item(item, p, r, tm, tn, stride)) continue;  // empty item
+      const uint32_t hdr = reinterpret_cast<const uint32_t*>(&fp.src[r])[kSrcWordHeader];
+      const int na = hdr & 0xff, nb = (hdr >> 8) & 0xff;
+      const uint32_t a_neg = (hdr >> 16) & 0xff, b_neg = hdr >> 24;
+      for (int kb = 0; ok && kb < p.nk; ++kb) {
+        float aA[32];
+        float aB[8][4];
+#pragma unroll
+        for (int e = 0; e < 32; ++e) aA[e] = 0.f;
+#pragma unroll
+        for (int v = 0; v < 8; ++v)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) aB[v][e] = 0.f;
+        // the k-step's slots: half 0 (A sources, then B sources), then half 1
+        for (int h = 0; h < 2; ++h) {
+          for (int w = 0; w < na + nb; ++w) {
+            if (h == g && ok) {
+              ok = mbar_wait(smem_u32(&slot_full[slot]), sph, p.timeout_ns, abort_flag);
+              if (ok) {
+                const uint8_t* sl = slots + slot * kSlotBytes;
+                if (w < na) {
+                  const float sg = ((a_neg >> w) & 1u) ? -1.f : 1.f;
+#pragma unroll
+                  for (int c = 0; c < 8; ++c) {
+                    const float4 x =
+                        *reinterpret_cast<const float4*>(sl + arow * 128 + ((c ^ (arow & 7)) << 4));
+                    aA[4 * c] = fmaf(sg, x.x, aA[4 * c]);
+                    aA[4 * c + 1] = fmaf(sg, x.y, aA[4 * c + 1]);
+                    aA[4 * c + 2] = fmaf(sg, x.z, aA[4 * c + 2]);
+                    aA[4 * c + 3] = fmaf(sg, x.w, aA[4 * c + 3]);
+                  }
+                } else {
+                  const float sg = ((b_neg >> (w - na)) & 1u) ? -1.f : 1.f;
+#pragma unroll
+                  for (int v = 0; v < 8; ++v) {
+                    const float4 x = *reinterpret_cast<const float4*>(sl + (bk0 + 4 * v) * 512 + nq * 16);
+                    aB[v][0] = fmaf(sg, x.x, aB[v][0]);
+                    aB[v][1] = fmaf(sg, x.y, aB[v][1]);
+                    aB[v][2] = fmaf(sg, x.z, aB[v][2]);
+                    aB[v][3] = fmaf(sg, x.w, aB[v][3]);
+                  }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&slot_empty[slot]));
+              }
+            }
+            if (++slot == NS) {
+              slot = 0;
+              sph ^= 1u;
+            }
+          }
+        }
+        if (!ok) break;
+        // the stage's previous UMMAs (A in TMEM, B in shared memory) have completed
+        if (!mbar_wait(smem_u32(&op_empty[o]), oph ^ 1u, p.timeout_ns, abort_flag)) {
+          ok = false;
+          break;
+        }
+        // A sums: k = 32 g .. 32 g + 31 of row arow -> 16 columns per term
+        {
+          uint32_t hi[16], lo[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            if (TERMS == 3)
+              split2(aA[2 * i], aA[2 * i + 1], hi[i], lo[i]);
+            else
+              hi[i] = pack_bf16x2(aA[2 * i], aA[2 * i + 1]);
+          }
+          const uint32_t ta = tmem_base + lane_bits + Cfg::kACol0 + static_cast<uint32_t>(o) * Cfg::kAStageCols +
+                              static_cast<uint32_t>(16 * g);
+          tmem_st_32x32b_x16(ta, hi);
+          if (TERMS == 3) tmem_st_32x32b_x16(ta + Cfg::kTermCols, lo);
+        }
+        // B sums: k-rows 32 g + bk0 + 4 v, columns 4 nq .. + 3, MN-major swizzled
+        uint8_t* st = smem + o * Cfg::kStageBytes;
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+          const int kk = 32 * g + bk0 + 4 * v;
+          const int c = (nq & 15) >> 1;  // 8-wide chunk inside the 64-wide n atom
+          const uint32_t off = (nq >> 4) * 8192 + (kk >> 3) * 1024 + (kk & 7) * 128 +
+                               ((c ^ (kk & 7)) << 4) + (nq & 1) * 8;
+          if (TERMS == 3) {
+            uint2 hv, lv;
+            split2(aB[v][0], aB[v][1], hv.x, lv.x);
+            split2(aB[v][2], aB[v][3], hv.y, lv.y);
+            *reinterpret_cast<uint2*>(st + off) = hv;
+            *reinterpret_cast<uint2*>(st + Cfg::kBTermBytes + off) = lv;
+          } else {
+            uint2 hv;
+            hv.x = pack_bf16x2(aB[v][0], aB[v][1]);
+            hv.y = pack_bf16x2(aB[v][2], aB[v][3]);
+            *reinterpret_cast<uint2*>(st + off) = hv;
+          }
+        }
+        fence_proxy_async_smem();  // generic-proxy stores -> visible to the tensor core
+        tmem_wait_st();            // this thread's TMEM stores have completed
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster(mapa_shared(smem_u32(&op_full[o]), 0));
+        if (++o == S) {
+          o = 0;
+          oph ^= 1u;
+        }
+      }
+    }
+    // every operand-stage release of the even CTA's MMA thread has arrived before the CTA retires
+    for (int i = 0; ok && i < S; ++i) {
+      ok = mbar_wait(smem_u32(&op_empty[o]), oph ^ 1u, p.timeout_ns, abort_flag);
+      if (++o == S) {
+        o = 0;
+        oph ^= 1u;
+      }
+    }
+    if (!ok) {
+      if (lane == 0) atomicOr(p.err, kErrTransformWait);
+      *abort_flag = 1;
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();  // neither CTA retires while the other may still signal it
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc_pair(tmem_base, Cfg::kTmemCols);
+  }
+}
+
+}  // namespace fmm

@@ -437,7 +437,8 @@ __device__ __forceinline__ bool mma_role(const Work& work, uint8_t* smem, uint64
 //
 // PAIR: the CTA with rank `rank` of a pair owns rows 128 * rank .. + 127 of each 256-row pair
 // tile; each warp releases the accumulator with one arrival on the even CTA's barrier.
-template <int BN, class Work, bool PAIR = false>
+// NACC: accumulators in TMEM (2: double-buffered at columns acc * BN; 1: one at column 0).
+template <int BN, class Work, bool PAIR = false, int NACC = 2>
 __device__ __forceinline__ bool epilogue_role(const Work& work, uint8_t* epi_smem,
                                               uint64_t* acc_full, uint64_t* acc_empty,
                                               uint32_t tmem_base, volatile int* abort_flag,
@@ -456,8 +457,8 @@ __device__ __forceinline__ bool epilogue_role(const Work& work, uint8_t* epi_sme
     const CommonParams& p = work.get(item, local);
     int r, tm, tn;
     if (!decode_item(local, p, r, tm, tn, stride)) continue;  // empty item
-    const int acc = it & 1;
-    const uint32_t acc_par = (it >> 1) & 1;
+    const int acc = NACC == 2 ? (it & 1) : 0;
+    const uint32_t acc_par = NACC == 2 ? ((it >> 1) & 1) : (it & 1);
     ++it;
     if (!mbar_wait(smem_u32(&acc_full[acc]), acc_par, timeout_ns, abort_flag)) {
       ok = false;

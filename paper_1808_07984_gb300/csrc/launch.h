@@ -45,5 +45,8 @@ bool packed_config_supported(int tile_n, int terms, bool bf16);
 constexpr int kFusedTransformWarps = 8;
 cudaError_t launch_fused(const FusedParams& p, int terms, int transform_warps, bool pair, int grid,
                          cudaStream_t s);
+// The same products in CTA pairs with the A-operand sums held in tensor memory
+// (fmm_fused_ts.cuh); terms in {1, 3}.
+cudaError_t launch_fused_ts(const FusedParams& p, int terms, int grid, cudaStream_t s);
 
 }  // namespace fmm

@@ -38,7 +38,7 @@ def _to_device(X, ld_pad, dtype):
 def run(m, n, k, levels, variant="split3", dist="uniform", seed=0, alpha=1.0, beta=0.0,
         tile_n=0, pads=(0, 0, 0), c_fill=None, rows=None, schedule="auto", algo="auto", bk=0,
         cta_pair=None, round_tiles=0, pipeline=None, fringe="pad", basis="strassen",
-        deterministic=False, outer_scaling=False):
+        deterministic=False, outer_scaling=False, fused_kernel="auto"):
     A, B = synth.problem(m, n, k, seed, dist)
     in_dtype = {"bf16": torch.bfloat16, "f16": torch.float16}.get(variant, torch.float32)
     Ad = _to_device(A, pads[0], in_dtype)
@@ -54,7 +54,7 @@ def run(m, n, k, levels, variant="split3", dist="uniform", seed=0, alpha=1.0, be
     fmm.gemm(Ad, Bd, Cd, alpha=alpha, beta=beta, levels=levels, variant=variant, tile_n=tile_n,
              schedule=schedule, algo=algo, bk=bk, cta_pair=cta_pair, round_tiles=round_tiles,
              pipeline=pipeline, fringe=fringe, basis=basis, deterministic=deterministic,
-             outer_scaling=outer_scaling)
+             outer_scaling=outer_scaling, fused_kernel=fused_kernel)
     fmm.device_status()
     # sampled rows are gathered on the device (a full-size C is several GB)
     Csel = Cd if rows is None else Cd[torch.from_numpy(np.asarray(rows)).to(Cd.device)]
@@ -616,6 +616,33 @@ def test_fused_float_shapes(m, n, k, levels, variant):
     assert err <= tolerance(variant, levels, k), err
 
 
+@pytest.mark.parametrize("fused_kernel", ["smem", "tmem"])
+@pytest.mark.parametrize("variant", ["split3", "plain_bf16"])
+@pytest.mark.parametrize("m,n,k", [(16, 16, 16), (300, 520, 200), (129, 257, 65), (1000, 1200, 300),
+                                   (520, 8, 400), (600, 700, 1030)])
+def test_fused_kernels_int_bit_exact(m, n, k, variant, fused_kernel):
+    """Both on-chip kernels (CTA pairs): operand sums of both operands in shared memory, or the
+    A-operand sums in tensor memory; one and two levels, and the hybrid two-level scheme."""
+    for levels, algo in ((1, "fused"), (2, "fused"), (2, "hybrid")):
+        C, C64, _, _ = run(m, n, k, levels, variant, dist="int", seed=3 * m + n + k, algo=algo,
+                           pads=(_pad4(k), _pad4(n), 0), fused_kernel=fused_kernel)
+        np.testing.assert_array_equal(C, C64, err_msg=f"{algo} L={levels}")
+
+
+@pytest.mark.parametrize("schedule", ["product", "rounds"])
+def test_fused_tmem_kernel_float_and_schedules(schedule):
+    C, C64, An, Bn = run(1100, 900, 1300, 1, "split3", dist="gaussian", seed=44, algo="fused",
+                         fused_kernel="tmem", schedule=schedule)
+    assert oracle.normwise_error(C, C64, An, Bn) <= tolerance("split3", 1, 1300)
+
+
+def test_fused_tmem_kernel_needs_cta_pairs():
+    A = torch.zeros((64, 64), device="cuda")
+    with pytest.raises(fmm.FmmError) as ei:
+        fmm.gemm(A, A, levels=1, algo="fused", cta_pair=False, fused_kernel="tmem")
+    assert ei.value.status == 3
+
+
 def test_fused_matches_packed_closely():
     """Same arithmetic, different place of the sums: results agree to FP32 rounding."""
     A, B = synth.problem(1024, 768, 896, 41, "uniform")
@@ -628,10 +655,21 @@ def test_fused_matches_packed_closely():
         assert rel < 1e-6, rel
 
 
-def test_fused_full_size_sampled_rows():
+@pytest.mark.parametrize("fused_kernel", ["smem", "tmem"])
+def test_fused_full_size_sampled_rows(fused_kernel):
     rows = np.unique(synth.rng(5).integers(0, 8192, size=8))
-    C, C64, An, Bn = run(8192, 8192, 8192, 2, "split3", seed=21, rows=rows, algo="fused")
+    C, C64, An, Bn = run(8192, 8192, 8192, 2, "split3", seed=21, rows=rows, algo="fused",
+                         fused_kernel=fused_kernel)
     assert oracle.normwise_error(C, C64, An, Bn) <= 1e-6
+
+
+@pytest.mark.parametrize("algo", ["fused", "hybrid"])
+def test_fused_full_size_int_bit_exact(algo):
+    """Small integers at 16384^3, two levels, sums formed on chip (default kernel): sampled
+    rows equal the FP64 oracle exactly."""
+    rows = np.unique(np.concatenate([[0, 16383], synth.rng(17).integers(0, 16384, size=4)]))
+    C, C64, _, _ = run(16384, 16384, 16384, 2, "split3", dist="int", seed=61, rows=rows, algo=algo)
+    np.testing.assert_array_equal(C, C64)
 
 
 def test_fused_rejects_unaligned_leading_dimension():
