@@ -20,9 +20,10 @@
 
 namespace fmm {
 
-// Device error word written by bounded waits inside the kernels (read and cleared by
-// fmm_device_status).
-__device__ unsigned int g_device_err;
+// Device error record written by bounded waits inside the kernels (read and cleared by
+// fmm_device_status): [0] error bits, [1] site of the first wait that gave up, [2] its work
+// item, [3] its k-step (low 16 bits) and block index (high 16 bits).
+__device__ unsigned int g_device_err[4];
 
 namespace {
 
@@ -1594,14 +1595,15 @@ fmm_status fmm_device_status(void* stream) {
   if (st != FMM_OK) return st;
   cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-  unsigned word = 0;
-  e = cudaMemcpy(&word, dev.err, sizeof word, cudaMemcpyDeviceToHost);
+  unsigned rec[4] = {0, 0, 0, 0};
+  e = cudaMemcpy(rec, dev.err, sizeof rec, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
-  if (word != 0) {
-    const unsigned zero = 0;
-    e = cudaMemcpy(dev.err, &zero, sizeof zero, cudaMemcpyHostToDevice);
+  const unsigned word = rec[0];
+  if (word != 0 || rec[1] != 0) {
+    const unsigned zero[4] = {0, 0, 0, 0};
+    e = cudaMemcpy(dev.err, zero, sizeof zero, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "clearing the device error word");
-    char buf[160];
+    char buf[320];
     if (word & (kErrPairTmem | kErrBadParams)) {
       std::snprintf(buf, sizeof buf, "device-side check failed: %s (error bits 0x%x)",
                     (word & kErrPairTmem) ? "CTA pair holds different TMEM columns"
@@ -1609,7 +1611,15 @@ fmm_status fmm_device_status(void* stream) {
                     word);
       return fail(FMM_ERR_CUDA, buf);
     }
-    std::snprintf(buf, sizeof buf, "device-side wait timed out (error bits 0x%x)", word);
+    static const char* const kSites[] = {"none", "producer: source slot", "producer: operand stage",
+                                         "MMA: accumulator", "MMA: operand stage", "epilogue: accumulator",
+                                         "transform: source slot", "transform: operand stage", "teardown"};
+    if (rec[1] != 0 && rec[1] < sizeof kSites / sizeof kSites[0])
+      std::snprintf(buf, sizeof buf,
+                    "device-side wait timed out (error bits 0x%x; first: %s, item %d, k-step %u, block %u)", word,
+                    kSites[rec[1]], static_cast<int>(rec[2]), rec[3] & 0xffffu, rec[3] >> 16);
+    else
+      std::snprintf(buf, sizeof buf, "device-side wait timed out (error bits 0x%x)", word);
     return fail(FMM_ERR_TIMEOUT, buf);
   }
   return FMM_OK;

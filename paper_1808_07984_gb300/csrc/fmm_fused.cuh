@@ -58,25 +58,35 @@ __device__ __forceinline__ void split2(float x0, float x1, uint32_t& hi, uint32_
 // Producer of the fused kernels (one thread): for every item, k-step and 32-deep k half, one
 // FP32 tile per source block of the product's A-operand (128 rows x 32 k, 128-byte swizzle),
 // then per source block of its B-operand (32 k x 128 n, this CTA's columns), each into the next
-// slot of an NS-slot ring.  Returns false if a wait gave up or a parameter block named a tensor
-// map outside its table (error bit set).
-template <int NS, bool PAIR>
+// slot of a ring.  RINGS = 1: one ring of NS slots for both k halves; RINGS = 2: k half h goes
+// to ring h (slots h * NS / 2 .. (h + 1) * NS / 2 - 1), so that every slot -- and its pair of
+// barriers -- is only ever consumed by the threads that form that half (a slot shared by two
+// consumer groups could be awaited by one group while the other's use of it is still a phase
+// behind, which the parity of an mbarrier wait cannot tell apart).  Returns false if a wait
+// gave up or a parameter block named a tensor map outside its table (error bit set).
+template <int NS, bool PAIR, int RINGS = 1>
 __device__ __forceinline__ bool fused_producer(const FusedParams& fp, uint8_t* slots, uint64_t* slot_full,
                                                uint64_t* slot_empty, int rank, int first, int stride,
                                                volatile int* abort_flag) {
+  static_assert(RINGS == 1 || RINGS == 2, "one ring, or one per k half");
+  constexpr int NPR = NS / RINGS;  // slots per ring
   const CommonParams& p = fp.c;
   constexpr int TN = PAIR ? 2 * kFusedBN : kFusedBN;
-  int slot = 0;
-  uint32_t sph = 0;
+  int slot[2] = {0, 0};
+  uint32_t sph[2] = {0, 0};
   bool ok = true;
-  auto issue = [&](const CUtensorMap* map, int x, int y) -> bool {
-    if (!mbar_wait(smem_u32(&slot_empty[slot]), sph ^ 1u, p.timeout_ns, abort_flag)) return false;
-    const uint32_t fb = smem_u32(&slot_full[slot]);
+  auto issue = [&](int ring, const CUtensorMap* map, int x, int y, int item, int kb) -> bool {
+    const int sidx = ring * NPR + slot[ring];
+    if (!mbar_wait(smem_u32(&slot_empty[sidx]), sph[ring] ^ 1u, p.timeout_ns, abort_flag)) {
+      record_wait_failure(p.err, kSiteProducerSlot, item, kb);
+      return false;
+    }
+    const uint32_t fb = smem_u32(&slot_full[sidx]);
     mbar_arrive_expect_tx(fb, kSlotBytes);
-    tma_load_2d(smem_u32(slots + slot * kSlotBytes), map, fb, x, y);
-    if (++slot == NS) {
-      slot = 0;
-      sph ^= 1u;
+    tma_load_2d(smem_u32(slots + sidx * kSlotBytes), map, fb, x, y);
+    if (++slot[ring] == NPR) {
+      slot[ring] = 0;
+      sph[ring] ^= 1u;
     }
     return true;
   };
@@ -100,10 +110,11 @@ __device__ __forceinline__ bool fused_producer(const FusedParams& fp, uint8_t* s
     const int b_col = tn * TN + rank * kFusedBN;
     for (int kb = 0; ok && kb < p.nk; ++kb) {
       for (int h = 0; ok && h < 2; ++h) {
+        const int ring = RINGS == 2 ? h : 0;
         for (int w = 0; ok && w < na; ++w)
-          ok = issue(&fp.tmSA[(ablk >> (8 * w)) & 0xff], kb * kBK + 32 * h, a_row);
+          ok = issue(ring, &fp.tmSA[(ablk >> (8 * w)) & 0xff], kb * kBK + 32 * h, a_row, item, kb);
         for (int w = 0; ok && w < nb; ++w)
-          ok = issue(&fp.tmSB[(bblk >> (8 * w)) & 0xff], b_col, kb * kBK + 32 * h);
+          ok = issue(ring, &fp.tmSB[(bblk >> (8 * w)) & 0xff], b_col, kb * kBK + 32 * h, item, kb);
       }
     }
   }

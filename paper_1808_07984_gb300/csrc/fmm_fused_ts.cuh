@@ -10,10 +10,10 @@
 //
 // CTA pairs (clusters of two CTAs) on 256 x 256 output tiles:
 //   warp 0      producer (fused_producer): one FP32 tile per source block and 32-deep k half
-//               into a ring of kSlots 16 KB slots;
+//               into the half's ring of 16 KB slots;
 //   warps 8-15  transform.  Warps 8-11 form k half 0 of every k-step, warps 12-15 half 1, each
-//               group reading only its own half's slots.  Thread (lane quarter q = warp % 4,
-//               lane l) owns A row 32q + l: it adds that row of each A source slot with its
+//               group reading the slots of its own ring (the producer loads half h into ring
+//               h).  Thread (lane quarter q = warp % 4, lane l) owns A row 32q + l: it adds that row of each A source slot with its
 //               sign, splits the 32 sums into BF16 hi / lo and stores them into its CTA's TMEM
 //               at the stage's A columns (32 k per half = 16 columns per term).  It also adds
 //               8 k-rows x 4 columns of each B source slot and writes the split B sums into the
@@ -33,7 +33,7 @@ template <int TERMS>
 struct FusedTsCfg {
   static constexpr int kTileN = 2 * kFusedBN;  // UMMA N of the pair tile
   static constexpr int kStages = 3;            // operand stages (A in TMEM, B in shared memory)
-  static constexpr int kSlots = 6;             // FP32 source slots
+  static constexpr int kSlots = 6;             // FP32 source slots: two rings of three, one per k half
   static constexpr uint32_t kBTermBytes = kBK * kFusedBN * 2;  // 64 k x 128 n BF16 per term
   static constexpr uint32_t kStageBytes = (TERMS == 3 ? 2u : 1u) * kBTermBytes;
   static constexpr uint32_t kSlotOffset = kStages * kStageBytes;
@@ -64,10 +64,16 @@ __device__ __forceinline__ bool mma_role_ts(const CommonParams& p, uint8_t* smem
     int r, tm, tn;
     if (!decode_item(item, p, r, tm, tn, stride)) continue;  // empty item
     // one accumulator: both epilogues have read the previous item's out of TMEM
-    if (!mbar_wait_cluster(smem_u32(&acc_empty[0]), (it & 1) ^ 1u, p.timeout_ns, abort_flag)) return false;
+    if (!mbar_wait_cluster(smem_u32(&acc_empty[0]), (it & 1) ^ 1u, p.timeout_ns, abort_flag)) {
+      record_wait_failure(p.err, kSiteMmaAcc, item, 0);
+      return false;
+    }
     tc_fence_after();
     for (int kb = 0; kb < p.nk; ++kb) {
-      if (!mbar_wait_cluster(smem_u32(&op_full[o]), oph, p.timeout_ns, abort_flag)) return false;
+      if (!mbar_wait_cluster(smem_u32(&op_full[o]), oph, p.timeout_ns, abort_flag)) {
+        record_wait_failure(p.err, kSiteMmaStage, item, kb);
+        return false;
+      }
       tc_fence_after();
       uint8_t* st = smem + o * Cfg::kStageBytes;
       const uint64_t db_hi = make_sdesc_mnmajor_sw128(smem_u32(st), kMnAtom, 1024);
@@ -95,7 +101,11 @@ __device__ __forceinline__ bool mma_role_ts(const CommonParams& p, uint8_t* smem
     ++it;
   }
   // both epilogues have read the last accumulator before the CTAs may retire
-  return it == 0 || mbar_wait_cluster(smem_u32(&acc_empty[0]), (it & 1) ^ 1u, p.timeout_ns, abort_flag);
+  if (it > 0 && !mbar_wait_cluster(smem_u32(&acc_empty[0]), (it & 1) ^ 1u, p.timeout_ns, abort_flag)) {
+    record_wait_failure(p.err, kSiteTeardown, -1, 0);
+    return false;
+  }
+  return true;
 }
 
 template <int TERMS>
@@ -125,7 +135,7 @@ __global__ void __launch_bounds__(fused_threads<8>(), 1) fmm_fused_ts_kernel(con
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) {
       mbar_init(smem_u32(&slot_full[s]), 1);
-      mbar_init(smem_u32(&slot_empty[s]), 4);  // the four transform warps of the slot's k half
+      mbar_init(smem_u32(&slot_empty[s]), 4);  // the four transform warps of the ring's k half
     }
     for (int s = 0; s < S; ++s) {
       mbar_init(smem_u32(&op_full[s]), 2 * 8);  // the transform warps of both CTAs
@@ -160,7 +170,8 @@ __global__ void __launch_bounds__(fused_threads<8>(), 1) fmm_fused_ts_kernel(con
   if (!run) {
     // nothing issued: fall through to the teardown
   } else if (warp == 0) {
-    if (lane == 0 && !fused_producer<NS, true>(fp, slots, slot_full, slot_empty, rank, first, stride, abort_flag)) {
+    if (lane == 0 &&
+        !fused_producer<NS, true, 2>(fp, slots, slot_full, slot_empty, rank, first, stride, abort_flag)) {
       atomicOr(p.err, kErrProducerWait);
       *abort_flag = 1;
       drain_pause(2000000ull);
@@ -190,6 +201,7 @@ __global__ void __launch_bounds__(fused_threads<8>(), 1) fmm_fused_ts_kernel(con
     const int bk0 = tb >> 5;           // first B k-row (of 32) of the half: bk0 + 4v, v < 8
     const int nq = tb & 31;            // B columns 4 nq .. 4 nq + 3
     const uint32_t lane_bits = static_cast<uint32_t>(32 * q) << 16;
+    constexpr int NPR = NS / 2;        // slots of this half's ring
     int slot = 0;
     uint32_t sph = 0;
     int o = 0;
@@ -210,48 +222,47 @@ __global__ void __launch_bounds__(fused_threads<8>(), 1) fmm_fused_ts_kernel(con
         for (int v = 0; v < 8; ++v)
 #pragma unroll
           for (int e = 0; e < 4; ++e) aB[v][e] = 0.f;
-        // the k-step's slots: half 0 (A sources, then B sources), then half 1
-        for (int h = 0; h < 2; ++h) {
-          for (int w = 0; w < na + nb; ++w) {
-            if (h == g && ok) {
-              ok = mbar_wait(smem_u32(&slot_full[slot]), sph, p.timeout_ns, abort_flag);
-              if (ok) {
-                const uint8_t* sl = slots + slot * kSlotBytes;
-                if (w < na) {
-                  const float sg = ((a_neg >> w) & 1u) ? -1.f : 1.f;
+        // this half's slots of the k-step (its own ring): A sources, then B sources
+        for (int w = 0; ok && w < na + nb; ++w) {
+          const int sidx = g * NPR + slot;
+          ok = mbar_wait(smem_u32(&slot_full[sidx]), sph, p.timeout_ns, abort_flag);
+          if (!ok) {
+            if (lane == 0) record_wait_failure(p.err, kSiteTransformSlot, item, kb);
+            break;
+          }
+          const uint8_t* sl = slots + sidx * kSlotBytes;
+          if (w < na) {
+            const float sg = ((a_neg >> w) & 1u) ? -1.f : 1.f;
 #pragma unroll
-                  for (int c = 0; c < 8; ++c) {
-                    const float4 x =
-                        *reinterpret_cast<const float4*>(sl + arow * 128 + ((c ^ (arow & 7)) << 4));
-                    aA[4 * c] = fmaf(sg, x.x, aA[4 * c]);
-                    aA[4 * c + 1] = fmaf(sg, x.y, aA[4 * c + 1]);
-                    aA[4 * c + 2] = fmaf(sg, x.z, aA[4 * c + 2]);
-                    aA[4 * c + 3] = fmaf(sg, x.w, aA[4 * c + 3]);
-                  }
-                } else {
-                  const float sg = ((b_neg >> (w - na)) & 1u) ? -1.f : 1.f;
+            for (int c = 0; c < 8; ++c) {
+              const float4 x = *reinterpret_cast<const float4*>(sl + arow * 128 + ((c ^ (arow & 7)) << 4));
+              aA[4 * c] = fmaf(sg, x.x, aA[4 * c]);
+              aA[4 * c + 1] = fmaf(sg, x.y, aA[4 * c + 1]);
+              aA[4 * c + 2] = fmaf(sg, x.z, aA[4 * c + 2]);
+              aA[4 * c + 3] = fmaf(sg, x.w, aA[4 * c + 3]);
+            }
+          } else {
+            const float sg = ((b_neg >> (w - na)) & 1u) ? -1.f : 1.f;
 #pragma unroll
-                  for (int v = 0; v < 8; ++v) {
-                    const float4 x = *reinterpret_cast<const float4*>(sl + (bk0 + 4 * v) * 512 + nq * 16);
-                    aB[v][0] = fmaf(sg, x.x, aB[v][0]);
-                    aB[v][1] = fmaf(sg, x.y, aB[v][1]);
-                    aB[v][2] = fmaf(sg, x.z, aB[v][2]);
-                    aB[v][3] = fmaf(sg, x.w, aB[v][3]);
-                  }
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&slot_empty[slot]));
-              }
+            for (int v = 0; v < 8; ++v) {
+              const float4 x = *reinterpret_cast<const float4*>(sl + (bk0 + 4 * v) * 512 + nq * 16);
+              aB[v][0] = fmaf(sg, x.x, aB[v][0]);
+              aB[v][1] = fmaf(sg, x.y, aB[v][1]);
+              aB[v][2] = fmaf(sg, x.z, aB[v][2]);
+              aB[v][3] = fmaf(sg, x.w, aB[v][3]);
             }
-            if (++slot == NS) {
-              slot = 0;
-              sph ^= 1u;
-            }
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&slot_empty[sidx]));
+          if (++slot == NPR) {
+            slot = 0;
+            sph ^= 1u;
           }
         }
         if (!ok) break;
         // the stage's previous UMMAs (A in TMEM, B in shared memory) have completed
         if (!mbar_wait(smem_u32(&op_empty[o]), oph ^ 1u, p.timeout_ns, abort_flag)) {
+          if (lane == 0) record_wait_failure(p.err, kSiteTransformStage, item, kb);
           ok = false;
           break;
         }
@@ -305,6 +316,7 @@ __global__ void __launch_bounds__(fused_threads<8>(), 1) fmm_fused_ts_kernel(con
     // every operand-stage release of the even CTA's MMA thread has arrived before the CTA retires
     for (int i = 0; ok && i < S; ++i) {
       ok = mbar_wait(smem_u32(&op_empty[o]), oph ^ 1u, p.timeout_ns, abort_flag);
+      if (!ok && lane == 0) record_wait_failure(p.err, kSiteTeardown, -1, i);
       if (++o == S) {
         o = 0;
         oph ^= 1u;

@@ -97,6 +97,26 @@ enum ErrBits : unsigned {
   kErrBadParams = 64u,  // a parameter block named a tensor map outside its table
 };
 
+// Where a bounded wait gave up first.  The device error record is four words: [0] the error
+// bits above, [1] the site of the first wait that gave up (0 = none), [2] its work item,
+// [3] its k-step (low 16 bits) and block index (high 16 bits); fmm_device_status reports it.
+enum WaitSite : unsigned {
+  kSiteProducerSlot = 1,    // producer: a source slot (or operand stage) to become free
+  kSiteProducerStage = 2,
+  kSiteMmaAcc = 3,          // MMA issuer: the accumulator to be drained by the epilogue
+  kSiteMmaStage = 4,        // MMA issuer: an operand stage to be filled
+  kSiteEpilogueAcc = 5,     // epilogue: an accumulator to be finished
+  kSiteTransformSlot = 6,   // transform: a source slot to be loaded
+  kSiteTransformStage = 7,  // transform: an operand stage to be released by the UMMAs
+  kSiteTeardown = 8,        // final waits before the CTA retires
+};
+__device__ __forceinline__ void record_wait_failure(unsigned int* err, unsigned site, int item, int kb) {
+  if (atomicCAS(err + 1, 0u, site) == 0u) {
+    err[2] = static_cast<unsigned>(item);
+    err[3] = (static_cast<unsigned>(kb) & 0xffffu) | (blockIdx.x << 16);
+  }
+}
+
 struct DestEntry {
   int64_t offset;  // element offset of the destination block's origin inside C
   int32_t rows;    // rows of that block that exist in C (<= h_m)
@@ -461,6 +481,7 @@ __device__ __forceinline__ bool epilogue_role(const Work& work, uint8_t* epi_sme
     const uint32_t acc_par = NACC == 2 ? ((it >> 1) & 1) : (it & 1);
     ++it;
     if (!mbar_wait(smem_u32(&acc_full[acc]), acc_par, timeout_ns, abort_flag)) {
+      if (lane == 0) record_wait_failure(p.err, kSiteEpilogueAcc, item, 0);
       ok = false;
       break;
     }
