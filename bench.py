@@ -59,6 +59,8 @@ def parse_args():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the short measurements of the other configurations")
     ap.add_argument("--extra-steps", type=int, default=3)
+    ap.add_argument("--no-e2e", action="store_true",
+                    help="skip the end-to-end measurement through host buffers (sweeps)")
     return ap.parse_args()
 
 
@@ -604,62 +606,64 @@ def main():
     # and its C back to pinned host memory inside the timed region.  Two device buffer sets
     # and three streams (H2D, compute, D2H) let the copies of one step overlap the products
     # of its neighbours, as a serving loop would run.
-    bufs = [(A_d, B_d, C_d)] + [(torch.empty_like(A_d), torch.empty_like(B_d), torch.empty_like(C_d))]
-    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
-    C_hs = [C_h, torch.empty_like(C_h).pin_memory()]
+    e2e = None
+    if not a.no_e2e:
+        bufs = [(A_d, B_d, C_d)] + [(torch.empty_like(A_d), torch.empty_like(B_d), torch.empty_like(C_d))]
+        s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+        C_hs = [C_h, torch.empty_like(C_h).pin_memory()]
 
-    def e2e_loop(nsteps):
-        # buffer set b: step i's inputs may be overwritten once step i-2's product has read
-        # them, its C once step i-2's result has been copied out; so the input copies of one
-        # step and the output copy of another run at the same time (both directions of the
-        # host link) while a third step's product computes
-        ev_in = [torch.cuda.Event() for _ in range(2)]
-        ev_done = [None, None]
-        ev_free = [None, None]
-        for i in range(nsteps):
-            b = i % 2
-            Ab, Bb, Cb = bufs[b]
-            with torch.cuda.stream(s_in):
-                if ev_done[b] is not None:
-                    s_in.wait_event(ev_done[b])
-                Ab.copy_(A_h, non_blocking=True)
-                Bb.copy_(B_h, non_blocking=True)
-                ev_in[b].record(s_in)
-            stream.wait_event(ev_in[b])
-            if ev_free[b] is not None:
-                stream.wait_event(ev_free[b])
-            fmm.gemm(Ab, Bb, Cb, 1.0, 0.0, levels=a.levels, variant=a.variant, algo=a.algo,
-                     tile_n=a.tile_n, workspace=ws, stream=stream)
-            ev_done[b] = torch.cuda.Event()
-            ev_done[b].record(stream)
-            with torch.cuda.stream(s_out):
-                s_out.wait_event(ev_done[b])
-                C_hs[b].copy_(Cb, non_blocking=True)
-                ev_free[b] = torch.cuda.Event()
-                ev_free[b].record(s_out)
-        stream.wait_stream(s_in)
-        stream.wait_stream(s_out)
+        def e2e_loop(nsteps):
+            # buffer set b: step i's inputs may be overwritten once step i-2's product has read
+            # them, its C once step i-2's result has been copied out; so the input copies of one
+            # step and the output copy of another run at the same time (both directions of the
+            # host link) while a third step's product computes
+            ev_in = [torch.cuda.Event() for _ in range(2)]
+            ev_done = [None, None]
+            ev_free = [None, None]
+            for i in range(nsteps):
+                b = i % 2
+                Ab, Bb, Cb = bufs[b]
+                with torch.cuda.stream(s_in):
+                    if ev_done[b] is not None:
+                        s_in.wait_event(ev_done[b])
+                    Ab.copy_(A_h, non_blocking=True)
+                    Bb.copy_(B_h, non_blocking=True)
+                    ev_in[b].record(s_in)
+                stream.wait_event(ev_in[b])
+                if ev_free[b] is not None:
+                    stream.wait_event(ev_free[b])
+                fmm.gemm(Ab, Bb, Cb, 1.0, 0.0, levels=a.levels, variant=a.variant, algo=a.algo,
+                         tile_n=a.tile_n, workspace=ws, stream=stream)
+                ev_done[b] = torch.cuda.Event()
+                ev_done[b].record(stream)
+                with torch.cuda.stream(s_out):
+                    s_out.wait_event(ev_done[b])
+                    C_hs[b].copy_(Cb, non_blocking=True)
+                    ev_free[b] = torch.cuda.Event()
+                    ev_free[b].record(s_out)
+            stream.wait_stream(s_in)
+            stream.wait_stream(s_out)
 
-    e2e_loop(max(2, a.warmup))
-    torch.cuda.synchronize()
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    s_in.wait_stream(stream)
-    s_out.wait_stream(stream)
-    e2e_loop(a.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    fmm.device_status()
-    ms_e2e = slowest(e0.elapsed_time(e1) / a.steps)
-    e2e = {"value": job_value(world, flops, ms_e2e), "unit": UNIT,
-           "h2d_bytes_per_step": int(A_h.numel() * 4 + B_h.numel() * 4),
-           "d2h_bytes_per_step": int(C_h.numel() * 4), "ms_per_step": ms_e2e,
-           "overlap": "H2D, compute and D2H on three streams, two device buffer sets; the H2D of "
-                      "one step, the D2H of another and the product of a third run concurrently"}
-    del bufs
+        e2e_loop(max(2, a.warmup))
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s_in.wait_stream(stream)
+        s_out.wait_stream(stream)
+        e2e_loop(a.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        fmm.device_status()
+        ms_e2e = slowest(e0.elapsed_time(e1) / a.steps)
+        e2e = {"value": job_value(world, flops, ms_e2e), "unit": UNIT,
+               "h2d_bytes_per_step": int(A_h.numel() * 4 + B_h.numel() * 4),
+               "d2h_bytes_per_step": int(C_h.numel() * 4), "ms_per_step": ms_e2e,
+               "overlap": "H2D, compute and D2H on three streams, two device buffer sets; the H2D of "
+                          "one step, the D2H of another and the product of a third run concurrently"}
+        del bufs
 
     if rank != 0:
         if dist is not None:

@@ -139,7 +139,12 @@ typedef struct fmm_options {
                          2 = CTA pairs only: the A-operand sums stored in tensor memory
                          (tcgen05.st) and read from there by the UMMAs, the B-operand sums in
                          shared memory (half the shared-memory traffic of the operand tiles) */
-    int reserved[3]; /* zero */
+    int store_first; /* packed algorithm, beta = 0, levels >= 1: 0 = automatic (on), 1 = off (C is
+                        zeroed first and every product adds into it), 2 = on: the products run in
+                        a few launch phases so that the first update of every C block stores it
+                        (no zeroing pass, no read of C by those updates); not with the pipelined,
+                        deterministic or outside-scaling modes, nor in batched plans */
+    int reserved[2]; /* zero */
 } fmm_options;
 
 /* Bytes of workspace fmm_gemm needs for this problem (0 when none).  Returns

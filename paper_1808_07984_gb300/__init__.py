@@ -42,7 +42,7 @@ class _Options(ctypes.Structure):
                 ("schedule", ctypes.c_int), ("bk", ctypes.c_int), ("cta_pair", ctypes.c_int),
                 ("round_tiles", ctypes.c_int), ("fringe", ctypes.c_int), ("pipeline", ctypes.c_int),
                 ("basis", ctypes.c_int), ("deterministic", ctypes.c_int), ("outer_scaling", ctypes.c_int),
-                ("fused_kernel", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("fused_kernel", ctypes.c_int), ("store_first", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 _lib = None
@@ -147,8 +147,9 @@ FUSED_KERNELS = {"auto": 0, "smem": 1, "tmem": 2}
 
 def _opts(algo="auto", tile_n=0, num_ctas=0, schedule="auto", bk=0, cta_pair=None, round_tiles=0,
           pipeline=None, fringe="pad", basis="strassen", deterministic=False, outer_scaling=False,
-          fused_kernel="auto"):
+          fused_kernel="auto", store_first=None):
     o = _Options()
+    o.store_first = 0 if store_first is None else (2 if store_first else 1)
     o.fused_kernel = FUSED_KERNELS[fused_kernel] if isinstance(fused_kernel, str) else int(fused_kernel)
     o.outer_scaling = 1 if outer_scaling else 0
     o.deterministic = 1 if deterministic else 0
@@ -192,7 +193,8 @@ def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
          variant="split3", algo="auto", tile_n: int = 0, num_ctas: int = 0,
          workspace=None, stream=None, schedule="auto", bk: int = 0, cta_pair=None,
          round_tiles: int = 0, pipeline=None, fringe="pad", basis="strassen",
-         deterministic: bool = False, outer_scaling: bool = False, fused_kernel="auto"):
+         deterministic: bool = False, outer_scaling: bool = False, fused_kernel="auto",
+         store_first=None):
     """C = alpha * A @ B + beta * C on the current CUDA device (torch tensors).
 
     A (m x k) and B (k x n) are row-major CUDA tensors of the element type the
@@ -209,7 +211,10 @@ def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
     ownership mode, bitwise reproducible results.  ``outer_scaling``: exact power-of-two
     scaling of the rows of A and columns of B around the product (badly scaled inputs).
     ``fused_kernel`` (fused and hybrid algorithms): "auto", "smem" (both operands' sums in shared
-    memory) or "tmem" (CTA pairs: the A-operand sums in tensor memory).
+    memory) or "tmem" (CTA pairs: the A-operand sums in tensor memory).  ``store_first``
+    (packed, beta = 0): None = automatic (on), True / False = the first update of every C
+    block stores it (products in launch phases, no zeroing pass), or zero C and add every
+    product.
     ``levels="auto"``: the level count and basis the analytic model (``model.py``) predicts
     fastest for this shape and variant (classical, Strassen at one or two levels, or the
     <3,2,3> basis); ``basis`` is then ignored.
@@ -245,7 +250,7 @@ def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
     ws_ptr = workspace.data_ptr() if workspace is not None else None
     ws_bytes = workspace.numel() if workspace is not None else 0
     o = _opts(algo, tile_n, num_ctas, schedule, bk, cta_pair, round_tiles, pipeline, fringe, basis,
-              deterministic, outer_scaling, fused_kernel)
+              deterministic, outer_scaling, fused_kernel, store_first)
     st = load().fmm_gemm_ex(m, n, k, float(alpha), A.data_ptr(), max(A.stride(0), 1),
                             B.data_ptr(), max(B.stride(0), 1), float(beta), C.data_ptr(),
                             max(C.stride(0), 1), int(levels), v, ws_ptr, ws_bytes,

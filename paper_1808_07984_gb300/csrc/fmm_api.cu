@@ -320,6 +320,7 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
                                                : "the fused and hybrid algorithms use 128-wide tiles");
     pl.tile_n = fused_n;
   }
+  if (opt && (opt->store_first < 0 || opt->store_first > 2)) return fail(FMM_ERR_ARG, "store_first must be 0, 1 or 2");
   const int fk = opt ? opt->fused_kernel : 0;
   if (fk < 0 || fk > 2) return fail(FMM_ERR_ARG, "fused_kernel must be 0, 1 or 2");
   if (fk == 2 && on_chip && !pl.pair)
@@ -456,8 +457,11 @@ fmm_status fill_common(CommonParams& c, const Plan& pl, const std::vector<Produc
       de.cols = static_cast<int32_t>(cols);
       de.coef = alpha * static_cast<float>(t.sign);
       de.block = t.block;
+      de.store = 0;
+      de.pad = 0;
     }
     c.prod[i].count = cnt;
+    c.prod[i].sum_index = static_cast<int32_t>(i);
   }
   if (c.c_tma) {
     // one FP32 map per non-empty destination block, clipped to the block's extent in C
@@ -778,7 +782,45 @@ struct PackedJob {
   PackedParams params;
   // pipelined plans: one parameter block per top-level product (its 7^(L-1) products)
   std::vector<PackedParams> chunks;
+  // store-first plans (beta = 0): one parameter block per launch phase; C is not zeroed
+  std::vector<PackedParams> phases;
 };
+
+// Launch phases in which, with beta = 0, the first update of every C block is a store: no
+// zeroing pass before the products and no read of C by the first update of each block.  A
+// product joins the current phase unless one of its destination blocks is being stored by a
+// product already in it; it stores into each of its blocks that no earlier phase has written
+// and adds into the others.  Phases run as separate launches in stream order, so every store
+// has landed before any addition into its block.  Sets DestEntry::store; returns the product
+// lists of the phases (Strassen: 1 + 4 + 2 products at one level, 1 + 12 + 24 + 12 at two).
+std::vector<std::vector<int>> plan_store_phases(CommonParams& c) {
+  const int R = c.num_products;
+  std::vector<int> phase_of(R, -1);
+  bool written[kMaxSources] = {};
+  std::vector<std::vector<int>> phases;
+  int left = R;
+  while (left > 0) {
+    bool storing[kMaxSources] = {};
+    std::vector<int> ph;
+    for (int r = 0; r < R; ++r) {
+      if (phase_of[r] >= 0) continue;
+      bool ok = true;
+      for (int d = 0; d < c.prod[r].count; ++d) ok = ok && !storing[c.prod[r].d[d].block];
+      if (!ok) continue;
+      phase_of[r] = static_cast<int>(phases.size());
+      ph.push_back(r);
+      --left;
+      for (int d = 0; d < c.prod[r].count; ++d) {
+        DestEntry& de = c.prod[r].d[d];
+        de.store = written[de.block] ? 0 : 1;
+        if (de.store) storing[de.block] = true;
+      }
+    }
+    for (int b = 0; b < kMaxSources; ++b) written[b] = written[b] || storing[b];
+    phases.push_back(ph);
+  }
+  return phases;
+}
 
 // batched = true: the job joins a batched launch, which never pipelines.
 fmm_status prepare_packed(const Plan& pl, int64_t m, int64_t n, int64_t k, float alpha, Operand a,
@@ -933,6 +975,23 @@ fmm_status prepare_packed(const Plan& pl, int64_t m, int64_t n, int64_t k, float
     job.pl.pipeline = true;
   if (batched) job.pl.pipeline = false;
   job.chunks.clear();
+  job.phases.clear();
+  const int sf = opt ? opt->store_first : 0;
+  if (sf == 0 || sf == 2) {
+    if (beta == 0.0f && pl.R > 1 && !batched && !job.pl.pipeline && !pl.deterministic && !pl.outer_scaling &&
+        pl.algo == FMM_ALGO_PACKED) {
+      const std::vector<std::vector<int>> ph = plan_store_phases(pp->c);
+      const int64_t tiles = static_cast<int64_t>(pp->c.tiles_m) * pp->c.tiles_n;
+      job.phases.resize(ph.size(), *pp);
+      for (size_t i = 0; i < ph.size(); ++i) {
+        PackedParams& q = job.phases[i];
+        const int P = static_cast<int>(ph[i].size());
+        for (int j = 0; j < kMaxProducts; ++j) q.c.prod[j] = j < P ? pp->c.prod[ph[i][j]] : ProductDests{};
+        q.c.num_products = P;
+        q.c.num_items = static_cast<int32_t>(P * tiles);
+      }
+    }
+  }
   if (job.pl.pipeline) {
     // top-level product c: products c * P .. c * P + P - 1 (P = 7^(L-1)), kernel-local 0 .. P-1
     const int P = pl.R / 7;
@@ -940,7 +999,10 @@ fmm_status prepare_packed(const Plan& pl, int64_t m, int64_t n, int64_t k, float
     for (int c = 0; c < 7 && st == FMM_OK; ++c) {
       PackedParams& q = job.chunks[c];
       st = encode_maps(&q, c * P, P);
-      for (int j = 0; j < kMaxProducts; ++j) q.c.prod[j] = j < P ? pp->c.prod[c * P + j] : ProductDests{};
+      for (int j = 0; j < kMaxProducts; ++j) {
+        q.c.prod[j] = j < P ? pp->c.prod[c * P + j] : ProductDests{};
+        q.c.prod[j].sum_index = j;  // this launch's maps start at top-level product c's sums
+      }
       q.c.num_products = P;
       const int64_t tiles = static_cast<int64_t>(pp->c.tiles_m) * pp->c.tiles_n;
       q.c.num_items = static_cast<int32_t>(
@@ -1069,7 +1131,7 @@ fmm_status launch_passes(const PackedJob& job, const DeviceInfo& dev, cudaStream
                            : launch_outer_rescale(job.C, job.m, job.n, job.ldc, job.sa.row_maxbits,
                                                   job.sb.col_maxbits, -1, job.beta, dev.sms, s);
     if (e != cudaSuccess) return cuda_fail(e, "outside-scaling passes");
-  } else if (job.beta != 1.0f && !(job.has_work && job.params.c.c_store)) {
+  } else if (job.beta != 1.0f && !(job.has_work && (job.params.c.c_store || !job.phases.empty()))) {
     PhaseScope ps(kPhaseBeta, s);
     cudaError_t e = launch_beta(job.C, job.m, job.n, job.ldc, job.beta, dev.sms, s);
     if (e != cudaSuccess) return cuda_fail(e, "beta pass");
@@ -1145,11 +1207,18 @@ fmm_status gemm_core(const Plan& pl, int64_t m, int64_t n, int64_t k, float alph
   }
   if (st == FMM_OK) st = launch_passes(*job, dev, s);
   if (st == FMM_OK && job->has_work) {
-    ka->one = job->params;
-    cudaError_t e;
-    {
+    cudaError_t e = cudaSuccess;
+    if (job->phases.empty()) {
+      ka->one = job->params;
       PhaseScope ps(kPhaseTensor, s);
       e = launch_packed(*ka, pl.tile_n, pl.terms, pl.bf16, pl.a_mn, pl.b_mn, pl.bk, pl.pair, job->grid, s);
+    } else {
+      // store-first phases, in stream order (each phase's stores land before the next adds)
+      PhaseScope ps(kPhaseTensor, s, static_cast<int>(job->phases.size()));
+      for (size_t i = 0; i < job->phases.size() && e == cudaSuccess; ++i) {
+        ka->one = job->phases[i];
+        e = launch_packed(*ka, pl.tile_n, pl.terms, pl.bf16, pl.a_mn, pl.b_mn, pl.bk, pl.pair, job->grid, s);
+      }
     }
     if (e != cudaSuccess) st = cuda_fail(e, "tensor-core pass");
     if (st == FMM_OK && pl.outer_scaling) {

@@ -123,11 +123,13 @@ struct DestEntry {
   int32_t cols;    // columns of that block that exist in C (<= h_n)
   float coef;      // alpha * W[c, r]
   int32_t block;   // destination block index bi * 2^L + bj (selects its tensor map)
+  int32_t store;   // 1: this is the block's first update (beta = 0): store, do not add
+  int32_t pad;
 };
 
 struct ProductDests {
   int32_t count;
-  int32_t pad;
+  int32_t sum_index;  // index of the product's operand sums (3-D tensor maps, panel maxima)
   DestEntry d[kMaxDest];
 };
 
@@ -500,8 +502,8 @@ __device__ __forceinline__ bool epilogue_role(const Work& work, uint8_t* epi_sme
     // undo the operand scaling of this (product, tile) exactly: 2^(s_A + s_B); rows past the
     // last A panel (odd CTA of a last, half-empty pair tile) are zero and need none
     const int shift = (p.maxbits_a && tm_cta < p.panels_a)
-                          ? panel_shift(p.maxbits_a[r * p.panels_a + tm_cta]) +
-                                panel_shift(p.maxbits_b[r * p.panels_b + tn])
+                          ? panel_shift(p.maxbits_a[pd.sum_index * p.panels_a + tm_cta]) +
+                                panel_shift(p.maxbits_b[pd.sum_index * p.panels_b + tn])
                           : 0;
     // destinations are grouped by the sign of W[c, r] (coef = alpha * W[c, r])
     auto wneg = [&](const DestEntry& de) { return ((de.coef < 0.f) != (alpha < 0.f)) ? 1 : 0; };
@@ -545,7 +547,7 @@ __device__ __forceinline__ bool epilogue_role(const Work& work, uint8_t* epi_sme
             for (int d = 0; d < kMaxDest; ++d) {
               const DestEntry& de = pd.d[d];
               if (d >= pd.count || wneg(de) != sg) continue;
-              if (c_store)
+              if (c_store || de.store)
                 tma_store_2d(&tmC[de.block], smem_u32(sb), col0, row0);
               else
                 tma_reduce_add_2d(&tmC[de.block], smem_u32(sb), col0, row0);
@@ -566,7 +568,7 @@ __device__ __forceinline__ bool epilogue_role(const Work& work, uint8_t* epi_sme
             const int nrows = min(32, de.rows - row0);
             // two loops, not one with the branch inside: the reduction loop is the hot one
             // (Strassen destinations), and a branch in it slows it measurably
-            if (c_store) {
+            if (c_store || de.store) {
 #pragma unroll 4
               for (int i = 0; i < nrows; ++i) {
                 const float x = *reinterpret_cast<const float*>(sb + i * 128 + (((lane >> 2) ^ (i & 7)) << 4) +
@@ -709,6 +711,7 @@ __global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_co
         if (!decode_item(local, p, r, tm, tn, stride)) continue;  // empty item
         const int a_row = (PAIR ? 2 * tm + rank : tm) * kBM;  // first A row of this CTA
         const int b_col = tn * BN + rank * BNL;               // first B column of this CTA
+        const int z = p.prod[r].sum_index;                    // the product's operand sums
         for (int kb = 0; kb < p.nk; ++kb) {
           if (!mbar_wait(smem_u32(&empty[stage]), phase ^ 1u, timeout_ns, abort_flag)) {
             ok = false;
@@ -721,9 +724,9 @@ __global__ void __launch_bounds__(kThreads, 1) fmm_packed_kernel(const __grid_co
           if (rank == 0) mbar_arrive_expect_tx(fb_local, (PAIR ? 2 : 1) * Cfg::kStageBytes);
           auto load = [&](uint32_t dst, const CUtensorMap* map, int c0, int c1) {
             if (PAIR)
-              tma_load_3d_pair(dst, map, fb, c0, c1, r);
+              tma_load_3d_pair(dst, map, fb, c0, c1, z);
             else
-              tma_load_3d(dst, map, fb, c0, c1, r);
+              tma_load_3d(dst, map, fb, c0, c1, z);
           };
           if (A_MN) {
             // A operand sums stored k-rows x m-cols: two boxes of 64 (m) x BK (k)

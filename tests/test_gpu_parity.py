@@ -38,7 +38,7 @@ def _to_device(X, ld_pad, dtype):
 def run(m, n, k, levels, variant="split3", dist="uniform", seed=0, alpha=1.0, beta=0.0,
         tile_n=0, pads=(0, 0, 0), c_fill=None, rows=None, schedule="auto", algo="auto", bk=0,
         cta_pair=None, round_tiles=0, pipeline=None, fringe="pad", basis="strassen",
-        deterministic=False, outer_scaling=False, fused_kernel="auto"):
+        deterministic=False, outer_scaling=False, fused_kernel="auto", store_first=None):
     A, B = synth.problem(m, n, k, seed, dist)
     in_dtype = {"bf16": torch.bfloat16, "f16": torch.float16}.get(variant, torch.float32)
     Ad = _to_device(A, pads[0], in_dtype)
@@ -54,7 +54,7 @@ def run(m, n, k, levels, variant="split3", dist="uniform", seed=0, alpha=1.0, be
     fmm.gemm(Ad, Bd, Cd, alpha=alpha, beta=beta, levels=levels, variant=variant, tile_n=tile_n,
              schedule=schedule, algo=algo, bk=bk, cta_pair=cta_pair, round_tiles=round_tiles,
              pipeline=pipeline, fringe=fringe, basis=basis, deterministic=deterministic,
-             outer_scaling=outer_scaling, fused_kernel=fused_kernel)
+             outer_scaling=outer_scaling, fused_kernel=fused_kernel, store_first=store_first)
     fmm.device_status()
     # sampled rows are gathered on the device (a full-size C is several GB)
     Csel = Cd if rows is None else Cd[torch.from_numpy(np.asarray(rows)).to(Cd.device)]
@@ -827,6 +827,48 @@ def test_full_size_int_sampled_rows_bit_exact(m, n, k, levels):
     rows = np.unique(np.concatenate([[0, m - 1], synth.rng(m + k).integers(0, m, size=6)]))
     C, C64, _, _ = run(m, n, k, levels, "split3", dist="int", seed=k + levels, rows=rows)
     np.testing.assert_array_equal(C, C64)
+
+
+# ------------------------------------------- store-first phases (beta = 0)
+@pytest.mark.parametrize("store_first", [True, False])
+@pytest.mark.parametrize("pad_c", [0, 1])
+@pytest.mark.parametrize("levels,basis", [(1, "strassen"), (2, "strassen"), (1, "winograd"), (1, "b323")])
+@pytest.mark.parametrize("m,n,k", [(300, 520, 200), (129, 257, 65), (1000, 1200, 300), (520, 8, 400)])
+def test_store_first_phases_bit_exact(m, n, k, levels, basis, pad_c, store_first):
+    """beta = 0: the products run in launch phases whose first update of each C block is a
+    store; C starts as NaN, so a block that some product adds into before it was stored, or
+    that no product stores, shows up.  Aligned C (TMA stores) and unaligned C (element-wise
+    stores), every basis, fringe blocks."""
+    C, C64, _, _ = run(m, n, k, levels, "split3", dist="int", seed=m + k + levels, basis=basis,
+                       pads=(0, 0, pad_c), c_fill=float("nan"), store_first=store_first)
+    np.testing.assert_array_equal(C, C64)
+
+
+@pytest.mark.parametrize("levels", [1, 2])
+def test_store_first_negative_alpha_and_float(levels):
+    A, B = synth.problem(136, 264, 72, 93, "int")
+    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    Cd = torch.full((136, 264), float("nan"), device="cuda")
+    fmm.gemm(Ad, Bd, Cd, alpha=-2.0, beta=0.0, levels=levels)
+    fmm.device_status()
+    np.testing.assert_array_equal(Cd.cpu().numpy(), oracle.classical(A, B, None, -2.0, 0.0))
+    C, C64, An, Bn = run(700, 900, 1100, levels, "split3", dist="gaussian", seed=94, c_fill=float("nan"))
+    assert oracle.normwise_error(C, C64, An, Bn) <= tolerance("split3", levels, 1100)
+
+
+def test_store_first_backward_and_16bit():
+    """The backward products (transposed operands) and the 16-bit arithmetic take the phases too."""
+    A, B = synth.problem(300, 200, 136, 95, "int")
+    dC = synth.small_int((300, 200), 96)
+    for levels in (1, 2):
+        dA, dB = fmm.gemm_backward(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(),
+                                   torch.from_numpy(dC).cuda(), levels=levels)
+        fmm.device_status()
+        np.testing.assert_array_equal(dA.cpu().numpy(), oracle.classical(dC, np.ascontiguousarray(B.T)))
+        np.testing.assert_array_equal(dB.cpu().numpy(), oracle.classical(np.ascontiguousarray(A.T), dC))
+        for variant in ("bf16", "f16"):
+            C, C64, _, _ = run(300, 520, 200, levels, variant, dist="int", seed=97, c_fill=float("nan"))
+            np.testing.assert_array_equal(C, C64)
 
 
 # ----------------------------------------------------------- failure path
