@@ -284,7 +284,8 @@ def run_extras(a, fmm, torch, dev, stream, peak, peak_src):
             mma = mma_flops(m, n, k, lv, variant, basis) * (flops / (2.0 * m * n * k))
             r = {"levels": lv, "variant": variant, "basis": basis,
                  "value": flops / (ms * 1e-3) * 1e-12, "ms_per_step": ms,
-                 "roofline": {"bound": "tensor", "kernel": "fmm_packed_kernel",
+                 "roofline": {"bound": "tensor",
+                              "kernel": "fmm_fused_ts_kernel" if label.startswith("hybrid") else "fmm_packed_kernel",
                               "kernel_ms_per_step": ker_ms,
                               "launches_per_step": prof["tensor"][1] / steps,
                               "achieved": mma / (ker_ms * 1e-3) * 1e-12 if ker_ms > 0 else None,
@@ -348,11 +349,17 @@ def run_extras(a, fmm, torch, dev, stream, peak, peak_src):
     for variant in ("split3", "plain_bf16"):
         ch = [("strassen_L2", 2, "strassen"), ("strassen_L1", 1, "strassen"), ("classical", 0, "strassen")]
         ws = ws_for(m, n, k, ch, variant)
+        wsh = torch.empty(max(fmm.workspace_size(m, n, k, 2, variant, "hybrid"), 256), dtype=torch.uint8,
+                          device=dev)
+        runs = split3_runs(Ad, Bd, Cd, ws, ch, variant)
+        # the same product with the 49 bottom-level operand sums formed on chip (hybrid scheme)
+        runs["hybrid_L2"] = (2, variant, "strassen",
+                             lambda v=variant, w=wsh: fmm.gemm(Ad, Bd, Cd, 1.0, 0.0, levels=2, variant=v,
+                                                               algo="hybrid", workspace=w, stream=stream))
         entry(f"strassen-{variant}-odd-m{m}-n{n}-k{k}", {"variant": variant, "lda": k, "ldb": n, "ldc": n,
               "inputs": "N(0,1) float32, seeded; tight (odd) leading dimensions"}, m, n, k,
-              split3_runs(Ad, Bd, Cd, ws, ch, variant), 2.0 * m * n * k,
-              lambda: sampled_error(oracle, Cd, A, B, rows))
-        del ws
+              runs, 2.0 * m * n * k, lambda: sampled_error(oracle, Cd, A, B, rows))
+        del ws, wsh
     del Ad, Bd, Cd, A, B
 
     # C3: BF16 linear layer, forward C = A B and backward dA = dC B^T, dB = A^T dC

@@ -275,9 +275,13 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
     return fail(FMM_ERR_UNSUPPORTED, "the hybrid algorithm is a two-level scheme (levels = 2)");
   pl.algo = algo == FMM_ALGO_AUTO ? FMM_ALGO_PACKED : algo;
   const bool on_chip = pl.algo == FMM_ALGO_FUSED || pl.algo == FMM_ALGO_HYBRID;
-  if (on_chip && (pl.in_type != kInF32 || a_mn || !b_mn))
+  // the fused kernels read FP32 source tiles: the caller's FP32 operands (fused), or the FP32
+  // top-level sums the hybrid scheme forms from FP32 or BF16 operands
+  if (on_chip && (a_mn || !b_mn))
+    return fail(FMM_ERR_UNSUPPORTED, "the fused and hybrid algorithms are built for the forward product");
+  if (on_chip && pl.in_type != kInF32 && !(pl.algo == FMM_ALGO_HYBRID && pl.in_type == kInBF16))
     return fail(FMM_ERR_UNSUPPORTED,
-                "the fused and hybrid algorithms take FP32 A and B (split3 or plain_bf16) in the forward product");
+                "the fused algorithm takes FP32 A and B (split3 or plain_bf16); the hybrid also BF16");
   pl.tile_n = (opt && opt->tile_n) ? opt->tile_n : 0;
   const int sched = opt ? opt->schedule : 0;
   if (sched < 0 || sched > 2) return fail(FMM_ERR_ARG, "schedule must be 0, 1 or 2");
@@ -650,7 +654,7 @@ fmm_status gemm_hybrid(const Plan& pl, int64_t m, int64_t n, int64_t k, float al
   cudaError_t e;
   {
     PhaseScope ps(kPhasePack, s);
-    e = launch_operand_sums(sa, 1, false, false, kInF32, 0, dev.sms, s);
+    e = launch_operand_sums(sa, 1, false, false, pl.in_type, 0, dev.sms, s);
   }
   if (e != cudaSuccess) return cuda_fail(e, "top-level operand sums (A)");
   SumParams sb = sa;
@@ -666,7 +670,7 @@ fmm_status gemm_hybrid(const Plan& pl, int64_t m, int64_t n, int64_t k, float al
   sb.vec_ok = (reinterpret_cast<uintptr_t>(B) % 16 == 0 && ldb % 4 == 0) ? 1 : 0;
   {
     PhaseScope ps(kPhasePack, s);
-    e = launch_operand_sums(sb, 1, true, false, kInF32, 0, dev.sms, s);
+    e = launch_operand_sums(sb, 1, true, false, pl.in_type, 0, dev.sms, s);
   }
   if (e != cudaSuccess) return cuda_fail(e, "top-level operand sums (B)");
 

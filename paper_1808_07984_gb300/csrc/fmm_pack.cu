@@ -443,6 +443,9 @@ static cudaError_t launch_sums_b(const SumParams& p, int levels, int in_type, in
   }
   if (in_type == kInBF16 && p.terms == 1 && !out16)
     return launch_sums_l<__nv_bfloat16, 0, IS_B, TQ, 1>(p, levels, num_sms, s);
+  // FP32 sums of BF16 operands (top level of the hybrid scheme)
+  if (in_type == kInBF16 && p.terms == 0)
+    return levels == 1 ? launch_sums_t<__nv_bfloat16, 0, 1, IS_B, TQ, 0>(p, num_sms, s) : cudaErrorInvalidValue;
   if (in_type == kInF16 && p.terms == 1 && out16) {
     if (!p.maxbits) return launch_sums_l<__half, 1, IS_B, TQ, 1>(p, levels, num_sms, s);
     // two passes: panel maxima, then the sums scaled by 2^-s (maxbits zeroed by the caller)

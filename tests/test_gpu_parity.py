@@ -699,6 +699,34 @@ def test_hybrid_full_size_sampled_rows():
     assert oracle.normwise_error(C, C64, An, Bn) <= 1e-6
 
 
+@pytest.mark.parametrize("m,n,k", [(16, 16, 16), (300, 520, 200), (129, 257, 65), (1000, 1200, 300)])
+def test_hybrid_bf16_operands_int_bit_exact(m, n, k):
+    """BF16 operands on the hybrid scheme: FP32 top-level sums of the BF16 values, the 49
+    bottom-level sums formed on chip and rounded once to BF16."""
+    C, C64, _, _ = run(m, n, k, 2, "bf16", dist="int", seed=11 * m + n + k, algo="hybrid")
+    np.testing.assert_array_equal(C, C64)
+
+
+def test_hybrid_bf16_operands_float():
+    C, C64, An, Bn = run(640, 384, 768, 2, "bf16", dist="gaussian", seed=12, algo="hybrid")
+    assert oracle.normwise_error(C, C64, An, Bn) <= tolerance("bf16", 2, 768)
+
+
+@pytest.mark.parametrize("pads", [(1, 3, 1), (0, 0, 1), (5, 0, 0)])
+def test_hybrid_unaligned_leading_dimensions_bit_exact(pads):
+    """Odd leading dimensions: the top-level sum pass reads any row stride and writes aligned
+    FP32 sums, so the on-chip bottom level runs unchanged; unaligned C takes the element-wise
+    write-back."""
+    C, C64, _, _ = run(300, 520, 203, 2, "split3", dist="int", seed=13, algo="hybrid", pads=pads)
+    np.testing.assert_array_equal(C, C64)
+
+
+def test_hybrid_odd_30001_29999_4097_sampled_rows():
+    rows = np.unique(np.concatenate([[0, 30000], synth.rng(19).integers(0, 30001, size=6)]))
+    C, C64, An, Bn = run(30001, 29999, 4097, 2, "split3", dist="gaussian", seed=24, rows=rows, algo="hybrid")
+    assert oracle.normwise_error(C, C64, An, Bn) <= tolerance("split3", 2, 4097)
+
+
 # ------------------------------------------- large odd sizes with dynamic fringes
 @pytest.mark.parametrize("variant,levels", [("split3", 2), ("plain_bf16", 2), ("split3", 0)])
 def test_odd_30001_29999_4097_sampled_rows(variant, levels):
