@@ -734,8 +734,9 @@ def main():
         "operand_sums": {"bound": "hbm", "algorithmic_bytes_per_step": sum_bytes, "ms_per_step": pack_ms,
                          "achieved_gbs": sum_bytes / (pack_ms * 1e-3) * 1e-9 if pack_ms > 0 else None},
         "beta": {"bound": "hbm",
-                 "kind": ("none: the classical product stores C (beta = 0)" if a.levels == 0 and
-                          a.algo in ("auto", "packed") else "C zeroed by cudaMemsetAsync (beta = 0)"),
+                 "kind": (("none: the classical product stores C (beta = 0)" if a.levels == 0 else
+                           "none: the first update of each C block stores it (store-first launch phases)")
+                          if prof["beta"][1] == 0 else "C zeroed by cudaMemsetAsync (beta = 0)"),
                  "algorithmic_bytes_per_step": 4 * m * n, "ms_per_step": beta_ms,
                  "achieved_gbs": 4 * m * n / (beta_ms * 1e-3) * 1e-9 if beta_ms > 0 else None},
         "peak_gbs": hbm, "peak_source": "measured (HBM copy)" if hbm else None,
