@@ -207,9 +207,11 @@ fmm_status fmm_gemm_backward(int64_t m, int64_t n, int64_t k,
                              const float* dC, int64_t lddc, float* dA, int64_t ldda,
                              float* dB, int64_t lddb, int levels, int variant,
                              void* workspace, size_t ws_bytes, void* stream);
-/* As fmm_gemm_backward, with options (NULL = defaults).  The backward products run on
- * the packed algorithm in CTA pairs: algo must be 0 or FMM_ALGO_PACKED, cta_pair 0 or 2;
- * pipeline, round_tiles, schedule, tile_n and num_ctas apply as in fmm_gemm_ex. */
+/* As fmm_gemm_backward, with options (NULL = defaults).  The backward products run in CTA
+ * pairs (cta_pair 0 or 2) on the packed algorithm (algo 0 or FMM_ALGO_PACKED), or with the
+ * operand sums formed on chip (FMM_ALGO_FUSED: FP32 A and B, split3 or plain_bf16; the
+ * tensor-memory kernel reads B^T and A^T as transposed tiles; no workspace); pipeline,
+ * round_tiles, schedule, tile_n and num_ctas apply as in fmm_gemm_ex. */
 fmm_status fmm_gemm_backward_ex(int64_t m, int64_t n, int64_t k,
                                 const void* A, int64_t lda, const void* B, int64_t ldb,
                                 const float* dC, int64_t lddc, float* dA, int64_t ldda,

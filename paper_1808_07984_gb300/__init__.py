@@ -277,11 +277,14 @@ def workspace_size_backward(m, n, k, levels=1, variant="split3") -> int:
 
 
 def gemm_backward(A, B, dC, levels: int = 1, variant="split3", need_dA=True, need_dB=True,
-                  workspace=None, stream=None, pipeline=None, basis="strassen", deterministic=False):
+                  workspace=None, stream=None, pipeline=None, basis="strassen", deterministic=False,
+                  algo="auto"):
     """(dA, dB) = (dC @ B.T, A.T @ dC) as Strassen products through fmm_gemm_backward_ex.
 
     A (m x k) and B (k x n) have the variant's element type, dC (m x n) is float32; the
-    gradients are float32 (None where not requested).  ``pipeline`` as in gemm()."""
+    gradients are float32 (None where not requested).  ``pipeline`` as in gemm();
+    ``algo="fused"``: the operand sums are formed on chip from the transposed tiles (FP32
+    inputs, no workspace)."""
     import torch
     v = _variant(variant)
     m, k = A.shape
@@ -296,7 +299,7 @@ def gemm_backward(A, B, dC, levels: int = 1, variant="split3", need_dA=True, nee
         raise FmmError(1, "dC must be a float32 CUDA tensor with contiguous rows")
     dA = torch.empty((m, k), dtype=torch.float32, device=A.device) if need_dA else None
     dB = torch.empty((k, n), dtype=torch.float32, device=A.device) if need_dB else None
-    o = _opts(pipeline=pipeline, basis=basis, deterministic=deterministic)
+    o = _opts(algo=algo, pipeline=pipeline, basis=basis, deterministic=deterministic)
     ws_need = load().fmm_workspace_size_backward_ex(m, n, k, levels, v, ctypes.byref(o))
     if ws_need == ctypes.c_size_t(-1).value:
         raise FmmError(3, "unsupported combination")

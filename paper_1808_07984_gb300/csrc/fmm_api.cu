@@ -277,8 +277,8 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
   const bool on_chip = pl.algo == FMM_ALGO_FUSED || pl.algo == FMM_ALGO_HYBRID;
   // the fused kernels read FP32 source tiles: the caller's FP32 operands (fused), or the FP32
   // top-level sums the hybrid scheme forms from FP32 or BF16 operands
-  if (on_chip && (a_mn || !b_mn))
-    return fail(FMM_ERR_UNSUPPORTED, "the fused and hybrid algorithms are built for the forward product");
+  if (pl.algo == FMM_ALGO_HYBRID && (a_mn || !b_mn))
+    return fail(FMM_ERR_UNSUPPORTED, "the hybrid algorithm is built for the forward product");
   if (on_chip && pl.in_type != kInF32 && !(pl.algo == FMM_ALGO_HYBRID && pl.in_type == kInBF16))
     return fail(FMM_ERR_UNSUPPORTED,
                 "the fused algorithm takes FP32 A and B (split3 or plain_bf16); the hybrid also BF16");
@@ -330,6 +330,11 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
   if (fk == 2 && on_chip && !pl.pair)
     return fail(FMM_ERR_UNSUPPORTED, "the tensor-memory fused kernel runs in CTA pairs");
   pl.fused_ts = on_chip && pl.pair && fk != 1;
+  // the backward products (A' stored by rows of k, or B' by rows of n) run on chip in the
+  // tensor-memory kernel
+  if (on_chip && (a_mn || !b_mn) && (!pl.fused_ts || (a_mn && !b_mn)))
+    return fail(FMM_ERR_UNSUPPORTED,
+                "the fused algorithm runs the backward products in the tensor-memory kernel (CTA pairs)");
   if (!on_chip && !pl.pair && (a_mn || !b_mn))
     return fail(FMM_ERR_UNSUPPORTED, "single-CTA tiles are built for the forward product only");
   const int pipe = opt ? opt->pipeline : 0;
@@ -542,13 +547,16 @@ fmm_status gemm_fused(const Plan& pl, int64_t m, int64_t n, int64_t k, float alp
     const int64_t ar = b < na_blk ? block_extent(m, pl.hm, bi) : 0;
     const int64_t ac = b < na_blk ? block_extent(k, pl.hk, bj) : 0;
     if (ar > 0 && ac > 0) {
-      const cuuint64_t dims[2] = {static_cast<cuuint64_t>(ac), static_cast<cuuint64_t>(ar)};
+      // A' stored m x k (box 32 k x 128 rows, 128-byte swizzle), or by rows of k (a_mn: the
+      // block (bi, bj) of A' is the source's block (bj, bi); box 128 m x 32 k)
+      const cuuint64_t dims[2] = {static_cast<cuuint64_t>(pl.a_mn ? ar : ac), static_cast<cuuint64_t>(pl.a_mn ? ac : ar)};
       const cuuint64_t strides[1] = {static_cast<cuuint64_t>(lda * 4)};
-      const cuuint32_t box[2] = {32, 128};
+      const cuuint32_t box[2] = {pl.a_mn ? 128u : 32u, pl.a_mn ? 32u : 128u};
       const cuuint32_t estr[2] = {1, 1};
-      CUresult cr = g_encode(&fp->tmSA[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
-                             const_cast<float*>(Af + (bi * pl.hm * lda + bj * pl.hk)), dims, strides,
-                             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+      const float* base = pl.a_mn ? Af + (bj * pl.hk * lda + bi * pl.hm) : Af + (bi * pl.hm * lda + bj * pl.hk);
+      CUresult cr = g_encode(&fp->tmSA[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims,
+                             strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             pl.a_mn ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       if (cr != CUDA_SUCCESS) st = fail(FMM_ERR_CUDA, "cuTensorMapEncodeTiled (A block) failed");
       a_live[b] = true;
@@ -558,13 +566,18 @@ fmm_status gemm_fused(const Plan& pl, int64_t m, int64_t n, int64_t k, float alp
     const int64_t br = b < nb_blk ? block_extent(k, pl.hk, bl) : 0;
     const int64_t bc = b < nb_blk ? block_extent(n, pl.hn, bn) : 0;
     if (st == FMM_OK && br > 0 && bc > 0) {
-      const cuuint64_t dims[2] = {static_cast<cuuint64_t>(bc), static_cast<cuuint64_t>(br)};
+      // B' stored k x n (box 128 n x 32 k), or by rows of n (!b_mn: the block (bl, bn) of B' is
+      // the source's block (bn, bl); box 32 k x 128 n-rows, 128-byte swizzle)
+      const bool kmaj = !pl.b_mn;
+      const cuuint64_t dims[2] = {static_cast<cuuint64_t>(kmaj ? br : bc), static_cast<cuuint64_t>(kmaj ? bc : br)};
       const cuuint64_t strides[1] = {static_cast<cuuint64_t>(ldb * 4)};
-      const cuuint32_t box[2] = {static_cast<cuuint32_t>(kFusedTileN), 32};
+      const cuuint32_t box[2] = {kmaj ? 32u : static_cast<cuuint32_t>(kFusedTileN),
+                                 kmaj ? static_cast<cuuint32_t>(kFusedTileN) : 32u};
       const cuuint32_t estr[2] = {1, 1};
-      CUresult cr = g_encode(&fp->tmSB[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
-                             const_cast<float*>(Bf + (bl * pl.hk * ldb + bn * pl.hn)), dims, strides,
-                             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+      const float* base = kmaj ? Bf + (bn * pl.hn * ldb + bl * pl.hk) : Bf + (bl * pl.hk * ldb + bn * pl.hn);
+      CUresult cr = g_encode(&fp->tmSB[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims,
+                             strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             kmaj ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       if (cr != CUDA_SUCCESS) st = fail(FMM_ERR_CUDA, "cuTensorMapEncodeTiled (B block) failed");
       b_live[b] = true;
@@ -604,7 +617,7 @@ fmm_status gemm_fused(const Plan& pl, int64_t m, int64_t n, int64_t k, float alp
   cudaError_t e;
   {
     PhaseScope ps(kPhaseTensor, s);
-    e = pl.fused_ts ? launch_fused_ts(*fp, pl.terms, grid, s)
+    e = pl.fused_ts ? launch_fused_ts(*fp, pl.terms, pl.a_mn, pl.b_mn, grid, s)
                     : launch_fused(*fp, pl.terms, kFusedTransformWarps, pl.pair, grid, s);
   }
   delete fp;
@@ -714,7 +727,7 @@ fmm_status gemm_hybrid(const Plan& pl, int64_t m, int64_t n, int64_t k, float al
   }
   {
     PhaseScope ps(kPhaseTensor, s);
-    e = pl.fused_ts ? launch_fused_ts(*fp, pl.terms, grid, s)
+    e = pl.fused_ts ? launch_fused_ts(*fp, pl.terms, pl.a_mn, pl.b_mn, grid, s)
                     : launch_fused(*fp, pl.terms, kFusedTransformWarps, pl.pair, grid, s);
   }
   delete fp;

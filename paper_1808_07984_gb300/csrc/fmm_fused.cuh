@@ -62,9 +62,11 @@ __device__ __forceinline__ void split2(float x0, float x1, uint32_t& hi, uint32_
 // to ring h (slots h * NS / 2 .. (h + 1) * NS / 2 - 1), so that every slot -- and its pair of
 // barriers -- is only ever consumed by the threads that form that half (a slot shared by two
 // consumer groups could be awaited by one group while the other's use of it is still a phase
-// behind, which the parity of an mbarrier wait cannot tell apart).  Returns false if a wait
-// gave up or a parameter block named a tensor map outside its table (error bit set).
-template <int NS, bool PAIR, int RINGS = 1>
+// behind, which the parity of an mbarrier wait cannot tell apart).  A_MN: the A-operand
+// blocks are stored by rows of k (their maps are {m, k}, box 128 x 32); B_KM: the B-operand
+// blocks are stored by rows of n (maps {k, n}, box 32 x 128, 128-byte swizzle).  Returns false
+// if a wait gave up or a parameter block named a tensor map outside its table (error bit set).
+template <int NS, bool PAIR, int RINGS = 1, bool A_MN = false, bool B_KM = false>
 __device__ __forceinline__ bool fused_producer(const FusedParams& fp, uint8_t* slots, uint64_t* slot_full,
                                                uint64_t* slot_empty, int rank, int first, int stride,
                                                volatile int* abort_flag) {
@@ -111,10 +113,13 @@ __device__ __forceinline__ bool fused_producer(const FusedParams& fp, uint8_t* s
     for (int kb = 0; ok && kb < p.nk; ++kb) {
       for (int h = 0; ok && h < 2; ++h) {
         const int ring = RINGS == 2 ? h : 0;
+        const int kx = kb * kBK + 32 * h;
         for (int w = 0; ok && w < na; ++w)
-          ok = issue(ring, &fp.tmSA[(ablk >> (8 * w)) & 0xff], kb * kBK + 32 * h, a_row, item, kb);
+          ok = A_MN ? issue(ring, &fp.tmSA[(ablk >> (8 * w)) & 0xff], a_row, kx, item, kb)
+                    : issue(ring, &fp.tmSA[(ablk >> (8 * w)) & 0xff], kx, a_row, item, kb);
         for (int w = 0; ok && w < nb; ++w)
-          ok = issue(ring, &fp.tmSB[(bblk >> (8 * w)) & 0xff], b_col, kb * kBK + 32 * h, item, kb);
+          ok = B_KM ? issue(ring, &fp.tmSB[(bblk >> (8 * w)) & 0xff], kx, b_col, item, kb)
+                    : issue(ring, &fp.tmSB[(bblk >> (8 * w)) & 0xff], b_col, kx, item, kb);
       }
     }
   }

@@ -21,6 +21,13 @@
 //   warp 1      (even CTA) issues the cta_group::2 UMMAs: A from TMEM (each CTA's 128 rows),
 //               B from shared memory (each CTA's 128 columns);
 //   warps 4-7   multi-destination write-back (epilogue_role) of the accumulator.
+// Transposed sources (the backward products dA = dC B^T and dB = A^T dC, Section 3 on the
+// transposed operands): A_MN -- the A operand is stored K-major by rows of k (its source tile
+// is 32 k-rows x 128 m, 512-byte rows, loaded like a B tile); each thread gathers its row's 32
+// k-values from one column of the tile (conflict-free: a warp reads 32 consecutive words).
+// B_KM -- the B operand is stored with n rows of k (its source tile is 128 n-rows x 32 k,
+// 128-byte swizzle, loaded like an A tile); thread tb owns n-row tb, adds its row like an A row
+// and writes the B-operand tile K-major (128-byte swizzle) for a K-major UMMA descriptor.
 // TMEM (512 columns): the 256-column accumulator, then kStages A stages of 32 columns per term.
 // The accumulator is single-buffered (the A stages take the other half of TMEM): the UMMAs of
 // an item start once both epilogues have read the previous item's accumulator out.
@@ -51,13 +58,13 @@ struct FusedTsCfg {
 };
 
 // UMMA issue of the TS kernel (one thread of the even CTA).  Returns false if a wait gave up.
-template <int TERMS>
+template <int TERMS, bool B_KM>
 __device__ __forceinline__ bool mma_role_ts(const CommonParams& p, uint8_t* smem, uint64_t* op_full,
                                             uint64_t* op_empty, uint64_t* acc_full, uint64_t* acc_empty,
                                             uint32_t tmem_base, volatile int* abort_flag) {
   using Cfg = FusedTsCfg<TERMS>;
   constexpr int S = Cfg::kStages;
-  constexpr uint32_t idesc = make_idesc_f16(2 * kBM, Cfg::kTileN, true, false, true);
+  constexpr uint32_t idesc = make_idesc_f16(2 * kBM, Cfg::kTileN, true, false, !B_KM);
   constexpr uint32_t kMnAtom = kBK * 128;  // bytes between 64-wide n atoms of a B tile
   const int first = static_cast<int>(blockIdx.x >> 1), stride = static_cast<int>(gridDim.x >> 1);
   int o = 0;
@@ -79,15 +86,19 @@ __device__ __forceinline__ bool mma_role_ts(const CommonParams& p, uint8_t* smem
       }
       tc_fence_after();
       uint8_t* st = smem + o * Cfg::kStageBytes;
-      const uint64_t db_hi = make_sdesc_mnmajor_sw128(smem_u32(st), kMnAtom, 1024);
-      const uint64_t db_lo = make_sdesc_mnmajor_sw128(smem_u32(st + Cfg::kBTermBytes), kMnAtom, 1024);
+      // B tile: MN-major (two 64-wide n atoms of 64 k-rows) or K-major (128 n-rows of 64 k)
+      const uint64_t db_hi = B_KM ? make_sdesc_kmajor_sw128(smem_u32(st))
+                                  : make_sdesc_mnmajor_sw128(smem_u32(st), kMnAtom, 1024);
+      const uint64_t db_lo = B_KM ? make_sdesc_kmajor_sw128(smem_u32(st + Cfg::kBTermBytes))
+                                  : make_sdesc_mnmajor_sw128(smem_u32(st + Cfg::kBTermBytes), kMnAtom, 1024);
       const uint32_t a_hi = tmem_base + Cfg::kACol0 + static_cast<uint32_t>(o) * Cfg::kAStageCols;
       const uint32_t a_lo = a_hi + Cfg::kTermCols;
 #pragma unroll
       for (int kk = 0; kk < kBK / 16; ++kk) {
-        // k16 slice: 8 TMEM columns of A; 16 k-rows (two 1024-byte atoms) of B, >> 4 encoded
+        // k16 slice: 8 TMEM columns of A; of B 16 k-rows (two 1024-byte atoms, MN-major) or 32
+        // bytes inside the 128-byte rows (K-major), >> 4 encoded
         const uint32_t ka = static_cast<uint32_t>(8 * kk);
-        const uint64_t kb16 = static_cast<uint64_t>(kk * 128);
+        const uint64_t kb16 = static_cast<uint64_t>(B_KM ? kk * 2 : kk * 128);
         umma_f16_ts_pair(tmem_base, a_hi + ka, db_hi + kb16, idesc, (kb | kk) != 0 ? 1u : 0u);
         if (TERMS == 3) {
           umma_f16_ts_pair(tmem_base, a_hi + ka, db_lo + kb16, idesc, 1u);
@@ -111,7 +122,7 @@ __device__ __forceinline__ bool mma_role_ts(const CommonParams& p, uint8_t* smem
   return true;
 }
 
-template <int TERMS>
+template <int TERMS, bool A_MN = false, bool B_KM = false>
 __global__ void __launch_bounds__(fused_threads<8>(), 1) fmm_fused_ts_kernel(const __grid_constant__ FusedParams fp) {
   using Cfg = FusedTsCfg<TERMS>;
   constexpr int S = Cfg::kStages;
@@ -174,14 +185,15 @@ __global__ void __launch_bounds__(fused_threads<8>(), 1) fmm_fused_ts_kernel(con
     // nothing issued: fall through to the teardown
   } else if (warp == 0) {
     if (lane == 0 &&
-        !fused_producer<NS, true, 2>(fp, slots, slot_full, slot_empty, rank, first, stride, abort_flag)) {
+        !fused_producer<NS, true, 2, A_MN, B_KM>(fp, slots, slot_full, slot_empty, rank, first, stride,
+                                                abort_flag)) {
       atomicOr(p.err, kErrProducerWait);
       *abort_flag = 1;
       drain_pause(2000000ull);
     }
   } else if (warp == 1) {
     if (lane == 0 && rank == 0) {
-      if (!mma_role_ts<TERMS>(p, smem, op_full, op_empty, acc_full, acc_empty, tmem_base, abort_flag)) {
+      if (!mma_role_ts<TERMS, B_KM>(p, smem, op_full, op_empty, acc_full, acc_empty, tmem_base, abort_flag)) {
         atomicOr(p.err, kErrMmaWait);
         *abort_flag = 1;
         drain_pause(2000000ull);
@@ -236,23 +248,42 @@ __global__ void __launch_bounds__(fused_threads<8>(), 1) fmm_fused_ts_kernel(con
           const uint8_t* sl = slots + sidx * kSlotBytes;
           if (w < na) {
             const float sg = ((a_neg >> w) & 1u) ? -1.f : 1.f;
+            if (A_MN) {
+              // 32 k-rows x 128 m: this row's k-values are one column of the tile
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-              const float4 x = *reinterpret_cast<const float4*>(sl + arow * 128 + ((c ^ (arow & 7)) << 4));
-              aA[4 * c] = fmaf(sg, x.x, aA[4 * c]);
-              aA[4 * c + 1] = fmaf(sg, x.y, aA[4 * c + 1]);
-              aA[4 * c + 2] = fmaf(sg, x.z, aA[4 * c + 2]);
-              aA[4 * c + 3] = fmaf(sg, x.w, aA[4 * c + 3]);
+              for (int kk = 0; kk < 32; ++kk)
+                aA[kk] = fmaf(sg, *reinterpret_cast<const float*>(sl + kk * 512 + arow * 4), aA[kk]);
+            } else {
+#pragma unroll
+              for (int c = 0; c < 8; ++c) {
+                const float4 x = *reinterpret_cast<const float4*>(sl + arow * 128 + ((c ^ (arow & 7)) << 4));
+                aA[4 * c] = fmaf(sg, x.x, aA[4 * c]);
+                aA[4 * c + 1] = fmaf(sg, x.y, aA[4 * c + 1]);
+                aA[4 * c + 2] = fmaf(sg, x.z, aA[4 * c + 2]);
+                aA[4 * c + 3] = fmaf(sg, x.w, aA[4 * c + 3]);
+              }
             }
           } else {
             const float sg = ((b_neg >> (w - na)) & 1u) ? -1.f : 1.f;
+            if (B_KM) {
+              // 128 n-rows x 32 k, 128-byte swizzle: n-row tb, 32 k-values (aB as 8 x 4 in k order)
 #pragma unroll
-            for (int v = 0; v < 8; ++v) {
-              const float4 x = *reinterpret_cast<const float4*>(sl + (bk0 + 4 * v) * 512 + nq * 16);
-              aB[v][0] = fmaf(sg, x.x, aB[v][0]);
-              aB[v][1] = fmaf(sg, x.y, aB[v][1]);
-              aB[v][2] = fmaf(sg, x.z, aB[v][2]);
-              aB[v][3] = fmaf(sg, x.w, aB[v][3]);
+              for (int c = 0; c < 8; ++c) {
+                const float4 x = *reinterpret_cast<const float4*>(sl + tb * 128 + ((c ^ (tb & 7)) << 4));
+                aB[c][0] = fmaf(sg, x.x, aB[c][0]);
+                aB[c][1] = fmaf(sg, x.y, aB[c][1]);
+                aB[c][2] = fmaf(sg, x.z, aB[c][2]);
+                aB[c][3] = fmaf(sg, x.w, aB[c][3]);
+              }
+            } else {
+#pragma unroll
+              for (int v = 0; v < 8; ++v) {
+                const float4 x = *reinterpret_cast<const float4*>(sl + (bk0 + 4 * v) * 512 + nq * 16);
+                aB[v][0] = fmaf(sg, x.x, aB[v][0]);
+                aB[v][1] = fmaf(sg, x.y, aB[v][1]);
+                aB[v][2] = fmaf(sg, x.z, aB[v][2]);
+                aB[v][3] = fmaf(sg, x.w, aB[v][3]);
+              }
             }
           }
           __syncwarp();
@@ -284,10 +315,34 @@ __global__ void __launch_bounds__(fused_threads<8>(), 1) fmm_fused_ts_kernel(con
           tmem_st_32x32b_x16(ta, hi);
           if (TERMS == 3) tmem_st_32x32b_x16(ta + Cfg::kTermCols, lo);
         }
-        // B sums: k-rows 32 g + bk0 + 4 v, columns 4 nq .. + 3, MN-major swizzled
         uint8_t* st = smem + o * Cfg::kStageBytes;
+        if (B_KM) {
+          // B sums of n-row tb, k = 32 g .. 32 g + 31: 16-byte chunks 4 g .. 4 g + 3 of the
+          // row's 128 bytes, K-major 128-byte swizzle
 #pragma unroll
-        for (int v = 0; v < 8; ++v) {
+          for (int j = 0; j < 4; ++j) {
+            const uint32_t off = tb * 128 + (((4 * g + j) ^ (tb & 7)) << 4);
+            if (TERMS == 3) {
+              uint4 hv, lv;
+              split2(aB[2 * j][0], aB[2 * j][1], hv.x, lv.x);
+              split2(aB[2 * j][2], aB[2 * j][3], hv.y, lv.y);
+              split2(aB[2 * j + 1][0], aB[2 * j + 1][1], hv.z, lv.z);
+              split2(aB[2 * j + 1][2], aB[2 * j + 1][3], hv.w, lv.w);
+              *reinterpret_cast<uint4*>(st + off) = hv;
+              *reinterpret_cast<uint4*>(st + Cfg::kBTermBytes + off) = lv;
+            } else {
+              uint4 hv;
+              hv.x = pack_bf16x2(aB[2 * j][0], aB[2 * j][1]);
+              hv.y = pack_bf16x2(aB[2 * j][2], aB[2 * j][3]);
+              hv.z = pack_bf16x2(aB[2 * j + 1][0], aB[2 * j + 1][1]);
+              hv.w = pack_bf16x2(aB[2 * j + 1][2], aB[2 * j + 1][3]);
+              *reinterpret_cast<uint4*>(st + off) = hv;
+            }
+          }
+        }
+        // B sums: k-rows 32 g + bk0 + 4 v, columns 4 nq .. + 3, MN-major swizzled
+#pragma unroll
+        for (int v = 0; !B_KM && v < 8; ++v) {
           const int kk = 32 * g + bk0 + 4 * v;
           const int c = (nq & 15) >> 1;  // 8-wide chunk inside the 64-wide n atom
           const uint32_t off = (nq >> 4) * 8192 + (kk >> 3) * 1024 + (kk & 7) * 128 +

@@ -46,7 +46,8 @@ constexpr int kFusedTransformWarps = 8;
 cudaError_t launch_fused(const FusedParams& p, int terms, int transform_warps, bool pair, int grid,
                          cudaStream_t s);
 // The same products in CTA pairs with the A-operand sums held in tensor memory
-// (fmm_fused_ts.cuh); terms in {1, 3}.
-cudaError_t launch_fused_ts(const FusedParams& p, int terms, int grid, cudaStream_t s);
+// (fmm_fused_ts.cuh); terms in {1, 3}.  a_mn: A' stored by rows of k; b_mn: B' stored by
+// rows of k (false: by rows of n).  Built: (a_mn, b_mn) = (0, 1), (0, 0), (1, 1).
+cudaError_t launch_fused_ts(const FusedParams& p, int terms, bool a_mn, bool b_mn, int grid, cudaStream_t s);
 
 }  // namespace fmm

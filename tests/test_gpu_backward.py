@@ -96,6 +96,65 @@ def test_backward_float(m, n, k, levels, variant):
     assert _err(dB.cpu().numpy(), oracle.classical(At, dC), nA, nC) <= _tol(variant, levels, m)
 
 
+@pytest.mark.parametrize("variant", ["split3", "plain_bf16"])
+@pytest.mark.parametrize("levels", [1, 2])
+@pytest.mark.parametrize("m,n,k", [(16, 16, 16), (300, 200, 136), (129, 65, 257), (520, 8, 400), (1000, 1200, 300)])
+def test_backward_fused_int_bit_exact(m, n, k, levels, variant):
+    """dA = dC B^T and dB = A^T dC with the operand sums formed on chip: the tensor-memory
+    kernel reads B^T as tiles stored by rows of n and A^T as tiles stored by rows of k."""
+    pad = lambda c: (-c) % 4
+    A, B = synth.problem(m, n, k, 17 + m, "int")
+    dC = synth.small_int((m, n), 18 + n)
+
+    def dev(X):
+        r, c = X.shape
+        t = torch.zeros((r, c + pad(c)), dtype=torch.float32, device="cuda")
+        t[:, :c] = torch.from_numpy(X).cuda()
+        return t[:, :c]
+    dA, dB = fmm.gemm_backward(dev(A), dev(B), dev(dC), levels=levels, variant=variant, algo="fused")
+    fmm.device_status()
+    np.testing.assert_array_equal(dA.cpu().numpy(), oracle.classical(dC, np.ascontiguousarray(B.T)))
+    np.testing.assert_array_equal(dB.cpu().numpy(), oracle.classical(np.ascontiguousarray(A.T), dC))
+
+
+@pytest.mark.parametrize("levels", [1, 2])
+def test_backward_fused_float(levels):
+    m, n, k = 700, 520, 900
+    A, B = synth.problem(m, n, k, 19, "gaussian")
+    dC = synth.gaussian((m, n), 20)
+    dA, dB = fmm.gemm_backward(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(),
+                               torch.from_numpy(dC).cuda(), levels=levels, algo="fused")
+    fmm.device_status()
+    nA, nB, nC = (np.linalg.norm(X.astype(np.float64)) for X in (A, B, dC))
+    assert _err(dA.cpu().numpy(), oracle.classical(dC, np.ascontiguousarray(B.T)), nC, nB) <= _tol("split3", levels, n)
+    assert _err(dB.cpu().numpy(), oracle.classical(np.ascontiguousarray(A.T), dC), nA, nC) <= _tol("split3", levels, m)
+
+
+def test_backward_fused_full_size_sampled_rows():
+    """The C3 layer shape in FP32 (8192 x 4096 x 4096), gradients on chip, sampled rows."""
+    m, k, n = 8192, 4096, 4096
+    A, B = synth.problem(m, n, k, 21, "gaussian")
+    dC = synth.gaussian((m, n), 22)
+    dA, dB = fmm.gemm_backward(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(),
+                               torch.from_numpy(dC).cuda(), levels=1, algo="fused")
+    fmm.device_status()
+    rng = synth.rng(23)
+    ra = np.unique(rng.integers(0, m, size=6))
+    rb = np.unique(rng.integers(0, k, size=6))
+    dA64 = oracle.classical(dC, np.ascontiguousarray(B.T), rows=ra)
+    dB64 = oracle.classical(np.ascontiguousarray(A.T), dC, rows=rb)
+    nB, nC = np.linalg.norm(B.astype(np.float64)), np.linalg.norm(dC.astype(np.float64))
+    assert _err(dA.cpu().numpy()[ra], dA64, np.linalg.norm(dC[ra].astype(np.float64)), nB) <= _tol("split3", 1, n)
+    assert _err(dB.cpu().numpy()[rb], dB64, np.linalg.norm(A[:, rb].astype(np.float64)), nC) <= _tol("split3", 1, m)
+
+
+def test_backward_fused_rejected_for_16bit_operands():
+    A = torch.zeros((64, 64), dtype=torch.bfloat16, device="cuda")
+    with pytest.raises(fmm.FmmError) as ei:
+        fmm.gemm_backward(A, A, torch.zeros((64, 64), device="cuda"), levels=1, variant="bf16", algo="fused")
+    assert ei.value.status == 3
+
+
 def test_backward_bf16_inputs_fp32_grads():
     """BF16 A and B, FP32 dC: each operand sum is rounded once to BF16."""
     m, n, k = 384, 256, 320
