@@ -279,9 +279,9 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
   // top-level sums the hybrid scheme forms from FP32 or BF16 operands
   if (pl.algo == FMM_ALGO_HYBRID && (a_mn || !b_mn))
     return fail(FMM_ERR_UNSUPPORTED, "the hybrid algorithm is built for the forward product");
-  if (on_chip && pl.in_type != kInF32 && !(pl.algo == FMM_ALGO_HYBRID && pl.in_type == kInBF16))
+  if (on_chip && pl.in_type != kInF32 && pl.algo != FMM_ALGO_HYBRID)
     return fail(FMM_ERR_UNSUPPORTED,
-                "the fused algorithm takes FP32 A and B (split3 or plain_bf16); the hybrid also BF16");
+                "the fused algorithm takes FP32 A and B (split3 or plain_bf16); the hybrid also BF16 and FP16");
   pl.tile_n = (opt && opt->tile_n) ? opt->tile_n : 0;
   const int sched = opt ? opt->schedule : 0;
   if (sched < 0 || sched > 2) return fail(FMM_ERR_ARG, "schedule must be 0, 1 or 2");
@@ -329,6 +329,8 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
   if (fk < 0 || fk > 2) return fail(FMM_ERR_ARG, "fused_kernel must be 0, 1 or 2");
   if (fk == 2 && on_chip && !pl.pair)
     return fail(FMM_ERR_UNSUPPORTED, "the tensor-memory fused kernel runs in CTA pairs");
+  if (on_chip && pl.scaled && (!pl.pair || fk == 1))
+    return fail(FMM_ERR_UNSUPPORTED, "scaled FP16 products with on-chip sums run in the tensor-memory kernel");
   pl.fused_ts = on_chip && pl.pair && fk != 1;
   // the backward products (A' stored by rows of k, or B' by rows of n) run on chip in the
   // tensor-memory kernel
@@ -383,7 +385,7 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
     // seven top-level sums of each operand in FP32, blocks of 2h x 2h
     pl.a_bytes = static_cast<size_t>(round_up(7 * (2 * pl.hm) * (2 * pl.hk) * 4, 256));
     pl.b_bytes = static_cast<size_t>(round_up(7 * (2 * pl.hk) * (2 * pl.hn) * 4, 256));
-    pl.ws = pl.a_bytes + pl.b_bytes;
+    pl.ws = pl.a_bytes + pl.b_bytes + (pl.scaled ? pl.scale_bytes : 0);
   }
   if (pl.outer_scaling && pl.ws > 0) {
     // float bits of max |x| of the m rows of A and the n columns of B
@@ -617,7 +619,7 @@ fmm_status gemm_fused(const Plan& pl, int64_t m, int64_t n, int64_t k, float alp
   cudaError_t e;
   {
     PhaseScope ps(kPhaseTensor, s);
-    e = pl.fused_ts ? launch_fused_ts(*fp, pl.terms, pl.a_mn, pl.b_mn, grid, s)
+    e = pl.fused_ts ? launch_fused_ts(*fp, pl.terms, pl.a_mn, pl.b_mn, pl.scaled, grid, s)
                     : launch_fused(*fp, pl.terms, kFusedTransformWarps, pl.pair, grid, s);
   }
   delete fp;
@@ -687,6 +689,45 @@ fmm_status gemm_hybrid(const Plan& pl, int64_t m, int64_t n, int64_t k, float al
   }
   if (e != cudaSuccess) return cuda_fail(e, "top-level operand sums (B)");
 
+  // FP16: panel maxima of the 49 bottom-level operand sums, one pass over each top-level sum
+  unsigned* maxbits = pl.scaled ? reinterpret_cast<unsigned*>(static_cast<uint8_t*>(ws) + pl.a_bytes + pl.b_bytes)
+                                : nullptr;
+  if (maxbits) {
+    e = cudaMemsetAsync(maxbits, 0, pl.scale_bytes, s);
+    if (e != cudaSuccess) return cuda_fail(e, "clearing the panel maxima");
+    for (int r1 = 0; r1 < 7; ++r1) {
+      SumParams ma;
+      std::memset(&ma, 0, sizeof ma);
+      ma.X = P + r1 * h1m * h1k;
+      ma.ldx = h1k;
+      ma.rows = h1m;
+      ma.cols = h1k;
+      ma.hr = pl.hm;
+      ma.hc = pl.hk;
+      ma.terms = 1;
+      ma.chunk = -1;
+      ma.vec_ok = 1;
+      ma.maxbits = maxbits + static_cast<int64_t>(r1) * 7 * pl.panels_a;
+      ma.npanels = static_cast<int32_t>(pl.panels_a);
+      ma.panel_w = kBM;
+      ma.scale_rows = 1;
+      SumParams mb = ma;
+      mb.X = Q + r1 * h1k * h1n;
+      mb.ldx = h1n;
+      mb.rows = h1k;
+      mb.cols = h1n;
+      mb.hr = pl.hk;
+      mb.hc = pl.hn;
+      mb.maxbits = maxbits + 49 * pl.panels_a + static_cast<int64_t>(r1) * 7 * pl.panels_b;
+      mb.npanels = static_cast<int32_t>(pl.panels_b);
+      mb.panel_w = pl.tile_n;
+      mb.scale_rows = 0;
+      PhaseScope ps(kPhasePack, s, 2);
+      e = launch_operand_maxima(ma, false, dev.sms, s);
+      if (e == cudaSuccess) e = launch_operand_maxima(mb, true, dev.sms, s);
+      if (e != cudaSuccess) return cuda_fail(e, "panel maxima of the bottom-level sums");
+    }
+  }
   FusedParams* fp = new FusedParams;
   std::memset(fp, 0, sizeof(FusedParams));
   fmm_status st = FMM_OK;
@@ -725,9 +766,15 @@ fmm_status gemm_hybrid(const Plan& pl, int64_t m, int64_t n, int64_t k, float al
     delete fp;
     return st;
   }
+  if (maxbits) {
+    fp->c.maxbits_a = maxbits;
+    fp->c.maxbits_b = maxbits + 49 * pl.panels_a;
+    fp->c.panels_a = static_cast<int32_t>(pl.panels_a);
+    fp->c.panels_b = static_cast<int32_t>(pl.panels_b);
+  }
   {
     PhaseScope ps(kPhaseTensor, s);
-    e = pl.fused_ts ? launch_fused_ts(*fp, pl.terms, pl.a_mn, pl.b_mn, grid, s)
+    e = pl.fused_ts ? launch_fused_ts(*fp, pl.terms, pl.a_mn, pl.b_mn, pl.scaled, grid, s)
                     : launch_fused(*fp, pl.terms, kFusedTransformWarps, pl.pair, grid, s);
   }
   delete fp;

@@ -19,6 +19,7 @@
 // UMMA work); the transform warps of both CTAs arrive on the even CTA's operand barrier.
 #pragma once
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include "fmm_kernels.cuh"
 
 namespace fmm {
@@ -44,6 +45,11 @@ struct FusedCfg {
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo_elem, float hi_elem) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo_elem, hi_elem);  // .x = lo_elem
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ uint32_t pack_f16x2(float lo_elem, float hi_elem) {
+  const __half2 v = __floats2half2_rn(lo_elem, hi_elem);  // .x = lo_elem
   return *reinterpret_cast<const uint32_t*>(&v);
 }
 

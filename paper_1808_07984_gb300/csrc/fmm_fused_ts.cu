@@ -7,11 +7,11 @@
 
 namespace fmm {
 
-template <int TERMS, bool A_MN, bool B_KM>
+template <int TERMS, bool A_MN, bool B_KM, bool F16 = false>
 static cudaError_t launch_fused_ts_t(const FusedParams& p, int grid, cudaStream_t s) {
   using Cfg = FusedTsCfg<TERMS>;
   static_assert(Cfg::kSmemBytes <= 232448, "shared memory per CTA");
-  auto kern = fmm_fused_ts_kernel<TERMS, A_MN, B_KM>;
+  auto kern = fmm_fused_ts_kernel<TERMS, A_MN, B_KM, F16>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(Cfg::kSmemBytes));
   if (e != cudaSuccess) return e;
@@ -38,9 +38,12 @@ static cudaError_t launch_fused_ts_t(const FusedParams& p, int grid, cudaStream_
   return cudaLaunchKernelEx(&cfg, kern, p);
 }
 
-cudaError_t launch_fused_ts(const FusedParams& p, int terms, bool a_mn, bool b_mn, int grid, cudaStream_t s) {
+cudaError_t launch_fused_ts(const FusedParams& p, int terms, bool a_mn, bool b_mn, bool f16, int grid,
+                            cudaStream_t s) {
   // forward (A K-major, B MN-major), dA = dC B^T (B stored by rows of n), dB = A^T dC (A
-  // stored by rows of k)
+  // stored by rows of k); FP16 operands with panel scaling: forward only
+  if (f16) return (terms == 1 && !a_mn && b_mn) ? launch_fused_ts_t<1, false, false, true>(p, grid, s)
+                                                : cudaErrorInvalidValue;
   if (!a_mn && b_mn) {
     if (terms == 3) return launch_fused_ts_t<3, false, false>(p, grid, s);
     if (terms == 1) return launch_fused_ts_t<1, false, false>(p, grid, s);

@@ -28,6 +28,10 @@
 // B_KM -- the B operand is stored with n rows of k (its source tile is 128 n-rows x 32 k,
 // 128-byte swizzle, loaded like an A tile); thread tb owns n-row tb, adds its row like an A row
 // and writes the B-operand tile K-major (128-byte swizzle) for a K-major UMMA descriptor.
+// F16 (one term): FP16 operands with power-of-two scaling -- each product's A-operand sums of
+// this CTA's 128-row panel and B-operand sums of the tile's columns are multiplied by 2^-s
+// (the panel maxima, p.maxbits_a / maxbits_b, were found by a pass before this kernel) before
+// the FP16 rounding, and the epilogue multiplies by 2^(s_A + s_B) exactly.
 // TMEM (512 columns): the 256-column accumulator, then kStages A stages of 32 columns per term.
 // The accumulator is single-buffered (the A stages take the other half of TMEM): the UMMAs of
 // an item start once both epilogues have read the previous item's accumulator out.
@@ -58,13 +62,13 @@ struct FusedTsCfg {
 };
 
 // UMMA issue of the TS kernel (one thread of the even CTA).  Returns false if a wait gave up.
-template <int TERMS, bool B_KM>
+template <int TERMS, bool B_KM, bool F16 = false>
 __device__ __forceinline__ bool mma_role_ts(const CommonParams& p, uint8_t* smem, uint64_t* op_full,
                                             uint64_t* op_empty, uint64_t* acc_full, uint64_t* acc_empty,
                                             uint32_t tmem_base, volatile int* abort_flag) {
   using Cfg = FusedTsCfg<TERMS>;
   constexpr int S = Cfg::kStages;
-  constexpr uint32_t idesc = make_idesc_f16(2 * kBM, Cfg::kTileN, true, false, !B_KM);
+  constexpr uint32_t idesc = make_idesc_f16(2 * kBM, Cfg::kTileN, !F16, false, !B_KM);
   constexpr uint32_t kMnAtom = kBK * 128;  // bytes between 64-wide n atoms of a B tile
   const int first = static_cast<int>(blockIdx.x >> 1), stride = static_cast<int>(gridDim.x >> 1);
   int o = 0;
@@ -122,8 +126,9 @@ __device__ __forceinline__ bool mma_role_ts(const CommonParams& p, uint8_t* smem
   return true;
 }
 
-template <int TERMS, bool A_MN = false, bool B_KM = false>
+template <int TERMS, bool A_MN = false, bool B_KM = false, bool F16 = false>
 __global__ void __launch_bounds__(fused_threads<8>(), 1) fmm_fused_ts_kernel(const __grid_constant__ FusedParams fp) {
+  static_assert(!F16 || TERMS == 1, "FP16 operands: one term");
   using Cfg = FusedTsCfg<TERMS>;
   constexpr int S = Cfg::kStages;
   constexpr int NS = Cfg::kSlots;
@@ -193,7 +198,7 @@ __global__ void __launch_bounds__(fused_threads<8>(), 1) fmm_fused_ts_kernel(con
     }
   } else if (warp == 1) {
     if (lane == 0 && rank == 0) {
-      if (!mma_role_ts<TERMS, B_KM>(p, smem, op_full, op_empty, acc_full, acc_empty, tmem_base, abort_flag)) {
+      if (!mma_role_ts<TERMS, B_KM, F16>(p, smem, op_full, op_empty, acc_full, acc_empty, tmem_base, abort_flag)) {
         atomicOr(p.err, kErrMmaWait);
         *abort_flag = 1;
         drain_pause(2000000ull);
@@ -228,6 +233,13 @@ __global__ void __launch_bounds__(fused_threads<8>(), 1) fmm_fused_ts_kernel(con
       const uint32_t hdr = reinterpret_cast<const uint32_t*>(&fp.src[r])[kSrcWordHeader];
       const int na = hdr & 0xff, nb = (hdr >> 8) & 0xff;
       const uint32_t a_neg = (hdr >> 16) & 0xff, b_neg = hdr >> 24;
+      // FP16: the shifts of this item's A panel (this CTA's 128 rows) and B panel (tile column)
+      int sh_a = 0, sh_b = 0;
+      if (F16) {
+        const int tm_cta = 2 * tm + rank;
+        if (tm_cta < p.panels_a) sh_a = panel_shift(p.maxbits_a[r * p.panels_a + tm_cta]);
+        sh_b = panel_shift(p.maxbits_b[r * p.panels_b + tn]);
+      }
       for (int kb = 0; ok && kb < p.nk; ++kb) {
         float aA[32];
         float aB[8][4];
@@ -307,6 +319,8 @@ __global__ void __launch_bounds__(fused_threads<8>(), 1) fmm_fused_ts_kernel(con
           for (int i = 0; i < 16; ++i) {
             if (TERMS == 3)
               split2(aA[2 * i], aA[2 * i + 1], hi[i], lo[i]);
+            else if (F16)
+              hi[i] = pack_f16x2(ldexpf(aA[2 * i], -sh_a), ldexpf(aA[2 * i + 1], -sh_a));
             else
               hi[i] = pack_bf16x2(aA[2 * i], aA[2 * i + 1]);
           }
@@ -353,6 +367,11 @@ __global__ void __launch_bounds__(fused_threads<8>(), 1) fmm_fused_ts_kernel(con
             split2(aB[v][2], aB[v][3], hv.y, lv.y);
             *reinterpret_cast<uint2*>(st + off) = hv;
             *reinterpret_cast<uint2*>(st + Cfg::kBTermBytes + off) = lv;
+          } else if (F16) {
+            uint2 hv;
+            hv.x = pack_f16x2(ldexpf(aB[v][0], -sh_b), ldexpf(aB[v][1], -sh_b));
+            hv.y = pack_f16x2(ldexpf(aB[v][2], -sh_b), ldexpf(aB[v][3], -sh_b));
+            *reinterpret_cast<uint2*>(st + off) = hv;
           } else {
             uint2 hv;
             hv.x = pack_bf16x2(aB[v][0], aB[v][1]);

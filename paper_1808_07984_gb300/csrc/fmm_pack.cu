@@ -443,9 +443,11 @@ static cudaError_t launch_sums_b(const SumParams& p, int levels, int in_type, in
   }
   if (in_type == kInBF16 && p.terms == 1 && !out16)
     return launch_sums_l<__nv_bfloat16, 0, IS_B, TQ, 1>(p, levels, num_sms, s);
-  // FP32 sums of BF16 operands (top level of the hybrid scheme)
+  // FP32 sums of 16-bit operands (top level of the hybrid scheme)
   if (in_type == kInBF16 && p.terms == 0)
     return levels == 1 ? launch_sums_t<__nv_bfloat16, 0, 1, IS_B, TQ, 0>(p, num_sms, s) : cudaErrorInvalidValue;
+  if (in_type == kInF16 && p.terms == 0)
+    return levels == 1 ? launch_sums_t<__half, 0, 1, IS_B, TQ, 0>(p, num_sms, s) : cudaErrorInvalidValue;
   if (in_type == kInF16 && p.terms == 1 && out16) {
     if (!p.maxbits) return launch_sums_l<__half, 1, IS_B, TQ, 1>(p, levels, num_sms, s);
     // two passes: panel maxima, then the sums scaled by 2^-s (maxbits zeroed by the caller)
@@ -504,6 +506,12 @@ cudaError_t launch_operand_sums(const SumParams& p, int levels, bool is_b, bool 
   }
   return transq ? launch_sums_b<false, true>(p, levels, in_type, out16, num_sms, s)
                 : launch_sums_b<false, false>(p, levels, in_type, out16, num_sms, s);
+}
+
+cudaError_t launch_operand_maxima(const SumParams& p, bool is_b, int num_sms, cudaStream_t s) {
+  // one level of sums of an FP32 matrix, only their panel maxima (maxbits zeroed by the caller)
+  return is_b ? launch_sums_t<float, 1, 1, true, false, 1, 1>(p, num_sms, s)
+              : launch_sums_t<float, 1, 1, false, false, 1, 1>(p, num_sms, s);
 }
 
 cudaError_t launch_beta(float* C, int64_t m, int64_t n, int64_t ldc, float beta, int num_sms,

@@ -712,6 +712,40 @@ def test_hybrid_bf16_operands_float():
     assert oracle.normwise_error(C, C64, An, Bn) <= tolerance("bf16", 2, 768)
 
 
+@pytest.mark.parametrize("m,n,k", [(16, 16, 16), (300, 520, 200), (129, 257, 65), (1000, 1200, 300)])
+def test_hybrid_f16_scaled_int_bit_exact(m, n, k):
+    """FP16 operands on the hybrid scheme: FP32 top-level sums, then per (product, panel) the
+    power of two that puts the panel's largest bottom-level sum in [2^14, 2^15) (a maxima pass
+    before the kernel), applied on chip before the FP16 rounding and undone in the epilogue."""
+    C, C64, _, _ = run(m, n, k, 2, "f16", dist="int", seed=13 * m + n + k, algo="hybrid")
+    np.testing.assert_array_equal(C, C64)
+
+
+def test_hybrid_f16_scaled_float_and_badly_scaled():
+    C, C64, An, Bn = run(640, 384, 768, 2, "f16", dist="gaussian", seed=14, algo="hybrid")
+    assert oracle.normwise_error(C, C64, An, Bn) <= tolerance("f16", 2, 768)
+    C, C64, An, Bn = run(512, 512, 512, 2, "f16", dist="badly_scaled", seed=15, algo="hybrid")
+    assert np.all(np.isfinite(C))
+    assert oracle.normwise_error(C, C64, An, Bn) <= tolerance("f16", 2, 512)
+
+
+def test_hybrid_f16_large_values_do_not_overflow():
+    """Sums of FP16 inputs near 2^15 exceed FP16's range unscaled (65504)."""
+    A = (synth.uniform((256, 256), 82) * 30000.0).astype(np.float32)
+    B = (synth.uniform((256, 256), 83) * 30000.0).astype(np.float32)
+    Ad = torch.from_numpy(A).half().cuda()
+    Bd = torch.from_numpy(B).half().cuda()
+    C = fmm.gemm(Ad, Bd, levels=2, variant="f16", algo="hybrid")
+    fmm.device_status()
+    Ab = Ad.cpu().view(torch.int16).numpy().view(np.uint16)
+    Bb = Bd.cpu().view(torch.int16).numpy().view(np.uint16)
+    C64 = oracle.classical(Ab, Bb, a_code=oracle.ORC_F16, b_code=oracle.ORC_F16)
+    Cn = C.cpu().numpy()
+    assert np.all(np.isfinite(Cn))
+    err = oracle.normwise_error(Cn, C64, float(Ad.float().norm()), float(Bd.float().norm()))
+    assert err <= tolerance("f16", 2, 256), err
+
+
 @pytest.mark.parametrize("pads", [(1, 3, 1), (0, 0, 1), (5, 0, 0)])
 def test_hybrid_unaligned_leading_dimensions_bit_exact(pads):
     """Odd leading dimensions: the top-level sum pass reads any row stride and writes aligned
