@@ -285,7 +285,8 @@ def run_extras(a, fmm, torch, dev, stream, peak, peak_src):
             r = {"levels": lv, "variant": variant, "basis": basis,
                  "value": flops / (ms * 1e-3) * 1e-12, "ms_per_step": ms,
                  "roofline": {"bound": "tensor",
-                              "kernel": "fmm_fused_ts_kernel" if label.startswith("hybrid") else "fmm_packed_kernel",
+                              "kernel": ("fmm_fused_ts_kernel" if label.startswith(("hybrid", "fused"))
+                                         else "fmm_packed_kernel"),
                               "kernel_ms_per_step": ker_ms,
                               "launches_per_step": prof["tensor"][1] / steps,
                               "achieved": mma / (ker_ms * 1e-3) * 1e-12 if ker_ms > 0 else None,
@@ -389,6 +390,32 @@ def run_extras(a, fmm, torch, dev, stream, peak, peak_src):
           "inputs": "N(0,1) cast to BF16, dC N(0,1) float32, seeded"}, m, n, k, runs,
           3 * 2.0 * m * n * k,
           lambda: sampled_error(oracle, Cd, Ab, Bb, rows, oracle.ORC_BF16, oracle.ORC_BF16))
+    del Ad, Bd, Gd, Cd, runs
+
+    # the C3 layer shape in FP32 with every operand sum formed on chip: forward (fused kernel)
+    # and backward (the same kernel on the transposed tiles), against the classical layer
+    m, k, n = 8192, 4096, 4096
+    A = synth.gaussian((m, k), 1610)
+    B = synth.gaussian((k, n), 1611)
+    G = synth.gaussian((m, n), 1612)
+    Ad, Bd, Gd = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev), torch.from_numpy(G).to(dev)
+    Cd = torch.empty((m, n), dtype=torch.float32, device=dev)
+    runs = {}
+    for label, lv, algo in (("fused_L1", 1, "fused"), ("classical", 0, "auto")):
+        wsf = torch.empty(max(fmm.workspace_size(m, n, k, lv, "split3", algo), 256), dtype=torch.uint8, device=dev)
+        wsb = torch.empty(max(fmm.workspace_size_backward(m, n, k, lv, "split3"), 256), dtype=torch.uint8,
+                          device=dev)
+
+        def layer32(lv=lv, algo=algo, wsf=wsf, wsb=wsb):
+            fmm.gemm(Ad, Bd, Cd, 1.0, 0.0, levels=lv, algo=algo, workspace=wsf, stream=stream)
+            fmm.gemm_backward(Ad, Bd, Gd, levels=lv, algo=algo, workspace=None if algo == "fused" else wsb,
+                              stream=stream)
+        runs[label] = (lv, "split3", "strassen", layer32)
+    rows = np.unique(synth.rng(8193).integers(0, m, size=6))
+    entry(f"strassen-split3-linear-fwd-bwd-on-chip-m{m}-k{k}-n{n}", {"variant": "split3",
+          "step": "forward C = A B, backward dA = dC B^T and dB = A^T dC; operand sums formed on chip",
+          "inputs": "N(0,1) float32, seeded"}, m, n, k, runs, 3 * 2.0 * m * n * k,
+          lambda: sampled_error(oracle, Cd, A, B, rows))
     del Ad, Bd, Gd, Cd, runs
 
     # C4: 256 uneven FP16 products (multiples of 256 in [1024, 8192]) in one persistent
