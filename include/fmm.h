@@ -142,8 +142,10 @@ typedef struct fmm_options {
     int store_first; /* packed algorithm, beta = 0, levels >= 1: 0 = automatic (on), 1 = off (C is
                         zeroed first and every product adds into it), 2 = on: the products run in
                         a few launch phases so that the first update of every C block stores it
-                        (no zeroing pass, no read of C by those updates); not with the pipelined,
-                        deterministic or outside-scaling modes, nor in batched plans */
+                        (no zeroing pass, no read of C by those updates); in the deterministic
+                        mode the products of each tile position run in order on one worker, so
+                        the first one to update a block stores it within the single launch;
+                        not with the pipelined or outside-scaling modes, nor in batched plans */
     int reserved[2]; /* zero */
 } fmm_options;
 

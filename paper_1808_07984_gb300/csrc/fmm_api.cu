@@ -848,6 +848,9 @@ struct PackedJob {
   std::vector<PackedParams> chunks;
   // store-first plans (beta = 0): one parameter block per launch phase; C is not zeroed
   std::vector<PackedParams> phases;
+  // store-first in the ownership mode (one launch; each tile position's products run in order
+  // on one worker, each item's C updates complete before the next item's): C is not zeroed
+  bool owned_store = false;
 };
 
 // Launch phases in which, with beta = 0, the first update of every C block is a store: no
@@ -1040,7 +1043,20 @@ fmm_status prepare_packed(const Plan& pl, int64_t m, int64_t n, int64_t k, float
   if (batched) job.pl.pipeline = false;
   job.chunks.clear();
   job.phases.clear();
+  job.owned_store = false;
   const int sf = opt ? opt->store_first : 0;
+  if ((sf == 0 || sf == 2) && beta == 0.0f && pl.R > 1 && !batched && !job.pl.pipeline && pl.deterministic &&
+      !pl.outer_scaling && pl.algo == FMM_ALGO_PACKED) {
+    // ownership order: the first product (in product order) to update a block stores it
+    bool written[kMaxSources] = {};
+    for (int r = 0; r < pp->c.num_products; ++r)
+      for (int d = 0; d < pp->c.prod[r].count; ++d) {
+        DestEntry& de = pp->c.prod[r].d[d];
+        de.store = written[de.block] ? 0 : 1;
+        written[de.block] = true;
+      }
+    job.owned_store = true;
+  }
   if (sf == 0 || sf == 2) {
     if (beta == 0.0f && pl.R > 1 && !batched && !job.pl.pipeline && !pl.deterministic && !pl.outer_scaling &&
         pl.algo == FMM_ALGO_PACKED) {
@@ -1195,7 +1211,8 @@ fmm_status launch_passes(const PackedJob& job, const DeviceInfo& dev, cudaStream
                            : launch_outer_rescale(job.C, job.m, job.n, job.ldc, job.sa.row_maxbits,
                                                   job.sb.col_maxbits, -1, job.beta, dev.sms, s);
     if (e != cudaSuccess) return cuda_fail(e, "outside-scaling passes");
-  } else if (job.beta != 1.0f && !(job.has_work && (job.params.c.c_store || !job.phases.empty()))) {
+  } else if (job.beta != 1.0f &&
+             !(job.has_work && (job.params.c.c_store || !job.phases.empty() || job.owned_store))) {
     PhaseScope ps(kPhaseBeta, s);
     cudaError_t e = launch_beta(job.C, job.m, job.n, job.ldc, job.beta, dev.sms, s);
     if (e != cudaSuccess) return cuda_fail(e, "beta pass");

@@ -906,6 +906,17 @@ def test_store_first_phases_bit_exact(m, n, k, levels, basis, pad_c, store_first
     np.testing.assert_array_equal(C, C64)
 
 
+@pytest.mark.parametrize("levels,basis", [(1, "strassen"), (2, "strassen"), (1, "b323")])
+@pytest.mark.parametrize("pad_c", [0, 1])
+@pytest.mark.parametrize("m,n,k", [(300, 520, 200), (1000, 1200, 300), (600, 2100, 96)])
+def test_store_first_in_ownership_mode_bit_exact(m, n, k, levels, basis, pad_c):
+    """Deterministic (ownership) mode with beta = 0: one launch, every tile position's products
+    in order on one worker, the first product to update a block stores it; C starts as NaN."""
+    C, C64, _, _ = run(m, n, k, levels, "split3", dist="int", seed=m + n + levels, basis=basis,
+                       pads=(0, 0, pad_c), c_fill=float("nan"), deterministic=True)
+    np.testing.assert_array_equal(C, C64)
+
+
 @pytest.mark.parametrize("levels", [1, 2])
 def test_store_first_negative_alpha_and_float(levels):
     A, B = synth.problem(136, 264, 72, 93, "int")
