@@ -146,6 +146,21 @@ def test_option_errors_need_no_gpu(lib):
     assert _call_ex(lib, levels=2, basis=2) == 3            # <3,2,3>: one level
     assert _call_ex(lib, algo=3, levels=2, basis=2) == 3    # <3,2,3>: no hybrid (two-level) form
     assert _call_ex(lib, basis=2, pipeline=2) == 3          # <3,2,3>: one table pass
+    assert _call_ex(lib, fused_kernel=3) == 1
+    assert _call_ex(lib, fused_kernel=-1) == 1
+    assert _call_ex(lib, store_first=3) == 1
+    assert _call_ex(lib, algo=2, cta_pair=1, fused_kernel=2) == 3  # tensor-memory kernel: CTA pairs
+
+
+def test_options_struct_matches_the_header():
+    """The binding's fmm_options has the header's fields in the header's order and size."""
+    import re
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "fmm.h")).read()
+    body = hdr[hdr.index("typedef struct fmm_options {"):hdr.index("} fmm_options;")]
+    fields = re.findall(r"^\s*int\s+(\w+)(\[(\d+)\])?;", body, re.M)
+    names = [f[0] for f in fields]
+    assert names == [f[0] for f in fmm._Options._fields_]
+    assert ctypes.sizeof(fmm._Options) == 4 * sum(int(f[2]) if f[2] else 1 for f in fields)
 
 
 def test_basis_shapes(lib):
