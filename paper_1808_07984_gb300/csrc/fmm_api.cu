@@ -306,8 +306,11 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
   pl.hn = grid_block(n, pl.gn);
   pl.hk = grid_block(k, pl.gk);
   // automatic choice (measured on GB300): tile rounds, which keep the destination blocks of
-  // a round in L2
-  pl.schedule = sched == 1 ? kSchedProductMajor : kSchedTileRounds;
+  // a round in L2; with the sums formed on chip, product-major order (all pairs on one
+  // product, so the source tiles of its blocks are shared in L2 by every tile in flight:
+  // +9 % one level, +7 % hybrid at 16384^3 over tile rounds of one tile per pair)
+  const bool on_chip_algo = pl.algo == FMM_ALGO_FUSED || pl.algo == FMM_ALGO_HYBRID;
+  pl.schedule = (sched == 1 || (sched == 0 && on_chip_algo)) ? kSchedProductMajor : kSchedTileRounds;
   const int bk = opt ? opt->bk : 0;
   const int cta_pair = opt ? opt->cta_pair : 0;
   if (cta_pair < 0 || cta_pair > 2) return fail(FMM_ERR_ARG, "cta_pair must be 0, 1 or 2");
