@@ -321,6 +321,15 @@ int fmm_product_table(int levels, int8_t* U, int8_t* V, int8_t* W);
  * that of product r in C block (i, j); U holds g_m g_k R entries, V g_k g_n R, W g_m g_n R.
  * Returns R, or -1 for a bad argument or a basis and level count that are not built. */
 int fmm_product_table_ex(int levels, int basis, int8_t* U, int8_t* V, int8_t* W);
+
+/* The store-first launch phases the library runs for beta = 0 (fmm_options.store_first):
+ * phase_of[r] (R entries) receives the phase of product r, store[c * R + r] (g_m g_n R
+ * entries, the layout of W above) is 1 where product r stores C block c -- the block's first
+ * update -- and 0 where it adds into it or does not touch it.  Returns the number of phases,
+ * or -1 (levels < 1, or a basis and level count that is not built).  Host only, no CUDA call.
+ * The paper runs the instances in any order with atomic updates (Section 3.3); this planner
+ * orders them so that C needs no zeroing pass. */
+int fmm_store_phases(int levels, int basis, int* phase_of, int8_t* store);
 /* Block grid and product count of `levels` levels of a basis: dims[0..3] = g_m, g_k, g_n,
  * R (levels 0: 1, 1, 1, 1; Strassen and Strassen-Winograd: 2^L, 2^L, 2^L, 7^L; basis 2 at
  * one level: 3, 2, 3, 15).  Returns 0, or -1 for a combination that is not built. */

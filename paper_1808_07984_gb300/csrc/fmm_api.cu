@@ -8,6 +8,7 @@
 #include <atomic>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -1819,6 +1820,30 @@ int fmm_product_table_ex(int levels, int basis, int8_t* U, int8_t* V, int8_t* W)
     for (const Term& t : prods[r].c) W[t.block * R + r] = static_cast<int8_t>(t.sign);
   }
   return R;
+}
+
+int fmm_store_phases(int levels, int basis, int* phase_of, int8_t* store) {
+  BasisShape sh;
+  if (!phase_of || !store || levels < 1 || !basis_shape(levels, basis, sh)) return -1;
+  const int R = sh.R, nblocks = sh.gm * sh.gn;
+  if (R > kMaxProducts || nblocks > kMaxSources) return -1;
+  const std::vector<Product> prods = make_products(levels, basis);
+  std::unique_ptr<CommonParams> c(new CommonParams);
+  std::memset(c.get(), 0, sizeof(CommonParams));
+  c->num_products = R;
+  for (int r = 0; r < R; ++r) {
+    int cnt = 0;
+    for (const Term& t : prods[r].c) c->prod[r].d[cnt++].block = t.block;
+    c->prod[r].count = cnt;
+  }
+  const std::vector<std::vector<int>> ph = plan_store_phases(*c);
+  std::memset(store, 0, static_cast<size_t>(R) * nblocks);
+  for (size_t i = 0; i < ph.size(); ++i)
+    for (int r : ph[i]) phase_of[r] = static_cast<int>(i);
+  for (int r = 0; r < R; ++r)
+    for (int d = 0; d < c->prod[r].count; ++d)
+      store[c->prod[r].d[d].block * R + r] = static_cast<int8_t>(c->prod[r].d[d].store);
+  return static_cast<int>(ph.size());
 }
 
 fmm_status fmm_profile_enable(int on) {

@@ -196,3 +196,40 @@ def test_b323_workspace_sizes(lib):
     b = -(-15 * hk * hn * 2 // 256) * 256
     assert fmm.workspace_size(m, n, k, 1, basis="b323") == 2 * (a + b)
     assert fmm.workspace_size(m, n, k, 1, "plain_bf16", basis="b323") == a + b
+
+
+@pytest.mark.parametrize("levels,basis,want", [(1, 0, [1, 4, 2]), (2, 0, [1, 12, 24, 12]), (1, 1, None), (1, 2, None)])
+def test_store_first_phases_are_a_valid_order(lib, levels, basis, want):
+    """Host-side plan of the store-first launch phases (no GPU): every C block that some
+    product updates is stored by exactly one product, that product runs in a strictly earlier
+    phase than every other product updating the block, and no phase holds two products that
+    touch a block one of them stores.  Strassen's phase sizes are the documented ones."""
+    lib.fmm_store_phases.restype = ctypes.c_int
+    lib.fmm_store_phases.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    gm, gk, gn, R = fmm.basis_shape(levels, basis)
+    _, _, W = fmm.product_table(levels, basis)
+    phase = np.zeros(R, dtype=np.int32)
+    store = np.zeros(gm * gn * R, dtype=np.int8)
+    nph = lib.fmm_store_phases(levels, basis, phase.ctypes.data, store.ctypes.data)
+    assert nph >= 1
+    store = store.reshape(gm * gn, R)
+    assert set(np.unique(phase)) == set(range(nph))
+    for c in range(gm * gn):
+        touch = np.nonzero(W[c])[0]
+        if len(touch) == 0:
+            continue
+        storers = np.nonzero(store[c])[0]
+        assert len(storers) == 1, (c, storers)
+        s = storers[0]
+        assert W[c, s] != 0
+        for r in touch:
+            if r != s:
+                assert phase[r] > phase[s], (c, r, s)
+    for ph in range(nph):
+        members = np.nonzero(phase == ph)[0]
+        for c in range(gm * gn):
+            if store[c, members].any():
+                assert np.count_nonzero(W[c, members]) == 1, (ph, c)
+    if want is not None:
+        assert [int(np.count_nonzero(phase == p)) for p in range(nph)] == want
+    assert lib.fmm_store_phases(0, 0, phase.ctypes.data, store.ctypes.data) == -1
