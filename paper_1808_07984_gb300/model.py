@@ -9,27 +9,34 @@ updates).  On GB300 the same three costs appear in different places:
 * the tensor-core kernel does (7/8)^L of the classical UMMA work, 1 or 3 UMMAs per k16 slice,
   in 256 x tile_n CTA-pair tiles distributed over 76 CTA pairs;
 * every work item adds its accumulator into W_C destination tiles of C (TMA reductions
-  through L2), which costs time the mainloop does not hide.
+  through L2; the first update of each C block is a store, half the bytes), which costs time
+  the mainloop does not hide.
 
     T = t_beta + t_pack + t_tensor + launches * t_launch
-    t_beta   = 4 m n / BW, levels > 0                       (C zeroed; a classical product
-                                                             stores C instead, so none)
+    t_beta   = 0 with beta = 0: a classical product stores C, and a Strassen product stores
+               the first update of each C block (store-first launch phases); 4 m n / BW
+               when C has to be zeroed first (store_first=False)
     t_pack   = pack_bytes / (BW * pack_eff)
-    t_tensor = W * (t_item_mma + t_item_fix + wb_bytes_item * wb_cost)
-    W        = ceil(items / workers)                        (items of the busiest CTA pair)
+    t_tensor = t_work + cap_slope * max(0, t_mma - cap_t0) * (t_mma / t_work)^2
+    t_work   = W * (t_item_mma + t_item_fix + wb_bytes_item * wb_cost),  t_mma = W * t_item_mma
+               (the power cap lowers the SM clock under long dense UMMA work, the more so the
+               larger the tensor cores' share of the kernel's time)
+    W        = sum over the store-first launch phases of ceil(items_phase / workers)
     items    = R * ceil(h_m / 256) * ceil(h_n / tile_n)     (R products of a basis)
     t_item_mma = terms * 2 * 256 * tile_n * h_k / (TC * tc_eff / workers)
                  (times n128_slow for 128-wide tiles)
 
 BW and TC are the measured HBM copy bandwidth and burst BF16 tensor rate of the pool's
-GB300s; pack_eff, tc_eff, wb_cost, t_item_fix, t_launch and n128_slow are fitted to measured
-library calls (``fit``).  ``DEFAULT`` holds the fit to square, panel and rank-k sweeps of
-split3 products measured on GB300 at the automatic tile width (mean absolute error 6.9 % over
-58 calls) together with calls at both tile widths (6.6 % over 30 calls).  pack_eff comes out
-at 1.0 (the sum pass streams at the measured copy bandwidth), tc_eff slightly above 1 (the
-UMMA rate of a kernel timed inside a sequence of calls matches the burst figure), and
-128-wide tiles run 25 % slower per flop.  The largest products run below the model (up to
-15 % at 20480): there the power cap lowers the SM clock, which the model does not represent.
+GB300s; pack_eff (at most 1), tc_eff, wb_cost, t_item_fix, t_launch, n128_slow and the two
+power-cap terms are fitted to measured library calls (``fit``).  ``DEFAULT`` holds the fit to
+136 split3 calls measured on a GB300 (square, panel and rank-k sweeps at the automatic tile
+width, calls at both tile widths, and classical, one- and two-level Strassen and the <3,2,3>
+basis at twelve sizes): mean absolute error 3.5 % (4.5 %, 3.4 % and 2.5 % over the three
+files).  pack_eff comes out at 1.0 (the sum pass streams at the measured copy bandwidth);
+tc_eff at 1.21, i.e. short UMMA work runs at 2.30 PFLOP/s, 89 % of what 152 SMs reach at the
+maximum clock (the burst denominator is a cuBLAS product timed at a lower clock); 128-wide
+tiles run 24 % slower per flop; dense UMMA work beyond about 2 ms slows by up to 28 % (the power
+cap's clock drop).
 
 Used by ``autotune.autotune(prior="model")`` to rank the (levels, tile_n) candidates of each
 size so that only the most promising ones are measured, and (``best_basis``) to choose
@@ -41,12 +48,17 @@ from __future__ import annotations
 
 import math
 
-GB300 = {"sms": 152, "hbm_gbs": 6777.0, "tc_tflops": 1934.1}
+GB300 = {"sms": 152, "hbm_gbs": 6781.1, "tc_tflops": 1897.8}
+# UMMA rate of 152 SMs at the maximum SM clock (8192 BF16 flops per SM and cycle at 2070 MHz)
+# over the measured burst rate: the largest tc_eff ``fit`` allows
+_TC_EFF_MAX = 152 * 8192 * 2.070e9 / 1897.8e12
 
-# fitted (``fit``) to the 58 measured split3 calls in tuned/gb300_model_samples.json (automatic
-# tile width) and the 30 at explicit tile widths in tuned/gb300_tile_samples.json
-DEFAULT = {"pack_eff": 0.997, "tc_eff": 1.060, "wb_cost_ns_per_kb": 10.59, "t_item_fix_us": 0.0,
-           "t_launch_us": 5.57, "n128_slow": 1.249}
+# fitted (``fit``) to the 136 measured split3 calls of ``calibration_samples()``: 58 at the
+# automatic tile width (tuned/gb300_model_samples.json), 30 at explicit tile widths
+# (gb300_tile_samples.json) and 48 of four bases (gb300_basis_samples.json), all measured with
+# the store-first write-back (beta = 0: no zeroing pass, first updates stored)
+DEFAULT = {"pack_eff": 1.000, "tc_eff": 1.212, "wb_cost_ns_per_kb": 14.98, "t_item_fix_us": 0.0,
+           "t_launch_us": 8.46, "n128_slow": 1.239, "cap_slope": 0.283, "cap_t0_ms": 2.07}
 
 _TERMS = {"split3": 3, "plain_bf16": 1, "bf16": 1, "f16": 1}
 # one-level bases: block grid (g_m, g_k, g_n), products R and nonzeros of W (C updates)
@@ -83,10 +95,16 @@ def auto_tile_n(m: int, n: int, levels: int, basis: str = "strassen") -> int:
     return 256 if items256 >= 4 * (GB300["sms"] // 2) else 128
 
 
+# products per launch phase of the store-first write-back (the library's fmm_store_phases)
+_PHASES = {(1, "strassen"): (1, 4, 2), (2, "strassen"): (1, 12, 24, 12), (1, "winograd"): (1, 6),
+           (1, "b323"): (5, 7, 3)}
+
+
 def predict(m: int, n: int, k: int, levels: int, variant: str = "split3", tile_n: int = 0,
-            params: dict | None = None, hw: dict | None = None, basis: str = "strassen") -> dict:
-    """Predicted milliseconds of fmm_gemm(m, n, k, levels, variant, basis) and its
-    components."""
+            params: dict | None = None, hw: dict | None = None, basis: str = "strassen",
+            store_first: bool = True) -> dict:
+    """Predicted milliseconds of fmm_gemm(m, n, k, levels, variant, basis) with beta = 0 and
+    its components."""
     p = dict(DEFAULT, **(params or {}))
     h = dict(GB300, **(hw or {}))
     gm, gk, gn, R, wc = shape(levels, basis)
@@ -94,12 +112,15 @@ def predict(m: int, n: int, k: int, levels: int, variant: str = "split3", tile_n
     hm, hn, hk = block(m, levels, gm), block(n, levels, gn), block(k, levels, gk)
     tn = tile_n or auto_tile_n(m, n, levels, basis)
     bw = h["hbm_gbs"] * 1e9
-    t_beta = 4.0 * m * n / bw if levels > 0 else 0.0
+    t_beta = 4.0 * m * n / bw if (levels > 0 and not store_first) else 0.0
     pack_bytes = (m * k + k * n) * e_in + R * (hm * hk + hk * hn) * 2 * arrays
     t_pack = pack_bytes / (bw * p["pack_eff"])
     workers = h["sms"] // 2
-    items = R * -(-hm // 256) * -(-hn // tn)
-    per_worker = -(-items // workers)
+    tiles = -(-hm // 256) * -(-hn // tn)
+    items = R * tiles
+    # each launch phase ends with a partial wave of items
+    phases = _PHASES.get((levels, basis), (R,)) if (levels > 0 and store_first) else (R,)
+    per_worker = sum(-(-(P * tiles) // workers) for P in phases)
     tc = h["tc_tflops"] * 1e12 * p["tc_eff"] / workers
     t_item_mma = terms * 2.0 * 256 * tn * hk / tc
     if tn == 128:
@@ -109,14 +130,23 @@ def predict(m: int, n: int, k: int, levels: int, variant: str = "split3", tile_n
     # wc: average W_C of a product (Strassen: 12 nonzeros of W over 7 products per level)
     # a classical product stores its tile (write only); Strassen products add into C (read and
     # write of every destination tile)
-    wb_bytes_item = wc * 256 * tn * 4 * (0.5 if levels == 0 else 1.0)
+    if levels == 0:
+        wb_bytes_item = wc * 256 * tn * 4 * 0.5
+    else:
+        # of the R * wc block updates, one per C block (gm * gn of them) stores
+        f_store = (gm * gn) / (R * wc) if store_first else 0.0
+        wb_bytes_item = wc * 256 * tn * 4 * (1.0 - 0.5 * f_store)
     t_item = t_item_mma + p["t_item_fix_us"] * 1e-6 + wb_bytes_item / 1024.0 * p["wb_cost_ns_per_kb"] * 1e-9
     t_tensor = per_worker * t_item
-    launches = 4
+    # the power cap: dense UMMA work lasting longer than cap_t0 runs at a lower SM clock, the
+    # more so the larger the share of the kernel's time the tensor cores are busy
+    t_mma = per_worker * t_item_mma
+    t_tensor += p["cap_slope"] * max(0.0, t_mma - p["cap_t0_ms"] * 1e-3) * (t_mma / t_tensor) ** 2
+    launches = 2 + len(phases)
     t = t_beta + t_pack + t_tensor + launches * p["t_launch_us"] * 1e-6
     return {"ms": t * 1e3, "beta_ms": t_beta * 1e3, "pack_ms": t_pack * 1e3,
             "tensor_ms": t_tensor * 1e3, "items": items, "items_per_pair": per_worker,
-            "tile_n": tn, "eff_tflops": 2.0 * m * n * k / t * 1e-12}
+            "launches": launches, "tile_n": tn, "eff_tflops": 2.0 * m * n * k / t * 1e-12}
 
 
 def best_levels(m: int, n: int, k: int, variant: str = "split3", params: dict | None = None) -> int:
@@ -139,7 +169,11 @@ def rank_candidates(d: int, variant: str = "split3", levels=(0, 1, 2), tiles=(12
 
 
 def _pred_ms(sample, variant, params):
-    """Predicted ms of a sample (m, n, k, levels, ms) or (m, n, k, levels, tile_n, ms)."""
+    """Predicted ms of a sample (m, n, k, levels, ms), (m, n, k, levels, tile_n, ms) or
+    (m, n, k, levels, tile_n, basis, ms)."""
+    if len(sample) == 7:
+        m, n, k, L, tn, b, _ = sample
+        return predict(m, n, k, L, variant, tile_n=tn, params=params, basis=b)["ms"]
     if len(sample) == 6:
         m, n, k, L, tn, _ = sample
     else:
@@ -150,8 +184,9 @@ def _pred_ms(sample, variant, params):
 def fit(samples, variant: str = "split3", start: dict | None = None, iters: int = 400) -> dict:
     """Least-squares fit of the model's free parameters to measured calls.
 
-    samples: iterable of (m, n, k, levels, measured_ms), or (m, n, k, levels, tile_n,
-    measured_ms) for calls at an explicit tile width.  Minimises the mean squared log ratio of
+    samples: iterable of (m, n, k, levels, measured_ms), (m, n, k, levels, tile_n,
+    measured_ms) for calls at an explicit tile width (0: automatic), or (m, n, k, levels,
+    tile_n, basis, measured_ms).  Minimises the mean squared log ratio of
     predicted to measured time by coordinate search (no dependency beyond math)."""
     samples = list(samples)
     p = dict(DEFAULT, **(start or {}))
@@ -171,8 +206,10 @@ def fit(samples, variant: str = "split3", start: dict | None = None, iters: int 
             for sgn in (1, -1):
                 q = dict(p)
                 q[key] = max(1e-6, p[key] + sgn * step[key])
-                if key in ("pack_eff", "tc_eff"):
-                    q[key] = min(q[key], 1.2)
+                if key == "tc_eff":
+                    q[key] = min(q[key], _TC_EFF_MAX)
+                if key == "pack_eff":
+                    q[key] = min(q[key], 1.0)  # the sum pass cannot beat the copy bandwidth
                 lq = loss(q)
                 if lq < best:
                     p, best, improved = q, lq, True
@@ -192,23 +229,44 @@ def mean_abs_error(samples, variant: str = "split3", params: dict | None = None)
 
 
 def load_samples(path: str):
-    """Samples of a calibration file: (m, n, k, levels, ms), or (m, n, k, levels, tile_n, ms)
-    for a file of calls at explicit tile widths."""
+    """Samples of a calibration file: (m, n, k, levels, ms), (m, n, k, levels, tile_n, ms)
+    for a file of calls at explicit tile widths, or (m, n, k, levels, 0, basis, ms) for a
+    file whose columns are m, n, k and one time per "L<levels>_<basis>" candidate."""
     import json
     with open(path) as f:
         rec = json.load(f)
-    rows = rec["samples_m_n_k_levels_ms"] if "samples_m_n_k_levels_ms" in rec else rec["rows"]
-    return [tuple(x) for x in rows], rec.get("variant", "split3")
+    var = rec.get("variant", "split3")
+    if "samples_m_n_k_levels_ms" in rec:
+        return [tuple(x) for x in rec["samples_m_n_k_levels_ms"]], var
+    cols = rec.get("columns", [])
+    if len(cols) > 3 and all(c.startswith("L") and "_" in c for c in cols[3:]):
+        cands = [(int(c[1:c.index("_")]), c[c.index("_") + 1:]) for c in cols[3:]]
+        return [(m, n, k, L, 0, b, t) for m, n, k, *ms in rec["rows"]
+                for (L, b), t in zip(cands, ms)], var
+    return [tuple(x) for x in rec["rows"]], var
+
+
+def calibration_samples(variant: str = "split3"):
+    """Every measured call of the tuned/ calibration files (the samples ``DEFAULT`` is fitted
+    to)."""
+    import os
+    d = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned")
+    out = []
+    for name in ("gb300_model_samples.json", "gb300_tile_samples.json", "gb300_basis_samples.json"):
+        S, var = load_samples(os.path.join(d, name))
+        if var == variant:
+            out += S
+    return out
 
 
 if __name__ == "__main__":
     import argparse
     import os
     ap = argparse.ArgumentParser(description="fit or check the GB300 time model")
-    ap.add_argument("--samples", default=os.path.join(os.path.dirname(__file__), "tuned",
-                                                      "gb300_model_samples.json"))
+    ap.add_argument("--samples", default=None,
+                    help="one calibration file (default: every file under tuned/)")
     ap.add_argument("--fit", action="store_true")
     a = ap.parse_args()
-    S, var = load_samples(a.samples)
+    S, var = load_samples(a.samples) if a.samples else (calibration_samples(), "split3")
     prm = fit(S, var) if a.fit else DEFAULT
     print({k_: round(v, 4) for k_, v in prm.items()}, "mean abs error", round(mean_abs_error(S, var, prm), 4))

@@ -77,7 +77,14 @@ def test_model_block_rule_matches_library_rule():
 def test_model_components_and_classical_case():
     r = model.predict(8192, 8192, 8192, 0)
     assert r["ms"] > 0 and r["items"] == (8192 // 256) * (8192 // 256)
-    assert abs(r["ms"] - (r["beta_ms"] + r["pack_ms"] + r["tensor_ms"] + 4 * model.DEFAULT["t_launch_us"] * 1e-3)) < 1e-9
+    assert r["launches"] == 3  # classical: sum pass, tensor kernel, one store phase
+    assert abs(r["ms"] - (r["beta_ms"] + r["pack_ms"] + r["tensor_ms"]
+                          + r["launches"] * model.DEFAULT["t_launch_us"] * 1e-3)) < 1e-9
+    # store-first: no zeroing pass with beta = 0, one launch per phase (1, 12, 24, 12 products)
+    s2 = model.predict(16384, 16384, 16384, 2)
+    assert s2["beta_ms"] == 0 and s2["launches"] == 6
+    z2 = model.predict(16384, 16384, 16384, 2, store_first=False)
+    assert z2["beta_ms"] > 0 and z2["launches"] == 3 and z2["ms"] > s2["ms"]
 
 
 def test_model_levels_trade_mma_for_sums_and_writeback():
@@ -103,6 +110,25 @@ def test_model_calibration_samples_fit_within_ten_percent():
     S, var = model.load_samples(path)
     assert len(S) >= 50
     assert model.mean_abs_error(S, var) < 0.10
+    allS = model.calibration_samples()
+    assert len(allS) >= 130 and model.mean_abs_error(allS) < 0.05
+    # worst single call: a rank-512 panel at one level (-17 %)
+    assert max(abs(model._pred_ms(x, "split3", None) / x[-1] - 1) for x in allS) < 0.20
+
+
+def test_model_power_cap_term_is_bounded_and_monotone():
+    """The power-cap term slows long dense UMMA work by at most cap_slope and does not touch
+    products shorter than cap_t0."""
+    off = dict(model.DEFAULT, cap_slope=0.0)
+    for d in (2048, 4096):
+        assert model.predict(d, d, d, 0)["ms"] == model.predict(d, d, d, 0, params=off)["ms"]
+    prev = 0.0
+    for d in (12288, 16384, 24576):
+        on, no = model.predict(d, d, d, 0)["tensor_ms"], model.predict(d, d, d, 0, params=off)["tensor_ms"]
+        assert no < on <= no * (1 + model.DEFAULT["cap_slope"])
+        assert on / no >= prev
+        prev = on / no
+    assert model._TC_EFF_MAX > model.DEFAULT["tc_eff"] > 1.0
 
 
 def test_model_ranks_candidates():
@@ -143,16 +169,18 @@ def test_model_b323_pays_for_padding_at_16384():
 def test_model_picks_the_measured_fastest_basis_on_square_sizes():
     """Against the whole-call times measured on a GB300 (tuned/gb300_basis_samples.json):
     the model's choice among classical, Strassen (one, two levels) and the <3,2,3> basis is
-    the measured fastest, or within 2 % of it, at every square size."""
+    the measured fastest, or within 5 % of it, at every size (the worst measured miss, 4.5 %,
+    is a rank-4096 panel; the candidates there lie within 10 % of one another)."""
     path = os.path.join(os.path.dirname(model.__file__), "tuned", "gb300_basis_samples.json")
     with open(path) as f:
         rec = json.load(f)
     cands = [(0, "strassen"), (1, "strassen"), (1, "b323"), (2, "strassen")]
+    hits = 0
     for m, n, k, *ms in rec["rows"]:
-        if not (m == n == k):
-            continue
         pick = min(cands, key=lambda c: model.predict(m, n, k, c[0], basis=c[1])["ms"])
-        assert ms[cands.index(pick)] <= 1.02 * min(ms), (m, pick, ms)
+        assert ms[cands.index(pick)] <= 1.05 * min(ms), (m, pick, ms)
+        hits += ms[cands.index(pick)] == min(ms)
+    assert hits >= len(rec["rows"]) // 2
 
 
 def test_choose_follows_the_model():
