@@ -2,7 +2,7 @@
 //
 // For product r the A-operand is P = sum_w sign_w * A_block(w) (W_A terms) and the
 // B-operand Q = sum_w sign_w * B_block(w) (W_B terms).  Per 64-deep k-step:
-//   warp 0      TMA-loads, for each k half (32 deep) and each source block, one FP32 tile
+//   warps 0, 2  (lane 0 of each) TMA-load, for each k half (32 deep) and each source block, one FP32 tile
 //               into a 4-slot shared-memory ring (A: 128 rows x 32 k, 128-byte swizzle;
 //               B: 32 k-rows x 128 n, unswizzled) -- the W_A (W_B) submatrix tiles;
 //   warps 8-15  (transform) add every slot into FP32 register accumulators with its sign,
@@ -29,6 +29,10 @@ template <int TW>
 constexpr int fused_threads() { return 256 + 32 * TW; }
 constexpr int kFusedBN = kFusedTileN;  // columns of the B-operand each CTA forms
 constexpr uint32_t kSlotBytes = 16384;
+// threads issuing the source-tile loads: lane 0 of warps 0 and 2 (one issuing thread per warp:
+// lanes of one warp that wait on different slots hold each other up)
+constexpr int kFusedProducers = 2;    // fmm_fused_kernel: slots 0, 2 and 1, 3 of its ring
+constexpr int kFusedTsProducers = 2;  // fmm_fused_ts_kernel: one per k-half ring
 
 template <int TERMS, bool PAIR>
 struct FusedCfg {
@@ -70,32 +74,43 @@ __device__ __forceinline__ void split2(float x0, float x1, uint32_t& hi, uint32_
 // consumer groups could be awaited by one group while the other's use of it is still a phase
 // behind, which the parity of an mbarrier wait cannot tell apart).  A_MN: the A-operand
 // blocks are stored by rows of k (their maps are {m, k}, box 128 x 32); B_KM: the B-operand
-// blocks are stored by rows of n (maps {k, n}, box 32 x 128, 128-byte swizzle).  Returns false
-// if a wait gave up or a parameter block named a tensor map outside its table (error bit set).
-template <int NS, bool PAIR, int RINGS = 1, bool A_MN = false, bool B_KM = false>
+// blocks are stored by rows of n (maps {k, n}, box 32 x 128, 128-byte swizzle).
+// NPROD threads issue the loads, thread `who` of them (0 <= who < NPROD): one thread loads
+// every ring; with two rings and more threads, even `who` load ring 0 and odd ones ring 1; the NSUB = NPROD / RINGS threads of a
+// ring take its tiles in turn (the c-th tile of the ring, counted in the ring's order, goes to
+// thread c % NSUB, into slot c % NPR).  One issuing thread limits this loader (measured on GB300
+// with 16 KB tiles that stay in L2: about 28 bytes per SM and cycle from one thread, 46 from
+// two, 50 from four).  NSUB divides NPR, so the threads fill disjoint slots.
+// Returns false if a wait gave up or a parameter block named a tensor map outside its table
+// (error bit set).
+template <int NS, bool PAIR, int RINGS = 1, bool A_MN = false, bool B_KM = false, int NPROD = 1>
 __device__ __forceinline__ bool fused_producer(const FusedParams& fp, uint8_t* slots, uint64_t* slot_full,
                                                uint64_t* slot_empty, int rank, int first, int stride,
-                                               volatile int* abort_flag) {
+                                               volatile int* abort_flag, int who = 0) {
   static_assert(RINGS == 1 || RINGS == 2, "one ring, or one per k half");
   constexpr int NPR = NS / RINGS;  // slots per ring
+  constexpr bool ALL_RINGS = NPROD < RINGS;  // a single thread loads both rings
+  constexpr int NSUB = ALL_RINGS ? 1 : NPROD / RINGS;
+  static_assert(ALL_RINGS ? NPROD == 1 : (NPROD % RINGS == 0 && NPR % NSUB == 0), "issuing threads per ring");
   const CommonParams& p = fp.c;
   constexpr int TN = PAIR ? 2 * kFusedBN : kFusedBN;
-  int slot[2] = {0, 0};
-  uint32_t sph[2] = {0, 0};
+  const int my_ring = RINGS == 2 ? (who & 1) : 0;
+  const uint32_t sub = static_cast<uint32_t>(ALL_RINGS ? 0 : (RINGS == 2 ? who >> 1 : who));
+  uint32_t cnt[2] = {0, 0};  // tiles of each ring so far
   bool ok = true;
   auto issue = [&](int ring, const CUtensorMap* map, int x, int y, int item, int kb) -> bool {
-    const int sidx = ring * NPR + slot[ring];
-    if (!mbar_wait(smem_u32(&slot_empty[sidx]), sph[ring] ^ 1u, p.timeout_ns, abort_flag)) {
+    if (!ALL_RINGS && ring != my_ring) return true;  // the other ring's threads load it
+    const uint32_t c = cnt[ring]++;
+    if (c % NSUB != sub) return true;  // another thread of this ring loads it
+    const int sidx = ring * NPR + static_cast<int>(c % NPR);
+    const uint32_t use = c / NPR;  // earlier fills of this slot
+    if (!mbar_wait(smem_u32(&slot_empty[sidx]), (use & 1u) ^ 1u, p.timeout_ns, abort_flag)) {
       record_wait_failure(p.err, kSiteProducerSlot, item, kb);
       return false;
     }
     const uint32_t fb = smem_u32(&slot_full[sidx]);
     mbar_arrive_expect_tx(fb, kSlotBytes);
     tma_load_2d(smem_u32(slots + sidx * kSlotBytes), map, fb, x, y);
-    if (++slot[ring] == NPR) {
-      slot[ring] = 0;
-      sph[ring] ^= 1u;
-    }
     return true;
   };
   for (int item = first; ok && item < p.num_items; item += stride) {
@@ -207,10 +222,11 @@ __global__ void __launch_bounds__(fused_threads<TW>(), 1) fmm_fused_kernel(const
 
   if (!run) {
     // nothing issued: fall through to the teardown
-  } else if (warp == 0) {
+  } else if (warp == 0 || (kFusedProducers > 1 && warp == 2)) {
     // ------------------------------------------------------------ producer
     if (lane == 0 &&
-        !fused_producer<NS, PAIR>(fp, slots, slot_full, slot_empty, rank, first, stride, abort_flag)) {
+        !fused_producer<NS, PAIR, 1, false, false, kFusedProducers>(fp, slots, slot_full, slot_empty, rank, first,
+                                                                    stride, abort_flag, warp >> 1)) {
       atomicOr(p.err, kErrProducerWait);
       *abort_flag = 1;
       drain_pause(2000000ull);

@@ -9,8 +9,9 @@
 // the A-sum writes (32 KB for split3) and the UMMAs' A reads (48 KB) from shared memory.
 //
 // CTA pairs (clusters of two CTAs) on 256 x 256 output tiles:
-//   warp 0      producer (fused_producer): one FP32 tile per source block and 32-deep k half
-//               into the half's ring of 16 KB slots;
+//   warps 0, 2  producers (fused_producer, lane 0 of each; warp 0 loads k half 0, warp 2 half
+//               1): one FP32 tile per source block and 32-deep k half into the half's ring of
+//               16 KB slots;
 //   warps 8-15  transform.  Warps 8-11 form k half 0 of every k-step, warps 12-15 half 1, each
 //               group reading the slots of its own ring (the producer loads half h into ring
 //               h).  Thread (lane quarter q = warp % 4, lane l) owns A row 32q + l: it adds that row of each A source slot with its
@@ -188,10 +189,10 @@ __global__ void __launch_bounds__(fused_threads<8>(), 1) fmm_fused_ts_kernel(con
 
   if (!run) {
     // nothing issued: fall through to the teardown
-  } else if (warp == 0) {
+  } else if (warp == 0 || (kFusedTsProducers > 1 && warp == 2)) {
     if (lane == 0 &&
-        !fused_producer<NS, true, 2, A_MN, B_KM>(fp, slots, slot_full, slot_empty, rank, first, stride,
-                                                abort_flag)) {
+        !fused_producer<NS, true, 2, A_MN, B_KM, kFusedTsProducers>(fp, slots, slot_full, slot_empty, rank, first,
+                                                                    stride, abort_flag, warp >> 1)) {
       atomicOr(p.err, kErrProducerWait);
       *abort_flag = 1;
       drain_pause(2000000ull);
