@@ -79,9 +79,12 @@ typedef enum fmm_algo {
     FMM_ALGO_PACKED = 1,
     /* Operand sums are formed on chip while tiles are loaded (Section 3.1):
      * TMA stages the W_A (W_B) source tiles, transform warps add them with
-     * their signs, round/split, and feed the tensor cores.  No workspace.
-     * Needs lda, ldb multiples of 4 (FP32) / 8 (16-bit) and 16-byte aligned
-     * A, B. */
+     * their signs, round/split, and feed the tensor cores.  No workspace,
+     * except for FP16 operands: the panel maxima of their operand sums, found
+     * by a pass over A and B that does not store the sums.  FP32 operands in
+     * both fused kernels; BF16 and FP16 operands in the tensor-memory kernel
+     * (CTA pairs), forward products, FP16 with Strassen's basis.  Needs lda,
+     * ldb multiples of 4 (FP32) / 8 (16-bit) and 16-byte aligned A, B. */
     FMM_ALGO_FUSED = 2,
     /* levels == 2 only: top-level sums materialised in FP32 in the workspace
      * (Section 3.4, hybrid), bottom level fused as in FMM_ALGO_FUSED. */

@@ -280,9 +280,6 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
   // top-level sums the hybrid scheme forms from FP32 or BF16 operands
   if (pl.algo == FMM_ALGO_HYBRID && (a_mn || !b_mn))
     return fail(FMM_ERR_UNSUPPORTED, "the hybrid algorithm is built for the forward product");
-  if (on_chip && pl.in_type != kInF32 && pl.algo != FMM_ALGO_HYBRID)
-    return fail(FMM_ERR_UNSUPPORTED,
-                "the fused algorithm takes FP32 A and B (split3 or plain_bf16); the hybrid also BF16 and FP16");
   pl.tile_n = (opt && opt->tile_n) ? opt->tile_n : 0;
   const int sched = opt ? opt->schedule : 0;
   if (sched < 0 || sched > 2) return fail(FMM_ERR_ARG, "schedule must be 0, 1 or 2");
@@ -336,6 +333,13 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
   if (on_chip && pl.scaled && (!pl.pair || fk == 1))
     return fail(FMM_ERR_UNSUPPORTED, "scaled FP16 products with on-chip sums run in the tensor-memory kernel");
   pl.fused_ts = on_chip && pl.pair && fk != 1;
+  // 16-bit operands: the hybrid scheme (FP32 top-level sums), or the tensor-memory kernel on
+  // the caller's BF16 / FP16 source tiles (forward products; FP16 panel scaling: Strassen)
+  if (pl.algo == FMM_ALGO_FUSED && pl.in_type != kInF32 &&
+      (!pl.fused_ts || a_mn || !b_mn || (pl.scaled && pl.basis != kBasisStrassen)))
+    return fail(FMM_ERR_UNSUPPORTED,
+                "the fused algorithm takes BF16 and FP16 operands in the tensor-memory kernel (CTA pairs, "
+                "forward products; FP16 with Strassen's basis)");
   // the backward products (A' stored by rows of k, or B' by rows of n) run on chip in the
   // tensor-memory kernel
   if (on_chip && (a_mn || !b_mn) && (!pl.fused_ts || (a_mn && !b_mn)))
@@ -379,7 +383,9 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
   pl.b_bytes = static_cast<size_t>(round_up(static_cast<int64_t>(pl.R) * b_rows * pl.ldb_w * 2, 256));
   const size_t arrays = pl.terms == 3 ? 2 : 1;
   pl.ws = (m == 0 || n == 0 || k == 0 || pl.algo == FMM_ALGO_FUSED) ? 0 : arrays * (pl.a_bytes + pl.b_bytes);
-  if (pl.scaled && pl.ws > 0) {
+  const bool fused_scaled = pl.algo == FMM_ALGO_FUSED && pl.scaled && m > 0 && n > 0 && k > 0;
+  if (pl.scaled && (pl.ws > 0 || fused_scaled)) {
+    // FP16: the panel maxima of the operand sums (the only workspace of a fused FP16 product)
     pl.panels_a = (pl.hm + kBM - 1) / kBM;
     pl.panels_b = (pl.hn + pl.tile_n - 1) / pl.tile_n;
     pl.scale_bytes = static_cast<size_t>(round_up(pl.R * (pl.panels_a + pl.panels_b) * 4, 256));
@@ -533,9 +539,17 @@ fmm_status fill_common(CommonParams& c, const Plan& pl, const std::vector<Produc
 }
 
 // Fused path: FP32 source tiles are summed on chip; no workspace.
+// 16-bit operands (forward products, tensor-memory kernel): the source tiles are the caller's
+// BF16 or FP16 values; an FP16 product first records the panel maxima of its operand sums in
+// `ws` (the only workspace it takes).
 fmm_status gemm_fused(const Plan& pl, int64_t m, int64_t n, int64_t k, float alpha, const void* A,
-                      int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc,
+                      int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, void* ws,
                       const DeviceInfo& dev, const fmm_options* opt, cudaStream_t s) {
+  const bool s16 = pl.in_type != kInF32;
+  const size_t esz = s16 ? 2 : 4;
+  const CUtensorMapDataType dtype = !s16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                         : (pl.in_type == kInF16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                                 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
   const std::vector<Product> prods = make_products(pl.L, pl.basis);
   // A blocks a = i * g_k + l (g_m x g_k grid), B blocks b = l * g_n + j (g_k x g_n grid)
   const int na_blk = pl.gm * pl.gk, nb_blk = pl.gk * pl.gn;
@@ -546,8 +560,8 @@ fmm_status gemm_fused(const Plan& pl, int64_t m, int64_t n, int64_t k, float alp
   fmm_status st = FMM_OK;
   std::vector<bool> a_live(na_blk, false), b_live(nb_blk, false);
   for (int b = 0; b < std::max(na_blk, nb_blk) && st == FMM_OK; ++b) {
-    const float* Af = static_cast<const float*>(A);
-    const float* Bf = static_cast<const float*>(B);
+    const uint8_t* Af = static_cast<const uint8_t*>(A);
+    const uint8_t* Bf = static_cast<const uint8_t*>(B);
     // A block b = (bi, bj): rows of m, columns of k
     const int bi = b / pl.gk, bj = b % pl.gk;
     const int64_t ar = b < na_blk ? block_extent(m, pl.hm, bi) : 0;
@@ -556,14 +570,16 @@ fmm_status gemm_fused(const Plan& pl, int64_t m, int64_t n, int64_t k, float alp
       // A' stored m x k (box 32 k x 128 rows, 128-byte swizzle), or by rows of k (a_mn: the
       // block (bi, bj) of A' is the source's block (bj, bi); box 128 m x 32 k)
       const cuuint64_t dims[2] = {static_cast<cuuint64_t>(pl.a_mn ? ar : ac), static_cast<cuuint64_t>(pl.a_mn ? ac : ar)};
-      const cuuint64_t strides[1] = {static_cast<cuuint64_t>(lda * 4)};
+      const cuuint64_t strides[1] = {static_cast<cuuint64_t>(lda * esz)};
       const cuuint32_t box[2] = {pl.a_mn ? 128u : 32u, pl.a_mn ? 32u : 128u};
       const cuuint32_t estr[2] = {1, 1};
-      const float* base = pl.a_mn ? Af + (bj * pl.hk * lda + bi * pl.hm) : Af + (bi * pl.hm * lda + bj * pl.hk);
-      CUresult cr = g_encode(&fp->tmSA[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims,
-                             strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                             pl.a_mn ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B,
-                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      const uint8_t* base = Af + esz * (pl.a_mn ? (bj * pl.hk * lda + bi * pl.hm) : (bi * pl.hm * lda + bj * pl.hk));
+      // rows of 32 FP32 values (128 bytes, 128-byte swizzle) or 32 16-bit values (64 bytes)
+      const CUtensorMapSwizzle swz = pl.a_mn ? CU_TENSOR_MAP_SWIZZLE_NONE
+                                             : (s16 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B);
+      CUresult cr = g_encode(&fp->tmSA[b], dtype, 2, const_cast<uint8_t*>(base), dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       if (cr != CUDA_SUCCESS) st = fail(FMM_ERR_CUDA, "cuTensorMapEncodeTiled (A block) failed");
       a_live[b] = true;
     }
@@ -576,13 +592,13 @@ fmm_status gemm_fused(const Plan& pl, int64_t m, int64_t n, int64_t k, float alp
       // the source's block (bn, bl); box 32 k x 128 n-rows, 128-byte swizzle)
       const bool kmaj = !pl.b_mn;
       const cuuint64_t dims[2] = {static_cast<cuuint64_t>(kmaj ? br : bc), static_cast<cuuint64_t>(kmaj ? bc : br)};
-      const cuuint64_t strides[1] = {static_cast<cuuint64_t>(ldb * 4)};
+      const cuuint64_t strides[1] = {static_cast<cuuint64_t>(ldb * esz)};
       const cuuint32_t box[2] = {kmaj ? 32u : static_cast<cuuint32_t>(kFusedTileN),
                                  kmaj ? static_cast<cuuint32_t>(kFusedTileN) : 32u};
       const cuuint32_t estr[2] = {1, 1};
-      const float* base = kmaj ? Bf + (bn * pl.hn * ldb + bl * pl.hk) : Bf + (bl * pl.hk * ldb + bn * pl.hn);
-      CUresult cr = g_encode(&fp->tmSB[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims,
-                             strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+      const uint8_t* base = Bf + esz * (kmaj ? (bn * pl.hn * ldb + bl * pl.hk) : (bl * pl.hk * ldb + bn * pl.hn));
+      CUresult cr = g_encode(&fp->tmSB[b], dtype, 2, const_cast<uint8_t*>(base), dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE,
                              kmaj ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       if (cr != CUDA_SUCCESS) st = fail(FMM_ERR_CUDA, "cuTensorMapEncodeTiled (B block) failed");
@@ -621,9 +637,60 @@ fmm_status gemm_fused(const Plan& pl, int64_t m, int64_t n, int64_t k, float alp
     return st;
   }
   cudaError_t e;
+  if (pl.scaled) {
+    // FP16: per (product, panel) the largest |operand sum|, one pass over each operand that
+    // forms the sums without storing them; the kernel's transform and epilogue read the row of
+    // the product's basis index
+    unsigned* maxbits = static_cast<unsigned*>(ws);
+    e = cudaMemsetAsync(maxbits, 0, pl.scale_bytes, s);
+    if (e != cudaSuccess) {
+      delete fp;
+      return cuda_fail(e, "clearing the panel maxima");
+    }
+    SumParams ma;
+    std::memset(&ma, 0, sizeof ma);
+    ma.X = A;
+    ma.ldx = lda;
+    ma.rows = m;
+    ma.cols = k;
+    ma.hr = pl.hm;
+    ma.hc = pl.hk;
+    ma.terms = 1;
+    ma.chunk = -1;
+    ma.vec_ok = 1;  // 16-byte aligned base and rows (validate_core)
+    ma.maxbits = maxbits;
+    ma.npanels = static_cast<int32_t>(pl.panels_a);
+    ma.panel_w = kBM;
+    ma.scale_rows = 1;
+    SumParams mb = ma;
+    mb.X = B;
+    mb.ldx = ldb;
+    mb.rows = k;
+    mb.cols = n;
+    mb.hr = pl.hk;
+    mb.hc = pl.hn;
+    mb.maxbits = maxbits + static_cast<int64_t>(pl.R) * pl.panels_a;
+    mb.npanels = static_cast<int32_t>(pl.panels_b);
+    mb.panel_w = pl.tile_n;
+    mb.scale_rows = 0;
+    {
+      PhaseScope ps(kPhasePack, s, 2);
+      e = launch_operand_maxima_f16(ma, pl.L, false, dev.sms, s);
+      if (e == cudaSuccess) e = launch_operand_maxima_f16(mb, pl.L, true, dev.sms, s);
+    }
+    if (e != cudaSuccess) {
+      delete fp;
+      return cuda_fail(e, "panel maxima of the operand sums");
+    }
+    fp->c.maxbits_a = ma.maxbits;
+    fp->c.maxbits_b = mb.maxbits;
+    fp->c.panels_a = static_cast<int32_t>(pl.panels_a);
+    fp->c.panels_b = static_cast<int32_t>(pl.panels_b);
+    for (size_t i = 0; i < live.size(); ++i) fp->c.prod[i].sum_index = static_cast<int32_t>(live[i]);
+  }
   {
     PhaseScope ps(kPhaseTensor, s);
-    e = pl.fused_ts ? launch_fused_ts(*fp, pl.terms, pl.a_mn, pl.b_mn, pl.scaled, grid, s)
+    e = pl.fused_ts ? launch_fused_ts(*fp, pl.terms, pl.a_mn, pl.b_mn, pl.scaled, s16, grid, s)
                     : launch_fused(*fp, pl.terms, kFusedTransformWarps, pl.pair, grid, s);
   }
   delete fp;
@@ -778,7 +845,7 @@ fmm_status gemm_hybrid(const Plan& pl, int64_t m, int64_t n, int64_t k, float al
   }
   {
     PhaseScope ps(kPhaseTensor, s);
-    e = pl.fused_ts ? launch_fused_ts(*fp, pl.terms, pl.a_mn, pl.b_mn, pl.scaled, grid, s)
+    e = pl.fused_ts ? launch_fused_ts(*fp, pl.terms, pl.a_mn, pl.b_mn, pl.scaled, false, grid, s)
                     : launch_fused(*fp, pl.terms, kFusedTransformWarps, pl.pair, grid, s);
   }
   delete fp;
@@ -826,8 +893,10 @@ fmm_status validate_core(const Plan& pl, int64_t m, int64_t n, int64_t k, Operan
   }
   if (pl.algo == FMM_ALGO_FUSED && k > 0 &&
       (reinterpret_cast<uintptr_t>(a.X) % 16 != 0 || reinterpret_cast<uintptr_t>(b.X) % 16 != 0 ||
-       a.ld % 4 != 0 || b.ld % 4 != 0))
-    return fail(FMM_ERR_ALIGN, "the fused algorithm needs 16-byte aligned A and B and lda, ldb multiples of 4");
+       (a.ld * elem_bytes(a.type)) % 16 != 0 || (b.ld * elem_bytes(b.type)) % 16 != 0))
+    return fail(FMM_ERR_ALIGN,
+                "the fused algorithm needs 16-byte aligned A and B and rows of a multiple of 16 bytes "
+                "(lda, ldb multiples of 4 for FP32, of 8 for 16-bit operands)");
   return FMM_OK;
 }
 
@@ -1276,7 +1345,7 @@ fmm_status gemm_core(const Plan& pl, int64_t m, int64_t n, int64_t k, float alph
       if (e != cudaSuccess) return cuda_fail(e, "beta pass");
     }
     if (k == 0 || alpha == 0.0f) return FMM_OK;
-    if (pl.algo == FMM_ALGO_FUSED) return gemm_fused(pl, m, n, k, alpha, a.X, a.ld, b.X, b.ld, C, ldc, dev, opt, s);
+    if (pl.algo == FMM_ALGO_FUSED) return gemm_fused(pl, m, n, k, alpha, a.X, a.ld, b.X, b.ld, C, ldc, ws, dev, opt, s);
     return gemm_hybrid(pl, m, n, k, alpha, a.X, a.ld, b.X, b.ld, C, ldc, ws, dev, opt, s);
   }
 

@@ -83,7 +83,9 @@ __device__ __forceinline__ void split2(float x0, float x1, uint32_t& hi, uint32_
 // two, 50 from four).  NSUB divides NPR, so the threads fill disjoint slots.
 // Returns false if a wait gave up or a parameter block named a tensor map outside its table
 // (error bit set).
-template <int NS, bool PAIR, int RINGS = 1, bool A_MN = false, bool B_KM = false, int NPROD = 1>
+// TILE_BYTES: bytes of one source tile (FP32 tiles fill a 16 KB slot, 16-bit tiles half of it).
+template <int NS, bool PAIR, int RINGS = 1, bool A_MN = false, bool B_KM = false, int NPROD = 1,
+          uint32_t TILE_BYTES = kSlotBytes>
 __device__ __forceinline__ bool fused_producer(const FusedParams& fp, uint8_t* slots, uint64_t* slot_full,
                                                uint64_t* slot_empty, int rank, int first, int stride,
                                                volatile int* abort_flag, int who = 0) {
@@ -109,7 +111,7 @@ __device__ __forceinline__ bool fused_producer(const FusedParams& fp, uint8_t* s
       return false;
     }
     const uint32_t fb = smem_u32(&slot_full[sidx]);
-    mbar_arrive_expect_tx(fb, kSlotBytes);
+    mbar_arrive_expect_tx(fb, TILE_BYTES);
     tma_load_2d(smem_u32(slots + sidx * kSlotBytes), map, fb, x, y);
     return true;
   };

@@ -7,11 +7,11 @@
 
 namespace fmm {
 
-template <int TERMS, bool A_MN, bool B_KM, bool F16 = false>
+template <int TERMS, bool A_MN, bool B_KM, bool F16 = false, bool S16 = false>
 static cudaError_t launch_fused_ts_t(const FusedParams& p, int grid, cudaStream_t s) {
   using Cfg = FusedTsCfg<TERMS>;
   static_assert(Cfg::kSmemBytes <= 232448, "shared memory per CTA");
-  auto kern = fmm_fused_ts_kernel<TERMS, A_MN, B_KM, F16>;
+  auto kern = fmm_fused_ts_kernel<TERMS, A_MN, B_KM, F16, S16>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(Cfg::kSmemBytes));
   if (e != cudaSuccess) return e;
@@ -38,12 +38,18 @@ static cudaError_t launch_fused_ts_t(const FusedParams& p, int grid, cudaStream_
   return cudaLaunchKernelEx(&cfg, kern, p);
 }
 
-cudaError_t launch_fused_ts(const FusedParams& p, int terms, bool a_mn, bool b_mn, bool f16, int grid,
+cudaError_t launch_fused_ts(const FusedParams& p, int terms, bool a_mn, bool b_mn, bool f16, bool s16, int grid,
                             cudaStream_t s) {
   // forward (A K-major, B MN-major), dA = dC B^T (B stored by rows of n), dB = A^T dC (A
-  // stored by rows of k); FP16 operands with panel scaling: forward only
-  if (f16) return (terms == 1 && !a_mn && b_mn) ? launch_fused_ts_t<1, false, false, true>(p, grid, s)
-                                                : cudaErrorInvalidValue;
+  // stored by rows of k); FP16 operands with panel scaling, and 16-bit source tiles: forward
+  // only
+  const bool fwd = !a_mn && b_mn;
+  if (s16) {
+    if (terms != 1 || !fwd) return cudaErrorInvalidValue;
+    return f16 ? launch_fused_ts_t<1, false, false, true, true>(p, grid, s)
+               : launch_fused_ts_t<1, false, false, false, true>(p, grid, s);
+  }
+  if (f16) return (terms == 1 && fwd) ? launch_fused_ts_t<1, false, false, true>(p, grid, s) : cudaErrorInvalidValue;
   if (!a_mn && b_mn) {
     if (terms == 3) return launch_fused_ts_t<3, false, false>(p, grid, s);
     if (terms == 1) return launch_fused_ts_t<1, false, false>(p, grid, s);

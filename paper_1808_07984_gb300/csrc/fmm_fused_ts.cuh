@@ -29,6 +29,9 @@
 // B_KM -- the B operand is stored with n rows of k (its source tile is 128 n-rows x 32 k,
 // 128-byte swizzle, loaded like an A tile); thread tb owns n-row tb, adds its row like an A row
 // and writes the B-operand tile K-major (128-byte swizzle) for a K-major UMMA descriptor.
+// S16 (forward products, one term): the source blocks are the caller's BF16 (or, with F16, FP16)
+// operands; a tile of 128 rows x 32 k (64-byte swizzle) or 32 k-rows x 128 n takes half a slot,
+// and the transform converts each value to FP32 (exactly) before adding it.
 // F16 (one term): FP16 operands with power-of-two scaling -- each product's A-operand sums of
 // this CTA's 128-row panel and B-operand sums of the tile's columns are multiplied by 2^-s
 // (the panel maxima, p.maxbits_a / maxbits_b, were found by a pass before this kernel) before
@@ -127,9 +130,24 @@ __device__ __forceinline__ bool mma_role_ts(const CommonParams& p, uint8_t* smem
   return true;
 }
 
-template <int TERMS, bool A_MN = false, bool B_KM = false, bool F16 = false>
+// Two 16-bit values of a 32-bit word (the lower address in the low half) as floats: BF16, or FP16
+// when F16.  Both conversions are exact.
+template <bool F16>
+__device__ __forceinline__ void unpack16(uint32_t w, float& lo, float& hi) {
+  if (F16) {
+    const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w));
+    lo = f.x;
+    hi = f.y;
+  } else {
+    lo = __uint_as_float(w << 16);
+    hi = __uint_as_float(w & 0xFFFF0000u);
+  }
+}
+
+template <int TERMS, bool A_MN = false, bool B_KM = false, bool F16 = false, bool S16 = false>
 __global__ void __launch_bounds__(fused_threads<8>(), 1) fmm_fused_ts_kernel(const __grid_constant__ FusedParams fp) {
   static_assert(!F16 || TERMS == 1, "FP16 operands: one term");
+  static_assert(!S16 || (TERMS == 1 && !A_MN && !B_KM), "16-bit source tiles: forward products, one term");
   using Cfg = FusedTsCfg<TERMS>;
   constexpr int S = Cfg::kStages;
   constexpr int NS = Cfg::kSlots;
@@ -191,8 +209,8 @@ __global__ void __launch_bounds__(fused_threads<8>(), 1) fmm_fused_ts_kernel(con
     // nothing issued: fall through to the teardown
   } else if (warp == 0 || (kFusedTsProducers > 1 && warp == 2)) {
     if (lane == 0 &&
-        !fused_producer<NS, true, 2, A_MN, B_KM, kFusedTsProducers>(fp, slots, slot_full, slot_empty, rank, first,
-                                                                    stride, abort_flag, warp >> 1)) {
+        !fused_producer<NS, true, 2, A_MN, B_KM, kFusedTsProducers, S16 ? kSlotBytes / 2 : kSlotBytes>(
+            fp, slots, slot_full, slot_empty, rank, first, stride, abort_flag, warp >> 1)) {
       atomicOr(p.err, kErrProducerWait);
       *abort_flag = 1;
       drain_pause(2000000ull);
@@ -238,8 +256,9 @@ __global__ void __launch_bounds__(fused_threads<8>(), 1) fmm_fused_ts_kernel(con
       int sh_a = 0, sh_b = 0;
       if (F16) {
         const int tm_cta = 2 * tm + rank;
-        if (tm_cta < p.panels_a) sh_a = panel_shift(p.maxbits_a[r * p.panels_a + tm_cta]);
-        sh_b = panel_shift(p.maxbits_b[r * p.panels_b + tn]);
+        const int z = p.prod[r].sum_index;  // the product's row of panel maxima
+        if (tm_cta < p.panels_a) sh_a = panel_shift(p.maxbits_a[z * p.panels_a + tm_cta]);
+        sh_b = panel_shift(p.maxbits_b[z * p.panels_b + tn]);
       }
       for (int kb = 0; ok && kb < p.nk; ++kb) {
         float aA[32];
@@ -261,7 +280,22 @@ __global__ void __launch_bounds__(fused_threads<8>(), 1) fmm_fused_ts_kernel(con
           const uint8_t* sl = slots + sidx * kSlotBytes;
           if (w < na) {
             const float sg = ((a_neg >> w) & 1u) ? -1.f : 1.f;
-            if (A_MN) {
+            if (S16) {
+              // 128 rows x 32 k of 16-bit values, 64-byte rows, 64-byte swizzle: 16-byte chunk
+              // c of the row sits at chunk c ^ ((row >> 1) & 3)
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                const uint4 x = *reinterpret_cast<const uint4*>(sl + arow * 64 + ((c ^ ((arow >> 1) & 3)) << 4));
+                const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                  float lo, hi;
+                  unpack16<F16>(w[j], lo, hi);
+                  aA[8 * c + 2 * j] = fmaf(sg, lo, aA[8 * c + 2 * j]);
+                  aA[8 * c + 2 * j + 1] = fmaf(sg, hi, aA[8 * c + 2 * j + 1]);
+                }
+              }
+            } else if (A_MN) {
               // 32 k-rows x 128 m: this row's k-values are one column of the tile
 #pragma unroll
               for (int kk = 0; kk < 32; ++kk)
@@ -287,6 +321,19 @@ __global__ void __launch_bounds__(fused_threads<8>(), 1) fmm_fused_ts_kernel(con
                 aB[c][1] = fmaf(sg, x.y, aB[c][1]);
                 aB[c][2] = fmaf(sg, x.z, aB[c][2]);
                 aB[c][3] = fmaf(sg, x.w, aB[c][3]);
+              }
+            } else if (S16) {
+              // 32 k-rows x 128 n of 16-bit values, 256-byte rows, unswizzled
+#pragma unroll
+              for (int v = 0; v < 8; ++v) {
+                const uint2 x = *reinterpret_cast<const uint2*>(sl + (bk0 + 4 * v) * 256 + nq * 8);
+                float b0, b1, b2, b3;
+                unpack16<F16>(x.x, b0, b1);
+                unpack16<F16>(x.y, b2, b3);
+                aB[v][0] = fmaf(sg, b0, aB[v][0]);
+                aB[v][1] = fmaf(sg, b1, aB[v][1]);
+                aB[v][2] = fmaf(sg, b2, aB[v][2]);
+                aB[v][3] = fmaf(sg, b3, aB[v][3]);
               }
             } else {
 #pragma unroll

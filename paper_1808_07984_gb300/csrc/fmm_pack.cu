@@ -514,6 +514,12 @@ cudaError_t launch_operand_maxima(const SumParams& p, bool is_b, int num_sms, cu
               : launch_sums_t<float, 1, 1, false, false, 1, 1>(p, num_sms, s);
 }
 
+cudaError_t launch_operand_maxima_f16(const SumParams& p, int levels, bool is_b, int num_sms, cudaStream_t s) {
+  // SCALE 1: only the panel maxima (maxbits zeroed by the caller)
+  return is_b ? launch_sums_l<__half, 1, true, false, 1, 1>(p, levels, num_sms, s)
+              : launch_sums_l<__half, 1, false, false, 1, 1>(p, levels, num_sms, s);
+}
+
 cudaError_t launch_beta(float* C, int64_t m, int64_t n, int64_t ldc, float beta, int num_sms,
                         cudaStream_t s) {
   const int64_t total = m * n;

@@ -21,6 +21,9 @@ cudaError_t launch_operand_sums(const SumParams& p, int levels, bool is_b, bool 
 // panel_w rows, B: of panel_w columns) into p.maxbits, without storing the sums: the scale
 // pass of the hybrid scheme's FP16 bottom level.
 cudaError_t launch_operand_maxima(const SumParams& p, bool is_b, int num_sms, cudaStream_t s);
+// Panel maxima of the 7^levels operand sums of an FP16 operand (forward layout), without
+// storing the sums: the scale pass of FP16 products whose sums are formed on chip.
+cudaError_t launch_operand_maxima_f16(const SumParams& p, int levels, bool is_b, int num_sms, cudaStream_t s);
 // Operand sums of every product of a basis table (see TableSumParams) for one operand.
 cudaError_t launch_table_sums(const TableSumParams& tp, int in_type, int out16, int num_sms, cudaStream_t s);
 cudaError_t launch_beta(float* C, int64_t m, int64_t n, int64_t ldc, float beta, int num_sms,
@@ -52,8 +55,10 @@ cudaError_t launch_fused(const FusedParams& p, int terms, int transform_warps, b
 // The same products in CTA pairs with the A-operand sums held in tensor memory
 // (fmm_fused_ts.cuh); terms in {1, 3}.  a_mn: A' stored by rows of k; b_mn: B' stored by
 // rows of k (false: by rows of n).  Built: (a_mn, b_mn) = (0, 1), (0, 0), (1, 1).  f16: FP16
-// UMMAs on panel-scaled sums (terms 1, forward; p.c.maxbits_a / maxbits_b set).
-cudaError_t launch_fused_ts(const FusedParams& p, int terms, bool a_mn, bool b_mn, bool f16, int grid,
+// UMMAs on panel-scaled sums (terms 1, forward; p.c.maxbits_a / maxbits_b set).  s16: the
+// source maps are 16-bit (BF16, or FP16 with f16; A box 32 x 128 with 64-byte swizzle, B box
+// 128 x 32; terms 1, forward).
+cudaError_t launch_fused_ts(const FusedParams& p, int terms, bool a_mn, bool b_mn, bool f16, bool s16, int grid,
                             cudaStream_t s);
 
 }  // namespace fmm

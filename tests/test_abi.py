@@ -117,12 +117,12 @@ def test_oracle_is_not_linked_by_the_library():
     assert b"oracle_gemm" not in data
 
 
-def _call_ex(lib, levels=1, algo=0, **opt):
+def _call_ex(lib, levels=1, algo=0, variant=0, **opt):
     o = fmm._Options()
     for key, v in opt.items():
         setattr(o, key, v)
     o.algo = algo
-    return lib.fmm_gemm_ex(16, 16, 16, 1.0, 0x10000, 16, 0x20000, 16, 0.0, 0x30000, 16, levels, 0,
+    return lib.fmm_gemm_ex(16, 16, 16, 1.0, 0x10000, 16, 0x20000, 16, 0.0, 0x30000, 16, levels, variant,
                            0x100000, 1 << 30, None, ctypes.byref(o))
 
 
@@ -150,6 +150,11 @@ def test_option_errors_need_no_gpu(lib):
     assert _call_ex(lib, fused_kernel=-1) == 1
     assert _call_ex(lib, store_first=3) == 1
     assert _call_ex(lib, algo=2, cta_pair=1, fused_kernel=2) == 3  # tensor-memory kernel: CTA pairs
+    # 16-bit operands on chip: tensor-memory kernel (CTA pairs); FP16 scaling: Strassen's basis
+    assert _call_ex(lib, algo=2, variant=1, cta_pair=1) == 3
+    assert _call_ex(lib, algo=2, variant=1, fused_kernel=1) == 3
+    assert _call_ex(lib, algo=2, variant=2, basis=2) == 3
+    assert _call_ex(lib, algo=2, variant=2, basis=1) == 3
 
 
 def test_options_struct_matches_the_header():
@@ -233,3 +238,16 @@ def test_store_first_phases_are_a_valid_order(lib, levels, basis, want):
     if want is not None:
         assert [int(np.count_nonzero(phase == p)) for p in range(nph)] == want
     assert lib.fmm_store_phases(0, 0, phase.ctypes.data, store.ctypes.data) == -1
+
+
+def test_fused_workspace_is_the_fp16_panel_maxima(lib):
+    """The fused algorithm stores no operand sums: no workspace for FP32 and BF16 operands, and
+    for FP16 operands only the panel maxima of the operand sums (7^L products x (128-row panels
+    of A + 256-column panels of B) x 4 bytes, rounded up to 256)."""
+    assert fmm.workspace_size(1024, 1024, 1024, 1, "split3", algo="fused") == 0
+    assert fmm.workspace_size(1024, 1024, 1024, 1, "bf16", algo="fused") == 0
+    for levels, R in ((1, 7), (2, 49)):
+        h = 1024 >> levels
+        panels = -(-h // 128) + -(-h // 256)
+        want = -(-(R * panels * 4) // 256) * 256
+        assert fmm.workspace_size(1024, 1024, 1024, levels, "f16", algo="fused") == want

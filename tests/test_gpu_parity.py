@@ -761,6 +761,81 @@ def test_hybrid_odd_30001_29999_4097_sampled_rows():
     assert oracle.normwise_error(C, C64, An, Bn) <= tolerance("split3", 2, 4097)
 
 
+# ------------------------------------------------------ fused, 16-bit operands
+@pytest.mark.parametrize("variant", ["bf16", "f16"])
+@pytest.mark.parametrize("levels", [1, 2])
+@pytest.mark.parametrize("m,n,k", [(16, 16, 16), (304, 520, 200), (136, 264, 72), (1000, 1200, 304)])
+def test_fused_16bit_operands_int_bit_exact(variant, levels, m, n, k):
+    """BF16 and FP16 operands with every operand sum formed on chip from the caller's 16-bit
+    tiles (tensor-memory kernel, no stored sums; FP16 scaled per panel by the power of two the
+    maxima pass found): small integers equal the FP64 oracle exactly, ragged tiles included."""
+    C, C64, _, _ = run(m, n, k, levels, variant, dist="int", seed=7 * m + n + 3 * k + levels, algo="fused")
+    np.testing.assert_array_equal(C, C64)
+
+
+@pytest.mark.parametrize("variant", ["bf16", "f16"])
+@pytest.mark.parametrize("levels", [1, 2])
+def test_fused_16bit_operands_float(variant, levels):
+    C, C64, An, Bn = run(640, 384, 768, levels, variant, dist="gaussian", seed=40 + levels, algo="fused")
+    assert oracle.normwise_error(C, C64, An, Bn) <= tolerance(variant, levels, 768)
+
+
+def test_fused_f16_badly_scaled_and_large_values():
+    """Badly scaled FP16 inputs stay finite and within the FP16 bound; inputs near 2^15, whose
+    sums exceed FP16's range unscaled, do not overflow."""
+    C, C64, An, Bn = run(512, 512, 512, 1, "f16", dist="badly_scaled", seed=43, algo="fused")
+    assert np.all(np.isfinite(C))
+    assert oracle.normwise_error(C, C64, An, Bn) <= tolerance("f16", 1, 512)
+    A = (synth.uniform((256, 256), 84) * 30000.0).astype(np.float32)
+    B = (synth.uniform((256, 256), 85) * 30000.0).astype(np.float32)
+    Ad = torch.from_numpy(A).half().cuda()
+    Bd = torch.from_numpy(B).half().cuda()
+    C = fmm.gemm(Ad, Bd, levels=1, variant="f16", algo="fused")
+    fmm.device_status()
+    Ab = Ad.cpu().view(torch.int16).numpy().view(np.uint16)
+    Bb = Bd.cpu().view(torch.int16).numpy().view(np.uint16)
+    C64 = oracle.classical(Ab, Bb, a_code=oracle.ORC_F16, b_code=oracle.ORC_F16)
+    Cn = C.cpu().numpy()
+    assert np.all(np.isfinite(Cn))
+    err = oracle.normwise_error(Cn, C64, float(Ad.float().norm()), float(Bd.float().norm()))
+    assert err <= tolerance("f16", 1, 256), err
+
+
+def test_fused_bf16_operands_other_bases_bit_exact():
+    for basis in ("winograd", "b323"):
+        C, C64, _, _ = run(312, 264, 200, 1, "bf16", dist="int", seed=44, algo="fused", basis=basis)
+        np.testing.assert_array_equal(C, C64)
+
+
+@pytest.mark.parametrize("variant,levels", [("bf16", 1), ("f16", 2)])
+def test_fused_16bit_full_size_sampled_rows(variant, levels):
+    rows = np.unique(np.concatenate([[0, 8191], synth.rng(23).integers(0, 8192, size=4)]))
+    C, C64, An, Bn = run(8192, 8192, 8192, levels, variant, seed=45, rows=rows, algo="fused")
+    assert oracle.normwise_error(C, C64, An, Bn) <= tolerance(variant, levels, 8192)
+
+
+def test_fused_16bit_operands_refusals():
+    """16-bit operands on chip: forward products in the tensor-memory kernel (CTA pairs) with
+    rows of a multiple of 16 bytes; FP16 scaling with Strassen's basis only."""
+    A = torch.zeros((64, 64), device="cuda", dtype=torch.bfloat16)
+    B = torch.zeros((64, 64), device="cuda", dtype=torch.bfloat16)
+    for kw in ({"cta_pair": False}, {"fused_kernel": "smem"}):
+        with pytest.raises(fmm.FmmError) as ei:
+            fmm.gemm(A, B, levels=1, variant="bf16", algo="fused", **kw)
+        assert ei.value.status == 3
+    with pytest.raises(fmm.FmmError) as ei:
+        fmm.gemm(A.half(), B.half(), levels=1, variant="f16", algo="fused", basis="b323")
+    assert ei.value.status == 3
+    with pytest.raises(fmm.FmmError) as ei:
+        fmm.gemm_backward(A, B, torch.zeros((64, 64), device="cuda"), levels=1, variant="bf16", algo="fused")
+    assert ei.value.status == 3
+    Au = torch.zeros((64, 68), device="cuda", dtype=torch.bfloat16)
+    Bu = torch.zeros((68, 64), device="cuda", dtype=torch.bfloat16)
+    with pytest.raises(fmm.FmmError) as ei:
+        fmm.gemm(Au, Bu, levels=1, variant="bf16", algo="fused")
+    assert ei.value.status == 2
+
+
 # ------------------------------------------- large odd sizes with dynamic fringes
 @pytest.mark.parametrize("variant,levels", [("split3", 2), ("plain_bf16", 2), ("split3", 0)])
 def test_odd_30001_29999_4097_sampled_rows(variant, levels):
