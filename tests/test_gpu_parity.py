@@ -764,11 +764,13 @@ def test_hybrid_odd_30001_29999_4097_sampled_rows():
 # ------------------------------------------------------ fused, 16-bit operands
 @pytest.mark.parametrize("variant", ["bf16", "f16"])
 @pytest.mark.parametrize("levels", [1, 2])
-@pytest.mark.parametrize("m,n,k", [(16, 16, 16), (304, 520, 200), (136, 264, 72), (1000, 1200, 304)])
+@pytest.mark.parametrize("m,n,k", [(8, 24, 16), (16, 16, 16), (304, 520, 200), (136, 264, 72), (1000, 1200, 304)])
 def test_fused_16bit_operands_int_bit_exact(variant, levels, m, n, k):
     """BF16 and FP16 operands with every operand sum formed on chip from the caller's 16-bit
     tiles (tensor-memory kernel, no stored sums; FP16 scaled per panel by the power of two the
-    maxima pass found): small integers equal the FP64 oracle exactly, ragged tiles included."""
+    maxima pass found): small integers equal the FP64 oracle exactly, ragged tiles included, and
+    shapes so small that some blocks lie wholly outside the matrices (their products are dropped
+    and the remaining ones keep their rows of panel maxima)."""
     C, C64, _, _ = run(m, n, k, levels, variant, dist="int", seed=7 * m + n + 3 * k + levels, algo="fused")
     np.testing.assert_array_equal(C, C64)
 
