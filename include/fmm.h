@@ -130,8 +130,12 @@ typedef struct fmm_options {
                           (pair), which applies the C updates of all 7^L products in a fixed
                           order, each item's after the previous item's have completed; results
                           are bitwise reproducible (tile-rounds schedule, one tile per CTA
-                          pair per round).  0 = updates from different CTAs may land in any
-                          order (default) */
+                          pair per round).  0 = automatic: the ownership order for one-level
+                          products of 7 products with beta = 0, h_k <= 512, 16-byte aligned C
+                          rows and every other option at its default (there it is faster: the
+                          first update of each C block stores it and the later ones find the
+                          block in L2); otherwise updates from different CTAs may land in any
+                          order */
     int outer_scaling; /* 1 = outside power-of-two scaling (packed, forward product): every row
                           of A and column of B is scaled by 2^-e so that its largest magnitude
                           lies in [1, 2) before the operand sums are formed, and C is scaled

@@ -963,9 +963,28 @@ std::vector<std::vector<int>> plan_store_phases(CommonParams& c) {
 }
 
 // batched = true: the job joins a batched launch, which never pipelines.
-fmm_status prepare_packed(const Plan& pl, int64_t m, int64_t n, int64_t k, float alpha, Operand a,
+fmm_status prepare_packed(const Plan& plan, int64_t m, int64_t n, int64_t k, float alpha, Operand a,
                           Operand b, float beta, float* C, int64_t ldc, void* ws, const DeviceInfo& dev,
                           const fmm_options* opt, PackedJob& job, bool batched = false) {
+  Plan pl = plan;
+  // Automatic ownership order (measured on GB300, split3, m = n = 16384): with beta = 0 and
+  // short one-level products (h_k <= 512) each tile position's seven products run in order on
+  // one worker, so the first product to update a C block stores it and the later updates find
+  // the block in L2 (k = 512: 303 against 258 effective TFLOPS with launch phases; k = 1024:
+  // 506 against 467).  From h_k = 768 on, and at two levels (49 products per tile position,
+  // padded rounds), the launch phases are faster.  Only with the options' defaults and C rows
+  // that TMA addresses; the results are then bitwise reproducible as well.
+  const int sf_opt = opt ? opt->store_first : 0;
+  const int pipe_opt = opt ? opt->pipeline : 0;
+  const int det_opt = opt ? opt->deterministic : 0;
+  const int sched_opt = opt ? opt->schedule : 0;
+  const int rt_opt = opt ? opt->round_tiles : 0;
+  if (!batched && !pl.deterministic && det_opt == 0 && sf_opt == 0 && pipe_opt == 0 && sched_opt == 0 &&
+      rt_opt == 0 && beta == 0.0f && pl.algo == FMM_ALGO_PACKED && pl.L == 1 && pl.R == 7 && pl.hk <= 512 &&
+      !pl.outer_scaling && reinterpret_cast<uintptr_t>(C) % 16 == 0 && ldc % 4 == 0) {
+    pl.deterministic = true;
+    pl.schedule = kSchedTileRounds;
+  }
   job.pl = pl;
   job.m = m; job.n = n; job.k = k; job.ldc = ldc;
   job.alpha = alpha; job.beta = beta; job.C = C;

@@ -488,6 +488,24 @@ def test_deterministic_results_are_bitwise_reproducible(opts):
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
 
 
+def test_short_one_level_products_run_in_ownership_order_by_default():
+    """beta = 0, one level, h_k <= 512 (here k = 1000, h_k = 504) with the default options: the
+    library runs each tile position's products in order on one worker, so the float result is
+    bitwise the ownership mode's (and reproducible), bit-exact on integers, and within the
+    bound; k = 2000 (h_k = 1000) keeps the launch phases, which still meet the bound."""
+    m, n = 1800, 2000
+    outs = [run(m, n, 1000, 1, "split3", seed=71)[0] for _ in range(3)]
+    owned = run(m, n, 1000, 1, "split3", seed=71, deterministic=True)[0]
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    assert np.array_equal(outs[0], owned)
+    C, C64, An, Bn = run(m, n, 1000, 1, "split3", seed=71)
+    assert oracle.normwise_error(C, C64, An, Bn) <= tolerance("split3", 1, 1000)
+    C, C64, _, _ = run(m, n, 1000, 1, "split3", dist="int", seed=72, c_fill=float("nan"))
+    np.testing.assert_array_equal(C, C64)
+    C, C64, An, Bn = run(m, n, 2000, 1, "split3", seed=73)
+    assert oracle.normwise_error(C, C64, An, Bn) <= tolerance("split3", 1, 2000)
+
+
 @pytest.mark.parametrize("levels", [0, 1, 2])
 @pytest.mark.parametrize("m,n,k,pads", [(300, 520, 200, (0, 0, 0)), (129, 257, 65, (0, 0, 1)),
                                         (1000, 1200, 300, (0, 0, 0))])
