@@ -50,6 +50,8 @@ def parse_args():
     ap.add_argument("--tile-n", type=int, default=0)
     ap.add_argument("--schedule", choices=["auto", "product", "rounds"], default="auto",
                     help="work order of the packed tensor-core kernel (product-major or tile rounds)")
+    ap.add_argument("--round-tiles", type=int, default=0,
+                    help="tile-rounds schedule: output tiles per round (0 = automatic)")
     ap.add_argument("--err-rows", type=int, default=16)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -129,6 +131,7 @@ def config_dict(a, k, extra=None):
         "variant": a.variant,
         "algo": a.algo,
         "schedule": getattr(a, "schedule", "auto"),
+        "round_tiles": getattr(a, "round_tiles", 0),
         "inputs": "A, B float32 uniform[-1,1] seeded (synthetic); row-major; alpha=1, beta=0",
         "l2": "inputs larger than L2 (no flush between steps)",
         "comparator": "same library, levels=0, same arithmetic",
@@ -556,7 +559,7 @@ def main():
     def step(levels, algo=None, fused_kernel="auto"):
         fmm.gemm(A_d, B_d, C_d, 1.0, 0.0, levels=levels, variant=a.variant, algo=algo or a.algo,
                  tile_n=0 if algo else a.tile_n, workspace=ws, stream=stream, fused_kernel=fused_kernel,
-                 schedule="auto" if algo else a.schedule)
+                 schedule="auto" if algo else a.schedule, round_tiles=0 if algo else a.round_tiles)
 
     def barrier():
         if dist is not None:
@@ -671,7 +674,8 @@ def main():
                 if ev_free[b] is not None:
                     stream.wait_event(ev_free[b])
                 fmm.gemm(Ab, Bb, Cb, 1.0, 0.0, levels=a.levels, variant=a.variant, algo=a.algo,
-                         tile_n=a.tile_n, workspace=ws, stream=stream, schedule=a.schedule)
+                         tile_n=a.tile_n, workspace=ws, stream=stream, schedule=a.schedule,
+                         round_tiles=a.round_tiles)
                 ev_done[b] = torch.cuda.Event()
                 ev_done[b].record(stream)
                 with torch.cuda.stream(s_out):
@@ -744,7 +748,8 @@ def main():
     peak, sustained, peak_src = tensor_peak(peaks)
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
-                "traffic": recorded_traffic(workload_name(a, k)) if a.schedule == "auto" else None,
+                "traffic": (recorded_traffic(workload_name(a, k))
+                            if a.schedule == "auto" and a.round_tiles == 0 else None),
                 "frac_of_sustained_peak": (achieved / sustained) if sustained else None,
                 "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                 "peak_source": peak_src + " of measured; timed region " +
