@@ -963,7 +963,8 @@ def test_badly_scaled_two_level():
 
 
 # -------------------------------------------------- full size, sampled rows
-@pytest.mark.parametrize("n,k,levels", [(16384, 16384, 2), (16384, 512, 2), (8192, 8192, 1)])
+@pytest.mark.parametrize("n,k,levels", [(16384, 16384, 2), (16384, 512, 2), (8192, 8192, 1), (16384, 512, 1),
+                                         (16384, 1024, 1), (16384, 2048, 1)])
 def test_full_size_sampled_rows(n, k, levels):
     m = n
     rows = np.unique(synth.rng(123).integers(0, m, size=12))
@@ -973,14 +974,16 @@ def test_full_size_sampled_rows(n, k, levels):
 
 
 @pytest.mark.parametrize("m,n,k,levels", [(16384, 16384, 16384, 2), (30001, 29999, 4097, 2),
-                                          (30001, 29999, 4097, 1)])
+                                          (30001, 29999, 4097, 1), (16384, 16384, 512, 1),
+                                          (16384, 16384, 2048, 1)])
 def test_full_size_int_sampled_rows_bit_exact(m, n, k, levels):
     """Small integers at the benchmark's sizes: every operand sum, product and partial sum is an
     integer far below 2**24, so each sampled element must equal the FP64 oracle exactly.  This
     reaches the full-size paths: 76 CTA pairs, three stages, 64-deep k-steps by the hundred,
     tile rounds; at 30001 x 29999 x 4097 the tight leading dimensions (odd lda, ldb, ldc) take
     the unaligned-operand sum pass and the element-wise write-back, and the last block row and
-    column are zero-padded fringes."""
+    column are zero-padded fringes; the rank-512 update runs in the ownership order, the
+    rank-2048 one in store-first launch phases."""
     rows = np.unique(np.concatenate([[0, m - 1], synth.rng(m + k).integers(0, m, size=6)]))
     C, C64, _, _ = run(m, n, k, levels, "split3", dist="int", seed=k + levels, rows=rows)
     np.testing.assert_array_equal(C, C64)
