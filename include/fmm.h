@@ -131,7 +131,7 @@ typedef struct fmm_options {
                           order, each item's after the previous item's have completed; results
                           are bitwise reproducible (tile-rounds schedule, one tile per CTA
                           pair per round).  0 = automatic: the ownership order for one-level
-                          products of 7 products with beta = 0, h_k <= 512, 16-byte aligned C
+                          Strassen products with beta = 0, h_k <= 512, 16-byte aligned C
                           rows and every other option at its default (there it is faster: the
                           first update of each C block stores it and the later ones find the
                           block in L2); otherwise updates from different CTAs may land in any

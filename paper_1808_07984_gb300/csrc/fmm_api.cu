@@ -972,15 +972,18 @@ fmm_status prepare_packed(const Plan& plan, int64_t m, int64_t n, int64_t k, flo
   // one worker, so the first product to update a C block stores it and the later updates find
   // the block in L2 (k = 512: 303 against 258 effective TFLOPS with launch phases; k = 1024:
   // 506 against 467).  From h_k = 768 on, and at two levels (49 products per tile position,
-  // padded rounds), the launch phases are faster.  Only with the options' defaults and C rows
-  // that TMA addresses; the results are then bitwise reproducible as well.
+  // padded rounds), the launch phases are faster; with the Winograd form (two C updates per
+  // product) already at h_k = 512 (8192^2 x 1024: 383 against 411).  Strassen's basis only,
+  // the options at their defaults and C rows that TMA addresses; the results are then
+  // bitwise reproducible as well.
   const int sf_opt = opt ? opt->store_first : 0;
   const int pipe_opt = opt ? opt->pipeline : 0;
   const int det_opt = opt ? opt->deterministic : 0;
   const int sched_opt = opt ? opt->schedule : 0;
   const int rt_opt = opt ? opt->round_tiles : 0;
   if (!batched && !pl.deterministic && det_opt == 0 && sf_opt == 0 && pipe_opt == 0 && sched_opt == 0 &&
-      rt_opt == 0 && beta == 0.0f && pl.algo == FMM_ALGO_PACKED && pl.L == 1 && pl.R == 7 && pl.hk <= 512 &&
+      rt_opt == 0 && beta == 0.0f && pl.algo == FMM_ALGO_PACKED && pl.L == 1 && pl.basis == kBasisStrassen &&
+      pl.hk <= 512 &&
       !pl.outer_scaling && reinterpret_cast<uintptr_t>(C) % 16 == 0 && ldc % 4 == 0) {
     pl.deterministic = true;
     pl.schedule = kSchedTileRounds;
