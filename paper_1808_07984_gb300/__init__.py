@@ -244,19 +244,27 @@ def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
     # a classical product of 16-bit operands that TMA can read in place needs no workspace
     in_place = (int(levels) == 0 and v in (VARIANTS["bf16"], VARIANTS["f16"]) and algo in ("auto", "packed")
                 and not outer_scaling
-                and all(X.data_ptr() % 16 == 0 and max(X.stride(0), 1) % 8 == 0 for X in (A, B)))
+                and all(X.data_ptr() % 16 == 0 and _ld(X) % 8 == 0 for X in (A, B)))
     if workspace is None and ws_need > 0 and not in_place:
         workspace = torch.empty(ws_need, dtype=torch.uint8, device=A.device)
     ws_ptr = workspace.data_ptr() if workspace is not None else None
     ws_bytes = workspace.numel() if workspace is not None else 0
     o = _opts(algo, tile_n, num_ctas, schedule, bk, cta_pair, round_tiles, pipeline, fringe, basis,
               deterministic, outer_scaling, fused_kernel, store_first)
-    st = load().fmm_gemm_ex(m, n, k, float(alpha), A.data_ptr(), max(A.stride(0), 1),
-                            B.data_ptr(), max(B.stride(0), 1), float(beta), C.data_ptr(),
-                            max(C.stride(0), 1), int(levels), v, ws_ptr, ws_bytes,
+    st = load().fmm_gemm_ex(m, n, k, float(alpha), A.data_ptr(), _ld(A),
+                            B.data_ptr(), _ld(B), float(beta), C.data_ptr(),
+                            _ld(C), int(levels), v, ws_ptr, ws_bytes,
                             _stream_handle(stream), ctypes.byref(o))
     _check(st)
     return C
+
+
+def _ld(X) -> int:
+    """Row stride of a row-major 2-D tensor in elements; for a tensor without elements (whose
+    stride torch leaves at 0 or 1) the row length, which the C ABI's checks expect."""
+    if X.numel() == 0:
+        return max(int(X.shape[1]) if X.dim() == 2 else 1, 1)
+    return max(X.stride(0), 1)
 
 
 def choose(m: int, n: int, k: int, variant="split3"):
@@ -306,8 +314,8 @@ def gemm_backward(A, B, dC, levels: int = 1, variant="split3", need_dA=True, nee
     if workspace is None and ws_need > 0:
         workspace = torch.empty(ws_need, dtype=torch.uint8, device=A.device)
     st = load().fmm_gemm_backward_ex(
-        m, n, k, A.data_ptr(), max(A.stride(0), 1), B.data_ptr(), max(B.stride(0), 1),
-        dC.data_ptr(), max(dC.stride(0), 1),
+        m, n, k, A.data_ptr(), _ld(A), B.data_ptr(), _ld(B),
+        dC.data_ptr(), _ld(dC),
         dA.data_ptr() if dA is not None else None, max(k, 1),
         dB.data_ptr() if dB is not None else None, max(n, 1),
         int(levels), v, workspace.data_ptr() if workspace is not None else None,
@@ -443,9 +451,9 @@ class BatchedPlan:
         self._A = VP(*[a.data_ptr() for a in As])
         self._B = VP(*[b.data_ptr() for b in Bs])
         self._C = VP(*[c.data_ptr() for c in Cs])
-        self._lda = I64(*[max(a.stride(0), 1) for a in As])
-        self._ldb = I64(*[max(b.stride(0), 1) for b in Bs])
-        self._ldc = I64(*[max(c.stride(0), 1) for c in Cs])
+        self._lda = I64(*[_ld(a) for a in As])
+        self._ldb = I64(*[_ld(b) for b in Bs])
+        self._ldc = I64(*[_ld(c) for c in Cs])
         self._tune = tune if isinstance(tune, TuneTable) else (tune_table(tune) if tune is not None
                                                                else _default_tune(self.variant))
         ws = L.fmm_batched_workspace_size(cnt, self._m, self._n, self._k, self.variant,

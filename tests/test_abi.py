@@ -109,6 +109,9 @@ def test_argument_errors_need_no_gpu(lib):
     assert _call(lib, ws=0x100010) == 2                  # workspace misaligned
     assert b"workspace" in lib.fmm_last_error() or b"aligned" in lib.fmm_last_error()
     assert _call(lib, m=0) == 0                          # empty problem: no-op
+    # block sizes beyond the 32-bit tile coordinates are refused on the host
+    assert _call(lib, m=1 << 33, ldc=16) == 1
+    assert _call(lib, n=1 << 33, ldb=1 << 33, ldc=1 << 33) == 1
 
 
 def test_oracle_is_not_linked_by_the_library():

@@ -779,6 +779,32 @@ def test_hybrid_odd_30001_29999_4097_sampled_rows():
     assert oracle.normwise_error(C, C64, An, Bn) <= tolerance("split3", 2, 4097)
 
 
+# ------------------------------------------------------ degenerate problems
+@pytest.mark.parametrize("levels,algo", [(0, "auto"), (1, "auto"), (2, "auto"), (1, "fused"), (2, "hybrid")])
+def test_degenerate_shapes(levels, algo):
+    """k = 0 scales C by beta; alpha = 0 likewise (no product is formed); m = 0 or n = 0 leaves
+    C untouched; 1 x 1 x 1 and 1 x 9 x 1 products (all but one block empty at every level) are
+    exact."""
+    C0 = synth.uniform((40, 48), 81)
+    for (m, n, k, alpha, beta) in [(40, 48, 0, 1.0, 0.5), (40, 48, 32, 0.0, 2.0)]:
+        A = torch.from_numpy(synth.uniform((m, max(k, 1)), 82)[:, :k].copy()).cuda()
+        B = torch.from_numpy(synth.uniform((max(k, 1), n), 83)[:k].copy()).cuda()
+        Cd = torch.from_numpy(C0.copy()).cuda()
+        fmm.gemm(A, B, Cd, alpha=alpha, beta=beta, levels=levels, algo=algo)
+        fmm.device_status()
+        np.testing.assert_array_equal(Cd.cpu().numpy(), (np.float32(beta) * C0).astype(np.float32))
+    for (m, n) in [(0, 48), (40, 0)]:
+        Cd = torch.full((max(m, 1), max(n, 1)), 7.0, device="cuda")[:m, :n]
+        fmm.gemm(torch.zeros((m, 32), device="cuda"), torch.zeros((32, n), device="cuda"), Cd, levels=levels,
+                 algo=algo)
+        fmm.device_status()
+    for (m, n, k) in [(1, 1, 1), (1, 9, 1), (8, 8, 8)]:
+        # the fused kernels need rows of a multiple of 16 bytes: pad the leading dimensions
+        pads = ((-k) % 4, (-n) % 4, 0) if algo == "fused" else (0, 0, 0)
+        C, C64, _, _ = run(m, n, k, levels, "split3", dist="int", seed=84 + m + n, algo=algo, pads=pads)
+        np.testing.assert_array_equal(C, C64)
+
+
 # ------------------------------------------------------ fused, 16-bit operands
 @pytest.mark.parametrize("variant", ["bf16", "f16"])
 @pytest.mark.parametrize("levels", [1, 2])
