@@ -124,8 +124,12 @@ typedef struct fmm_options {
                         2 = a <3,2,3> basis of rank 15 (levels <= 1, packed or fused; A split into
                         3 x 2 blocks, B into 2 x 3, C into 3 x 3; 15 products instead of the
                         classical 18, so 5/6 of the classical MMA work against Strassen's 7/8;
-                        no pipelining).  Bases other than 0 form their operand sums in one
-                        table-driven pass per operand. */
+                        no pipelining); 3 = the <2,3,2> basis of rank 11 (levels <= 1, packed
+                        or fused; A split into 2 x 3 blocks, B into 3 x 2, C into 2 x 2:
+                        Strassen's seven products on the first two block columns of A and block
+                        rows of B plus the four block products of the third, 11/12 of the
+                        classical MMA work; no pipelining).  Bases other than 0 form their
+                        operand sums in one table-driven pass per operand. */
     int deterministic; /* 1 = ownership mode: each output tile position belongs to one CTA
                           (pair), which applies the C updates of all 7^L products in a fixed
                           order, each item's after the previous item's have completed; results

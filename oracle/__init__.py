@@ -15,7 +15,8 @@ with A (m x k), B (k x n), C (m x n), row-major.  Two routes are provided:
   "winograd"`` applies the Strassen-Winograd variant's seven products instead
   (Section 6 names it among the algorithms the primitive can carry).
 * ``table_matmul`` -- FP64 one-level product by any basis table <g_m, g_k, g_n; R>
-  (the <3,2,3> scheme of rank 15 below, or the 2x2 tables), same fringe rule.
+  (the <3,2,3> scheme of rank 15 and the <2,3,2> scheme of rank 11 below, or the
+  2x2 tables), same fringe rule.
 
 Supporting definitions: the 2x2 coefficient matrices U, V, W of Eq. (3), their
 Kronecker powers for multi-level Strassen (Section 3.4), the Brent-equation
@@ -169,8 +170,36 @@ B323_W = np.array([
     [0,  -1,  1,  0,  0,  0, -1,  0,  0, -1,  0,  0,  0,  0,  0],   # C(2,2)
 ], dtype=np.int64)
 
+# ---------------------------------------------------------------------------
+# A <2,3,2; 11> basis: A split into 2 x 3 blocks, B into 3 x 2, C into 2 x 2
+# (same block numbering).  C = A(:, 0:2) B(0:2, :) + A(:, 2) B(2, :): the seven
+# products of Eq. (3) on the first part -- whose quadrant q = 2*row + col is
+# block row*3 + col of A and row*2 + col of B and of C -- then the four block
+# products A(i,2) B(2,j) added into C(i,j).  Eleven products where the classical
+# scheme needs twelve.
+# ---------------------------------------------------------------------------
+def _b232_tables():
+    U = np.zeros((6, 11), dtype=np.int64)
+    V = np.zeros((6, 11), dtype=np.int64)
+    W = np.zeros((4, 11), dtype=np.int64)
+    for q in range(4):
+        row, col = divmod(q, 2)
+        U[row * 3 + col, :7] = STRASSEN_U[q]
+        V[row * 2 + col, :7] = STRASSEN_V[q]
+        W[row * 2 + col, :7] = STRASSEN_W[q]
+    for i in range(2):
+        for j in range(2):
+            r = 7 + 2 * i + j
+            U[i * 3 + 2, r] = 1
+            V[2 * 2 + j, r] = 1
+            W[i * 2 + j, r] = 1
+    return U, V, W
+
+
+B232_U, B232_V, B232_W = _b232_tables()
+
 # block grid (g_m, g_k, g_n) of each one-level basis
-BASIS_DIMS = {"strassen": (2, 2, 2), "winograd": (2, 2, 2), "b323": (3, 2, 3)}
+BASIS_DIMS = {"strassen": (2, 2, 2), "winograd": (2, 2, 2), "b323": (3, 2, 3), "b232": (2, 3, 2)}
 
 
 def basis_tables(basis: str = "strassen"):

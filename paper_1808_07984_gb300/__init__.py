@@ -139,7 +139,7 @@ SCHEDULES = {"auto": 0, "product": 1, "rounds": 2}
 
 
 FRINGES = {"pad": 0, "peel": 1}
-BASES = {"strassen": 0, "winograd": 1, "b323": 2}
+BASES = {"strassen": 0, "winograd": 1, "b323": 2, "b232": 3}
 
 
 FUSED_KERNELS = {"auto": 0, "smem": 1, "tmem": 2}
@@ -206,8 +206,9 @@ def gemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, levels: int = 1,
     ``pipeline``: None = automatic, True / False = overlap the operand-sum passes with the
     tensor-core kernel one top-level product at a time, or not.  ``fringe``: "pad" (zero
     padding of the blocks) or "peel" (Strassen on the evenly splitting core plus classical
-    strip products).  ``basis``: "strassen", "winograd" (one level) or "b323"
-    (the <3,2,3> basis of rank 15, one level, packed or fused algorithm).  ``deterministic``:
+    strip products).  ``basis``: "strassen", "winograd" (one level), "b323" (the <3,2,3>
+    basis of rank 15) or "b232" (the <2,3,2> basis of rank 11), the last two one level, packed
+    or fused algorithm.  ``deterministic``:
     ownership mode, bitwise reproducible results.  ``outer_scaling``: exact power-of-two
     scaling of the rows of A and columns of B around the product (badly scaled inputs).
     ``fused_kernel`` (fused and hybrid algorithms): "auto", "smem" (both operands' sums in shared

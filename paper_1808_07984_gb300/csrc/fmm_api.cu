@@ -167,6 +167,26 @@ std::vector<Product> make_products(int L, int basis = kBasisStrassen) {
     }
     return out;
   }
+  if (basis == kBasis232 && L == 1) {
+    // A blocks a = i*3 + l, B blocks b = l*2 + j, C blocks c = i*2 + j; Strassen's quadrant
+    // q = 2*row + col of the leading 2 x 2 x 2 part maps to those numbers
+    std::vector<Product> out(11);
+    for (int r = 0; r < 7; ++r)
+      for (int q = 0; q < 4; ++q) {
+        const int row = q / 2, col = q % 2;
+        if (const int u = strassen_u(r, q)) out[r].a.push_back({row * 3 + col, u});
+        if (const int v = strassen_v(r, q)) out[r].b.push_back({row * 2 + col, v});
+        if (const int w = strassen_w(r, q)) out[r].c.push_back({row * 2 + col, w});
+      }
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j) {
+        Product& pr = out[7 + 2 * i + j];
+        pr.a.push_back({i * 3 + 2, 1});
+        pr.b.push_back({2 * 2 + j, 1});
+        pr.c.push_back({i * 2 + j, 1});
+      }
+    return out;
+  }
   const int R = ipow(7, L), Q = ipow(4, L), g = 1 << L;
   std::vector<Product> out(R);
   for (int r = 0; r < R; ++r) {
@@ -212,6 +232,10 @@ bool basis_shape(int levels, int basis, BasisShape& out) {
     out = {3, 2, 3, 15};
     return true;
   }
+  if (basis == kBasis232 && levels == 1) {
+    out = {2, 3, 2, 11};
+    return true;
+  }
   return false;
 }
 
@@ -236,7 +260,7 @@ struct Plan {
   bool pair = false;  // packed kernel in CTA pairs: 256-row tiles shared by two CTAs
   bool fused_ts = false;  // fused kernel with the A-operand sums in tensor memory
   int pipeline_mode = 0;  // fmm_options.pipeline: 0 automatic, 1 off, 2 on
-  int basis = kBasisStrassen;  // coefficient tables (Strassen, Strassen-Winograd or <3,2,3>)
+  int basis = kBasisStrassen;  // coefficient tables (Strassen, Strassen-Winograd, <3,2,3> or <2,3,2>)
   int gm = 1, gk = 1, gn = 1;  // block grid of A (gm x gk), B (gk x gn) and C (gm x gn)
   bool deterministic = false;  // ownership mode (fixed order of the C updates)
   bool outer_scaling = false;  // power-of-two row (A) / column (B) scaling around the product
@@ -284,15 +308,16 @@ fmm_status make_plan(int64_t m, int64_t n, int64_t k, int levels, int variant, c
   const int sched = opt ? opt->schedule : 0;
   if (sched < 0 || sched > 2) return fail(FMM_ERR_ARG, "schedule must be 0, 1 or 2");
   const int basis = opt ? opt->basis : 0;
-  if (basis < kBasisStrassen || basis > kBasis323) return fail(FMM_ERR_ARG, "basis must be 0, 1 or 2");
+  if (basis < kBasisStrassen || basis > kBasis232) return fail(FMM_ERR_ARG, "basis must be 0, 1, 2 or 3");
   if (basis == kBasisWinograd && (levels > 1 || pl.algo == FMM_ALGO_HYBRID))
     return fail(FMM_ERR_UNSUPPORTED, "the Winograd basis is built for one level (packed or fused)");
-  if (basis == kBasis323 && levels > 1)
-    return fail(FMM_ERR_UNSUPPORTED, "the <3,2,3> basis is built for one level");
-  if (basis == kBasis323 && levels == 1 && pl.algo == FMM_ALGO_HYBRID)
+  const bool table_basis = basis == kBasis323 || basis == kBasis232;
+  if (table_basis && levels > 1)
+    return fail(FMM_ERR_UNSUPPORTED, "the <3,2,3> and <2,3,2> bases are built for one level");
+  if (table_basis && levels == 1 && pl.algo == FMM_ALGO_HYBRID)
     return fail(FMM_ERR_UNSUPPORTED, "the hybrid algorithm is a two-level Strassen scheme");
-  if (basis == kBasis323 && levels == 1 && opt && opt->pipeline == 2)
-    return fail(FMM_ERR_UNSUPPORTED, "the <3,2,3> basis forms its sums in one pass (no pipelining)");
+  if (table_basis && levels == 1 && opt && opt->pipeline == 2)
+    return fail(FMM_ERR_UNSUPPORTED, "the <3,2,3> and <2,3,2> bases form their sums in one pass (no pipelining)");
   pl.basis = levels == 0 ? kBasisStrassen : basis;
   BasisShape shape;
   if (!basis_shape(levels, pl.basis, shape)) return fail(FMM_ERR_UNSUPPORTED, "basis and levels not built");

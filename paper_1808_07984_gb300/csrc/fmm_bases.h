@@ -14,6 +14,12 @@ namespace fmm {
 
 // fmm_options.basis values beyond kBasisStrassen (0) and kBasisWinograd (1)
 constexpr int kBasis323 = 2;
+// <2,3,2; 11>: A split into 2 x 3 blocks, B into 3 x 2, C into 2 x 2; eleven products where
+// the classical scheme needs twelve (the least possible for this shape).  Products 0..6 are
+// Strassen's Eq. 3 on the first two block columns of A and block rows of B; products 7..10
+// add the outer product A(:, 2) B(2, :) block by block: M_{7 + 2i + j} = A(i,2) B(2,j) into
+// C(i,j).  Built from the Strassen tables in make_products (no separate table).
+constexpr int kBasis232 = 3;
 
 constexpr int kMaxTableBlocks = 9;  // source blocks of one operand in a table pass
 constexpr int kMaxTableRank = 32;   // products of one table pass

@@ -62,7 +62,8 @@ DEFAULT = {"pack_eff": 1.000, "tc_eff": 1.212, "wb_cost_ns_per_kb": 14.98, "t_it
 
 _TERMS = {"split3": 3, "plain_bf16": 1, "bf16": 1, "f16": 1}
 # one-level bases: block grid (g_m, g_k, g_n), products R and nonzeros of W (C updates)
-BASES = {"strassen": (2, 2, 2, 7, 12), "winograd": (2, 2, 2, 7, 14), "b323": (3, 2, 3, 15, 30)}
+BASES = {"strassen": (2, 2, 2, 7, 12), "winograd": (2, 2, 2, 7, 14), "b323": (3, 2, 3, 15, 30),
+         "b232": (2, 3, 2, 11, 16)}
 _IN_BYTES = {"split3": 4, "plain_bf16": 4, "bf16": 2, "f16": 2}
 _ARRAYS = {"split3": 2, "plain_bf16": 1, "bf16": 1, "f16": 1}
 
@@ -97,7 +98,7 @@ def auto_tile_n(m: int, n: int, levels: int, basis: str = "strassen") -> int:
 
 # products per launch phase of the store-first write-back (the library's fmm_store_phases)
 _PHASES = {(1, "strassen"): (1, 4, 2), (2, "strassen"): (1, 12, 24, 12), (1, "winograd"): (1, 6),
-           (1, "b323"): (5, 7, 3)}
+           (1, "b323"): (5, 7, 3), (1, "b232"): (3, 8)}
 
 
 def predict(m: int, n: int, k: int, levels: int, variant: str = "split3", tile_n: int = 0,

@@ -136,7 +136,7 @@ def test_option_errors_need_no_gpu(lib):
     assert _call_ex(lib, schedule=5) == 1
     assert _call_ex(lib, bk=48) == 1
     assert _call_ex(lib, pipeline=3) == 1
-    assert _call_ex(lib, basis=3) == 1
+    assert _call_ex(lib, basis=4) == 1
     assert _call_ex(lib, basis=-1) == 1
     assert _call_ex(lib, deterministic=2) == 1
     assert _call_ex(lib, outer_scaling=2) == 1
@@ -196,6 +196,25 @@ def test_library_b323_tables_match_oracle_and_brent(lib):
     assert int(np.count_nonzero(W, axis=0).max()) <= 4
 
 
+def test_library_b232_tables_match_oracle_and_brent(lib):
+    assert fmm.basis_shape(1, "b232") == (2, 3, 2, 11)
+    with pytest.raises(fmm.FmmError):
+        fmm.basis_shape(2, "b232")
+    U, V, W = fmm.product_table(1, "b232")
+    OU, OV, OW = oracle.BASES["b232"]
+    np.testing.assert_array_equal(U, OU)
+    np.testing.assert_array_equal(V, OV)
+    np.testing.assert_array_equal(W, OW)
+    for i, l, l2, j, i2, j2 in np.ndindex(2, 3, 3, 2, 2, 2):
+        got = int(np.sum(U[i * 3 + l].astype(np.int64) * V[l2 * 2 + j] * W[i2 * 2 + j2]))
+        assert got == (1 if (l == l2 and i == i2 and j == j2) else 0)
+    # refused combinations (host checks, no GPU)
+    assert _call_ex(lib, levels=2, basis=3) == 3
+    assert _call_ex(lib, levels=1, basis=3, pipeline=2) == 3
+    assert _call_ex(lib, algo=3, levels=2, basis=3) == 3
+    assert _call_ex(lib, basis=4) == 1
+
+
 def test_b323_workspace_sizes(lib):
     # 15 products of (h_m x h_k) A sums and (h_k x h_n) B sums, BF16 hi and lo
     m = n = k = 3000
@@ -206,7 +225,8 @@ def test_b323_workspace_sizes(lib):
     assert fmm.workspace_size(m, n, k, 1, "plain_bf16", basis="b323") == a + b
 
 
-@pytest.mark.parametrize("levels,basis,want", [(1, 0, [1, 4, 2]), (2, 0, [1, 12, 24, 12]), (1, 1, None), (1, 2, None)])
+@pytest.mark.parametrize("levels,basis,want", [(1, 0, [1, 4, 2]), (2, 0, [1, 12, 24, 12]), (1, 1, None), (1, 2, None),
+                                               (1, 3, None)])
 def test_store_first_phases_are_a_valid_order(lib, levels, basis, want):
     """Host-side plan of the store-first launch phases (no GPU): every C block that some
     product updates is stored by exactly one product, that product runs in a strictly earlier

@@ -67,14 +67,15 @@ def test_backward_winograd_int_bit_exact(m, n, k):
     np.testing.assert_array_equal(dB.cpu().numpy(), oracle.classical(np.ascontiguousarray(A.T), dC))
 
 
+@pytest.mark.parametrize("basis", ["b323", "b232"])
 @pytest.mark.parametrize("m,n,k", [(300, 200, 136), (129, 65, 257), (600, 610, 250)])
-def test_backward_b323_int_bit_exact(m, n, k):
+def test_backward_table_basis_int_bit_exact(m, n, k, basis):
     """dA = dC B^T and dB = A^T dC as <3,2,3> products: the table pass reads the stored
     operand blocks transposed."""
     A, B = synth.problem(m, n, k, 21 + m, "int")
     dC = synth.small_int((m, n), 22 + n)
     dA, dB = fmm.gemm_backward(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(),
-                               torch.from_numpy(dC).cuda(), levels=1, basis="b323")
+                               torch.from_numpy(dC).cuda(), levels=1, basis=basis)
     fmm.device_status()
     np.testing.assert_array_equal(dA.cpu().numpy(), oracle.classical(dC, np.ascontiguousarray(B.T)))
     np.testing.assert_array_equal(dB.cpu().numpy(), oracle.classical(np.ascontiguousarray(A.T), dC))

@@ -344,106 +344,119 @@ def test_classical_beta_nonzero_still_adds():
     assert oracle.normwise_error(C, C64, An, Bn) <= tolerance("split3", 0, 256)
 
 
-# ------------------------------------------------ the <3,2,3> basis of rank 15 (Section 6)
+# ------------- the <3,2,3> basis of rank 15 and the <2,3,2> basis of rank 11 (Section 6)
+@pytest.mark.parametrize("basis", ["b323", "b232"])
 @pytest.mark.parametrize("opts", [{}, {"pads": (0, 0, 1)}, {"cta_pair": False}, {"fringe": "peel"},
                                   {"deterministic": True}, {"round_tiles": 1}, {"tile_n": 128},
                                   {"tile_n": 256}, {"outer_scaling": True}, {"schedule": "product"}])
 @pytest.mark.parametrize("m,n,k", [(300, 520, 200), (129, 257, 65), (1000, 1200, 300), (1, 300, 1),
                                    (7, 5, 3), (1800, 776, 130)])
-def test_b323_basis_bit_exact(m, n, k, opts):
-    """Fifteen products over 3 x 2 blocks of A and 2 x 3 of B, each added into its (at most
-    three) 3 x 3 blocks of C: exact on small integers through every packed option."""
+def test_table_basis_bit_exact(m, n, k, opts, basis):
+    """<3,2,3>: fifteen products over 3 x 2 blocks of A and 2 x 3 of B, each added into its (at
+    most three) 3 x 3 blocks of C; <2,3,2>: eleven products over 2 x 3 blocks of A and 3 x 2 of
+    B into 2 x 2 blocks of C: exact on small integers through every packed option."""
     o = dict(opts)
     pads = o.pop("pads", (0, 0, 0))
-    C, C64, _, _ = run(m, n, k, 1, "split3", dist="int", seed=47 * m + k, basis="b323", pads=pads, **o)
+    C, C64, _, _ = run(m, n, k, 1, "split3", dist="int", seed=47 * m + k, basis=basis, pads=pads, **o)
     np.testing.assert_array_equal(C, C64)
 
 
+@pytest.mark.parametrize("basis", ["b323", "b232"])
 @pytest.mark.parametrize("variant", ["split3", "plain_bf16", "bf16", "f16"])
 @pytest.mark.parametrize("m,n,k", [(600, 520, 400), (771, 1030, 515)])
-def test_b323_basis_float(variant, m, n, k):
-    C, C64, An, Bn = run(m, n, k, 1, variant, seed=49, basis="b323")
+def test_table_basis_float(variant, m, n, k, basis):
+    C, C64, An, Bn = run(m, n, k, 1, variant, seed=49, basis=basis)
     assert oracle.normwise_error(C, C64, An, Bn) <= tolerance(variant, 1, k)
 
 
+@pytest.mark.parametrize("basis", ["b323", "b232"])
 @pytest.mark.parametrize("variant", ["split3", "f16"])
-def test_b323_basis_alpha_beta(variant):
-    C, C64, An, Bn = run(700, 900, 350, 1, variant, seed=51, alpha=-1.5, beta=0.75, basis="b323")
+def test_table_basis_alpha_beta(variant, basis):
+    C, C64, An, Bn = run(700, 900, 350, 1, variant, seed=51, alpha=-1.5, beta=0.75, basis=basis)
     assert oracle.normwise_error(C, C64, An, Bn) <= tolerance(variant, 1, 350)
 
 
-def test_b323_basis_matches_the_oracle_table_product():
-    """The library's fifteen products against the oracle's restatement of the same table
+@pytest.mark.parametrize("basis", ["b323", "b232"])
+def test_table_basis_matches_the_oracle_table_product(basis):
+    """The library's products against the oracle's restatement of the same table
     (FP64), on values whose sums and products are exact in every precision involved."""
     m, n, k = 240, 330, 160
     A, B = synth.problem(m, n, k, 53, "int")
     Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
-    C = fmm.gemm(Ad, Bd, levels=1, basis="b323")
+    C = fmm.gemm(Ad, Bd, levels=1, basis=basis)
     fmm.device_status()
-    np.testing.assert_array_equal(C.cpu().numpy(), oracle.table_matmul(A, B, basis="b323"))
+    np.testing.assert_array_equal(C.cpu().numpy(), oracle.table_matmul(A, B, basis=basis))
 
 
-def test_b323_basis_sampled_rows_4096():
+@pytest.mark.parametrize("basis", ["b323", "b232"])
+def test_table_basis_sampled_rows_4096(basis):
     rows = np.array([0, 1, 1365, 1366, 1367, 2730, 2731, 4095])  # first rows of each third
-    C, C64, An, Bn = run(4096, 4096, 4096, 1, "split3", seed=55, rows=rows, basis="b323")
+    C, C64, An, Bn = run(4096, 4096, 4096, 1, "split3", seed=55, rows=rows, basis=basis)
     assert oracle.normwise_error(C, C64, An, Bn) <= tolerance("split3", 1, 4096)
 
 
-def test_b323_deterministic_bitwise_reproducible():
+@pytest.mark.parametrize("basis", ["b323", "b232"])
+def test_table_basis_deterministic_bitwise_reproducible(basis):
     m, n, k = 1900, 1700, 1100
-    outs = [run(m, n, k, 1, "split3", seed=75, deterministic=True, basis="b323")[0] for _ in range(3)]
+    outs = [run(m, n, k, 1, "split3", seed=75, deterministic=True, basis=basis)[0] for _ in range(3)]
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
 
 
-def test_b323_outer_scaling_keeps_badly_scaled_rows_accurate():
-    """The <3,2,3> sums combine up to four blocks: without outside scaling badly scaled rows
+@pytest.mark.parametrize("basis", ["b323", "b232"])
+def test_table_basis_outer_scaling_keeps_badly_scaled_rows_accurate(basis):
+    """The <3,2,3> sums combine up to four blocks (the <2,3,2> ones up to two): without outside scaling badly scaled rows
     and columns lose accuracy as with Strassen; with it every element keeps FP32-level accuracy
     against its own scale."""
     m = n = k = 600
     A, B = synth.problem(m, n, k, 77, "badly_scaled")
     Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
     C64 = oracle.classical(A, B)
-    scaled = fmm.gemm(Ad, Bd, levels=1, basis="b323", outer_scaling=True).cpu().numpy().astype(np.float64)
+    scaled = fmm.gemm(Ad, Bd, levels=1, basis=basis, outer_scaling=True).cpu().numpy().astype(np.float64)
     fmm.device_status()
     assert _componentwise(scaled, C64, A, B) <= 1e-5
 
 
-def test_b323_f16_large_magnitudes_panel_scaled():
+@pytest.mark.parametrize("basis", ["b323", "b232"])
+def test_table_basis_f16_large_magnitudes_panel_scaled(basis):
     """FP16 operands near the top of the range: four-term sums would overflow FP16 unscaled;
     the per-panel power-of-two scaling keeps them exact on these integers."""
     m, n, k = 384, 390, 256
     A = (synth.small_int((m, k), 7) * 8000.0).astype(np.float32)
     B = (synth.small_int((k, n), 8) * 0.5).astype(np.float32)
     C = fmm.gemm(torch.from_numpy(A).half().cuda(), torch.from_numpy(B).half().cuda(), levels=1,
-                 variant="f16", basis="b323")
+                 variant="f16", basis=basis)
     fmm.device_status()
     np.testing.assert_array_equal(C.cpu().numpy(), oracle.classical(A, B))
 
 
-def test_b323_basis_rejected_where_not_built():
+def test_table_bases_rejected_where_not_built():
     A = torch.zeros((64, 64), device="cuda")
-    with pytest.raises(fmm.FmmError):
-        fmm.gemm(A, A, levels=2, basis="b323")
-    with pytest.raises(fmm.FmmError):
-        fmm.gemm(A, A, levels=2, basis="b323", algo="hybrid")
+    for basis in ("b323", "b232"):
+        with pytest.raises(fmm.FmmError):
+            fmm.gemm(A, A, levels=2, basis=basis)
+        with pytest.raises(fmm.FmmError):
+            fmm.gemm(A, A, levels=2, basis=basis, algo="hybrid")
 
 
+@pytest.mark.parametrize("basis", ["b323", "b232"])
 @pytest.mark.parametrize("opts", [{}, {"cta_pair": False}, {"deterministic": True}, {"pads": (0, 0, 1)}])
 @pytest.mark.parametrize("m,n,k", [(300, 520, 200), (129, 257, 65), (1000, 1200, 300), (7, 5, 3)])
-def test_b323_fused_bit_exact(m, n, k, opts):
-    """The <3,2,3> basis with its operand sums formed on chip (fused kernel): up to four FP32
-    source tiles per operand, fifteen products, destinations in the 3 x 3 C grid."""
+def test_table_basis_fused_bit_exact(m, n, k, opts, basis):
+    """The table bases with their operand sums formed on chip (fused kernel): <3,2,3> with up to
+    four FP32 source tiles per operand, fifteen products and destinations in the 3 x 3 C grid;
+    <2,3,2> with eleven products into the 2 x 2 C grid."""
     o = dict(opts)
     pads = o.pop("pads", (0, 0, 0))
     pads = (_pad4(k), _pad4(n), pads[2])
-    C, C64, _, _ = run(m, n, k, 1, "split3", dist="int", seed=81 * m + k, basis="b323", algo="fused",
+    C, C64, _, _ = run(m, n, k, 1, "split3", dist="int", seed=81 * m + k, basis=basis, algo="fused",
                        pads=pads, **o)
     np.testing.assert_array_equal(C, C64)
 
 
+@pytest.mark.parametrize("basis", ["b323", "b232"])
 @pytest.mark.parametrize("variant", ["split3", "plain_bf16"])
-def test_b323_fused_float(variant):
-    C, C64, An, Bn = run(600, 520, 400, 1, variant, seed=83, basis="b323", algo="fused",
+def test_table_basis_fused_float(variant, basis):
+    C, C64, An, Bn = run(600, 520, 400, 1, variant, seed=83, basis=basis, algo="fused",
                          pads=(_pad4(400), _pad4(520), 0))
     assert oracle.normwise_error(C, C64, An, Bn) <= tolerance(variant, 1, 400)
 
@@ -1018,7 +1031,8 @@ def test_full_size_int_sampled_rows_bit_exact(m, n, k, levels):
 # ------------------------------------------- store-first phases (beta = 0)
 @pytest.mark.parametrize("store_first", [True, False])
 @pytest.mark.parametrize("pad_c", [0, 1])
-@pytest.mark.parametrize("levels,basis", [(1, "strassen"), (2, "strassen"), (1, "winograd"), (1, "b323")])
+@pytest.mark.parametrize("levels,basis", [(1, "strassen"), (2, "strassen"), (1, "winograd"), (1, "b323"),
+                                          (1, "b232")])
 @pytest.mark.parametrize("m,n,k", [(300, 520, 200), (129, 257, 65), (1000, 1200, 300), (520, 8, 400)])
 def test_store_first_phases_bit_exact(m, n, k, levels, basis, pad_c, store_first):
     """beta = 0: the products run in launch phases whose first update of each C block is a
@@ -1030,7 +1044,7 @@ def test_store_first_phases_bit_exact(m, n, k, levels, basis, pad_c, store_first
     np.testing.assert_array_equal(C, C64)
 
 
-@pytest.mark.parametrize("levels,basis", [(1, "strassen"), (2, "strassen"), (1, "b323")])
+@pytest.mark.parametrize("levels,basis", [(1, "strassen"), (2, "strassen"), (1, "b323"), (1, "b232")])
 @pytest.mark.parametrize("pad_c", [0, 1])
 @pytest.mark.parametrize("m,n,k", [(300, 520, 200), (1000, 1200, 300), (600, 2100, 96)])
 def test_store_first_in_ownership_mode_bit_exact(m, n, k, levels, basis, pad_c):

@@ -368,6 +368,30 @@ def test_b323_shape_of_the_scheme():
     assert int(np.count_nonzero(W, axis=0).max()) == 3   # at most three C blocks per product
 
 
+def test_b232_brent_equations_hold():
+    U, V, W = oracle.BASES["b232"]
+    assert U.shape == (6, 11) and V.shape == (6, 11) and W.shape == (4, 11)
+    assert oracle.brent_residual_grid((2, 3, 2), U, V, W) == 0
+
+
+def test_b232_brent_detects_every_single_coefficient_change():
+    U, V, W = (M.copy() for M in oracle.BASES["b232"])
+    for M in (U, V, W):
+        for idx in itertools.product(range(M.shape[0]), range(11)):
+            old = M[idx]
+            for new in {-1, 0, 1} - {old}:
+                M[idx] = new
+                assert oracle.brent_residual_grid((2, 3, 2), U, V, W) > 0
+            M[idx] = old
+
+
+def test_b232_shape_of_the_scheme():
+    U, V, W = oracle.BASES["b232"]
+    assert set(np.unique(np.concatenate([U.ravel(), V.ravel(), W.ravel()]))) <= {-1, 0, 1}
+    assert [int(np.count_nonzero(M)) for M in (U, V, W)] == [16, 16, 16]
+    assert int(np.count_nonzero(W, axis=0).max()) == 2   # at most two C blocks per product
+
+
 def test_grid_block_rule():
     assert oracle.grid_block(16384, 3) == 5464
     assert oracle.grid_block(16384, 2) == oracle.block_size(16384, 1) == 8192
@@ -378,11 +402,12 @@ def test_grid_block_rule():
 
 @pytest.mark.parametrize("m,n,k", [(18, 18, 12), (7, 11, 5), (64, 40, 33), (3, 200, 2), (100, 1, 9)])
 @pytest.mark.parametrize("align", [1, 8])
-def test_b323_exact_on_small_integers(m, n, k, align):
+@pytest.mark.parametrize("basis", ["b323", "b232"])
+def test_table_bases_exact_on_small_integers(m, n, k, align, basis):
     A, B = synth.problem(m, n, k, seed=11 * m + n, dist="int")
     C = synth.small_int((m, n), 5)
     want = oracle.classical(A, B, C, alpha=2.0, beta=-3.0)
-    got = oracle.table_matmul(A, B, C, alpha=2.0, beta=-3.0, basis="b323", align=align)
+    got = oracle.table_matmul(A, B, C, alpha=2.0, beta=-3.0, basis=basis, align=align)
     np.testing.assert_array_equal(got, want)
 
 
@@ -399,8 +424,9 @@ def test_table_matmul_empty_and_beta_only():
     assert oracle.table_matmul(np.zeros((0, 4)), np.zeros((4, 3))).shape == (0, 3)
 
 
-def test_b323_float_agrees_with_classical_within_fp64_rounding():
+@pytest.mark.parametrize("basis", ["b323", "b232"])
+def test_table_bases_float_agree_with_classical_within_fp64_rounding(basis):
     A, B = synth.problem(96, 90, 64, seed=9, dist="uniform")
-    got = oracle.table_matmul(A, B, basis="b323")
+    got = oracle.table_matmul(A, B, basis=basis)
     want = oracle.classical(A, B)
     assert np.abs(got - want).max() <= 1e-12 * np.abs(A).max() * np.abs(B).max() * 64

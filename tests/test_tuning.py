@@ -150,6 +150,7 @@ def test_native_tuner_rejects_bad_arguments_without_gpu():
 
 def test_model_basis_shapes_and_default_unchanged():
     assert model.shape(1, "b323") == (3, 2, 3, 15, 2.0)
+    assert model.shape(1, "b232")[:4] == (2, 3, 2, 11)
     assert model.shape(2, "strassen")[:4] == (4, 4, 4, 49)
     assert model.block(16384, 1, 3) == 5464
     for d in (4096, 16384):
@@ -223,3 +224,18 @@ def test_model_tile_samples_and_ranking():
     for d, meas in by_size.items():
         first = model.rank_candidates(d)[0]
         assert meas[first] <= 1.05 * min(meas.values()), (d, first, meas)
+
+
+def test_model_phases_match_the_library_plan():
+    """The model's store-first phase sizes are the library's own plan (fmm_store_phases)."""
+    import ctypes
+    import numpy as np
+    lib = fmm.load()
+    lib.fmm_store_phases.restype = ctypes.c_int
+    lib.fmm_store_phases.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    for (levels, basis), sizes in model._PHASES.items():
+        gm, gk, gn, R = fmm.basis_shape(levels, basis)
+        phase = np.zeros(R, dtype=np.int32)
+        store = np.zeros(gm * gn * R, dtype=np.int8)
+        nph = lib.fmm_store_phases(levels, fmm.BASES[basis], phase.ctypes.data, store.ctypes.data)
+        assert tuple(int(np.count_nonzero(phase == p)) for p in range(nph)) == tuple(sizes), (levels, basis)
