@@ -326,7 +326,7 @@ fmm_status fmm_debug_wait_timeout(void* stream);
  * Source: Section 3, Eq. (3), and its Kronecker power for Section 3.4. */
 int fmm_product_table(int levels, int8_t* U, int8_t* V, int8_t* W);
 /* As fmm_product_table for a basis (fmm_options.basis: 0 Strassen, 1 Strassen-Winograd,
- * 2 the <3,2,3> basis of rank 15).  With the basis's block grid (g_m, g_k, g_n) and its R
+ * 2 the <3,2,3> basis of rank 15, 3 the <2,3,2> basis of rank 11).  With the basis's block grid (g_m, g_k, g_n) and its R
  * products (fmm_basis_shape): U[(i * g_k + l) * R + r] is the coefficient of A block (i, l)
  * in product r, V[(l * g_n + j) * R + r] that of B block (l, j), W[(i * g_n + j) * R + r]
  * that of product r in C block (i, j); U holds g_m g_k R entries, V g_k g_n R, W g_m g_n R.
@@ -343,7 +343,8 @@ int fmm_product_table_ex(int levels, int basis, int8_t* U, int8_t* V, int8_t* W)
 int fmm_store_phases(int levels, int basis, int* phase_of, int8_t* store);
 /* Block grid and product count of `levels` levels of a basis: dims[0..3] = g_m, g_k, g_n,
  * R (levels 0: 1, 1, 1, 1; Strassen and Strassen-Winograd: 2^L, 2^L, 2^L, 7^L; basis 2 at
- * one level: 3, 2, 3, 15).  Returns 0, or -1 for a combination that is not built. */
+ * one level: 3, 2, 3, 15; basis 3 at one level: 2, 3, 2, 11).  Returns 0, or -1 for a
+ * combination that is not built. */
 int fmm_basis_shape(int levels, int basis, int* dims);
 
 /* Phase timing.  While enabled, each launch of a phase -- 0: beta pass,
